@@ -1,0 +1,280 @@
+/*
+ * nnqs.h -- C ABI of the GB300 (sm_103a) library for the local-energy hot
+ * path of the transformer neural-network quantum state method (arXiv
+ * 2306.16705, "NNQS-Transformer").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Bitstrings are packed into W = ceil(N/64) little-endian uint64 words:
+ *   qubit j is bit (j % 64) of word (j / 64); a bitstring occupies W
+ *   consecutive words.  Qubit 2p is the alpha spin orbital of spatial
+ *   orbital p and qubit 2p+1 its beta partner (Sec. 3.3, interleaved
+ *   Jordan-Wigner order).  |1> = occupied.  N <= 128.
+ * - log psi is stored as two doubles per state: (log|psi|, phase), so
+ *   psi = exp(log|psi| + i phase) (Sec. 3.1 writes psi = |psi| e^{i phi}).
+ * - Complex outputs are two doubles (Re, Im).
+ * - "device" pointers are CUDA device pointers owned by the caller; "host"
+ *   pointers are ordinary host memory owned by the caller.  Opaque handles
+ *   are owned by the library and released by the matching *_free.
+ * - Calls taking a stream enqueue their work on it and return without
+ *   waiting, unless their comment says they synchronise.  Argument errors
+ *   are returned synchronously; errors the GPU detects (a sample outside the
+ *   electron-number sector, a duplicate sample, a full hash table, a
+ *   non-finite value) are written to a status word at the start of the
+ *   caller's workspace and read with nnqs_workspace_status().
+ * - Workspace: every call that needs scratch device memory takes a
+ *   caller-allocated device buffer `workspace` of at least the size its
+ *   *_workspace_size function returns (256-byte aligned).  The library
+ *   itself allocates device memory only in nnqs_build_pauli and
+ *   nnqs_sample (documented there).
+ * - No exception crosses the ABI.  nnqs_last_error() returns a thread-local
+ *   message for the last non-OK status returned on this thread.
+ */
+#ifndef NNQS_H
+#define NNQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *nnqs_stream; /* a cudaStream_t; NULL = default stream */
+
+typedef enum {
+    NNQS_OK = 0,
+    NNQS_E_INVAL = 1,        /* bad argument (null pointer, size, unsupported shape) */
+    NNQS_E_NOMEM = 2,        /* host or device allocation failed */
+    NNQS_E_CUDA = 3,         /* a CUDA runtime call failed */
+    NNQS_E_TABLE_FULL = 4,   /* a bounded hash probe ran out of slots */
+    NNQS_E_TIMEOUT = 5,      /* a bounded device wait gave up */
+    NNQS_E_SECTOR = 6,       /* a sample breaks the (n_alpha, n_beta) sector */
+    NNQS_E_NONFINITE = 7,    /* NaN or Inf met in an input or result */
+    NNQS_E_UNSUPPORTED = 8,  /* valid request this build does not implement */
+    NNQS_E_DUPLICATE = 9,    /* the sample table holds a bitstring twice */
+    NNQS_E_WORKSPACE = 10    /* workspace null, misaligned or too small */
+} nnqs_status;
+
+/* nnqs_eloc modes (Sec. 3.4 (4)): NNQS_SA sums over x' in the sample table
+ * S only (the paper's sample-aware scheme); NNQS_EXACT sums over every x'
+ * with H_{x x'} != 0 structurally (Eq. Eloc as written). */
+enum { NNQS_SA = 0, NNQS_EXACT = 1 };
+
+/* Arithmetic of the ansatz: NNQS_FP64 = FP64 everywhere (the plain path);
+ * NNQS_MIXED = BF16 operands on tcgen05 tensor cores with FP32 accumulation
+ * and FP32 normalisation/softmax; NNQS_FP32 = FP32 CUDA cores.  Local-energy
+ * ratios, sums and statistics are FP64 in every mode. */
+enum { NNQS_FP64 = 0, NNQS_MIXED = 1, NNQS_FP32 = 2 };
+
+/* nnqs_eloc flags: choice of the sample-aware sweep.  GROUPS walks the
+ * X/Y-mask groups for every sample (Alg. 2); PAIRS walks sample pairs and
+ * looks the pair's X/Y mask up in a group hash; AUTO picks the cheaper by
+ * their pair counts.  Both give the same sum. */
+enum { NNQS_SWEEP_AUTO = 0, NNQS_SWEEP_GROUPS = 1, NNQS_SWEEP_PAIRS = 2 };
+
+const char *nnqs_last_error(void);
+const char *nnqs_status_string(int status);
+const char *nnqs_version(void);
+
+/* Reads the device status word at the head of `workspace` (synchronises
+ * `stream` first).  Returns NNQS_OK or the first error a kernel recorded;
+ * `bad_index` (host, may be NULL) receives the offending row or -1. */
+nnqs_status nnqs_workspace_status(const void *workspace, nnqs_stream stream, int64_t *bad_index);
+
+/* ------------------------------------------------------------------ */
+/* Hamiltonian: Eq. (eham) -> Jordan-Wigner Pauli strings, Eq. (sham),  */
+/* merged, coefficient-folded and grouped by X/Y mask as in Alg. 1 and  */
+/* Sec. 3.4 (1).                                                         */
+/* ------------------------------------------------------------------ */
+typedef struct nnqs_ham nnqs_ham;
+
+/* Builds H = e_core + sum_{pq,s} h[p][q] a+_{ps} a_{qs}
+ *          + 1/2 sum_{pqrs,s,t} eri[p][q][r][s] a+_{ps} a+_{rt} a_{st} a_{qs}
+ * (Eq. eham in chemist notation, real integrals), maps it by Jordan-Wigner
+ * (a+_j = Z_{<j}(X_j - iY_j)/2), merges equal strings, folds
+ * coef = Re(c) Re((-i)^{nY}) (Alg. 1), drops |coef| < drop_tol and groups
+ * the survivors by their X/Y mask.  Groups are in ascending X/Y-mask order
+ * and terms within a group in ascending Y/Z-mask order (most significant
+ * word first).
+ *   n_spatial   1..64 spatial orbitals (N = 2 n_spatial qubits)
+ *   h           host, n*n row-major, symmetric
+ *   eri         host, n^4 row-major (pq|rs), 8-fold symmetric
+ *   out         receives the handle; its tables are uploaded to the current
+ *               CUDA device (the library allocates them with cudaMalloc).
+ * Runs on the host (OpenMP) and synchronises the device once. */
+nnqs_status nnqs_build_pauli(int n_spatial, const double *h, const double *eri, double e_core,
+                             double drop_tol, nnqs_ham **out);
+
+/* nnqs_build_pauli without the device upload: the handle serves
+ * nnqs_ham_info, nnqs_ham_export and nnqs_coupled_host only (calls that need
+ * device tables return NNQS_E_INVAL).  Needs no GPU. */
+nnqs_status nnqs_build_pauli_host(int n_spatial, const double *h, const double *eri, double e_core,
+                                  double drop_tol, nnqs_ham **out);
+
+/* info[0..5] (host) = n_qubits, n_words W, n_terms N_h, n_groups N_XY,
+ * largest group size, device bytes held by the handle. */
+nnqs_status nnqs_ham_info(const nnqs_ham *H, int64_t info[6]);
+
+/* Host copies of the grouped tables (Alg. 1 output): xy[N_XY][W] group X/Y
+ * masks, off[N_XY+1] CSR term offsets, yz[N_h][W] term Y/Z masks, coef[N_h]
+ * folded coefficients.  Any pointer may be NULL to skip that table. */
+nnqs_status nnqs_ham_export(const nnqs_ham *H, uint64_t *xy, int64_t *off, uint64_t *yz,
+                            double *coef);
+
+void nnqs_ham_free(nnqs_ham *H);
+
+/* ------------------------------------------------------------------ */
+/* Ansatz: transformer amplitude + MLP phase (Sec. 3.1), number mask    */
+/* (Sec. 3.3).                                                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_qubits;     /* N, even, <= 128 */
+    int32_t n_alpha;      /* electrons of each spin (mask of Sec. 3.3) */
+    int32_t n_beta;
+    int32_t d_model;      /* embedding width d, multiple of n_heads */
+    int32_t n_layers;     /* decoder layers */
+    int32_t n_heads;
+    int32_t phase_hidden; /* phase MLP width (N x H x H x 1) */
+    int32_t reserved;     /* must be 0 */
+} nnqs_model_cfg;
+
+typedef struct nnqs_model nnqs_model;
+
+/* Parameters live in ONE caller-owned FP32 device array in this order
+ * (Linear weights [out][in], row-major):
+ *   tok_emb[5][d] pos_emb[T][d]                       (T = N/2)
+ *   per layer l: ln1.g[d] ln1.b[d] attn.wqkv[3d][d] attn.bqkv[3d]
+ *                attn.wo[d][d] attn.bo[d] ln2.g[d] ln2.b[d]
+ *                ffn.w1[4d][d] ffn.b1[4d] ffn.w2[d][4d] ffn.b2[d]
+ *   lnf.g[d] lnf.b[d] head.w[4][d] head.b[4]
+ *   phase.w1[H][N] phase.b1[H] phase.w2[H][H] phase.b2[H] phase.w3[1][H] phase.b3[1]
+ * The network: token t holds spatial orbital n-1-t as 2*y_beta + y_alpha;
+ * the input sequence is a start token (id 4) then tokens 0..T-2; pre-LN
+ * decoder layers with causal multi-head attention and a 4d erf-GELU FFN;
+ * final LayerNorm (eps 1e-5); a d->4 head; the Sec. 3.3 mask (caps and
+ * reachability) and a renormalised softmax give pi~(x_t | x_<t);
+ * log|psi| = 1/2 sum_t log pi~; phase = MLP(x) with ReLU on the 0/1
+ * occupations in qubit order. */
+nnqs_status nnqs_model_create(const nnqs_model_cfg *cfg, nnqs_model **out);
+void nnqs_model_free(nnqs_model *M);
+int64_t nnqs_model_param_count(const nnqs_model *M);
+/* offset/numel (host) of the named tensor, names as listed above */
+nnqs_status nnqs_model_param_offset(const nnqs_model *M, const char *name, int64_t *offset,
+                                    int64_t *numel);
+
+size_t nnqs_logpsi_workspace_size(const nnqs_model *M, int64_t n, int prec);
+
+/* (log|psi|, phase) of n packed bitstrings x (device, [n][W]) into out
+ * (device, [n][2] double).  A bitstring outside the sector gets
+ * log|psi| = -inf and sets NNQS_E_SECTOR in the workspace status. */
+nnqs_status nnqs_logpsi(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n,
+                        int prec, double *out, void *workspace, size_t workspace_bytes,
+                        nnqs_stream stream);
+
+size_t nnqs_logpsi_backward_workspace_size(const nnqs_model *M, int64_t n, int prec);
+
+/* Reverse mode of nnqs_logpsi:
+ *   grad = sum_i seed[i][0] d log|psi_i| / d theta + seed[i][1] d phase_i / d theta
+ * seed device [n][2] double.  The gradient is written (overwritten) to
+ * grad_f64 (device, double [P]) and/or grad_f32 (device, float [P]); at
+ * least one must be non-NULL.  Accumulation is in FP64 for NNQS_FP64 and
+ * FP32 otherwise.  Recomputes the forward (no activations are kept between
+ * calls); samples are processed in chunks whose activations fit the
+ * workspace. */
+nnqs_status nnqs_logpsi_backward(const nnqs_model *M, const float *params, const uint64_t *x,
+                                 int64_t n, int prec, const double *seed, double *grad_f64,
+                                 float *grad_f32, void *workspace, size_t workspace_bytes,
+                                 nnqs_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Local energy, Eq. (Eloc), with Alg. 2's fused evaluation (Sec. 3.4).  */
+/* ------------------------------------------------------------------ */
+size_t nnqs_eloc_workspace_size(const nnqs_ham *H, const nnqs_model *M, int64_t n_lut,
+                                int64_t n_rows, int mode, int prec);
+
+/* E_loc(x) = sum_{x'} H_{x x'} psi(x')/psi(x) for x = lut[row_begin + i],
+ * i < n_rows, written to eloc_out (device, [n_rows][2] double).
+ *   lut         device [n_lut][W]: the unique samples S (any order, no
+ *               duplicates, all in the (n_alpha, n_beta) sector)
+ *   lut_logpsi  device [n_lut][2]: (log|psi|, phase) of each lut row; read
+ *               in NNQS_SA mode, ignored in NNQS_EXACT mode
+ *   M, params   the ansatz; required in NNQS_EXACT mode (log psi of every
+ *               coupled x' and of x is computed with precision `prec`),
+ *               ignored in NNQS_SA mode (may be NULL)
+ *   flags       NNQS_SWEEP_* (NNQS_SA only)
+ * NNQS_EXACT synchronises once to size the forward over the unique coupled
+ * set; NNQS_SA is fully asynchronous. */
+nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *params,
+                      const uint64_t *lut, const double *lut_logpsi, int64_t n_lut,
+                      int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int mode,
+                      int prec, int flags, double *eloc_out, void *workspace,
+                      size_t workspace_bytes, nnqs_stream stream);
+
+/* Coupled set of one row (parity and debugging): every x' = x ^ m over the
+ * groups m that keep the sector, in group order, with H_{x x'} (host
+ * outputs, at most `cap` entries; *count receives the number).  Host-side,
+ * synchronous. */
+nnqs_status nnqs_coupled_host(const nnqs_ham *H, const uint64_t *x, int n_alpha, int n_beta,
+                              uint64_t *xp, double *hxx, int64_t cap, int64_t *count);
+
+/* ------------------------------------------------------------------ */
+/* Energy, variance and gradient (Sec. 2.1, Eqs. energy and the          */
+/* gradient estimator).                                                  */
+/* ------------------------------------------------------------------ */
+size_t nnqs_energy_stats_workspace_size(int64_t n);
+
+/* stats (device, 4 doubles) = Re E, Im E, Var, sum w with
+ * E = sum_i w_i E_loc,i / sum_i w_i and Var = sum_i w_i |E_loc,i - E|^2 / sum w.
+ * eloc device [n][2]; weights device [n] uint64 sample counts. */
+nnqs_status nnqs_energy_stats(const double *eloc, const uint64_t *weights, int64_t n,
+                              double *stats, void *workspace, size_t workspace_bytes,
+                              nnqs_stream stream);
+
+size_t nnqs_energy_grad_workspace_size(const nnqs_ham *H, const nnqs_model *M, int64_t n_u,
+                                       int prec);
+
+/* One energy/gradient evaluation on the unique samples S with counts w:
+ * log psi(S) -> sample-aware E_loc (Alg. 2) -> stats -> gradient
+ * grad = 2 Re sum_i w_i (E_loc,i - E) d ln psi_i^* / sum w  (Sec. 2.1, with
+ * E_loc held fixed and E the complex weighted mean).  Outputs (device):
+ * stats[4] as nnqs_energy_stats, eloc_out [n_u][2] (may be NULL),
+ * grad_f64 / grad_f32 as nnqs_logpsi_backward (at least one non-NULL). */
+nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, const float *params,
+                             const uint64_t *samples, const uint64_t *weights, int64_t n_u,
+                             int prec, double *stats, double *eloc_out, double *grad_f64,
+                             float *grad_f32, void *workspace, size_t workspace_bytes,
+                             nnqs_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Batch autoregressive sampling (Sec. 3.1 BAS, mask of Sec. 3.3).       */
+/* ------------------------------------------------------------------ */
+size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec);
+
+/* Draws n_samples samples from |psi|^2 as unique bitstrings with counts:
+ * at each of the T steps every unique prefix with weight w splits w over
+ * its 4 children by a multinomial draw from pi~ (sequential binomials on a
+ * Philox4x32-10 counter stream keyed by (seed, step, prefix)); zero-weight
+ * children are pruned.  Outputs (device) samples_out [max_unique][W] and
+ * weights_out [max_unique]; *n_unique_out (host) = unique samples written,
+ * sorted ascending.  Returns NNQS_E_TABLE_FULL if a step holds more than
+ * max_unique prefixes.  Synchronises the stream once per step (the width
+ * of the next step is data-dependent). */
+nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uint64_t n_samples,
+                        uint64_t seed, int prec, int64_t max_unique, uint64_t *samples_out,
+                        uint64_t *weights_out, int64_t *n_unique_out, void *workspace,
+                        size_t workspace_bytes, nnqs_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Optimiser step.                                                       */
+/* ------------------------------------------------------------------ */
+/* Adam (no weight decay), in place on device FP32 arrays of length n;
+ * `step` is the 1-based count after this update. */
+nnqs_status nnqs_adam_step(float *params, const float *grad, float *m, float *v, int64_t n,
+                           int64_t step, double lr, double beta1, double beta2, double eps,
+                           nnqs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNQS_H */

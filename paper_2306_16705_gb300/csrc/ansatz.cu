@@ -1,0 +1,1247 @@
+// Ansatz of Sec. 3.1 (transformer amplitude + MLP phase) with the number
+// mask of Sec. 3.3: forward log psi and its reverse mode, on CUDA cores,
+// templated over the arithmetic type R (double for NNQS_FP64, float for
+// NNQS_FP32 and for the non-GEMM parts of NNQS_MIXED).
+//
+// Layout: activations of a chunk of C samples are row-major [C*T][width]
+// (one row per token).  The FP32 parameters are converted once per call to
+// R in the workspace.  Samples are processed in chunks so that the saved
+// activations of one chunk fit the workspace; weight gradients accumulate
+// across chunks in R.
+//
+// Reductions over samples (weight and bias gradients) run with split-K /
+// split-row partial buffers summed in a fixed order: results do not depend
+// on scheduling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "dev_common.cuh"
+#include "model.h"
+#include "tc_gemm.h"
+
+namespace nnqs {
+namespace {
+
+// ------------------------------------------------------------------ math
+template <class R>
+__device__ __forceinline__ R erf_(R x);
+template <>
+__device__ __forceinline__ double erf_<double>(double x) { return erf(x); }
+template <>
+__device__ __forceinline__ float erf_<float>(float x) { return erff(x); }
+template <class R>
+__device__ __forceinline__ R exp_(R x);
+template <>
+__device__ __forceinline__ double exp_<double>(double x) { return exp(x); }
+template <>
+__device__ __forceinline__ float exp_<float>(float x) { return expf(x); }
+template <class R>
+__device__ __forceinline__ R log_(R x);
+template <>
+__device__ __forceinline__ double log_<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float log_<float>(float x) { return logf(x); }
+template <class R>
+__device__ __forceinline__ R rsqrt_(R x);
+template <>
+__device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+template <class R>
+__device__ __forceinline__ R gelu_(R x) {
+    return R(0.5) * x * (R(1) + erf_<R>(x * R(0.70710678118654752440)));
+}
+template <class R>
+__device__ __forceinline__ R gelu_grad_(R x) {
+    return R(0.5) * (R(1) + erf_<R>(x * R(0.70710678118654752440))) +
+           x * exp_<R>(R(-0.5) * x * x) * R(0.39894228040143267794);
+}
+
+template <class R>
+__device__ __forceinline__ R neg_inf() {
+    return -R(INFINITY);
+}
+
+__device__ __forceinline__ int bit_of(const uint64_t *x, int j) { return (int)((x[j >> 6] >> (j & 63)) & 1ull); }
+
+// token at position t of a bitstring: spatial orbital p = T-1-t,
+// value y_alpha + 2 y_beta (Sec. 3.3, reverse order)
+__device__ __forceinline__ int token_at(const uint64_t *x, int T, int t) {
+    const int p = T - 1 - t;
+    return bit_of(x, 2 * p) + 2 * bit_of(x, 2 * p + 1);
+}
+
+// ------------------------------------------------------------------ small kernels
+template <class R>
+__global__ void k_convert_params(const float *__restrict__ src, R *__restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (R)src[i];
+}
+
+template <class R>
+__global__ void k_fill(R *__restrict__ p, int64_t n, R v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// h[(i*T+t)*d + c] = tok_emb[inp][c] + pos_emb[t][c]; tok[i*T+t] = token t
+// (S = sequence length, <= T; prefixes of length S-1 use S = their length + 1)
+template <class R>
+__global__ void k_embed(const uint64_t *__restrict__ x, int W, int64_t n, int S, int T, int d,
+                        const R *__restrict__ tok_emb, const R *__restrict__ pos_emb, R *__restrict__ h,
+                        uint8_t *__restrict__ tok) {
+    const int64_t total = n * S * d;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % d);
+        const int t = (int)((idx / d) % S);
+        const int64_t i = idx / ((int64_t)S * d);
+        const uint64_t *xi = x + i * W;
+        const int inp = t == 0 ? 4 : token_at(xi, T, t - 1);
+        h[idx] = tok_emb[inp * d + c] + pos_emb[t * d + c];
+        if (c == 0) tok[i * S + t] = (uint8_t)token_at(xi, T, t);
+    }
+}
+
+// ------------------------------------------------------------------ LayerNorm
+constexpr int kMaxDPerLane = 8;  // d <= 256
+
+template <class R>
+__global__ void k_ln_fwd(const R *__restrict__ x, const R *__restrict__ g, const R *__restrict__ b, R *__restrict__ y,
+                         R *__restrict__ mean, R *__restrict__ rstd, int64_t rows, int d) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const R *xr = x + row * d;
+    R v[kMaxDPerLane];
+    R s = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxDPerLane; ++k) {
+        const int c = lane + 32 * k;
+        v[k] = c < d ? xr[c] : R(0);
+        s += v[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const R mu = s / R(d);
+    R q = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxDPerLane; ++k) {
+        const int c = lane + 32 * k;
+        const R z = c < d ? v[k] - mu : R(0);
+        q += z * z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const R rs = R(1) / sqrt(q / R(d) + R(1e-5));
+#pragma unroll
+    for (int k = 0; k < kMaxDPerLane; ++k) {
+        const int c = lane + 32 * k;
+        if (c < d) y[row * d + c] = (v[k] - mu) * rs * g[c] + b[c];
+    }
+    if (lane == 0) {
+        if (mean) mean[row] = mu;
+        if (rstd) rstd[row] = rs;
+    }
+}
+
+// dx of LayerNorm, added into acc: acc += rstd (dxh - mean(dxh) - xh mean(dxh xh)), dxh = dy g
+template <class R>
+__global__ void k_ln_bwd(const R *__restrict__ x, const R *__restrict__ mean, const R *__restrict__ rstd,
+                         const R *__restrict__ g, const R *__restrict__ dy, R *__restrict__ acc, int64_t rows, int d) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const R mu = mean[row], rs = rstd[row];
+    R xh[kMaxDPerLane], dxh[kMaxDPerLane];
+    R s1 = 0, s2 = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxDPerLane; ++k) {
+        const int c = lane + 32 * k;
+        if (c < d) {
+            xh[k] = (x[row * d + c] - mu) * rs;
+            dxh[k] = dy[row * d + c] * g[c];
+        } else {
+            xh[k] = dxh[k] = 0;
+        }
+        s1 += dxh[k];
+        s2 += dxh[k] * xh[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    s1 /= R(d);
+    s2 /= R(d);
+#pragma unroll
+    for (int k = 0; k < kMaxDPerLane; ++k) {
+        const int c = lane + 32 * k;
+        if (c < d) acc[row * d + c] += rs * (dxh[k] - s1 - xh[k] * s2);
+    }
+}
+
+// ------------------------------------------------------------------ column reductions
+// partial[blk][c] = sum over this block's rows of f(row, c); modes:
+//   0: A[r][c]                 (bias gradients)
+//   1: A[r][c] * xh(r, c)      (LayerNorm gain gradient, xh from X, mean, rstd)
+constexpr int kColThreads = 256;
+
+template <class R, int MODE>
+__global__ void k_colred(const R *__restrict__ A, const R *__restrict__ X, const R *__restrict__ mean,
+                         const R *__restrict__ rstd, int64_t rows, int cols, int64_t rows_per_block,
+                         R *__restrict__ partial) {
+    __shared__ R sh[kColThreads];
+    const int64_t r0 = blockIdx.x * rows_per_block;
+    const int64_t r1 = min(rows, r0 + rows_per_block);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int cb = 0; cb < cols; cb += 32) {
+        const int c = cb + lane;
+        R s = 0;
+        if (c < cols) {
+            for (int64_t r = r0 + warp; r < r1; r += kColThreads / 32) {
+                R v = A[r * cols + c];
+                if (MODE == 1) v *= (X[r * cols + c] - mean[r]) * rstd[r];
+                s += v;
+            }
+        }
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        if (warp == 0) {
+            R t = 0;
+            for (int w = 0; w < kColThreads / 32; ++w) t += sh[w * 32 + lane];
+            if (c < cols) partial[blockIdx.x * (int64_t)cols + c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[c] += sum_b partial[b][c]
+template <class R>
+__global__ void k_sum_partials(const R *__restrict__ partial, int64_t nblk, int64_t cols, R *__restrict__ out) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    R s = 0;
+    for (int64_t b = 0; b < nblk; ++b) s += partial[b * cols + c];
+    out[c] += s;
+}
+
+// ------------------------------------------------------------------ GEMM (CUDA cores)
+// C[m][n] = sum_k A(m,k) B(n,k), A(m,k) = A[m*sAm + k*sAk], B(n,k) = B[n*sBn + k*sBk],
+// then an epilogue.  Tile 64x64x16, 256 threads, 4x4 outputs per thread.
+enum Epi { EPI_STORE = 0, EPI_GELU = 1, EPI_RELU = 2, EPI_RESID = 3, EPI_ACCUM = 4 };
+constexpr int GM = 64, GN = 64, GK = 16;
+
+template <class R>
+struct GemmArgs {
+    const R *A;
+    int64_t sAm, sAk;
+    const R *B;
+    int64_t sBn, sBk;
+    R *C;
+    int64_t ldc;
+    R *C2;           // EPI_GELU / EPI_RELU: activation output
+    const R *bias;   // [N] or null
+    const R *resid;  // EPI_RESID: C = resid + acc + bias
+    int64_t M, N, K;
+    int64_t kchunk;  // split-K chunk
+    R *partial;      // split-K partials [splits][M][N] or null
+};
+
+template <class R, int EPI>
+__device__ __forceinline__ void epilogue(const GemmArgs<R> &g, int64_t m, int64_t n, R acc) {
+    const int64_t o = m * g.ldc + n;
+    const R bv = g.bias ? g.bias[n] : R(0);
+    if (EPI == EPI_STORE) {
+        g.C[o] = acc + bv;
+    } else if (EPI == EPI_GELU) {
+        const R v = acc + bv;
+        g.C[o] = v;
+        g.C2[o] = gelu_<R>(v);
+    } else if (EPI == EPI_RELU) {
+        const R v = acc + bv;
+        g.C[o] = v;
+        g.C2[o] = v > R(0) ? v : R(0);
+    } else if (EPI == EPI_RESID) {
+        g.C[o] = g.resid[o] + acc + bv;
+    } else {
+        g.C[o] += acc;
+    }
+}
+
+template <class R, int EPI>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs<R> g) {
+    __shared__ R As[GK][GM + 1];
+    __shared__ R Bs[GK][GN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = blockIdx.y * (int64_t)GM, n0 = blockIdx.x * (int64_t)GN;
+    const int64_t k_begin = blockIdx.z * g.kchunk;
+    const int64_t k_end = min(g.K, k_begin + g.kchunk);
+    const bool a_kfast = g.sAk == 1, b_kfast = g.sBk == 1;
+    R acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += GK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = threadIdx.x + 256 * r;
+            int mm, kk;
+            if (a_kfast) {
+                kk = e % GK;
+                mm = e / GK;
+            } else {
+                mm = e % GM;
+                kk = e / GM;
+            }
+            const int64_t m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < g.M && k < k_end) ? g.A[m * g.sAm + k * g.sAk] : R(0);
+            int nn, kb;
+            if (b_kfast) {
+                kb = e % GK;
+                nn = e / GK;
+            } else {
+                nn = e % GN;
+                kb = e / GN;
+            }
+            const int64_t n = n0 + nn, k2 = k0 + kb;
+            Bs[kb][nn] = (n < g.N && k2 < k_end) ? g.B[n * g.sBn + k2 * g.sBk] : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            R a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m >= g.M || n >= g.N) continue;
+            if (g.partial)
+                g.partial[(blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
+            else
+                epilogue<R, EPI>(g, m, n, acc[i][j]);
+        }
+}
+
+template <class R, int EPI>
+__global__ void k_gemm_reduce(GemmArgs<R> g, int64_t splits) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= g.M * g.N) return;
+    const int64_t m = idx / g.N, n = idx % g.N;
+    R s = 0;
+    for (int64_t z = 0; z < splits; ++z) s += g.partial[z * g.M * g.N + idx];
+    epilogue<R, EPI>(g, m, n, s);
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
+// Scratch for split-K partials and column reductions (elements of R).
+template <class R>
+struct Scratch {
+    R *buf;
+    size_t elems;
+};
+
+template <class R>
+nnqs_status gemm(cudaStream_t s, int epi, const R *A, int64_t sAm, int64_t sAk, const R *B, int64_t sBn, int64_t sBk,
+                 R *C, int64_t ldc, R *C2, const R *bias, const R *resid, int64_t M, int64_t N, int64_t K,
+                 Scratch<R> scr) {
+    if (M == 0 || N == 0) return NNQS_OK;
+    GemmArgs<R> g{A, sAm, sAk, B, sBn, sBk, C, ldc, C2, bias, resid, M, N, K, K, nullptr};
+    const int64_t tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+    int64_t splits = 1;
+    if (tiles < 2 * sm_count() && K > 4 * GK * 16) {
+        splits = std::min<int64_t>((2 * sm_count() + tiles - 1) / tiles, (K + 255) / 256);
+        splits = std::min<int64_t>(splits, (int64_t)(scr.elems / size_t(M * N)));
+        splits = std::max<int64_t>(splits, 1);
+    }
+    if (splits > 1) {
+        g.kchunk = (((K + splits - 1) / splits) + GK - 1) / GK * GK;
+        splits = (K + g.kchunk - 1) / g.kchunk;
+        g.partial = scr.buf;
+    }
+    dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM), (unsigned)splits);
+#define NNQS_GEMM_CASE(E)                                                                 \
+    case E:                                                                               \
+        k_gemm<R, E><<<grid, 256, 0, s>>>(g);                                             \
+        if (splits > 1) {                                                                 \
+            NNQS_CUDA_TRY(cudaGetLastError());                                            \
+            k_gemm_reduce<R, E><<<grid_for(M * N, 256), 256, 0, s>>>(g, splits);          \
+        }                                                                                 \
+        break;
+    switch (epi) {
+        NNQS_GEMM_CASE(EPI_STORE)
+        NNQS_GEMM_CASE(EPI_GELU)
+        NNQS_GEMM_CASE(EPI_RELU)
+        NNQS_GEMM_CASE(EPI_RESID)
+        NNQS_GEMM_CASE(EPI_ACCUM)
+        default: return set_error(NNQS_E_INVAL, "bad GEMM epilogue");
+    }
+#undef NNQS_GEMM_CASE
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+// Y[rows][out] (epilogue) = X[rows][in] W[out][in]^T
+template <class R>
+nnqs_status linear_fwd(cudaStream_t s, int epi, const R *X, int64_t rows, int64_t in, const R *Wt, int64_t out,
+                       const R *bias, R *Y, R *Y2, const R *resid, Scratch<R> scr) {
+    return gemm<R>(s, epi, X, in, 1, Wt, in, 1, Y, out, Y2, bias, resid, rows, out, in, scr);
+}
+// dX[rows][in] (= or +=) dY[rows][out] W[out][in]
+template <class R>
+nnqs_status linear_dx(cudaStream_t s, int epi, const R *dY, int64_t rows, int64_t out, const R *Wt, int64_t in, R *dX,
+                      Scratch<R> scr) {
+    return gemm<R>(s, epi, dY, out, 1, Wt, 1, in, dX, in, nullptr, nullptr, nullptr, rows, in, out, scr);
+}
+// dW[out][in] += dY[rows][out]^T X[rows][in]
+template <class R>
+nnqs_status linear_dw(cudaStream_t s, const R *dY, int64_t rows, int64_t out, const R *X, int64_t in, R *dW,
+                      Scratch<R> scr) {
+    return gemm<R>(s, EPI_ACCUM, dY, 1, out, X, 1, in, dW, in, nullptr, nullptr, nullptr, out, in, rows, scr);
+}
+
+template <class R>
+nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *mean, const R *rstd, int64_t rows,
+                   int cols, R *out, Scratch<R> scr) {
+    if (rows == 0) return NNQS_OK;
+    int64_t nblk = std::min<int64_t>((rows + 255) / 256, 4 * sm_count());
+    nblk = std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(cols)));
+    nblk = std::max<int64_t>(nblk, 1);
+    const int64_t rpb = (rows + nblk - 1) / nblk;
+    nblk = (rows + rpb - 1) / rpb;
+    if (mode == 0)
+        k_colred<R, 0><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf);
+    else
+        k_colred<R, 1><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    k_sum_partials<R><<<grid_for(cols, 256), 256, 0, s>>>(scr.buf, nblk, cols, out);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+// ------------------------------------------------------------------ attention
+// One thread per (sample, head, query): causal softmax(q k^T / sqrt(dh)) v
+// with an online max/sum; also writes the log-sum-exp for the backward.
+template <class R, int DH>
+__global__ void k_attn_fwd(const R *__restrict__ qkv, R *__restrict__ o, R *__restrict__ lse, int64_t n, int T, int H,
+                           int d) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * H * T) return;
+    const int q = (int)(idx % T);
+    const int hh = (int)((idx / T) % H);
+    const int64_t i = idx / ((int64_t)T * H);
+    const R scale = R(1) / sqrt(R(DH));
+    const R *base = qkv + i * T * 3 * d;
+    R qv[DH], acc[DH];
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+        qv[c] = base[q * 3 * d + hh * DH + c] * scale;
+        acc[c] = 0;
+    }
+    R m = neg_inf<R>(), l = 0;
+    for (int j = 0; j <= q; ++j) {
+        const R *kj = base + j * 3 * d + d + hh * DH;
+        const R *vj = base + j * 3 * d + 2 * d + hh * DH;
+        R sc = 0;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
+        const R mn = sc > m ? sc : m;
+        const R corr = exp_<R>(m - mn);
+        const R p = exp_<R>(sc - mn);
+        l = l * corr + p;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) acc[c] = acc[c] * corr + p * vj[c];
+        m = mn;
+    }
+    const R inv = R(1) / l;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) o[(i * T + q) * d + hh * DH + c] = acc[c] * inv;
+    lse[idx] = m + log_<R>(l);
+}
+
+// dq for each query: dq = scale sum_j p_ij (dp_ij - D_i) k_j, dp_ij = do_i . v_j,
+// D_i = do_i . o_i
+template <class R, int DH>
+__global__ void k_attn_bwd_q(const R *__restrict__ qkv, const R *__restrict__ o, const R *__restrict__ lse,
+                             const R *__restrict__ dout, R *__restrict__ dqkv, R *__restrict__ Dbuf, int64_t n, int T,
+                             int H, int d) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * H * T) return;
+    const int q = (int)(idx % T);
+    const int hh = (int)((idx / T) % H);
+    const int64_t i = idx / ((int64_t)T * H);
+    const R scale = R(1) / sqrt(R(DH));
+    const R *base = qkv + i * T * 3 * d;
+    R qv[DH], dov[DH], dq[DH];
+    R D = 0;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+        qv[c] = base[q * 3 * d + hh * DH + c] * scale;
+        dov[c] = dout[(i * T + q) * d + hh * DH + c];
+        D += dov[c] * o[(i * T + q) * d + hh * DH + c];
+        dq[c] = 0;
+    }
+    Dbuf[idx] = D;
+    const R L = lse[idx];
+    for (int j = 0; j <= q; ++j) {
+        const R *kj = base + j * 3 * d + d + hh * DH;
+        const R *vj = base + j * 3 * d + 2 * d + hh * DH;
+        R sc = 0, dp = 0;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            sc += qv[c] * kj[c];
+            dp += dov[c] * vj[c];
+        }
+        const R ds = exp_<R>(sc - L) * (dp - D);
+#pragma unroll
+        for (int c = 0; c < DH; ++c) dq[c] += ds * kj[c];
+    }
+#pragma unroll
+    for (int c = 0; c < DH; ++c) dqkv[(i * T + q) * 3 * d + hh * DH + c] = dq[c] * scale;
+}
+
+// dk, dv for each key j: dv = sum_{i>=j} p_ij do_i, dk = scale sum_{i>=j} p_ij (dp_ij - D_i) q_i
+template <class R, int DH>
+__global__ void k_attn_bwd_kv(const R *__restrict__ qkv, const R *__restrict__ lse, const R *__restrict__ dout,
+                              const R *__restrict__ Dbuf, R *__restrict__ dqkv, int64_t n, int T, int H, int d) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * H * T) return;
+    const int j = (int)(idx % T);
+    const int hh = (int)((idx / T) % H);
+    const int64_t i = idx / ((int64_t)T * H);
+    const R scale = R(1) / sqrt(R(DH));
+    const R *base = qkv + i * T * 3 * d;
+    R kv[DH], vv[DH], dk[DH], dv[DH];
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+        kv[c] = base[j * 3 * d + d + hh * DH + c];
+        vv[c] = base[j * 3 * d + 2 * d + hh * DH + c];
+        dk[c] = dv[c] = 0;
+    }
+    const int64_t row0 = (i * H + hh) * T;
+    for (int q = j; q < T; ++q) {
+        const R *qq = base + q * 3 * d + hh * DH;
+        const R *dq = dout + (i * T + q) * d + hh * DH;
+        R sc = 0, dp = 0;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            sc += qq[c] * kv[c];
+            dp += dq[c] * vv[c];
+        }
+        const R p = exp_<R>(sc * scale - lse[row0 + q]);
+        const R ds = p * (dp - Dbuf[row0 + q]);
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            dv[c] += p * dq[c];
+            dk[c] += ds * qq[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+        dqkv[(i * T + j) * 3 * d + d + hh * DH + c] = dk[c] * scale;
+        dqkv[(i * T + j) * 3 * d + 2 * d + hh * DH + c] = dv[c];
+    }
+}
+
+// ------------------------------------------------------------------ head + masked log-softmax
+// One warp per sample, lanes over positions.  pi~ of the 4 children at each
+// position is stored for the backward; log|psi| = 1/2 sum_t log pi~(x_t).
+template <class R>
+__global__ void k_head(const uint64_t *__restrict__ x, int W, const R *__restrict__ hf, const R *__restrict__ hw,
+                       const R *__restrict__ hb, const uint8_t *__restrict__ tok, int64_t n, int T, int d,
+                       int n_alpha, int n_beta, R *__restrict__ pi, double2 *__restrict__ out, DevStatus *st,
+                       int64_t row_offset) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const uint64_t *xi = x + i * W;
+    R sum = 0;
+    bool bad = false;
+    for (int t = lane; t < T; t += 32) {
+        // electrons already placed on orbitals p' > p = T-1-t (tokens < t)
+        int ca = 0, cb = 0;
+        for (int p2 = T - t; p2 < T; ++p2) {
+            ca += bit_of(xi, 2 * p2);
+            cb += bit_of(xi, 2 * p2 + 1);
+        }
+        const int rem = T - 1 - t;
+        const R *hr = hf + (i * T + t) * d;
+        R z[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            R a = hb[v];
+            for (int c = 0; c < d; ++c) a += hr[c] * hw[v * d + c];
+            z[v] = a;
+        }
+        bool ok[4];
+        R zmax = neg_inf<R>();
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int a = ca + (v & 1), b = cb + (v >> 1);
+            ok[v] = a <= n_alpha && b <= n_beta && a + rem >= n_alpha && b + rem >= n_beta;
+            if (ok[v] && z[v] > zmax) zmax = z[v];
+        }
+        R se = 0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (ok[v]) se += exp_<R>(z[v] - zmax);
+        const R lse = zmax + log_<R>(se);
+        const int tk = tok[i * T + t];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) pi[(i * T + t) * 4 + v] = ok[v] ? exp_<R>(z[v] - lse) : R(0);
+        if (ok[tk])
+            sum += z[tk] - lse;
+        else
+            bad = true;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        const double la = bad ? -(double)INFINITY : 0.5 * (double)sum;
+        out[i].x = la;
+        if (bad) record_status(st, NNQS_E_SECTOR, row_offset + i);
+    }
+}
+
+// pi~(v | prefix) at position S-1 for each prefix (sampling): cond[i][4], FP64
+template <class R>
+__global__ void k_cond_last(const uint64_t *__restrict__ x, int W, const R *__restrict__ hf, const R *__restrict__ hw,
+                            const R *__restrict__ hb, int64_t n, int S, int T, int d, int n_alpha, int n_beta,
+                            double *__restrict__ cond, DevStatus *st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t *xi = x + i * W;
+    const int t = S - 1;
+    int ca = 0, cb = 0;
+    for (int p2 = T - t; p2 < T; ++p2) {
+        ca += bit_of(xi, 2 * p2);
+        cb += bit_of(xi, 2 * p2 + 1);
+    }
+    const int rem = T - 1 - t;
+    const R *hr = hf + (i * S + t) * d;
+    double z[4], zmax = -INFINITY;
+    bool ok[4], any = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        R a = hb[v];
+        for (int c = 0; c < d; ++c) a += hr[c] * hw[v * d + c];
+        z[v] = (double)a;
+        const int aa = ca + (v & 1), bb = cb + (v >> 1);
+        ok[v] = aa <= n_alpha && bb <= n_beta && aa + rem >= n_alpha && bb + rem >= n_beta;
+        if (ok[v]) {
+            any = true;
+            zmax = fmax(zmax, z[v]);
+        }
+    }
+    double se = 0.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        if (ok[v]) se += exp(z[v] - zmax);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) cond[i * 4 + v] = ok[v] ? exp(z[v] - zmax) / se : 0.0;
+    if (!any) record_status(st, NNQS_E_SECTOR, i);
+}
+
+// dz[(i*T+t)*4+v] = 1/2 dla_i ([v = x_t] - pi_v) on allowed children
+template <class R>
+__global__ void k_head_bwd(const R *__restrict__ pi, const uint8_t *__restrict__ tok, const double2 *__restrict__ seed,
+                           int64_t n, int T, R *__restrict__ dz) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * T * 4) return;
+    const int v = (int)(idx & 3);
+    const int64_t row = idx >> 2;
+    const int64_t i = row / T;
+    const R p = pi[idx];
+    const R g = R(0.5) * (R)seed[i].x;
+    dz[idx] = p > R(0) || (int)tok[row] == v ? g * (((int)tok[row] == v ? R(1) : R(0)) - p) : R(0);
+}
+
+// ------------------------------------------------------------------ phase MLP
+// z1[i][u] = b1[u] + sum over occupied qubits j of W1[u][j]; r1 = relu(z1)
+template <class R>
+__global__ void k_phase_in(const uint64_t *__restrict__ x, int W, int N, const R *__restrict__ w1,
+                           const R *__restrict__ b1, int64_t n, int P, R *__restrict__ z1, R *__restrict__ r1,
+                           R *__restrict__ xf) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * P) return;
+    const int u = (int)(idx % P);
+    const int64_t i = idx / P;
+    const uint64_t *xi = x + i * W;
+    R a = b1[u];
+    for (int j = 0; j < N; ++j)
+        if (bit_of(xi, j)) a += w1[(int64_t)u * N + j];
+    z1[idx] = a;
+    r1[idx] = a > R(0) ? a : R(0);
+    if (xf)
+        for (int j = u; j < N; j += P) xf[i * N + j] = (R)bit_of(xi, j);
+}
+
+// phase_i = b3 + sum_u r2[i][u] w3[u]  (one warp per sample)
+template <class R>
+__global__ void k_phase_out(const R *__restrict__ r2, const R *__restrict__ w3, const R *__restrict__ b3, int64_t n,
+                            int P, double2 *__restrict__ out) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    R s = 0;
+    for (int u = lane; u < P; u += 32) s += r2[i * P + u] * w3[u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i].y = (double)(s + b3[0]);
+}
+
+// seeds: dla, dph of the chunk as R columns
+template <class R>
+__global__ void k_seed_cols(const double2 *__restrict__ seed, int64_t n, R *__restrict__ dph) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dph[i] = (R)seed[i].y;
+}
+
+// dz2 = dph_i w3[u] [z2 > 0]
+template <class R>
+__global__ void k_phase_dz2(const R *__restrict__ dph, const R *__restrict__ w3, const R *__restrict__ z2, int64_t n,
+                            int P, R *__restrict__ dz2) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * P) return;
+    const int u = (int)(idx % P);
+    dz2[idx] = z2[idx] > R(0) ? dph[idx / P] * w3[u] : R(0);
+}
+
+// a[idx] *= [z > 0]  or  a[idx] *= gelu'(z)
+template <class R, bool GELU>
+__global__ void k_act_bwd(R *__restrict__ a, const R *__restrict__ z, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (GELU)
+            a[i] *= gelu_grad_<R>(z[i]);
+        else
+            a[i] = z[i] > R(0) ? a[i] : R(0);
+    }
+}
+
+// token-embedding gradient: out[v][c] += sum over rows with input id v of dh[row][c]
+template <class R>
+__global__ void k_tok_grad(const R *__restrict__ dh, const uint8_t *__restrict__ tok, int64_t n, int T, int d,
+                           int64_t rows_per_block, R *__restrict__ partial) {
+    const int64_t rows = n * T;
+    const int64_t r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        R s[5] = {0, 0, 0, 0, 0};
+        for (int64_t r = r0; r < r1; ++r) {
+            const int t = (int)(r % T);
+            const int inp = t == 0 ? 4 : (int)tok[r - 1];
+            const R v = dh[r * d + c];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) s[k] += (inp == k) ? v : R(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) partial[(blockIdx.x * 5 + k) * (int64_t)d + c] = s[k];
+    }
+}
+
+// ------------------------------------------------------------------ orchestration
+template <class R>
+struct Views {  // parameter views (type R) in the converted copy
+    const R *tok, *pos, *lnf_g, *lnf_b, *hw, *hb, *w1p, *b1p, *w2p, *b2p, *w3p, *b3p;
+    struct L {
+        const R *ln1g, *ln1b, *wqkv, *bqkv, *wo, *bo, *ln2g, *ln2b, *w1, *b1, *w2, *b2;
+    };
+    std::vector<L> layer;
+};
+
+template <class R>
+Views<R> make_views(const nnqs_model *M, const R *p) {
+    const ParamLayout &Lo = M->lay;
+    Views<R> v;
+    v.tok = p + Lo.tok_emb;
+    v.pos = p + Lo.pos_emb;
+    v.lnf_g = p + Lo.lnf_g;
+    v.lnf_b = p + Lo.lnf_b;
+    v.hw = p + Lo.head_w;
+    v.hb = p + Lo.head_b;
+    v.w1p = p + Lo.ph_w1;
+    v.b1p = p + Lo.ph_b1;
+    v.w2p = p + Lo.ph_w2;
+    v.b2p = p + Lo.ph_b2;
+    v.w3p = p + Lo.ph_w3;
+    v.b3p = p + Lo.ph_b3;
+    for (auto &l : Lo.layer)
+        v.layer.push_back({p + l.ln1_g, p + l.ln1_b, p + l.wqkv, p + l.bqkv, p + l.wo, p + l.bo, p + l.ln2_g,
+                           p + l.ln2_b, p + l.w1, p + l.b1, p + l.w2, p + l.b2});
+    return v;
+}
+
+// Per-chunk activation buffers.  With `keep` every layer's tensors are
+// kept for the backward; otherwise one set is reused.
+template <class R>
+struct Acts {
+    int64_t C = 0;
+    bool keep = false;
+    uint8_t *tok = nullptr;
+    R *hbuf = nullptr;   // keep: [L+1][C*T*d] residual stream before each layer / final
+    R *hmid = nullptr;   // keep: [L][C*T*d]
+    R *a = nullptr, *a2 = nullptr, *qkv = nullptr, *o = nullptr, *u = nullptr, *gu = nullptr;
+    R *mean1 = nullptr, *rstd1 = nullptr, *mean2 = nullptr, *rstd2 = nullptr, *lse = nullptr;
+    R *hf = nullptr, *meanf = nullptr, *rstdf = nullptr, *pi = nullptr;
+    R *z1 = nullptr, *r1 = nullptr, *z2 = nullptr, *r2 = nullptr, *xf = nullptr;
+    Scratch<R> scr{nullptr, 0};
+};
+
+template <class R>
+void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) {
+    const int64_t T = M->T, d = M->d, L = M->L, F = M->F, P = M->P, rows = C * T, H = M->H;
+    const int64_t Lk = keep ? L : 1;
+    A.C = C;
+    A.keep = keep;
+    A.tok = a.take<uint8_t>(rows);
+    A.hbuf = a.take<R>((keep ? (L + 1) : 2) * rows * d);
+    A.hmid = a.take<R>(Lk * rows * d);
+    A.a = a.take<R>(Lk * rows * d);
+    A.a2 = a.take<R>(Lk * rows * d);
+    A.qkv = a.take<R>(Lk * rows * 3 * d);
+    A.o = a.take<R>(Lk * rows * d);
+    A.u = a.take<R>(Lk * rows * F);
+    A.gu = a.take<R>(Lk * rows * F);
+    A.mean1 = a.take<R>(Lk * rows);
+    A.rstd1 = a.take<R>(Lk * rows);
+    A.mean2 = a.take<R>(Lk * rows);
+    A.rstd2 = a.take<R>(Lk * rows);
+    A.lse = a.take<R>(Lk * C * H * T);
+    A.hf = a.take<R>(rows * d);
+    A.meanf = a.take<R>(rows);
+    A.rstdf = a.take<R>(rows);
+    A.pi = a.take<R>(rows * 4);
+    A.z1 = a.take<R>(C * P);
+    A.r1 = a.take<R>(C * P);
+    A.z2 = a.take<R>(C * P);
+    A.r2 = a.take<R>(C * P);
+    A.xf = keep ? a.take<R>(C * M->N) : nullptr;
+    // split-K / column-reduction partials: enough for the largest weight
+    const int64_t wmax = std::max<int64_t>({3 * d * d, F * d, P * P, P * (int64_t)M->N});
+    A.scr.elems = size_t(std::max<int64_t>(8 * wmax, 4 * 152 * std::max<int64_t>(F, P) * 5));
+    A.scr.buf = a.take<R>(A.scr.elems);
+}
+
+template <int DH_, class R>
+nnqs_status launch_attn_fwd(cudaStream_t s, const R *qkv, R *o, R *lse, int64_t n, int T, int H, int d) {
+    k_attn_fwd<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, n, T, H, d);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+template <class R>
+nnqs_status attn_fwd(cudaStream_t s, int dh, const R *qkv, R *o, R *lse, int64_t n, int T, int H, int d) {
+    switch (dh) {
+        case 1: return launch_attn_fwd<1>(s, qkv, o, lse, n, T, H, d);
+        case 2: return launch_attn_fwd<2>(s, qkv, o, lse, n, T, H, d);
+        case 4: return launch_attn_fwd<4>(s, qkv, o, lse, n, T, H, d);
+        case 8: return launch_attn_fwd<8>(s, qkv, o, lse, n, T, H, d);
+        case 16: return launch_attn_fwd<16>(s, qkv, o, lse, n, T, H, d);
+        case 32: return launch_attn_fwd<32>(s, qkv, o, lse, n, T, H, d);
+        case 64: return launch_attn_fwd<64>(s, qkv, o, lse, n, T, H, d);
+        default: return set_error(NNQS_E_UNSUPPORTED, "head dimension must be a power of two <= 64");
+    }
+}
+
+template <int DH_, class R>
+nnqs_status launch_attn_bwd(cudaStream_t s, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
+                            int64_t n, int T, int H, int d) {
+    k_attn_bwd_q<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    k_attn_bwd_kv<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, lse, dout, Dbuf, dqkv, n, T, H, d);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+template <class R>
+nnqs_status attn_bwd(cudaStream_t s, int dh, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
+                     int64_t n, int T, int H, int d) {
+    switch (dh) {
+        case 1: return launch_attn_bwd<1>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 2: return launch_attn_bwd<2>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 4: return launch_attn_bwd<4>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 8: return launch_attn_bwd<8>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 16: return launch_attn_bwd<16>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 32: return launch_attn_bwd<32>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 64: return launch_attn_bwd<64>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        default: return set_error(NNQS_E_UNSUPPORTED, "head dimension must be a power of two <= 64");
+    }
+}
+
+// Forward of one chunk of C samples (x: [C][W]), writing out[C] (log|psi|, phase).
+// cond != null: sampling mode -- x are prefixes of S-1 tokens, the output is
+// pi~(. | prefix) at position S-1 (no phase, no log psi).
+template <class R>
+nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
+                          double2 *out, DevStatus *st, int64_t row_offset, const TcWeights *tcw, cudaStream_t s,
+                          int S = 0, double *cond = nullptr) {
+    const int Tm = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, W = M->W, N = M->N;
+    const int T = S > 0 ? S : Tm;  // sequence length of this pass
+    const int64_t rows = C * T;
+    k_embed<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, T, Tm, d, V.tok, V.pos, A.hbuf, A.tok);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    for (int l = 0; l < L; ++l) {
+        const auto &Lw = V.layer[l];
+        const int64_t k = A.keep ? l : 0;
+        R *hin = A.keep ? A.hbuf + l * rows * d : A.hbuf;
+        R *hout = A.keep ? A.hbuf + (l + 1) * rows * d : A.hbuf;
+        R *hmid = A.hmid + k * rows * d;
+        R *a = A.a + k * rows * d, *a2 = A.a2 + k * rows * d, *qkv = A.qkv + k * rows * 3 * d, *o = A.o + k * rows * d;
+        R *u = A.u + k * rows * F, *gu = A.gu + k * rows * F;
+        k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, Lw.ln1g, Lw.ln1b, a, A.mean1 + k * rows,
+                                                             A.rstd1 + k * rows, rows, d);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        if (tcw) {
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 0), EPI_STORE, a, rows, d, Lw.bqkv, qkv, nullptr, nullptr));
+        } else {
+            NNQS_TRY(linear_fwd<R>(s, EPI_STORE, a, rows, d, Lw.wqkv, 3 * d, Lw.bqkv, qkv, nullptr, nullptr, A.scr));
+        }
+        NNQS_TRY(attn_fwd<R>(s, M->dh, qkv, o, A.lse + k * C * H * T, C, T, H, d));
+        if (tcw) {
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 1), EPI_RESID, o, rows, d, Lw.bo, hmid, nullptr, hin));
+        } else {
+            NNQS_TRY(linear_fwd<R>(s, EPI_RESID, o, rows, d, Lw.wo, d, Lw.bo, hmid, nullptr, hin, A.scr));
+        }
+        k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, Lw.ln2g, Lw.ln2b, a2, A.mean2 + k * rows,
+                                                             A.rstd2 + k * rows, rows, d);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        if (tcw) {
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 2), EPI_GELU, a2, rows, d, Lw.b1, u, gu, nullptr));
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 3), EPI_RESID, gu, rows, F, Lw.b2, hout, nullptr, hmid));
+        } else {
+            NNQS_TRY(linear_fwd<R>(s, EPI_GELU, a2, rows, d, Lw.w1, F, Lw.b1, u, gu, nullptr, A.scr));
+            NNQS_TRY(linear_fwd<R>(s, EPI_RESID, gu, rows, F, Lw.w2, d, Lw.b2, hout, nullptr, hmid, A.scr));
+        }
+    }
+    const R *hlast = A.keep ? A.hbuf + (int64_t)L * rows * d : A.hbuf;
+    k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, V.lnf_g, V.lnf_b, A.hf, A.meanf, A.rstdf, rows, d);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    if (cond) {
+        k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, T, Tm, d, M->cfg.n_alpha,
+                                                        M->cfg.n_beta, cond, st);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        return NNQS_OK;
+    }
+    k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
+                                                    M->cfg.n_beta, A.pi, out, st, row_offset);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    // phase MLP
+    k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    if (tcw) {
+        NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(L, 0), EPI_RELU, A.r1, C, P, V.b2p, A.z2, A.r2, nullptr));
+    } else {
+        NNQS_TRY(linear_fwd<R>(s, EPI_RELU, A.r1, C, P, V.w2p, P, V.b2p, A.z2, A.r2, nullptr, A.scr));
+    }
+    k_phase_out<R><<<grid_for(C * 32, 256), 256, 0, s>>>(A.r2, V.w3p, V.b3p, C, P, out);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+// Gradient buffers for the backward of one chunk.
+template <class R>
+struct Grads {
+    R *dh, *dtmp, *dqkv, *du, *Dbuf, *dz, *dph, *dz1, *dz2;
+    double2 *lp;  // forward output of the recomputation (not used further)
+};
+
+template <class R>
+void take_grads(const nnqs_model *M, int64_t C, Arena &a, Grads<R> &G) {
+    const int64_t T = M->T, d = M->d, F = M->F, P = M->P, rows = C * T, H = M->H;
+    G.dh = a.take<R>(rows * d);
+    G.dtmp = a.take<R>(rows * std::max<int64_t>(d, 4));
+    G.dqkv = a.take<R>(rows * 3 * d);
+    G.du = a.take<R>(rows * F);
+    G.Dbuf = a.take<R>(C * H * T);
+    G.dz = a.take<R>(rows * 4);
+    G.dph = a.take<R>(C);
+    G.dz1 = a.take<R>(C * P);
+    G.dz2 = a.take<R>(C * P);
+    G.lp = a.take<double2>(C);
+}
+
+template <class R>
+nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
+                           Grads<R> &G, const double2 *seed, R *gacc, cudaStream_t s) {
+    const int T = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, N = M->N;
+    const int64_t rows = C * T;
+    const ParamLayout &Lo = M->lay;
+    Scratch<R> scr = A.scr;
+    (void)x;
+    // ---- phase MLP
+    k_seed_cols<R><<<grid_for(C, 256), 256, 0, s>>>(seed, C, G.dph);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    // dW3[0][u] += sum_i dph_i r2[i][u]; db3 += sum_i dph_i
+    NNQS_TRY(linear_dw<R>(s, G.dph, C, 1, A.r2, P, gacc + Lo.ph_w3, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dph, nullptr, nullptr, nullptr, C, 1, gacc + Lo.ph_b3, scr));
+    k_phase_dz2<R><<<grid_for(C * P, 256), 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, G.dz2);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_TRY(linear_dw<R>(s, G.dz2, C, P, A.r1, P, gacc + Lo.ph_w2, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dz2, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b2, scr));
+    NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz2, C, P, V.w2p, P, G.dz1, scr));
+    k_act_bwd<R, false><<<grid_for(C * P, 256), 256, 0, s>>>(G.dz1, A.z1, C * P);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_TRY(linear_dw<R>(s, G.dz1, C, P, A.xf, N, gacc + Lo.ph_w1, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, scr));
+    // ---- head
+    k_head_bwd<R><<<grid_for(rows * 4, 256), 256, 0, s>>>(A.pi, A.tok, seed, C, T, G.dz);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_TRY(linear_dw<R>(s, G.dz, rows, 4, A.hf, d, gacc + Lo.head_w, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dz, nullptr, nullptr, nullptr, rows, 4, gacc + Lo.head_b, scr));
+    NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz, rows, 4, V.hw, d, G.dtmp, scr));
+    // final LayerNorm
+    const R *hlast = A.hbuf + (int64_t)L * rows * d;
+    k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0));
+    k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_TRY(colsum<R>(s, 1, G.dtmp, hlast, A.meanf, A.rstdf, rows, d, gacc + Lo.lnf_g, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lo.lnf_b, scr));
+    for (int l = L - 1; l >= 0; --l) {
+        const auto &Lw = V.layer[l];
+        const auto &Lg = Lo.layer[l];
+        const R *hin = A.hbuf + (int64_t)l * rows * d;
+        const R *hmid = A.hmid + (int64_t)l * rows * d;
+        const R *a = A.a + (int64_t)l * rows * d, *a2 = A.a2 + (int64_t)l * rows * d;
+        const R *qkv = A.qkv + (int64_t)l * rows * 3 * d, *o = A.o + (int64_t)l * rows * d;
+        const R *u = A.u + (int64_t)l * rows * F, *gu = A.gu + (int64_t)l * rows * F;
+        // FFN: hout = hmid + gelu(a2 W1^T + b1) W2^T + b2
+        NNQS_TRY(linear_dw<R>(s, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.b2, scr));
+        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dh, rows, d, Lw.w2, F, G.du, scr));
+        k_act_bwd<R, true><<<grid_for(rows * F, 256), 256, 0, s>>>(G.du, u, rows * F);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_TRY(linear_dw<R>(s, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, scr));
+        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.du, rows, F, Lw.w1, d, G.dtmp, scr));
+        k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
+                                                             G.dtmp, G.dh, rows, d);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, rows, d, gacc + Lg.ln2_g, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln2_b, scr));
+        // attention: hmid = hin + attn(a) Wo^T + bo
+        NNQS_TRY(linear_dw<R>(s, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.bo, scr));
+        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
+        NNQS_TRY(attn_bwd<R>(s, M->dh, qkv, o, A.lse + (int64_t)l * C * H * T, G.dtmp, G.dqkv, G.Dbuf, C, T, H, d));
+        NNQS_TRY(linear_dw<R>(s, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, scr));
+        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
+        k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
+                                                             G.dtmp, G.dh, rows, d);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hin, A.mean1 + l * rows, A.rstd1 + l * rows, rows, d, gacc + Lg.ln1_g, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln1_b, scr));
+    }
+    // embeddings: pos[t][c] += sum_i dh[i][t][c]; tok[v][c] += sum over inputs v
+    NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, C, T * d, gacc + Lo.pos_emb, scr));
+    {
+        int64_t nblk = std::min<int64_t>((rows + 63) / 64, 2 * sm_count());
+        nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(5 * d))));
+        const int64_t rpb = (rows + nblk - 1) / nblk;
+        nblk = (rows + rpb - 1) / rpb;
+        k_tok_grad<R><<<(unsigned)nblk, 128, 0, s>>>(G.dh, A.tok, C, T, d, rpb, scr.buf);
+        NNQS_CUDA_TRY(cudaGetLastError());
+        k_sum_partials<R><<<grid_for(5 * d, 256), 256, 0, s>>>(scr.buf, nblk, 5 * d, gacc + Lo.tok_emb);
+        NNQS_CUDA_TRY(cudaGetLastError());
+    }
+    return NNQS_OK;
+}
+
+template <class R>
+__global__ void k_grad_out(const R *__restrict__ g, int64_t n, double *__restrict__ g64, float *__restrict__ g32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (g64) g64[i] = (double)g[i];
+        if (g32) g32[i] = (float)g[i];
+    }
+}
+
+// samples per chunk: keep the saved activations within ~6 GB
+int64_t chunk_for(const nnqs_model *M, int64_t n, size_t rbytes, bool backward) {
+    const int64_t per = (int64_t)rbytes * M->T * M->d * (backward ? (16 * M->L + 12) : 12) +
+                        (int64_t)rbytes * 5 * M->P;
+    const int64_t budget = backward ? (int64_t(6) << 30) : (int64_t(3) << 30);
+    int64_t c = std::max<int64_t>(256, budget / std::max<int64_t>(per, 1));
+    c = std::min<int64_t>(c, 32768);
+    return std::max<int64_t>(1, std::min(c, n));
+}
+
+template <class R>
+size_t workspace_impl(const nnqs_model *M, int64_t n, bool backward, bool tensor) {
+    Arena a(nullptr);
+    a.take<char>(kStatusBytes);
+    a.take<R>(M->lay.total);  // converted parameters
+    if (backward) a.take<R>(M->lay.total);  // gradient accumulator
+    if (tensor) tc_weights_take(M, a);
+    const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), backward);
+    Acts<R> A;
+    take_acts<R>(M, C, backward, a, A);
+    if (backward) {
+        Grads<R> G;
+        take_grads<R>(M, C, a, G);
+    }
+    return a.used + 1024;
+}
+
+template <class R>
+nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, double *out, Arena &ws,
+                         DevStatus *st, bool tensor, cudaStream_t s) {
+    R *pr = ws.take<R>(M->lay.total);
+    TcWeights tcw{};
+    if (tensor) tc_weights_take(M, ws, &tcw);
+    const int64_t C = chunk_for(M, n, sizeof(R), false);
+    Acts<R> A;
+    take_acts<R>(M, C, false, ws, A);
+    k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
+    const Views<R> V = make_views<R>(M, pr);
+    for (int64_t c0 = 0; c0 < n; c0 += C) {
+        const int64_t cn = std::min(C, n - c0);
+        NNQS_TRY(forward_chunk<R>(M, V, x + c0 * M->W, cn, A, reinterpret_cast<double2 *>(out) + c0, st, c0,
+                                  tensor ? &tcw : nullptr, s));
+    }
+    return NNQS_OK;
+}
+
+template <class R>
+nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, const double *seed,
+                          double *g64, float *g32, Arena &ws, DevStatus *st, cudaStream_t s) {
+    R *pr = ws.take<R>(M->lay.total);
+    R *gacc = ws.take<R>(M->lay.total);
+    const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
+    Acts<R> A;
+    take_acts<R>(M, C, true, ws, A);
+    Grads<R> G;
+    take_grads<R>(M, C, ws, G);
+    k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
+    k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0));
+    NNQS_CUDA_TRY(cudaGetLastError());
+    const Views<R> V = make_views<R>(M, pr);
+    for (int64_t c0 = 0; c0 < n; c0 += C) {
+        const int64_t cn = std::min(C, n - c0);
+        const uint64_t *xc = x + c0 * M->W;
+        NNQS_TRY(forward_chunk<R>(M, V, xc, cn, A, G.lp, st, c0, nullptr, s));
+        NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc, s));
+    }
+    k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+template <class R>
+size_t cond_workspace_impl(const nnqs_model *M, int64_t max_prefixes, bool tensor) {
+    Arena a(nullptr);
+    a.take<R>(M->lay.total);
+    if (tensor) tc_weights_take(M, a);
+    const int64_t C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(R), false);
+    Acts<R> A;
+    take_acts<R>(M, C, false, a, A);
+    return a.used + 1024;
+}
+
+}  // namespace
+
+struct CondCtx {
+    int prec = NNQS_FP64;
+    bool tensor = false;
+    void *params = nullptr;  // converted copy (double or float)
+    int64_t C = 0;
+    TcWeights tcw;
+    Acts<float> Af;
+    Acts<double> Ad;
+};
+
+size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec) {
+    if (prec == NNQS_FP64) return cond_workspace_impl<double>(M, max_prefixes, false);
+    return cond_workspace_impl<float>(M, max_prefixes, prec == NNQS_MIXED);
+}
+
+nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, Arena &ws,
+                        CondCtx **out, cudaStream_t s) {
+    CondCtx *c = new (std::nothrow) CondCtx();
+    if (!c) return set_error(NNQS_E_NOMEM, "host allocation failed");
+    *out = c;
+    c->prec = prec;
+    c->tensor = prec == NNQS_MIXED;
+    if (prec == NNQS_FP64) {
+        double *pr = ws.take<double>(M->lay.total);
+        c->params = pr;
+        c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(double), false);
+        take_acts<double>(M, c->C, false, ws, c->Ad);
+        k_convert_params<double><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
+    } else {
+        float *pr = ws.take<float>(M->lay.total);
+        c->params = pr;
+        if (c->tensor) tc_weights_take(M, ws, &c->tcw);
+        c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(float), false);
+        take_acts<float>(M, c->C, false, ws, c->Af);
+        k_convert_params<float><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
+        if (c->tensor) NNQS_TRY(tc_weights_prepare(M, params, c->tcw, s));
+    }
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+void cond_destroy(CondCtx *c) { delete c; }
+
+nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int S, double *cond,
+                      DevStatus *st, cudaStream_t s) {
+    for (int64_t c0 = 0; c0 < n; c0 += ctx->C) {
+        const int64_t cn = std::min(ctx->C, n - c0);
+        if (ctx->prec == NNQS_FP64) {
+            const Views<double> V = make_views<double>(M, static_cast<double *>(ctx->params));
+            NNQS_TRY(forward_chunk<double>(M, V, prefixes + c0 * M->W, cn, ctx->Ad, nullptr, st, c0, nullptr, s, S,
+                                           cond + c0 * 4));
+        } else {
+            const Views<float> V = make_views<float>(M, static_cast<float *>(ctx->params));
+            NNQS_TRY(forward_chunk<float>(M, V, prefixes + c0 * M->W, cn, ctx->Af, nullptr, st, c0,
+                                          ctx->tensor ? &ctx->tcw : nullptr, s, S, cond + c0 * 4));
+        }
+    }
+    return NNQS_OK;
+}
+
+size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward) {
+    if (prec == NNQS_FP64) return workspace_impl<double>(M, n, backward, false);
+    return workspace_impl<float>(M, n, backward, prec == NNQS_MIXED && !backward);
+}
+
+nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
+                           double *out, Arena &ws, DevStatus *st, cudaStream_t s) {
+    if (prec == NNQS_FP64) return forward_impl<double>(M, params, x, n, out, ws, st, false, s);
+    return forward_impl<float>(M, params, x, n, out, ws, st, prec == NNQS_MIXED, s);
+}
+
+nnqs_status logpsi_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
+                            const double *seed, double *g64, float *g32, Arena &ws, DevStatus *st, cudaStream_t s) {
+    if (prec == NNQS_FP64) return backward_impl<double>(M, params, x, n, seed, g64, g32, ws, st, s);
+    return backward_impl<float>(M, params, x, n, seed, g64, g32, ws, st, s);
+}
+
+}  // namespace nnqs

@@ -1,0 +1,375 @@
+// Local energy, Eq. (Eloc), sample-aware form (Sec. 3.4 (2)-(5), Alg. 2),
+// re-mapped to sm_103a.
+//
+// E_loc(x) = sum_{x' in S} H_{x x'} psi(x') / psi(x),
+// H_{x x'} = sum_{t in group(x ^ x')} coef_t (-1)^{popc(x & yz_t)}.
+//
+// The paper gives one thread a whole sample and walks every X/Y group of
+// the Hamiltonian for it (Alg. 2).  Here a CTA takes a tile of rows x and a
+// chunk of the work so that the grid fills 152 SMs, and writes one partial
+// sum per (chunk, row); a second kernel adds the partials in chunk order so
+// the result does not depend on scheduling.  The diagonal group (x' = x,
+// the largest group) is evaluated by one warp per row in its own kernel so
+// that it does not serialise a warp of the sweep.
+//
+// Two sweeps give the same sum:
+//   GROUPS  for each row and each non-diagonal group m: x' = x ^ m kept iff
+//           it has the sector's electron counts, then probed in the hash of
+//           S (the role of the sorted id_lut search of Alg. 2).
+//   PAIRS   for each row x and each sample y in S: m = x ^ y is looked up
+//           in the hash of group X/Y masks when popc(m) is at most the
+//           largest group weight.  Cost |rows| x |S| instead of
+//           |rows| x N_XY.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dev_common.cuh"
+#include "internal.h"
+#include "sweep_common.cuh"
+
+namespace nnqs {
+namespace {
+
+constexpr int kSweepThreads = 128;
+constexpr int kGroupTile = 256;   // groups staged in shared memory per step
+constexpr int kPairTile = 512;    // samples staged in shared memory per step
+constexpr int kPairRows = 2;      // rows per thread in the pair sweep
+
+template <int W>
+__global__ void k_build_lut_hash(const uint64_t *__restrict__ lut, int64_t n_lut, int n_qubits,
+                                 int n_alpha, int n_beta, HashTab<W> tab, DevStatus *st) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_lut) return;
+    Bits<W> k = load_bits<W>(lut, i);
+    int na = 0, nb = 0;
+    bool high = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        na += __popcll(k.w[w] & kEven);
+        nb += __popcll(k.w[w] & ~kEven);
+        int lo = n_qubits - 64 * w;  // valid bits in this word
+        if (lo < 64) high |= (lo <= 0) ? (k.w[w] != 0) : ((k.w[w] >> lo) != 0);
+    }
+    if (high) {
+        record_status(st, NNQS_E_INVAL, i);
+        return;
+    }
+    if (na != n_alpha || nb != n_beta) {
+        record_status(st, NNQS_E_SECTOR, i);
+        return;
+    }
+    bool fresh = false;
+    int64_t slot = tab.insert(k, &fresh);
+    if (slot < 0) {
+        record_status(st, NNQS_E_TABLE_FULL, i);
+        return;
+    }
+    if (!fresh) {
+        record_status(st, NNQS_E_DUPLICATE, i);
+        return;
+    }
+    tab.vals[slot] = (int32_t)i;
+}
+
+// GROUPS sweep.  grid = (row tiles of 128, group chunks).
+template <int W>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_sweep_groups(const uint64_t *__restrict__ gxy, const uint32_t *__restrict__ goff,
+                   const uint8_t *__restrict__ gspin, int64_t g_begin, int64_t g_end,
+                   int64_t groups_per_chunk, const uint64_t *__restrict__ tyz,
+                   const double *__restrict__ tcoef, const uint64_t *__restrict__ lut,
+                   const double2 *__restrict__ lut_lp, HashTab<W> tab, int64_t row_begin,
+                   int64_t n_rows, double2 *__restrict__ partial) {
+    __shared__ uint64_t s_xy[kGroupTile * W];
+    __shared__ uint8_t s_spin[kGroupTile];
+    const int64_t r = blockIdx.x * (int64_t)kSweepThreads + threadIdx.x;
+    const bool active = r < n_rows;
+    Bits<W> x{};
+    double2 lx = make_double2(0.0, 0.0);
+    if (active) {
+        x = load_bits<W>(lut, row_begin + r);
+        lx = lut_lp[row_begin + r];
+    }
+    const int64_t c0 = g_begin + blockIdx.y * groups_per_chunk;
+    const int64_t c1 = min(g_end, c0 + groups_per_chunk);
+    double er = 0.0, ei = 0.0;
+    for (int64_t gt = c0; gt < c1; gt += kGroupTile) {
+        const int ntile = (int)min((int64_t)kGroupTile, c1 - gt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < ntile * W; k += kSweepThreads) s_xy[k] = gxy[gt * W + k];
+        for (int k = threadIdx.x; k < ntile; k += kSweepThreads) s_spin[k] = gspin[gt + k];
+        __syncthreads();
+        if (!active) continue;
+        for (int k = 0; k < ntile; ++k) {
+            const uint8_t sp = s_spin[k];
+            int ra = 0, rb = 0;  // electrons the mask removes, per spin
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint64_t v = s_xy[k * W + w] & x.w[w];
+                ra += __popcll(v & kEven);
+                rb += __popcll(v & ~kEven);
+            }
+            if (sp == 0xFF || ra != (sp & 15) || rb != (sp >> 4)) continue;
+            Bits<W> xp;
+#pragma unroll
+            for (int w = 0; w < W; ++w) xp.w[w] = x.w[w] ^ s_xy[k * W + w];
+            const int32_t j = tab.find(xp);
+            if (j < 0) continue;
+            const int64_t g = gt + k;
+            const double coef = group_coef<W>(x, __ldg(goff + g), __ldg(goff + g + 1), tyz, tcoef);
+            const double2 q = ratio(lx, lut_lp[j]);
+            er += coef * q.x;
+            ei += coef * q.y;
+        }
+    }
+    if (active) partial[blockIdx.y * n_rows + r] = make_double2(er, ei);
+}
+
+// PAIRS sweep.  grid = (row tiles of 128 * kPairRows, sample chunks).
+template <int W>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_sweep_pairs(const uint64_t *__restrict__ lut, const double2 *__restrict__ lut_lp,
+                  int64_t n_lut, int64_t cols_per_chunk, int max_weight, HashTab<W> gtab,
+                  const uint32_t *__restrict__ goff, const uint64_t *__restrict__ tyz,
+                  const double *__restrict__ tcoef, int64_t row_begin, int64_t n_rows,
+                  double2 *__restrict__ partial) {
+    __shared__ uint64_t s_y[kPairTile * W];
+    const int64_t rbase = blockIdx.x * (int64_t)(kSweepThreads * kPairRows);
+    Bits<W> x[kPairRows];
+    double2 lx[kPairRows];
+    bool act[kPairRows];
+    double er[kPairRows], ei[kPairRows];
+#pragma unroll
+    for (int q = 0; q < kPairRows; ++q) {
+        const int64_t r = rbase + q * kSweepThreads + threadIdx.x;
+        act[q] = r < n_rows;
+        er[q] = ei[q] = 0.0;
+        if (act[q]) {
+            x[q] = load_bits<W>(lut, row_begin + r);
+            lx[q] = lut_lp[row_begin + r];
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) x[q].w[w] = 0;
+            lx[q] = make_double2(0.0, 0.0);
+        }
+    }
+    const int64_t c0 = blockIdx.y * cols_per_chunk;
+    const int64_t c1 = min(n_lut, c0 + cols_per_chunk);
+    for (int64_t ct = c0; ct < c1; ct += kPairTile) {
+        const int ntile = (int)min((int64_t)kPairTile, c1 - ct);
+        __syncthreads();
+        for (int k = threadIdx.x; k < ntile * W; k += kSweepThreads) s_y[k] = lut[ct * W + k];
+        __syncthreads();
+        for (int k = 0; k < ntile; ++k) {
+            Bits<W> y;
+#pragma unroll
+            for (int w = 0; w < W; ++w) y.w[w] = s_y[k * W + w];
+#pragma unroll
+            for (int q = 0; q < kPairRows; ++q) {
+                int d = 0;
+                Bits<W> m;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    m.w[w] = x[q].w[w] ^ y.w[w];
+                    d += __popcll(m.w[w]);
+                }
+                // d == 0 is the diagonal, handled by k_diag
+                if (d == 0 || d > max_weight || !act[q]) continue;
+                const int32_t g = gtab.find(m);
+                if (g < 0) continue;
+                const double coef = group_coef<W>(x[q], __ldg(goff + g), __ldg(goff + g + 1), tyz, tcoef);
+                const double2 rr = ratio(lx[q], lut_lp[ct + k]);
+                er[q] += coef * rr.x;
+                ei[q] += coef * rr.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kPairRows; ++q) {
+        const int64_t r = rbase + q * kSweepThreads + threadIdx.x;
+        if (act[q]) partial[blockIdx.y * n_rows + r] = make_double2(er[q], ei[q]);
+    }
+}
+
+struct SaPlan {
+    bool pairs;
+    int64_t row_tiles, chunks, per_chunk;
+    int64_t g_begin, g_end;
+    bool has_diag;
+};
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms;
+}
+
+SaPlan plan_sa(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags) {
+    SaPlan p{};
+    p.has_diag = H->n_groups > 0 && H->gxy[0] == 0 && (H->W == 1 || H->gxy[1] == 0);
+    p.g_begin = p.has_diag ? 1 : 0;
+    p.g_end = H->n_groups;
+    const int64_t work_groups = n_rows * (p.g_end - p.g_begin);
+    const int64_t work_pairs = n_rows * n_lut;
+    if (flags == NNQS_SWEEP_GROUPS)
+        p.pairs = false;
+    else if (flags == NNQS_SWEEP_PAIRS)
+        p.pairs = true;
+    else
+        p.pairs = work_pairs < work_groups;
+    // enough CTAs for ~8 per SM
+    const int64_t target = 8 * (int64_t)num_sms();
+    if (p.pairs) {
+        p.row_tiles = std::max<int64_t>(1, (n_rows + kSweepThreads * kPairRows - 1) / (kSweepThreads * kPairRows));
+        int64_t max_chunks = std::max<int64_t>(1, (n_lut + kPairTile - 1) / kPairTile);
+        p.chunks = std::min(max_chunks, std::max<int64_t>(1, (target + p.row_tiles - 1) / p.row_tiles));
+        p.per_chunk = (n_lut + p.chunks - 1) / p.chunks;
+        p.per_chunk = std::max<int64_t>(1, p.per_chunk);
+        p.chunks = std::max<int64_t>(1, (n_lut + p.per_chunk - 1) / p.per_chunk);
+    } else {
+        const int64_t ng = p.g_end - p.g_begin;
+        p.row_tiles = std::max<int64_t>(1, (n_rows + kSweepThreads - 1) / kSweepThreads);
+        int64_t max_chunks = std::max<int64_t>(1, (ng + kGroupTile - 1) / kGroupTile);
+        p.chunks = std::min(max_chunks, std::max<int64_t>(1, (target + p.row_tiles - 1) / p.row_tiles));
+        p.per_chunk = std::max<int64_t>(1, (ng + p.chunks - 1) / p.chunks);
+        p.chunks = ng > 0 ? (ng + p.per_chunk - 1) / p.per_chunk : 0;
+    }
+    return p;
+}
+
+template <int W>
+nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp, int64_t n_lut,
+                         int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int flags,
+                         double *out, Arena &ws, DevStatus *status, cudaStream_t s) {
+    const SaPlan p = plan_sa(H, n_lut, n_rows, flags);
+    const int64_t cap = pow2_at_least(std::max<int64_t>(2, 2 * n_lut));
+    uint64_t *hkeys = ws.take<uint64_t>(size_t(cap) * W);
+    int32_t *hvals = ws.take<int32_t>(size_t(cap));
+    double *diag = ws.take<double>(size_t(std::max<int64_t>(1, n_rows)));
+    double2 *partial = ws.take<double2>(size_t(std::max<int64_t>(1, p.chunks * n_rows)));
+    if (ws.base == nullptr) return NNQS_OK;  // sizing pass
+
+    if (n_rows == 0) return NNQS_OK;
+    NNQS_CUDA_TRY(cudaMemsetAsync(hkeys, 0xFF, size_t(cap) * W * 8, s));
+    HashTab<W> tab{hkeys, hvals, uint64_t(cap - 1)};
+    k_build_lut_hash<W><<<grid_for(n_lut, 256), 256, 0, s>>>(lut, n_lut, H->n_qubits, n_alpha, n_beta, tab, status);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    if (p.has_diag) {
+        k_diag<W><<<grid_for(n_rows * 32, 256), 256, 0, s>>>(lut, row_begin, n_rows, (uint32_t)H->goff[0],
+                                                             (uint32_t)H->goff[1], H->d_tyz, H->d_tcoef, diag);
+        NNQS_CUDA_TRY(cudaGetLastError());
+    }
+    const double2 *lp2 = reinterpret_cast<const double2 *>(lut_lp);
+    if (p.chunks > 0) {
+        dim3 grid((unsigned)p.row_tiles, (unsigned)p.chunks);
+        if (p.pairs) {
+            const int maxw = H->max_xy_weight;
+            HashTab<W> gtab{H->d_ghkeys, H->d_ghvals, uint64_t(H->ghcap - 1)};
+            k_sweep_pairs<W><<<grid, kSweepThreads, 0, s>>>(lut, lp2, n_lut, p.per_chunk, maxw, gtab, H->d_goff,
+                                                            H->d_tyz, H->d_tcoef, row_begin, n_rows, partial);
+        } else {
+            k_sweep_groups<W><<<grid, kSweepThreads, 0, s>>>(H->d_gxy, H->d_goff, H->d_gspin, p.g_begin, p.g_end,
+                                                             p.per_chunk, H->d_tyz, H->d_tcoef, lut, lp2, tab,
+                                                             row_begin, n_rows, partial);
+        }
+        NNQS_CUDA_TRY(cudaGetLastError());
+    }
+    k_reduce_partials<<<grid_for(n_rows, 256), 256, 0, s>>>(p.has_diag ? diag : nullptr, partial, p.chunks, n_rows,
+                                                            reinterpret_cast<double2 *>(out));
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+// ---- energy statistics: one CTA, fixed-order tree reductions ----
+constexpr int kStatThreads = 1024;
+
+__device__ void block_sum3(double &a, double &b, double &c, double *sh) {
+    const int t = threadIdx.x;
+    sh[t] = a;
+    sh[kStatThreads + t] = b;
+    sh[2 * kStatThreads + t] = c;
+    __syncthreads();
+    for (int off = kStatThreads / 2; off > 0; off >>= 1) {
+        if (t < off) {
+            sh[t] += sh[t + off];
+            sh[kStatThreads + t] += sh[kStatThreads + t + off];
+            sh[2 * kStatThreads + t] += sh[2 * kStatThreads + t + off];
+        }
+        __syncthreads();
+    }
+    a = sh[0];
+    b = sh[kStatThreads];
+    c = sh[2 * kStatThreads];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kStatThreads)
+    k_stats(const double2 *__restrict__ e, const uint64_t *__restrict__ w, int64_t n, double *__restrict__ stats) {
+    extern __shared__ double sh[];
+    double sw = 0.0, sr = 0.0, si = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kStatThreads) {
+        const double wi = (double)w[i];
+        const double2 v = e[i];
+        sw += wi;
+        sr += wi * v.x;
+        si += wi * v.y;
+    }
+    block_sum3(sw, sr, si, sh);
+    const double er = sr / sw, ei = si / sw;
+    double sv = 0.0, z0 = 0.0, z1 = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kStatThreads) {
+        const double wi = (double)w[i];
+        const double2 v = e[i];
+        const double dr = v.x - er, di = v.y - ei;
+        sv += wi * (dr * dr + di * di);
+    }
+    block_sum3(sv, z0, z1, sh);
+    if (threadIdx.x == 0) {
+        stats[0] = er;
+        stats[1] = ei;
+        stats[2] = sv / sw;
+        stats[3] = sw;
+    }
+}
+
+}  // namespace
+
+// bytes for either sweep (the size query does not know which one a call forces)
+size_t eloc_sa_workspace(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int) {
+    size_t best = 0;
+    for (int f : {NNQS_SWEEP_GROUPS, NNQS_SWEEP_PAIRS}) {
+        Arena a(nullptr);
+        a.take<char>(kStatusBytes);
+        if (H->W == 1)
+            eloc_sa_impl<1>(H, nullptr, nullptr, n_lut, 0, n_rows, 0, 0, f, nullptr, a, nullptr, nullptr);
+        else
+            eloc_sa_impl<2>(H, nullptr, nullptr, n_lut, 0, n_rows, 0, 0, f, nullptr, a, nullptr, nullptr);
+        best = std::max(best, a.used + 256);
+    }
+    return best;
+}
+
+nnqs_status eloc_sa(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp, int64_t n_lut,
+                    int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int flags, double *out,
+                    Arena &ws, DevStatus *status, cudaStream_t s) {
+    if (H->W == 1)
+        return eloc_sa_impl<1>(H, lut, lut_lp, n_lut, row_begin, n_rows, n_alpha, n_beta, flags, out, ws, status, s);
+    return eloc_sa_impl<2>(H, lut, lut_lp, n_lut, row_begin, n_rows, n_alpha, n_beta, flags, out, ws, status, s);
+}
+
+size_t stats_workspace(int64_t) { return kStatusBytes + 256; }
+
+nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, double *stats, Arena &, cudaStream_t s) {
+    k_stats<<<1, kStatThreads, 3 * kStatThreads * sizeof(double), s>>>(reinterpret_cast<const double2 *>(eloc), w, n,
+                                                                        stats);
+    NNQS_CUDA_TRY(cudaGetLastError());
+    return NNQS_OK;
+}
+
+}  // namespace nnqs

@@ -1,0 +1,59 @@
+// Ansatz handle: configuration and the flat FP32 parameter layout of
+// include/nnqs.h.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace nnqs {
+
+struct LayerOff {
+    int64_t ln1_g, ln1_b, wqkv, bqkv, wo, bo, ln2_g, ln2_b, w1, b1, w2, b2;
+};
+
+struct ParamLayout {
+    int64_t tok_emb, pos_emb;
+    std::vector<LayerOff> layer;
+    int64_t lnf_g, lnf_b, head_w, head_b;
+    int64_t ph_w1, ph_b1, ph_w2, ph_b2, ph_w3, ph_b3;
+    int64_t total;
+    std::vector<std::pair<std::string, std::pair<int64_t, int64_t>>> named;  // name -> (offset, numel)
+};
+
+}  // namespace nnqs
+
+struct nnqs_model {
+    nnqs_model_cfg cfg;
+    int N, T, W, d, L, H, dh, F, P;  // qubits, tokens, words, width, layers, heads, head dim, FFN width, phase hidden
+    nnqs::ParamLayout lay;
+};
+
+namespace nnqs {
+
+ParamLayout make_layout(const nnqs_model_cfg &c);
+
+// ansatz.cu
+size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward);
+nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
+                           double *out, Arena &ws, DevStatus *st, cudaStream_t s);
+nnqs_status logpsi_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
+                            const double *seed, double *grad64, float *grad32, Arena &ws, DevStatus *st,
+                            cudaStream_t s);
+
+// conditionals pi~(. | prefix) for the sampler (ansatz.cu)
+struct CondCtx;
+size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec);
+nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, Arena &ws,
+                        CondCtx **out, cudaStream_t s);
+nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int S, double *cond,
+                      DevStatus *st, cudaStream_t s);
+void cond_destroy(CondCtx *c);
+
+// eloc_exact.cu
+size_t eloc_exact_workspace(const nnqs_ham *H, const nnqs_model *M, int64_t n_lut, int64_t n_rows, int prec);
+nnqs_status eloc_exact(const nnqs_ham *H, const nnqs_model *M, const float *params, const uint64_t *lut,
+                       int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int prec,
+                       double *out, Arena &ws, DevStatus *st, cudaStream_t s);
+
+}  // namespace nnqs

@@ -1,0 +1,363 @@
+// Batch autoregressive sampling (BAS, Sec. 3.1, Fig. bas(b)) with the
+// number mask of Sec. 3.3.
+//
+// The tree of unique prefixes is kept level by level on the device: a level
+// is a list of prefixes (packed bitstrings with the first t tokens set) and
+// their sample counts.  A step runs the ansatz on every prefix to get
+// pi~(. | prefix), splits each count over the 4 children with a multinomial
+// draw (sequential binomials), drops zero counts and writes the next level
+// in (parent, child) order.  Because children are emitted in token order and
+// the first token holds the most significant qubits, the final level comes
+// out sorted ascending by key.
+//
+// Randomness: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
+// seed, with counter (prefix index, step, draw index); binomials by inversion
+// for small means and by transformed rejection (Hormann 1993, "The
+// generation of binomial random variates") otherwise.  Every loop has a fixed
+// iteration cap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "internal.h"
+#include "model.h"
+
+namespace nnqs {
+namespace {
+
+// ---------------------------------------------------------------- Philox4x32-10
+struct Philox {
+    uint32_t k0, k1;
+    uint32_t c0, c1, c2, c3;
+    uint32_t out[4];
+    int used = 4;
+
+    __device__ void next_block() {
+        uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = c3, a = k0, b = k1;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            if (r > 0) {
+                a += 0x9E3779B9u;
+                b += 0xBB67AE85u;
+            }
+            const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+            const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+            const uint32_t n0 = hi1 ^ x1 ^ a, n1 = lo1, n2 = hi0 ^ x3 ^ b, n3 = lo0;
+            x0 = n0;
+            x1 = n1;
+            x2 = n2;
+            x3 = n3;
+        }
+        out[0] = x0;
+        out[1] = x1;
+        out[2] = x2;
+        out[3] = x3;
+        used = 0;
+        ++c3;  // next block of this stream
+    }
+    __device__ uint32_t u32() {
+        if (used >= 4) next_block();
+        return out[used++];
+    }
+    // uniform in (0, 1), 53 bits
+    __device__ double uniform() {
+        const uint64_t a = u32() >> 5, b = u32() >> 6;
+        return ((double)(a * 67108864ull + b) + 0.5) * (1.0 / 9007199254740992.0);
+    }
+};
+
+// log(k!) - [(k + 1/2) log(k + 1) - (k + 1) + log(2 pi)/2]: Stirling remainder
+__device__ double stirling_tail(double k) {
+    if (k < 10.0) {
+        return lgamma(k + 1.0) - ((k + 0.5) * log(k + 1.0) - (k + 1.0) + 0.91893853320467274178);
+    }
+    const double kp = k + 1.0, k2 = kp * kp;
+    return (1.0 / 12.0 - (1.0 / 360.0 - (1.0 / 1260.0) / k2) / k2) / kp;
+}
+
+// inversion (sequential search from 0) for n p < 14, p <= 1/2
+__device__ uint64_t binom_inversion(uint64_t n, double p, Philox &rng, DevStatus *st) {
+    const double q = 1.0 - p, s = p / q, a = (double(n) + 1.0) * s;
+    const double r0 = exp(double(n) * log1p(-p));
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        double u = rng.uniform(), r = r0;
+        uint64_t k = 0;
+        bool done = false;
+        for (int it = 0; it < 1000; ++it) {
+            if (u <= r) {
+                done = true;
+                break;
+            }
+            u -= r;
+            ++k;
+            if (k > n) break;
+            r *= (a / double(k) - s);
+        }
+        if (done && k <= n) return k;
+    }
+    record_status(st, NNQS_E_TIMEOUT, -2);
+    return (uint64_t)floor(double(n) * p);
+}
+
+// Transformed rejection with squeeze (BTRS form) for n p >= 14, p <= 1/2:
+// proposal k = floor((2a/us + b) u + c) with u ~ U(-1/2, 1/2); accept
+// quickly inside the squeeze, otherwise compare log(v * hat) with the exact
+// log f(k)/f(m) written through Stirling's series (f the binomial pmf,
+// m its mode).
+__device__ uint64_t binom_btrs(uint64_t n_, double p, Philox &rng, DevStatus *st) {
+    const double n = (double)n_;
+    const double q = 1.0 - p;
+    const double m = floor((n + 1.0) * p);
+    const double r = p / q;
+    const double spq = sqrt(n * p * q);
+    const double b = 1.15 + 2.53 * spq;
+    const double a = -0.0873 + 0.0248 * b + 0.01 * p;
+    const double c = n * p + 0.5;
+    const double alpha = (2.83 + 5.1 / b) * spq;
+    const double vr = 0.92 - 4.2 / b;
+    for (int it = 0; it < 10000; ++it) {
+        const double u = rng.uniform() - 0.5;
+        double v = rng.uniform();
+        const double us = 0.5 - fabs(u);
+        const double kf = floor((2.0 * a / us + b) * u + c);
+        if (kf < 0.0 || kf > n) continue;
+        if (us >= 0.07 && v <= vr) return (uint64_t)kf;
+        v = log(v * alpha / (a / (us * us) + b));
+        const double bound = (m + 0.5) * log((m + 1.0) / (r * (n - m + 1.0))) +
+                             (n + 1.0) * log((n - m + 1.0) / (n - kf + 1.0)) +
+                             (kf + 0.5) * log(r * (n - kf + 1.0) / (kf + 1.0)) + stirling_tail(m) +
+                             stirling_tail(n - m) - stirling_tail(kf) - stirling_tail(n - kf);
+        if (v <= bound) return (uint64_t)kf;
+    }
+    record_status(st, NNQS_E_TIMEOUT, -3);
+    return (uint64_t)m;
+}
+
+__device__ uint64_t binomial(uint64_t n, double p, Philox &rng, DevStatus *st) {
+    if (n == 0 || !(p > 0.0)) return 0;
+    if (p >= 1.0) return n;
+    const bool flip = p > 0.5;
+    const double pp = flip ? 1.0 - p : p;
+    const uint64_t k = (double(n) * pp < 14.0) ? binom_inversion(n, pp, rng, st) : binom_btrs(n, pp, rng, st);
+    const uint64_t kk = k > n ? n : k;
+    return flip ? n - kk : kk;
+}
+
+// multinomial split of each prefix's count; nchild[i] = children with count > 0
+__global__ void k_split(const uint64_t *__restrict__ w, const double *__restrict__ cond, int64_t n, int step,
+                        uint64_t seed, uint64_t *__restrict__ counts, int32_t *__restrict__ nchild, DevStatus *st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Philox rng;
+    rng.k0 = (uint32_t)seed;
+    rng.k1 = (uint32_t)(seed >> 32);
+    rng.c0 = (uint32_t)i;
+    rng.c1 = (uint32_t)((uint64_t)i >> 32);
+    rng.c2 = (uint32_t)step;
+    rng.c3 = 0;
+    uint64_t rem = w[i];
+    double prem = 1.0;
+    int last = -1;  // the last child the mask allows takes what is left
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        if (cond[i * 4 + v] > 0.0) last = v;
+    if (last < 0 && rem > 0) record_status(st, NNQS_E_SECTOR, i);
+    int nc = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double pv = cond[i * 4 + v];
+        uint64_t k = 0;
+        if (v == last) {
+            k = rem;
+        } else if (v < last && pv > 0.0 && rem > 0) {
+            const double q = prem > 0.0 ? fmin(1.0, fmax(0.0, pv / prem)) : 0.0;
+            k = binomial(rem, q, rng, st);
+        }
+        counts[i * 4 + v] = k;
+        rem -= k;
+        prem -= pv;
+        nc += k > 0;
+    }
+    nchild[i] = nc;
+}
+
+// exclusive scan, 1024 per block; block totals to bsum
+constexpr int kScan = 1024;
+__global__ void k_scan_blocks(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ out,
+                              int64_t *__restrict__ bsum) {
+    __shared__ int64_t sh[kScan];
+    const int64_t i = blockIdx.x * (int64_t)kScan + threadIdx.x;
+    const int64_t v = i < n ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < kScan; off <<= 1) {
+        const int64_t t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = sh[threadIdx.x] - v;
+    if (threadIdx.x == kScan - 1) bsum[blockIdx.x] = sh[kScan - 1];
+}
+
+// sequential scan of the block totals in one block, chunk by chunk
+__global__ void k_scan_sums(int64_t *__restrict__ bsum, int64_t nb, int64_t *__restrict__ total) {
+    __shared__ int64_t sh[kScan];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nb; c0 += kScan) {
+        const int64_t i = c0 + threadIdx.x;
+        const int64_t v = i < nb ? bsum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < kScan; off <<= 1) {
+            const int64_t t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == kScan - 1) carry += sh[kScan - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ bsum) {
+    const int64_t i = blockIdx.x * (int64_t)kScan + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+// children of prefix i in token order at slots off[i] ...
+__global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
+                       const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
+                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, DevStatus *st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = off[i];
+    const int p = T - 1 - step;  // orbital of this token
+    for (int v = 0; v < 4; ++v) {
+        const uint64_t c = counts[i * 4 + v];
+        if (c == 0) continue;
+        if (j >= cap) {
+            record_status(st, NNQS_E_TABLE_FULL, i);
+            return;
+        }
+        for (int w = 0; w < W; ++w) npref[j * W + w] = pref[i * W + w];
+        if (v & 1) npref[j * W + ((2 * p) >> 6)] |= 1ull << ((2 * p) & 63);
+        if (v & 2) npref[j * W + ((2 * p + 1) >> 6)] |= 1ull << ((2 * p + 1) & 63);
+        nw[j] = c;
+        ++j;
+    }
+}
+
+struct SLayout {
+    uint64_t *pref[2], *w[2], *counts;
+    double *cond;
+    int32_t *nchild;
+    int64_t *off, *bsum, *total;
+    char *region;
+};
+
+SLayout slayout(const nnqs_model *M, int64_t cap, int prec, Arena &a) {
+    SLayout L{};
+    const int W = M->W;
+    for (int k = 0; k < 2; ++k) {
+        L.pref[k] = a.take<uint64_t>(size_t(cap) * W);
+        L.w[k] = a.take<uint64_t>(size_t(cap));
+    }
+    L.counts = a.take<uint64_t>(size_t(cap) * 4);
+    L.cond = a.take<double>(size_t(cap) * 4);
+    L.nchild = a.take<int32_t>(size_t(cap));
+    L.off = a.take<int64_t>(size_t(cap));
+    L.bsum = a.take<int64_t>(size_t((cap + kScan - 1) / kScan + 1));
+    L.total = a.take<int64_t>(1);
+    L.region = a.take<char>(cond_workspace(M, cap, prec));
+    return L;
+}
+
+}  // namespace
+}  // namespace nnqs
+
+using namespace nnqs;
+
+extern "C" size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec) {
+    if (!M || max_unique < 1) return 0;
+    Arena a(nullptr);
+    a.take<char>(kStatusBytes);
+    slayout(M, max_unique, prec, a);
+    return a.used + 1024;
+}
+
+extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uint64_t n_samples, uint64_t seed,
+                                   int prec, int64_t max_unique, uint64_t *samples_out, uint64_t *weights_out,
+                                   int64_t *n_unique_out, void *workspace, size_t workspace_bytes, nnqs_stream stream) {
+    if (!M || !params || !samples_out || !weights_out || !n_unique_out || max_unique < 1)
+        return set_error(NNQS_E_INVAL, "null argument or max_unique < 1");
+    if (prec != NNQS_FP64 && prec != NNQS_FP32 && prec != NNQS_MIXED) return set_error(NNQS_E_INVAL, "bad precision");
+    if (n_samples > (uint64_t(1) << 53)) return set_error(NNQS_E_INVAL, "n_samples above 2^53");
+    *n_unique_out = 0;
+    const size_t need = nnqs_sample_workspace_size(M, max_unique, prec);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256 || workspace_bytes < need)
+        return set_error(NNQS_E_WORKSPACE, "workspace null, misaligned or smaller than " + std::to_string(need));
+    cudaStream_t s = (cudaStream_t)stream;
+    NNQS_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(DevStatus), s));
+    Arena a(workspace);
+    DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
+    const SLayout L = slayout(M, max_unique, prec, a);
+    if (n_samples == 0) return NNQS_OK;
+    Arena sub(L.region);
+    CondCtx *ctx = nullptr;
+    nnqs_status rc = cond_create(M, params, prec, max_unique, sub, &ctx, s);
+    if (rc != NNQS_OK) {
+        cond_destroy(ctx);
+        return rc;
+    }
+    const int W = M->W, T = M->T;
+    // level 0: the empty prefix holds every sample
+    NNQS_CUDA_TRY(cudaMemsetAsync(L.pref[0], 0, size_t(W) * 8, s));
+    NNQS_CUDA_TRY(cudaMemcpyAsync(L.w[0], &n_samples, 8, cudaMemcpyHostToDevice, s));
+    int64_t n = 1;
+    int cur = 0;
+    for (int t = 0; t < T && rc == NNQS_OK; ++t) {
+        rc = cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s);
+        if (rc != NNQS_OK) break;
+        k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st);
+        const int64_t nb = (n + kScan - 1) / kScan;
+        k_scan_blocks<<<(unsigned)nb, kScan, 0, s>>>(L.nchild, n, L.off, L.bsum);
+        k_scan_sums<<<1, kScan, 0, s>>>(L.bsum, nb, L.total);
+        k_scan_add<<<(unsigned)nb, kScan, 0, s>>>(L.off, n, L.bsum);
+        int64_t next = 0;
+        cudaError_t e = cudaMemcpyAsync(&next, L.total, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_error(e, "sampler step");
+            break;
+        }
+        if (next > max_unique) {
+            rc = set_error(NNQS_E_TABLE_FULL, "step " + std::to_string(t) + " holds " + std::to_string(next) +
+                                                  " prefixes, above max_unique " + std::to_string(max_unique));
+            break;
+        }
+        k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t, max_unique, L.pref[cur ^ 1],
+                                                L.w[cur ^ 1], st);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = cuda_error(e, "sampler kernels");
+            break;
+        }
+        cur ^= 1;
+        n = next;
+    }
+    cond_destroy(ctx);
+    if (rc != NNQS_OK) return rc;
+    NNQS_CUDA_TRY(cudaMemcpyAsync(samples_out, L.pref[cur], size_t(n) * W * 8, cudaMemcpyDeviceToDevice, s));
+    NNQS_CUDA_TRY(cudaMemcpyAsync(weights_out, L.w[cur], size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+    *n_unique_out = n;
+    return NNQS_OK;
+}

@@ -1,0 +1,27 @@
+// BF16 tensor-core (tcgen05) linear layers for NNQS_MIXED: BF16 copies of
+// the weight matrices, and Y = X W^T + epilogue with FP32 accumulation.
+#pragma once
+#include "model.h"
+
+namespace nnqs {
+
+struct TcWeights {
+    int n_slots = 0;
+    void *bf16 = nullptr;          // all weight matrices, BF16, padded
+    int64_t off[4 * 64 + 1] = {};  // element offset of each slot
+    int32_t rows[4 * 64 + 1] = {}, cols[4 * 64 + 1] = {}, prows[4 * 64 + 1] = {}, pcols[4 * 64 + 1] = {};
+    int64_t src[4 * 64 + 1] = {};  // offset of the FP32 source matrix in the parameter vector
+};
+
+// slot of a weight: layer l, which = 0 qkv, 1 out-proj, 2 FFN-in, 3 FFN-out;
+// (L, 0) = phase MLP hidden layer
+inline int tc_slot(int layer, int which) { return layer * 4 + which; }
+
+void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w = nullptr);
+nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeights &w, cudaStream_t s);
+
+template <class R>
+nnqs_status tc_linear_fwd(cudaStream_t s, const TcWeights &w, int slot, int epi, const R *X, int64_t rows,
+                          int64_t in, const R *bias, R *Y, R *Y2, const R *resid);
+
+}  // namespace nnqs

@@ -164,6 +164,55 @@ def random_sector_samples(n_spatial: int, n_alpha: int, n_beta: int,
     return sort_keys(np.array(out, dtype=np.uint64))
 
 
+def clustered_sector_samples(n_spatial: int, n_alpha: int, n_beta: int, n_unique: int,
+                             seed: int, n_centers: int = 8, orbitals=None) -> np.ndarray:
+    """``n_unique`` distinct sector bitstrings concentrated around a few random
+    centres: each is a centre with 0-2 electrons moved within their spin
+    (the shape of a sample set drawn from a peaked wave function, where many
+    samples are coupled to each other).  ``orbitals`` restricts occupations
+    to a subset of spatial orbitals.  Sorted."""
+    rng = np.random.default_rng(seed)
+    orbs = np.arange(n_spatial) if orbitals is None else np.asarray(orbitals)
+    N = 2 * n_spatial
+    centres = []
+    for _ in range(n_centers):
+        a = rng.choice(orbs, n_alpha, replace=False)
+        b = rng.choice(orbs, n_beta, replace=False)
+        centres.append((set(a.tolist()), set(b.tolist())))
+    seen = set()
+    out = []
+    guard = 0
+    while len(out) < n_unique:
+        guard += 1
+        if guard > 200 * n_unique + 10000:
+            raise ValueError("cannot draw that many distinct clustered samples")
+        a, b = centres[rng.integers(n_centers)]
+        a, b = set(a), set(b)
+        for _ in range(rng.integers(0, 3)):
+            spin = a if rng.random() < 0.5 else b
+            occ = sorted(spin)
+            free = sorted(set(orbs.tolist()) - spin)
+            if occ and free:
+                spin.remove(occ[rng.integers(len(occ))])
+                spin.add(free[rng.integers(len(free))])
+        bits = np.zeros(N, dtype=np.uint8)
+        bits[[2 * p for p in a]] = 1
+        bits[[2 * p + 1 for p in b]] = 1
+        key = bits.tobytes()
+        if key in seen:
+            continue
+        seen.add(key)
+        out.append(bits)
+    return sort_keys(pack_occupations(np.array(out)))
+
+
+def random_logpsi(n: int, seed: int, amp_std: float = 1.0, phase_std: float = 1.0) -> np.ndarray:
+    """[n, 2] table of (log|psi|, phase) values, N(0, amp_std) and
+    N(0, phase_std): a stand-in wave-function table for sample-aware sums."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.normal(0.0, amp_std, n), rng.normal(0.0, phase_std, n)], axis=1)
+
+
 def uniform_counts(n_unique: int, n_draws: int, seed: int) -> np.ndarray:
     """Counts from ``n_draws`` uniform draws with replacement over n_unique
     states (zero counts kept)."""

@@ -1,0 +1,132 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function
+include/nnqs.h declares, and its host-side Hamiltonian builder (Eq. eham ->
+Eq. sham, Alg. 1) reproduces the oracle's tables: masks, offsets and the
+coupled sets bit for bit, coefficients to rounding."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as OH
+from paper_2306_16705_gb300 import _build
+from paper_2306_16705_gb300 import binding as B
+from paper_2306_16705_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    B.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "nnqs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nnqs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    import ctypes
+    L = ctypes.CDLL(B.lib_path())
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding declares the same set
+    assert set(names) == set(B._SIGS), set(names) ^ set(B._SIGS)
+
+
+def _compare(n, seed, rank, e_core=0.0):
+    h, eri = I.integrals(n, seed, rank)
+    ham = B.build_pauli(h, eri, e_core, device=False)
+    gxy, off, yz, coef = ham.export()
+    oxy, oyz, ocoef = OH.build(h, eri, e_core)
+    ogxy, ooff, _, _ = OH.group(oxy, oyz, ocoef)
+    assert np.array_equal(gxy, ogxy)
+    assert np.array_equal(off, ooff)
+    assert np.array_equal(yz, oyz)
+    assert np.abs(coef - ocoef).max() <= 1e-13 * max(1.0, np.abs(ocoef).max())
+    return ham, (oxy, oyz, ocoef)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6])
+def test_host_builder_matches_oracle_small(n):
+    _compare(n, 40 + n, 3, e_core=0.7)
+
+
+def test_host_builder_matches_oracle_n40_and_coupled_sets():
+    wl = I.WORKLOADS["n40"]
+    ham, (oxy, oyz, ocoef) = _compare(wl.n_spatial, wl.seed, wl.rank)
+    info = ham.info()
+    assert (info["n_terms"], info["n_groups"]) == (233001, 46171)
+    S = I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 3, seed=5)
+    for x in S:
+        xs, hs = ham.coupled(x, wl.n_alpha, wl.n_beta)
+        oxs, ohs = OH.coupled(oxy, oyz, ocoef, x, wl.n_alpha, wl.n_beta)
+        o = np.lexsort([xs[:, w] for w in range(xs.shape[1])])
+        assert np.array_equal(xs[o], oxs)  # same set, bit-exact
+        assert np.abs(hs[o] - ohs).max() < 1e-12
+
+
+def test_host_builder_two_words():
+    """A 70-qubit molecule (two words per bitstring) with a sparse active set
+    so the oracle stays fast: orbitals straddling qubit 64."""
+    n = 35
+    h0, eri0 = I.integrals(5, 77, 3)
+    act = [0, 16, 31, 32, 34]
+    h = np.zeros((n, n))
+    eri = np.zeros((n, n, n, n))
+    h[np.ix_(act, act)] = h0
+    eri[np.ix_(act, act, act, act)] = eri0
+    ham, (oxy, oyz, ocoef) = _compare_arrays(h, eri)
+    assert ham.info()["n_words"] == 2
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        occ = np.zeros(70, dtype=np.uint8)
+        for p in rng.choice(act, 2, replace=False):
+            occ[2 * p] = 1
+        for p in rng.choice(act, 3, replace=False):
+            occ[2 * p + 1] = 1
+        x = I.pack_occupations(occ[None])[0]
+        xs, hs = ham.coupled(x, 2, 3)
+        oxs, ohs = OH.coupled(oxy, oyz, ocoef, x, 2, 3)
+        o = np.lexsort([xs[:, w] for w in range(2)])
+        assert np.array_equal(xs[o], oxs)
+        assert np.abs(hs[o] - ohs).max() < 1e-12
+
+
+def _compare_arrays(h, eri):
+    ham = B.build_pauli(h, eri, device=False)
+    gxy, off, yz, coef = ham.export()
+    oxy, oyz, ocoef = OH.build(h, eri)
+    ogxy, ooff, _, _ = OH.group(oxy, oyz, ocoef)
+    assert np.array_equal(gxy, ogxy) and np.array_equal(off, ooff) and np.array_equal(yz, oyz)
+    assert np.abs(coef - ocoef).max() <= 1e-13 * max(1.0, np.abs(ocoef).max())
+    return ham, (oxy, oyz, ocoef)
+
+
+def test_argument_errors_are_status_codes():
+    h, eri = I.integrals(2, 0, 1)
+    with pytest.raises(B.NNQSError) as e:
+        B.build_pauli(np.zeros((65, 65)), np.zeros((1,)), device=False)
+    assert e.value.status == B.E_INVAL
+    bad = h.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(B.NNQSError) as e:
+        B.build_pauli(bad, eri, device=False)
+    assert e.value.status == B.E_NONFINITE
+
+
+def test_model_layout_matches_named_shapes():
+    wl = I.WORKLOADS["n40"]
+    m = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+    shapes = I.ansatz_shapes(wl.n_qubits, wl.d_model, wl.n_layers)
+    off = 0
+    for name, shape in shapes:
+        o, n = m.offset(name)
+        assert (o, n) == (off, int(np.prod(shape))), name
+        off += n
+    assert m.n_params == off

@@ -1,0 +1,112 @@
+"""GPU parity of the ansatz (Sec. 3.1, mask of Sec. 3.3): log psi forward
+and its reverse mode through the C ABI against the FP64 oracle, FP64 and
+FP32 paths, including chunked batches and out-of-sector inputs.
+
+Tolerances: FP64 path 1e-10 relative (different summation order only);
+FP32 path 2e-4 absolute on log|psi| and phase (single rounding over ~10^2
+accumulated terms per output); gradients relative to the largest entry of
+each tensor: 1e-9 (FP64), 2e-3 (FP32)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ansatz as OA
+from paper_2306_16705_gb300 import binding as B
+from paper_2306_16705_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    B.lib()
+
+
+def make(n_qubits, na, nb, d, L, H, seed, hidden=512, std=0.3):
+    params = I.ansatz_params(n_qubits, d, L, seed, std=std, bias_std=0.1, phase_std=0.15)
+    if hidden != 512:
+        params = {k: v for k, v in params.items()}
+        rng = np.random.default_rng(seed + 1)
+        params["phase.w1"] = rng.normal(0, 0.15, (hidden, n_qubits)).astype(np.float32)
+        params["phase.b1"] = rng.normal(0, 0.1, hidden).astype(np.float32)
+        params["phase.w2"] = rng.normal(0, 0.15, (hidden, hidden)).astype(np.float32)
+        params["phase.b2"] = rng.normal(0, 0.1, hidden).astype(np.float32)
+        params["phase.w3"] = rng.normal(0, 0.15, (1, hidden)).astype(np.float32)
+    m = B.Model(n_qubits, na, nb, d, L, H, hidden)
+    return m, params, m.pack(params)
+
+
+CASES = [  # (name, n_qubits, n_alpha, n_beta, d, L, heads, n_samples)
+    ("n12", 12, 3, 3, 32, 2, 4, 400),
+    ("n40", 40, 10, 10, 64, 4, 8, 300),
+    ("w2", 70, 5, 6, 16, 2, 2, 100),
+    ("dh16", 24, 4, 5, 64, 1, 4, 200),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+def test_logpsi_matches_oracle(case, prec):
+    name, N, na, nb, d, L, H, ns = case
+    m, params, flat = make(N, na, nb, d, L, H, seed=11)
+    x = I.random_sector_samples(N // 2, na, nb, ns, seed=3)
+    got = B.logpsi(m, flat, B.to_device_bits(x), prec).cpu().numpy()
+    la, ph = OA.forward(params, I.unpack_bits(x, N), na, nb, H)
+    if prec == B.FP64:
+        assert np.abs(got[:, 0] - la).max() <= 1e-10 * max(1.0, np.abs(la).max())
+        assert np.abs(got[:, 1] - ph).max() <= 1e-10 * max(1.0, np.abs(ph).max())
+    else:
+        assert np.abs(got[:, 0] - la).max() <= 2e-4 * max(1.0, np.abs(la).max())
+        assert np.abs(got[:, 1] - ph).max() <= 2e-4 * max(1.0, np.abs(ph).max())
+
+
+def test_logpsi_normalised_on_gpu():
+    """sum over the whole sector of |psi|^2 = exp(2 log|psi|) is 1."""
+    m, params, flat = make(12, 3, 3, 32, 2, 4, seed=2)
+    S = I.sector_states(6, 3, 3)
+    lp = B.logpsi(m, flat, B.to_device_bits(S), B.FP64).cpu().numpy()
+    assert abs(np.exp(2 * lp[:, 0]).sum() - 1.0) < 1e-12
+
+
+def test_logpsi_chunked_batch():
+    """More samples than one activation chunk: results are independent of the
+    chunking (rows repeat; log psi needs no uniqueness)."""
+    m, params, flat = make(12, 3, 3, 32, 2, 4, seed=5)
+    S = I.sector_states(6, 3, 3)
+    x = np.concatenate([S] * 90)  # 36000 rows > one chunk of 32768
+    got = B.logpsi(m, flat, B.to_device_bits(x), B.FP64).cpu().numpy()
+    ref = B.logpsi(m, flat, B.to_device_bits(S), B.FP64).cpu().numpy()
+    assert np.array_equal(got, np.concatenate([ref] * 90))
+
+
+def test_out_of_sector_reports_status():
+    m, params, flat = make(12, 3, 3, 32, 2, 4, seed=5)
+    x = I.sector_states(6, 3, 3)[:20].copy()
+    x[4, 0] ^= np.uint64(1)
+    with pytest.raises(B.NNQSError) as e:
+        B.logpsi(m, flat, B.to_device_bits(x), B.FP64)
+    assert e.value.status == B.E_SECTOR
+    out = B.logpsi(m, flat, B.to_device_bits(x), B.FP64, check=False).cpu().numpy()
+    assert out[4, 0] == -np.inf and np.all(np.isfinite(np.delete(out[:, 0], 4)))
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+def test_backward_matches_oracle(case, prec):
+    name, N, na, nb, d, L, H, ns = case
+    ns = min(ns, 160)
+    m, params, flat = make(N, na, nb, d, L, H, seed=13, hidden=96 if N > 40 else 512)
+    x = I.random_sector_samples(N // 2, na, nb, ns, seed=4)
+    rng = np.random.default_rng(0)
+    seed = np.stack([rng.normal(size=ns), rng.normal(size=ns)], 1)
+    g = B.logpsi_backward(m, flat, B.to_device_bits(x), torch.from_numpy(seed).cuda(), prec)
+    G = m.unpack(g, params)
+    _, _, cache = OA.forward(params, I.unpack_bits(x, N), na, nb, H, want_cache=True)
+    R = OA.backward(cache, seed[:, 0], seed[:, 1])
+    tol = 1e-9 if prec == B.FP64 else 2e-3
+    for k in params:
+        ref = R[k]
+        err = np.abs(G[k] - ref).max()
+        assert err <= tol * max(1e-3, np.abs(ref).max()), (k, err, np.abs(ref).max())

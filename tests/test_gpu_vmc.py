@@ -1,0 +1,208 @@
+"""GPU parity of the rest of the VMC step against the oracle: exact-mode
+local energy (every coupled x', Eq. Eloc), the composite energy/gradient call
+(Sec. 2.1 estimator), finite differences of its surrogate, the batch
+autoregressive sampler (Sec. 3.1 BAS, mask of Sec. 3.3) and Adam."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ansatz as OA
+from oracle import hamiltonian as OH
+from oracle import vmc as OV
+from paper_2306_16705_gb300 import binding as B
+from paper_2306_16705_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    B.lib()
+
+
+def model_for(wl, seed=7, std=0.3, hidden=512):
+    params = I.ansatz_params(wl.n_qubits, wl.d_model, wl.n_layers, seed, std=std, bias_std=0.1,
+                             phase_std=0.1)
+    m = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads, hidden)
+    return m, params, m.pack(params)
+
+
+def c(a):
+    a = a.cpu().numpy()
+    return a[:, 0] + 1j * a[:, 1]
+
+
+@pytest.fixture(scope="module")
+def n12():
+    wl = I.WORKLOADS["n12"]
+    h, eri = I.workload_integrals(wl)
+    return wl, B.build_pauli(h, eri), OH.build(h, eri), h, eri
+
+
+def test_exact_mode_n12(n12):
+    wl, ham, strings, h, eri = n12
+    m, params, flat = model_for(wl)
+    S = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    rows = S[::7].copy()
+
+    def fn(packed):
+        return OA.forward(params, I.unpack_bits(packed, wl.n_qubits), wl.n_alpha, wl.n_beta, wl.n_heads)
+
+    ref = OH.eloc_exact(*strings, rows, wl.n_alpha, wl.n_beta, fn)
+    got = c(B.eloc(ham, B.to_device_bits(rows), None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=m,
+                   params=flat, prec=B.FP64))
+    assert np.abs(got - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
+    # exact over the whole sector == sample-aware with S = whole sector
+    la, ph = fn(S)
+    sa = c(B.eloc(ham, B.to_device_bits(S), torch.from_numpy(np.stack([la, ph], 1)).cuda(),
+                  wl.n_alpha, wl.n_beta))
+    ex = c(B.eloc(ham, B.to_device_bits(S), None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=m,
+                  params=flat, prec=B.FP64))
+    assert np.abs(sa - ex).max() <= 1e-10 * max(1.0, np.abs(ex).max())
+
+
+def test_exact_mode_n40_two_rows():
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    strings = OH.build(h, eri)
+    m, params, flat = model_for(wl, std=0.2)
+    rows = I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 2, seed=12)
+
+    def fn(packed):
+        return OA.forward(params, I.unpack_bits(packed, wl.n_qubits), wl.n_alpha, wl.n_beta, wl.n_heads)
+
+    ref = OH.eloc_exact(*strings, rows, wl.n_alpha, wl.n_beta, fn)
+    got = c(B.eloc(ham, B.to_device_bits(rows), None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=m,
+                   params=flat, prec=B.FP64))
+    assert np.abs(got - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
+
+
+def test_energy_grad_matches_oracle(n12):
+    wl, ham, strings, h, eri = n12
+    m, params, flat = model_for(wl, seed=8)
+    S = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    w = I.uniform_counts(len(S), 1024, seed=0)
+    keep = w > 0
+    S, w = S[keep], w[keep]
+    stats, el, g = B.energy_grad(ham, m, flat, B.to_device_bits(S),
+                                 torch.from_numpy(w.view(np.int64)).cuda(), B.FP64)
+    bits = I.unpack_bits(S, wl.n_qubits)
+    la, ph = OA.forward(params, bits, wl.n_alpha, wl.n_beta, wl.n_heads)
+    ref_el = OH.eloc_lut(*strings, S, np.stack([la, ph], 1), S, wl.n_alpha, wl.n_beta)
+    assert np.abs(c(el) - ref_el).max() <= 1e-10 * max(1.0, np.abs(ref_el).max())
+    E, var = OV.energy_stats(ref_el, w)
+    st = stats.cpu().numpy()
+    assert abs(st[0] - E.real) < 1e-10 and abs(st[1] - E.imag) < 1e-10
+    assert abs(st[2] - var) < 1e-9 * max(1, var) and st[3] == w.sum()
+    G = m.unpack(g, params)
+    R = OV.energy_grad(params, bits, ref_el, w, wl.n_alpha, wl.n_beta, wl.n_heads)
+    for k in params:
+        assert np.abs(G[k] - R[k]).max() <= 1e-8 * max(1e-3, np.abs(R[k]).max()), k
+
+
+def test_energy_grad_finite_differences_n76():
+    """76 qubits (two words), d=64, 4 layers: the FP64 gradient against central
+    differences (h = 1e-4) of the surrogate 2 sum w [Re(E_loc-E) log|psi| +
+    Im(E_loc-E) phase] / sum w with E_loc, E frozen, on 16 random parameters."""
+    wl = I.WORKLOADS["n76"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    m, params, flat = model_for(wl, seed=21, std=0.1)
+    S = I.clustered_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 256, seed=5, n_centers=4)
+    w = np.random.default_rng(1).integers(1, 100, size=len(S)).astype(np.uint64)
+    xs = B.to_device_bits(S)
+    wt = torch.from_numpy(w.view(np.int64)).cuda()
+    stats, el, g = B.energy_grad(ham, m, flat, xs, wt, B.FP64)
+    st = stats.cpu().numpy()
+    e = c(el)
+    seed = np.stack([2 * w * (e.real - st[0]) / st[3], 2 * w * (e.imag - st[1]) / st[3]], 1)
+
+    def surrogate(fl):
+        lp = B.logpsi(m, fl, xs, B.FP64).cpu().numpy()
+        return float((seed[:, 0] * lp[:, 0]).sum() + (seed[:, 1] * lp[:, 1]).sum())
+
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(3)
+    idx = rng.choice(m.n_params, size=16, replace=False)
+    for k in idx:
+        fp = flat.clone()
+        fm = flat.clone()
+        fp[k] += 1e-4
+        fm[k] -= 1e-4
+        step = float(fp[k].item()) - float(fm[k].item())  # exact FP32 step
+        fd = (surrogate(fp) - surrogate(fm)) / step
+        assert abs(fd - g[k]) <= 1e-5 * max(1.0, abs(fd)) + 1e-7, (k, fd, g[k])
+
+
+def test_sampler_statistics_n12():
+    """Sum of counts = N_s, samples unique, sorted and in the sector, and a
+    chi-square test of the counts against the exact |psi|^2."""
+    wl = I.WORKLOADS["n12"]
+    m, params, flat = model_for(wl, seed=9, std=0.5)
+    S = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    p = OV.exact_distribution(params, I.unpack_bits(S, wl.n_qubits), wl.n_alpha, wl.n_beta,
+                              wl.n_heads)
+    for prec in (B.FP64, B.FP32):
+        Ns = 1_000_000
+        xs, ws = B.sample(m, flat, Ns, seed=123, max_unique=4096, prec=prec)
+        x = B.from_device_bits(xs)
+        wc = ws.cpu().numpy().astype(np.uint64)
+        assert wc.sum() == Ns and np.all(wc > 0)
+        assert np.array_equal(I.sort_keys(x), x)
+        assert len({int(v) for v in x[:, 0]}) == len(x)
+        pos = np.searchsorted(S[:, 0], x[:, 0])
+        assert np.all(S[pos, 0] == x[:, 0])  # every sample is a sector state
+        counts = np.zeros(len(S))
+        counts[pos] = wc
+        expct = Ns * p
+        big = expct > 20
+        chi2 = (((counts - expct) ** 2)[big] / expct[big]).sum()
+        dof = big.sum() - 1
+        # 5-sigma bound of the chi-square distribution
+        assert chi2 < dof + 5 * np.sqrt(2 * dof), (chi2, dof)
+
+
+def test_sampler_large_counts_and_determinism():
+    """N_s = 10^12 exercises the large-mean binomial; frequencies agree with
+    |psi|^2 within 6 standard deviations; the same seed repeats exactly."""
+    wl = I.WORKLOADS["n12"]
+    m, params, flat = model_for(wl, seed=10, std=0.5)
+    S = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    p = OV.exact_distribution(params, I.unpack_bits(S, wl.n_qubits), wl.n_alpha, wl.n_beta,
+                              wl.n_heads)
+    Ns = 10 ** 12
+    xs, ws = B.sample(m, flat, Ns, seed=7, max_unique=4096, prec=B.FP64)
+    x = B.from_device_bits(xs)
+    wc = ws.cpu().numpy().astype(np.uint64)
+    assert int(wc.sum()) == Ns
+    pos = np.searchsorted(S[:, 0], x[:, 0])
+    counts = np.zeros(len(S))
+    counts[pos] = wc.astype(np.float64)
+    sd = np.sqrt(Ns * p * (1 - p))
+    ok = p > 1e-9
+    assert np.all(np.abs(counts - Ns * p)[ok] <= 6 * sd[ok] + 1)
+    xs2, ws2 = B.sample(m, flat, Ns, seed=7, max_unique=4096, prec=B.FP64)
+    assert torch.equal(xs, xs2) and torch.equal(ws, ws2)
+    xs3, ws3 = B.sample(m, flat, Ns, seed=8, max_unique=4096, prec=B.FP64)
+    assert not torch.equal(ws, ws3)
+    with pytest.raises(B.NNQSError) as e:
+        B.sample(m, flat, Ns, seed=7, max_unique=100, prec=B.FP64)
+    assert e.value.status == B.E_TABLE_FULL
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(0)
+    n = 100003
+    theta = rng.normal(size=n).astype(np.float32)
+    pt = torch.from_numpy(theta.copy()).cuda()
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    th, mm, vv = theta.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in range(1, 4):
+        g = rng.normal(size=n).astype(np.float32)
+        B.adam_step(pt, torch.from_numpy(g).cuda(), m, v, step, lr=1e-3)
+        th, mm, vv = OV.adam_step(th, g.astype(np.float64), mm, vv, step)
+    assert np.abs(pt.cpu().numpy() - th).max() < 1e-6
