@@ -82,6 +82,21 @@ const char *nnqs_version(void);
  * `bad_index` (host, may be NULL) receives the offending row or -1. */
 nnqs_status nnqs_workspace_status(const void *workspace, nnqs_stream stream, int64_t *bad_index);
 
+/* Tracing.  Every kernel launch is counted per kernel family (the kernel's
+ * name); with profiling enabled each launch is also bracketed by CUDA
+ * events on its stream.  nnqs_profile_read synchronises the device, folds
+ * the recorded events into per-family totals and returns the number of
+ * families; family `index` (0-based) fills name (host, name_cap bytes),
+ * launches and total_ms (host, may be NULL).  Not part of the numerical
+ * method: instrumentation for benchmarks and tests. */
+void nnqs_profile_enable(int on);
+void nnqs_profile_reset(void);
+int nnqs_profile_read(int index, char *name, int name_cap, uint64_t *launches, double *total_ms);
+/* algorithmic work the launch sites attributed to family `index` since the
+ * last reset: floating-point operations and bytes (host outputs) */
+int nnqs_profile_work(int index, double *flops, double *bytes);
+uint64_t nnqs_launch_count(void); /* kernel launches since the library loaded */
+
 /* ------------------------------------------------------------------ */
 /* Hamiltonian: Eq. (eham) -> Jordan-Wigner Pauli strings, Eq. (sham),  */
 /* merged, coefficient-folded and grouped by X/Y mask as in Alg. 1 and  */

@@ -94,6 +94,12 @@ _SIGS = {
     "nnqs_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                    ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "nnqs_profile_enable": (None, [ctypes.c_int]),
+    "nnqs_profile_reset": (None, []),
+    "nnqs_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "nnqs_profile_work": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "nnqs_launch_count": (ctypes.c_uint64, []),
     "nnqs_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
@@ -386,3 +392,34 @@ def to_device_bits(x: np.ndarray, device="cuda") -> torch.Tensor:
 
 def from_device_bits(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+def profile_enable(on: bool = True):
+    lib().nnqs_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().nnqs_profile_reset()
+
+
+def launch_count() -> int:
+    return int(lib().nnqs_launch_count())
+
+
+def profile() -> dict:
+    """Per kernel family: launches, total device ms (while enabled), and the
+    algorithmic flops / bytes the library attributed to its launches."""
+    L = lib()
+    n = L.nnqs_profile_read(-1, None, 0, None, None)
+    out = {}
+    for i in range(n):
+        name = ctypes.create_string_buffer(128)
+        la = ctypes.c_uint64(0)
+        ms = ctypes.c_double(0)
+        L.nnqs_profile_read(i, name, 128, ctypes.byref(la), ctypes.byref(ms))
+        fl = ctypes.c_double(0)
+        by = ctypes.c_double(0)
+        L.nnqs_profile_work(i, ctypes.byref(fl), ctypes.byref(by))
+        out[name.value.decode()] = {"launches": la.value, "ms": ms.value, "flops": fl.value,
+                                    "bytes": by.value}
+    return out

@@ -386,13 +386,13 @@ nnqs_status gemm(cudaStream_t s, int epi, const R *A, int64_t sAm, int64_t sAk, 
         g.partial = scr.buf;
     }
     dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM), (unsigned)splits);
-#define NNQS_GEMM_CASE(E)                                                                 \
-    case E:                                                                               \
-        k_gemm<R, E><<<grid, 256, 0, s>>>(g);                                             \
-        if (splits > 1) {                                                                 \
-            NNQS_CUDA_TRY(cudaGetLastError());                                            \
-            k_gemm_reduce<R, E><<<grid_for(M * N, 256), 256, 0, s>>>(g, splits);          \
-        }                                                                                 \
+    note_work("k_gemm", 2.0 * double(M) * double(N) * double(K),
+              double(sizeof(R)) * (double(M) * K + double(N) * K + double(M) * N));
+#define NNQS_GEMM_CASE(E)                                                                           \
+    case E:                                                                                         \
+        NNQS_LAUNCH("k_gemm", s, k_gemm<R, E><<<grid, 256, 0, s>>>(g));                             \
+        if (splits > 1)                                                                             \
+            NNQS_LAUNCH("k_gemm_reduce", s, k_gemm_reduce<R, E><<<grid_for(M * N, 256), 256, 0, s>>>(g, splits)); \
         break;
     switch (epi) {
         NNQS_GEMM_CASE(EPI_STORE)
@@ -403,7 +403,6 @@ nnqs_status gemm(cudaStream_t s, int epi, const R *A, int64_t sAm, int64_t sAk, 
         default: return set_error(NNQS_E_INVAL, "bad GEMM epilogue");
     }
 #undef NNQS_GEMM_CASE
-    NNQS_CUDA_TRY(cudaGetLastError());
     return NNQS_OK;
 }
 
@@ -436,12 +435,10 @@ nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *me
     const int64_t rpb = (rows + nblk - 1) / nblk;
     nblk = (rows + rpb - 1) / rpb;
     if (mode == 0)
-        k_colred<R, 0><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf);
+        NNQS_LAUNCH("k_colred", s, k_colred<R, 0><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf));
     else
-        k_colred<R, 1><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf);
-    NNQS_CUDA_TRY(cudaGetLastError());
-    k_sum_partials<R><<<grid_for(cols, 256), 256, 0, s>>>(scr.buf, nblk, cols, out);
-    NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_colred", s, k_colred<R, 1><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf));
+    NNQS_LAUNCH("k_sum_partials", s, k_sum_partials<R><<<grid_for(cols, 256), 256, 0, s>>>(scr.buf, nblk, cols, out));
     return NNQS_OK;
 }
 
@@ -850,8 +847,7 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
 
 template <int DH_, class R>
 nnqs_status launch_attn_fwd(cudaStream_t s, const R *qkv, R *o, R *lse, int64_t n, int T, int H, int d) {
-    k_attn_fwd<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, n, T, H, d);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_attn_fwd", s, k_attn_fwd<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, n, T, H, d));
     return NNQS_OK;
 }
 
@@ -872,10 +868,8 @@ nnqs_status attn_fwd(cudaStream_t s, int dh, const R *qkv, R *o, R *lse, int64_t
 template <int DH_, class R>
 nnqs_status launch_attn_bwd(cudaStream_t s, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
                             int64_t n, int T, int H, int d) {
-    k_attn_bwd_q<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-    NNQS_CUDA_TRY(cudaGetLastError());
-    k_attn_bwd_kv<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, lse, dout, Dbuf, dqkv, n, T, H, d);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_attn_bwd_q", s, k_attn_bwd_q<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d));
+    NNQS_LAUNCH("k_attn_bwd_kv", s, k_attn_bwd_kv<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, lse, dout, Dbuf, dqkv, n, T, H, d));
     return NNQS_OK;
 }
 
@@ -904,8 +898,7 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     const int Tm = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, W = M->W, N = M->N;
     const int T = S > 0 ? S : Tm;  // sequence length of this pass
     const int64_t rows = C * T;
-    k_embed<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, T, Tm, d, V.tok, V.pos, A.hbuf, A.tok);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_embed", s, k_embed<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, T, Tm, d, V.tok, V.pos, A.hbuf, A.tok));
     for (int l = 0; l < L; ++l) {
         const auto &Lw = V.layer[l];
         const int64_t k = A.keep ? l : 0;
@@ -914,9 +907,8 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
         R *hmid = A.hmid + k * rows * d;
         R *a = A.a + k * rows * d, *a2 = A.a2 + k * rows * d, *qkv = A.qkv + k * rows * 3 * d, *o = A.o + k * rows * d;
         R *u = A.u + k * rows * F, *gu = A.gu + k * rows * F;
-        k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, Lw.ln1g, Lw.ln1b, a, A.mean1 + k * rows,
-                                                             A.rstd1 + k * rows, rows, d);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, Lw.ln1g, Lw.ln1b, a, A.mean1 + k * rows,
+                                                             A.rstd1 + k * rows, rows, d));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 0), EPI_STORE, a, rows, d, Lw.bqkv, qkv, nullptr, nullptr));
         } else {
@@ -928,9 +920,8 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
         } else {
             NNQS_TRY(linear_fwd<R>(s, EPI_RESID, o, rows, d, Lw.wo, d, Lw.bo, hmid, nullptr, hin, A.scr));
         }
-        k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, Lw.ln2g, Lw.ln2b, a2, A.mean2 + k * rows,
-                                                             A.rstd2 + k * rows, rows, d);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, Lw.ln2g, Lw.ln2b, a2, A.mean2 + k * rows,
+                                                             A.rstd2 + k * rows, rows, d));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 2), EPI_GELU, a2, rows, d, Lw.b1, u, gu, nullptr));
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 3), EPI_RESID, gu, rows, F, Lw.b2, hout, nullptr, hmid));
@@ -940,27 +931,22 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
         }
     }
     const R *hlast = A.keep ? A.hbuf + (int64_t)L * rows * d : A.hbuf;
-    k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, V.lnf_g, V.lnf_b, A.hf, A.meanf, A.rstdf, rows, d);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, V.lnf_g, V.lnf_b, A.hf, A.meanf, A.rstdf, rows, d));
     if (cond) {
-        k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, T, Tm, d, M->cfg.n_alpha,
-                                                        M->cfg.n_beta, cond, st);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_cond_last", s, k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, T, Tm, d, M->cfg.n_alpha,
+                                                        M->cfg.n_beta, cond, st));
         return NNQS_OK;
     }
-    k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
-                                                    M->cfg.n_beta, A.pi, out, st, row_offset);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_head", s, k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
+                                                    M->cfg.n_beta, A.pi, out, st, row_offset));
     // phase MLP
-    k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_phase_in", s, k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
     if (tcw) {
         NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(L, 0), EPI_RELU, A.r1, C, P, V.b2p, A.z2, A.r2, nullptr));
     } else {
         NNQS_TRY(linear_fwd<R>(s, EPI_RELU, A.r1, C, P, V.w2p, P, V.b2p, A.z2, A.r2, nullptr, A.scr));
     }
-    k_phase_out<R><<<grid_for(C * 32, 256), 256, 0, s>>>(A.r2, V.w3p, V.b3p, C, P, out);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_phase_out", s, k_phase_out<R><<<grid_for(C * 32, 256), 256, 0, s>>>(A.r2, V.w3p, V.b3p, C, P, out));
     return NNQS_OK;
 }
 
@@ -995,31 +981,26 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     Scratch<R> scr = A.scr;
     (void)x;
     // ---- phase MLP
-    k_seed_cols<R><<<grid_for(C, 256), 256, 0, s>>>(seed, C, G.dph);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_seed_cols", s, k_seed_cols<R><<<grid_for(C, 256), 256, 0, s>>>(seed, C, G.dph));
     // dW3[0][u] += sum_i dph_i r2[i][u]; db3 += sum_i dph_i
     NNQS_TRY(linear_dw<R>(s, G.dph, C, 1, A.r2, P, gacc + Lo.ph_w3, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dph, nullptr, nullptr, nullptr, C, 1, gacc + Lo.ph_b3, scr));
-    k_phase_dz2<R><<<grid_for(C * P, 256), 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, G.dz2);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_phase_dz2", s, k_phase_dz2<R><<<grid_for(C * P, 256), 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, G.dz2));
     NNQS_TRY(linear_dw<R>(s, G.dz2, C, P, A.r1, P, gacc + Lo.ph_w2, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dz2, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b2, scr));
     NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz2, C, P, V.w2p, P, G.dz1, scr));
-    k_act_bwd<R, false><<<grid_for(C * P, 256), 256, 0, s>>>(G.dz1, A.z1, C * P);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_act_bwd", s, k_act_bwd<R, false><<<grid_for(C * P, 256), 256, 0, s>>>(G.dz1, A.z1, C * P));
     NNQS_TRY(linear_dw<R>(s, G.dz1, C, P, A.xf, N, gacc + Lo.ph_w1, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, scr));
     // ---- head
-    k_head_bwd<R><<<grid_for(rows * 4, 256), 256, 0, s>>>(A.pi, A.tok, seed, C, T, G.dz);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_head_bwd", s, k_head_bwd<R><<<grid_for(rows * 4, 256), 256, 0, s>>>(A.pi, A.tok, seed, C, T, G.dz));
     NNQS_TRY(linear_dw<R>(s, G.dz, rows, 4, A.hf, d, gacc + Lo.head_w, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dz, nullptr, nullptr, nullptr, rows, 4, gacc + Lo.head_b, scr));
     NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz, rows, 4, V.hw, d, G.dtmp, scr));
     // final LayerNorm
     const R *hlast = A.hbuf + (int64_t)L * rows * d;
-    k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0));
-    k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0)));
+    NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d));
     NNQS_TRY(colsum<R>(s, 1, G.dtmp, hlast, A.meanf, A.rstdf, rows, d, gacc + Lo.lnf_g, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lo.lnf_b, scr));
     for (int l = L - 1; l >= 0; --l) {
@@ -1034,14 +1015,12 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         NNQS_TRY(linear_dw<R>(s, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.b2, scr));
         NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dh, rows, d, Lw.w2, F, G.du, scr));
-        k_act_bwd<R, true><<<grid_for(rows * F, 256), 256, 0, s>>>(G.du, u, rows * F);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_act_bwd", s, k_act_bwd<R, true><<<grid_for(rows * F, 256), 256, 0, s>>>(G.du, u, rows * F));
         NNQS_TRY(linear_dw<R>(s, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
         NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, scr));
         NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.du, rows, F, Lw.w1, d, G.dtmp, scr));
-        k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
-                                                             G.dtmp, G.dh, rows, d);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
+                                                             G.dtmp, G.dh, rows, d));
         NNQS_TRY(colsum<R>(s, 1, G.dtmp, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, rows, d, gacc + Lg.ln2_g, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln2_b, scr));
         // attention: hmid = hin + attn(a) Wo^T + bo
@@ -1052,9 +1031,8 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         NNQS_TRY(linear_dw<R>(s, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, scr));
         NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
-        k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
-                                                             G.dtmp, G.dh, rows, d);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
+                                                             G.dtmp, G.dh, rows, d));
         NNQS_TRY(colsum<R>(s, 1, G.dtmp, hin, A.mean1 + l * rows, A.rstd1 + l * rows, rows, d, gacc + Lg.ln1_g, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln1_b, scr));
     }
@@ -1065,10 +1043,8 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(5 * d))));
         const int64_t rpb = (rows + nblk - 1) / nblk;
         nblk = (rows + rpb - 1) / rpb;
-        k_tok_grad<R><<<(unsigned)nblk, 128, 0, s>>>(G.dh, A.tok, C, T, d, rpb, scr.buf);
-        NNQS_CUDA_TRY(cudaGetLastError());
-        k_sum_partials<R><<<grid_for(5 * d, 256), 256, 0, s>>>(scr.buf, nblk, 5 * d, gacc + Lo.tok_emb);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_tok_grad", s, k_tok_grad<R><<<(unsigned)nblk, 128, 0, s>>>(G.dh, A.tok, C, T, d, rpb, scr.buf));
+        NNQS_LAUNCH("k_sum_partials", s, k_sum_partials<R><<<grid_for(5 * d, 256), 256, 0, s>>>(scr.buf, nblk, 5 * d, gacc + Lo.tok_emb));
     }
     return NNQS_OK;
 }
@@ -1117,8 +1093,7 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
     const int64_t C = chunk_for(M, n, sizeof(R), false);
     Acts<R> A;
     take_acts<R>(M, C, false, ws, A);
-    k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
     const Views<R> V = make_views<R>(M, pr);
     for (int64_t c0 = 0; c0 < n; c0 += C) {
@@ -1139,9 +1114,8 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
     take_acts<R>(M, C, true, ws, A);
     Grads<R> G;
     take_grads<R>(M, C, ws, G);
-    k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
-    k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0));
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
+    NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
     const Views<R> V = make_views<R>(M, pr);
     for (int64_t c0 = 0; c0 < n; c0 += C) {
         const int64_t cn = std::min(C, n - c0);
@@ -1149,8 +1123,7 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
         NNQS_TRY(forward_chunk<R>(M, V, xc, cn, A, G.lp, st, c0, nullptr, s));
         NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc, s));
     }
-    k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
     return NNQS_OK;
 }
 
@@ -1194,14 +1167,14 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
         c->params = pr;
         c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(double), false);
         take_acts<double>(M, c->C, false, ws, c->Ad);
-        k_convert_params<double><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
+        NNQS_LAUNCH("k_convert_params", s, k_convert_params<double><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     } else {
         float *pr = ws.take<float>(M->lay.total);
         c->params = pr;
         if (c->tensor) tc_weights_take(M, ws, &c->tcw);
         c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(float), false);
         take_acts<float>(M, c->C, false, ws, c->Af);
-        k_convert_params<float><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total);
+        NNQS_LAUNCH("k_convert_params", s, k_convert_params<float><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
         if (c->tensor) NNQS_TRY(tc_weights_prepare(M, params, c->tcw, s));
     }
     NNQS_CUDA_TRY(cudaGetLastError());

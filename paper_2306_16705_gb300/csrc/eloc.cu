@@ -258,31 +258,34 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
     if (n_rows == 0) return NNQS_OK;
     NNQS_CUDA_TRY(cudaMemsetAsync(hkeys, 0xFF, size_t(cap) * W * 8, s));
     HashTab<W> tab{hkeys, hvals, uint64_t(cap - 1)};
-    k_build_lut_hash<W><<<grid_for(n_lut, 256), 256, 0, s>>>(lut, n_lut, H->n_qubits, n_alpha, n_beta, tab, status);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_build_lut_hash", s, k_build_lut_hash<W><<<grid_for(n_lut, 256), 256, 0, s>>>(lut, n_lut, H->n_qubits, n_alpha, n_beta, tab, status));
     if (p.has_diag) {
-        k_diag<W><<<grid_for(n_rows * 32, 256), 256, 0, s>>>(lut, row_begin, n_rows, (uint32_t)H->goff[0],
-                                                             (uint32_t)H->goff[1], H->d_tyz, H->d_tcoef, diag);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_diag", s, k_diag<W><<<grid_for(n_rows * 32, 256), 256, 0, s>>>(lut, row_begin, n_rows, (uint32_t)H->goff[0],
+                                                             (uint32_t)H->goff[1], H->d_tyz, H->d_tcoef, diag));
     }
     const double2 *lp2 = reinterpret_cast<const double2 *>(lut_lp);
     if (p.chunks > 0) {
         dim3 grid((unsigned)p.row_tiles, (unsigned)p.chunks);
         if (p.pairs) {
             const int maxw = H->max_xy_weight;
+            // algorithmic work: one (row, sample) mask test each; bytes = one
+            // read of the sample table per row tile
+            note_work("k_sweep_pairs", double(n_rows) * double(n_lut),
+                      double(p.row_tiles) * double(n_lut) * (8.0 * W + 16.0));
             HashTab<W> gtab{H->d_ghkeys, H->d_ghvals, uint64_t(H->ghcap - 1)};
-            k_sweep_pairs<W><<<grid, kSweepThreads, 0, s>>>(lut, lp2, n_lut, p.per_chunk, maxw, gtab, H->d_goff,
-                                                            H->d_tyz, H->d_tcoef, row_begin, n_rows, partial);
+            NNQS_LAUNCH("k_sweep_pairs", s, k_sweep_pairs<W><<<grid, kSweepThreads, 0, s>>>(lut, lp2, n_lut, p.per_chunk, maxw, gtab, H->d_goff,
+                                                            H->d_tyz, H->d_tcoef, row_begin, n_rows, partial));
         } else {
-            k_sweep_groups<W><<<grid, kSweepThreads, 0, s>>>(H->d_gxy, H->d_goff, H->d_gspin, p.g_begin, p.g_end,
+            note_work("k_sweep_groups", double(n_rows) * double(p.g_end - p.g_begin),
+                      double(p.row_tiles) * double(p.g_end - p.g_begin) * (8.0 * W + 1.0));
+            NNQS_LAUNCH("k_sweep_groups", s, k_sweep_groups<W><<<grid, kSweepThreads, 0, s>>>(H->d_gxy, H->d_goff, H->d_gspin, p.g_begin, p.g_end,
                                                              p.per_chunk, H->d_tyz, H->d_tcoef, lut, lp2, tab,
-                                                             row_begin, n_rows, partial);
+                                                             row_begin, n_rows, partial));
         }
         NNQS_CUDA_TRY(cudaGetLastError());
     }
-    k_reduce_partials<<<grid_for(n_rows, 256), 256, 0, s>>>(p.has_diag ? diag : nullptr, partial, p.chunks, n_rows,
-                                                            reinterpret_cast<double2 *>(out));
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_reduce_partials", s, k_reduce_partials<<<grid_for(n_rows, 256), 256, 0, s>>>(p.has_diag ? diag : nullptr, partial, p.chunks, n_rows,
+                                                            reinterpret_cast<double2 *>(out)));
     return NNQS_OK;
 }
 
@@ -366,9 +369,8 @@ nnqs_status eloc_sa(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp
 size_t stats_workspace(int64_t) { return kStatusBytes + 256; }
 
 nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, double *stats, Arena &, cudaStream_t s) {
-    k_stats<<<1, kStatThreads, 3 * kStatThreads * sizeof(double), s>>>(reinterpret_cast<const double2 *>(eloc), w, n,
-                                                                        stats);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_stats", s, k_stats<<<1, kStatThreads, 3 * kStatThreads * sizeof(double), s>>>(reinterpret_cast<const double2 *>(eloc), w, n,
+                                                                        stats));
     return NNQS_OK;
 }
 

@@ -219,16 +219,13 @@ nnqs_status exact_impl(const nnqs_ham *H, const nnqs_model *M, const float *para
     NNQS_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, size_t(p.cap) * W * 8, s));
     NNQS_CUDA_TRY(cudaMemsetAsync(counter, 0, 8, s));
     HashTab<W> tab{keys, vals, uint64_t(p.cap - 1)};
-    k_insert_rows<W><<<grid_for(n_rows, 256), 256, 0, s>>>(lut, row_begin, n_rows, H->n_qubits, n_alpha, n_beta, tab, st);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_insert_rows", s, k_insert_rows<W><<<grid_for(n_rows, 256), 256, 0, s>>>(lut, row_begin, n_rows, H->n_qubits, n_alpha, n_beta, tab, st));
     if (p.chunks > 0) {
         dim3 grid((unsigned)p.row_tiles, (unsigned)p.chunks);
-        k_expand<W><<<grid, kThreads, 0, s>>>(H->d_gxy, H->d_gspin, p.g_begin, p.g_end, p.per_chunk, lut, row_begin,
-                                               n_rows, tab, st);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_expand", s, k_expand<W><<<grid, kThreads, 0, s>>>(H->d_gxy, H->d_gspin, p.g_begin, p.g_end, p.per_chunk, lut, row_begin,
+                                               n_rows, tab, st));
     }
-    k_compact<W><<<grid_for(p.cap, 256), 256, 0, s>>>(tab, p.cap, ulist, counter);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_compact", s, k_compact<W><<<grid_for(p.cap, 256), 256, 0, s>>>(tab, p.cap, ulist, counter));
     unsigned long long nU = 0;
     NNQS_CUDA_TRY(cudaMemcpyAsync(&nU, counter, 8, cudaMemcpyDeviceToHost, s));
     NNQS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -238,20 +235,17 @@ nnqs_status exact_impl(const nnqs_ham *H, const nnqs_model *M, const float *para
     if ((int64_t)nU > p.bound) return set_error(NNQS_E_TABLE_FULL, "coupled set larger than its bound");
     NNQS_TRY(logpsi_forward(M, params, ulist, (int64_t)nU, prec, lpU, ws, st, s));
     if (p.has_diag) {
-        k_diag<W><<<grid_for(n_rows * 32, 256), 256, 0, s>>>(lut, row_begin, n_rows, (uint32_t)H->goff[0],
-                                                             (uint32_t)H->goff[1], H->d_tyz, H->d_tcoef, diag);
-        NNQS_CUDA_TRY(cudaGetLastError());
+        NNQS_LAUNCH("k_diag", s, k_diag<W><<<grid_for(n_rows * 32, 256), 256, 0, s>>>(lut, row_begin, n_rows, (uint32_t)H->goff[0],
+                                                             (uint32_t)H->goff[1], H->d_tyz, H->d_tcoef, diag));
     }
     if (p.chunks > 0) {
         dim3 grid((unsigned)p.row_tiles, (unsigned)p.chunks);
-        k_sweep_exact<W><<<grid, kThreads, 0, s>>>(H->d_gxy, H->d_goff, H->d_gspin, p.g_begin, p.g_end, p.per_chunk,
+        NNQS_LAUNCH("k_sweep_exact", s, k_sweep_exact<W><<<grid, kThreads, 0, s>>>(H->d_gxy, H->d_goff, H->d_gspin, p.g_begin, p.g_end, p.per_chunk,
                                                    H->d_tyz, H->d_tcoef, lut, row_begin, n_rows, tab,
-                                                   reinterpret_cast<const double2 *>(lpU), partial, st);
-        NNQS_CUDA_TRY(cudaGetLastError());
+                                                   reinterpret_cast<const double2 *>(lpU), partial, st));
     }
-    k_reduce_partials<<<grid_for(n_rows, 256), 256, 0, s>>>(p.has_diag ? diag : nullptr, partial, p.chunks, n_rows,
-                                                            reinterpret_cast<double2 *>(out));
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_reduce_partials", s, k_reduce_partials<<<grid_for(n_rows, 256), 256, 0, s>>>(p.has_diag ? diag : nullptr, partial, p.chunks, n_rows,
+                                                            reinterpret_cast<double2 *>(out)));
     return NNQS_OK;
 }
 

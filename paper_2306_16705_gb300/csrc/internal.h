@@ -28,6 +28,30 @@ nnqs_status cuda_error(cudaError_t e, const char *where);
         if (_s != NNQS_OK) return _s;        \
     } while (0)
 
+// ---- launches: counting and optional CUDA-event timing (prof.cpp) ---------
+cudaError_t note_launch();  // counts one launch, returns cudaGetLastError()
+// algorithmic work (flops, bytes) of a launch, for roofline accounting
+void note_work(const char *name, double flops, double bytes);
+class ProfScope {
+   public:
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+
+   private:
+    const char *name_;
+    cudaStream_t s_;
+    cudaEvent_t e0_{}, e1_{};
+    bool on_ = false;
+};
+
+// every kernel launch of the library goes through this macro
+#define NNQS_LAUNCH(name, stream, ...)                   \
+    do {                                                 \
+        nnqs::ProfScope _nnqs_ps((name), (stream));      \
+        __VA_ARGS__;                                     \
+        NNQS_CUDA_TRY(nnqs::note_launch());              \
+    } while (0)
+
 // ---- device status word (first 256 bytes of every workspace) --------------
 // code: first error recorded (atomicCAS from 0); index: offending row.
 struct DevStatus {

@@ -37,8 +37,7 @@ extern "C" nnqs_status nnqs_adam_step(float *params, const float *grad, float *m
     const float lr_t = (float)(lr * std::sqrt(c2) / c1), eps_t = (float)(eps * std::sqrt(c2));
     const int block = 256;
     const int64_t blocks = std::min<int64_t>((n + block - 1) / block, 152 * 16);
-    k_adam<<<(unsigned)blocks, block, 0, (cudaStream_t)stream>>>(params, grad, m, v, n, lr_t, (float)beta1,
-                                                                 (float)beta2, eps_t);
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_adam", (cudaStream_t)stream, k_adam<<<(unsigned)blocks, block, 0, (cudaStream_t)stream>>>(params, grad, m, v, n, lr_t, (float)beta1,
+                                                                 (float)beta2, eps_t));
     return NNQS_OK;
 }

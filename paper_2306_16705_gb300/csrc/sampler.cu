@@ -324,36 +324,27 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     NNQS_CUDA_TRY(cudaMemcpyAsync(L.w[0], &n_samples, 8, cudaMemcpyHostToDevice, s));
     int64_t n = 1;
     int cur = 0;
-    for (int t = 0; t < T && rc == NNQS_OK; ++t) {
-        rc = cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s);
-        if (rc != NNQS_OK) break;
-        k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st);
+    auto step = [&](int t) -> nnqs_status {
+        NNQS_TRY(cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s));
+        NNQS_LAUNCH("k_split", s, k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts,
+                                                                           L.nchild, st));
         const int64_t nb = (n + kScan - 1) / kScan;
-        k_scan_blocks<<<(unsigned)nb, kScan, 0, s>>>(L.nchild, n, L.off, L.bsum);
-        k_scan_sums<<<1, kScan, 0, s>>>(L.bsum, nb, L.total);
-        k_scan_add<<<(unsigned)nb, kScan, 0, s>>>(L.off, n, L.bsum);
+        NNQS_LAUNCH("k_scan_blocks", s, k_scan_blocks<<<(unsigned)nb, kScan, 0, s>>>(L.nchild, n, L.off, L.bsum));
+        NNQS_LAUNCH("k_scan_sums", s, k_scan_sums<<<1, kScan, 0, s>>>(L.bsum, nb, L.total));
+        NNQS_LAUNCH("k_scan_add", s, k_scan_add<<<(unsigned)nb, kScan, 0, s>>>(L.off, n, L.bsum));
         int64_t next = 0;
-        cudaError_t e = cudaMemcpyAsync(&next, L.total, 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            rc = cuda_error(e, "sampler step");
-            break;
-        }
-        if (next > max_unique) {
-            rc = set_error(NNQS_E_TABLE_FULL, "step " + std::to_string(t) + " holds " + std::to_string(next) +
-                                                  " prefixes, above max_unique " + std::to_string(max_unique));
-            break;
-        }
-        k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t, max_unique, L.pref[cur ^ 1],
-                                                L.w[cur ^ 1], st);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            rc = cuda_error(e, "sampler kernels");
-            break;
-        }
+        NNQS_CUDA_TRY(cudaMemcpyAsync(&next, L.total, 8, cudaMemcpyDeviceToHost, s));
+        NNQS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (next > max_unique)
+            return set_error(NNQS_E_TABLE_FULL, "step " + std::to_string(t) + " holds " + std::to_string(next) +
+                                                    " prefixes, above max_unique " + std::to_string(max_unique));
+        NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t,
+                                                                         max_unique, L.pref[cur ^ 1], L.w[cur ^ 1], st));
         cur ^= 1;
         n = next;
-    }
+        return NNQS_OK;
+    };
+    for (int t = 0; t < T && rc == NNQS_OK; ++t) rc = step(t);
     cond_destroy(ctx);
     if (rc != NNQS_OK) return rc;
     NNQS_CUDA_TRY(cudaMemcpyAsync(samples_out, L.pref[cur], size_t(n) * W * 8, cudaMemcpyDeviceToDevice, s));

@@ -90,9 +90,8 @@ extern "C" nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, 
         Arena sub(L.region);
         NNQS_TRY(energy_stats(eloc, weights, n_u, stats, sub, s));
     }
-    k_seeds<<<grid_for(n_u, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(eloc), weights, stats, n_u,
-                                               reinterpret_cast<double2 *>(L.seed));
-    NNQS_CUDA_TRY(cudaGetLastError());
+    NNQS_LAUNCH("k_seeds", s, k_seeds<<<grid_for(n_u, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(eloc), weights, stats, n_u,
+                                               reinterpret_cast<double2 *>(L.seed)));
     {
         Arena sub(L.region);
         NNQS_TRY(logpsi_backward(M, params, samples, n_u, prec, L.seed, grad_f64, grad_f32, sub, st, s));

@@ -1,0 +1,104 @@
+"""VMC step on the GPU (Sec. 2.1, Fig. serial_flow): batch autoregressive
+sampling -> log psi -> sample-aware local energy -> energy statistics ->
+gradient -> Adam, every stage through the C ABI of libnnqs.so.
+
+``EnergyFunction`` exposes the same estimator as a torch.autograd.Function:
+its forward returns Re E and keeps the hand-written gradient
+2 Re E_p[(E_loc - E) d ln psi*] (computed by nnqs_energy_grad, E_loc held
+fixed) for its backward.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import binding as B
+
+
+class EnergyFunction(torch.autograd.Function):
+    """E(params) over the given unique samples and counts.  Backward returns
+    dE/dparams from the library's reverse mode (no autograd tape)."""
+
+    @staticmethod
+    def forward(ctx, params, ham, model, samples, weights, prec):
+        stats, el, grad = B.energy_grad(ham, model, params.detach(), samples, weights, prec,
+                                        check=True, dtype=params.dtype)
+        ctx.save_for_backward(grad)
+        ctx.eloc = el
+        ctx.stats = stats
+        return stats[0].to(params.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (grad,) = ctx.saved_tensors
+        return grad_out * grad, None, None, None, None, None
+
+
+@dataclasses.dataclass
+class StepResult:
+    energy: float
+    energy_imag: float
+    variance: float
+    n_samples: float
+    n_unique: int
+
+
+class VMC:
+    """Training state: parameters, Adam moments and reusable workspaces."""
+
+    def __init__(self, ham: B.Hamiltonian, model: B.Model, params: torch.Tensor, prec=B.MIXED,
+                 n_samples: int = 16384, max_unique: int = 1 << 16, lr: float = 1e-3,
+                 betas=(0.9, 0.999), eps: float = 1e-8, seed: int = 0):
+        self.ham, self.model, self.prec = ham, model, prec
+        self.params = params.contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self.n_samples, self.max_unique = int(n_samples), int(max_unique)
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.seed = int(seed)
+        self._ws_sample = None
+        self._ws_grad = None
+        self.grad = torch.empty_like(self.params)
+        self.last_samples = None
+        self.last_weights = None
+        self.last_stats = None
+
+    def sample(self, seed=None):
+        seed = self.seed * 1_000_003 + self.t if seed is None else seed
+        nb = B.lib().nnqs_sample_workspace_size(self.model.handle, self.max_unique, self.prec)
+        if self._ws_sample is None or self._ws_sample.numel() < nb:
+            self._ws_sample = B.workspace(nb, self.params.device)
+        return B.sample(self.model, self.params, self.n_samples, seed, self.max_unique, self.prec,
+                        check=False, ws=self._ws_sample)
+
+    def step(self, check: bool = False) -> torch.Tensor:
+        """One VMC iteration; returns the device stats tensor [Re E, Im E, Var,
+        sum w] (no host synchronisation beyond the sampler's)."""
+        x, w = self.sample()
+        stats, _, _ = B.energy_grad(self.ham, self.model, self.params, x, w, self.prec,
+                                    check=check, ws=self._ws_grad_for(x.shape[0]),
+                                    want_eloc=False, grad_out=self.grad)
+        self.t += 1
+        B.adam_step(self.params, self.grad, self.m, self.v, self.t, self.lr, self.betas[0],
+                    self.betas[1], self.eps)
+        self.last_samples, self.last_weights, self.last_stats = x, w, stats
+        return stats
+
+    def _ws_grad_for(self, n):
+        nb = B.lib().nnqs_energy_grad_workspace_size(self.ham.handle, self.model.handle, n, self.prec)
+        if self._ws_grad is None or self._ws_grad.numel() < nb:
+            self._ws_grad = B.workspace(int(nb * 1.25), self.params.device)
+        return self._ws_grad
+
+    def state_dict(self) -> dict:
+        return {"params": self.params.detach().cpu(), "m": self.m.cpu(), "v": self.v.cpu(),
+                "t": self.t, "seed": self.seed}
+
+    def load_state_dict(self, sd: dict):
+        self.params.copy_(sd["params"].to(self.params.device))
+        self.m.copy_(sd["m"].to(self.m.device))
+        self.v.copy_(sd["v"].to(self.v.device))
+        self.t = int(sd["t"])
+        self.seed = int(sd["seed"])
