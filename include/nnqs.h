@@ -226,6 +226,33 @@ nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *param
                       int prec, int flags, double *eloc_out, void *workspace,
                       size_t workspace_bytes, nnqs_stream stream);
 
+/* nnqs_eloc in NNQS_SA mode for callers that cannot allocate device memory:
+ * code running inside a host application that owns the GPU's memory (a
+ * framework whose pool has reserved the device, a plugin interface that
+ * hands out no allocator) cannot provide a workspace, and cudaMalloc itself
+ * synchronises the device, which a latency-bound caller cannot afford.  This
+ * entry point takes no workspace and allocates nothing: its scratch is one
+ * fixed 64 MiB array in device memory that every GPU loading the library
+ * holds until the process exits.  The paper has no counterpart: this is a
+ * calling convention, not part of the method.
+ *   Arguments and result as nnqs_eloc (mode NNQS_SA).  A call whose
+ *   scratch would exceed 64 MiB (roughly 10^6 rows and table entries for
+ *   N <= 64, somewhat fewer for two-word bitstrings) is rejected with
+ *   NNQS_E_INVAL; use nnqs_eloc with a workspace then.
+ *   check != 0: synchronise `stream` and return the status the kernels
+ *   recorded (sample outside the sector, duplicate, ...); check == 0: fully
+ *   asynchronous, such errors are not reported.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * previous call's contents (each call clears what must start at zero): calls
+ * whose execution overlaps on the GPU -- from two streams, or two host
+ * threads -- race on it and must be serialised by the caller. */
+nnqs_status nnqs_eloc_sa_noalloc(const nnqs_ham *H, const uint64_t *lut, const double *lut_logpsi,
+                                 int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha,
+                                 int n_beta, int flags, double *eloc_out, int check,
+                                 nnqs_stream stream);
+
 /* Coupled set of one row (parity and debugging): every x' = x ^ m over the
  * groups m that keep the sector, in group order, with H_{x x'} (host
  * outputs, at most `cap` entries; *count receives the number).  Host-side,

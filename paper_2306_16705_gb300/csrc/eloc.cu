@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "dev_common.cuh"
 #include "internal.h"
@@ -375,3 +376,75 @@ nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, doubl
 }
 
 }  // namespace nnqs
+
+// ---------------------------------------------------------------- no-allocation variant
+// Scratch for nnqs_eloc_sa_noalloc: one file-scope device array, present on
+// every GPU that loads this library until the process exits.  Host code must
+// not use the symbol itself as a device address: its device address is
+// looked up once per device with cudaGetSymbolAddress.
+namespace nnqs {
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// device address of the scratch array on the current device (looked up on
+// the first call per device, with that device current)
+nnqs_status noalloc_scratch(void **out) {
+    int dev = 0;
+    NNQS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(NNQS_E_UNSUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        NNQS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return NNQS_OK;
+}
+}  // namespace
+}  // namespace nnqs
+
+extern "C" nnqs_status nnqs_eloc_sa_noalloc(const nnqs_ham *H, const uint64_t *lut, const double *lut_logpsi,
+                                            int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha,
+                                            int n_beta, int flags, double *eloc_out, int check,
+                                            nnqs_stream stream) {
+    using namespace nnqs;
+    if (!H || !H->d_gxy) return set_error(NNQS_E_INVAL, "null Hamiltonian or one without device tables");
+    if (n_lut < 0 || n_rows < 0 || row_begin < 0 || row_begin + n_rows > n_lut)
+        return set_error(NNQS_E_INVAL, "rows out of range of the sample table");
+    if (n_lut >= (int64_t(1) << 31)) return set_error(NNQS_E_INVAL, "sample table larger than 2^31 rows");
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > H->n_spatial || n_beta > H->n_spatial)
+        return set_error(NNQS_E_INVAL, "electron counts out of range");
+    if (H->n_qubits % 64 == 0 && n_alpha == H->n_spatial && n_beta == H->n_spatial)
+        return set_error(NNQS_E_UNSUPPORTED, "fully occupied 64/128-qubit sector");
+    if (flags < NNQS_SWEEP_AUTO || flags > NNQS_SWEEP_PAIRS) return set_error(NNQS_E_INVAL, "unknown flags");
+    if (n_rows > 0 && (!lut || !lut_logpsi || !eloc_out)) return set_error(NNQS_E_INVAL, "null device pointer");
+    const size_t need = eloc_sa_workspace(H, n_lut, n_rows, flags);
+    if (need > kNoAllocScratchBytes)
+        return set_error(NNQS_E_INVAL, "nnqs_eloc_sa_noalloc: this table needs " + std::to_string(need) +
+                                           " bytes of scratch, above the fixed " +
+                                           std::to_string(kNoAllocScratchBytes) +
+                                           "; use nnqs_eloc with a workspace");
+    void *scratch = nullptr;
+    NNQS_TRY(noalloc_scratch(&scratch));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the status word starts at
+    // zero and the hash table is cleared inside eloc_sa
+    NNQS_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(DevStatus), s));
+    Arena a(scratch);
+    DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
+    NNQS_TRY(eloc_sa(H, lut, lut_logpsi, n_lut, row_begin, n_rows, n_alpha, n_beta, flags, eloc_out, a, st, s));
+    if (!check) return NNQS_OK;
+    NNQS_CUDA_TRY(cudaStreamSynchronize(s));
+    DevStatus hst{};
+    NNQS_CUDA_TRY(cudaMemcpy(&hst, scratch, sizeof hst, cudaMemcpyDeviceToHost));
+    if (hst.code != 0)
+        return set_error((nnqs_status)hst.code, std::string("device reported: ") + nnqs_status_string(hst.code) +
+                                                    " at row " + std::to_string(hst.index));
+    return NNQS_OK;
+}
