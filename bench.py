@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (default steps/2, min 2)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-samples", type=int, default=N_SAMPLES, help="N_s per step (smaller for profiling)")
     return ap.parse_args()
 
 
@@ -220,7 +223,7 @@ def run_ours(args):
 
     def make(p):
         # replicas: each rank samples its own batch (different seeds)
-        return VMC(ham, model, params0.clone(), prec=p, n_samples=N_SAMPLES, max_unique=1 << 15,
+        return VMC(ham, model, params0.clone(), prec=p, n_samples=args.n_samples, max_unique=1 << 15,
                    seed=1000 + rank)
 
     vmc = make(prec)
@@ -229,27 +232,34 @@ def run_ours(args):
     torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
-    B.profile_reset()
-    B.profile_enable(True)
-    l0 = B.launch_count()
-    n_u_total = 0
-    times = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local, not args.no_clocks) as clk:
-        for _ in range(args.steps):
+
+    def timed(n_steps, v):
+        ts, nu = [], 0
+        for _ in range(n_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            vmc.step()
+            v.step()
             e1.record(stream)
             e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            n_u_total += int(vmc.last_samples.shape[0])
+            ts.append(e0.elapsed_time(e1))
+            nu += int(v.last_samples.shape[0])
+        return ts, nu
+
+    l0 = B.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local, not args.no_clocks) as clk:
+        times, n_u_total = timed(args.steps, vmc)
     torch.cuda.synchronize()
     launches = B.launch_count() - l0
+    # the same number of steps again with every launch bracketed by CUDA
+    # events: per-kernel device times for the roofline
+    B.profile_reset()
+    B.profile_enable(True)
+    prof_times, _ = timed(args.steps, vmc)
     prof = B.profile()
     B.profile_enable(False)
     ms_step = float(np.mean(times))
@@ -288,13 +298,14 @@ def run_ours(args):
         "dtype": {"fp32": "f32 ansatz / f64 local energy", "mixed": "bf16+f32 ansatz / f64 local energy",
                   "fp64": "f64"}[args.prec],
         "data": "synthetic (random integrals seed 1 rank 16; random-init ansatz)",
-        "config": {"workload": "n40: 40 spin orbitals, 20 electrons, N_s=16384 -> N_u~16384, "
+        "config": {"workload": f"n40: 40 spin orbitals, 20 electrons, N_s={args.n_samples}, "
                                "d=64 L=4 H=8, 233001 Pauli strings / 46171 groups",
                    "n_terms": info["n_terms"], "n_groups": info["n_groups"],
                    "n_u_mean": n_u_total / (args.steps * world), "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "flushed between steps (256 MB memset)"},
         "gpu_launches": launches,
         "roofline": roof,
+        "profiled_ms_per_step": float(np.mean(prof_times)),
         "kernels_ms": {k: round(v["ms"], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
     }
     if not args.no_clocks:
@@ -331,7 +342,7 @@ def run_ours(args):
     st_host = torch.empty(4, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e2e_t = []
-    for _ in range(max(2, args.steps // 2)):
+    for _ in range(max(2, args.steps // 2) if args.e2e_steps < 0 else args.e2e_steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -343,13 +354,13 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_t.append(e0.elapsed_time(e1))
-    ms_e2e = float(np.mean(e2e_t))
+    ms_e2e = float(np.mean(e2e_t)) if e2e_t else float("nan")
     nbytes = vmc.params.numel() * 4
     line["e2e"] = {"value": int(vmc.last_samples.shape[0]) * info["n_terms"] * world / (ms_e2e / 1e3),
                    "unit": "pairs/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 32,
                    "ms_per_step": ms_e2e}
 
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             base = OracleStep(wl).run(512, 48)
             line["cpu_baseline"] = {"value": base["pairs_per_s"], "unit": "pairs/s", "cores": cores(),
