@@ -291,7 +291,14 @@ nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, const float
 /* ------------------------------------------------------------------ */
 /* Batch autoregressive sampling (Sec. 3.1 BAS, mask of Sec. 3.3).       */
 /* ------------------------------------------------------------------ */
-size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec);
+/* nnqs_sample flags: by default each step evaluates only the new token of
+ * every prefix against a key/value cache of the prefix tree (each node keeps
+ * its own rows; memory T * max_unique * n_layers * 3 d values);
+ * NNQS_SAMPLE_RECOMPUTE re-runs the whole prefix at every step instead (no
+ * cache).  Both give bit-identical draws. */
+enum { NNQS_SAMPLE_RECOMPUTE = 1 };
+
+size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec, int flags);
 
 /* Draws n_samples samples from |psi|^2 as unique bitstrings with counts:
  * at each of the T steps every unique prefix with weight w splits w over
@@ -303,9 +310,9 @@ size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int p
  * max_unique prefixes.  Synchronises the stream once per step (the width
  * of the next step is data-dependent). */
 nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uint64_t n_samples,
-                        uint64_t seed, int prec, int64_t max_unique, uint64_t *samples_out,
-                        uint64_t *weights_out, int64_t *n_unique_out, void *workspace,
-                        size_t workspace_bytes, nnqs_stream stream);
+                        uint64_t seed, int prec, int flags, int64_t max_unique,
+                        uint64_t *samples_out, uint64_t *weights_out, int64_t *n_unique_out,
+                        void *workspace, size_t workspace_bytes, nnqs_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* Optimiser step.                                                       */

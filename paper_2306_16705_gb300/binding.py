@@ -94,10 +94,12 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                         ctypes.c_void_p]),
-    "nnqs_sample_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]),
+    "nnqs_sample_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                                     ctypes.c_int]),
     "nnqs_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
-                                   ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.c_void_p]),
     "nnqs_profile_enable": (None, [ctypes.c_int]),
     "nnqs_profile_reset": (None, []),
     "nnqs_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p,
@@ -365,19 +367,23 @@ def energy_grad(ham: Hamiltonian, model: Model, params, samples, weights, prec=F
     return stats, el, grad
 
 
+SAMPLE_RECOMPUTE = 1
+
+
 def sample(model: Model, params, n_samples: int, seed: int, max_unique: int, prec=FP64,
-           check=True, ws=None):
+           check=True, ws=None, flags=0):
     """nnqs_sample: (samples [n_u, W] uint64 as int64 tensor, weights [n_u])."""
     W = model.n_words
     dev = params.device
     s = torch.empty((max_unique, W), dtype=torch.int64, device=dev)
     w = torch.empty(max_unique, dtype=torch.int64, device=dev)
     nu = ctypes.c_int64(0)
-    nb = lib().nnqs_sample_workspace_size(model.handle, max_unique, prec)
+    nb = lib().nnqs_sample_workspace_size(model.handle, max_unique, prec, flags)
     if ws is None or ws.numel() < nb:
         ws = workspace(nb, dev)
-    _check(lib().nnqs_sample(model.handle, _ptr(params), int(n_samples), int(seed), prec, max_unique,
-                             _ptr(s), _ptr(w), ctypes.byref(nu), _ptr(ws), ws.numel(), _stream()))
+    _check(lib().nnqs_sample(model.handle, _ptr(params), int(n_samples), int(seed), prec, flags,
+                             max_unique, _ptr(s), _ptr(w), ctypes.byref(nu), _ptr(ws), ws.numel(),
+                             _stream()))
     if check:
         workspace_status(ws)
     return s[:nu.value], w[:nu.value]

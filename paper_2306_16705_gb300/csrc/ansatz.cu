@@ -627,22 +627,82 @@ __global__ void k_head(const uint64_t *__restrict__ x, int W, const R *__restric
     }
 }
 
+// ---- key/value-cached decoding for the sampler --------------------------
+// Every node of the prefix tree owns one row of q|k|v per layer in a pool
+// [node][L][3d]; a node at depth t attends over the rows of its ancestors
+// at depths 0..t (found through parent pointers) and itself, in depth order,
+// which is the order the full forward visits keys.
+template <class R>
+__global__ void k_embed_decode(const uint64_t *__restrict__ x, int W, int64_t n, int t, int T, int d,
+                               const R *__restrict__ tok_emb, const R *__restrict__ pos_emb, R *__restrict__ h) {
+    const int64_t total = n * d;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % d);
+        const int64_t i = idx / d;
+        const int inp = t == 0 ? 4 : token_at(x + i * W, T, t - 1);
+        h[idx] = tok_emb[inp * d + c] + pos_emb[t * d + c];
+    }
+}
+
+constexpr int kMaxDepth = 64;
+
+template <class R, int DH>
+__global__ void k_attn_decode(const R *__restrict__ pool, const int64_t *__restrict__ parent, int64_t g0, int64_t n,
+                              int t, int L, int l, int H, int d, R *__restrict__ o) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * H) return;
+    const int hh = (int)(idx % H);
+    const int64_t i = idx / H;
+    int64_t anc[kMaxDepth];
+    anc[t] = g0 + i;
+    for (int lev = t - 1; lev >= 0; --lev) anc[lev] = parent[anc[lev + 1]];
+    const int64_t row = 3 * (int64_t)d;
+    const R scale = R(1) / sqrt(R(DH));
+    R qv[DH], acc[DH];
+    const R *qp = pool + (anc[t] * L + l) * row + hh * DH;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+        qv[c] = qp[c] * scale;
+        acc[c] = 0;
+    }
+    R m = neg_inf<R>(), lsum = 0;
+    for (int j = 0; j <= t; ++j) {
+        const R *base = pool + (anc[j] * L + l) * row;
+        const R *kj = base + d + hh * DH;
+        const R *vj = base + 2 * d + hh * DH;
+        R sc = 0;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
+        const R mn = sc > m ? sc : m;
+        const R corr = exp_<R>(m - mn);
+        const R p = exp_<R>(sc - mn);
+        lsum = lsum * corr + p;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) acc[c] = acc[c] * corr + p * vj[c];
+        m = mn;
+    }
+    const R inv = R(1) / lsum;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) o[i * d + hh * DH + c] = acc[c] * inv;
+}
+
 // pi~(v | prefix) at position S-1 for each prefix (sampling): cond[i][4], FP64
+// (rows of hf have stride S; the row used is i*S + S-1; t = the position)
 template <class R>
 __global__ void k_cond_last(const uint64_t *__restrict__ x, int W, const R *__restrict__ hf, const R *__restrict__ hw,
-                            const R *__restrict__ hb, int64_t n, int S, int T, int d, int n_alpha, int n_beta,
+                            const R *__restrict__ hb, int64_t n, int S, int t, int T, int d, int n_alpha, int n_beta,
                             double *__restrict__ cond, DevStatus *st) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t *xi = x + i * W;
-    const int t = S - 1;
     int ca = 0, cb = 0;
     for (int p2 = T - t; p2 < T; ++p2) {
         ca += bit_of(xi, 2 * p2);
         cb += bit_of(xi, 2 * p2 + 1);
     }
     const int rem = T - 1 - t;
-    const R *hr = hf + (i * S + t) * d;
+    const R *hr = hf + (i * S + S - 1) * d;
     double z[4], zmax = -INFINITY;
     bool ok[4], any = false;
 #pragma unroll
@@ -933,8 +993,7 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     const R *hlast = A.keep ? A.hbuf + (int64_t)L * rows * d : A.hbuf;
     NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, V.lnf_g, V.lnf_b, A.hf, A.meanf, A.rstdf, rows, d));
     if (cond) {
-        NNQS_LAUNCH("k_cond_last", s, k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, T, Tm, d, M->cfg.n_alpha,
-                                                        M->cfg.n_beta, cond, st));
+        NNQS_LAUNCH("k_cond_last", s, k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, T, T - 1, Tm, d, M->cfg.n_alpha, M->cfg.n_beta, cond, st));
         return NNQS_OK;
     }
     NNQS_LAUNCH("k_head", s, k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
@@ -1128,9 +1187,10 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
 }
 
 template <class R>
-size_t cond_workspace_impl(const nnqs_model *M, int64_t max_prefixes, bool tensor) {
+size_t cond_workspace_impl(const nnqs_model *M, int64_t max_prefixes, bool tensor, int64_t kv_nodes) {
     Arena a(nullptr);
     a.take<R>(M->lay.total);
+    a.take<R>(size_t(kv_nodes) * M->L * 3 * M->d);
     if (tensor) tc_weights_take(M, a);
     const int64_t C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(R), false);
     Acts<R> A;
@@ -1140,6 +1200,70 @@ size_t cond_workspace_impl(const nnqs_model *M, int64_t max_prefixes, bool tenso
 
 }  // namespace
 
+template <int DH_, class R>
+nnqs_status launch_attn_decode(cudaStream_t s, const R *pool, const int64_t *parent, int64_t g0, int64_t n, int t,
+                               int L, int l, int H, int d, R *o) {
+    NNQS_LAUNCH("k_attn_decode", s,
+                k_attn_decode<R, DH_><<<grid_for(n * H, 128), 128, 0, s>>>(pool, parent, g0, n, t, L, l, H, d, o));
+    return NNQS_OK;
+}
+
+template <class R>
+nnqs_status attn_decode(cudaStream_t s, int dh, const R *pool, const int64_t *parent, int64_t g0, int64_t n, int t,
+                        int L, int l, int H, int d, R *o) {
+    switch (dh) {
+        case 1: return launch_attn_decode<1>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 2: return launch_attn_decode<2>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 4: return launch_attn_decode<4>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 8: return launch_attn_decode<8>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 16: return launch_attn_decode<16>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 32: return launch_attn_decode<32>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 64: return launch_attn_decode<64>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        default: return set_error(NNQS_E_UNSUPPORTED, "head dimension must be a power of two <= 64");
+    }
+}
+
+// one decoding step for C prefixes at depth t (global node ids g0 ...)
+template <class R>
+nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, int t, int64_t g0,
+                         R *pool, const int64_t *parent, Acts<R> &A, double *cond, DevStatus *st,
+                         const TcWeights *tcw, cudaStream_t s) {
+    const int T = M->T, d = M->d, L = M->L, F = M->F, H = M->H, W = M->W;
+    const int64_t rows = C;
+    R *h = A.hbuf;
+    NNQS_LAUNCH("k_embed", s, k_embed_decode<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, t, T, d, V.tok, V.pos, h));
+    for (int l = 0; l < L; ++l) {
+        const auto &Lw = V.layer[l];
+        R *qkv = pool + (g0 * L + l) * 3 * (int64_t)d;
+        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(h, Lw.ln1g, Lw.ln1b, A.a, nullptr, nullptr, rows, d));
+        if (tcw) {
+            NNQS_TRY(tc_linear_fwd_ld<R>(s, *tcw, tc_slot(l, 0), EPI_STORE, A.a, rows, d, Lw.bqkv, qkv, (int64_t)L * 3 * d,
+                                         nullptr, nullptr));
+        } else {
+            NNQS_TRY(gemm<R>(s, EPI_STORE, A.a, d, 1, Lw.wqkv, d, 1, qkv, (int64_t)L * 3 * d, nullptr, Lw.bqkv, nullptr,
+                             rows, 3 * d, d, A.scr));
+        }
+        NNQS_TRY(attn_decode<R>(s, M->dh, pool, parent, g0, C, t, L, l, H, d, A.o));
+        if (tcw) {
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 1), EPI_RESID, A.o, rows, d, Lw.bo, h, nullptr, h));
+        } else {
+            NNQS_TRY(linear_fwd<R>(s, EPI_RESID, A.o, rows, d, Lw.wo, d, Lw.bo, h, nullptr, h, A.scr));
+        }
+        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(h, Lw.ln2g, Lw.ln2b, A.a2, nullptr, nullptr, rows, d));
+        if (tcw) {
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 2), EPI_GELU, A.a2, rows, d, Lw.b1, A.u, A.gu, nullptr));
+            NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 3), EPI_RESID, A.gu, rows, F, Lw.b2, h, nullptr, h));
+        } else {
+            NNQS_TRY(linear_fwd<R>(s, EPI_GELU, A.a2, rows, d, Lw.w1, F, Lw.b1, A.u, A.gu, nullptr, A.scr));
+            NNQS_TRY(linear_fwd<R>(s, EPI_RESID, A.gu, rows, F, Lw.w2, d, Lw.b2, h, nullptr, h, A.scr));
+        }
+    }
+    NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(h, V.lnf_g, V.lnf_b, A.hf, nullptr, nullptr, rows, d));
+    NNQS_LAUNCH("k_cond_last", s, k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, 1, t, T, d,
+                                                                             M->cfg.n_alpha, M->cfg.n_beta, cond, st));
+    return NNQS_OK;
+}
+
 struct CondCtx {
     int prec = NNQS_FP64;
     bool tensor = false;
@@ -1148,28 +1272,33 @@ struct CondCtx {
     TcWeights tcw;
     Acts<float> Af;
     Acts<double> Ad;
+    void *pool = nullptr;  // key/value cache [nodes][L][3d]
+    int64_t pool_nodes = 0;
 };
 
-size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec) {
-    if (prec == NNQS_FP64) return cond_workspace_impl<double>(M, max_prefixes, false);
-    return cond_workspace_impl<float>(M, max_prefixes, prec == NNQS_MIXED);
+size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec, int64_t kv_nodes) {
+    if (prec == NNQS_FP64) return cond_workspace_impl<double>(M, max_prefixes, false, kv_nodes);
+    return cond_workspace_impl<float>(M, max_prefixes, prec == NNQS_MIXED, kv_nodes);
 }
 
-nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, Arena &ws,
-                        CondCtx **out, cudaStream_t s) {
+nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, int64_t kv_nodes,
+                        Arena &ws, CondCtx **out, cudaStream_t s) {
     CondCtx *c = new (std::nothrow) CondCtx();
     if (!c) return set_error(NNQS_E_NOMEM, "host allocation failed");
     *out = c;
     c->prec = prec;
     c->tensor = prec == NNQS_MIXED;
+    c->pool_nodes = kv_nodes;
     if (prec == NNQS_FP64) {
         double *pr = ws.take<double>(M->lay.total);
+        c->pool = ws.take<double>(size_t(kv_nodes) * M->L * 3 * M->d);
         c->params = pr;
         c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(double), false);
         take_acts<double>(M, c->C, false, ws, c->Ad);
         NNQS_LAUNCH("k_convert_params", s, k_convert_params<double><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     } else {
         float *pr = ws.take<float>(M->lay.total);
+        c->pool = ws.take<float>(size_t(kv_nodes) * M->L * 3 * M->d);
         c->params = pr;
         if (c->tensor) tc_weights_take(M, ws, &c->tcw);
         c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(float), false);
@@ -1182,6 +1311,25 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
 }
 
 void cond_destroy(CondCtx *c) { delete c; }
+
+nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int t,
+                             int64_t g0, const int64_t *parent, double *cond, DevStatus *st, cudaStream_t s) {
+    if (t >= kMaxDepth) return set_error(NNQS_E_UNSUPPORTED, "more than 64 tokens");
+    if (g0 + n > ctx->pool_nodes) return set_error(NNQS_E_TABLE_FULL, "key/value cache full");
+    for (int64_t c0 = 0; c0 < n; c0 += ctx->C) {
+        const int64_t cn = std::min(ctx->C, n - c0);
+        if (ctx->prec == NNQS_FP64) {
+            const Views<double> V = make_views<double>(M, static_cast<double *>(ctx->params));
+            NNQS_TRY(decode_chunk<double>(M, V, prefixes + c0 * M->W, cn, t, g0 + c0, static_cast<double *>(ctx->pool),
+                                          parent, ctx->Ad, cond + c0 * 4, st, nullptr, s));
+        } else {
+            const Views<float> V = make_views<float>(M, static_cast<float *>(ctx->params));
+            NNQS_TRY(decode_chunk<float>(M, V, prefixes + c0 * M->W, cn, t, g0 + c0, static_cast<float *>(ctx->pool),
+                                         parent, ctx->Af, cond + c0 * 4, st, ctx->tensor ? &ctx->tcw : nullptr, s));
+        }
+    }
+    return NNQS_OK;
+}
 
 nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int S, double *cond,
                       DevStatus *st, cudaStream_t s) {

@@ -43,11 +43,17 @@ nnqs_status logpsi_backward(const nnqs_model *M, const float *params, const uint
 
 // conditionals pi~(. | prefix) for the sampler (ansatz.cu)
 struct CondCtx;
-size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec);
-nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, Arena &ws,
-                        CondCtx **out, cudaStream_t s);
+// kv_nodes: capacity of the key/value cache in tree nodes (0 = no cache)
+size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec, int64_t kv_nodes);
+nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, int64_t kv_nodes,
+                        Arena &ws, CondCtx **out, cudaStream_t s);
+// full recomputation over the S = t+1 positions of every prefix
 nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int S, double *cond,
                       DevStatus *st, cudaStream_t s);
+// cached: only position t; prefixes are tree nodes g0..g0+n-1, parent[g] the
+// node one level up
+nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int t,
+                             int64_t g0, const int64_t *parent, double *cond, DevStatus *st, cudaStream_t s);
 void cond_destroy(CondCtx *c);
 
 // eloc_exact.cu

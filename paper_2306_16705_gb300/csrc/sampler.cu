@@ -4,7 +4,11 @@
 // The tree of unique prefixes is kept level by level on the device: a level
 // is a list of prefixes (packed bitstrings with the first t tokens set) and
 // their sample counts.  A step runs the ansatz on every prefix to get
-// pi~(. | prefix), splits each count over the 4 children with a multinomial
+// pi~(. | prefix) -- by default only at the new position, attending over
+// the cached keys and values of the prefix's ancestors (each tree node keeps
+// its own rows; children point at their parent), so the cost of a step is
+// one token per prefix rather than t -- splits each count over the 4 children
+// with a multinomial
 // draw (sequential binomials), drops zero counts and writes the next level
 // in (parent, child) order.  Because children are emitted in token order and
 // the first token holds the most significant qubits, the final level comes
@@ -236,7 +240,8 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
 // children of prefix i in token order at slots off[i] ...
 __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
                        const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
-                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, DevStatus *st) {
+                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, int64_t *__restrict__ parent,
+                       int64_t g_cur, int64_t g_next, DevStatus *st) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t j = off[i];
@@ -252,6 +257,7 @@ __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__rest
         if (v & 1) npref[j * W + ((2 * p) >> 6)] |= 1ull << ((2 * p) & 63);
         if (v & 2) npref[j * W + ((2 * p + 1) >> 6)] |= 1ull << ((2 * p + 1) & 63);
         nw[j] = c;
+        if (parent) parent[g_next + j] = g_cur + i;  // tree link for the key/value cache
         ++j;
     }
 }
@@ -260,11 +266,12 @@ struct SLayout {
     uint64_t *pref[2], *w[2], *counts;
     double *cond;
     int32_t *nchild;
-    int64_t *off, *bsum, *total;
+    int64_t *off, *bsum, *total, *parent;
     char *region;
+    int64_t kv_nodes;
 };
 
-SLayout slayout(const nnqs_model *M, int64_t cap, int prec, Arena &a) {
+SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &a) {
     SLayout L{};
     const int W = M->W;
     for (int k = 0; k < 2; ++k) {
@@ -277,7 +284,9 @@ SLayout slayout(const nnqs_model *M, int64_t cap, int prec, Arena &a) {
     L.off = a.take<int64_t>(size_t(cap));
     L.bsum = a.take<int64_t>(size_t((cap + kScan - 1) / kScan + 1));
     L.total = a.take<int64_t>(1);
-    L.region = a.take<char>(cond_workspace(M, cap, prec));
+    L.kv_nodes = cached ? int64_t(M->T) * cap + 1 : 0;
+    L.parent = cached ? a.take<int64_t>(size_t(L.kv_nodes)) : nullptr;
+    L.region = a.take<char>(cond_workspace(M, cap, prec, L.kv_nodes));
     return L;
 }
 
@@ -286,34 +295,37 @@ SLayout slayout(const nnqs_model *M, int64_t cap, int prec, Arena &a) {
 
 using namespace nnqs;
 
-extern "C" size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec) {
+extern "C" size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec, int flags) {
     if (!M || max_unique < 1) return 0;
     Arena a(nullptr);
     a.take<char>(kStatusBytes);
-    slayout(M, max_unique, prec, a);
+    slayout(M, max_unique, prec, !(flags & NNQS_SAMPLE_RECOMPUTE), a);
     return a.used + 1024;
 }
 
 extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uint64_t n_samples, uint64_t seed,
-                                   int prec, int64_t max_unique, uint64_t *samples_out, uint64_t *weights_out,
-                                   int64_t *n_unique_out, void *workspace, size_t workspace_bytes, nnqs_stream stream) {
+                                   int prec, int flags, int64_t max_unique, uint64_t *samples_out,
+                                   uint64_t *weights_out, int64_t *n_unique_out, void *workspace,
+                                   size_t workspace_bytes, nnqs_stream stream) {
     if (!M || !params || !samples_out || !weights_out || !n_unique_out || max_unique < 1)
         return set_error(NNQS_E_INVAL, "null argument or max_unique < 1");
     if (prec != NNQS_FP64 && prec != NNQS_FP32 && prec != NNQS_MIXED) return set_error(NNQS_E_INVAL, "bad precision");
+    if (flags & ~NNQS_SAMPLE_RECOMPUTE) return set_error(NNQS_E_INVAL, "unknown sampler flags");
     if (n_samples > (uint64_t(1) << 53)) return set_error(NNQS_E_INVAL, "n_samples above 2^53");
     *n_unique_out = 0;
-    const size_t need = nnqs_sample_workspace_size(M, max_unique, prec);
+    const bool cached = !(flags & NNQS_SAMPLE_RECOMPUTE);
+    const size_t need = nnqs_sample_workspace_size(M, max_unique, prec, flags);
     if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256 || workspace_bytes < need)
         return set_error(NNQS_E_WORKSPACE, "workspace null, misaligned or smaller than " + std::to_string(need));
     cudaStream_t s = (cudaStream_t)stream;
     NNQS_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(DevStatus), s));
     Arena a(workspace);
     DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
-    const SLayout L = slayout(M, max_unique, prec, a);
+    const SLayout L = slayout(M, max_unique, prec, cached, a);
     if (n_samples == 0) return NNQS_OK;
     Arena sub(L.region);
     CondCtx *ctx = nullptr;
-    nnqs_status rc = cond_create(M, params, prec, max_unique, sub, &ctx, s);
+    nnqs_status rc = cond_create(M, params, prec, max_unique, L.kv_nodes, sub, &ctx, s);
     if (rc != NNQS_OK) {
         cond_destroy(ctx);
         return rc;
@@ -324,8 +336,12 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     NNQS_CUDA_TRY(cudaMemcpyAsync(L.w[0], &n_samples, 8, cudaMemcpyHostToDevice, s));
     int64_t n = 1;
     int cur = 0;
+    int64_t g_cur = 0;  // tree-node id of the first prefix of the current level
     auto step = [&](int t) -> nnqs_status {
-        NNQS_TRY(cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s));
+        if (cached)
+            NNQS_TRY(cond_step_cached(M, ctx, L.pref[cur], n, t, g_cur, L.parent, L.cond, st, s));
+        else
+            NNQS_TRY(cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s));
         NNQS_LAUNCH("k_split", s, k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts,
                                                                            L.nchild, st));
         const int64_t nb = (n + kScan - 1) / kScan;
@@ -339,8 +355,10 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
             return set_error(NNQS_E_TABLE_FULL, "step " + std::to_string(t) + " holds " + std::to_string(next) +
                                                     " prefixes, above max_unique " + std::to_string(max_unique));
         NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t,
-                                                                         max_unique, L.pref[cur ^ 1], L.w[cur ^ 1], st));
+                                                                         max_unique, L.pref[cur ^ 1], L.w[cur ^ 1],
+                                                                         L.parent, g_cur, g_cur + n, st));
         cur ^= 1;
+        g_cur += n;
         n = next;
         return NNQS_OK;
     };

@@ -24,4 +24,9 @@ template <class R>
 nnqs_status tc_linear_fwd(cudaStream_t s, const TcWeights &w, int slot, int epi, const R *X, int64_t rows,
                           int64_t in, const R *bias, R *Y, R *Y2, const R *resid);
 
+// as tc_linear_fwd with an explicit output row stride ldy
+template <class R>
+nnqs_status tc_linear_fwd_ld(cudaStream_t s, const TcWeights &w, int slot, int epi, const R *X, int64_t rows,
+                             int64_t in, const R *bias, R *Y, int64_t ldy, R *Y2, const R *resid);
+
 }  // namespace nnqs

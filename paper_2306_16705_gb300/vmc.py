@@ -9,8 +9,6 @@ fixed) for its backward.
 """
 from __future__ import annotations
 
-import dataclasses
-
 import torch
 
 from . import binding as B
@@ -33,15 +31,6 @@ class EnergyFunction(torch.autograd.Function):
     def backward(ctx, grad_out):
         (grad,) = ctx.saved_tensors
         return grad_out * grad, None, None, None, None, None
-
-
-@dataclasses.dataclass
-class StepResult:
-    energy: float
-    energy_imag: float
-    variance: float
-    n_samples: float
-    n_unique: int
 
 
 class VMC:
@@ -67,7 +56,7 @@ class VMC:
 
     def sample(self, seed=None):
         seed = self.seed * 1_000_003 + self.t if seed is None else seed
-        nb = B.lib().nnqs_sample_workspace_size(self.model.handle, self.max_unique, self.prec)
+        nb = B.lib().nnqs_sample_workspace_size(self.model.handle, self.max_unique, self.prec, 0)
         if self._ws_sample is None or self._ws_sample.numel() < nb:
             self._ws_sample = B.workspace(nb, self.params.device)
         return B.sample(self.model, self.params, self.n_samples, seed, self.max_unique, self.prec,

@@ -206,3 +206,16 @@ def test_adam_matches_oracle():
         B.adam_step(pt, torch.from_numpy(g).cuda(), m, v, step, lr=1e-3)
         th, mm, vv = OV.adam_step(th, g.astype(np.float64), mm, vv, step)
     assert np.abs(pt.cpu().numpy() - th).max() < 1e-6
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("wl_name,ns", [("n12", 100_000), ("n40", 4096)])
+def test_sampler_kv_cache_equals_recompute(wl_name, ns, prec):
+    """The key/value-cached sampler (one new token per prefix per step) draws
+    exactly the samples of the full recomputation with the same seed."""
+    wl = I.WORKLOADS[wl_name]
+    m, params, flat = model_for(wl, seed=12, std=0.3)
+    xa, wa = B.sample(m, flat, ns, seed=5, max_unique=8192, prec=prec)
+    xb, wb = B.sample(m, flat, ns, seed=5, max_unique=8192, prec=prec, flags=B.SAMPLE_RECOMPUTE)
+    assert torch.equal(xa, xb) and torch.equal(wa, wb)
+    assert int(wa.sum().item()) == ns
