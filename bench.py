@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--prec", default="mixed", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (default steps/2, min 2)")
@@ -227,15 +227,28 @@ def run_ours(args):
                    seed=1000 + rank)
 
     vmc = make(prec)
+    p_init = vmc.params.clone()
     for _ in range(args.warmup):
         vmc.step()
+    vmc.params.copy_(p_init)
+    vmc.m.zero_()
+    vmc.v.zero_()
+    vmc.t = 0
     torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
     def timed(n_steps, v):
+        # every timed step starts from the same random-init parameters and
+        # Adam state (restored outside the timed region; the Adam update
+        # itself runs inside), so each step samples the same distribution
+        p0, m0, v0, t0 = v.params.clone(), v.m.clone(), v.v.clone(), v.t
         ts, nu = [], 0
         for _ in range(n_steps):
+            v.params.copy_(p0)
+            v.m.copy_(m0)
+            v.v.copy_(v0)
+            v.t = t0
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -277,7 +290,21 @@ def run_ours(args):
     fam = max(prof.items(), key=lambda kv: kv[1]["ms"])
     name, f = fam
     avg_ms = f["ms"] / max(1, f["launches"])
-    if name == "k_gemm":
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if name == "k_tc_gemm":
+        pk = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        achieved = f["flops"] / (f["ms"] / 1e3) / 1e12
+        roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback 1.7 PFLOP/s",
+                "achieved_gbs": f["bytes"] / (f["ms"] / 1e3) / 1e9,
+                "hbm_frac": f["bytes"] / (f["ms"] / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+                "launches": f["launches"], "avg_launch_ms": avg_ms}
+    elif name == "k_gemm":
         achieved = f["flops"] / (f["ms"] / 1e3) / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
@@ -294,7 +321,7 @@ def run_ours(args):
     line = {
         "metric": "local-energy (sample x Pauli-term) evals/sec, whole VMC step",
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms_step, "step_ms": [round(t, 3) for t in times], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32 ansatz / f64 local energy", "mixed": "bf16+f32 ansatz / f64 local energy",
                   "fp64": "f64"}[args.prec],
         "data": "synthetic (random integrals seed 1 rank 16; random-init ansatz)",
@@ -316,25 +343,25 @@ def run_ours(args):
         v64 = make(B.FP64)
         v64.step()
         torch.cuda.synchronize()
-        t64, nu64 = [], 0
-        for _ in range(args.fp64_steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            v64.step()
-            e1.record(stream)
-            e1.synchronize()
-            t64.append(e0.elapsed_time(e1))
-            nu64 += int(v64.last_samples.shape[0])
+        t64, nu64 = timed(args.fp64_steps, v64)
         ms64 = float(np.mean(t64))
         # energy of the same samples and parameters through both precisions
         x, w = vmc.last_samples, vmc.last_weights
         s_fast, _, _ = B.energy_grad(ham, model, vmc.params, x, w, prec)
+        s_32, _, _ = B.energy_grad(ham, model, vmc.params, x, w, B.FP32)
         s_64, _, _ = B.energy_grad(ham, model, vmc.params, x, w, B.FP64)
         line["fp64_plain"] = {"ms_per_step": ms64, "value": nu64 * info["n_terms"] / (ms64 * args.fp64_steps / 1e3),
                               "unit": "pairs/s", "speedup_of_fast_path": ms64 / ms_step,
-                              "energy_diff_ha": abs(float(s_fast[0]) - float(s_64[0]))}
+                              "energy_ha": float(s_64[0]),
+                              "energy_diff_ha": abs(float(s_fast[0]) - float(s_64[0])),
+                              "energy_diff_fp32_ha": abs(float(s_32[0]) - float(s_64[0]))}
+        if prec != B.FP32:
+            v32 = make(B.FP32)
+            v32.step()
+            t32, nu32 = timed(max(2, args.fp64_steps), v32)
+            ms32 = float(np.mean(t32))
+            line["fp32_path"] = {"ms_per_step": ms32, "value": nu32 * info["n_terms"] / (ms32 * len(t32) / 1e3),
+                                 "unit": "pairs/s"}
 
     # end to end through the public API with host buffers: parameters in
     # from pinned memory, energy statistics and parameters out, every step
@@ -342,7 +369,13 @@ def run_ours(args):
     st_host = torch.empty(4, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e2e_t = []
+    p_host.copy_(p_init.cpu())
+    m0, v0 = torch.zeros_like(vmc.m), torch.zeros_like(vmc.v)
     for _ in range(max(2, args.steps // 2) if args.e2e_steps < 0 else args.e2e_steps):
+        vmc.m.copy_(m0)
+        vmc.v.copy_(v0)
+        vmc.t = 0
+        p_host.copy_(p_init.cpu())
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)

@@ -1149,6 +1149,7 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
     R *pr = ws.take<R>(M->lay.total);
     TcWeights tcw{};
     if (tensor) tc_weights_take(M, ws, &tcw);
+    tcw.st = st;
     const int64_t C = chunk_for(M, n, sizeof(R), false);
     Acts<R> A;
     take_acts<R>(M, C, false, ws, A);
@@ -1165,9 +1166,12 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
 
 template <class R>
 nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, const double *seed,
-                          double *g64, float *g32, Arena &ws, DevStatus *st, cudaStream_t s) {
+                          double *g64, float *g32, Arena &ws, DevStatus *st, bool tensor, cudaStream_t s) {
     R *pr = ws.take<R>(M->lay.total);
     R *gacc = ws.take<R>(M->lay.total);
+    TcWeights tcw{};
+    if (tensor) tc_weights_take(M, ws, &tcw);
+    tcw.st = st;
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
     Acts<R> A;
     take_acts<R>(M, C, true, ws, A);
@@ -1175,11 +1179,13 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
     take_grads<R>(M, C, ws, G);
     NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
+    if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
     const Views<R> V = make_views<R>(M, pr);
     for (int64_t c0 = 0; c0 < n; c0 += C) {
         const int64_t cn = std::min(C, n - c0);
         const uint64_t *xc = x + c0 * M->W;
-        NNQS_TRY(forward_chunk<R>(M, V, xc, cn, A, G.lp, st, c0, nullptr, s));
+        // recompute the forward (tensor cores for NNQS_MIXED), keeping activations
+        NNQS_TRY(forward_chunk<R>(M, V, xc, cn, A, G.lp, st, c0, tensor ? &tcw : nullptr, s));
         NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc, s));
     }
     NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
@@ -1316,6 +1322,7 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
                              int64_t g0, const int64_t *parent, double *cond, DevStatus *st, cudaStream_t s) {
     if (t >= kMaxDepth) return set_error(NNQS_E_UNSUPPORTED, "more than 64 tokens");
     if (g0 + n > ctx->pool_nodes) return set_error(NNQS_E_TABLE_FULL, "key/value cache full");
+    ctx->tcw.st = st;
     for (int64_t c0 = 0; c0 < n; c0 += ctx->C) {
         const int64_t cn = std::min(ctx->C, n - c0);
         if (ctx->prec == NNQS_FP64) {
@@ -1333,6 +1340,7 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
 
 nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int S, double *cond,
                       DevStatus *st, cudaStream_t s) {
+    ctx->tcw.st = st;
     for (int64_t c0 = 0; c0 < n; c0 += ctx->C) {
         const int64_t cn = std::min(ctx->C, n - c0);
         if (ctx->prec == NNQS_FP64) {
@@ -1350,7 +1358,7 @@ nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixe
 
 size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward) {
     if (prec == NNQS_FP64) return workspace_impl<double>(M, n, backward, false);
-    return workspace_impl<float>(M, n, backward, prec == NNQS_MIXED && !backward);
+    return workspace_impl<float>(M, n, backward, prec == NNQS_MIXED);
 }
 
 nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
@@ -1361,8 +1369,8 @@ nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint6
 
 nnqs_status logpsi_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
                             const double *seed, double *g64, float *g32, Arena &ws, DevStatus *st, cudaStream_t s) {
-    if (prec == NNQS_FP64) return backward_impl<double>(M, params, x, n, seed, g64, g32, ws, st, s);
-    return backward_impl<float>(M, params, x, n, seed, g64, g32, ws, st, s);
+    if (prec == NNQS_FP64) return backward_impl<double>(M, params, x, n, seed, g64, g32, ws, st, false, s);
+    return backward_impl<float>(M, params, x, n, seed, g64, g32, ws, st, prec == NNQS_MIXED, s);
 }
 
 }  // namespace nnqs

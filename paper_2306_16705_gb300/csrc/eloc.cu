@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kSweepThreads)
                   const double *__restrict__ tcoef, int64_t row_begin, int64_t n_rows,
                   double2 *__restrict__ partial) {
     __shared__ uint64_t s_y[kPairTile * W];
+    const int lane = threadIdx.x & 31;
     const int64_t rbase = blockIdx.x * (int64_t)(kSweepThreads * kPairRows);
     Bits<W> x[kPairRows];
     double2 lx[kPairRows];
@@ -166,6 +167,8 @@ __global__ void __launch_bounds__(kSweepThreads)
             Bits<W> y;
 #pragma unroll
             for (int w = 0; w < W; ++w) y.w[w] = s_y[k * W + w];
+            int32_t g[kPairRows];
+            bool any = false;
 #pragma unroll
             for (int q = 0; q < kPairRows; ++q) {
                 int d = 0;
@@ -176,13 +179,41 @@ __global__ void __launch_bounds__(kSweepThreads)
                     d += __popcll(m.w[w]);
                 }
                 // d == 0 is the diagonal, handled by k_diag
-                if (d == 0 || d > max_weight || !act[q]) continue;
-                const int32_t g = gtab.find(m);
-                if (g < 0) continue;
-                const double coef = group_coef<W>(x[q], __ldg(goff + g), __ldg(goff + g + 1), tyz, tcoef);
-                const double2 rr = ratio(lx[q], lut_lp[ct + k]);
-                er[q] += coef * rr.x;
-                ei[q] += coef * rr.y;
+                g[q] = (d == 0 || d > max_weight || !act[q]) ? -1 : gtab.find(m);
+                any |= g[q] >= 0;
+            }
+            unsigned hits = __ballot_sync(0xffffffffu, any);
+            if (hits == 0) continue;
+            // each lane's ratios psi(y)/psi(x) in parallel, then the whole warp
+            // sums the popcount signs of one hit's group at a time
+            double2 rr[kPairRows];
+#pragma unroll
+            for (int q = 0; q < kPairRows; ++q)
+                rr[q] = g[q] >= 0 ? ratio(lx[q], lut_lp[ct + k]) : make_double2(0.0, 0.0);
+            while (hits) {
+                const int leader = __ffs(hits) - 1;
+                hits &= hits - 1;
+#pragma unroll
+                for (int q = 0; q < kPairRows; ++q) {
+                    const int32_t gq = __shfl_sync(0xffffffffu, g[q], leader);
+                    if (gq < 0) continue;
+                    Bits<W> xq;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) xq.w[w] = __shfl_sync(0xffffffffu, x[q].w[w], leader);
+                    const uint32_t t0 = __ldg(goff + gq), t1 = __ldg(goff + gq + 1);
+                    double c = 0.0;
+                    for (uint32_t t = t0 + lane; t < t1; t += 32) {
+                        const Bits<W> yz = load_bits<W>(tyz, t);
+                        const double v = __ldg(tcoef + t);
+                        c += (popc_and<W>(xq, yz) & 1) ? -v : v;
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+                    if (lane == leader) {
+                        er[q] += c * rr[q].x;
+                        ei[q] += c * rr[q].y;
+                    }
+                }
             }
         }
     }

@@ -1,28 +1,146 @@
-// Placeholder until the tcgen05 kernel lands: NNQS_MIXED reports
-// NNQS_E_UNSUPPORTED.
+// Host side of the tcgen05 linear layers used by NNQS_MIXED: BF16 copies of
+// the weight matrices (K padded to 64 with zeros) and the launch of
+// tc::k_tc_gemm.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dev_common.cuh"
+#include "tc_gemm.cuh"
 #include "tc_gemm.h"
 
 namespace nnqs {
-void tc_weights_take(const nnqs_model *, Arena &, TcWeights *) {}
-nnqs_status tc_weights_prepare(const nnqs_model *, const float *, TcWeights &, cudaStream_t) {
-    return set_error(NNQS_E_UNSUPPORTED, "tensor-core path not built yet");
+namespace {
+
+__global__ void k_to_bf16_padded(const float *__restrict__ src, int64_t N, int64_t K, int64_t Kpad,
+                                 __nv_bfloat16 *__restrict__ dst) {
+    const int64_t total = N * Kpad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = i / Kpad, k = i % Kpad;
+        dst[i] = __float2bfloat16_rn(k < K ? src[n * K + k] : 0.f);
+    }
 }
+
+int64_t kpad_of(int64_t K) { return (K + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK; }
+
+// (N, K, source offset) of every slot
+void slot_shapes(const nnqs_model *M, int slot, int64_t &N, int64_t &K, int64_t &src) {
+    const int l = slot / 4, which = slot % 4;
+    const int64_t d = M->d, F = M->F;
+    if (l == M->L) {
+        N = M->P;
+        K = M->P;
+        src = M->lay.ph_w2;
+        return;
+    }
+    const auto &lo = M->lay.layer[l];
+    switch (which) {
+        case 0: N = 3 * d; K = d; src = lo.wqkv; break;
+        case 1: N = d; K = d; src = lo.wo; break;
+        case 2: N = F; K = d; src = lo.w1; break;
+        default: N = d; K = F; src = lo.w2; break;
+    }
+}
+
+bool g_attr_set[4] = {false, false, false, false};
+
+template <int EPI>
+nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s) {
+    if (!g_attr_set[EPI]) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           tc::kSmemBytes));
+        g_attr_set[EPI] = true;
+    }
+    dim3 grid((unsigned)((g.M + tc::kTileM - 1) / tc::kTileM), (unsigned)n_tiles_n);
+    NNQS_LAUNCH("k_tc_gemm", s, tc::k_tc_gemm<EPI><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(g));
+    return NNQS_OK;
+}
+
+}  // namespace
+
+void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
+    const int n_slots = 4 * M->L + 1;
+    int64_t total = 0;
+    TcWeights tmp;
+    TcWeights &t = w ? *w : tmp;
+    t.n_slots = n_slots;
+    for (int sl = 0; sl < n_slots; ++sl) {
+        if (sl / 4 == M->L && sl % 4 != 0) continue;
+        int64_t N, K, src;
+        slot_shapes(M, sl, N, K, src);
+        t.off[sl] = total;
+        t.rows[sl] = (int32_t)N;
+        t.cols[sl] = (int32_t)K;
+        t.pcols[sl] = (int32_t)kpad_of(K);
+        t.src[sl] = src;
+        total += N * kpad_of(K);
+    }
+    t.bf16 = a.take<__nv_bfloat16>(size_t(total));
+}
+
+nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeights &w, cudaStream_t s) {
+    for (int sl = 0; sl < w.n_slots; ++sl) {
+        if (sl / 4 == M->L && sl % 4 != 0) continue;
+        const int64_t N = w.rows[sl], K = w.cols[sl], Kp = w.pcols[sl];
+        __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(w.bf16) + w.off[sl];
+        NNQS_LAUNCH("k_to_bf16", s,
+                    k_to_bf16_padded<<<(unsigned)std::min<int64_t>((N * Kp + 255) / 256, 4096), 256, 0, s>>>(
+                        params + w.src[sl], N, K, Kp, dst));
+    }
+    return NNQS_OK;
+}
+
+template <>
+nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot, int epi, const float *X,
+                                    int64_t rows, int64_t in, const float *bias, float *Y, int64_t ldy, float *Y2,
+                                    const float *resid) {
+    if (rows == 0) return NNQS_OK;
+    if (in != w.cols[slot]) return set_error(NNQS_E_INVAL, "tensor-core layer: input width mismatch");
+    tc::Args g{};
+    g.X = X;
+    g.ldx = in;
+    g.Wt = static_cast<const __nv_bfloat16 *>(w.bf16) + w.off[slot];
+    g.Kpad = w.pcols[slot];
+    g.bias = bias;
+    g.resid = resid;
+    g.Y = Y;
+    g.Y2 = Y2;
+    g.ldy = ldy;
+    g.M = rows;
+    g.N = w.rows[slot];
+    g.K = in;
+    g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
+    int cols = 32;
+    while (cols < g.Nt) cols <<= 1;
+    g.tmem_cols = cols;
+    g.st = w.st;
+    const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
+    note_work("k_tc_gemm", 2.0 * double(rows) * double(g.N) * double(in),
+              4.0 * double(rows) * in + 2.0 * double(g.N) * g.Kpad + 4.0 * double(rows) * g.N);
+    switch (epi) {
+        case tc::EPI_STORE: return launch<tc::EPI_STORE>(g, ntn, s);
+        case tc::EPI_GELU: return launch<tc::EPI_GELU>(g, ntn, s);
+        case tc::EPI_RELU: return launch<tc::EPI_RELU>(g, ntn, s);
+        case tc::EPI_RESID: return launch<tc::EPI_RESID>(g, ntn, s);
+        default: return set_error(NNQS_E_INVAL, "tensor-core layer: bad epilogue");
+    }
+}
+
+template <>
+nnqs_status tc_linear_fwd_ld<double>(cudaStream_t, const TcWeights &, int, int, const double *, int64_t, int64_t,
+                                     const double *, double *, int64_t, double *, const double *) {
+    return set_error(NNQS_E_UNSUPPORTED, "the tensor-core path computes in BF16/FP32, not FP64");
+}
+
 template <class R>
-nnqs_status tc_linear_fwd(cudaStream_t, const TcWeights &, int, int, const R *, int64_t, int64_t, const R *, R *, R *,
-                          const R *) {
-    return set_error(NNQS_E_UNSUPPORTED, "tensor-core path not built yet");
+nnqs_status tc_linear_fwd(cudaStream_t s, const TcWeights &w, int slot, int epi, const R *X, int64_t rows, int64_t in,
+                          const R *bias, R *Y, R *Y2, const R *resid) {
+    return tc_linear_fwd_ld<R>(s, w, slot, epi, X, rows, in, bias, Y, w.rows[slot], Y2, resid);
 }
 template nnqs_status tc_linear_fwd<float>(cudaStream_t, const TcWeights &, int, int, const float *, int64_t, int64_t,
                                           const float *, float *, float *, const float *);
 template nnqs_status tc_linear_fwd<double>(cudaStream_t, const TcWeights &, int, int, const double *, int64_t, int64_t,
                                            const double *, double *, double *, const double *);
-template <class R>
-nnqs_status tc_linear_fwd_ld(cudaStream_t, const TcWeights &, int, int, const R *, int64_t, int64_t, const R *, R *,
-                             int64_t, R *, const R *) {
-    return set_error(NNQS_E_UNSUPPORTED, "tensor-core path not built yet");
-}
-template nnqs_status tc_linear_fwd_ld<float>(cudaStream_t, const TcWeights &, int, int, const float *, int64_t,
-                                             int64_t, const float *, float *, int64_t, float *, const float *);
-template nnqs_status tc_linear_fwd_ld<double>(cudaStream_t, const TcWeights &, int, int, const double *, int64_t,
-                                              int64_t, const double *, double *, int64_t, double *, const double *);
+
 }  // namespace nnqs

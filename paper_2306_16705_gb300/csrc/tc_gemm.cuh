@@ -1,0 +1,247 @@
+// tcgen05 (5th-generation tensor core) GEMM for the ansatz's linear layers:
+//   Y[M][N] (epilogue) = X[M][K] W[N][K]^T,  X FP32 -> BF16, W BF16, FP32 accumulate in TMEM.
+//
+// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 256, a multiple of
+// 16).  K is walked in chunks of 64 BF16 (one 128-byte row per operand row):
+// all threads convert/stage the chunk into shared memory in the K-major
+// 128-byte-swizzle layout (8-row x 128 B atoms, 16-byte granules XOR-ed by the
+// row index within the atom), one thread issues four M=128, K=16 MMAs and
+// commits them to an mbarrier, and every thread waits on it before the
+// buffer is refilled.  The epilogue reads the accumulator with tcgen05.ld
+// (warp w owns TMEM lanes 32w..32w+31 = tile rows) and applies bias /
+// activation / residual in FP32.
+//
+// Every wait is bounded: on a timeout the kernel records NNQS_E_TIMEOUT,
+// skips the epilogue and still releases its TMEM.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace nnqs {
+namespace tc {
+
+constexpr int kThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kChunkK = 64;                      // BF16 per 128-byte row
+constexpr int kABytes = kTileM * kChunkK * 2;    // 16 KB
+constexpr int kMaxN = 256;
+constexpr int kBBytes = kMaxN * kChunkK * 2;     // 32 KB
+constexpr int kSmemBytes = kABytes + kBBytes + 1024 + 64;
+
+enum { EPI_STORE = 0, EPI_GELU = 1, EPI_RELU = 2, EPI_RESID = 3 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t(1) << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= uint64_t((1024u >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;
+    d |= uint64_t(2) << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// bounded wait on an mbarrier phase; false on timeout (~2 s at 2 GHz)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    const long long t0 = clock64();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 4000000000ll) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+struct Args {
+    const float *X;        // [M][ldx], K valid columns
+    int64_t ldx;
+    const __nv_bfloat16 *Wt;  // [Npad][Kpad] BF16, zero padded
+    int64_t Kpad;
+    const float *bias;     // [N] or null
+    const float *resid;    // EPI_RESID: [M][ldy]
+    float *Y;              // [M][ldy]
+    float *Y2;             // activation output for GELU/RELU
+    int64_t ldy;
+    int64_t M, N, K;
+    int Nt;                // N per CTA (multiple of 16, <= 256)
+    int tmem_cols;         // power of two >= max(32, Nt)
+    DevStatus *st;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms want 1024-byte alignment
+    uint8_t *sbase = smem_raw + (base - raw);
+    uint8_t *sA = sbase;
+    uint8_t *sB = sbase + kABytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sbase + kABytes + kBBytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + kABytes + kBBytes + 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t m0 = blockIdx.x * (int64_t)kTileM;
+    const int64_t n0 = blockIdx.y * (int64_t)g.Nt;
+    const int Nt = g.Nt;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(g.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = idesc_bf16(kTileM, Nt);
+    const uint32_t mb = smem_u32(mbar);
+
+    bool ok = true;
+    uint32_t phase = 0;
+    const int nchunks = (int)((g.K + kChunkK - 1) / kChunkK);
+    for (int kc = 0; kc < nchunks && ok; ++kc) {
+        const int64_t k0 = (int64_t)kc * kChunkK;
+        // A: 128 rows x 8 granules of 8 BF16 (from 8 FP32 each)
+        for (int it = tid; it < kTileM * 8; it += kThreads) {
+            const int r = it >> 3, c = it & 7;
+            const int64_t m = m0 + r;
+            const int64_t k = k0 + c * 8;
+            uint32_t packed[4] = {0u, 0u, 0u, 0u};
+            if (m < g.M) {
+                const float *src = g.X + m * g.ldx + k;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float v0 = (k + 2 * e < g.K) ? src[2 * e] : 0.f;
+                    const float v1 = (k + 2 * e + 1 < g.K) ? src[2 * e + 1] : 0.f;
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                    packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+                }
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4));
+            *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+        // B: Nt rows x 8 granules straight from the padded BF16 weights
+        for (int it = tid; it < Nt * 8; it += kThreads) {
+            const int r = it >> 3, c = it & 7;
+            const int64_t n = n0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (n < g.N) v = *reinterpret_cast<const uint4 *>(g.Wt + n * g.Kpad + k0 + c * 8);
+            *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) = v;
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (tid == 0) {
+            const uint64_t da = desc_sw128(smem_u32(sA)), db = desc_sw128(smem_u32(sB));
+#pragma unroll
+            for (int k = 0; k < kChunkK / 16; ++k)  // +32 bytes per K=16 step inside the swizzle atom
+                mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+            mma_commit(mb);
+        }
+        ok = mbar_wait(mb, phase);
+        phase ^= 1u;
+    }
+    fence_after_sync();
+    if (!ok) {
+        if (tid == 0) {
+            if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -10;
+        }
+    } else {
+        const int row = warp * 32 + lane;
+        const int64_t m = m0 + row;
+        const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
+        for (int c0 = 0; c0 < Nt; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(lane_base + uint32_t(c0), r);
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int64_t n = n0 + c0 + j;
+                if (n >= g.N) continue;
+                const float acc = __uint_as_float(r[j]);
+                const float v = acc + (g.bias ? g.bias[n] : 0.f);
+                const int64_t o = m * g.ldy + n;
+                if (EPI == EPI_STORE) {
+                    g.Y[o] = v;
+                } else if (EPI == EPI_GELU) {
+                    g.Y[o] = v;
+                    g.Y2[o] = gelu_f(v);
+                } else if (EPI == EPI_RELU) {
+                    g.Y[o] = v;
+                    g.Y2[o] = v > 0.f ? v : 0.f;
+                } else {
+                    g.Y[o] = g.resid[o] + v;
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
+    }
+}
+
+}  // namespace tc
+}  // namespace nnqs

@@ -11,6 +11,7 @@ struct TcWeights {
     int64_t off[4 * 64 + 1] = {};  // element offset of each slot
     int32_t rows[4 * 64 + 1] = {}, cols[4 * 64 + 1] = {}, prows[4 * 64 + 1] = {}, pcols[4 * 64 + 1] = {};
     int64_t src[4 * 64 + 1] = {};  // offset of the FP32 source matrix in the parameter vector
+    DevStatus *st = nullptr;       // where a timed-out wait is recorded
 };
 
 // slot of a weight: layer l, which = 0 qkv, 1 out-proj, 2 FFN-in, 3 FFN-out;
@@ -28,5 +29,13 @@ nnqs_status tc_linear_fwd(cudaStream_t s, const TcWeights &w, int slot, int epi,
 template <class R>
 nnqs_status tc_linear_fwd_ld(cudaStream_t s, const TcWeights &w, int slot, int epi, const R *X, int64_t rows,
                              int64_t in, const R *bias, R *Y, int64_t ldy, R *Y2, const R *resid);
+template <>
+nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot, int epi, const float *X,
+                                    int64_t rows, int64_t in, const float *bias, float *Y, int64_t ldy, float *Y2,
+                                    const float *resid);
+template <>
+nnqs_status tc_linear_fwd_ld<double>(cudaStream_t s, const TcWeights &w, int slot, int epi, const double *X,
+                                     int64_t rows, int64_t in, const double *bias, double *Y, int64_t ldy,
+                                     double *Y2, const double *resid);
 
 }  // namespace nnqs

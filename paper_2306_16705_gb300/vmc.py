@@ -50,6 +50,8 @@ class VMC:
         self._ws_sample = None
         self._ws_grad = None
         self.grad = torch.empty_like(self.params)
+        # size both workspaces once for the largest sample set a step can hold
+        self._ws_grad_for(self.max_unique)
         self.last_samples = None
         self.last_weights = None
         self.last_stats = None
@@ -78,7 +80,7 @@ class VMC:
     def _ws_grad_for(self, n):
         nb = B.lib().nnqs_energy_grad_workspace_size(self.ham.handle, self.model.handle, n, self.prec)
         if self._ws_grad is None or self._ws_grad.numel() < nb:
-            self._ws_grad = B.workspace(int(nb * 1.25), self.params.device)
+            self._ws_grad = B.workspace(int(nb), self.params.device)
         return self._ws_grad
 
     def state_dict(self) -> dict:

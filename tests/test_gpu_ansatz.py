@@ -110,3 +110,31 @@ def test_backward_matches_oracle(case, prec):
         ref = R[k]
         err = np.abs(G[k] - ref).max()
         assert err <= tol * max(1e-3, np.abs(ref).max()), (k, err, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_logpsi_mixed_tensor_cores(case):
+    """NNQS_MIXED: linear layers on tcgen05 with BF16 operands and FP32
+    accumulation.  BF16 keeps 8 significant bits, so log psi (a sum of T
+    log-probabilities) is checked to 2e-2 of its scale against the FP64
+    oracle, and must be far closer to it than a wrong kernel would be."""
+    name, N, na, nb, d, L, H, ns = case
+    m, params, flat = make(N, na, nb, d, L, H, seed=11)
+    x = I.random_sector_samples(N // 2, na, nb, ns, seed=3)
+    got = B.logpsi(m, flat, B.to_device_bits(x), B.MIXED).cpu().numpy()
+    la, ph = OA.forward(params, I.unpack_bits(x, N), na, nb, H)
+    assert np.abs(got[:, 0] - la).max() <= 2e-2 * max(1.0, np.abs(la).max())
+    assert np.abs(got[:, 1] - ph).max() <= 2e-2 * max(1.0, np.abs(ph).max())
+    # the error is at BF16 level, not at the level of an unrelated answer
+    assert np.corrcoef(got[:, 0], la)[0, 1] > 0.999
+
+
+def test_backward_mixed_close_to_fp64():
+    N, na, nb, d, L, H = 40, 10, 10, 64, 4, 8
+    m, params, flat = make(N, na, nb, d, L, H, seed=13)
+    x = B.to_device_bits(I.random_sector_samples(N // 2, na, nb, 200, seed=4))
+    rng = np.random.default_rng(0)
+    seed = torch.from_numpy(np.stack([rng.normal(size=200), rng.normal(size=200)], 1)).cuda()
+    g64 = B.logpsi_backward(m, flat, x, seed, B.FP64).cpu().numpy()
+    gmx = B.logpsi_backward(m, flat, x, seed, B.MIXED).cpu().numpy()
+    assert np.linalg.norm(gmx - g64) <= 5e-2 * np.linalg.norm(g64)

@@ -208,7 +208,7 @@ def test_adam_matches_oracle():
     assert np.abs(pt.cpu().numpy() - th).max() < 1e-6
 
 
-@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.MIXED])
 @pytest.mark.parametrize("wl_name,ns", [("n12", 100_000), ("n40", 4096)])
 def test_sampler_kv_cache_equals_recompute(wl_name, ns, prec):
     """The key/value-cached sampler (one new token per prefix per step) draws
@@ -219,3 +219,19 @@ def test_sampler_kv_cache_equals_recompute(wl_name, ns, prec):
     xb, wb = B.sample(m, flat, ns, seed=5, max_unique=8192, prec=prec, flags=B.SAMPLE_RECOMPUTE)
     assert torch.equal(xa, xb) and torch.equal(wa, wb)
     assert int(wa.sum().item()) == ns
+
+
+def test_energy_grad_mixed_and_fp32_against_fp64(n12):
+    """Energies of the three arithmetic paths on the same samples and
+    parameters.  With these deliberately large weights (std 0.3) FP32 lands
+    a few 1e-6 Ha from FP64 and BF16 a few 1e-3; the benchmark reports the
+    differences on its own workload.  Bounded loosely here: 1e-5 and 1e-1
+    relative."""
+    wl, ham, strings, h, eri = n12
+    m, params, flat = model_for(wl, seed=8)
+    S = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    w = torch.from_numpy(np.ones(len(S), dtype=np.int64)).cuda()
+    xs = B.to_device_bits(S)
+    e = {p: B.energy_grad(ham, m, flat, xs, w, p)[0].cpu().numpy()[0] for p in (B.FP64, B.FP32, B.MIXED)}
+    assert abs(e[B.FP32] - e[B.FP64]) < 1e-5 * abs(e[B.FP64])
+    assert abs(e[B.MIXED] - e[B.FP64]) < 1e-1 * abs(e[B.FP64])
