@@ -425,6 +425,31 @@ nnqs_status linear_dw(cudaStream_t s, const R *dY, int64_t rows, int64_t out, co
     return gemm<R>(s, EPI_ACCUM, dY, 1, out, X, 1, in, dW, in, nullptr, nullptr, nullptr, out, in, rows, scr);
 }
 
+// backward GEMMs of the weights that have BF16 copies: tensor cores for
+// NNQS_MIXED (tcw != null, FP32 activations), CUDA cores otherwise
+template <class R>
+nnqs_status bw_dx(cudaStream_t s, const TcWeights *tcw, int slot, const R *dY, int64_t rows, int64_t out, const R *Wt,
+                  int64_t in, R *dX, Scratch<R> scr) {
+    return linear_dx<R>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr);
+}
+template <>
+nnqs_status bw_dx<float>(cudaStream_t s, const TcWeights *tcw, int slot, const float *dY, int64_t rows, int64_t out,
+                         const float *Wt, int64_t in, float *dX, Scratch<float> scr) {
+    if (tcw) return tc_linear_dx(s, *tcw, slot, dY, rows, dX);
+    return linear_dx<float>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr);
+}
+template <class R>
+nnqs_status bw_dw(cudaStream_t s, const TcWeights *tcw, const R *dY, int64_t rows, int64_t out, const R *X,
+                  int64_t in, R *dW, Scratch<R> scr) {
+    return linear_dw<R>(s, dY, rows, out, X, in, dW, scr);
+}
+template <>
+nnqs_status bw_dw<float>(cudaStream_t s, const TcWeights *tcw, const float *dY, int64_t rows, int64_t out,
+                         const float *X, int64_t in, float *dW, Scratch<float> scr) {
+    if (tcw) return tc_linear_dw(s, dY, rows, out, X, in, dW, scr.buf, scr.elems, tcw->st);
+    return linear_dw<float>(s, dY, rows, out, X, in, dW, scr);
+}
+
 template <class R>
 nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *mean, const R *rstd, int64_t rows,
                    int cols, R *out, Scratch<R> scr) {
@@ -901,7 +926,8 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     A.xf = keep ? a.take<R>(C * M->N) : nullptr;
     // split-K / column-reduction partials: enough for the largest weight
     const int64_t wmax = std::max<int64_t>({3 * d * d, F * d, P * P, P * (int64_t)M->N});
-    A.scr.elems = size_t(std::max<int64_t>(8 * wmax, 4 * 152 * std::max<int64_t>(F, P) * 5));
+    // split-K partials of weight gradients: ~300 splits of a layer matrix
+    A.scr.elems = size_t(std::max<int64_t>({8 * wmax, 4 * 152 * std::max<int64_t>(F, P) * 5, 300 * F * d}));
     A.scr.buf = a.take<R>(A.scr.elems);
 }
 
@@ -1033,7 +1059,7 @@ void take_grads(const nnqs_model *M, int64_t C, Arena &a, Grads<R> &G) {
 
 template <class R>
 nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
-                           Grads<R> &G, const double2 *seed, R *gacc, cudaStream_t s) {
+                           Grads<R> &G, const double2 *seed, R *gacc, const TcWeights *tcw, cudaStream_t s) {
     const int T = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, N = M->N;
     const int64_t rows = C * T;
     const ParamLayout &Lo = M->lay;
@@ -1045,9 +1071,9 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     NNQS_TRY(linear_dw<R>(s, G.dph, C, 1, A.r2, P, gacc + Lo.ph_w3, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dph, nullptr, nullptr, nullptr, C, 1, gacc + Lo.ph_b3, scr));
     NNQS_LAUNCH("k_phase_dz2", s, k_phase_dz2<R><<<grid_for(C * P, 256), 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, G.dz2));
-    NNQS_TRY(linear_dw<R>(s, G.dz2, C, P, A.r1, P, gacc + Lo.ph_w2, scr));
+    NNQS_TRY(bw_dw<R>(s, tcw, G.dz2, C, P, A.r1, P, gacc + Lo.ph_w2, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dz2, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b2, scr));
-    NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz2, C, P, V.w2p, P, G.dz1, scr));
+    NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(L, 0), G.dz2, C, P, V.w2p, P, G.dz1, scr));
     NNQS_LAUNCH("k_act_bwd", s, k_act_bwd<R, false><<<grid_for(C * P, 256), 256, 0, s>>>(G.dz1, A.z1, C * P));
     NNQS_TRY(linear_dw<R>(s, G.dz1, C, P, A.xf, N, gacc + Lo.ph_w1, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, scr));
@@ -1071,25 +1097,25 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         const R *qkv = A.qkv + (int64_t)l * rows * 3 * d, *o = A.o + (int64_t)l * rows * d;
         const R *u = A.u + (int64_t)l * rows * F, *gu = A.gu + (int64_t)l * rows * F;
         // FFN: hout = hmid + gelu(a2 W1^T + b1) W2^T + b2
-        NNQS_TRY(linear_dw<R>(s, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
+        NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.b2, scr));
-        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dh, rows, d, Lw.w2, F, G.du, scr));
+        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr));
         NNQS_LAUNCH("k_act_bwd", s, k_act_bwd<R, true><<<grid_for(rows * F, 256), 256, 0, s>>>(G.du, u, rows * F));
-        NNQS_TRY(linear_dw<R>(s, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
+        NNQS_TRY(bw_dw<R>(s, tcw, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
         NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, scr));
-        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.du, rows, F, Lw.w1, d, G.dtmp, scr));
+        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 2), G.du, rows, F, Lw.w1, d, G.dtmp, scr));
         NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
                                                              G.dtmp, G.dh, rows, d));
         NNQS_TRY(colsum<R>(s, 1, G.dtmp, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, rows, d, gacc + Lg.ln2_g, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln2_b, scr));
         // attention: hmid = hin + attn(a) Wo^T + bo
-        NNQS_TRY(linear_dw<R>(s, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
+        NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.bo, scr));
-        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
+        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 1), G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
         NNQS_TRY(attn_bwd<R>(s, M->dh, qkv, o, A.lse + (int64_t)l * C * H * T, G.dtmp, G.dqkv, G.Dbuf, C, T, H, d));
-        NNQS_TRY(linear_dw<R>(s, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
+        NNQS_TRY(bw_dw<R>(s, tcw, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, scr));
-        NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
+        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 0), G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
         NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
                                                              G.dtmp, G.dh, rows, d));
         NNQS_TRY(colsum<R>(s, 1, G.dtmp, hin, A.mean1 + l * rows, A.rstd1 + l * rows, rows, d, gacc + Lg.ln1_g, scr));
@@ -1186,7 +1212,8 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
         const uint64_t *xc = x + c0 * M->W;
         // recompute the forward (tensor cores for NNQS_MIXED), keeping activations
         NNQS_TRY(forward_chunk<R>(M, V, xc, cn, A, G.lp, st, c0, tensor ? &tcw : nullptr, s));
-        NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc, s));
+        NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc,
+                                   tensor ? &tcw : nullptr, s));
     }
     NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
     return NNQS_OK;

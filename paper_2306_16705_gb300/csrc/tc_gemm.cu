@@ -22,6 +22,25 @@ __global__ void k_to_bf16_padded(const float *__restrict__ src, int64_t N, int64
     }
 }
 
+// transposed copy: dst[k][n] = W[n][k] for n < N, zero for N <= n < Npad
+__global__ void k_to_bf16_transposed(const float *__restrict__ src, int64_t N, int64_t K, int64_t Npad,
+                                     __nv_bfloat16 *__restrict__ dst) {
+    const int64_t total = K * Npad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / Npad, n = i % Npad;
+        dst[i] = __float2bfloat16_rn(n < N ? src[n * K + k] : 0.f);
+    }
+}
+
+// dW[i] += sum_z partial[z][i], splits in order
+__global__ void k_tc_reduce(const float *__restrict__ partial, int64_t splits, int64_t n, float *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc = 0.f;
+    for (int64_t z = 0; z < splits; ++z) acc += partial[z * n + i];
+    out[i] += acc;
+}
+
 int64_t kpad_of(int64_t K) { return (K + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK; }
 
 // (N, K, source offset) of every slot
@@ -43,18 +62,24 @@ void slot_shapes(const nnqs_model *M, int slot, int64_t &N, int64_t &K, int64_t 
     }
 }
 
-bool g_attr_set[4] = {false, false, false, false};
+bool g_attr_set[2][4] = {};
 
-template <int EPI>
-nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s) {
-    if (!g_attr_set[EPI]) {
-        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int EPI, bool TRANS = false>
+nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s, int64_t splits = 1) {
+    if (!g_attr_set[TRANS][EPI]) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            tc::kSmemBytes));
-        g_attr_set[EPI] = true;
+        g_attr_set[TRANS][EPI] = true;
     }
-    dim3 grid((unsigned)((g.M + tc::kTileM - 1) / tc::kTileM), (unsigned)n_tiles_n);
-    NNQS_LAUNCH("k_tc_gemm", s, tc::k_tc_gemm<EPI><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(g));
+    dim3 grid((unsigned)n_tiles_n, (unsigned)((g.M + tc::kTileM - 1) / tc::kTileM), (unsigned)splits);
+    NNQS_LAUNCH("k_tc_gemm", s, tc::k_tc_gemm<EPI, TRANS><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(g));
     return NNQS_OK;
+}
+
+int tmem_cols_for(int Nt) {
+    int cols = 32;
+    while (cols < Nt) cols <<= 1;
+    return cols;
 }
 
 }  // namespace
@@ -75,6 +100,9 @@ void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
         t.pcols[sl] = (int32_t)kpad_of(K);
         t.src[sl] = src;
         total += N * kpad_of(K);
+        t.toff[sl] = total;
+        t.tpcols[sl] = (int32_t)kpad_of(N);
+        total += K * kpad_of(N);
     }
     t.bf16 = a.take<__nv_bfloat16>(size_t(total));
 }
@@ -87,7 +115,66 @@ nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeigh
         NNQS_LAUNCH("k_to_bf16", s,
                     k_to_bf16_padded<<<(unsigned)std::min<int64_t>((N * Kp + 255) / 256, 4096), 256, 0, s>>>(
                         params + w.src[sl], N, K, Kp, dst));
+        const int64_t Np = w.tpcols[sl];
+        __nv_bfloat16 *tdst = static_cast<__nv_bfloat16 *>(w.bf16) + w.toff[sl];
+        NNQS_LAUNCH("k_to_bf16", s,
+                    k_to_bf16_transposed<<<(unsigned)std::min<int64_t>((K * Np + 255) / 256, 4096), 256, 0, s>>>(
+                        params + w.src[sl], N, K, Np, tdst));
     }
+    return NNQS_OK;
+}
+
+nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX) {
+    if (rows == 0) return NNQS_OK;
+    tc::Args g{};
+    const int64_t out = w.rows[slot], in = w.cols[slot];
+    g.X = dY;
+    g.ldx = out;
+    g.Wt = static_cast<const __nv_bfloat16 *>(w.bf16) + w.toff[slot];
+    g.Kpad = w.tpcols[slot];
+    g.Y = dX;
+    g.ldy = in;
+    g.M = rows;
+    g.N = in;
+    g.K = out;
+    g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
+    g.vec_x = (out % 4 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0);
+    g.tmem_cols = tmem_cols_for(g.Nt);
+    g.st = w.st;
+    note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
+              4.0 * double(rows) * out + 2.0 * double(in) * g.Kpad + 4.0 * double(rows) * in);
+    return launch<tc::EPI_STORE>(g, (g.N + g.Nt - 1) / g.Nt, s);
+}
+
+nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t out, const float *X, int64_t in,
+                         float *dW, float *scratch, size_t scratch_elems, DevStatus *st) {
+    if (rows == 0) return NNQS_OK;
+    tc::Args g{};
+    g.X = dY;
+    g.ldx = out;
+    g.Xb = X;
+    g.ldb = in;
+    g.M = out;
+    g.N = in;
+    g.K = rows;
+    g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
+    g.tmem_cols = tmem_cols_for(g.Nt);
+    g.st = st;
+    const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
+    const int64_t tiles = ((g.M + tc::kTileM - 1) / tc::kTileM) * ntn;
+    int64_t splits = std::max<int64_t>(1, (2 * 152 + tiles - 1) / tiles);
+    splits = std::min<int64_t>(splits, (rows + tc::kChunkK - 1) / tc::kChunkK);
+    splits = std::min<int64_t>(splits, (int64_t)(scratch_elems / size_t(out * in)));
+    if (splits < 1) return set_error(NNQS_E_WORKSPACE, "tensor-core weight gradient: scratch too small");
+    g.kchunk = ((rows + splits - 1) / splits + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK;
+    splits = (rows + g.kchunk - 1) / g.kchunk;
+    g.Y = scratch;
+    g.ldy = in;
+    note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
+              4.0 * double(rows) * (out + in) + 4.0 * double(splits) * out * in);
+    NNQS_TRY((launch<tc::EPI_STORE, true>(g, ntn, s, splits)));
+    NNQS_LAUNCH("k_tc_reduce", s,
+                k_tc_reduce<<<grid_for(out * in, 256), 256, 0, s>>>(scratch, splits, out * in, dW));
     return NNQS_OK;
 }
 
@@ -111,9 +198,8 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     g.N = w.rows[slot];
     g.K = in;
     g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
-    int cols = 32;
-    while (cols < g.Nt) cols <<= 1;
-    g.tmem_cols = cols;
+    g.vec_x = (in % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+    g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
     note_work("k_tc_gemm", 2.0 * double(rows) * double(g.N) * double(in),

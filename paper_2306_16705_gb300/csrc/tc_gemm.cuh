@@ -1,8 +1,8 @@
 // tcgen05 (5th-generation tensor core) GEMM for the ansatz's linear layers:
 //   Y[M][N] (epilogue) = X[M][K] W[N][K]^T,  X FP32 -> BF16, W BF16, FP32 accumulate in TMEM.
 //
-// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 256, a multiple of
-// 16).  K is walked in chunks of 64 BF16 (one 128-byte row per operand row):
+// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 128, a multiple of
+// 16; four CTAs share an SM).  K is walked in chunks of 64 BF16 (one 128-byte row per operand row):
 // all threads convert/stage the chunk into shared memory in the K-major
 // 128-byte-swizzle layout (8-row x 128 B atoms, 16-byte granules XOR-ed by the
 // row index within the atom), one thread issues four M=128, K=16 MMAs and
@@ -27,7 +27,7 @@ constexpr int kThreads = 128;
 constexpr int kTileM = 128;
 constexpr int kChunkK = 64;                      // BF16 per 128-byte row
 constexpr int kABytes = kTileM * kChunkK * 2;    // 16 KB
-constexpr int kMaxN = 256;
+constexpr int kMaxN = 128;                       // N per CTA: TMEM 128 columns, 4 CTAs per SM
 constexpr int kBBytes = kMaxN * kChunkK * 2;     // 32 KB
 constexpr int kSmemBytes = kABytes + kBBytes + 1024 + 64;
 
@@ -118,12 +118,20 @@ struct Args {
     int64_t ldy;
     int64_t M, N, K;
     int Nt;                // N per CTA (multiple of 16, <= 256)
+    int vec_x;             // X rows 16-byte aligned (float4 loads allowed)
+    const float *Xb;       // TRANS: second operand [K][ldb]
+    int64_t ldb;
+    int64_t kchunk;        // TRANS: reduction rows per blockIdx.z (multiple of 64)
     int tmem_cols;         // power of two >= max(32, Nt)
     DevStatus *st;
 };
 
-template <int EPI>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
+// TRANS = false: Y = X W^T (X FP32 [M][ldx], W BF16 [N][Kpad]).
+// TRANS = true : Y = A^T B over a long K (weight gradients): A(m,k) =
+//   X[k*ldx + m], B(n,k) = Xb[k*ldb + n], both FP32 and staged transposed;
+//   blockIdx.z takes rows [z*kchunk, (z+1)*kchunk) of the reduction.
+template <int EPI, bool TRANS>
+__global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms want 1024-byte alignment
@@ -134,8 +142,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + kABytes + kBBytes + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t m0 = blockIdx.x * (int64_t)kTileM;
-    const int64_t n0 = blockIdx.y * (int64_t)g.Nt;
+    // N tiles vary fastest so the CTAs sharing an A tile run together (A is
+    // then read from HBM once and from L2 after)
+    const int64_t m0 = blockIdx.y * (int64_t)kTileM;
+    const int64_t n0 = blockIdx.x * (int64_t)g.Nt;
     const int Nt = g.Nt;
 
     if (warp == 0) {
@@ -157,24 +167,66 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
 
     bool ok = true;
     uint32_t phase = 0;
-    const int nchunks = (int)((g.K + kChunkK - 1) / kChunkK);
+    const int64_t kbeg = TRANS ? blockIdx.z * g.kchunk : 0;
+    const int64_t kend = TRANS ? min(g.K, kbeg + g.kchunk) : g.K;
+    const int nchunks = (int)((kend - kbeg + kChunkK - 1) / kChunkK);
     for (int kc = 0; kc < nchunks && ok; ++kc) {
-        const int64_t k0 = (int64_t)kc * kChunkK;
-        // A: 128 rows x 8 granules of 8 BF16 (from 8 FP32 each)
+        const int64_t k0 = kbeg + (int64_t)kc * kChunkK;
+        if (TRANS) {
+            // A(m, k) = X[k][m]: consecutive threads take consecutive m, so each
+            // of the 8 loads of a warp reads 32 consecutive floats of one row
+            for (int it = tid; it < kTileM * 8; it += kThreads) {
+                const int r = it & (kTileM - 1), c = it >> 7;
+                const int64_t m = m0 + r;
+                uint32_t packed[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int64_t ka = k0 + c * 8 + 2 * e, kb = ka + 1;
+                    const float v0 = (m < g.M && ka < kend) ? __ldg(g.X + ka * g.ldx + m) : 0.f;
+                    const float v1 = (m < g.M && kb < kend) ? __ldg(g.X + kb * g.ldx + m) : 0.f;
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                    packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+                }
+                *reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4)) =
+                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            }
+            for (int it = tid; it < Nt * 8; it += kThreads) {
+                const int r = it % Nt, c = it / Nt;
+                const int64_t n = n0 + r;
+                uint32_t packed[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int64_t ka = k0 + c * 8 + 2 * e, kb = ka + 1;
+                    const float v0 = (n < g.N && ka < kend) ? __ldg(g.Xb + ka * g.ldb + n) : 0.f;
+                    const float v1 = (n < g.N && kb < kend) ? __ldg(g.Xb + kb * g.ldb + n) : 0.f;
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                    packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+                }
+                *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) =
+                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            }
+        } else {
+        // A: 128 rows x 8 granules of 8 BF16 (from 8 FP32 each); 8 consecutive
+        // threads cover one row's 256 contiguous bytes
         for (int it = tid; it < kTileM * 8; it += kThreads) {
             const int r = it >> 3, c = it & 7;
             const int64_t m = m0 + r;
             const int64_t k = k0 + c * 8;
-            uint32_t packed[4] = {0u, 0u, 0u, 0u};
-            if (m < g.M) {
-                const float *src = g.X + m * g.ldx + k;
+            float v[8];
+            if (m < g.M && g.vec_x && k + 8 <= g.K) {
+                const float4 *src = reinterpret_cast<const float4 *>(g.X + m * g.ldx + k);
+                const float4 a = __ldg(src), b = __ldg(src + 1);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float v0 = (k + 2 * e < g.K) ? src[2 * e] : 0.f;
-                    const float v1 = (k + 2 * e + 1 < g.K) ? src[2 * e + 1] : 0.f;
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-                    packed[e] = *reinterpret_cast<uint32_t *>(&b2);
-                }
+                for (int e = 0; e < 8; ++e) v[e] = (m < g.M && k + e < g.K) ? g.X[m * g.ldx + k + e] : 0.f;
+            }
+            uint32_t packed[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                packed[e] = *reinterpret_cast<uint32_t *>(&b2);
             }
             uint4 *dst = reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4));
             *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -187,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
             if (n < g.N) v = *reinterpret_cast<const uint4 *>(g.Wt + n * g.Kpad + k0 + c * 8);
             *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) = v;
         }
+        }
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
@@ -198,7 +251,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
                 mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
             mma_commit(mb);
         }
-        ok = mbar_wait(mb, phase);
+        // every thread saw the MMAs retire (or gave up) before the buffers are
+        // reused; the flag is made CTA-uniform so no barrier below diverges
+        ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
         phase ^= 1u;
     }
     fence_after_sync();
@@ -207,20 +262,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
             if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -10;
         }
     } else {
+        // 32-column slabs: TMEM -> shared (row per thread) -> global (8
+        // threads per 128-byte row segment, coalesced), epilogue applied on
+        // the way out.  The operand buffers are free once the MMAs retired.
+        float *slab = reinterpret_cast<float *>(sbase);  // [128][33]
         const int row = warp * 32 + lane;
-        const int64_t m = m0 + row;
         const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
-        for (int c0 = 0; c0 < Nt; c0 += 16) {
+        for (int c0 = 0; c0 < Nt; c0 += 32) {
             uint32_t r[16];
             tmem_ld16(lane_base + uint32_t(c0), r);
-            if (m >= g.M) continue;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int64_t n = n0 + c0 + j;
-                if (n >= g.N) continue;
-                const float acc = __uint_as_float(r[j]);
-                const float v = acc + (g.bias ? g.bias[n] : 0.f);
-                const int64_t o = m * g.ldy + n;
+            for (int j = 0; j < 16; ++j) slab[row * 33 + j] = __uint_as_float(r[j]);
+            tmem_ld16(lane_base + uint32_t(c0 + 16), r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) slab[row * 33 + 16 + j] = __uint_as_float(r[j]);
+            __syncthreads();
+            for (int it = tid; it < kTileM * 32; it += kThreads) {
+                const int rr = it >> 5, cc = it & 31;
+                const int64_t m = m0 + rr, n = n0 + c0 + cc;
+                if (m >= g.M || n >= g.N) continue;
+                const float v = slab[rr * 33 + cc] + (g.bias ? __ldg(g.bias + n) : 0.f);
+                const int64_t o = (TRANS ? blockIdx.z * g.M * g.ldy : 0) + m * g.ldy + n;
                 if (EPI == EPI_STORE) {
                     g.Y[o] = v;
                 } else if (EPI == EPI_GELU) {
@@ -233,6 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(Args g) {
                     g.Y[o] = g.resid[o] + v;
                 }
             }
+            __syncthreads();
         }
     }
     fence_before_sync();

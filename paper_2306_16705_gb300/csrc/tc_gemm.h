@@ -11,6 +11,8 @@ struct TcWeights {
     int64_t off[4 * 64 + 1] = {};  // element offset of each slot
     int32_t rows[4 * 64 + 1] = {}, cols[4 * 64 + 1] = {}, prows[4 * 64 + 1] = {}, pcols[4 * 64 + 1] = {};
     int64_t src[4 * 64 + 1] = {};  // offset of the FP32 source matrix in the parameter vector
+    int64_t toff[4 * 64 + 1] = {};  // transposed copy W^T [cols][pad(rows)] for input gradients
+    int32_t tpcols[4 * 64 + 1] = {};
     DevStatus *st = nullptr;       // where a timed-out wait is recorded
 };
 
@@ -37,5 +39,12 @@ template <>
 nnqs_status tc_linear_fwd_ld<double>(cudaStream_t s, const TcWeights &w, int slot, int epi, const double *X,
                                      int64_t rows, int64_t in, const double *bias, double *Y, int64_t ldy,
                                      double *Y2, const double *resid);
+
+// dX[rows][in] = dY[rows][out] W[out][in] on tensor cores (W^T copy of `slot`)
+nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX);
+// dW[out][in] += dY[rows][out]^T X[rows][in] on tensor cores, split over rows;
+// partials go to `scratch` (scratch_elems floats) and are added in order
+nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t out, const float *X, int64_t in,
+                         float *dW, float *scratch, size_t scratch_elems, DevStatus *st);
 
 }  // namespace nnqs
