@@ -238,7 +238,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def timed(n_steps, v):
+    def timed(n_steps, v, stages=None):
         # every timed step starts from the same random-init parameters and
         # Adam state (restored outside the timed region; the Adam update
         # itself runs inside), so each step samples the same distribution
@@ -253,11 +253,16 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            v.step()
+            marks = [] if stages is not None else None
+            v.step(marks=marks)
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
             nu += int(v.last_samples.shape[0])
+            if stages is not None:
+                stages["sample"] += e0.elapsed_time(marks[0])
+                stages["energy_grad"] += marks[0].elapsed_time(marks[1])
+                stages["adam"] += marks[1].elapsed_time(marks[2])
         return ts, nu
 
     l0 = B.launch_count()
@@ -272,7 +277,8 @@ def run_ours(args):
     # events: per-kernel device times for the roofline
     B.profile_reset()
     B.profile_enable(True)
-    prof_times, _ = timed(args.steps, vmc)
+    stages = {"sample": 0.0, "energy_grad": 0.0, "adam": 0.0}
+    prof_times, _ = timed(args.steps, vmc, stages)
     prof = B.profile()
     B.profile_enable(False)
     ms_step = float(np.mean(times))
@@ -333,6 +339,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roof,
         "profiled_ms_per_step": float(np.mean(prof_times)),
+        "stage_ms_per_step": {k: round(v / args.steps, 3) for k, v in stages.items()},
         "kernels_ms": {k: round(v["ms"], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
     }
     if not args.no_clocks:

@@ -64,16 +64,27 @@ class VMC:
         return B.sample(self.model, self.params, self.n_samples, seed, self.max_unique, self.prec,
                         check=False, ws=self._ws_sample)
 
-    def step(self, check: bool = False) -> torch.Tensor:
+    def step(self, check: bool = False, marks=None) -> torch.Tensor:
         """One VMC iteration; returns the device stats tensor [Re E, Im E, Var,
-        sum w] (no host synchronisation beyond the sampler's)."""
+        sum w] (no host synchronisation beyond the sampler's).  ``marks``: a
+        list that receives a CUDA event after sampling, after the energy and
+        gradient, and after the update (stage timing)."""
         x, w = self.sample()
+        if marks is not None:
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record()
         stats, _, _ = B.energy_grad(self.ham, self.model, self.params, x, w, self.prec,
                                     check=check, ws=self._ws_grad_for(x.shape[0]),
                                     want_eloc=False, grad_out=self.grad)
+        if marks is not None:
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record()
         self.t += 1
         B.adam_step(self.params, self.grad, self.m, self.v, self.t, self.lr, self.betas[0],
                     self.betas[1], self.eps)
+        if marks is not None:
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record()
         self.last_samples, self.last_weights, self.last_stats = x, w, stats
         return stats
 
