@@ -72,8 +72,16 @@ nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s, int64_t
         g_attr_set[TRANS][EPI] = true;
     }
     dim3 grid((unsigned)n_tiles_n, (unsigned)((g.M + tc::kTileM - 1) / tc::kTileM), (unsigned)splits);
-    NNQS_LAUNCH("k_tc_gemm", s, tc::k_tc_gemm<EPI, TRANS><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(g));
+    NNQS_LAUNCH("k_tc_gemm", s, (tc::k_tc_gemm<EPI, TRANS><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(g)));
     return NNQS_OK;
+}
+
+// N per CTA: the whole N when it fits in 64 columns, else 128-column tiles
+// when N is a multiple of 128, else 64-column tiles (epilogue slabs are 64
+// columns wide)
+int nt_for(int64_t N) {
+    if (N <= 64) return (int)((N + 15) / 16 * 16);
+    return (N % 128 == 0) ? 128 : 64;
 }
 
 int tmem_cols_for(int Nt) {
@@ -137,7 +145,7 @@ nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const flo
     g.M = rows;
     g.N = in;
     g.K = out;
-    g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
+    g.Nt = nt_for(g.N);
     g.vec_x = (out % 4 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
@@ -157,7 +165,7 @@ nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t 
     g.M = out;
     g.N = in;
     g.K = rows;
-    g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
+    g.Nt = nt_for(g.N);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = st;
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
@@ -184,6 +192,10 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
                                     const float *resid) {
     if (rows == 0) return NNQS_OK;
     if (in != w.cols[slot]) return set_error(NNQS_E_INVAL, "tensor-core layer: input width mismatch");
+    if ((epi == tc::EPI_GELU || epi == tc::EPI_RELU) && Y2 == nullptr)
+        return set_error(NNQS_E_INVAL, "tensor-core layer: activation output missing");
+    if (epi == tc::EPI_RESID && resid == nullptr)
+        return set_error(NNQS_E_INVAL, "tensor-core layer: residual input missing");
     tc::Args g{};
     g.X = X;
     g.ldx = in;
@@ -197,7 +209,7 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     g.M = rows;
     g.N = w.rows[slot];
     g.K = in;
-    g.Nt = (int)std::min<int64_t>(tc::kMaxN, (g.N + 15) / 16 * 16);
+    g.Nt = nt_for(g.N);
     g.vec_x = (in % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;

@@ -106,6 +106,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
+__device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
+    uint32_t p[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        p[e] = *reinterpret_cast<uint32_t *>(&b2);
+    }
+    return make_uint4(p[0], p[1], p[2], p[3]);
+}
+
 struct Args {
     const float *X;        // [M][ldx], K valid columns
     int64_t ldx;
@@ -170,76 +180,81 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
     const int64_t kbeg = TRANS ? blockIdx.z * g.kchunk : 0;
     const int64_t kend = TRANS ? min(g.K, kbeg + g.kchunk) : g.K;
     const int nchunks = (int)((kend - kbeg + kChunkK - 1) / kChunkK);
-    for (int kc = 0; kc < nchunks && ok; ++kc) {
-        const int64_t k0 = kbeg + (int64_t)kc * kChunkK;
-        if (TRANS) {
-            // A(m, k) = X[k][m]: consecutive threads take consecutive m, so each
-            // of the 8 loads of a warp reads 32 consecutive floats of one row
-            for (int it = tid; it < kTileM * 8; it += kThreads) {
+    // operand granules of one K chunk, held in registers as packed BF16:
+    // 8 A granules and up to 8 B granules per thread
+    uint4 ra[8], rb[8];
+    auto load_chunk = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float v[8];
+            if (TRANS) {
+                // A(m, k) = X[k][m]: a warp's 32 threads read 32 consecutive m of one row
+                const int it = tid + i * kThreads;
                 const int r = it & (kTileM - 1), c = it >> 7;
                 const int64_t m = m0 + r;
-                uint32_t packed[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int64_t ka = k0 + c * 8 + 2 * e, kb = ka + 1;
-                    const float v0 = (m < g.M && ka < kend) ? __ldg(g.X + ka * g.ldx + m) : 0.f;
-                    const float v1 = (m < g.M && kb < kend) ? __ldg(g.X + kb * g.ldx + m) : 0.f;
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-                    packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+                for (int e = 0; e < 8; ++e) {
+                    const int64_t k = k0 + c * 8 + e;
+                    v[e] = (m < g.M && k < kend) ? __ldg(g.X + k * g.ldx + m) : 0.f;
                 }
-                *reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4)) =
-                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            } else {
+                // A rows: 8 consecutive threads cover one row's 64 FP32 values
+                const int it = tid + i * kThreads;
+                const int r = it >> 3, c = it & 7;
+                const int64_t m = m0 + r;
+                const int64_t k = k0 + c * 8;
+                if (m < g.M && g.vec_x && k + 8 <= g.K) {
+                    const float4 *src = reinterpret_cast<const float4 *>(g.X + m * g.ldx + k);
+                    const float4 a = __ldg(src), b = __ldg(src + 1);
+                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = (m < g.M && k + e < g.K) ? g.X[m * g.ldx + k + e] : 0.f;
+                }
             }
-            for (int it = tid; it < Nt * 8; it += kThreads) {
+            ra[i] = pack8(v);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i * kThreads >= Nt * 8) break;  // Nt/16 granule rounds
+            const int it = tid + i * kThreads;
+            if (TRANS) {
                 const int r = it % Nt, c = it / Nt;
                 const int64_t n = n0 + r;
-                uint32_t packed[4];
+                float v[8];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int64_t ka = k0 + c * 8 + 2 * e, kb = ka + 1;
-                    const float v0 = (n < g.N && ka < kend) ? __ldg(g.Xb + ka * g.ldb + n) : 0.f;
-                    const float v1 = (n < g.N && kb < kend) ? __ldg(g.Xb + kb * g.ldb + n) : 0.f;
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-                    packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+                for (int e = 0; e < 8; ++e) {
+                    const int64_t k = k0 + c * 8 + e;
+                    v[e] = (n < g.N && k < kend) ? __ldg(g.Xb + k * g.ldb + n) : 0.f;
                 }
-                *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) =
-                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
-            }
-        } else {
-        // A: 128 rows x 8 granules of 8 BF16 (from 8 FP32 each); 8 consecutive
-        // threads cover one row's 256 contiguous bytes
-        for (int it = tid; it < kTileM * 8; it += kThreads) {
-            const int r = it >> 3, c = it & 7;
-            const int64_t m = m0 + r;
-            const int64_t k = k0 + c * 8;
-            float v[8];
-            if (m < g.M && g.vec_x && k + 8 <= g.K) {
-                const float4 *src = reinterpret_cast<const float4 *>(g.X + m * g.ldx + k);
-                const float4 a = __ldg(src), b = __ldg(src + 1);
-                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                rb[i] = pack8(v);
             } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = (m < g.M && k + e < g.K) ? g.X[m * g.ldx + k + e] : 0.f;
+                const int r = it >> 3, c = it & 7;
+                const int64_t n = n0 + r;
+                rb[i] = n < g.N ? __ldg(reinterpret_cast<const uint4 *>(g.Wt + n * g.Kpad + k0 + c * 8))
+                                : make_uint4(0u, 0u, 0u, 0u);
             }
-            uint32_t packed[4];
+        }
+    };
+    auto store_chunk = [&]() {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-                packed[e] = *reinterpret_cast<uint32_t *>(&b2);
-            }
-            uint4 *dst = reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4));
-            *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        for (int i = 0; i < 8; ++i) {
+            const int it = tid + i * kThreads;
+            const int r = TRANS ? (it & (kTileM - 1)) : (it >> 3), c = TRANS ? (it >> 7) : (it & 7);
+            *reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4)) = ra[i];
         }
-        // B: Nt rows x 8 granules straight from the padded BF16 weights
-        for (int it = tid; it < Nt * 8; it += kThreads) {
-            const int r = it >> 3, c = it & 7;
-            const int64_t n = n0 + r;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (n < g.N) v = *reinterpret_cast<const uint4 *>(g.Wt + n * g.Kpad + k0 + c * 8);
-            *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) = v;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i * kThreads >= Nt * 8) break;
+            const int it = tid + i * kThreads;
+            const int r = TRANS ? (it % Nt) : (it >> 3), c = TRANS ? (it / Nt) : (it & 7);
+            *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) = rb[i];
         }
-        }
+    };
+    if (nchunks > 0) load_chunk(kbeg);
+    for (int kc = 0; kc < nchunks && ok; ++kc) {
+        store_chunk();
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
@@ -251,6 +266,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
                 mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
             mma_commit(mb);
         }
+        // the next chunk's loads are in flight while the MMAs run
+        if (kc + 1 < nchunks) load_chunk(kbeg + int64_t(kc + 1) * kChunkK);
         // every thread saw the MMAs retire (or gave up) before the buffers are
         // reused; the flag is made CTA-uniform so no barrier below diverges
         ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
@@ -262,37 +279,60 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
             if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -10;
         }
     } else {
-        // 32-column slabs: TMEM -> shared (row per thread) -> global (8
-        // threads per 128-byte row segment, coalesced), epilogue applied on
-        // the way out.  The operand buffers are free once the MMAs retired.
-        float *slab = reinterpret_cast<float *>(sbase);  // [128][33]
+        // 64-column slabs: TMEM -> shared (thread = row) -> global (a warp
+        // writes 32 consecutive floats of one row), epilogue applied on the way
+        // out.  The operand buffers (32 KB) are free once the MMAs retired; the
+        // slab [128][64] is XOR-swizzled by the row so both phases are free of
+        // bank conflicts.  Residual and bias values of a batch are loaded before
+        // any of its stores: Y may alias the residual, and batching keeps the
+        // loads in flight together instead of one dependent round trip each.
+        float *slab = reinterpret_cast<float *>(sbase);
         const int row = warp * 32 + lane;
         const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
-        for (int c0 = 0; c0 < Nt; c0 += 32) {
-            uint32_t r[16];
-            tmem_ld16(lane_base + uint32_t(c0), r);
+        const int64_t zoff = TRANS ? int64_t(blockIdx.z) * g.M * g.ldy : 0;
+        for (int c0 = 0; c0 < Nt; c0 += 64) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) slab[row * 33 + j] = __uint_as_float(r[j]);
-            tmem_ld16(lane_base + uint32_t(c0 + 16), r);
+            for (int q = 0; q < 4; ++q) {
+                if (c0 + 16 * q >= Nt) break;
+                uint32_t r[16];
+                tmem_ld16(lane_base + uint32_t(c0 + 16 * q), r);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) slab[row * 33 + 16 + j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 16; ++j) slab[row * 64 + ((16 * q + j) ^ (row & 31))] = __uint_as_float(r[j]);
+            }
             __syncthreads();
-            for (int it = tid; it < kTileM * 32; it += kThreads) {
-                const int rr = it >> 5, cc = it & 31;
-                const int64_t m = m0 + rr, n = n0 + c0 + cc;
-                if (m >= g.M || n >= g.N) continue;
-                const float v = slab[rr * 33 + cc] + (g.bias ? __ldg(g.bias + n) : 0.f);
-                const int64_t o = (TRANS ? blockIdx.z * g.M * g.ldy : 0) + m * g.ldy + n;
-                if (EPI == EPI_STORE) {
-                    g.Y[o] = v;
-                } else if (EPI == EPI_GELU) {
-                    g.Y[o] = v;
-                    g.Y2[o] = gelu_f(v);
-                } else if (EPI == EPI_RELU) {
-                    g.Y[o] = v;
-                    g.Y2[o] = v > 0.f ? v : 0.f;
-                } else {
-                    g.Y[o] = g.resid[o] + v;
+            // thread -> one column (tid & 63) of the slab and every other row
+            // starting at tid >> 6: a warp stores 32 consecutive floats of a row
+            const int cc = tid & 63, r0 = tid >> 6;
+            const int64_t n = n0 + c0 + cc;
+            const bool col_ok = (c0 + cc < Nt) && (n < g.N);
+            const float bias_v = (g.bias && col_ok) ? __ldg(g.bias + n) : 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float rv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int rr = r0 + 2 * (16 * b + j);
+                    const int64_t m = m0 + rr;
+                    rv[j] = (EPI == EPI_RESID && col_ok && m < g.M) ? g.resid[zoff + m * g.ldy + n] : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int rr = r0 + 2 * (16 * b + j);
+                    const int64_t m = m0 + rr;
+                    if (!col_ok || m >= g.M) continue;
+                    const float v = slab[rr * 64 + (cc ^ (rr & 31))] + bias_v;
+                    const int64_t o = zoff + m * g.ldy + n;
+                    if (EPI == EPI_STORE) {
+                        g.Y[o] = v;
+                    } else if (EPI == EPI_GELU) {
+                        g.Y[o] = v;
+                        g.Y2[o] = gelu_f(v);
+                    } else if (EPI == EPI_RELU) {
+                        g.Y[o] = v;
+                        g.Y2[o] = v > 0.f ? v : 0.f;
+                    } else {
+                        g.Y[o] = rv[j] + v;
+                    }
                 }
             }
             __syncthreads();
