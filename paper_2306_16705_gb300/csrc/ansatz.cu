@@ -591,6 +591,146 @@ __global__ void k_attn_bwd_kv(const R *__restrict__ qkv, const R *__restrict__ l
     }
 }
 
+// Shared-memory attention: one CTA per sample, the sample's q|k|v rows
+// staged once (padded rows, conflict-free column reads), one thread per
+// (head, position).  Used whenever a sample's rows fit in shared memory.
+template <class R, int DH>
+__global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R *__restrict__ lse, int T, int H,
+                                int d) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    R *sq = reinterpret_cast<R *>(sm_raw);  // [T][3d+1]
+    const int ldq = 3 * d + 1, ldo = d + 1;
+    R *so = sq + T * ldq;                    // [T][d+1]
+    const int64_t i = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const R *src = qkv + i * T * 3 * d;
+    for (int e = tid; e < T * 3 * d; e += nt) sq[(e / (3 * d)) * ldq + e % (3 * d)] = src[e];
+    __syncthreads();
+    if (tid < H * T) {
+        const int hh = tid / T, q = tid % T;
+        const R scale = R(1) / sqrt(R(DH));
+        R qv[DH], acc[DH];
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            qv[c] = sq[q * ldq + hh * DH + c] * scale;
+            acc[c] = 0;
+        }
+        R m = neg_inf<R>(), l = 0;
+        for (int j = 0; j <= q; ++j) {
+            const R *kj = sq + j * ldq + d + hh * DH;
+            const R *vj = sq + j * ldq + 2 * d + hh * DH;
+            R sc = 0;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
+            const R mn = sc > m ? sc : m;
+            const R corr = exp_<R>(m - mn);
+            const R p = exp_<R>(sc - mn);
+            l = l * corr + p;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) acc[c] = acc[c] * corr + p * vj[c];
+            m = mn;
+        }
+        const R inv = R(1) / l;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) so[q * ldo + hh * DH + c] = acc[c] * inv;
+        lse[(i * H + hh) * T + q] = m + log_<R>(l);
+    }
+    __syncthreads();
+    R *dst = o + i * T * d;
+    for (int e = tid; e < T * d; e += nt) dst[e] = so[(e / d) * ldo + e % d];
+}
+
+template <class R, int DH>
+__global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__ o, const R *__restrict__ lse,
+                                const R *__restrict__ dout, R *__restrict__ dqkv, int T, int H, int d) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int ldq = 3 * d + 1, ldo = d + 1;
+    R *sq = reinterpret_cast<R *>(sm_raw);  // q|k|v [T][3d+1]
+    R *sg = sq + T * ldq;                    // dq|dk|dv [T][3d+1]
+    R *sdo = sg + T * ldq;                   // dout [T][d+1]
+    R *so = sdo + T * ldo;                   // o [T][d+1]
+    R *slse = so + T * ldo;                  // [H][T]
+    R *sD = slse + H * T;                    // [H][T]
+    const int64_t i = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < T * 3 * d; e += nt) sq[(e / (3 * d)) * ldq + e % (3 * d)] = qkv[i * T * 3 * d + e];
+    for (int e = tid; e < T * d; e += nt) {
+        sdo[(e / d) * ldo + e % d] = dout[i * T * d + e];
+        so[(e / d) * ldo + e % d] = o[i * T * d + e];
+    }
+    for (int e = tid; e < H * T; e += nt) slse[e] = lse[i * H * T + e];
+    __syncthreads();
+    const R scale = R(1) / sqrt(R(DH));
+    const bool act = tid < H * T;
+    const int hh = act ? tid / T : 0, pos = act ? tid % T : 0;
+    if (act) {
+        // dq_q = scale sum_{j<=q} p_qj (dp_qj - D_q) k_j,  D_q = do_q . o_q
+        const int q = pos;
+        R qv[DH], dov[DH], dq[DH];
+        R D = 0;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            qv[c] = sq[q * ldq + hh * DH + c] * scale;
+            dov[c] = sdo[q * ldo + hh * DH + c];
+            D += dov[c] * so[q * ldo + hh * DH + c];
+            dq[c] = 0;
+        }
+        sD[hh * T + q] = D;
+        const R L = slse[hh * T + q];
+        for (int j = 0; j <= q; ++j) {
+            const R *kj = sq + j * ldq + d + hh * DH;
+            const R *vj = sq + j * ldq + 2 * d + hh * DH;
+            R sc = 0, dp = 0;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) {
+                sc += qv[c] * kj[c];
+                dp += dov[c] * vj[c];
+            }
+            const R ds = exp_<R>(sc - L) * (dp - D);
+#pragma unroll
+            for (int c = 0; c < DH; ++c) dq[c] += ds * kj[c];
+        }
+#pragma unroll
+        for (int c = 0; c < DH; ++c) sg[q * ldq + hh * DH + c] = dq[c] * scale;
+    }
+    __syncthreads();
+    if (act) {
+        // dv_j = sum_{q>=j} p_qj do_q,  dk_j = scale sum_{q>=j} p_qj (dp_qj - D_q) q_q
+        const int j = pos;
+        R kv[DH], vv[DH], dk[DH], dv[DH];
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            kv[c] = sq[j * ldq + d + hh * DH + c];
+            vv[c] = sq[j * ldq + 2 * d + hh * DH + c];
+            dk[c] = dv[c] = 0;
+        }
+        for (int q = j; q < T; ++q) {
+            const R *qq = sq + q * ldq + hh * DH;
+            const R *dq = sdo + q * ldo + hh * DH;
+            R sc = 0, dp = 0;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) {
+                sc += qq[c] * kv[c];
+                dp += dq[c] * vv[c];
+            }
+            const R p = exp_<R>(sc * scale - slse[hh * T + q]);
+            const R ds = p * (dp - sD[hh * T + q]);
+#pragma unroll
+            for (int c = 0; c < DH; ++c) {
+                dv[c] += p * dq[c];
+                dk[c] += ds * qq[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            sg[j * ldq + d + hh * DH + c] = dk[c] * scale;
+            sg[j * ldq + 2 * d + hh * DH + c] = dv[c];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < T * 3 * d; e += nt) dqkv[i * T * 3 * d + e] = sg[(e / (3 * d)) * ldq + e % (3 * d)];
+}
+
 // ------------------------------------------------------------------ head + masked log-softmax
 // One warp per sample, lanes over positions.  pi~ of the 4 children at each
 // position is stored for the backward; log|psi| = 1/2 sum_t log pi~(x_t).
@@ -931,8 +1071,28 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     A.scr.buf = a.take<R>(A.scr.elems);
 }
 
+constexpr size_t kAttnSmemMax = 200 * 1024;
+
+template <class R>
+size_t attn_fwd_smem_bytes(int T, int d) { return sizeof(R) * size_t(T) * (4 * d + 2); }
+template <class R>
+size_t attn_bwd_smem_bytes(int T, int H, int d) { return sizeof(R) * (size_t(T) * (8 * d + 4) + 2 * size_t(H) * T); }
+
+template <class K>
+nnqs_status allow_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) NNQS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return NNQS_OK;
+}
+
 template <int DH_, class R>
 nnqs_status launch_attn_fwd(cudaStream_t s, const R *qkv, R *o, R *lse, int64_t n, int T, int H, int d) {
+    const size_t sm = attn_fwd_smem_bytes<R>(T, d);
+    if (H * T <= 1024 && sm <= kAttnSmemMax && n > 0) {
+        NNQS_TRY(allow_smem(k_attn_fwd_smem<R, DH_>, sm));
+        const int threads = (H * T + 31) / 32 * 32;
+        NNQS_LAUNCH("k_attn_fwd", s, k_attn_fwd_smem<R, DH_><<<(unsigned)n, threads, sm, s>>>(qkv, o, lse, T, H, d));
+        return NNQS_OK;
+    }
     NNQS_LAUNCH("k_attn_fwd", s, k_attn_fwd<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, n, T, H, d));
     return NNQS_OK;
 }
@@ -954,6 +1114,14 @@ nnqs_status attn_fwd(cudaStream_t s, int dh, const R *qkv, R *o, R *lse, int64_t
 template <int DH_, class R>
 nnqs_status launch_attn_bwd(cudaStream_t s, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
                             int64_t n, int T, int H, int d) {
+    const size_t sm = attn_bwd_smem_bytes<R>(T, H, d);
+    if (H * T <= 1024 && sm <= kAttnSmemMax && n > 0) {
+        NNQS_TRY(allow_smem(k_attn_bwd_smem<R, DH_>, sm));
+        const int threads = (H * T + 31) / 32 * 32;
+        NNQS_LAUNCH("k_attn_bwd", s,
+                    k_attn_bwd_smem<R, DH_><<<(unsigned)n, threads, sm, s>>>(qkv, o, lse, dout, dqkv, T, H, d));
+        return NNQS_OK;
+    }
     NNQS_LAUNCH("k_attn_bwd_q", s, k_attn_bwd_q<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d));
     NNQS_LAUNCH("k_attn_bwd_kv", s, k_attn_bwd_kv<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, lse, dout, Dbuf, dqkv, n, T, H, d));
     return NNQS_OK;
