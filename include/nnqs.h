@@ -63,9 +63,13 @@ enum { NNQS_SA = 0, NNQS_EXACT = 1 };
 
 /* Arithmetic of the ansatz: NNQS_FP64 = FP64 everywhere (the plain path);
  * NNQS_MIXED = BF16 operands on tcgen05 tensor cores with FP32 accumulation
- * and FP32 normalisation/softmax; NNQS_FP32 = FP32 CUDA cores.  Local-energy
- * ratios, sums and statistics are FP64 in every mode. */
-enum { NNQS_FP64 = 0, NNQS_MIXED = 1, NNQS_FP32 = 2 };
+ * and FP32 normalisation/softmax; NNQS_FP32 = FP32 CUDA cores;
+ * NNQS_BF16X3 = as NNQS_MIXED, but every forward linear layer splits its
+ * operands into high and low BF16 parts (x = x_h + x_l, x_h = bf16(x)) and
+ * sums three tensor-core products x_h w_h + x_h w_l + x_l w_h, so log psi
+ * carries about 16 operand bits instead of 8 (the reverse mode stays BF16).
+ * Local-energy ratios, sums and statistics are FP64 in every mode. */
+enum { NNQS_FP64 = 0, NNQS_MIXED = 1, NNQS_FP32 = 2, NNQS_BF16X3 = 3 };
 
 /* nnqs_eloc flags: choice of the sample-aware sweep.  GROUPS walks the
  * X/Y-mask groups for every sample (Alg. 2); PAIRS walks sample pairs and

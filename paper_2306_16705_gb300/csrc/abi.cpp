@@ -216,6 +216,7 @@ nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *param
         return eloc_sa(H, lut, lut_logpsi, n_lut, row_begin, n_rows, n_alpha, n_beta, flags, eloc_out, a, st, s);
     }
     if (!M || !params) return set_error(NNQS_E_INVAL, "NNQS_EXACT needs the model and its parameters");
+    if (!prec_valid(prec)) return set_error(NNQS_E_INVAL, "bad precision");
     NNQS_TRY(check_ws(workspace, workspace_bytes, eloc_exact_workspace(H, M, n_lut, n_rows, prec)));
     NNQS_TRY(reset_status(workspace, s));
     Arena a(workspace);

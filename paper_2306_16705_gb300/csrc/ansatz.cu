@@ -185,49 +185,357 @@ __global__ void k_ln_bwd(const R *__restrict__ x, const R *__restrict__ mean, co
     }
 }
 
-// ------------------------------------------------------------------ column reductions
-// partial[blk][c] = sum over this block's rows of f(row, c); modes:
-//   0: A[r][c]                 (bias gradients)
-//   1: A[r][c] * xh(r, c)      (LayerNorm gain gradient, xh from X, mean, rstd)
-constexpr int kColThreads = 256;
+// FP32 rows with d = 4 LPR (LPR a power of two <= 32): LPR lanes per row, one
+// float4 per lane, 32/LPR rows per warp and kLnRows such row groups per warp
+// with every load issued before the first reduction (the one-row-per-warp
+// kernels above leave most of a warp idle and have one load in flight)
+constexpr int kLnRows = 4;
 
-template <class R, int MODE>
-__global__ void k_colred(const R *__restrict__ A, const R *__restrict__ X, const R *__restrict__ mean,
-                         const R *__restrict__ rstd, int64_t rows, int cols, int64_t rows_per_block,
-                         R *__restrict__ partial) {
-    __shared__ R sh[kColThreads];
-    const int64_t r0 = blockIdx.x * rows_per_block;
-    const int64_t r1 = min(rows, r0 + rows_per_block);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int cb = 0; cb < cols; cb += 32) {
-        const int c = cb + lane;
-        R s = 0;
-        if (c < cols) {
-            for (int64_t r = r0 + warp; r < r1; r += kColThreads / 32) {
-                R v = A[r * cols + c];
-                if (MODE == 1) v *= (X[r * cols + c] - mean[r]) * rstd[r];
-                s += v;
+template <int LPR>
+__global__ void __launch_bounds__(256) k_ln_fwd_v(const float *__restrict__ x, const float *__restrict__ g,
+                                                  const float *__restrict__ b, float *__restrict__ y,
+                                                  float *__restrict__ mean, float *__restrict__ rstd, int64_t rows) {
+    constexpr int RPW = 32 / LPR, d = 4 * LPR;
+    const int lane = threadIdx.x & 31, sub = lane / LPR, l = lane % LPR;
+    const int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (RPW * kLnRows);
+    float4 v[kLnRows];
+#pragma unroll
+    for (int u = 0; u < kLnRows; ++u) {
+        const int64_t row = base + u * RPW + sub;
+        v[u] = row < rows ? __ldg(reinterpret_cast<const float4 *>(x + row * d) + l) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 gg = __ldg(reinterpret_cast<const float4 *>(g) + l), bb = __ldg(reinterpret_cast<const float4 *>(b) + l);
+#pragma unroll
+    for (int u = 0; u < kLnRows; ++u) {
+        const int64_t row = base + u * RPW + sub;
+        float s = (v[u].x + v[u].y) + (v[u].z + v[u].w);
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float mu = s / float(d);
+        const float zx = v[u].x - mu, zy = v[u].y - mu, zz = v[u].z - mu, zw = v[u].w - mu;
+        float q = (zx * zx + zy * zy) + (zz * zz + zw * zw);
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        const float rs = 1.0f / sqrtf(q / float(d) + 1e-5f);
+        if (row < rows) {
+            reinterpret_cast<float4 *>(y + row * d)[l] =
+                make_float4(zx * rs * gg.x + bb.x, zy * rs * gg.y + bb.y, zz * rs * gg.z + bb.z, zw * rs * gg.w + bb.w);
+            if (l == 0) {
+                if (mean) mean[row] = mu;
+                if (rstd) rstd[row] = rs;
             }
         }
-        sh[threadIdx.x] = s;
+    }
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(256) k_ln_bwd_v(const float *__restrict__ x, const float *__restrict__ mean,
+                                                  const float *__restrict__ rstd, const float *__restrict__ g,
+                                                  const float *__restrict__ dy, float *__restrict__ acc, int64_t rows) {
+    constexpr int RPW = 32 / LPR, d = 4 * LPR;
+    const int lane = threadIdx.x & 31, sub = lane / LPR, l = lane % LPR;
+    const int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (RPW * kLnRows);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 xv[kLnRows], dv[kLnRows], av[kLnRows];
+    float mu[kLnRows], rs[kLnRows];
+#pragma unroll
+    for (int u = 0; u < kLnRows; ++u) {
+        const int64_t row = base + u * RPW + sub;
+        const bool ok = row < rows;
+        xv[u] = ok ? __ldg(reinterpret_cast<const float4 *>(x + row * d) + l) : z4;
+        dv[u] = ok ? __ldg(reinterpret_cast<const float4 *>(dy + row * d) + l) : z4;
+        av[u] = ok ? reinterpret_cast<const float4 *>(acc + row * d)[l] : z4;
+        mu[u] = ok ? mean[row] : 0.f;
+        rs[u] = ok ? rstd[row] : 0.f;
+    }
+    const float4 gg = __ldg(reinterpret_cast<const float4 *>(g) + l);
+#pragma unroll
+    for (int u = 0; u < kLnRows; ++u) {
+        const int64_t row = base + u * RPW + sub;
+        const float hx = (xv[u].x - mu[u]) * rs[u], hy = (xv[u].y - mu[u]) * rs[u];
+        const float hz = (xv[u].z - mu[u]) * rs[u], hw = (xv[u].w - mu[u]) * rs[u];
+        const float ex = dv[u].x * gg.x, ey = dv[u].y * gg.y, ez = dv[u].z * gg.z, ew = dv[u].w * gg.w;
+        float s1 = (ex + ey) + (ez + ew);
+        float s2 = (ex * hx + ey * hy) + (ez * hz + ew * hw);
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        s1 /= float(d);
+        s2 /= float(d);
+        if (row < rows) {
+            const float r = rs[u];
+            reinterpret_cast<float4 *>(acc + row * d)[l] =
+                make_float4(av[u].x + r * (ex - s1 - hx * s2), av[u].y + r * (ey - s1 - hy * s2),
+                            av[u].z + r * (ez - s1 - hz * s2), av[u].w + r * (ew - s1 - hw * s2));
+        }
+    }
+}
+
+inline bool al16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+template <class R>
+bool ln_vec_ok(int d) {
+    return sizeof(R) == 4 && d % 4 == 0 && d >= 4 && d <= 128 && ((d / 4) & (d / 4 - 1)) == 0;
+}
+
+template <int LPR>
+unsigned ln_blocks(int64_t rows) {
+    const int64_t per_block = 8 * (32 / LPR) * kLnRows;  // 8 warps
+    return (unsigned)((rows + per_block - 1) / per_block);
+}
+
+// y = LayerNorm(x) g + b over rows of d; mean/rstd per row if non-null
+template <class R>
+nnqs_status ln_fwd(cudaStream_t s, const R *x, const R *g, const R *b, R *y, R *mean, R *rstd, int64_t rows, int d) {
+    if (rows == 0) return NNQS_OK;
+    if constexpr (sizeof(R) == 4) {
+        if (ln_vec_ok<R>(d) && al16(x) && al16(g) && al16(b) && al16(y)) {
+            const float *xf = x, *gf = g, *bf = b;
+#define NNQS_LNF(LPR) NNQS_LAUNCH("k_ln_fwd", s, (k_ln_fwd_v<LPR><<<ln_blocks<LPR>(rows), 256, 0, s>>>(xf, gf, bf, y, mean, rstd, rows)))
+            switch (d / 4) {
+                case 1: NNQS_LNF(1); break;
+                case 2: NNQS_LNF(2); break;
+                case 4: NNQS_LNF(4); break;
+                case 8: NNQS_LNF(8); break;
+                case 16: NNQS_LNF(16); break;
+                default: NNQS_LNF(32); break;
+            }
+#undef NNQS_LNF
+            return NNQS_OK;
+        }
+    }
+    NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(x, g, b, y, mean, rstd, rows, d));
+    return NNQS_OK;
+}
+
+// acc += dx of LayerNorm for the output gradient dy
+template <class R>
+nnqs_status ln_bwd(cudaStream_t s, const R *x, const R *mean, const R *rstd, const R *g, const R *dy, R *acc,
+                   int64_t rows, int d) {
+    if (rows == 0) return NNQS_OK;
+    if constexpr (sizeof(R) == 4) {
+        if (ln_vec_ok<R>(d) && al16(x) && al16(g) && al16(dy) && al16(acc)) {
+#define NNQS_LNB(LPR) NNQS_LAUNCH("k_ln_bwd", s, (k_ln_bwd_v<LPR><<<ln_blocks<LPR>(rows), 256, 0, s>>>(x, mean, rstd, g, dy, acc, rows)))
+            switch (d / 4) {
+                case 1: NNQS_LNB(1); break;
+                case 2: NNQS_LNB(2); break;
+                case 4: NNQS_LNB(4); break;
+                case 8: NNQS_LNB(8); break;
+                case 16: NNQS_LNB(16); break;
+                default: NNQS_LNB(32); break;
+            }
+#undef NNQS_LNB
+            return NNQS_OK;
+        }
+    }
+    NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(x, mean, rstd, g, dy, acc, rows, d));
+    return NNQS_OK;
+}
+
+// ------------------------------------------------------------------ column reductions
+// Bias and LayerNorm-parameter gradients are column sums over all rows of a
+// [rows][cols] activation gradient.  k_colred: each block sums a contiguous
+// range of rows (16-byte vector loads, eight rows in flight per thread), the
+// row phases of a block are added in a fixed order into partial[blk][.], and
+// the last block to finish (counter in global memory, reset by that block)
+// adds the partial rows in a fixed order into out[.] (+=).  The result is
+// independent of the scheduling order.  Modes:
+//   0: out0[c] += sum_r A[r][c]                                  (bias)
+//   1: out0[c] += sum_r A[r][c] xh(r, c), out1[c] += sum_r A[r][c]  (LayerNorm
+//      gain and bias; xh = (X - mean) rstd)
+constexpr int kColThreads = 256;
+constexpr int kColUnroll = 8;
+
+template <class R, int VW>
+struct ColVec {
+    R v[VW];
+};
+
+template <class R, int VW>
+__device__ __forceinline__ ColVec<R, VW> ld_vec(const R *p) {
+    ColVec<R, VW> r;
+    if constexpr (VW * sizeof(R) == 16) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+        memcpy(&r, &u, 16);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) r.v[e] = p[e];
+    }
+    return r;
+}
+
+// as ld_vec through L2 only (data written by other blocks of this launch)
+template <class R, int VW>
+__device__ __forceinline__ ColVec<R, VW> ld_vec_cg(const R *p) {
+    ColVec<R, VW> r;
+    if constexpr (VW * sizeof(R) == 16) {
+        const uint4 u = __ldcg(reinterpret_cast<const uint4 *>(p));
+        memcpy(&r, &u, 16);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) r.v[e] = __ldcg(p + e);
+    }
+    return r;
+}
+
+// out[c] += sum_b partial[b * ld + c] for c_lo <= c < c_hi (one block).  A lane takes
+// VW consecutive columns, a warp a tile of 32 VW columns; the warps split the
+// column tiles and, when there are fewer tiles than warps, the rows b (split
+// q takes b = q, q + rs, ...), and the splits are added in order.  Eight rows
+// are loaded before they are added.
+template <class R, int VW>
+__device__ void sum_partial_rows(const R *partial, int64_t nblk, int64_t ld, int c_lo, int c_hi, R *out, R *sh) {
+    constexpr int NW = kColThreads / 32, TC = 32 * VW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_ct = (c_hi - c_lo + TC - 1) / TC;
+    const int rs = max(1, NW / n_ct);
+    const int tpar = NW / rs;
+    for (int t0 = 0; t0 < n_ct; t0 += tpar) {
+        const int ti = warp / rs, q = warp % rs, tile = t0 + ti;
+        const int c = c_lo + tile * TC + lane * VW;
+        R acc[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e] = 0;
+        if (ti < tpar && tile < n_ct && c < c_hi) {
+            int64_t b = q;
+            for (; b + 7 * rs < nblk; b += 8 * rs) {
+                ColVec<R, VW> v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = ld_vec_cg<R, VW>(partial + (b + u * rs) * ld + c);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc[e] += v[u].v[e];
+            }
+            for (; b < nblk; b += rs) {
+                const ColVec<R, VW> v = ld_vec_cg<R, VW>(partial + b * ld + c);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[e] += v.v[e];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) sh[warp * TC + lane * VW + e] = acc[e];
         __syncthreads();
-        if (warp == 0) {
-            R t = 0;
-            for (int w = 0; w < kColThreads / 32; ++w) t += sh[w * 32 + lane];
-            if (c < cols) partial[blockIdx.x * (int64_t)cols + c] = t;
+        for (int idx = threadIdx.x; idx < tpar * TC; idx += kColThreads) {
+            const int t2 = idx / TC, cc = idx % TC;
+            const int col = c_lo + (t0 + t2) * TC + cc;
+            if (t0 + t2 < n_ct && col < c_hi) {
+                R t = 0;
+                for (int k = 0; k < rs; ++k) t += sh[(t2 * rs + k) * TC + cc];
+                out[col] += t;
+            }
         }
         __syncthreads();
     }
 }
 
-// out[c] += sum_b partial[b][c]
+template <class R, int MODE, int VW>
+__global__ void __launch_bounds__(kColThreads) k_colred(const R *__restrict__ A, const R *__restrict__ X,
+                                                        const R *__restrict__ mean, const R *__restrict__ rstd,
+                                                        int64_t rows, int cols, int64_t rows_per_block,
+                                                        R *__restrict__ partial, unsigned *counter,
+                                                        R *__restrict__ out0, R *__restrict__ out1) {
+    __shared__ R sh[(MODE ? 2 : 1) * kColThreads * VW];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const int64_t r0 = blockIdx.x * rows_per_block;
+    const int64_t r1 = min(rows, r0 + rows_per_block);
+    const int64_t pcols = (MODE ? 2 : 1) * (int64_t)cols;
+    const int cv = cols / VW;                // vector columns
+    const int ct = min(cv, kColThreads);     // threads per row within a column tile
+    const int phases = kColThreads / ct;     // rows in parallel
+    const int p = tid / ct, j = tid % ct;
+    for (int v0 = 0; v0 < cv; v0 += ct) {
+        const int vc = v0 + j;
+        const bool act = p < phases && vc < cv;
+        R acc[VW], acc2[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e] = acc2[e] = 0;
+        if (act) {
+            int64_t r = r0 + p;
+            for (; r + (kColUnroll - 1) * phases < r1; r += kColUnroll * phases) {
+                ColVec<R, VW> va[kColUnroll], vx[kColUnroll];
+#pragma unroll
+                for (int u = 0; u < kColUnroll; ++u) {
+                    va[u] = ld_vec<R, VW>(A + (r + u * phases) * cols + vc * VW);
+                    if (MODE) vx[u] = ld_vec<R, VW>(X + (r + u * phases) * cols + vc * VW);
+                }
+#pragma unroll
+                for (int u = 0; u < kColUnroll; ++u) {
+                    R mu = 0, rs = 0;
+                    if (MODE) {
+                        mu = mean[r + u * phases];
+                        rs = rstd[r + u * phases];
+                    }
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        if (MODE) acc2[e] += va[u].v[e] * ((vx[u].v[e] - mu) * rs);
+                        acc[e] += va[u].v[e];
+                    }
+                }
+            }
+            for (; r < r1; r += phases) {
+                const ColVec<R, VW> va = ld_vec<R, VW>(A + r * cols + vc * VW);
+                ColVec<R, VW> vx;
+                R mu = 0, rs = 0;
+                if (MODE) {
+                    vx = ld_vec<R, VW>(X + r * cols + vc * VW);
+                    mu = mean[r];
+                    rs = rstd[r];
+                }
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    if (MODE) acc2[e] += va.v[e] * ((vx.v[e] - mu) * rs);
+                    acc[e] += va.v[e];
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            sh[tid * VW + e] = acc[e];
+            if (MODE) sh[(kColThreads + tid) * VW + e] = acc2[e];
+        }
+        __syncthreads();
+        if (p == 0 && vc < cv) {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                R t = 0, t2 = 0;
+                for (int q = 0; q < phases; ++q) {
+                    t += sh[(q * ct + j) * VW + e];
+                    if (MODE) t2 += sh[(kColThreads + q * ct + j) * VW + e];
+                }
+                const int64_t c = (int64_t)vc * VW + e;
+                if (MODE) {
+                    partial[blockIdx.x * pcols + c] = t2;         // gain part
+                    partial[blockIdx.x * pcols + cols + c] = t;   // bias part
+                } else {
+                    partial[blockIdx.x * pcols + c] = t;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // last block: add the partial rows of all blocks, in block order
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum_partial_rows<R, VW>(partial, gridDim.x, pcols, 0, cols, out0, sh);
+    if (MODE) sum_partial_rows<R, VW>(partial + cols, gridDim.x, pcols, 0, cols, out1, sh);
+    if (tid == 0) *counter = 0u;
+}
+
+// out[c] += sum_b partial[b][c]; block x takes columns [32 x, 32 x + 32)
 template <class R>
-__global__ void k_sum_partials(const R *__restrict__ partial, int64_t nblk, int64_t cols, R *__restrict__ out) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    R s = 0;
-    for (int64_t b = 0; b < nblk; ++b) s += partial[b * cols + c];
-    out[c] += s;
+__global__ void __launch_bounds__(kColThreads) k_sum_partials(const R *__restrict__ partial, int64_t nblk,
+                                                              int64_t cols, R *__restrict__ out) {
+    __shared__ R sh[kColThreads];
+    const int64_t c0 = blockIdx.x * 32;
+    sum_partial_rows<R, 1>(partial, nblk, cols, (int)c0, (int)min(cols, c0 + 32), out, sh);
 }
 
 // ------------------------------------------------------------------ GEMM (CUDA cores)
@@ -365,6 +673,7 @@ template <class R>
 struct Scratch {
     R *buf;
     size_t elems;
+    unsigned *ctr;  // column-reduction block counter, zero between launches
 };
 
 template <class R>
@@ -425,18 +734,25 @@ nnqs_status linear_dw(cudaStream_t s, const R *dY, int64_t rows, int64_t out, co
     return gemm<R>(s, EPI_ACCUM, dY, 1, out, X, 1, in, dW, in, nullptr, nullptr, nullptr, out, in, rows, scr);
 }
 
+template <class R>
+nnqs_status act_bwd(cudaStream_t s, int act, R *dX, const R *Z, int64_t n);
+
 // backward GEMMs of the weights that have BF16 copies: tensor cores for
-// NNQS_MIXED (tcw != null, FP32 activations), CUDA cores otherwise
+// NNQS_MIXED (tcw != null, FP32 activations), CUDA cores otherwise.
+// act 1 / 2: dX is then multiplied by GELU'(Z) / ReLU'(Z) (in the tensor-core
+// epilogue, or by a separate pass)
 template <class R>
 nnqs_status bw_dx(cudaStream_t s, const TcWeights *tcw, int slot, const R *dY, int64_t rows, int64_t out, const R *Wt,
-                  int64_t in, R *dX, Scratch<R> scr) {
-    return linear_dx<R>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr);
+                  int64_t in, R *dX, Scratch<R> scr, int act = 0, const R *Z = nullptr) {
+    NNQS_TRY(linear_dx<R>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr));
+    return act_bwd<R>(s, act, dX, Z, rows * in);
 }
 template <>
 nnqs_status bw_dx<float>(cudaStream_t s, const TcWeights *tcw, int slot, const float *dY, int64_t rows, int64_t out,
-                         const float *Wt, int64_t in, float *dX, Scratch<float> scr) {
-    if (tcw) return tc_linear_dx(s, *tcw, slot, dY, rows, dX);
-    return linear_dx<float>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr);
+                         const float *Wt, int64_t in, float *dX, Scratch<float> scr, int act, const float *Z) {
+    if (tcw) return tc_linear_dx(s, *tcw, slot, dY, rows, dX, act, Z);
+    NNQS_TRY(linear_dx<float>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr));
+    return act_bwd<float>(s, act, dX, Z, rows * in);
 }
 template <class R>
 nnqs_status bw_dw(cudaStream_t s, const TcWeights *tcw, const R *dY, int64_t rows, int64_t out, const R *X,
@@ -450,20 +766,30 @@ nnqs_status bw_dw<float>(cudaStream_t s, const TcWeights *tcw, const float *dY, 
     return linear_dw<float>(s, dY, rows, out, X, in, dW, scr);
 }
 
+// column sums of a [rows][cols] gradient into out0 (+=); mode 1 also the
+// LayerNorm gain gradient: out0 += sum A xh, out1 += sum A
 template <class R>
 nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *mean, const R *rstd, int64_t rows,
-                   int cols, R *out, Scratch<R> scr) {
+                   int cols, R *out0, R *out1, Scratch<R> scr) {
     if (rows == 0) return NNQS_OK;
-    int64_t nblk = std::min<int64_t>((rows + 255) / 256, 4 * sm_count());
-    nblk = std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(cols)));
+    constexpr int V = int(16 / sizeof(R));
+    const bool vec = cols % V == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
+                     (mode == 0 || reinterpret_cast<uintptr_t>(X) % 16 == 0);
+    const int64_t pc = (mode ? 2 : 1) * (int64_t)cols;
+    int64_t nblk = std::min<int64_t>((rows + 63) / 64, 2 * sm_count());
+    nblk = std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(pc)));
     nblk = std::max<int64_t>(nblk, 1);
     const int64_t rpb = (rows + nblk - 1) / nblk;
     nblk = (rows + rpb - 1) / rpb;
-    if (mode == 0)
-        NNQS_LAUNCH("k_colred", s, k_colred<R, 0><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf));
+    const unsigned g = (unsigned)nblk;
+    if (mode == 0 && vec)
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 0, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+    else if (mode == 0)
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 0, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+    else if (vec)
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
     else
-        NNQS_LAUNCH("k_colred", s, k_colred<R, 1><<<(unsigned)nblk, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf));
-    NNQS_LAUNCH("k_sum_partials", s, k_sum_partials<R><<<grid_for(cols, 256), 256, 0, s>>>(scr.buf, nblk, cols, out));
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
     return NNQS_OK;
 }
 
@@ -967,6 +1293,14 @@ __global__ void k_act_bwd(R *__restrict__ a, const R *__restrict__ z, int64_t n)
     }
 }
 
+// dX *= GELU'(Z) (act 1) or ReLU'(Z) (act 2)
+template <class R>
+nnqs_status act_bwd(cudaStream_t s, int act, R *dX, const R *Z, int64_t n) {
+    if (act == 1) NNQS_LAUNCH("k_act_bwd", s, (k_act_bwd<R, true><<<grid_for(n, 256), 256, 0, s>>>(dX, Z, n)));
+    if (act == 2) NNQS_LAUNCH("k_act_bwd", s, (k_act_bwd<R, false><<<grid_for(n, 256), 256, 0, s>>>(dX, Z, n)));
+    return NNQS_OK;
+}
+
 // token-embedding gradient: out[v][c] += sum over rows with input id v of dh[row][c]
 template <class R>
 __global__ void k_tok_grad(const R *__restrict__ dh, const uint8_t *__restrict__ tok, int64_t n, int T, int d,
@@ -1032,7 +1366,7 @@ struct Acts {
     R *mean1 = nullptr, *rstd1 = nullptr, *mean2 = nullptr, *rstd2 = nullptr, *lse = nullptr;
     R *hf = nullptr, *meanf = nullptr, *rstdf = nullptr, *pi = nullptr;
     R *z1 = nullptr, *r1 = nullptr, *z2 = nullptr, *r2 = nullptr, *xf = nullptr;
-    Scratch<R> scr{nullptr, 0};
+    Scratch<R> scr{nullptr, 0, nullptr};
 };
 
 template <class R>
@@ -1069,6 +1403,7 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     // split-K partials of weight gradients: ~300 splits of a layer matrix
     A.scr.elems = size_t(std::max<int64_t>({8 * wmax, 4 * 152 * std::max<int64_t>(F, P) * 5, 300 * F * d}));
     A.scr.buf = a.take<R>(A.scr.elems);
+    A.scr.ctr = a.take<unsigned>(64);
 }
 
 constexpr size_t kAttnSmemMax = 200 * 1024;
@@ -1161,7 +1496,7 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
         R *hmid = A.hmid + k * rows * d;
         R *a = A.a + k * rows * d, *a2 = A.a2 + k * rows * d, *qkv = A.qkv + k * rows * 3 * d, *o = A.o + k * rows * d;
         R *u = A.u + k * rows * F, *gu = A.gu + k * rows * F;
-        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, Lw.ln1g, Lw.ln1b, a, A.mean1 + k * rows,
+        NNQS_TRY(ln_fwd<R>(s, hin, Lw.ln1g, Lw.ln1b, a, A.mean1 + k * rows,
                                                              A.rstd1 + k * rows, rows, d));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 0), EPI_STORE, a, rows, d, Lw.bqkv, qkv, nullptr, nullptr));
@@ -1174,7 +1509,7 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
         } else {
             NNQS_TRY(linear_fwd<R>(s, EPI_RESID, o, rows, d, Lw.wo, d, Lw.bo, hmid, nullptr, hin, A.scr));
         }
-        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, Lw.ln2g, Lw.ln2b, a2, A.mean2 + k * rows,
+        NNQS_TRY(ln_fwd<R>(s, hmid, Lw.ln2g, Lw.ln2b, a2, A.mean2 + k * rows,
                                                              A.rstd2 + k * rows, rows, d));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 2), EPI_GELU, a2, rows, d, Lw.b1, u, gu, nullptr));
@@ -1185,7 +1520,7 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
         }
     }
     const R *hlast = A.keep ? A.hbuf + (int64_t)L * rows * d : A.hbuf;
-    NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, V.lnf_g, V.lnf_b, A.hf, A.meanf, A.rstdf, rows, d));
+    NNQS_TRY(ln_fwd<R>(s, hlast, V.lnf_g, V.lnf_b, A.hf, A.meanf, A.rstdf, rows, d));
     if (cond) {
         NNQS_LAUNCH("k_cond_last", s, k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, T, T - 1, Tm, d, M->cfg.n_alpha, M->cfg.n_beta, cond, st));
         return NNQS_OK;
@@ -1237,25 +1572,23 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     NNQS_LAUNCH("k_seed_cols", s, k_seed_cols<R><<<grid_for(C, 256), 256, 0, s>>>(seed, C, G.dph));
     // dW3[0][u] += sum_i dph_i r2[i][u]; db3 += sum_i dph_i
     NNQS_TRY(linear_dw<R>(s, G.dph, C, 1, A.r2, P, gacc + Lo.ph_w3, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dph, nullptr, nullptr, nullptr, C, 1, gacc + Lo.ph_b3, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dph, nullptr, nullptr, nullptr, C, 1, gacc + Lo.ph_b3, nullptr, scr));
     NNQS_LAUNCH("k_phase_dz2", s, k_phase_dz2<R><<<grid_for(C * P, 256), 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, G.dz2));
     NNQS_TRY(bw_dw<R>(s, tcw, G.dz2, C, P, A.r1, P, gacc + Lo.ph_w2, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dz2, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b2, scr));
-    NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(L, 0), G.dz2, C, P, V.w2p, P, G.dz1, scr));
-    NNQS_LAUNCH("k_act_bwd", s, k_act_bwd<R, false><<<grid_for(C * P, 256), 256, 0, s>>>(G.dz1, A.z1, C * P));
+    NNQS_TRY(colsum<R>(s, 0, G.dz2, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b2, nullptr, scr));
+    NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(L, 0), G.dz2, C, P, V.w2p, P, G.dz1, scr, 2, A.z1));
     NNQS_TRY(linear_dw<R>(s, G.dz1, C, P, A.xf, N, gacc + Lo.ph_w1, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, nullptr, scr));
     // ---- head
     NNQS_LAUNCH("k_head_bwd", s, k_head_bwd<R><<<grid_for(rows * 4, 256), 256, 0, s>>>(A.pi, A.tok, seed, C, T, G.dz));
     NNQS_TRY(linear_dw<R>(s, G.dz, rows, 4, A.hf, d, gacc + Lo.head_w, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dz, nullptr, nullptr, nullptr, rows, 4, gacc + Lo.head_b, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dz, nullptr, nullptr, nullptr, rows, 4, gacc + Lo.head_b, nullptr, scr));
     NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz, rows, 4, V.hw, d, G.dtmp, scr));
     // final LayerNorm
     const R *hlast = A.hbuf + (int64_t)L * rows * d;
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0)));
-    NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d));
-    NNQS_TRY(colsum<R>(s, 1, G.dtmp, hlast, A.meanf, A.rstdf, rows, d, gacc + Lo.lnf_g, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lo.lnf_b, scr));
+    NNQS_TRY(ln_bwd<R>(s, hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d));
+    NNQS_TRY(colsum<R>(s, 1, G.dtmp, hlast, A.meanf, A.rstdf, rows, d, gacc + Lo.lnf_g, gacc + Lo.lnf_b, scr));
     for (int l = L - 1; l >= 0; --l) {
         const auto &Lw = V.layer[l];
         const auto &Lg = Lo.layer[l];
@@ -1266,38 +1599,35 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         const R *u = A.u + (int64_t)l * rows * F, *gu = A.gu + (int64_t)l * rows * F;
         // FFN: hout = hmid + gelu(a2 W1^T + b1) W2^T + b2
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.b2, scr));
-        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr));
-        NNQS_LAUNCH("k_act_bwd", s, k_act_bwd<R, true><<<grid_for(rows * F, 256), 256, 0, s>>>(G.du, u, rows * F));
+        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.b2, nullptr, scr));
+        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr, 1, u));
         NNQS_TRY(bw_dw<R>(s, tcw, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 2), G.du, rows, F, Lw.w1, d, G.dtmp, scr));
-        NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
+        NNQS_TRY(ln_bwd<R>(s, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
                                                              G.dtmp, G.dh, rows, d));
-        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, rows, d, gacc + Lg.ln2_g, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln2_b, scr));
+        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, rows, d, gacc + Lg.ln2_g, gacc + Lg.ln2_b, scr));
         // attention: hmid = hin + attn(a) Wo^T + bo
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.bo, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.bo, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 1), G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
         NNQS_TRY(attn_bwd<R>(s, M->dh, qkv, o, A.lse + (int64_t)l * C * H * T, G.dtmp, G.dqkv, G.Dbuf, C, T, H, d));
         NNQS_TRY(bw_dw<R>(s, tcw, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, scr));
+        NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 0), G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
-        NNQS_LAUNCH("k_ln_bwd", s, k_ln_bwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
+        NNQS_TRY(ln_bwd<R>(s, hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
                                                              G.dtmp, G.dh, rows, d));
-        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hin, A.mean1 + l * rows, A.rstd1 + l * rows, rows, d, gacc + Lg.ln1_g, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dtmp, nullptr, nullptr, nullptr, rows, d, gacc + Lg.ln1_b, scr));
+        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hin, A.mean1 + l * rows, A.rstd1 + l * rows, rows, d, gacc + Lg.ln1_g, gacc + Lg.ln1_b, scr));
     }
     // embeddings: pos[t][c] += sum_i dh[i][t][c]; tok[v][c] += sum over inputs v
-    NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, C, T * d, gacc + Lo.pos_emb, scr));
+    NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, C, T * d, gacc + Lo.pos_emb, nullptr, scr));
     {
         int64_t nblk = std::min<int64_t>((rows + 63) / 64, 2 * sm_count());
         nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(5 * d))));
         const int64_t rpb = (rows + nblk - 1) / nblk;
         nblk = (rows + rpb - 1) / rpb;
         NNQS_LAUNCH("k_tok_grad", s, k_tok_grad<R><<<(unsigned)nblk, 128, 0, s>>>(G.dh, A.tok, C, T, d, rpb, scr.buf));
-        NNQS_LAUNCH("k_sum_partials", s, k_sum_partials<R><<<grid_for(5 * d, 256), 256, 0, s>>>(scr.buf, nblk, 5 * d, gacc + Lo.tok_emb));
+        NNQS_LAUNCH("k_sum_partials", s, k_sum_partials<R><<<(unsigned)((5 * d + 31) / 32), kColThreads, 0, s>>>(scr.buf, nblk, 5 * d, gacc + Lo.tok_emb));
     }
     return NNQS_OK;
 }
@@ -1314,7 +1644,7 @@ __global__ void k_grad_out(const R *__restrict__ g, int64_t n, double *__restric
 int64_t chunk_for(const nnqs_model *M, int64_t n, size_t rbytes, bool backward) {
     const int64_t per = (int64_t)rbytes * M->T * M->d * (backward ? (16 * M->L + 12) : 12) +
                         (int64_t)rbytes * 5 * M->P;
-    const int64_t budget = backward ? (int64_t(6) << 30) : (int64_t(3) << 30);
+    const int64_t budget = backward ? (int64_t(16) << 30) : (int64_t(3) << 30);
     int64_t c = std::max<int64_t>(256, budget / std::max<int64_t>(per, 1));
     c = std::min<int64_t>(c, 32768);
     return std::max<int64_t>(1, std::min(c, n));
@@ -1339,11 +1669,13 @@ size_t workspace_impl(const nnqs_model *M, int64_t n, bool backward, bool tensor
 
 template <class R>
 nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, double *out, Arena &ws,
-                         DevStatus *st, bool tensor, cudaStream_t s) {
+                         DevStatus *st, int tcm, cudaStream_t s) {
+    const bool tensor = tcm != 0;
     R *pr = ws.take<R>(M->lay.total);
     TcWeights tcw{};
     if (tensor) tc_weights_take(M, ws, &tcw);
     tcw.st = st;
+    tcw.split = tcm == 2;
     const int64_t C = chunk_for(M, n, sizeof(R), false);
     Acts<R> A;
     take_acts<R>(M, C, false, ws, A);
@@ -1360,17 +1692,20 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
 
 template <class R>
 nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, const double *seed,
-                          double *g64, float *g32, Arena &ws, DevStatus *st, bool tensor, cudaStream_t s) {
+                          double *g64, float *g32, Arena &ws, DevStatus *st, int tcm, cudaStream_t s) {
+    const bool tensor = tcm != 0;
     R *pr = ws.take<R>(M->lay.total);
     R *gacc = ws.take<R>(M->lay.total);
     TcWeights tcw{};
     if (tensor) tc_weights_take(M, ws, &tcw);
     tcw.st = st;
+    tcw.split = tcm == 2;
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
     Acts<R> A;
     take_acts<R>(M, C, true, ws, A);
     Grads<R> G;
     take_grads<R>(M, C, ws, G);
+    NNQS_CUDA_TRY(cudaMemsetAsync(A.scr.ctr, 0, sizeof(unsigned), s));
     NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
     if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
@@ -1383,6 +1718,38 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
         NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc,
                                    tensor ? &tcw : nullptr, s));
     }
+    NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
+    return NNQS_OK;
+}
+
+// forward with the activations kept, then `between` (which fills `seed`),
+// then the reverse mode on those activations: one forward instead of two
+template <class R>
+nnqs_status fwd_bwd_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, double *lp_out,
+                         const double *seed, double *g64, float *g32, Arena &ws, DevStatus *st, int tcm,
+                         cudaStream_t s, const std::function<nnqs_status()> &between) {
+    const bool tensor = tcm != 0;
+    R *pr = ws.take<R>(M->lay.total);
+    R *gacc = ws.take<R>(M->lay.total);
+    TcWeights tcw{};
+    if (tensor) tc_weights_take(M, ws, &tcw);
+    tcw.st = st;
+    tcw.split = tcm == 2;
+    const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
+    if (C < n) return set_error(NNQS_E_INVAL, "fused forward/backward needs one chunk");
+    Acts<R> A;
+    take_acts<R>(M, C, true, ws, A);
+    Grads<R> G;
+    take_grads<R>(M, C, ws, G);
+    NNQS_CUDA_TRY(cudaMemsetAsync(A.scr.ctr, 0, sizeof(unsigned), s));
+    NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
+    NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
+    if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
+    const Views<R> V = make_views<R>(M, pr);
+    NNQS_TRY(forward_chunk<R>(M, V, x, n, A, reinterpret_cast<double2 *>(lp_out), st, 0, tensor ? &tcw : nullptr, s));
+    NNQS_TRY(between());
+    NNQS_TRY(backward_chunk<R>(M, V, x, n, A, G, reinterpret_cast<const double2 *>(seed), gacc,
+                               tensor ? &tcw : nullptr, s));
     NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
     return NNQS_OK;
 }
@@ -1436,7 +1803,7 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
     for (int l = 0; l < L; ++l) {
         const auto &Lw = V.layer[l];
         R *qkv = pool + (g0 * L + l) * 3 * (int64_t)d;
-        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(h, Lw.ln1g, Lw.ln1b, A.a, nullptr, nullptr, rows, d));
+        NNQS_TRY(ln_fwd<R>(s, h, Lw.ln1g, Lw.ln1b, A.a, nullptr, nullptr, rows, d));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd_ld<R>(s, *tcw, tc_slot(l, 0), EPI_STORE, A.a, rows, d, Lw.bqkv, qkv, (int64_t)L * 3 * d,
                                          nullptr, nullptr));
@@ -1450,7 +1817,7 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
         } else {
             NNQS_TRY(linear_fwd<R>(s, EPI_RESID, A.o, rows, d, Lw.wo, d, Lw.bo, h, nullptr, h, A.scr));
         }
-        NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(h, Lw.ln2g, Lw.ln2b, A.a2, nullptr, nullptr, rows, d));
+        NNQS_TRY(ln_fwd<R>(s, h, Lw.ln2g, Lw.ln2b, A.a2, nullptr, nullptr, rows, d));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 2), EPI_GELU, A.a2, rows, d, Lw.b1, A.u, A.gu, nullptr));
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 3), EPI_RESID, A.gu, rows, F, Lw.b2, h, nullptr, h));
@@ -1459,7 +1826,7 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
             NNQS_TRY(linear_fwd<R>(s, EPI_RESID, A.gu, rows, F, Lw.w2, d, Lw.b2, h, nullptr, h, A.scr));
         }
     }
-    NNQS_LAUNCH("k_ln_fwd", s, k_ln_fwd<R><<<grid_for(rows * 32, 256), 256, 0, s>>>(h, V.lnf_g, V.lnf_b, A.hf, nullptr, nullptr, rows, d));
+    NNQS_TRY(ln_fwd<R>(s, h, V.lnf_g, V.lnf_b, A.hf, nullptr, nullptr, rows, d));
     NNQS_LAUNCH("k_cond_last", s, k_cond_last<R><<<grid_for(C, 128), 128, 0, s>>>(x, W, A.hf, V.hw, V.hb, C, 1, t, T, d,
                                                                              M->cfg.n_alpha, M->cfg.n_beta, cond, st));
     return NNQS_OK;
@@ -1479,7 +1846,7 @@ struct CondCtx {
 
 size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec, int64_t kv_nodes) {
     if (prec == NNQS_FP64) return cond_workspace_impl<double>(M, max_prefixes, false, kv_nodes);
-    return cond_workspace_impl<float>(M, max_prefixes, prec == NNQS_MIXED, kv_nodes);
+    return cond_workspace_impl<float>(M, max_prefixes, tc_mode(prec) != 0, kv_nodes);
 }
 
 nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int64_t max_prefixes, int64_t kv_nodes,
@@ -1488,7 +1855,7 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
     if (!c) return set_error(NNQS_E_NOMEM, "host allocation failed");
     *out = c;
     c->prec = prec;
-    c->tensor = prec == NNQS_MIXED;
+    c->tensor = tc_mode(prec) != 0;
     c->pool_nodes = kv_nodes;
     if (prec == NNQS_FP64) {
         double *pr = ws.take<double>(M->lay.total);
@@ -1502,6 +1869,7 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
         c->pool = ws.take<float>(size_t(kv_nodes) * M->L * 3 * M->d);
         c->params = pr;
         if (c->tensor) tc_weights_take(M, ws, &c->tcw);
+        c->tcw.split = tc_mode(prec) == 2;
         c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(float), false);
         take_acts<float>(M, c->C, false, ws, c->Af);
         NNQS_LAUNCH("k_convert_params", s, k_convert_params<float><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
@@ -1553,19 +1921,31 @@ nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixe
 
 size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward) {
     if (prec == NNQS_FP64) return workspace_impl<double>(M, n, backward, false);
-    return workspace_impl<float>(M, n, backward, prec == NNQS_MIXED);
+    return workspace_impl<float>(M, n, backward, tc_mode(prec) != 0);
 }
 
 nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
                            double *out, Arena &ws, DevStatus *st, cudaStream_t s) {
-    if (prec == NNQS_FP64) return forward_impl<double>(M, params, x, n, out, ws, st, false, s);
-    return forward_impl<float>(M, params, x, n, out, ws, st, prec == NNQS_MIXED, s);
+    if (prec == NNQS_FP64) return forward_impl<double>(M, params, x, n, out, ws, st, 0, s);
+    return forward_impl<float>(M, params, x, n, out, ws, st, tc_mode(prec), s);
 }
 
 nnqs_status logpsi_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
                             const double *seed, double *g64, float *g32, Arena &ws, DevStatus *st, cudaStream_t s) {
-    if (prec == NNQS_FP64) return backward_impl<double>(M, params, x, n, seed, g64, g32, ws, st, false, s);
-    return backward_impl<float>(M, params, x, n, seed, g64, g32, ws, st, prec == NNQS_MIXED, s);
+    if (prec == NNQS_FP64) return backward_impl<double>(M, params, x, n, seed, g64, g32, ws, st, 0, s);
+    return backward_impl<float>(M, params, x, n, seed, g64, g32, ws, st, tc_mode(prec), s);
+}
+
+bool logpsi_single_chunk(const nnqs_model *M, int64_t n, int prec) {
+    return chunk_for(M, std::max<int64_t>(n, 1), prec == NNQS_FP64 ? sizeof(double) : sizeof(float), true) >= n;
+}
+
+nnqs_status logpsi_forward_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
+                                    double *lp_out, const double *seed, double *g64, float *g32, Arena &ws,
+                                    DevStatus *st, cudaStream_t s, const std::function<nnqs_status()> &between) {
+    if (prec == NNQS_FP64)
+        return fwd_bwd_impl<double>(M, params, x, n, lp_out, seed, g64, g32, ws, st, 0, s, between);
+    return fwd_bwd_impl<float>(M, params, x, n, lp_out, seed, g64, g32, ws, st, tc_mode(prec), s, between);
 }
 
 }  // namespace nnqs

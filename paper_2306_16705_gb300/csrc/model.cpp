@@ -61,7 +61,7 @@ static nnqs_status check_ws2(void *ws, size_t have, size_t need) {
     return NNQS_OK;
 }
 
-static bool prec_ok(int p) { return p == NNQS_FP64 || p == NNQS_MIXED || p == NNQS_FP32; }
+static bool prec_ok(int p) { return prec_valid(p); }
 
 extern "C" {
 

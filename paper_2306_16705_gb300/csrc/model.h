@@ -1,6 +1,7 @@
 // Ansatz handle: configuration and the flat FP32 parameter layout of
 // include/nnqs.h.
 #pragma once
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -33,6 +34,10 @@ namespace nnqs {
 
 ParamLayout make_layout(const nnqs_model_cfg &c);
 
+inline bool prec_valid(int p) { return p == NNQS_FP64 || p == NNQS_MIXED || p == NNQS_FP32 || p == NNQS_BF16X3; }
+// tensor-core use of a precision: 0 none, 1 BF16 operands, 2 split BF16 operands in the forward layers
+inline int tc_mode(int p) { return p == NNQS_MIXED ? 1 : p == NNQS_BF16X3 ? 2 : 0; }
+
 // ansatz.cu
 size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward);
 nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
@@ -40,6 +45,14 @@ nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint6
 nnqs_status logpsi_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
                             const double *seed, double *grad64, float *grad32, Arena &ws, DevStatus *st,
                             cudaStream_t s);
+// true when n samples fit in one backward chunk (then the fused form below applies)
+bool logpsi_single_chunk(const nnqs_model *M, int64_t n, int prec);
+// log psi of n samples (activations kept) -> between() -> reverse mode with the
+// seeds `between` wrote, without a second forward; n must fit in one chunk.
+// Workspace: logpsi_workspace(M, n, prec, true).
+nnqs_status logpsi_forward_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
+                                    double *lp_out, const double *seed, double *grad64, float *grad32, Arena &ws,
+                                    DevStatus *st, cudaStream_t s, const std::function<nnqs_status()> &between);
 
 // conditionals pi~(. | prefix) for the sampler (ansatz.cu)
 struct CondCtx;

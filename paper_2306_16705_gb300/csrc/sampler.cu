@@ -309,7 +309,7 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
                                    size_t workspace_bytes, nnqs_stream stream) {
     if (!M || !params || !samples_out || !weights_out || !n_unique_out || max_unique < 1)
         return set_error(NNQS_E_INVAL, "null argument or max_unique < 1");
-    if (prec != NNQS_FP64 && prec != NNQS_FP32 && prec != NNQS_MIXED) return set_error(NNQS_E_INVAL, "bad precision");
+    if (!prec_valid(prec)) return set_error(NNQS_E_INVAL, "bad precision");
     if (flags & ~NNQS_SAMPLE_RECOMPUTE) return set_error(NNQS_E_INVAL, "unknown sampler flags");
     if (n_samples > (uint64_t(1) << 53)) return set_error(NNQS_E_INVAL, "n_samples above 2^53");
     *n_unique_out = 0;

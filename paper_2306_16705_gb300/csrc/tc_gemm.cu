@@ -1,6 +1,6 @@
-// Host side of the tcgen05 linear layers used by NNQS_MIXED: BF16 copies of
-// the weight matrices (K padded to 64 with zeros) and the launch of
-// tc::k_tc_gemm.
+// Host side of the tcgen05 linear layers used by NNQS_MIXED and NNQS_BF16X3:
+// BF16 copies of the weight matrices (K padded to 64 with zeros) and their
+// low parts, and the launch of tc::k_tc_gemm.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -13,12 +13,16 @@
 namespace nnqs {
 namespace {
 
+// dst = bf16(W) padded; dst_lo = bf16(W - bf16(W))
 __global__ void k_to_bf16_padded(const float *__restrict__ src, int64_t N, int64_t K, int64_t Kpad,
-                                 __nv_bfloat16 *__restrict__ dst) {
+                                 __nv_bfloat16 *__restrict__ dst, __nv_bfloat16 *__restrict__ dst_lo) {
     const int64_t total = N * Kpad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = i / Kpad, k = i % Kpad;
-        dst[i] = __float2bfloat16_rn(k < K ? src[n * K + k] : 0.f);
+        const float v = k < K ? src[n * K + k] : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        dst[i] = hi;
+        dst_lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
 }
 
@@ -62,17 +66,18 @@ void slot_shapes(const nnqs_model *M, int slot, int64_t &N, int64_t &K, int64_t 
     }
 }
 
-bool g_attr_set[2][4] = {};
+bool g_attr_set[2][2][tc::kNumEpi] = {};
 
-template <int EPI, bool TRANS = false>
+template <int EPI, bool TRANS = false, bool SPLIT = false>
 nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s, int64_t splits = 1) {
-    if (!g_attr_set[TRANS][EPI]) {
-        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           tc::kSmemBytes));
-        g_attr_set[TRANS][EPI] = true;
+    constexpr int smem = SPLIT ? tc::kSmemBytesSplit : tc::kSmemBytes;
+    if (!g_attr_set[TRANS][SPLIT][EPI]) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI, TRANS, SPLIT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        g_attr_set[TRANS][SPLIT][EPI] = true;
     }
     dim3 grid((unsigned)n_tiles_n, (unsigned)((g.M + tc::kTileM - 1) / tc::kTileM), (unsigned)splits);
-    NNQS_LAUNCH("k_tc_gemm", s, (tc::k_tc_gemm<EPI, TRANS><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(g)));
+    NNQS_LAUNCH("k_tc_gemm", s, (tc::k_tc_gemm<EPI, TRANS, SPLIT><<<grid, tc::kThreads, smem, s>>>(g)));
     return NNQS_OK;
 }
 
@@ -113,6 +118,7 @@ void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
         total += K * kpad_of(N);
     }
     t.bf16 = a.take<__nv_bfloat16>(size_t(total));
+    t.bf16_lo = a.take<__nv_bfloat16>(size_t(total));
 }
 
 nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeights &w, cudaStream_t s) {
@@ -120,9 +126,10 @@ nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeigh
         if (sl / 4 == M->L && sl % 4 != 0) continue;
         const int64_t N = w.rows[sl], K = w.cols[sl], Kp = w.pcols[sl];
         __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(w.bf16) + w.off[sl];
+        __nv_bfloat16 *dst_lo = static_cast<__nv_bfloat16 *>(w.bf16_lo) + w.off[sl];
         NNQS_LAUNCH("k_to_bf16", s,
                     k_to_bf16_padded<<<(unsigned)std::min<int64_t>((N * Kp + 255) / 256, 4096), 256, 0, s>>>(
-                        params + w.src[sl], N, K, Kp, dst));
+                        params + w.src[sl], N, K, Kp, dst, dst_lo));
         const int64_t Np = w.tpcols[sl];
         __nv_bfloat16 *tdst = static_cast<__nv_bfloat16 *>(w.bf16) + w.toff[sl];
         NNQS_LAUNCH("k_to_bf16", s,
@@ -132,8 +139,10 @@ nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeigh
     return NNQS_OK;
 }
 
-nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX) {
+nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX,
+                         int act, const float *Z) {
     if (rows == 0) return NNQS_OK;
+    if (act != 0 && Z == nullptr) return set_error(NNQS_E_INVAL, "tensor-core input gradient: pre-activation missing");
     tc::Args g{};
     const int64_t out = w.rows[slot], in = w.cols[slot];
     g.X = dY;
@@ -149,9 +158,13 @@ nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const flo
     g.vec_x = (out % 4 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
+    g.resid = Z;
     note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
-              4.0 * double(rows) * out + 2.0 * double(in) * g.Kpad + 4.0 * double(rows) * in);
-    return launch<tc::EPI_STORE>(g, (g.N + g.Nt - 1) / g.Nt, s);
+              4.0 * double(rows) * out + 2.0 * double(in) * g.Kpad + (act ? 8.0 : 4.0) * double(rows) * in);
+    const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
+    if (act == 1) return launch<tc::EPI_DGELU>(g, ntn, s);
+    if (act == 2) return launch<tc::EPI_DRELU>(g, ntn, s);
+    return launch<tc::EPI_STORE>(g, ntn, s);
 }
 
 nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t out, const float *X, int64_t in,
@@ -200,6 +213,7 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     g.X = X;
     g.ldx = in;
     g.Wt = static_cast<const __nv_bfloat16 *>(w.bf16) + w.off[slot];
+    g.Wt2 = static_cast<const __nv_bfloat16 *>(w.bf16_lo) + w.off[slot];
     g.Kpad = w.pcols[slot];
     g.bias = bias;
     g.resid = resid;
@@ -214,8 +228,21 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
-    note_work("k_tc_gemm", 2.0 * double(rows) * double(g.N) * double(in),
-              4.0 * double(rows) * in + 2.0 * double(g.N) * g.Kpad + 4.0 * double(rows) * g.N);
+    // algorithmic bytes: X in, the BF16 weights (and their low parts), Y out,
+    // plus the activation output or the residual read
+    const bool two = epi == tc::EPI_GELU || epi == tc::EPI_RELU || epi == tc::EPI_RESID;
+    note_work("k_tc_gemm", (w.split ? 6.0 : 2.0) * double(rows) * double(g.N) * double(in),
+              4.0 * double(rows) * in + (w.split ? 4.0 : 2.0) * double(g.N) * g.Kpad +
+                  (two ? 8.0 : 4.0) * double(rows) * g.N);
+    if (w.split) {
+        switch (epi) {
+            case tc::EPI_STORE: return launch<tc::EPI_STORE, false, true>(g, ntn, s);
+            case tc::EPI_GELU: return launch<tc::EPI_GELU, false, true>(g, ntn, s);
+            case tc::EPI_RELU: return launch<tc::EPI_RELU, false, true>(g, ntn, s);
+            case tc::EPI_RESID: return launch<tc::EPI_RESID, false, true>(g, ntn, s);
+            default: return set_error(NNQS_E_INVAL, "tensor-core layer: bad epilogue");
+        }
+    }
     switch (epi) {
         case tc::EPI_STORE: return launch<tc::EPI_STORE>(g, ntn, s);
         case tc::EPI_GELU: return launch<tc::EPI_GELU>(g, ntn, s);

@@ -30,8 +30,13 @@ constexpr int kABytes = kTileM * kChunkK * 2;    // 16 KB
 constexpr int kMaxN = 128;                       // N per CTA: TMEM 128 columns, 4 CTAs per SM
 constexpr int kBBytes = kMaxN * kChunkK * 2;     // 32 KB
 constexpr int kSmemBytes = kABytes + kBBytes + 1024 + 64;
+// split operands: high and low BF16 parts of A and B
+constexpr int kSmemBytesSplit = 2 * (kABytes + kBBytes) + 1024 + 64;
 
-enum { EPI_STORE = 0, EPI_GELU = 1, EPI_RELU = 2, EPI_RESID = 3 };
+// EPI_DGELU / EPI_DRELU (input gradients): Y = acc * act'(Z) with the
+// pre-activation Z passed as `resid`
+enum { EPI_STORE = 0, EPI_GELU = 1, EPI_RELU = 2, EPI_RESID = 3, EPI_DGELU = 4, EPI_DRELU = 5 };
+constexpr int kNumEpi = 6;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -105,6 +110,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// d gelu / dx = Phi(x) + x phi(x)
+__device__ __forceinline__ float gelu_grad_f(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143267794f;
+}
 
 __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
     uint32_t p[4];
@@ -120,9 +129,10 @@ struct Args {
     const float *X;        // [M][ldx], K valid columns
     int64_t ldx;
     const __nv_bfloat16 *Wt;  // [Npad][Kpad] BF16, zero padded
+    const __nv_bfloat16 *Wt2; // SPLIT: low parts W - bf16(W), same layout
     int64_t Kpad;
     const float *bias;     // [N] or null
-    const float *resid;    // EPI_RESID: [M][ldy]
+    const float *resid;    // EPI_RESID: [M][ldy] added; EPI_DGELU/DRELU: pre-activation [M][ldy]
     float *Y;              // [M][ldy]
     float *Y2;             // activation output for GELU/RELU
     int64_t ldy;
@@ -140,16 +150,24 @@ struct Args {
 // TRANS = true : Y = A^T B over a long K (weight gradients): A(m,k) =
 //   X[k*ldx + m], B(n,k) = Xb[k*ldb + n], both FP32 and staged transposed;
 //   blockIdx.z takes rows [z*kchunk, (z+1)*kchunk) of the reduction.
-template <int EPI, bool TRANS>
-__global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
+// SPLIT (TRANS = false only): X = Xh + Xl and W = Wh + Wl with BF16 parts
+//   (Xh = bf16(X), Xl = bf16(X - Xh)) and Y = Xh Wh + Xh Wl + Xl Wh: three
+//   MMAs per K step, operands good to about 16 bits instead of 8, the same
+//   global traffic.  Three CTAs per SM (64 KB of operand buffers each).
+template <int EPI, bool TRANS, bool SPLIT = false>
+__global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
+    static_assert(!(TRANS && SPLIT), "split operands are for the forward layers only");
+    constexpr int kOps = (SPLIT ? 2 : 1) * (kABytes + kBBytes);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms want 1024-byte alignment
     uint8_t *sbase = smem_raw + (base - raw);
     uint8_t *sA = sbase;
     uint8_t *sB = sbase + kABytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sbase + kABytes + kBBytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + kABytes + kBBytes + 16);
+    uint8_t *sA2 = sbase + kABytes + kBBytes;  // SPLIT: low parts
+    uint8_t *sB2 = sA2 + kABytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sbase + kOps);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + kOps + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // N tiles vary fastest so the CTAs sharing an A tile run together (A is
@@ -182,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
     const int nchunks = (int)((kend - kbeg + kChunkK - 1) / kChunkK);
     // operand granules of one K chunk, held in registers as packed BF16:
     // 8 A granules and up to 8 B granules per thread
-    uint4 ra[8], rb[8];
+    uint4 ra[8], rb[8], ra2[8], rb2[8];  // ra2/rb2: low parts (SPLIT)
     auto load_chunk = [&](int64_t k0) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -214,6 +232,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
                 }
             }
             ra[i] = pack8(v);
+            if (SPLIT) {
+                float lo[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) lo[e] = v[e] - __bfloat162float(__float2bfloat16_rn(v[e]));
+                ra2[i] = pack8(lo);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -234,6 +258,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
                 const int64_t n = n0 + r;
                 rb[i] = n < g.N ? __ldg(reinterpret_cast<const uint4 *>(g.Wt + n * g.Kpad + k0 + c * 8))
                                 : make_uint4(0u, 0u, 0u, 0u);
+                if (SPLIT)
+                    rb2[i] = n < g.N ? __ldg(reinterpret_cast<const uint4 *>(g.Wt2 + n * g.Kpad + k0 + c * 8))
+                                     : make_uint4(0u, 0u, 0u, 0u);
             }
         }
     };
@@ -243,6 +270,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
             const int it = tid + i * kThreads;
             const int r = TRANS ? (it & (kTileM - 1)) : (it >> 3), c = TRANS ? (it >> 7) : (it & 7);
             *reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4)) = ra[i];
+            if (SPLIT) *reinterpret_cast<uint4 *>(sA2 + r * 128 + ((c ^ (r & 7)) << 4)) = ra2[i];
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -250,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
             const int it = tid + i * kThreads;
             const int r = TRANS ? (it % Nt) : (it >> 3), c = TRANS ? (it / Nt) : (it & 7);
             *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) = rb[i];
+            if (SPLIT) *reinterpret_cast<uint4 *>(sB2 + r * 128 + ((c ^ (r & 7)) << 4)) = rb2[i];
         }
     };
     if (nchunks > 0) load_chunk(kbeg);
@@ -261,9 +290,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
         fence_after_sync();
         if (tid == 0) {
             const uint64_t da = desc_sw128(smem_u32(sA)), db = desc_sw128(smem_u32(sB));
+            const uint64_t da2 = desc_sw128(smem_u32(sA2)), db2 = desc_sw128(smem_u32(sB2));
 #pragma unroll
-            for (int k = 0; k < kChunkK / 16; ++k)  // +32 bytes per K=16 step inside the swizzle atom
-                mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < kChunkK / 16; ++k) {  // +32 bytes per K=16 step inside the swizzle atom
+                if (SPLIT) {  // small terms first
+                    mma_bf16(tmem, da2 + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                    mma_bf16(tmem, da + uint64_t(2 * k), db2 + uint64_t(2 * k), idesc, 1u);
+                    mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, 1u);
+                } else {
+                    mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                }
+            }
             mma_commit(mb);
         }
         // the next chunk's loads are in flight while the MMAs run
@@ -313,7 +350,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
                 for (int j = 0; j < 16; ++j) {
                     const int rr = r0 + 2 * (16 * b + j);
                     const int64_t m = m0 + rr;
-                    rv[j] = (EPI == EPI_RESID && col_ok && m < g.M) ? g.resid[zoff + m * g.ldy + n] : 0.f;
+                    rv[j] = ((EPI == EPI_RESID || EPI == EPI_DGELU || EPI == EPI_DRELU) && col_ok && m < g.M)
+                                ? g.resid[zoff + m * g.ldy + n]
+                                : 0.f;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -330,8 +369,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_tc_gemm(Args g) {
                     } else if (EPI == EPI_RELU) {
                         g.Y[o] = v;
                         g.Y2[o] = v > 0.f ? v : 0.f;
-                    } else {
+                    } else if (EPI == EPI_RESID) {
                         g.Y[o] = rv[j] + v;
+                    } else if (EPI == EPI_DGELU) {
+                        g.Y[o] = v * gelu_grad_f(rv[j]);
+                    } else {
+                        g.Y[o] = rv[j] > 0.f ? v : 0.f;
                     }
                 }
             }

@@ -1,5 +1,6 @@
-// BF16 tensor-core (tcgen05) linear layers for NNQS_MIXED: BF16 copies of
-// the weight matrices, and Y = X W^T + epilogue with FP32 accumulation.
+// BF16 tensor-core (tcgen05) linear layers for NNQS_MIXED and NNQS_BF16X3:
+// BF16 copies of the weight matrices (and their low parts), and
+// Y = X W^T + epilogue with FP32 accumulation.
 #pragma once
 #include "model.h"
 
@@ -7,7 +8,9 @@ namespace nnqs {
 
 struct TcWeights {
     int n_slots = 0;
+    bool split = false;            // forward layers with split operands (NNQS_BF16X3)
     void *bf16 = nullptr;          // all weight matrices, BF16, padded
+    void *bf16_lo = nullptr;       // low parts W - bf16(W) of the forward copies (same offsets)
     int64_t off[4 * 64 + 1] = {};  // element offset of each slot
     int32_t rows[4 * 64 + 1] = {}, cols[4 * 64 + 1] = {}, prows[4 * 64 + 1] = {}, pcols[4 * 64 + 1] = {};
     int64_t src[4 * 64 + 1] = {};  // offset of the FP32 source matrix in the parameter vector
@@ -40,8 +43,10 @@ nnqs_status tc_linear_fwd_ld<double>(cudaStream_t s, const TcWeights &w, int slo
                                      int64_t rows, int64_t in, const double *bias, double *Y, int64_t ldy,
                                      double *Y2, const double *resid);
 
-// dX[rows][in] = dY[rows][out] W[out][in] on tensor cores (W^T copy of `slot`)
-nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX);
+// dX[rows][in] = dY[rows][out] W[out][in] on tensor cores (W^T copy of `slot`);
+// act 1 / 2 multiplies by GELU'(Z) / ReLU'(Z) of the pre-activation Z[rows][in]
+nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX,
+                         int act = 0, const float *Z = nullptr);
 // dW[out][in] += dY[rows][out]^T X[rows][in] on tensor cores, split over rows;
 // partials go to `scratch` (scratch_elems floats) and are added in order
 nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t out, const float *X, int64_t in,

@@ -5,7 +5,10 @@
 //   E, Var                           Eq. (energy) with sample counts
 //   seeds 2 w (E_loc - E)/sum w      gradient estimator, E_loc held fixed
 //   grad                             ansatz reverse mode
-// Every stage is enqueued on the caller's stream; no host synchronisation.
+// When the samples fit in one activation chunk the forward's activations are
+// kept for the reverse mode (one forward per call); otherwise the reverse
+// mode recomputes them chunk by chunk.  Every stage is enqueued on the
+// caller's stream; no host synchronisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,10 +30,12 @@ __global__ void k_seeds(const double2 *__restrict__ eloc, const uint64_t *__rest
     seed[i] = make_double2(f * (eloc[i].x - stats[0]), f * (eloc[i].y - stats[1]));
 }
 
+// fused: the ansatz keeps its activations in `region` while E_loc and the
+// statistics run in `region2`; otherwise every stage reuses `region`
 struct Layout {
     double *lp, *eloc, *seed;
-    char *region;
-    size_t region_bytes;
+    bool fused;
+    char *region, *region2;
 };
 
 Layout layout(const nnqs_ham *H, const nnqs_model *M, int64_t n, int prec, Arena &a) {
@@ -38,9 +43,15 @@ Layout layout(const nnqs_ham *H, const nnqs_model *M, int64_t n, int prec, Arena
     L.lp = a.take<double>(size_t(2 * std::max<int64_t>(n, 1)));
     L.eloc = a.take<double>(size_t(2 * std::max<int64_t>(n, 1)));
     L.seed = a.take<double>(size_t(2 * std::max<int64_t>(n, 1)));
-    L.region_bytes = std::max({eloc_sa_workspace(H, n, n, NNQS_SWEEP_AUTO), logpsi_workspace(M, n, prec, false),
-                               logpsi_workspace(M, n, prec, true)});
-    L.region = a.take<char>(L.region_bytes);
+    const size_t ew = std::max(eloc_sa_workspace(H, n, n, NNQS_SWEEP_AUTO), stats_workspace(n));
+    L.fused = logpsi_single_chunk(M, n, prec);
+    if (L.fused) {
+        L.region = a.take<char>(logpsi_workspace(M, n, prec, true));
+        L.region2 = a.take<char>(ew);
+    } else {
+        L.region = a.take<char>(std::max({ew, logpsi_workspace(M, n, prec, false), logpsi_workspace(M, n, prec, true)}));
+        L.region2 = L.region;
+    }
     return L;
 }
 
@@ -66,7 +77,7 @@ extern "C" nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, 
     if (!params || !samples || !weights || !stats || (!grad_f64 && !grad_f32))
         return set_error(NNQS_E_INVAL, "null device pointer");
     if (M->N != H->n_qubits) return set_error(NNQS_E_INVAL, "model and Hamiltonian disagree on the qubit count");
-    if (prec != NNQS_FP64 && prec != NNQS_FP32 && prec != NNQS_MIXED) return set_error(NNQS_E_INVAL, "bad precision");
+    if (!prec_valid(prec)) return set_error(NNQS_E_INVAL, "bad precision");
     if (n_u >= (int64_t(1) << 31)) return set_error(NNQS_E_INVAL, "more than 2^31 samples");
     const size_t need = nnqs_energy_grad_workspace_size(H, M, n_u, prec);
     if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256 || workspace_bytes < need)
@@ -77,21 +88,32 @@ extern "C" nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, 
     DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
     const Layout L = layout(H, M, n_u, prec, a);
     double *eloc = eloc_out ? eloc_out : L.eloc;
+    // E_loc over S with the table log psi(S), statistics, seeds
+    auto middle = [&]() -> nnqs_status {
+        {
+            Arena sub(L.region2);
+            NNQS_TRY(eloc_sa(H, samples, L.lp, n_u, 0, n_u, M->cfg.n_alpha, M->cfg.n_beta, NNQS_SWEEP_AUTO, eloc,
+                             sub, st, s));
+        }
+        {
+            Arena sub(L.region2);
+            NNQS_TRY(energy_stats(eloc, weights, n_u, stats, sub, s));
+        }
+        NNQS_LAUNCH("k_seeds", s, k_seeds<<<grid_for(n_u, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(eloc),
+                                                                           weights, stats, n_u,
+                                                                           reinterpret_cast<double2 *>(L.seed)));
+        return NNQS_OK;
+    };
+    if (L.fused) {
+        Arena sub(L.region);
+        return logpsi_forward_backward(M, params, samples, n_u, prec, L.lp, L.seed, grad_f64, grad_f32, sub, st, s,
+                                       middle);
+    }
     {
         Arena sub(L.region);
         NNQS_TRY(logpsi_forward(M, params, samples, n_u, prec, L.lp, sub, st, s));
     }
-    {
-        Arena sub(L.region);
-        NNQS_TRY(eloc_sa(H, samples, L.lp, n_u, 0, n_u, M->cfg.n_alpha, M->cfg.n_beta, NNQS_SWEEP_AUTO, eloc, sub,
-                         st, s));
-    }
-    {
-        Arena sub(L.region);
-        NNQS_TRY(energy_stats(eloc, weights, n_u, stats, sub, s));
-    }
-    NNQS_LAUNCH("k_seeds", s, k_seeds<<<grid_for(n_u, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(eloc), weights, stats, n_u,
-                                               reinterpret_cast<double2 *>(L.seed)));
+    NNQS_TRY(middle());
     {
         Arena sub(L.region);
         NNQS_TRY(logpsi_backward(M, params, samples, n_u, prec, L.seed, grad_f64, grad_f32, sub, st, s));

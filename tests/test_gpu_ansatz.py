@@ -129,6 +129,26 @@ def test_logpsi_mixed_tensor_cores(case):
     assert np.corrcoef(got[:, 0], la)[0, 1] > 0.999
 
 
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_logpsi_bf16x3_split_operands(case):
+    """NNQS_BF16X3: the forward layers split X and W into high and low BF16
+    parts and add three tensor-core products, so the operands keep about 16
+    bits.  log psi is checked to 1e-3 of its scale against the FP64 oracle,
+    and its error must be at least 20 times below that of single BF16
+    operands on the same inputs."""
+    name, N, na, nb, d, L, H, ns = case
+    m, params, flat = make(N, na, nb, d, L, H, seed=11)
+    x = I.random_sector_samples(N // 2, na, nb, ns, seed=3)
+    xd = B.to_device_bits(x)
+    got = B.logpsi(m, flat, xd, B.BF16X3).cpu().numpy()
+    one = B.logpsi(m, flat, xd, B.MIXED).cpu().numpy()
+    la, ph = OA.forward(params, I.unpack_bits(x, N), na, nb, H)
+    ref = np.stack([la, ph], 1)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 1e-3 * scale
+    assert np.abs(got - ref).max() * 20 <= np.abs(one - ref).max()
+
+
 def test_backward_mixed_close_to_fp64():
     N, na, nb, d, L, H = 40, 10, 10, 64, 4, 8
     m, params, flat = make(N, na, nb, d, L, H, seed=13)
@@ -138,3 +158,5 @@ def test_backward_mixed_close_to_fp64():
     g64 = B.logpsi_backward(m, flat, x, seed, B.FP64).cpu().numpy()
     gmx = B.logpsi_backward(m, flat, x, seed, B.MIXED).cpu().numpy()
     assert np.linalg.norm(gmx - g64) <= 5e-2 * np.linalg.norm(g64)
+    gx3 = B.logpsi_backward(m, flat, x, seed, B.BF16X3).cpu().numpy()
+    assert np.linalg.norm(gx3 - g64) <= 5e-2 * np.linalg.norm(g64)

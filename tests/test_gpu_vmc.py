@@ -208,7 +208,7 @@ def test_adam_matches_oracle():
     assert np.abs(pt.cpu().numpy() - th).max() < 1e-6
 
 
-@pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.MIXED])
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.MIXED, B.BF16X3])
 @pytest.mark.parametrize("wl_name,ns", [("n12", 100_000), ("n40", 4096)])
 def test_sampler_kv_cache_equals_recompute(wl_name, ns, prec):
     """The key/value-cached sampler (one new token per prefix per step) draws
@@ -232,6 +232,30 @@ def test_energy_grad_mixed_and_fp32_against_fp64(n12):
     S = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
     w = torch.from_numpy(np.ones(len(S), dtype=np.int64)).cuda()
     xs = B.to_device_bits(S)
-    e = {p: B.energy_grad(ham, m, flat, xs, w, p)[0].cpu().numpy()[0] for p in (B.FP64, B.FP32, B.MIXED)}
+    precs = (B.FP64, B.FP32, B.MIXED, B.BF16X3)
+    e = {p: B.energy_grad(ham, m, flat, xs, w, p)[0].cpu().numpy()[0] for p in precs}
     assert abs(e[B.FP32] - e[B.FP64]) < 1e-5 * abs(e[B.FP64])
     assert abs(e[B.MIXED] - e[B.FP64]) < 1e-1 * abs(e[B.FP64])
+    assert abs(e[B.BF16X3] - e[B.FP64]) < 1e-4 * abs(e[B.FP64])
+    assert abs(e[B.BF16X3] - e[B.FP64]) < 0.05 * abs(e[B.MIXED] - e[B.FP64])
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.BF16X3])
+def test_energy_gate_n40_against_plain_fp64(prec):
+    """The 40-qubit, 20-electron step at full size (N_s = 16384 samples drawn
+    by the sampler from the random-init ansatz): the energy of the fast
+    arithmetic path and of the plain FP64 path on the same samples and
+    parameters differ by at most 1e-6 Ha, and the fused single-chunk
+    gradient of the fast path stays within 2e-2 of the FP64 gradient's norm."""
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    m = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+    flat = m.pack(I.workload_params(wl))
+    xs, w = B.sample(m, flat, 16384, seed=21, max_unique=1 << 15, prec=prec)
+    st64, _, g64 = B.energy_grad(ham, m, flat, xs, w, B.FP64)
+    stp, _, gp = B.energy_grad(ham, m, flat, xs, w, prec)
+    e64, ep = float(st64[0].item()), float(stp[0].item())
+    assert abs(ep - e64) <= 1e-6, (ep, e64)
+    g64, gp = g64.double().cpu().numpy(), gp.double().cpu().numpy()
+    assert np.linalg.norm(gp - g64) <= 2e-2 * np.linalg.norm(g64)
