@@ -178,6 +178,98 @@ def determinant_matrix(h, eri, states, e_core: float = 0.0):
     return M
 
 
+def _ladder(state: int, ops):
+    """Apply ladder operators (j, dagger), rightmost first, to the
+    determinant ``state`` (Python int, bit P = spin orbital P occupied) with
+    the sign (-1)^{occupied orbitals below j} of each step; None if the
+    result vanishes, else (new_state, sign)."""
+    sign = 1
+    for j, dag in reversed(ops):
+        occ = (state >> j) & 1
+        if occ == (1 if dag else 0):
+            return None
+        if bin(state & ((1 << j) - 1)).count("1") % 2:
+            sign = -sign
+        state ^= 1 << j
+    return state, sign
+
+
+def _g(eri, P, Q, R, S):
+    """<PQ|RS> = (PR|QS) for spin orbitals (spin deltas sigma_P = sigma_R and
+    sigma_Q = sigma_S), the chemist-to-physicist reading of Eq. (eham)."""
+    if P % 2 != R % 2 or Q % 2 != S % 2:
+        return 0.0
+    return float(eri[P // 2, R // 2, Q // 2, S // 2])
+
+
+def slater_condon(h, eri, x: int, xp: int, e_core: float = 0.0):
+    """<x|H|x'> for determinants x, x' (Python ints) by the Slater-Condon
+    rules, straight from the integrals (no Pauli strings):
+    equal: sum_I h_II + 1/2 sum_{I,J} <IJ||IJ>;
+    one orbital I -> A: s (h_IA + sum_{K common} <IK||AK>);
+    two orbitals I,J -> A,B: s <IJ||AB>;
+    where <PQ||RS> = <PQ|RS> - <PQ|SR> and s is the sign of
+    a+_I a_A |x'> (resp. a+_I a+_J a_B a_A |x'>) = s |x>.  Zero otherwise."""
+    d = x ^ xp
+    nd = bin(d).count("1")
+    if nd == 0:
+        occ = [P for P in range(x.bit_length()) if (x >> P) & 1]
+        e = e_core
+        for P in occ:
+            e += float(h[P // 2, P // 2])
+        for P in occ:
+            for Q in occ:
+                e += 0.5 * (_g(eri, P, Q, P, Q) - _g(eri, P, Q, Q, P))
+        return e
+    if nd == 2:
+        (I,) = [P for P in range(d.bit_length()) if (x >> P) & 1 and (d >> P) & 1]
+        (A,) = [P for P in range(d.bit_length()) if (xp >> P) & 1 and (d >> P) & 1]
+        if I % 2 != A % 2:
+            return 0.0
+        _, s = _ladder(xp, [(I, True), (A, False)])
+        v = float(h[I // 2, A // 2])
+        common = x & xp
+        for K in range(common.bit_length()):
+            if (common >> K) & 1:
+                v += _g(eri, I, K, A, K) - _g(eri, I, K, K, A)
+        return s * v
+    if nd == 4:
+        I, J = [P for P in range(d.bit_length()) if (x >> P) & 1 and (d >> P) & 1]
+        A, B = [P for P in range(d.bit_length()) if (xp >> P) & 1 and (d >> P) & 1]
+        _, s = _ladder(xp, [(I, True), (J, True), (B, False), (A, False)])
+        return s * (_g(eri, I, J, A, B) - _g(eri, I, J, B, A))
+    return 0.0
+
+
+def words_to_int(row) -> int:
+    """Packed little-endian uint64 words -> Python int."""
+    return sum(int(v) << (64 * k) for k, v in enumerate(np.asarray(row, dtype=np.uint64)))
+
+
+def eloc_slater_condon(h, eri, lut, lut_logpsi, rows):
+    """E_loc(x) = sum_{x' in lut} <x|H|x'> psi(x')/psi(x) over the sample
+    table (Eq. Eloc restricted to S, Sec. 3.4) with the matrix elements of
+    ``slater_condon``: a second path to the sample-aware local energy that
+    does not go through the Jordan-Wigner strings.  Also returns
+    sum_x' |<x|H|x'> psi(x')/psi(x)| per row.  ``lut`` [n, W] packed,
+    ``lut_logpsi`` [n, 2], ``rows`` indices into lut."""
+    lut = np.ascontiguousarray(lut, dtype=np.uint64)
+    lp = np.asarray(lut_logpsi, dtype=np.float64)
+    out = np.zeros(len(rows), dtype=complex)
+    scale = np.zeros(len(rows))
+    for k, i in enumerate(rows):
+        diff = sum(popcount(lut[:, w] ^ lut[i, w]) for w in range(lut.shape[1]))
+        x = words_to_int(lut[i])
+        for j in np.nonzero(diff <= 4)[0]:
+            hv = slater_condon(h, eri, x, words_to_int(lut[j]))
+            if hv == 0.0:
+                continue
+            r = np.exp(lp[j, 0] - lp[i, 0] + 1j * (lp[j, 1] - lp[i, 1]))
+            out[k] += hv * r
+            scale[k] += abs(hv * r)
+    return out, np.maximum(1.0, scale)
+
+
 def pauli_matrix(xy, yz, coef, n_qubits, states):
     """<s_i|H|s_j> from the folded strings: H_{x x'} = sum_t coef_t
     (-1)^{popc(x' & yz_t)} [x = x' ^ xy_t] (Eq. sham with Alg. 1 folding).

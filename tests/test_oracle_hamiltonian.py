@@ -265,3 +265,31 @@ def test_w2_bitstrings_match_w1_subset():
             # Z strings between orbitals 1 and 31 are empty here, so the
             # matrix elements agree exactly with the compact relabelling
             assert abs(M4[j, i] - hv) < 1e-13
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(6, 3, 3, 0), (5, 2, 3, 7), (4, 1, 2, 2)])
+def test_slater_condon_matches_determinant_rule(n, na, nb, seed):
+    """The closed-form Slater-Condon elements (integrals only) equal the
+    matrix built by applying the second-quantised operators of Eq. (eham) to
+    determinants, over a whole sector (every 0-, 1- and 2-orbital pair)."""
+    h, eri = I.integrals(n, seed, 4)
+    st = OH.sector_ints(n, na, nb)
+    M = OH.determinant_matrix(h, eri, st, 0.3)
+    S = np.array([[OH.slater_condon(h, eri, int(a), int(b), 0.3) for b in st] for a in st])
+    assert np.abs(S - M).max() < 1e-12 * max(1.0, np.abs(M).max())
+
+
+def test_eloc_slater_condon_matches_pauli_strings():
+    """The second sample-aware E_loc path (Slater-Condon elements, no strings)
+    equals the Pauli-string E_loc of Alg. 2 on clustered 40-qubit samples."""
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    xy, yz, coef = OH.build(h, eri)
+    lut = I.clustered_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 800, seed=3, n_centers=3)
+    lp = I.random_logpsi(len(lut), seed=4, amp_std=0.5)
+    rows = np.array([0, 17, 401, 799])
+    a = OH.eloc_lut(xy, yz, coef, lut, lp, lut[rows], wl.n_alpha, wl.n_beta)
+    b, sc = OH.eloc_slater_condon(h, eri, lut, lp, rows)
+    assert np.all(np.abs(a - b) <= 1e-11 * sc)
+    diag = np.array([OH.slater_condon(h, eri, OH.words_to_int(lut[i]), OH.words_to_int(lut[i])) for i in rows])
+    assert np.all(np.abs(b - diag) > 1e-3)  # off-diagonal pairs contribute
