@@ -21,6 +21,7 @@
 #include "dev_common.cuh"
 #include "model.h"
 #include "tc_gemm.h"
+#include "tc_gemm.cuh"
 
 namespace nnqs {
 namespace {
@@ -191,6 +192,19 @@ __global__ void k_ln_bwd(const R *__restrict__ x, const R *__restrict__ mean, co
 // kernels above leave most of a warp idle and have one load in flight)
 constexpr int kLnRows = 4;
 
+// per-lane pieces of the FP32 LayerNorm (one float4 of the row per lane);
+// the fused decode layer applies the same pieces in the same tree order
+__device__ __forceinline__ float ln_part_sum(float4 v) { return (v.x + v.y) + (v.z + v.w); }
+__device__ __forceinline__ float ln_part_sq(float4 v, float mu) {
+    const float zx = v.x - mu, zy = v.y - mu, zz = v.z - mu, zw = v.w - mu;
+    return (zx * zx + zy * zy) + (zz * zz + zw * zw);
+}
+__device__ __forceinline__ float ln_rstd(float q, int d) { return 1.0f / sqrtf(q / float(d) + 1e-5f); }
+__device__ __forceinline__ float4 ln_apply(float4 v, float mu, float rs, float4 gg, float4 bb) {
+    const float zx = v.x - mu, zy = v.y - mu, zz = v.z - mu, zw = v.w - mu;
+    return make_float4(zx * rs * gg.x + bb.x, zy * rs * gg.y + bb.y, zz * rs * gg.z + bb.z, zw * rs * gg.w + bb.w);
+}
+
 template <int LPR>
 __global__ void __launch_bounds__(256) k_ln_fwd_v(const float *__restrict__ x, const float *__restrict__ g,
                                                   const float *__restrict__ b, float *__restrict__ y,
@@ -208,18 +222,16 @@ __global__ void __launch_bounds__(256) k_ln_fwd_v(const float *__restrict__ x, c
 #pragma unroll
     for (int u = 0; u < kLnRows; ++u) {
         const int64_t row = base + u * RPW + sub;
-        float s = (v[u].x + v[u].y) + (v[u].z + v[u].w);
+        float s = ln_part_sum(v[u]);
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const float mu = s / float(d);
-        const float zx = v[u].x - mu, zy = v[u].y - mu, zz = v[u].z - mu, zw = v[u].w - mu;
-        float q = (zx * zx + zy * zy) + (zz * zz + zw * zw);
+        float q = ln_part_sq(v[u], mu);
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        const float rs = 1.0f / sqrtf(q / float(d) + 1e-5f);
+        const float rs = ln_rstd(q, d);
         if (row < rows) {
-            reinterpret_cast<float4 *>(y + row * d)[l] =
-                make_float4(zx * rs * gg.x + bb.x, zy * rs * gg.y + bb.y, zz * rs * gg.z + bb.z, zw * rs * gg.w + bb.w);
+            reinterpret_cast<float4 *>(y + row * d)[l] = ln_apply(v[u], mu, rs, gg, bb);
             if (l == 0) {
                 if (mean) mean[row] = mu;
                 if (rstd) rstd[row] = rs;
@@ -1058,6 +1070,49 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
 }
 
 // ------------------------------------------------------------------ head + masked log-softmax
+constexpr int kMaxHeadD = 256;
+
+// head weights [4][d] into shared memory (the whole block calls this)
+template <class R>
+__device__ void stage_head(const R *__restrict__ hw, int d, R *shw) {
+    for (int k = threadIdx.x; k < 4 * d; k += blockDim.x) shw[k] = hw[k];
+    __syncthreads();
+}
+
+// z[v] = hb[v] + sum_c hr[c] hw[v][c], c ascending; the row in 16-byte loads
+// when it is aligned (the sampler's conditionals and the forward's pi~ use
+// this same sum)
+template <class R>
+__device__ __forceinline__ void head_logits(const R *__restrict__ hr, const R *shw, const R *__restrict__ hb, int d,
+                                            R (&z)[4]) {
+    constexpr int V = int(16 / sizeof(R));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) z[v] = hb[v];
+    if (d % V == 0 && reinterpret_cast<uintptr_t>(hr) % 16 == 0) {
+        for (int c = 0; c < d; c += 2 * V) {
+            const ColVec<R, V> h0 = ld_vec<R, V>(hr + c);
+            const bool two = c + V < d;
+            const ColVec<R, V> h1 = two ? ld_vec<R, V>(hr + c + V) : h0;
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) z[v] += h0.v[e] * shw[v * d + c + e];
+            if (two) {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) z[v] += h1.v[e] * shw[v * d + c + V + e];
+            }
+        }
+    } else {
+        for (int c = 0; c < d; ++c) {
+            const R hv = hr[c];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) z[v] += hv * shw[v * d + c];
+        }
+    }
+}
+
 // One warp per sample, lanes over positions.  pi~ of the 4 children at each
 // position is stored for the backward; log|psi| = 1/2 sum_t log pi~(x_t).
 template <class R>
@@ -1065,6 +1120,8 @@ __global__ void k_head(const uint64_t *__restrict__ x, int W, const R *__restric
                        const R *__restrict__ hb, const uint8_t *__restrict__ tok, int64_t n, int T, int d,
                        int n_alpha, int n_beta, R *__restrict__ pi, double2 *__restrict__ out, DevStatus *st,
                        int64_t row_offset) {
+    __shared__ R shw[4 * kMaxHeadD];
+    stage_head<R>(hw, d, shw);
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -1079,14 +1136,8 @@ __global__ void k_head(const uint64_t *__restrict__ x, int W, const R *__restric
             cb += bit_of(xi, 2 * p2 + 1);
         }
         const int rem = T - 1 - t;
-        const R *hr = hf + (i * T + t) * d;
         R z[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            R a = hb[v];
-            for (int c = 0; c < d; ++c) a += hr[c] * hw[v * d + c];
-            z[v] = a;
-        }
+        head_logits<R>(hf + (i * T + t) * d, shw, hb, d, z);
         bool ok[4];
         R zmax = neg_inf<R>();
 #pragma unroll
@@ -1138,20 +1189,17 @@ __global__ void k_embed_decode(const uint64_t *__restrict__ x, int W, int64_t n,
 
 constexpr int kMaxDepth = 64;
 
+// One (prefix, head) of the cached attention: the prefix's node at depth t
+// attends over the nodes anc[0..t-1] of its ancestors and itself, in depth
+// order, with the online softmax of the full forward (same arithmetic, so the
+// cached sampler reproduces the recomputed conditionals bit for bit).
 template <class R, int DH>
-__global__ void k_attn_decode(const R *__restrict__ pool, const int64_t *__restrict__ parent, int64_t g0, int64_t n,
-                              int t, int L, int l, int H, int d, R *__restrict__ o) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n * H) return;
-    const int hh = (int)(idx % H);
-    const int64_t i = idx / H;
-    int64_t anc[kMaxDepth];
-    anc[t] = g0 + i;
-    for (int lev = t - 1; lev >= 0; --lev) anc[lev] = parent[anc[lev + 1]];
+__device__ __forceinline__ void attn_decode_row(const R *__restrict__ pool, const int32_t *__restrict__ anc_row,
+                                                int64_t self, int t, int L, int l, int d, int hh, R (&o)[DH]) {
     const int64_t row = 3 * (int64_t)d;
     const R scale = R(1) / sqrt(R(DH));
     R qv[DH], acc[DH];
-    const R *qp = pool + (anc[t] * L + l) * row + hh * DH;
+    const R *qp = pool + (self * L + l) * row + hh * DH;
 #pragma unroll
     for (int c = 0; c < DH; ++c) {
         qv[c] = qp[c] * scale;
@@ -1159,7 +1207,8 @@ __global__ void k_attn_decode(const R *__restrict__ pool, const int64_t *__restr
     }
     R m = neg_inf<R>(), lsum = 0;
     for (int j = 0; j <= t; ++j) {
-        const R *base = pool + (anc[j] * L + l) * row;
+        const int64_t node = j < t ? (int64_t)anc_row[j] : self;
+        const R *base = pool + (node * L + l) * row;
         const R *kj = base + d + hh * DH;
         const R *vj = base + 2 * d + hh * DH;
         R sc = 0;
@@ -1175,7 +1224,416 @@ __global__ void k_attn_decode(const R *__restrict__ pool, const int64_t *__restr
     }
     const R inv = R(1) / lsum;
 #pragma unroll
-    for (int c = 0; c < DH; ++c) o[i * d + hh * DH + c] = acc[c] * inv;
+    for (int c = 0; c < DH; ++c) o[c] = acc[c] * inv;
+}
+
+// anc: [n][T] ancestor table of the current level (row i lists the nodes of
+// prefix i at depths 0..t-1); prefix i is node g0 + i
+template <class R, int DH>
+__global__ void k_attn_decode(const R *__restrict__ pool, const int32_t *__restrict__ anc, int Tm, int64_t g0,
+                              int64_t n, int t, int L, int l, int H, int d, R *__restrict__ o) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * H) return;
+    const int hh = (int)(idx % H);
+    const int64_t i = idx / H;
+    R ov[DH];
+    attn_decode_row<R, DH>(pool, anc + i * Tm, g0 + i, t, L, l, d, hh, ov);
+#pragma unroll
+    for (int c = 0; c < DH; ++c) o[i * d + hh * DH + c] = ov[c];
+}
+
+// ---- fused key/value-cached decode layer on tensor cores (d = 64, F = 256)
+// One launch per layer and sampler step instead of seven: a CTA of 256
+// threads takes 128 prefixes (one new token each) through LayerNorm -> qkv
+// (rows written to the cache pool) -> attention over the cached ancestors ->
+// out-projection + residual -> LayerNorm -> FFN in four 64-column chunks
+// (W1 chunk, GELU, W2 chunk accumulated) -> residual, keeping the residual
+// rows in shared memory, the A operands as BF16 (split hi/lo) swizzled tiles
+// and the accumulators in TMEM.  Every step does the arithmetic of the
+// unfused path in the same order (same LayerNorm tree, same MMA order per
+// K step, same epilogue sums, the same attention loop), so the cached
+// sampler still reproduces the recomputed conditionals bit for bit.
+namespace dec {
+constexpr int kThreads = 256, kRows = 128, kD = 64, kQKV = 192, kF = 256;
+constexpr int kOffA = 0;         // A operand hi [128][64] BF16 (16 KB); lo at +16 KB
+constexpr int kOffG = 32768;     // FFN-out A chunk hi / lo (+16 KB); before the FFN: Wo hi / lo (+8 KB)
+constexpr int kOffB = 65536;     // Wqkv hi / lo (+24 KB); after the qkv MMA: W1 hi, W1 lo, W2 hi, W2 lo
+constexpr int kQkvLo = 24576;
+constexpr int kW1Hi = 0, kW1Lo = 32768, kW2Hi = 65536, kW2Lo = 98304;  // 4 chunks of 8 KB each
+constexpr int kOffH = kOffB + 131072;  // residual rows [128][65] FP32
+constexpr int kHS = 65;
+constexpr int kOffBar = kOffH + kRows * kHS * 4;
+constexpr int kSmem = kOffBar + 64 + 1024;  // 230,976 bytes
+constexpr uint32_t kColQKV = 0, kColO = 192, kColU = 256, kColY = 320, kTmemCols = 512;
+}  // namespace dec
+
+struct DecodeArgs {
+    float *h;  // [n][64] residual rows of the new tokens, updated in place
+    int64_t n;
+    float *pool;  // [node][L][192] q|k|v
+    int L, l, Tm, t;
+    int64_t g0;
+    const int32_t *anc;  // [n][Tm] ancestor nodes at depths 0..t-1
+    const float *ln1g, *ln1b, *ln2g, *ln2b, *bqkv, *bo, *b1, *b2;
+    const __nv_bfloat16 *wqkv, *wqkv_lo, *wo, *wo_lo, *w1, *w1_lo, *w2, *w2_lo;  // [N][Kpad], Kpad 64 (w2: 256)
+    DevStatus *st;
+};
+
+__device__ __forceinline__ void cp_async16(uint8_t *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// rows [r0, r0 + nr) and K columns [k0, k0 + 64) of W [.][kpad] into a SW128
+// tile, as asynchronous 16-byte copies (completed by cp_async_wait_all)
+__device__ __forceinline__ void dec_load_b(uint8_t *dst, const __nv_bfloat16 *__restrict__ W, int kpad, int r0, int nr,
+                                           int k0) {
+    for (int it = threadIdx.x; it < nr * 8; it += dec::kThreads) {
+        const int r = it >> 3, c = it & 7;
+        cp_async16(dst + r * 128 + ((c ^ (r & 7)) << 4), W + (int64_t)(r0 + r) * kpad + k0 + c * 8);
+    }
+}
+
+// one 8-column granule of an A tile row: BF16 high part, and the low part
+__device__ __forceinline__ void dec_store_granule(uint8_t *hi, uint8_t *lo, int r, int c, const float (&v)[8], bool split) {
+    const int off = r * 128 + ((c ^ (r & 7)) << 4);
+    *reinterpret_cast<uint4 *>(hi + off) = tc::pack8(v);
+    if (split) {
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = v[e] - __bfloat162float(__float2bfloat16_rn(v[e]));
+        *reinterpret_cast<uint4 *>(lo + off) = tc::pack8(x);
+    }
+}
+
+// LayerNorm of residual row r (shared, stride 65) into the A tile: the lane
+// sums of the 16-lane FP32 kernel combined in its butterfly order
+__device__ __forceinline__ void dec_layernorm_row(const float *sH, int r, const float *__restrict__ g,
+                                                  const float *__restrict__ b, uint8_t *aHi, uint8_t *aLo, bool split) {
+    float4 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        v[k] = make_float4(sH[r * dec::kHS + 4 * k], sH[r * dec::kHS + 4 * k + 1], sH[r * dec::kHS + 4 * k + 2],
+                           sH[r * dec::kHS + 4 * k + 3]);
+    float a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = ln_part_sum(v[k]);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < o; ++k) a[k] = a[k] + a[k + o];
+    const float mu = a[0] / float(dec::kD);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = ln_part_sq(v[k], mu);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < o; ++k) a[k] = a[k] + a[k + o];
+    const float rs = ln_rstd(a[0], dec::kD);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float4 y0 = ln_apply(v[2 * c], mu, rs, __ldg(reinterpret_cast<const float4 *>(g) + 2 * c),
+                                   __ldg(reinterpret_cast<const float4 *>(b) + 2 * c));
+        const float4 y1 = ln_apply(v[2 * c + 1], mu, rs, __ldg(reinterpret_cast<const float4 *>(g) + 2 * c + 1),
+                                   __ldg(reinterpret_cast<const float4 *>(b) + 2 * c + 1));
+        const float x[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+        dec_store_granule(aHi, aLo, r, c, x, split);
+    }
+}
+
+// NH consecutive heads of one prefix: the per-head arithmetic of
+// attn_decode_row, with the ancestor loop outside so that the keys and values
+// of all NH heads of an ancestor are loaded together, and the next
+// ancestor's node id fetched one step ahead
+template <int DH, int NH>
+__device__ __forceinline__ void dec_attention_heads(const float *__restrict__ pool, const int32_t *__restrict__ anc_row,
+                                                    int64_t self, int t, int L, int l, int hh0, float (&o)[NH][DH]) {
+    constexpr int d = dec::kD;
+    const int64_t row = 3 * (int64_t)d;
+    const float scale = 1.0f / sqrtf(float(DH));
+    float qv[NH][DH], acc[NH][DH], m[NH], lsum[NH];
+    const float *qp = pool + (self * L + l) * row + hh0 * DH;
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+#pragma unroll
+        for (int c = 0; c < DH; ++c) {
+            qv[h][c] = qp[h * DH + c] * scale;
+            acc[h][c] = 0.f;
+        }
+        m[h] = neg_inf<float>();
+        lsum[h] = 0.f;
+    }
+    int64_t node = t > 0 ? (int64_t)anc_row[0] : self;
+    for (int j = 0; j <= t; ++j) {
+        const int64_t next = j + 1 < t ? (int64_t)anc_row[j + 1] : self;
+        const float *base = pool + (node * L + l) * row;
+        float kk[NH * DH], vv[NH * DH];
+#pragma unroll
+        for (int e = 0; e < NH * DH; e += 4) {
+            const float4 k4 = *reinterpret_cast<const float4 *>(base + d + hh0 * DH + e);
+            const float4 v4 = *reinterpret_cast<const float4 *>(base + 2 * d + hh0 * DH + e);
+            kk[e] = k4.x; kk[e + 1] = k4.y; kk[e + 2] = k4.z; kk[e + 3] = k4.w;
+            vv[e] = v4.x; vv[e + 1] = v4.y; vv[e + 2] = v4.z; vv[e + 3] = v4.w;
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            float sc = 0;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) sc += qv[h][c] * kk[h * DH + c];
+            const float mn = sc > m[h] ? sc : m[h];
+            const float corr = exp_<float>(m[h] - mn);
+            const float p = exp_<float>(sc - mn);
+            lsum[h] = lsum[h] * corr + p;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) acc[h][c] = acc[h][c] * corr + p * vv[h * DH + c];
+            m[h] = mn;
+        }
+        node = next;
+    }
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+        const float inv = 1.0f / lsum[h];
+#pragma unroll
+        for (int c = 0; c < DH; ++c) o[h][c] = acc[h][c] * inv;
+    }
+}
+
+// 4 K steps of one 128 x N tile: (lo, hi), (hi, lo), (hi, hi) per step with
+// split operands, as the unfused kernel issues them
+__device__ __forceinline__ void dec_mma(uint32_t tmem, uint32_t aHi, uint32_t aLo, uint32_t bHi, uint32_t bLo, int N,
+                                        bool split, bool acc0) {
+    const uint32_t idesc = tc::idesc_bf16(dec::kRows, N);
+    const uint64_t da = tc::desc_sw128(aHi), db = tc::desc_sw128(bHi);
+    const uint64_t da2 = tc::desc_sw128(aLo), db2 = tc::desc_sw128(bLo);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t acc = (acc0 || k > 0) ? 1u : 0u;
+        if (split) {
+            tc::mma_bf16(tmem, da2 + uint64_t(2 * k), db + uint64_t(2 * k), idesc, acc);
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db2 + uint64_t(2 * k), idesc, 1u);
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, 1u);
+        } else {
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, acc);
+        }
+    }
+}
+
+template <bool SPLIT, int DH>
+__global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g) {
+    using namespace dec;
+    constexpr int H = kD / DH, NH = H / 2;  // heads per thread (two threads per row)
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sb = smem_raw + (base - raw);
+    uint8_t *aHi = sb + kOffA, *aLo = sb + kOffA + 16384;
+    uint8_t *gHi = sb + kOffG, *gLo = sb + kOffG + 16384;
+    uint8_t *bB = sb + kOffB;
+    float *sH = reinterpret_cast<float *>(sb + kOffH);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 16);
+    const uint32_t uA = base + kOffA, uA2 = base + kOffA + 16384, uG = base + kOffG, uG2 = base + kOffG + 16384;
+    const uint32_t uB = base + kOffB;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t m0 = blockIdx.x * (int64_t)kRows;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // residual rows and the qkv weights
+    dec_load_b(bB, g.wqkv, kD, 0, kQKV, 0);
+    if (SPLIT) dec_load_b(bB + kQkvLo, g.wqkv_lo, kD, 0, kQKV, 0);
+    for (int it = tid; it < kRows * (kD / 4); it += kThreads) {
+        const int r = it >> 4, c4 = it & 15;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m0 + r < g.n) v = *reinterpret_cast<const float4 *>(g.h + (m0 + r) * kD + 4 * c4);
+        sH[r * kHS + 4 * c4] = v.x;
+        sH[r * kHS + 4 * c4 + 1] = v.y;
+        sH[r * kHS + 4 * c4 + 2] = v.z;
+        sH[r * kHS + 4 * c4 + 3] = v.w;
+    }
+    cp_async_wait_all();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t mb = tc::smem_u32(mbar);
+    uint32_t phase = 0;
+    bool ok = true;
+    auto sync_async = [&]() {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+    auto wait_mma = [&]() {
+        ok = __syncthreads_and(tc::mbar_wait(mb, phase) ? 1 : 0) != 0;
+        phase ^= 1u;
+        tc::fence_after_sync();
+    };
+    const int q4 = warp & 3, half = warp >> 2, row = 32 * q4 + lane;
+    const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
+    const bool row_ok = m0 + row < g.n;
+
+    // ---- LayerNorm 1 -> qkv
+    if (tid < kRows) dec_layernorm_row(sH, tid, g.ln1g, g.ln1b, aHi, aLo, SPLIT);
+    sync_async();
+    if (tid == 0) {
+        dec_mma(tmem + kColQKV, uA, uA2, uB, uB + kQkvLo, kQKV, SPLIT, false);
+        tc::mma_commit(mb);
+    }
+    wait_mma();
+    if (ok) {
+        // Wo into the (idle) FFN-out tile, the FFN weights over Wqkv: copies
+        // in flight during the epilogue and the attention
+        dec_load_b(gHi, g.wo, kD, 0, kD, 0);
+        if (SPLIT) dec_load_b(gHi + 8192, g.wo_lo, kD, 0, kD, 0);
+#pragma unroll
+        for (int c = 0; c < kF / kD; ++c) {
+            dec_load_b(bB + kW1Hi + 8192 * c, g.w1, kD, kD * c, kD, 0);
+            dec_load_b(bB + kW2Hi + 8192 * c, g.w2, kF, 0, kD, kD * c);
+            if (SPLIT) {
+                dec_load_b(bB + kW1Lo + 8192 * c, g.w1_lo, kD, kD * c, kD, 0);
+                dec_load_b(bB + kW2Lo + 8192 * c, g.w2_lo, kF, 0, kD, kD * c);
+            }
+        }
+        // q|k|v + bias into the pool row of this node (warp half: 96 columns)
+        float *prow = g.pool + ((g.g0 + m0 + row) * g.L + g.l) * (int64_t)kQKV;
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const int c0 = 96 * half + 16 * b;
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColQKV + c0, r16);
+            if (row_ok) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4 *>(prow + c0 + j) =
+                        make_float4(__uint_as_float(r16[j]) + g.bqkv[c0 + j], __uint_as_float(r16[j + 1]) + g.bqkv[c0 + j + 1],
+                                    __uint_as_float(r16[j + 2]) + g.bqkv[c0 + j + 2],
+                                    __uint_as_float(r16[j + 3]) + g.bqkv[c0 + j + 3]);
+            }
+        }
+    }
+    __syncthreads();  // this CTA's pool rows are visible to all its threads
+    if (ok) {
+        // ---- attention (thread: one row, half the heads) -> A tile
+        const int r = tid & (kRows - 1);
+        const int hh0 = (tid >> 7) * NH;
+        float o[NH][DH];
+        if (m0 + r < g.n) {
+            dec_attention_heads<DH, NH>(g.pool, g.anc + (m0 + r) * g.Tm, g.g0 + m0 + r, g.t, g.L, g.l, hh0, o);
+        } else {
+#pragma unroll
+            for (int h = 0; h < NH; ++h)
+#pragma unroll
+                for (int c = 0; c < DH; ++c) o[h][c] = 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+#pragma unroll
+            for (int gi = 0; gi < DH / 8; ++gi) {
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = o[h][8 * gi + e];
+                dec_store_granule(aHi, aLo, r, (hh0 + h) * (DH / 8) + gi, x, SPLIT);
+            }
+    }
+    cp_async_wait_all();
+    sync_async();
+    if (ok) {
+        if (tid == 0) {
+            dec_mma(tmem + kColO, uA, uA2, uG, uG + 8192, kD, SPLIT, false);
+            tc::mma_commit(mb);
+        }
+        wait_mma();
+    }
+    if (ok) {
+        // h += attn Wo^T + bo (warp half: 32 columns)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int c0 = 32 * half + 16 * b;
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColO + c0, r16);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float v = __uint_as_float(r16[j]) + g.bo[c0 + j];
+                sH[row * kHS + c0 + j] = sH[row * kHS + c0 + j] + v;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- LayerNorm 2 -> FFN: MMA1(c) = LN2 W1_c^T, GELU -> G, MMA2(c) += G W2_c^T;
+    // MMA2(c) and MMA1(c+1) are committed together
+    if (ok && tid < kRows) dec_layernorm_row(sH, tid, g.ln2g, g.ln2b, aHi, aLo, SPLIT);
+    sync_async();
+    if (ok && tid == 0) {
+        dec_mma(tmem + kColU, uA, uA2, uB + kW1Hi, uB + kW1Lo, kD, SPLIT, false);
+        tc::mma_commit(mb);
+    }
+    for (int c = 0; c < kF / kD && ok; ++c) {
+        wait_mma();
+        if (!ok) break;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int c0 = 32 * half + 16 * b;
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColU + c0, r16);
+#pragma unroll
+            for (int gi = 0; gi < 2; ++gi) {
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = tc::gelu_f(__uint_as_float(r16[8 * gi + e]) + g.b1[kD * c + c0 + 8 * gi + e]);
+                dec_store_granule(gHi, gLo, row, (c0 >> 3) + gi, x, SPLIT);
+            }
+        }
+        sync_async();
+        if (tid == 0) {
+            dec_mma(tmem + kColY, uG, uG2, uB + kW2Hi + 8192 * c, uB + kW2Lo + 8192 * c, kD, SPLIT, c > 0);
+            if (c + 1 < kF / kD)
+                dec_mma(tmem + kColU, uA, uA2, uB + kW1Hi + 8192 * (c + 1), uB + kW1Lo + 8192 * (c + 1), kD, SPLIT,
+                        false);
+            tc::mma_commit(mb);
+        }
+    }
+    if (ok) wait_mma();
+    if (ok) {
+        // h += FFN + b2, back to global
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int c0 = 32 * half + 16 * b;
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColY + c0, r16);
+            if (row_ok) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float y = __uint_as_float(r16[j + e]) + g.b2[c0 + j + e];
+                        v[e] = sH[row * kHS + c0 + j + e] + y;
+                    }
+                    *reinterpret_cast<float4 *>(g.h + (m0 + row) * kD + c0 + j) = make_float4(v[0], v[1], v[2], v[3]);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -11;
+    }
+    cp_async_wait_all();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(dec::kTmemCols)
+                     : "memory");
+    }
 }
 
 // pi~(v | prefix) at position S-1 for each prefix (sampling): cond[i][4], FP64
@@ -1184,6 +1642,8 @@ template <class R>
 __global__ void k_cond_last(const uint64_t *__restrict__ x, int W, const R *__restrict__ hf, const R *__restrict__ hw,
                             const R *__restrict__ hb, int64_t n, int S, int t, int T, int d, int n_alpha, int n_beta,
                             double *__restrict__ cond, DevStatus *st) {
+    __shared__ R shw[4 * kMaxHeadD];
+    stage_head<R>(hw, d, shw);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t *xi = x + i * W;
@@ -1193,14 +1653,13 @@ __global__ void k_cond_last(const uint64_t *__restrict__ x, int W, const R *__re
         cb += bit_of(xi, 2 * p2 + 1);
     }
     const int rem = T - 1 - t;
-    const R *hr = hf + (i * S + S - 1) * d;
+    R zr[4];
+    head_logits<R>(hf + (i * S + S - 1) * d, shw, hb, d, zr);
     double z[4], zmax = -INFINITY;
     bool ok[4], any = false;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        R a = hb[v];
-        for (int c = 0; c < d; ++c) a += hr[c] * hw[v * d + c];
-        z[v] = (double)a;
+        z[v] = (double)zr[v];
         const int aa = ca + (v & 1), bb = cb + (v >> 1);
         ok[v] = aa <= n_alpha && bb <= n_beta && aa + rem >= n_alpha && bb + rem >= n_beta;
         if (ok[v]) {
@@ -1233,6 +1692,40 @@ __global__ void k_head_bwd(const R *__restrict__ pi, const uint8_t *__restrict__
 
 // ------------------------------------------------------------------ phase MLP
 // z1[i][u] = b1[u] + sum over occupied qubits j of W1[u][j]; r1 = relu(z1)
+// blocked form: thread u of a block keeps weight column u and walks 32
+// samples (bits staged in shared memory); same sum order as k_phase_in
+constexpr int kPhaseRows = 32;
+template <class R>
+__global__ void k_phase_in_blk(const uint64_t *__restrict__ x, int W, int N, const R *__restrict__ w1,
+                               const R *__restrict__ b1, int64_t n, int P, R *__restrict__ z1, R *__restrict__ r1,
+                               R *__restrict__ xf) {
+    __shared__ uint64_t xs[kPhaseRows * 2];
+    const int u = threadIdx.x;
+    const int64_t i0 = blockIdx.x * (int64_t)kPhaseRows;
+    const int ns = (int)min((int64_t)kPhaseRows, n - i0);
+    for (int k = threadIdx.x; k < ns * W; k += blockDim.x) xs[k] = x[i0 * W + k];
+    __syncthreads();
+    if (u >= P) return;
+    R a[kPhaseRows];
+    const R bu = b1[u];
+#pragma unroll
+    for (int k = 0; k < kPhaseRows; ++k) a[k] = bu;
+    for (int j = 0; j < N; ++j) {
+        const R wj = w1[(int64_t)u * N + j];
+#pragma unroll
+        for (int k = 0; k < kPhaseRows; ++k)
+            if (k < ns && ((xs[k * W + (j >> 6)] >> (j & 63)) & 1ull)) a[k] += wj;
+    }
+#pragma unroll
+    for (int k = 0; k < kPhaseRows; ++k) {
+        if (k >= ns) break;
+        const int64_t o = (i0 + k) * P + u;
+        z1[o] = a[k];
+        r1[o] = a[k] > R(0) ? a[k] : R(0);
+        if (xf && u < N) xf[(i0 + k) * N + u] = (R)((xs[k * W + (u >> 6)] >> (u & 63)) & 1ull);
+    }
+}
+
 template <class R>
 __global__ void k_phase_in(const uint64_t *__restrict__ x, int W, int N, const R *__restrict__ w1,
                            const R *__restrict__ b1, int64_t n, int P, R *__restrict__ z1, R *__restrict__ r1,
@@ -1301,24 +1794,80 @@ nnqs_status act_bwd(cudaStream_t s, int act, R *dX, const R *Z, int64_t n) {
     return NNQS_OK;
 }
 
-// token-embedding gradient: out[v][c] += sum over rows with input id v of dh[row][c]
-template <class R>
-__global__ void k_tok_grad(const R *__restrict__ dh, const uint8_t *__restrict__ tok, int64_t n, int T, int d,
-                           int64_t rows_per_block, R *__restrict__ partial) {
-    const int64_t rows = n * T;
+// token-embedding gradient: out[v][c] += sum over rows whose input token is v
+// of dh[row][c] (the input of position t is token t-1, the start id 4 at
+// t = 0).  Laid out like k_colred: 16-byte loads, row phases added in order,
+// partial[blk][5 d], the last block adds the blocks in order.
+template <class R, int VW>
+__global__ void __launch_bounds__(kColThreads) k_tok_grad(const R *__restrict__ dh, const uint8_t *__restrict__ tok,
+                                                          int64_t rows, int T, int d, int64_t rows_per_block,
+                                                          R *__restrict__ partial, unsigned *counter,
+                                                          R *__restrict__ out) {
+    __shared__ R sh[5 * kColThreads * VW];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
     const int64_t r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
-    for (int c = threadIdx.x; c < d; c += blockDim.x) {
-        R s[5] = {0, 0, 0, 0, 0};
-        for (int64_t r = r0; r < r1; ++r) {
-            const int t = (int)(r % T);
-            const int inp = t == 0 ? 4 : (int)tok[r - 1];
-            const R v = dh[r * d + c];
+    const int cv = d / VW, ct = min(cv, kColThreads), phases = kColThreads / ct;
+    const int p = tid / ct, j = tid % ct;
+    for (int v0 = 0; v0 < cv; v0 += ct) {
+        const int vc = v0 + j;
+        const bool act = p < phases && vc < cv;
+        R acc[5][VW];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) s[k] += (inp == k) ? v : R(0);
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) acc[k][e] = 0;
+        if (act) {
+            int64_t r = r0 + p;
+            for (; r + 3 * phases < r1; r += 4 * phases) {
+                ColVec<R, VW> va[4];
+                int inp[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t rr = r + u * phases;
+                    va[u] = ld_vec<R, VW>(dh + rr * d + vc * VW);
+                    inp[u] = (rr % T == 0) ? 4 : (int)tok[rr - 1];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k)
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) acc[k][e] += inp[u] == k ? va[u].v[e] : R(0);
+            }
+            for (; r < r1; r += phases) {
+                const ColVec<R, VW> va = ld_vec<R, VW>(dh + r * d + vc * VW);
+                const int inp = (r % T == 0) ? 4 : (int)tok[r - 1];
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc[k][e] += inp == k ? va.v[e] : R(0);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) partial[(blockIdx.x * 5 + k) * (int64_t)d + c] = s[k];
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) sh[(k * kColThreads + tid) * VW + e] = acc[k][e];
+        __syncthreads();
+        if (p == 0 && vc < cv) {
+            for (int k = 0; k < 5; ++k)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    R t = 0;
+                    for (int q = 0; q < phases; ++q) t += sh[(k * kColThreads + q * ct + j) * VW + e];
+                    partial[blockIdx.x * 5 * (int64_t)d + k * d + vc * VW + e] = t;
+                }
+        }
+        __syncthreads();
     }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum_partial_rows<R, VW>(partial, gridDim.x, 5 * d, 0, 5 * d, out, sh);
+    if (tid == 0) *counter = 0u;
 }
 
 // ------------------------------------------------------------------ orchestration
@@ -1528,7 +2077,10 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     NNQS_LAUNCH("k_head", s, k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
                                                     M->cfg.n_beta, A.pi, out, st, row_offset));
     // phase MLP
-    NNQS_LAUNCH("k_phase_in", s, k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
+    if (P <= 1024 && W <= 2 && N <= P)
+        NNQS_LAUNCH("k_phase_in", s, k_phase_in_blk<R><<<(unsigned)((C + kPhaseRows - 1) / kPhaseRows), (P + 31) / 32 * 32, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
+    else
+        NNQS_LAUNCH("k_phase_in", s, k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
     if (tcw) {
         NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(L, 0), EPI_RELU, A.r1, C, P, V.b2p, A.z2, A.r2, nullptr));
     } else {
@@ -1626,8 +2178,11 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(5 * d))));
         const int64_t rpb = (rows + nblk - 1) / nblk;
         nblk = (rows + rpb - 1) / rpb;
-        NNQS_LAUNCH("k_tok_grad", s, k_tok_grad<R><<<(unsigned)nblk, 128, 0, s>>>(G.dh, A.tok, C, T, d, rpb, scr.buf));
-        NNQS_LAUNCH("k_sum_partials", s, k_sum_partials<R><<<(unsigned)((5 * d + 31) / 32), kColThreads, 0, s>>>(scr.buf, nblk, 5 * d, gacc + Lo.tok_emb));
+        constexpr int V = int(16 / sizeof(R));
+        if (d % V == 0 && reinterpret_cast<uintptr_t>(G.dh) % 16 == 0)
+            NNQS_LAUNCH("k_tok_grad", s, (k_tok_grad<R, V><<<(unsigned)nblk, kColThreads, 0, s>>>(G.dh, A.tok, rows, T, d, rpb, scr.buf, scr.ctr, gacc + Lo.tok_emb)));
+        else
+            NNQS_LAUNCH("k_tok_grad", s, (k_tok_grad<R, 1><<<(unsigned)nblk, kColThreads, 0, s>>>(G.dh, A.tok, rows, T, d, rpb, scr.buf, scr.ctr, gacc + Lo.tok_emb)));
     }
     return NNQS_OK;
 }
@@ -1769,38 +2324,111 @@ size_t cond_workspace_impl(const nnqs_model *M, int64_t max_prefixes, bool tenso
 }  // namespace
 
 template <int DH_, class R>
-nnqs_status launch_attn_decode(cudaStream_t s, const R *pool, const int64_t *parent, int64_t g0, int64_t n, int t,
+nnqs_status launch_attn_decode(cudaStream_t s, const R *pool, const int32_t *anc, int Tm, int64_t g0, int64_t n, int t,
                                int L, int l, int H, int d, R *o) {
     NNQS_LAUNCH("k_attn_decode", s,
-                k_attn_decode<R, DH_><<<grid_for(n * H, 128), 128, 0, s>>>(pool, parent, g0, n, t, L, l, H, d, o));
+                k_attn_decode<R, DH_><<<grid_for(n * H, 128), 128, 0, s>>>(pool, anc, Tm, g0, n, t, L, l, H, d, o));
     return NNQS_OK;
 }
 
 template <class R>
-nnqs_status attn_decode(cudaStream_t s, int dh, const R *pool, const int64_t *parent, int64_t g0, int64_t n, int t,
+nnqs_status attn_decode(cudaStream_t s, int dh, const R *pool, const int32_t *anc, int Tm, int64_t g0, int64_t n, int t,
                         int L, int l, int H, int d, R *o) {
     switch (dh) {
-        case 1: return launch_attn_decode<1>(s, pool, parent, g0, n, t, L, l, H, d, o);
-        case 2: return launch_attn_decode<2>(s, pool, parent, g0, n, t, L, l, H, d, o);
-        case 4: return launch_attn_decode<4>(s, pool, parent, g0, n, t, L, l, H, d, o);
-        case 8: return launch_attn_decode<8>(s, pool, parent, g0, n, t, L, l, H, d, o);
-        case 16: return launch_attn_decode<16>(s, pool, parent, g0, n, t, L, l, H, d, o);
-        case 32: return launch_attn_decode<32>(s, pool, parent, g0, n, t, L, l, H, d, o);
-        case 64: return launch_attn_decode<64>(s, pool, parent, g0, n, t, L, l, H, d, o);
+        case 1: return launch_attn_decode<1>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 2: return launch_attn_decode<2>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 4: return launch_attn_decode<4>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 8: return launch_attn_decode<8>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 16: return launch_attn_decode<16>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 32: return launch_attn_decode<32>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 64: return launch_attn_decode<64>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
         default: return set_error(NNQS_E_UNSUPPORTED, "head dimension must be a power of two <= 64");
     }
 }
 
 // one decoding step for C prefixes at depth t (global node ids g0 ...)
+bool decode_fused_ok(const nnqs_model *M, const TcWeights &w) {
+    if (M->d != dec::kD || M->F != dec::kF || (M->dh != 8 && M->dh != 16)) return false;
+    for (int l = 0; l < M->L; ++l) {
+        if (w.pcols[tc_slot(l, 0)] != 64 || w.pcols[tc_slot(l, 1)] != 64 || w.pcols[tc_slot(l, 2)] != 64 ||
+            w.pcols[tc_slot(l, 3)] != 256)
+            return false;
+    }
+    return true;
+}
+
+template <bool SPLIT, int DH>
+nnqs_status launch_decode_layer(const DecodeArgs &g, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_decode_layer<SPLIT, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           dec::kSmem));
+        attr = true;
+    }
+    const unsigned grid = (unsigned)((g.n + dec::kRows - 1) / dec::kRows);
+    NNQS_LAUNCH("k_decode_layer", s, (k_decode_layer<SPLIT, DH><<<grid, dec::kThreads, dec::kSmem, s>>>(g)));
+    return NNQS_OK;
+}
+
+// one layer of the cached decode for n new tokens (rows h) in one launch
+nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, float *h, int64_t n,
+                               float *pool, const int32_t *anc, int t, int64_t g0, int l, DevStatus *st,
+                               cudaStream_t s) {
+    if (n == 0) return NNQS_OK;
+    const auto &Lw = V.layer[l];
+    const __nv_bfloat16 *hi = static_cast<const __nv_bfloat16 *>(w.bf16);
+    const __nv_bfloat16 *lo = static_cast<const __nv_bfloat16 *>(w.bf16_lo);
+    DecodeArgs g{};
+    g.h = h;
+    g.n = n;
+    g.pool = pool;
+    g.L = M->L;
+    g.l = l;
+    g.Tm = M->T;
+    g.t = t;
+    g.g0 = g0;
+    g.anc = anc;
+    g.ln1g = Lw.ln1g;
+    g.ln1b = Lw.ln1b;
+    g.ln2g = Lw.ln2g;
+    g.ln2b = Lw.ln2b;
+    g.bqkv = Lw.bqkv;
+    g.bo = Lw.bo;
+    g.b1 = Lw.b1;
+    g.b2 = Lw.b2;
+    g.wqkv = hi + w.off[tc_slot(l, 0)];
+    g.wqkv_lo = lo + w.off[tc_slot(l, 0)];
+    g.wo = hi + w.off[tc_slot(l, 1)];
+    g.wo_lo = lo + w.off[tc_slot(l, 1)];
+    g.w1 = hi + w.off[tc_slot(l, 2)];
+    g.w1_lo = lo + w.off[tc_slot(l, 2)];
+    g.w2 = hi + w.off[tc_slot(l, 3)];
+    g.w2_lo = lo + w.off[tc_slot(l, 3)];
+    g.st = st;
+    // work per launch (for the profile): the four GEMMs of the layer
+    note_work("k_decode_layer", 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
+              4.0 * double(n) * (2 * dec::kD + dec::kQKV) + 2.0 * (w.split ? 2.0 : 1.0) *
+                                                                 (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF));
+    if (w.split) return M->dh == 8 ? launch_decode_layer<true, 8>(g, s) : launch_decode_layer<true, 16>(g, s);
+    return M->dh == 8 ? launch_decode_layer<false, 8>(g, s) : launch_decode_layer<false, 16>(g, s);
+}
+
 template <class R>
 nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, int t, int64_t g0,
-                         R *pool, const int64_t *parent, Acts<R> &A, double *cond, DevStatus *st,
+                         R *pool, const int32_t *anc, Acts<R> &A, double *cond, DevStatus *st,
                          const TcWeights *tcw, cudaStream_t s) {
     const int T = M->T, d = M->d, L = M->L, F = M->F, H = M->H, W = M->W;
     const int64_t rows = C;
     R *h = A.hbuf;
     NNQS_LAUNCH("k_embed", s, k_embed_decode<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, t, T, d, V.tok, V.pos, h));
-    for (int l = 0; l < L; ++l) {
+    bool fused = false;
+    if constexpr (sizeof(R) == 4) {
+        if (tcw && decode_fused_ok(M, *tcw)) {
+            fused = true;
+            for (int l = 0; l < L; ++l) NNQS_TRY(decode_layer_fused(M, V, *tcw, h, C, pool, anc, t, g0, l, st, s));
+        }
+    }
+    for (int l = 0; l < L && !fused; ++l) {
         const auto &Lw = V.layer[l];
         R *qkv = pool + (g0 * L + l) * 3 * (int64_t)d;
         NNQS_TRY(ln_fwd<R>(s, h, Lw.ln1g, Lw.ln1b, A.a, nullptr, nullptr, rows, d));
@@ -1811,7 +2439,7 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
             NNQS_TRY(gemm<R>(s, EPI_STORE, A.a, d, 1, Lw.wqkv, d, 1, qkv, (int64_t)L * 3 * d, nullptr, Lw.bqkv, nullptr,
                              rows, 3 * d, d, A.scr));
         }
-        NNQS_TRY(attn_decode<R>(s, M->dh, pool, parent, g0, C, t, L, l, H, d, A.o));
+        NNQS_TRY(attn_decode<R>(s, M->dh, pool, anc, T, g0, C, t, L, l, H, d, A.o));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 1), EPI_RESID, A.o, rows, d, Lw.bo, h, nullptr, h));
         } else {
@@ -1882,7 +2510,7 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
 void cond_destroy(CondCtx *c) { delete c; }
 
 nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int t,
-                             int64_t g0, const int64_t *parent, double *cond, DevStatus *st, cudaStream_t s) {
+                             int64_t g0, const int32_t *anc, double *cond, DevStatus *st, cudaStream_t s) {
     if (t >= kMaxDepth) return set_error(NNQS_E_UNSUPPORTED, "more than 64 tokens");
     if (g0 + n > ctx->pool_nodes) return set_error(NNQS_E_TABLE_FULL, "key/value cache full");
     ctx->tcw.st = st;
@@ -1891,11 +2519,11 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
         if (ctx->prec == NNQS_FP64) {
             const Views<double> V = make_views<double>(M, static_cast<double *>(ctx->params));
             NNQS_TRY(decode_chunk<double>(M, V, prefixes + c0 * M->W, cn, t, g0 + c0, static_cast<double *>(ctx->pool),
-                                          parent, ctx->Ad, cond + c0 * 4, st, nullptr, s));
+                                          anc + c0 * M->T, ctx->Ad, cond + c0 * 4, st, nullptr, s));
         } else {
             const Views<float> V = make_views<float>(M, static_cast<float *>(ctx->params));
             NNQS_TRY(decode_chunk<float>(M, V, prefixes + c0 * M->W, cn, t, g0 + c0, static_cast<float *>(ctx->pool),
-                                         parent, ctx->Af, cond + c0 * 4, st, ctx->tensor ? &ctx->tcw : nullptr, s));
+                                         anc + c0 * M->T, ctx->Af, cond + c0 * 4, st, ctx->tensor ? &ctx->tcw : nullptr, s));
         }
     }
     return NNQS_OK;

@@ -63,10 +63,10 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
 // full recomputation over the S = t+1 positions of every prefix
 nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int S, double *cond,
                       DevStatus *st, cudaStream_t s);
-// cached: only position t; prefixes are tree nodes g0..g0+n-1, parent[g] the
-// node one level up
+// cached: only position t; prefixes are tree nodes g0..g0+n-1 and anc[i][0..t-1]
+// (row stride T) the nodes of prefix i's ancestors at depths 0..t-1
 nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int t,
-                             int64_t g0, const int64_t *parent, double *cond, DevStatus *st, cudaStream_t s);
+                             int64_t g0, const int32_t *anc, double *cond, DevStatus *st, cudaStream_t s);
 void cond_destroy(CondCtx *c);
 
 // eloc_exact.cu

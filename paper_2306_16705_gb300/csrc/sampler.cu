@@ -238,10 +238,13 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
 }
 
 // children of prefix i in token order at slots off[i] ...
+// children of prefix i go to rows off[i].. of the next level; with the
+// key/value cache each child's ancestor row is its parent's row plus the
+// parent's own node g_cur + i at depth `step`
 __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
                        const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
-                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, int64_t *__restrict__ parent,
-                       int64_t g_cur, int64_t g_next, DevStatus *st) {
+                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, const int32_t *__restrict__ anc,
+                       int32_t *__restrict__ nanc, int64_t g_cur, DevStatus *st) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t j = off[i];
@@ -257,7 +260,10 @@ __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__rest
         if (v & 1) npref[j * W + ((2 * p) >> 6)] |= 1ull << ((2 * p) & 63);
         if (v & 2) npref[j * W + ((2 * p + 1) >> 6)] |= 1ull << ((2 * p + 1) & 63);
         nw[j] = c;
-        if (parent) parent[g_next + j] = g_cur + i;  // tree link for the key/value cache
+        if (nanc) {
+            for (int lev = 0; lev < step; ++lev) nanc[j * T + lev] = anc[i * T + lev];
+            nanc[j * T + step] = (int32_t)(g_cur + i);
+        }
         ++j;
     }
 }
@@ -266,7 +272,8 @@ struct SLayout {
     uint64_t *pref[2], *w[2], *counts;
     double *cond;
     int32_t *nchild;
-    int64_t *off, *bsum, *total, *parent;
+    int64_t *off, *bsum, *total;
+    int32_t *anc[2];  // key/value cache: ancestor tables of the current and next level
     char *region;
     int64_t kv_nodes;
 };
@@ -285,7 +292,7 @@ SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &
     L.bsum = a.take<int64_t>(size_t((cap + kScan - 1) / kScan + 1));
     L.total = a.take<int64_t>(1);
     L.kv_nodes = cached ? int64_t(M->T) * cap + 1 : 0;
-    L.parent = cached ? a.take<int64_t>(size_t(L.kv_nodes)) : nullptr;
+    for (int k = 0; k < 2; ++k) L.anc[k] = cached ? a.take<int32_t>(size_t(cap) * M->T) : nullptr;
     L.region = a.take<char>(cond_workspace(M, cap, prec, L.kv_nodes));
     return L;
 }
@@ -322,6 +329,8 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     Arena a(workspace);
     DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
     const SLayout L = slayout(M, max_unique, prec, cached, a);
+    if (L.kv_nodes >= (int64_t(1) << 31))
+        return set_error(NNQS_E_UNSUPPORTED, "key/value cache above 2^31 nodes (T * max_unique)");
     if (n_samples == 0) return NNQS_OK;
     Arena sub(L.region);
     CondCtx *ctx = nullptr;
@@ -339,7 +348,7 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     int64_t g_cur = 0;  // tree-node id of the first prefix of the current level
     auto step = [&](int t) -> nnqs_status {
         if (cached)
-            NNQS_TRY(cond_step_cached(M, ctx, L.pref[cur], n, t, g_cur, L.parent, L.cond, st, s));
+            NNQS_TRY(cond_step_cached(M, ctx, L.pref[cur], n, t, g_cur, L.anc[cur], L.cond, st, s));
         else
             NNQS_TRY(cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s));
         NNQS_LAUNCH("k_split", s, k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts,
@@ -356,7 +365,7 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
                                                     " prefixes, above max_unique " + std::to_string(max_unique));
         NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t,
                                                                          max_unique, L.pref[cur ^ 1], L.w[cur ^ 1],
-                                                                         L.parent, g_cur, g_cur + n, st));
+                                                                         L.anc[cur], L.anc[cur ^ 1], g_cur, st));
         cur ^= 1;
         g_cur += n;
         n = next;

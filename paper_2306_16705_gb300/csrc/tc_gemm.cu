@@ -13,26 +13,29 @@
 namespace nnqs {
 namespace {
 
-// dst = bf16(W) padded; dst_lo = bf16(W - bf16(W))
-__global__ void k_to_bf16_padded(const float *__restrict__ src, int64_t N, int64_t K, int64_t Kpad,
-                                 __nv_bfloat16 *__restrict__ dst, __nv_bfloat16 *__restrict__ dst_lo) {
-    const int64_t total = N * Kpad;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = i / Kpad, k = i % Kpad;
-        const float v = k < K ? src[n * K + k] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        dst[i] = hi;
-        dst_lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
-}
+// every conversion of one tc_weights_prepare in one launch: job y is a
+// padded copy (with its low part) or a transposed copy of one slot
+struct ConvJob {
+    int64_t src, rows, cols, pad, dst;  // dst [rows][pad] BF16; source W [N][K] FP32
+    int trans;                          // 0: rows = N, cols = K; 1: rows = K, cols = N (dst = W^T)
+};
+constexpr int kMaxConvJobs = 40;
+struct ConvTab {
+    int n;
+    ConvJob j[kMaxConvJobs];
+};
 
-// transposed copy: dst[k][n] = W[n][k] for n < N, zero for N <= n < Npad
-__global__ void k_to_bf16_transposed(const float *__restrict__ src, int64_t N, int64_t K, int64_t Npad,
-                                     __nv_bfloat16 *__restrict__ dst) {
-    const int64_t total = K * Npad;
+__global__ void k_to_bf16_all(const float *__restrict__ params, ConvTab tab, __nv_bfloat16 *__restrict__ base,
+                              __nv_bfloat16 *__restrict__ base_lo) {
+    const ConvJob jb = tab.j[blockIdx.y];
+    const int64_t total = jb.rows * jb.pad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = i / Npad, n = i % Npad;
-        dst[i] = __float2bfloat16_rn(n < N ? src[n * K + k] : 0.f);
+        const int64_t r = i / jb.pad, c = i % jb.pad;
+        float v = 0.f;
+        if (c < jb.cols) v = jb.trans ? params[jb.src + c * jb.rows + r] : params[jb.src + r * jb.cols + c];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        base[jb.dst + i] = hi;
+        if (!jb.trans) base_lo[jb.dst + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
 }
 
@@ -84,9 +87,19 @@ nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s, int64_t
 // N per CTA: the whole N when it fits in 64 columns, else 128-column tiles
 // when N is a multiple of 128, else 64-column tiles (epilogue slabs are 64
 // columns wide)
-int nt_for(int64_t N) {
+int nt_base(int64_t N) {
     if (N <= 64) return (int)((N + 15) / 16 * 16);
     return (N % 128 == 0) ? 128 : 64;
+}
+
+// for few row tiles (the sampler's one-token steps) the N tiles are halved
+// down to 16 columns until two CTAs per SM are launched: a CTA's epilogue
+// then covers fewer columns and the launch finishes sooner
+int nt_for(int64_t M, int64_t N) {
+    int nt = nt_base(N);
+    const int64_t mt = (M + tc::kTileM - 1) / tc::kTileM;
+    while (nt > 16 && nt % 32 == 0 && mt * ((N + nt - 1) / nt) < 2 * 152) nt /= 2;
+    return nt;
 }
 
 int tmem_cols_for(int Nt) {
@@ -122,21 +135,25 @@ void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
 }
 
 nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeights &w, cudaStream_t s) {
+    ConvTab tab{};
+    auto flush = [&]() -> nnqs_status {
+        if (tab.n == 0) return NNQS_OK;
+        dim3 grid(64, (unsigned)tab.n);
+        NNQS_LAUNCH("k_to_bf16", s,
+                    k_to_bf16_all<<<grid, 256, 0, s>>>(params, tab, static_cast<__nv_bfloat16 *>(w.bf16),
+                                                       static_cast<__nv_bfloat16 *>(w.bf16_lo)));
+        tab.n = 0;
+        return NNQS_OK;
+    };
     for (int sl = 0; sl < w.n_slots; ++sl) {
         if (sl / 4 == M->L && sl % 4 != 0) continue;
-        const int64_t N = w.rows[sl], K = w.cols[sl], Kp = w.pcols[sl];
-        __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(w.bf16) + w.off[sl];
-        __nv_bfloat16 *dst_lo = static_cast<__nv_bfloat16 *>(w.bf16_lo) + w.off[sl];
-        NNQS_LAUNCH("k_to_bf16", s,
-                    k_to_bf16_padded<<<(unsigned)std::min<int64_t>((N * Kp + 255) / 256, 4096), 256, 0, s>>>(
-                        params + w.src[sl], N, K, Kp, dst, dst_lo));
-        const int64_t Np = w.tpcols[sl];
-        __nv_bfloat16 *tdst = static_cast<__nv_bfloat16 *>(w.bf16) + w.toff[sl];
-        NNQS_LAUNCH("k_to_bf16", s,
-                    k_to_bf16_transposed<<<(unsigned)std::min<int64_t>((K * Np + 255) / 256, 4096), 256, 0, s>>>(
-                        params + w.src[sl], N, K, Np, tdst));
+        const int64_t N = w.rows[sl], K = w.cols[sl];
+        if (tab.n + 2 > kMaxConvJobs) NNQS_TRY(flush());
+        // W [N][K] -> [N][Kpad] (+ low parts); W^T [K][Npad]
+        tab.j[tab.n++] = ConvJob{w.src[sl], N, K, w.pcols[sl], w.off[sl], 0};
+        tab.j[tab.n++] = ConvJob{w.src[sl], K, N, w.tpcols[sl], w.toff[sl], 1};
     }
-    return NNQS_OK;
+    return flush();
 }
 
 nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX,
@@ -154,7 +171,7 @@ nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const flo
     g.M = rows;
     g.N = in;
     g.K = out;
-    g.Nt = nt_for(g.N);
+    g.Nt = nt_for(g.M, g.N);
     g.vec_x = (out % 4 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
@@ -178,7 +195,9 @@ nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t 
     g.M = out;
     g.N = in;
     g.K = rows;
-    g.Nt = nt_for(g.N);
+    g.Nt = nt_base(g.N);
+    g.vec_x = (out % 4 == 0) && (in % 4 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0) &&
+              (reinterpret_cast<uintptr_t>(X) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = st;
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
@@ -223,7 +242,7 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     g.M = rows;
     g.N = w.rows[slot];
     g.K = in;
-    g.Nt = nt_for(g.N);
+    g.Nt = nt_for(g.M, g.N);
     g.vec_x = (in % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;

@@ -138,7 +138,7 @@ struct Args {
     int64_t ldy;
     int64_t M, N, K;
     int Nt;                // N per CTA (multiple of 16, <= 256)
-    int vec_x;             // X rows 16-byte aligned (float4 loads allowed)
+    int vec_x;             // X rows (TRANS: X and Xb rows) 16-byte aligned: float4 loads allowed
     const float *Xb;       // TRANS: second operand [K][ldb]
     int64_t ldb;
     int64_t kchunk;        // TRANS: reduction rows per blockIdx.z (multiple of 64)
@@ -201,7 +201,53 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
     // operand granules of one K chunk, held in registers as packed BF16:
     // 8 A granules and up to 8 B granules per thread
     uint4 ra[8], rb[8], ra2[8], rb2[8];  // ra2/rb2: low parts (SPLIT)
+    // TRANS with 16-byte rows (vec_x): a thread loads float4s of 4 consecutive
+    // m (or n) for the 8 k of one granule and transposes them in registers
+    // into 4 granules; granule i = 4q + j is row 4 (tid & 31) + j, k-granule
+    // (tid >> 5) + 4q of A, and row 4 (p % (Nt/4)) + j, k-granule p / (Nt/4)
+    // with p = tid + 128 q of B
+    const bool tvec = TRANS && g.vec_x;
+    auto load4x8 = [&](const float *src, int64_t ld, int64_t lim, int64_t c0i, int64_t k0g, float (&v)[4][8]) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t k = k0g + e;
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < kend) {
+                if (c0i + 3 < lim) {
+                    f = __ldg(reinterpret_cast<const float4 *>(src + k * ld + c0i));
+                } else {
+                    if (c0i < lim) f.x = __ldg(src + k * ld + c0i);
+                    if (c0i + 1 < lim) f.y = __ldg(src + k * ld + c0i + 1);
+                    if (c0i + 2 < lim) f.z = __ldg(src + k * ld + c0i + 2);
+                }
+            }
+            v[0][e] = f.x;
+            v[1][e] = f.y;
+            v[2][e] = f.z;
+            v[3][e] = f.w;
+        }
+    };
     auto load_chunk = [&](int64_t k0) {
+        if (tvec) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                float v[4][8];
+                load4x8(g.X, g.ldx, g.M, m0 + 4 * (tid & 31), k0 + 8 * ((tid >> 5) + 4 * q), v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ra[4 * q + j] = pack8(v[j]);
+            }
+            const int nq = Nt / 4;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int pidx = tid + kThreads * q;
+                if (pidx >= 8 * nq) break;
+                float v[4][8];
+                load4x8(g.Xb, g.ldb, g.N, n0 + 4 * (pidx % nq), k0 + 8 * (pidx / nq), v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) rb[4 * q + j] = pack8(v[j]);
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float v[8];
@@ -265,6 +311,22 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
         }
     };
     auto store_chunk = [&]() {
+        if (tvec) {
+            const int nq = Nt / 4;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = 4 * (tid & 31) + (i & 3), c = (tid >> 5) + 4 * (i >> 2);
+                *reinterpret_cast<uint4 *>(sA + r * 128 + ((c ^ (r & 7)) << 4)) = ra[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int pidx = tid + kThreads * (i >> 2);
+                if (pidx >= 8 * nq) break;
+                const int r = 4 * (pidx % nq) + (i & 3), c = pidx / nq;
+                *reinterpret_cast<uint4 *>(sB + r * 128 + ((c ^ (r & 7)) << 4)) = rb[i];
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int it = tid + i * kThreads;
@@ -317,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
         }
     } else {
         // 64-column slabs: TMEM -> shared (thread = row) -> global (a warp
-        // writes 32 consecutive floats of one row), epilogue applied on the way
+        // writes consecutive floats of a row), epilogue applied on the way
         // out.  The operand buffers (32 KB) are free once the MMAs retired; the
         // slab [128][64] is XOR-swizzled by the row so both phases are free of
         // bank conflicts.  Residual and bias values of a batch are loaded before
@@ -328,37 +390,42 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
         const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
         const int64_t zoff = TRANS ? int64_t(blockIdx.z) * g.M * g.ldy : 0;
         for (int c0 = 0; c0 < Nt; c0 += 64) {
+            const int sw = min(64, Nt - c0);  // slab width, a multiple of 16
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (c0 + 16 * q >= Nt) break;
+                if (16 * q >= sw) break;
                 uint32_t r[16];
                 tmem_ld16(lane_base + uint32_t(c0 + 16 * q), r);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) slab[row * 64 + ((16 * q + j) ^ (row & 31))] = __uint_as_float(r[j]);
             }
             __syncthreads();
-            // thread -> one column (tid & 63) of the slab and every other row
-            // starting at tid >> 6: a warp stores 32 consecutive floats of a row
-            const int cc = tid & 63, r0 = tid >> 6;
+            // thread -> one column (tid % sw) of the slab and the rows r0,
+            // r0 + rp, ... with r0 = tid / sw and rp = 128 / sw row phases:
+            // consecutive threads store consecutive floats of a row, and a
+            // narrow slab spreads its rows over more threads
+            const int rp = kThreads / sw;
+            const int cc = tid % sw, r0 = tid / sw;
             const int64_t n = n0 + c0 + cc;
-            const bool col_ok = (c0 + cc < Nt) && (n < g.N);
+            const bool col_ok = (r0 < rp) && (n < g.N);
             const float bias_v = (g.bias && col_ok) ? __ldg(g.bias + n) : 0.f;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
+            const int nrow = (kTileM + rp - 1) / rp;
+            for (int b = 0; 16 * b < nrow; ++b) {
                 float rv[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int rr = r0 + 2 * (16 * b + j);
+                    const int rr = r0 + rp * (16 * b + j);
                     const int64_t m = m0 + rr;
-                    rv[j] = ((EPI == EPI_RESID || EPI == EPI_DGELU || EPI == EPI_DRELU) && col_ok && m < g.M)
+                    rv[j] = ((EPI == EPI_RESID || EPI == EPI_DGELU || EPI == EPI_DRELU) && col_ok && rr < kTileM &&
+                             m < g.M)
                                 ? g.resid[zoff + m * g.ldy + n]
                                 : 0.f;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int rr = r0 + 2 * (16 * b + j);
+                    const int rr = r0 + rp * (16 * b + j);
                     const int64_t m = m0 + rr;
-                    if (!col_ok || m >= g.M) continue;
+                    if (!col_ok || rr >= kTileM || m >= g.M) continue;
                     const float v = slab[rr * 64 + (cc ^ (rr & 31))] + bias_v;
                     const int64_t o = zoff + m * g.ldy + n;
                     if (EPI == EPI_STORE) {
