@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "n40"
 N_SAMPLES = 16384
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FMA: SMs x lanes x 2 x max clock
+# DRAM read + write bytes per k_tc_gemm launch of this step, from one ncu capture of the current kernel
+# at this workload (profiles/k_tc_gemm_energy_grad_n40.md); None once the kernel changes
+TC_GEMM_TRAFFIC_BYTES = 359.1e6
 
 
 def parse():
@@ -309,8 +312,9 @@ def run_ours(args):
         tpk = float(peaks.get("bf16_tflops_sustained", 1700.0))
         gbs = f["bytes"] / (f["ms"] / 1e3) / 1e9
         tflops = f["flops"] / (f["ms"] / 1e3) / 1e12
+        traffic = TC_GEMM_TRAFFIC_BYTES if args.n_samples == N_SAMPLES and args.prec == "bf16x3" else None
         roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s", "frac": gbs / pk,
-                "traffic": None,
+                "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
                 "tensor_tflops": tflops, "tensor_frac_of_sustained_bf16": tflops / tpk,
                 "algorithmic_bytes_per_launch": f["bytes"] / max(1, f["launches"]),
