@@ -200,6 +200,18 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def aggregate_ranks(ms_step: float, n_u_total: int, dist, device):
+    """Replicas: the job's step time is the slowest rank's, its work the sum of
+    every rank's unique samples."""
+    import torch
+
+    t = torch.tensor([ms_step], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    nu = torch.tensor([n_u_total], device=device, dtype=torch.float64)
+    dist.all_reduce(nu)
+    return float(t.item()), int(nu.item())
+
+
 def run_ours(args):
     import torch
 
@@ -287,12 +299,7 @@ def run_ours(args):
     B.profile_enable(False)
     ms_step = float(np.mean(times))
     if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-        nu = torch.tensor([n_u_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(nu)
-        n_u_total = int(nu.item())
+        ms_step, n_u_total = aggregate_ranks(ms_step, n_u_total, dist, "cuda")
     pairs = n_u_total * info["n_terms"]
     value = pairs / (ms_step * args.steps / 1e3)
 
