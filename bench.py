@@ -36,7 +36,7 @@ N_SAMPLES = 16384
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FMA: SMs x lanes x 2 x max clock
 # DRAM read + write bytes per k_tc_gemm launch of this step, from one ncu capture of the current kernel
 # at this workload (profiles/k_tc_gemm_energy_grad_n40.md); None once the kernel changes
-TC_GEMM_TRAFFIC_BYTES = 359.1e6
+TC_GEMM_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -319,7 +319,8 @@ def run_ours(args):
         tpk = float(peaks.get("bf16_tflops_sustained", 1700.0))
         gbs = f["bytes"] / (f["ms"] / 1e3) / 1e9
         tflops = f["flops"] / (f["ms"] / 1e3) / 1e12
-        traffic = TC_GEMM_TRAFFIC_BYTES if args.n_samples == N_SAMPLES and args.prec == "bf16x3" else None
+        traffic = (TC_GEMM_TRAFFIC_BYTES if TC_GEMM_TRAFFIC_BYTES and args.n_samples == N_SAMPLES
+                   and args.prec == "bf16x3" else None)
         roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s", "frac": gbs / pk,
                 "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",

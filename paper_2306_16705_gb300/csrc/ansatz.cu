@@ -1248,8 +1248,9 @@ __global__ void k_attn_decode(const R *__restrict__ pool, const int32_t *__restr
 // (rows written to the cache pool) -> attention over the cached ancestors ->
 // out-projection + residual -> LayerNorm -> FFN in four 64-column chunks
 // (W1 chunk, GELU, W2 chunk accumulated) -> residual, keeping the residual
-// rows in shared memory, the A operands as BF16 (split hi/lo) swizzled tiles
-// and the accumulators in TMEM.  Every step does the arithmetic of the
+// rows in shared memory, the A operands as BF16 (split hi/lo) swizzled tiles,
+// the weights brought in by bulk copies of their pre-swizzled images, and the
+// accumulators in TMEM.  Every step does the arithmetic of the
 // unfused path in the same order (same LayerNorm tree, same MMA order per
 // K step, same epilogue sums, the same attention loop), so the cached
 // sampler still reproduces the recomputed conditionals bit for bit.
@@ -1275,23 +1276,24 @@ struct DecodeArgs {
     int64_t g0;
     const int32_t *anc;  // [n][Tm] ancestor nodes at depths 0..t-1
     const float *ln1g, *ln1b, *ln2g, *ln2b, *bqkv, *bo, *b1, *b2;
-    const __nv_bfloat16 *wqkv, *wqkv_lo, *wo, *wo_lo, *w1, *w1_lo, *w2, *w2_lo;  // [N][Kpad], Kpad 64 (w2: 256)
+    // swizzled shared-memory images of the weights (high part, then the low
+    // part): qkv [192 rows], out-projection [64], FFN in [256], FFN out
+    // [64 rows, 4 K blocks]
+    const __nv_bfloat16 *tqkv, *to, *t1, *t2;
     DevStatus *st;
 };
 
-__device__ __forceinline__ void cp_async16(uint8_t *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+// one bulk asynchronous copy global -> shared, completing `bytes` on mbar
+__device__ __forceinline__ void bulk_g2s(uint8_t *dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// rows [r0, r0 + nr) and K columns [k0, k0 + 64) of W [.][kpad] into a SW128
-// tile, as asynchronous 16-byte copies (completed by cp_async_wait_all)
-__device__ __forceinline__ void dec_load_b(uint8_t *dst, const __nv_bfloat16 *__restrict__ W, int kpad, int r0, int nr,
-                                           int k0) {
-    for (int it = threadIdx.x; it < nr * 8; it += dec::kThreads) {
-        const int r = it >> 3, c = it & 7;
-        cp_async16(dst + r * 128 + ((c ^ (r & 7)) << 4), W + (int64_t)(r0 + r) * kpad + k0 + c * 8);
-    }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
+                 "r"(bytes)
+                 : "memory");
 }
 
 // one 8-column granule of an A tile row: BF16 high part, and the low part
@@ -1431,9 +1433,11 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     uint8_t *bB = sb + kOffB;
     float *sH = reinterpret_cast<float *>(sb + kOffH);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + kOffBar);
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(sb + kOffBar + 8);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 16);
     const uint32_t uA = base + kOffA, uA2 = base + kOffA + 16384, uG = base + kOffG, uG2 = base + kOffG + 16384;
     const uint32_t uB = base + kOffB;
+    const uint32_t wb = tc::smem_u32(wbar);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t m0 = blockIdx.x * (int64_t)kRows;
@@ -1445,11 +1449,15 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     }
     if (tid == 0) {
         tc::mbar_init(tc::smem_u32(mbar), 1);
+        tc::mbar_init(wb, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // qkv weights (phase 0 of the weight barrier)
+        constexpr uint32_t q = kQKV * 128;
+        mbar_expect_tx(wb, SPLIT ? 2 * q : q);
+        bulk_g2s(bB, g.tqkv, q, wb);
+        if (SPLIT) bulk_g2s(bB + kQkvLo, g.tqkv + kQKV * kD, q, wb);
     }
-    // residual rows and the qkv weights
-    dec_load_b(bB, g.wqkv, kD, 0, kQKV, 0);
-    if (SPLIT) dec_load_b(bB + kQkvLo, g.wqkv_lo, kD, 0, kQKV, 0);
+    // residual rows
     for (int it = tid; it < kRows * (kD / 4); it += kThreads) {
         const int r = it >> 4, c4 = it & 15;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1459,7 +1467,6 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         sH[r * kHS + 4 * c4 + 2] = v.z;
         sH[r * kHS + 4 * c4 + 3] = v.w;
     }
-    cp_async_wait_all();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -1484,24 +1491,30 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
 
     // ---- LayerNorm 1 -> qkv
     if (tid < kRows) dec_layernorm_row(sH, tid, g.ln1g, g.ln1b, aHi, aLo, SPLIT);
+    int wissued = 1, wdone = 0;  // weight-barrier phases issued / seen complete
+    ok = __syncthreads_and(tc::mbar_wait(wb, 0) ? 1 : 0) != 0;
+    if (ok) wdone = 1;
     sync_async();
-    if (tid == 0) {
+    if (ok && tid == 0) {
         dec_mma(tmem + kColQKV, uA, uA2, uB, uB + kQkvLo, kQKV, SPLIT, false);
         tc::mma_commit(mb);
     }
-    wait_mma();
+    if (ok) wait_mma();
     if (ok) {
-        // Wo into the (idle) FFN-out tile, the FFN weights over Wqkv: copies
-        // in flight during the epilogue and the attention
-        dec_load_b(gHi, g.wo, kD, 0, kD, 0);
-        if (SPLIT) dec_load_b(gHi + 8192, g.wo_lo, kD, 0, kD, 0);
-#pragma unroll
-        for (int c = 0; c < kF / kD; ++c) {
-            dec_load_b(bB + kW1Hi + 8192 * c, g.w1, kD, kD * c, kD, 0);
-            dec_load_b(bB + kW2Hi + 8192 * c, g.w2, kF, 0, kD, kD * c);
+        // Wo into the (idle) FFN-out tile, the FFN weights over Wqkv (phase 1
+        // of the weight barrier): copies in flight during the epilogue and the
+        // attention
+        wissued = 2;
+        if (tid == 0) {
+            constexpr uint32_t bo = kD * 128, bf = kF * 128;  // 8 KB, 32 KB
+            mbar_expect_tx(wb, SPLIT ? 2 * (bo + 2 * bf) : bo + 2 * bf);
+            bulk_g2s(gHi, g.to, bo, wb);
+            bulk_g2s(bB + kW1Hi, g.t1, bf, wb);
+            bulk_g2s(bB + kW2Hi, g.t2, bf, wb);
             if (SPLIT) {
-                dec_load_b(bB + kW1Lo + 8192 * c, g.w1_lo, kD, kD * c, kD, 0);
-                dec_load_b(bB + kW2Lo + 8192 * c, g.w2_lo, kF, 0, kD, kD * c);
+                bulk_g2s(gHi + 8192, g.to + kD * kD, bo, wb);
+                bulk_g2s(bB + kW1Lo, g.t1 + kF * kD, bf, wb);
+                bulk_g2s(bB + kW2Lo, g.t2 + kD * kF, bf, wb);
             }
         }
         // q|k|v + bias into the pool row of this node (warp half: 96 columns)
@@ -1545,7 +1558,10 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
                 dec_store_granule(aHi, aLo, r, (hh0 + h) * (DH / 8) + gi, x, SPLIT);
             }
     }
-    cp_async_wait_all();
+    if (ok) {
+        ok = __syncthreads_and(tc::mbar_wait(wb, 1) ? 1 : 0) != 0;
+        if (ok) wdone = 2;
+    }
     sync_async();
     if (ok) {
         if (tid == 0) {
@@ -1625,8 +1641,9 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         }
     } else if (tid == 0) {
         if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -11;
+        // let weight copies still in flight land (bounded) before the CTA ends
+        for (int p = wdone; p < wissued; ++p) tc::mbar_wait(wb, (uint32_t)(p & 1));
     }
-    cp_async_wait_all();
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -1949,8 +1966,8 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     A.xf = keep ? a.take<R>(C * M->N) : nullptr;
     // split-K / column-reduction partials: enough for the largest weight
     const int64_t wmax = std::max<int64_t>({3 * d * d, F * d, P * P, P * (int64_t)M->N});
-    // split-K partials of weight gradients: ~300 splits of a layer matrix
-    A.scr.elems = size_t(std::max<int64_t>({8 * wmax, 4 * 152 * std::max<int64_t>(F, P) * 5, 300 * F * d}));
+    // split-K partials of weight gradients: ~600 splits of a layer matrix
+    A.scr.elems = size_t(std::max<int64_t>({8 * wmax, 4 * 152 * std::max<int64_t>(F, P) * 5, 640 * F * d}));
     A.scr.buf = a.take<R>(A.scr.elems);
     A.scr.ctr = a.take<unsigned>(64);
 }
@@ -2376,8 +2393,6 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
                                cudaStream_t s) {
     if (n == 0) return NNQS_OK;
     const auto &Lw = V.layer[l];
-    const __nv_bfloat16 *hi = static_cast<const __nv_bfloat16 *>(w.bf16);
-    const __nv_bfloat16 *lo = static_cast<const __nv_bfloat16 *>(w.bf16_lo);
     DecodeArgs g{};
     g.h = h;
     g.n = n;
@@ -2396,14 +2411,11 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
     g.bo = Lw.bo;
     g.b1 = Lw.b1;
     g.b2 = Lw.b2;
-    g.wqkv = hi + w.off[tc_slot(l, 0)];
-    g.wqkv_lo = lo + w.off[tc_slot(l, 0)];
-    g.wo = hi + w.off[tc_slot(l, 1)];
-    g.wo_lo = lo + w.off[tc_slot(l, 1)];
-    g.w1 = hi + w.off[tc_slot(l, 2)];
-    g.w1_lo = lo + w.off[tc_slot(l, 2)];
-    g.w2 = hi + w.off[tc_slot(l, 3)];
-    g.w2_lo = lo + w.off[tc_slot(l, 3)];
+    const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(w.tiles);
+    g.tqkv = tiles + w.tile_off[tc_slot(l, 0)];
+    g.to = tiles + w.tile_off[tc_slot(l, 1)];
+    g.t1 = tiles + w.tile_off[tc_slot(l, 2)];
+    g.t2 = tiles + w.tile_off[tc_slot(l, 3)];
     g.st = st;
     // work per launch (for the profile): the four GEMMs of the layer
     note_work("k_decode_layer", 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),

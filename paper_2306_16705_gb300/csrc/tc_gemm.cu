@@ -13,39 +13,103 @@
 namespace nnqs {
 namespace {
 
-// every conversion of one tc_weights_prepare in one launch: job y is a
-// padded copy (with its low part) or a transposed copy of one slot
+// every conversion of one tc_weights_prepare in one launch; job y is one of
+//   kind 0: W [N][K] -> dst [N][pad] BF16 and dst_lo = bf16(W - bf16(W))
+//   kind 1: W^T -> dst [K][pad] (rows = K, cols = N)
+//   kind 2: the swizzled shared-memory image of W [N][pad]: K block kc is
+//           N rows of 128 bytes at kc * N * 64 elements, granule c of row r
+//           stored at granule c ^ (r & 7); low parts in dst_lo
 struct ConvJob {
-    int64_t src, rows, cols, pad, dst;  // dst [rows][pad] BF16; source W [N][K] FP32
-    int trans;                          // 0: rows = N, cols = K; 1: rows = K, cols = N (dst = W^T)
+    int64_t src, rows, cols, pad;
+    __nv_bfloat16 *dst, *dst_lo;
+    int kind;
 };
-constexpr int kMaxConvJobs = 40;
+constexpr int kMaxConvJobs = 64;
 struct ConvTab {
     int n;
     ConvJob j[kMaxConvJobs];
 };
 
-__global__ void k_to_bf16_all(const float *__restrict__ params, ConvTab tab, __nv_bfloat16 *__restrict__ base,
-                              __nv_bfloat16 *__restrict__ base_lo) {
+__global__ void k_to_bf16_all(const float *__restrict__ params, ConvTab tab) {
     const ConvJob jb = tab.j[blockIdx.y];
     const int64_t total = jb.rows * jb.pad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / jb.pad, c = i % jb.pad;
+        int64_t r, c;
+        if (jb.kind == 2) {
+            const int64_t blk = jb.rows * 64;
+            const int64_t kc = i / blk, q = i % blk;
+            r = q / 64;
+            const int pos = (int)(q % 64);
+            c = kc * 64 + (((pos >> 3) ^ (int)(r & 7)) << 3) + (pos & 7);
+        } else {
+            r = i / jb.pad;
+            c = i % jb.pad;
+        }
         float v = 0.f;
-        if (c < jb.cols) v = jb.trans ? params[jb.src + c * jb.rows + r] : params[jb.src + r * jb.cols + c];
+        if (c < jb.cols) v = jb.kind == 1 ? params[jb.src + c * jb.rows + r] : params[jb.src + r * jb.cols + c];
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        base[jb.dst + i] = hi;
-        if (!jb.trans) base_lo[jb.dst + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        jb.dst[i] = hi;
+        if (jb.dst_lo) jb.dst_lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
 }
 
-// dW[i] += sum_z partial[z][i], splits in order
-__global__ void k_tc_reduce(const float *__restrict__ partial, int64_t splits, int64_t n, float *__restrict__ out) {
+// dW[o][i] += sum_z partial[z][.], splits in order; partial is [z][out][in],
+// or [z][in][out] when the GEMM ran transposed (trans)
+__global__ void k_tc_reduce(const float *__restrict__ partial, int64_t splits, int64_t out_n, int64_t in_n, int trans,
+                            float *__restrict__ dW) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = out_n * in_n;
     if (i >= n) return;
+    const int64_t src = trans ? (i % in_n) * out_n + i / in_n : i;
     float acc = 0.f;
-    for (int64_t z = 0; z < splits; ++z) acc += partial[z * n + i];
-    out[i] += acc;
+    for (int64_t z = 0; z < splits; ++z) acc += partial[z * n + src];
+    dW[i] += acc;
+}
+
+// the same sum with more threads: a block takes 128 consecutive partial
+// elements (a lane: 4 of them as float4), its 32 warps split the splits (warp
+// w: z = w, w + 32, ...), and the 32 warp sums are added in warp order
+__global__ void __launch_bounds__(1024) k_tc_reduce4(const float *__restrict__ partial, int64_t splits, int64_t out_n,
+                                                     int64_t in_n, int trans, float *__restrict__ dW) {
+    __shared__ float4 sh[32][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n = out_n * in_n;
+    const int64_t e0 = blockIdx.x * 128 + 4 * lane;  // first of this lane's 4 elements
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e0 < n) {
+        int64_t z = warp;
+        for (; z + 96 < splits; z += 128) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(partial + z * n + e0));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(partial + (z + 32) * n + e0));
+            const float4 c = __ldg(reinterpret_cast<const float4 *>(partial + (z + 64) * n + e0));
+            const float4 d = __ldg(reinterpret_cast<const float4 *>(partial + (z + 96) * n + e0));
+            acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+            acc.x += b.x; acc.y += b.y; acc.z += b.z; acc.w += b.w;
+            acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
+            acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
+        }
+        for (; z < splits; z += 32) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(partial + z * n + e0));
+            acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+        }
+    }
+    sh[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && e0 < n) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int w = 0; w < 32; ++w) {
+            const float4 v = sh[w][lane];
+            t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+        }
+        const float tv[4] = {t.x, t.y, t.z, t.w};
+        for (int k = 0; k < 4; ++k) {
+            const int64_t src = e0 + k;
+            if (src >= n) break;
+            // partial is [out][in], or [in][out] when transposed
+            const int64_t dst = trans ? (src % out_n) * in_n + src / out_n : src;
+            dW[dst] += tv[k];
+        }
+    }
 }
 
 int64_t kpad_of(int64_t K) { return (K + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK; }
@@ -84,12 +148,14 @@ nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s, int64_t
     return NNQS_OK;
 }
 
-// N per CTA: the whole N when it fits in 64 columns, else 128-column tiles
-// when N is a multiple of 128, else 64-column tiles (epilogue slabs are 64
-// columns wide)
+// N per CTA: the whole N rounded up to 16 when it fits in 128 columns, else
+// the widest multiple of 16 up to 128 that divides N (fewer N tiles restage
+// the A tile fewer times), else 128
 int nt_base(int64_t N) {
-    if (N <= 64) return (int)((N + 15) / 16 * 16);
-    return (N % 128 == 0) ? 128 : 64;
+    if (N <= 128) return (int)((N + 15) / 16 * 16);
+    for (int nt = 128; nt >= 16; nt -= 16)
+        if (N % nt == 0) return nt;
+    return 128;
 }
 
 // for few row tiles (the sampler's one-token steps) the N tiles are halved
@@ -99,6 +165,7 @@ int nt_for(int64_t M, int64_t N) {
     int nt = nt_base(N);
     const int64_t mt = (M + tc::kTileM - 1) / tc::kTileM;
     while (nt > 16 && nt % 32 == 0 && mt * ((N + nt - 1) / nt) < 2 * 152) nt /= 2;
+    if (nt % 16 != 0) nt = (nt + 15) / 16 * 16;
     return nt;
 }
 
@@ -132,6 +199,12 @@ void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
     }
     t.bf16 = a.take<__nv_bfloat16>(size_t(total));
     t.bf16_lo = a.take<__nv_bfloat16>(size_t(total));
+    int64_t tiles = 0;
+    for (int sl = 0; sl < 4 * M->L; ++sl) {
+        t.tile_off[sl] = tiles;
+        tiles += 2 * int64_t(t.rows[sl]) * t.pcols[sl];
+    }
+    t.tiles = a.take<__nv_bfloat16>(size_t(std::max<int64_t>(tiles, 1)));
 }
 
 nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeights &w, cudaStream_t s) {
@@ -139,19 +212,20 @@ nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeigh
     auto flush = [&]() -> nnqs_status {
         if (tab.n == 0) return NNQS_OK;
         dim3 grid(64, (unsigned)tab.n);
-        NNQS_LAUNCH("k_to_bf16", s,
-                    k_to_bf16_all<<<grid, 256, 0, s>>>(params, tab, static_cast<__nv_bfloat16 *>(w.bf16),
-                                                       static_cast<__nv_bfloat16 *>(w.bf16_lo)));
+        NNQS_LAUNCH("k_to_bf16", s, k_to_bf16_all<<<grid, 256, 0, s>>>(params, tab));
         tab.n = 0;
         return NNQS_OK;
     };
+    __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(w.bf16), *lo = static_cast<__nv_bfloat16 *>(w.bf16_lo);
+    __nv_bfloat16 *tl = static_cast<__nv_bfloat16 *>(w.tiles);
     for (int sl = 0; sl < w.n_slots; ++sl) {
         if (sl / 4 == M->L && sl % 4 != 0) continue;
-        const int64_t N = w.rows[sl], K = w.cols[sl];
-        if (tab.n + 2 > kMaxConvJobs) NNQS_TRY(flush());
-        // W [N][K] -> [N][Kpad] (+ low parts); W^T [K][Npad]
-        tab.j[tab.n++] = ConvJob{w.src[sl], N, K, w.pcols[sl], w.off[sl], 0};
-        tab.j[tab.n++] = ConvJob{w.src[sl], K, N, w.tpcols[sl], w.toff[sl], 1};
+        const int64_t N = w.rows[sl], K = w.cols[sl], Kp = w.pcols[sl];
+        if (tab.n + 3 > kMaxConvJobs) NNQS_TRY(flush());
+        tab.j[tab.n++] = ConvJob{w.src[sl], N, K, Kp, hi + w.off[sl], lo + w.off[sl], 0};
+        tab.j[tab.n++] = ConvJob{w.src[sl], K, N, w.tpcols[sl], hi + w.toff[sl], nullptr, 1};
+        if (sl < 4 * M->L)
+            tab.j[tab.n++] = ConvJob{w.src[sl], N, K, Kp, tl + w.tile_off[sl], tl + w.tile_off[sl] + N * Kp, 2};
     }
     return flush();
 }
@@ -187,13 +261,20 @@ nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const flo
 nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t out, const float *X, int64_t in,
                          float *dW, float *scratch, size_t scratch_elems, DevStatus *st) {
     if (rows == 0) return NNQS_OK;
+    // dW = dY^T X ([out][in]) or its transpose X^T dY ([in][out]): the
+    // orientation whose 128-row tiles and N tiles waste fewer padded rows
+    auto padded = [](int64_t M, int64_t N) {
+        const int64_t nt = nt_base(N);
+        return ((M + tc::kTileM - 1) / tc::kTileM * tc::kTileM) * ((N + nt - 1) / nt * nt);
+    };
+    const bool swap = padded(in, out) < padded(out, in);
     tc::Args g{};
-    g.X = dY;
-    g.ldx = out;
-    g.Xb = X;
-    g.ldb = in;
-    g.M = out;
-    g.N = in;
+    g.X = swap ? X : dY;
+    g.ldx = swap ? in : out;
+    g.Xb = swap ? dY : X;
+    g.ldb = swap ? out : in;
+    g.M = swap ? in : out;
+    g.N = swap ? out : in;
     g.K = rows;
     g.Nt = nt_base(g.N);
     g.vec_x = (out % 4 == 0) && (in % 4 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0) &&
@@ -202,19 +283,25 @@ nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t 
     g.st = st;
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
     const int64_t tiles = ((g.M + tc::kTileM - 1) / tc::kTileM) * ntn;
-    int64_t splits = std::max<int64_t>(1, (2 * 152 + tiles - 1) / tiles);
+    // about four CTAs per SM over the row splits
+    int64_t splits = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
     splits = std::min<int64_t>(splits, (rows + tc::kChunkK - 1) / tc::kChunkK);
     splits = std::min<int64_t>(splits, (int64_t)(scratch_elems / size_t(out * in)));
     if (splits < 1) return set_error(NNQS_E_WORKSPACE, "tensor-core weight gradient: scratch too small");
     g.kchunk = ((rows + splits - 1) / splits + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK;
     splits = (rows + g.kchunk - 1) / g.kchunk;
     g.Y = scratch;
-    g.ldy = in;
+    g.ldy = g.N;
     note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
               4.0 * double(rows) * (out + in) + 4.0 * double(splits) * out * in);
     NNQS_TRY((launch<tc::EPI_STORE, true>(g, ntn, s, splits)));
-    NNQS_LAUNCH("k_tc_reduce", s,
-                k_tc_reduce<<<grid_for(out * in, 256), 256, 0, s>>>(scratch, splits, out * in, dW));
+    if ((out * in) % 4 == 0)
+        NNQS_LAUNCH("k_tc_reduce", s,
+                    k_tc_reduce4<<<(unsigned)((out * in + 127) / 128), 1024, 0, s>>>(scratch, splits, out, in,
+                                                                                    swap ? 1 : 0, dW));
+    else
+        NNQS_LAUNCH("k_tc_reduce", s,
+                    k_tc_reduce<<<grid_for(out * in, 256), 256, 0, s>>>(scratch, splits, out, in, swap ? 1 : 0, dW));
     return NNQS_OK;
 }
 

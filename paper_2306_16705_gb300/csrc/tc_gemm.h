@@ -16,6 +16,11 @@ struct TcWeights {
     int64_t src[4 * 64 + 1] = {};  // offset of the FP32 source matrix in the parameter vector
     int64_t toff[4 * 64 + 1] = {};  // transposed copy W^T [cols][pad(rows)] for input gradients
     int32_t tpcols[4 * 64 + 1] = {};
+    // per forward slot, the shared-memory image of every 64-column K block
+    // (rows of 128 bytes, 16-byte granules XOR-swizzled by the row), high part
+    // at tile_off, low part right after: one bulk copy puts a block in place
+    void *tiles = nullptr;
+    int64_t tile_off[4 * 64 + 1] = {};
     DevStatus *st = nullptr;       // where a timed-out wait is recorded
 };
 
