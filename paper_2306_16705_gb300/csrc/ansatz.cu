@@ -1343,60 +1343,69 @@ __device__ __forceinline__ void dec_layernorm_row(const float *sH, int r, const 
     }
 }
 
-// NH consecutive heads of one prefix: the per-head arithmetic of
-// attn_decode_row, with the ancestor loop outside so that the keys and values
-// of all NH heads of an ancestor are loaded together, and the next
-// ancestor's node id fetched one step ahead
-template <int DH, int NH>
-__device__ __forceinline__ void dec_attention_heads(const float *__restrict__ pool, const int32_t *__restrict__ anc_row,
-                                                    int64_t self, int t, int L, int l, int hh0, float (&o)[NH][DH]) {
+// Head hh of NR prefixes (rows r0, r0 + 1, ...): the per-head arithmetic of
+// attn_decode_row for each row, with the ancestor loop outside so that the
+// keys and values of the NR rows are loaded together.  Threads hh = 0..H-1
+// of a row group sit in consecutive lanes, so a warp's load covers whole
+// 256-byte key (or value) segments of a few rows.
+// Rows at or past n (the tail of the last CTA) read row `safe` (a valid row)
+// instead and give zeros.
+template <int DH, int NR>
+__device__ __forceinline__ void dec_attention_rows(const float *__restrict__ pool, const int32_t *__restrict__ anc,
+                                                   int Tm, int64_t g0, int64_t r0, int64_t safe, int64_t n, int t,
+                                                   int L, int l, int hh, float (&o)[NR][DH]) {
     constexpr int d = dec::kD;
     const int64_t row = 3 * (int64_t)d;
     const float scale = 1.0f / sqrtf(float(DH));
-    float qv[NH][DH], acc[NH][DH], m[NH], lsum[NH];
-    const float *qp = pool + (self * L + l) * row + hh0 * DH;
+    float qv[NR][DH], acc[NR][DH], m[NR], lsum[NR];
+    bool ok[NR];
+    int64_t rr[NR];
 #pragma unroll
-    for (int h = 0; h < NH; ++h) {
+    for (int k = 0; k < NR; ++k) {
+        ok[k] = r0 + k < n;
+        rr[k] = ok[k] ? r0 + k : safe;
+        const float *qp = pool + ((g0 + rr[k]) * L + l) * row + hh * DH;
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
-            qv[h][c] = qp[h * DH + c] * scale;
-            acc[h][c] = 0.f;
+            qv[k][c] = qp[c] * scale;
+            acc[k][c] = 0.f;
         }
-        m[h] = neg_inf<float>();
-        lsum[h] = 0.f;
+        m[k] = neg_inf<float>();
+        lsum[k] = 0.f;
     }
-    int64_t node = t > 0 ? (int64_t)anc_row[0] : self;
     for (int j = 0; j <= t; ++j) {
-        const int64_t next = j + 1 < t ? (int64_t)anc_row[j + 1] : self;
-        const float *base = pool + (node * L + l) * row;
-        float kk[NH * DH], vv[NH * DH];
+        float kk[NR][DH], vv[NR][DH];
 #pragma unroll
-        for (int e = 0; e < NH * DH; e += 4) {
-            const float4 k4 = *reinterpret_cast<const float4 *>(base + d + hh0 * DH + e);
-            const float4 v4 = *reinterpret_cast<const float4 *>(base + 2 * d + hh0 * DH + e);
-            kk[e] = k4.x; kk[e + 1] = k4.y; kk[e + 2] = k4.z; kk[e + 3] = k4.w;
-            vv[e] = v4.x; vv[e + 1] = v4.y; vv[e + 2] = v4.z; vv[e + 3] = v4.w;
+        for (int k = 0; k < NR; ++k) {
+            const int64_t node = j < t ? (int64_t)anc[rr[k] * Tm + j] : g0 + rr[k];
+            const float *base = pool + (node * L + l) * row;
+#pragma unroll
+            for (int e = 0; e < DH; e += 4) {
+                const float4 k4 = *reinterpret_cast<const float4 *>(base + d + hh * DH + e);
+                const float4 v4 = *reinterpret_cast<const float4 *>(base + 2 * d + hh * DH + e);
+                kk[k][e] = k4.x; kk[k][e + 1] = k4.y; kk[k][e + 2] = k4.z; kk[k][e + 3] = k4.w;
+                vv[k][e] = v4.x; vv[k][e + 1] = v4.y; vv[k][e + 2] = v4.z; vv[k][e + 3] = v4.w;
+            }
         }
 #pragma unroll
-        for (int h = 0; h < NH; ++h) {
+        for (int k = 0; k < NR; ++k) {
             float sc = 0;
 #pragma unroll
-            for (int c = 0; c < DH; ++c) sc += qv[h][c] * kk[h * DH + c];
-            const float mn = sc > m[h] ? sc : m[h];
-            const float corr = exp_<float>(m[h] - mn);
+            for (int c = 0; c < DH; ++c) sc += qv[k][c] * kk[k][c];
+            const float mn = sc > m[k] ? sc : m[k];
+            const float corr = exp_<float>(m[k] - mn);
             const float p = exp_<float>(sc - mn);
-            lsum[h] = lsum[h] * corr + p;
+            lsum[k] = lsum[k] * corr + p;
 #pragma unroll
-            for (int c = 0; c < DH; ++c) acc[h][c] = acc[h][c] * corr + p * vv[h * DH + c];
-            m[h] = mn;
+            for (int c = 0; c < DH; ++c) acc[k][c] = acc[k][c] * corr + p * vv[k][c];
+            m[k] = mn;
         }
-        node = next;
     }
 #pragma unroll
-    for (int h = 0; h < NH; ++h) {
-        const float inv = 1.0f / lsum[h];
+    for (int k = 0; k < NR; ++k) {
+        const float inv = 1.0f / lsum[k];
 #pragma unroll
-        for (int c = 0; c < DH; ++c) o[h][c] = acc[h][c] * inv;
+        for (int c = 0; c < DH; ++c) o[k][c] = ok[k] ? acc[k][c] * inv : 0.f;
     }
 }
 
@@ -1423,7 +1432,7 @@ __device__ __forceinline__ void dec_mma(uint32_t tmem, uint32_t aHi, uint32_t aL
 template <bool SPLIT, int DH>
 __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g) {
     using namespace dec;
-    constexpr int H = kD / DH, NH = H / 2;  // heads per thread (two threads per row)
+    constexpr int H = kD / DH, NR = kRows * H / kThreads;  // rows per thread in the attention
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -1536,26 +1545,19 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     }
     __syncthreads();  // this CTA's pool rows are visible to all its threads
     if (ok) {
-        // ---- attention (thread: one row, half the heads) -> A tile
-        const int r = tid & (kRows - 1);
-        const int hh0 = (tid >> 7) * NH;
-        float o[NH][DH];
-        if (m0 + r < g.n) {
-            dec_attention_heads<DH, NH>(g.pool, g.anc + (m0 + r) * g.Tm, g.g0 + m0 + r, g.t, g.L, g.l, hh0, o);
-        } else {
+        // ---- attention (thread: head tid % H of the NR rows of group tid / H) -> A tile
+        const int hh = tid % H;
+        const int r0 = (tid / H) * NR;
+        float o[NR][DH];
+        dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g.g0, m0 + r0, m0, g.n, g.t, g.L, g.l, hh, o);
 #pragma unroll
-            for (int h = 0; h < NH; ++h)
-#pragma unroll
-                for (int c = 0; c < DH; ++c) o[h][c] = 0.f;
-        }
-#pragma unroll
-        for (int h = 0; h < NH; ++h)
+        for (int k = 0; k < NR; ++k)
 #pragma unroll
             for (int gi = 0; gi < DH / 8; ++gi) {
                 float x[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = o[h][8 * gi + e];
-                dec_store_granule(aHi, aLo, r, (hh0 + h) * (DH / 8) + gi, x, SPLIT);
+                for (int e = 0; e < 8; ++e) x[e] = o[k][8 * gi + e];
+                dec_store_granule(aHi, aLo, r0 + k, hh * (DH / 8) + gi, x, SPLIT);
             }
     }
     if (ok) {
