@@ -1373,12 +1373,18 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
         m[k] = neg_inf<float>();
         lsum[k] = 0.f;
     }
+    // node ids of step j + 1 are read while step j's keys and values load
+    int64_t node[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) node[k] = 0 < t ? (int64_t)anc[rr[k] * Tm] : g0 + rr[k];
     for (int j = 0; j <= t; ++j) {
         float kk[NR][DH], vv[NR][DH];
+        int64_t nnext[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) nnext[k] = j + 1 < t ? (int64_t)anc[rr[k] * Tm + j + 1] : g0 + rr[k];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            const int64_t node = j < t ? (int64_t)anc[rr[k] * Tm + j] : g0 + rr[k];
-            const float *base = pool + (node * L + l) * row;
+            const float *base = pool + (node[k] * L + l) * row;
 #pragma unroll
             for (int e = 0; e < DH; e += 4) {
                 const float4 k4 = *reinterpret_cast<const float4 *>(base + d + hh * DH + e);
@@ -1400,6 +1406,8 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
             for (int c = 0; c < DH; ++c) acc[k][c] = acc[k][c] * corr + p * vv[k][c];
             m[k] = mn;
         }
+#pragma unroll
+        for (int k = 0; k < NR; ++k) node[k] = nnext[k];
     }
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -1526,21 +1534,40 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
                 bulk_g2s(bB + kW2Lo, g.t2 + kD * kF, bf, wb);
             }
         }
-        // q|k|v + bias into the pool row of this node (warp half: 96 columns)
-        float *prow = g.pool + ((g.g0 + m0 + row) * g.L + g.l) * (int64_t)kQKV;
+        // q|k|v + bias into the pool rows of the new nodes, 64 columns at a
+        // time through the (free) A tile: TMEM -> shared (thread = row, 16-byte
+        // granules XOR-swizzled by the row) -> global (16 threads per row, each
+        // row a contiguous 256-byte segment)
+        float *slab = reinterpret_cast<float *>(aHi);
+        for (int c = 0; c < kQKV / 64; ++c) {
 #pragma unroll
-        for (int b = 0; b < 6; ++b) {
-            const int c0 = 96 * half + 16 * b;
-            uint32_t r16[16];
-            tc::tmem_ld16(tl + kColQKV + c0, r16);
-            if (row_ok) {
+            for (int b = 0; b < 2; ++b) {
+                const int cl = 32 * half + 16 * b;  // column within the chunk
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColQKV + 64 * c + cl, r16);
 #pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *reinterpret_cast<float4 *>(prow + c0 + j) =
-                        make_float4(__uint_as_float(r16[j]) + g.bqkv[c0 + j], __uint_as_float(r16[j + 1]) + g.bqkv[c0 + j + 1],
-                                    __uint_as_float(r16[j + 2]) + g.bqkv[c0 + j + 2],
-                                    __uint_as_float(r16[j + 3]) + g.bqkv[c0 + j + 3]);
+                for (int q = 0; q < 4; ++q) {
+                    const int gi = (cl >> 2) + q;
+                    const int col = 64 * c + 4 * gi;
+                    *reinterpret_cast<float4 *>(slab + row * 64 + 4 * (gi ^ (row & 15))) =
+                        make_float4(__uint_as_float(r16[4 * q]) + g.bqkv[col],
+                                    __uint_as_float(r16[4 * q + 1]) + g.bqkv[col + 1],
+                                    __uint_as_float(r16[4 * q + 2]) + g.bqkv[col + 2],
+                                    __uint_as_float(r16[4 * q + 3]) + g.bqkv[col + 3]);
+                }
             }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kRows * 16 / kThreads; ++i) {
+                const int it = tid + kThreads * i;
+                const int r = it >> 4, gi = it & 15;
+                if (m0 + r < g.n) {
+                    float *prow = g.pool + ((g.g0 + m0 + r) * g.L + g.l) * (int64_t)kQKV + 64 * c;
+                    *reinterpret_cast<float4 *>(prow + 4 * gi) =
+                        *reinterpret_cast<const float4 *>(slab + r * 64 + 4 * (gi ^ (r & 15)));
+                }
+            }
+            __syncthreads();
         }
     }
     __syncthreads();  // this CTA's pool rows are visible to all its threads
