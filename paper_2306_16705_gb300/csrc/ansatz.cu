@@ -550,6 +550,104 @@ __global__ void __launch_bounds__(kColThreads) k_sum_partials(const R *__restric
     sum_partial_rows<R, 1>(partial, nblk, cols, (int)c0, (int)min(cols, c0 + 32), out, sh);
 }
 
+// ---- LayerNorm backward with its parameter gradients (FP32, d = 4 LPR)
+// k_ln_bwd_v's arithmetic per row (acc += dx), and in the same pass the column
+// sums the reverse mode needs next: out_g += sum dy xh (gain), out_b += sum dy
+// (bias) and, if out_h is given, out_h += sum of the updated acc (the bias
+// gradient of the layer whose output gradient acc now is).  Warps walk row
+// groups grid-stride, a lane keeps the sums of its 4 columns, and the sums are
+// combined in a fixed order: the rows of a warp, the warps of a block, then
+// the last block adds the blocks' partial rows in block order.
+template <int LPR>
+__global__ void __launch_bounds__(256) k_ln_bwd_sums(const float *__restrict__ x, const float *__restrict__ mean,
+                                                     const float *__restrict__ rstd, const float *__restrict__ g,
+                                                     const float *__restrict__ dy, float *__restrict__ acc,
+                                                     int64_t rows, float *__restrict__ partial, unsigned *counter,
+                                                     float *__restrict__ out_g, float *__restrict__ out_b,
+                                                     float *__restrict__ out_h) {
+    constexpr int RPW = 32 / LPR, d = 4 * LPR, NW = 8;
+    __shared__ float sh[NW * 3 * d > kColThreads * 4 ? NW * 3 * d : kColThreads * 4];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, sub = lane / LPR, l = lane % LPR, warp = threadIdx.x >> 5;
+    const int64_t gw = blockIdx.x * (int64_t)NW + warp, GW = (int64_t)gridDim.x * NW;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 gg = __ldg(reinterpret_cast<const float4 *>(g) + l);
+    float sg[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f}, shh[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t base = gw * (RPW * kLnRows); base < rows; base += GW * (RPW * kLnRows)) {
+        float4 xv[kLnRows], dv[kLnRows], av[kLnRows];
+        float mu[kLnRows], rs[kLnRows];
+#pragma unroll
+        for (int u = 0; u < kLnRows; ++u) {
+            const int64_t row = base + u * RPW + sub;
+            const bool ok = row < rows;
+            xv[u] = ok ? __ldg(reinterpret_cast<const float4 *>(x + row * d) + l) : z4;
+            dv[u] = ok ? __ldg(reinterpret_cast<const float4 *>(dy + row * d) + l) : z4;
+            av[u] = ok ? reinterpret_cast<const float4 *>(acc + row * d)[l] : z4;
+            mu[u] = ok ? mean[row] : 0.f;
+            rs[u] = ok ? rstd[row] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kLnRows; ++u) {
+            const int64_t row = base + u * RPW + sub;
+            const float hx = (xv[u].x - mu[u]) * rs[u], hy = (xv[u].y - mu[u]) * rs[u];
+            const float hz = (xv[u].z - mu[u]) * rs[u], hw = (xv[u].w - mu[u]) * rs[u];
+            const float ex = dv[u].x * gg.x, ey = dv[u].y * gg.y, ez = dv[u].z * gg.z, ew = dv[u].w * gg.w;
+            float s1 = (ex + ey) + (ez + ew);
+            float s2 = (ex * hx + ey * hy) + (ez * hz + ew * hw);
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) {
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            s1 /= float(d);
+            s2 /= float(d);
+            if (row < rows) {
+                const float r = rs[u];
+                const float4 nv = make_float4(av[u].x + r * (ex - s1 - hx * s2), av[u].y + r * (ey - s1 - hy * s2),
+                                              av[u].z + r * (ez - s1 - hz * s2), av[u].w + r * (ew - s1 - hw * s2));
+                reinterpret_cast<float4 *>(acc + row * d)[l] = nv;
+                sg[0] += dv[u].x * hx; sg[1] += dv[u].y * hy; sg[2] += dv[u].z * hz; sg[3] += dv[u].w * hw;
+                sb[0] += dv[u].x; sb[1] += dv[u].y; sb[2] += dv[u].z; sb[3] += dv[u].w;
+                shh[0] += nv.x; shh[1] += nv.y; shh[2] += nv.z; shh[3] += nv.w;
+            }
+        }
+    }
+    // rows of the warp (lanes with the same columns), in sub order
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            sg[e] += __shfl_xor_sync(0xffffffffu, sg[e], o);
+            sb[e] += __shfl_xor_sync(0xffffffffu, sb[e], o);
+            shh[e] += __shfl_xor_sync(0xffffffffu, shh[e], o);
+        }
+    if (sub == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            sh[(warp * 3 + 0) * d + 4 * l + e] = sg[e];
+            sh[(warp * 3 + 1) * d + 4 * l + e] = sb[e];
+            sh[(warp * 3 + 2) * d + 4 * l + e] = shh[e];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < 3 * d; c += blockDim.x) {
+        const int k = c / d, cc = c % d;
+        float t = 0.f;
+        for (int w = 0; w < NW; ++w) t += sh[(w * 3 + k) * d + cc];
+        partial[blockIdx.x * 3 * (int64_t)d + c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum_partial_rows<float, 4>(partial, gridDim.x, 3 * d, 0, d, out_g, sh);
+    sum_partial_rows<float, 4>(partial + d, gridDim.x, 3 * d, 0, d, out_b, sh);
+    if (out_h) sum_partial_rows<float, 4>(partial + 2 * d, gridDim.x, 3 * d, 0, d, out_h, sh);
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 // ------------------------------------------------------------------ GEMM (CUDA cores)
 // C[m][n] = sum_k A(m,k) B(n,k), A(m,k) = A[m*sAm + k*sAk], B(n,k) = B[n*sBn + k*sBk],
 // then an epilogue.  Tile 64x64x16, 256 threads, 4x4 outputs per thread.
@@ -802,6 +900,38 @@ nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *me
         NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
     else
         NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+    return NNQS_OK;
+}
+
+// LayerNorm backward (acc += dx) with its gain and bias gradients (out_g,
+// out_b) and, when out_h is given, the column sums of the updated acc: one
+// pass for FP32 rows of d = 4 LPR, else the separate kernels
+template <class R>
+nnqs_status ln_bwd_sums(cudaStream_t s, const R *x, const R *mean, const R *rstd, const R *g, const R *dy, R *acc,
+                        int64_t rows, int d, R *out_g, R *out_b, R *out_h, Scratch<R> scr) {
+    if (rows == 0) return NNQS_OK;
+    if constexpr (sizeof(R) == 4) {
+        if (ln_vec_ok<R>(d) && al16(x) && al16(g) && al16(dy) && al16(acc) && d >= 4) {
+            const int lpr = d / 4;
+            const int64_t per_block = 8 * (32 / lpr) * kLnRows;
+            int64_t nblk = std::min<int64_t>((rows + per_block - 1) / per_block, 2 * sm_count());
+            nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(3 * d))));
+#define NNQS_LNS(LPR) NNQS_LAUNCH("k_ln_bwd", s, (k_ln_bwd_sums<LPR><<<(unsigned)nblk, 256, 0, s>>>(x, mean, rstd, g, dy, acc, rows, scr.buf, scr.ctr, out_g, out_b, out_h)))
+            switch (lpr) {
+                case 1: NNQS_LNS(1); break;
+                case 2: NNQS_LNS(2); break;
+                case 4: NNQS_LNS(4); break;
+                case 8: NNQS_LNS(8); break;
+                case 16: NNQS_LNS(16); break;
+                default: NNQS_LNS(32); break;
+            }
+#undef NNQS_LNS
+            return NNQS_OK;
+        }
+    }
+    NNQS_TRY(ln_bwd<R>(s, x, mean, rstd, g, dy, acc, rows, d));
+    NNQS_TRY(colsum<R>(s, 1, dy, x, mean, rstd, rows, d, out_g, out_b, scr));
+    if (out_h) NNQS_TRY(colsum<R>(s, 0, acc, nullptr, nullptr, nullptr, rows, d, out_h, nullptr, scr));
     return NNQS_OK;
 }
 
@@ -2185,8 +2315,9 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     // final LayerNorm
     const R *hlast = A.hbuf + (int64_t)L * rows * d;
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0)));
-    NNQS_TRY(ln_bwd<R>(s, hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d));
-    NNQS_TRY(colsum<R>(s, 1, G.dtmp, hlast, A.meanf, A.rstdf, rows, d, gacc + Lo.lnf_g, gacc + Lo.lnf_b, scr));
+    // (the column sums of the new dh are the last layer's FFN-out bias gradient)
+    NNQS_TRY(ln_bwd_sums<R>(s, hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d, gacc + Lo.lnf_g,
+                            gacc + Lo.lnf_b, gacc + Lo.layer[L - 1].b2, scr));
     for (int l = L - 1; l >= 0; --l) {
         const auto &Lw = V.layer[l];
         const auto &Lg = Lo.layer[l];
@@ -2196,26 +2327,23 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         const R *qkv = A.qkv + (int64_t)l * rows * 3 * d, *o = A.o + (int64_t)l * rows * d;
         const R *u = A.u + (int64_t)l * rows * F, *gu = A.gu + (int64_t)l * rows * F;
         // FFN: hout = hmid + gelu(a2 W1^T + b1) W2^T + b2
+        // (b2's gradient came with the LayerNorm backward that produced dh)
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.b2, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr, 1, u));
         NNQS_TRY(bw_dw<R>(s, tcw, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
         NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 2), G.du, rows, F, Lw.w1, d, G.dtmp, scr));
-        NNQS_TRY(ln_bwd<R>(s, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g,
-                                                             G.dtmp, G.dh, rows, d));
-        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, rows, d, gacc + Lg.ln2_g, gacc + Lg.ln2_b, scr));
+        NNQS_TRY(ln_bwd_sums<R>(s, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g, G.dtmp, G.dh, rows, d,
+                                gacc + Lg.ln2_g, gacc + Lg.ln2_b, gacc + Lg.bo, scr));
         // attention: hmid = hin + attn(a) Wo^T + bo
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, rows, d, gacc + Lg.bo, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 1), G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
         NNQS_TRY(attn_bwd<R>(s, M->dh, qkv, o, A.lse + (int64_t)l * C * H * T, G.dtmp, G.dqkv, G.Dbuf, C, T, H, d));
         NNQS_TRY(bw_dw<R>(s, tcw, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
         NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 0), G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
-        NNQS_TRY(ln_bwd<R>(s, hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g,
-                                                             G.dtmp, G.dh, rows, d));
-        NNQS_TRY(colsum<R>(s, 1, G.dtmp, hin, A.mean1 + l * rows, A.rstd1 + l * rows, rows, d, gacc + Lg.ln1_g, gacc + Lg.ln1_b, scr));
+        NNQS_TRY(ln_bwd_sums<R>(s, hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g, G.dtmp, G.dh, rows, d,
+                                gacc + Lg.ln1_g, gacc + Lg.ln1_b, l > 0 ? gacc + Lo.layer[l - 1].b2 : nullptr, scr));
     }
     // embeddings: pos[t][c] += sum_i dh[i][t][c]; tok[v][c] += sum over inputs v
     NNQS_TRY(colsum<R>(s, 0, G.dh, nullptr, nullptr, nullptr, C, T * d, gacc + Lo.pos_emb, nullptr, scr));
