@@ -1062,6 +1062,56 @@ __global__ void k_attn_bwd_kv(const R *__restrict__ qkv, const R *__restrict__ l
 // Shared-memory attention: one CTA per sample, the sample's q|k|v rows
 // staged once (padded rows, conflict-free column reads), one thread per
 // (head, position).  Used whenever a sample's rows fit in shared memory.
+// copies between a contiguous [T][w] block in global memory and shared rows
+// of stride ld (padded against bank conflicts): 16-byte global accesses when
+// w and the pointer allow, the (row, column) of a thread advanced by adds
+template <class R>
+__device__ __forceinline__ void rows_to_smem(R *dst, int ld, const R *__restrict__ src, int T, int w) {
+    constexpr int V = int(16 / sizeof(R));
+    if (w % V == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) {
+        const int wv = w / V, nt = blockDim.x;
+        const int sr = nt / wv, sc = nt % wv;
+        int r = threadIdx.x / wv, c = threadIdx.x % wv;
+        while (r < T) {
+            const ColVec<R, V> v = ld_vec<R, V>(src + (int64_t)r * w + c * V);
+#pragma unroll
+            for (int e = 0; e < V; ++e) dst[r * ld + c * V + e] = v.v[e];
+            r += sr;
+            c += sc;
+            if (c >= wv) {
+                c -= wv;
+                ++r;
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < T * w; e += blockDim.x) dst[(e / w) * ld + e % w] = src[e];
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void smem_to_rows(R *__restrict__ dst, const R *src, int ld, int T, int w) {
+    constexpr int V = int(16 / sizeof(R));
+    if (w % V == 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+        const int wv = w / V, nt = blockDim.x;
+        const int sr = nt / wv, sc = nt % wv;
+        int r = threadIdx.x / wv, c = threadIdx.x % wv;
+        while (r < T) {
+            ColVec<R, V> v;
+#pragma unroll
+            for (int e = 0; e < V; ++e) v.v[e] = src[r * ld + c * V + e];
+            *reinterpret_cast<ColVec<R, V> *>(dst + (int64_t)r * w + c * V) = v;
+            r += sr;
+            c += sc;
+            if (c >= wv) {
+                c -= wv;
+                ++r;
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < T * w; e += blockDim.x) dst[e] = src[(e / w) * ld + e % w];
+    }
+}
+
 template <class R, int DH>
 __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R *__restrict__ lse, int T, int H,
                                 int d) {
@@ -1072,7 +1122,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
     const int64_t i = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     const R *src = qkv + i * T * 3 * d;
-    for (int e = tid; e < T * 3 * d; e += nt) sq[(e / (3 * d)) * ldq + e % (3 * d)] = src[e];
+    rows_to_smem<R>(sq, ldq, src, T, 3 * d);
     __syncthreads();
     if (tid < H * T) {
         const int hh = tid / T, q = tid % T;
@@ -1105,7 +1155,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
     }
     __syncthreads();
     R *dst = o + i * T * d;
-    for (int e = tid; e < T * d; e += nt) dst[e] = so[(e / d) * ldo + e % d];
+    smem_to_rows<R>(dst, so, ldo, T, d);
 }
 
 template <class R, int DH>
@@ -1121,11 +1171,9 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     R *sD = slse + H * T;                    // [H][T]
     const int64_t i = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < T * 3 * d; e += nt) sq[(e / (3 * d)) * ldq + e % (3 * d)] = qkv[i * T * 3 * d + e];
-    for (int e = tid; e < T * d; e += nt) {
-        sdo[(e / d) * ldo + e % d] = dout[i * T * d + e];
-        so[(e / d) * ldo + e % d] = o[i * T * d + e];
-    }
+    rows_to_smem<R>(sq, ldq, qkv + i * T * 3 * d, T, 3 * d);
+    rows_to_smem<R>(sdo, ldo, dout + i * T * d, T, d);
+    rows_to_smem<R>(so, ldo, o + i * T * d, T, d);
     for (int e = tid; e < H * T; e += nt) slse[e] = lse[i * H * T + e];
     __syncthreads();
     const R scale = R(1) / sqrt(R(DH));
@@ -1196,7 +1244,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         }
     }
     __syncthreads();
-    for (int e = tid; e < T * 3 * d; e += nt) dqkv[i * T * 3 * d + e] = sg[(e / (3 * d)) * ldq + e % (3 * d)];
+    smem_to_rows<R>(dqkv + i * T * 3 * d, sg, ldq, T, 3 * d);
 }
 
 // ------------------------------------------------------------------ head + masked log-softmax
@@ -1866,6 +1914,112 @@ __global__ void k_head_bwd(const R *__restrict__ pi, const uint8_t *__restrict__
     dz[idx] = p > R(0) || (int)tok[row] == v ? g * (((int)tok[row] == v ? R(1) : R(0)) - p) : R(0);
 }
 
+// Head reverse mode in one pass (d = VW * cv): per row r = i*T + t,
+//   dz[v] = 1/2 seed_i ([v = x_t] - pi_v) on allowed children (as k_head_bwd),
+//   dh[r][c] = sum_v dz[v] hw[v][c]                       (input gradient),
+// and the column sums head_w[v][c] += sum_r dz[v] hf[r][c], head_b[v] +=
+// sum_r dz[v], combined in a fixed order like k_colred (row phases of a
+// block, then the last block adds the blocks in block order).
+template <class R, int VW>
+__global__ void __launch_bounds__(kColThreads) k_head_bwd_fused(const R *__restrict__ pi, const uint8_t *__restrict__ tok,
+                                                                const double2 *__restrict__ seed,
+                                                                const R *__restrict__ hf, const R *__restrict__ hw,
+                                                                int64_t rows, int T, int d, int64_t rows_per_block,
+                                                                R *__restrict__ dh, R *__restrict__ partial,
+                                                                unsigned *counter, R *__restrict__ out_w,
+                                                                R *__restrict__ out_b) {
+    __shared__ R sh[5 * kColThreads * VW];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const int64_t r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
+    const int cv = d / VW, ct = min(cv, kColThreads), phases = kColThreads / ct;
+    const int p = tid / ct, j = tid % ct;
+    const int64_t pw = 4 * (int64_t)d + 4;  // partial row: head_w [4][d], head_b [4]
+    for (int v0 = 0; v0 < cv; v0 += ct) {
+        const int vc = v0 + j;
+        const bool act = p < phases && vc < cv;
+        R aw[4][VW], ab[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            ab[v] = 0;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) aw[v][e] = 0;
+        }
+        if (act) {
+            R w[4][VW];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const ColVec<R, VW> wv = ld_vec<R, VW>(hw + v * d + vc * VW);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) w[v][e] = wv.v[e];
+            }
+            for (int64_t r = r0 + p; r < r1; r += phases) {
+                const int64_t i = r / T;
+                const int tk = tok[r];
+                const R gsc = R(0.5) * (R)seed[i].x;
+                R dz[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const R pv = pi[r * 4 + v];
+                    dz[v] = pv > R(0) || tk == v ? gsc * ((tk == v ? R(1) : R(0)) - pv) : R(0);
+                }
+                const ColVec<R, VW> hv = ld_vec<R, VW>(hf + r * d + vc * VW);
+                ColVec<R, VW> o;
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    R a = 0;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) a += dz[v] * w[v][e];
+                    o.v[e] = a;
+                }
+                *reinterpret_cast<ColVec<R, VW> *>(dh + r * d + vc * VW) = o;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    ab[v] += dz[v];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) aw[v][e] += dz[v] * hv.v[e];
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) sh[(v * kColThreads + tid) * VW + e] = aw[v][e];
+        __syncthreads();
+        if (p == 0 && vc < cv) {
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    R t = 0;
+                    for (int q = 0; q < phases; ++q) t += sh[(v * kColThreads + q * ct + j) * VW + e];
+                    partial[blockIdx.x * pw + v * d + vc * VW + e] = t;
+                }
+        }
+        __syncthreads();
+        // head_b from the threads of vector column 0 (each row counted once)
+        if (v0 == 0) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sh[v * kColThreads + tid] = (act && vc == 0) ? ab[v] : R(0);
+            __syncthreads();
+            if (tid < 4) {
+                R t = 0;
+                for (int q = 0; q < phases; ++q) t += sh[tid * kColThreads + q * ct];
+                partial[blockIdx.x * pw + 4 * d + tid] = t;
+            }
+            __syncthreads();
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum_partial_rows<R, 1>(partial, gridDim.x, pw, 0, 4 * d, out_w, sh);
+    sum_partial_rows<R, 1>(partial + 4 * d, gridDim.x, pw, 0, 4, out_b, sh);
+    if (tid == 0) *counter = 0u;
+}
+
 // ------------------------------------------------------------------ phase MLP
 // z1[i][u] = b1[u] + sum over occupied qubits j of W1[u][j]; r1 = relu(z1)
 // blocked form: thread u of a block keeps weight column u and walks 32
@@ -2308,10 +2462,17 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     NNQS_TRY(linear_dw<R>(s, G.dz1, C, P, A.xf, N, gacc + Lo.ph_w1, scr));
     NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, nullptr, scr));
     // ---- head
-    NNQS_LAUNCH("k_head_bwd", s, k_head_bwd<R><<<grid_for(rows * 4, 256), 256, 0, s>>>(A.pi, A.tok, seed, C, T, G.dz));
-    NNQS_TRY(linear_dw<R>(s, G.dz, rows, 4, A.hf, d, gacc + Lo.head_w, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dz, nullptr, nullptr, nullptr, rows, 4, gacc + Lo.head_b, nullptr, scr));
-    NNQS_TRY(linear_dx<R>(s, EPI_STORE, G.dz, rows, 4, V.hw, d, G.dtmp, scr));
+    {
+        constexpr int VH = int(16 / sizeof(R));
+        int64_t nblk = std::min<int64_t>((rows + 63) / 64, 2 * sm_count());
+        nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(4 * d + 4))));
+        const int64_t rpb = (rows + nblk - 1) / nblk;
+        nblk = (rows + rpb - 1) / rpb;
+        if (d % VH == 0 && al16(A.hf) && al16(V.hw) && al16(G.dtmp))
+            NNQS_LAUNCH("k_head_bwd", s, (k_head_bwd_fused<R, VH><<<(unsigned)nblk, kColThreads, 0, s>>>(A.pi, A.tok, seed, A.hf, V.hw, rows, T, d, rpb, G.dtmp, scr.buf, scr.ctr, gacc + Lo.head_w, gacc + Lo.head_b)));
+        else
+            NNQS_LAUNCH("k_head_bwd", s, (k_head_bwd_fused<R, 1><<<(unsigned)nblk, kColThreads, 0, s>>>(A.pi, A.tok, seed, A.hf, V.hw, rows, T, d, rpb, G.dtmp, scr.buf, scr.ctr, gacc + Lo.head_w, gacc + Lo.head_b)));
+    }
     // final LayerNorm
     const R *hlast = A.hbuf + (int64_t)L * rows * d;
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0)));
