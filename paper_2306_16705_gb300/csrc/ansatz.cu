@@ -1125,7 +1125,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
     rows_to_smem<R>(sq, ldq, src, T, 3 * d);
     __syncthreads();
     if (tid < H * T) {
-        const int hh = tid / T, q = tid % T;
+        const int hh = tid % H, q = tid / H;  // heads fastest: a warp holds a few positions (even loop trips)
         const R scale = R(1) / sqrt(R(DH));
         R qv[DH], acc[DH];
 #pragma unroll
@@ -1178,7 +1178,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     __syncthreads();
     const R scale = R(1) / sqrt(R(DH));
     const bool act = tid < H * T;
-    const int hh = act ? tid / T : 0, pos = act ? tid % T : 0;
+    const int hh = act ? tid % H : 0, pos = act ? tid / H : 0;  // heads fastest
     if (act) {
         // dq_q = scale sum_{j<=q} p_qj (dp_qj - D_q) k_j,  D_q = do_q . o_q
         const int q = pos;

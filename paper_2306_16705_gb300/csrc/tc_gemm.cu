@@ -112,6 +112,56 @@ __global__ void __launch_bounds__(1024) k_tc_reduce4(const float *__restrict__ p
     }
 }
 
+// ---- tensor maps for the TMA epilogue
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// FP32 [Z][M][ld] (N valid columns) as a 3-D tensor with 32 x 128 x 1 boxes and
+// the 128-byte swizzle; false when the layout does not meet the TMA rules
+// (16-byte aligned base and row stride)
+bool make_box_map(CUtensorMap *tm, const float *base, int64_t N, int64_t M, int64_t Z, int64_t ld) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || !base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * 4) % 16 != 0 || N < 1 || M < 1 ||
+        Z < 1)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)M, (cuuint64_t)Z};
+    const cuuint64_t strides[2] = {(cuuint64_t)(ld * 4), (cuuint64_t)(M * ld * 4)};
+    const cuuint32_t box[3] = {32, (cuuint32_t)tc::kTileM, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// turns on the TMA epilogue of g when every tensor it touches has a map
+void setup_tma(tc::Args &g, int epi, int64_t Z) {
+    g.use_tma = 0;
+    if (!make_box_map(&g.tmY, g.Y, g.N, g.M, Z, g.ldy)) return;
+    if ((epi == tc::EPI_GELU || epi == tc::EPI_RELU) && !make_box_map(&g.tmY2, g.Y2, g.N, g.M, Z, g.ldy)) return;
+    if ((epi == tc::EPI_RESID || epi == tc::EPI_DGELU || epi == tc::EPI_DRELU) &&
+        !make_box_map(&g.tmR, g.resid, g.N, g.M, Z, g.ldy))
+        return;
+    g.use_tma = 1;
+}
+
 int64_t kpad_of(int64_t K) { return (K + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK; }
 
 // (N, K, source offset) of every slot
@@ -250,6 +300,7 @@ nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const flo
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
     g.resid = Z;
+    setup_tma(g, act == 1 ? tc::EPI_DGELU : act == 2 ? tc::EPI_DRELU : tc::EPI_STORE, 1);
     note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
               4.0 * double(rows) * out + 2.0 * double(in) * g.Kpad + (act ? 8.0 : 4.0) * double(rows) * in);
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
@@ -292,6 +343,7 @@ nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t 
     splits = (rows + g.kchunk - 1) / g.kchunk;
     g.Y = scratch;
     g.ldy = g.N;
+    setup_tma(g, tc::EPI_STORE, splits);
     note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
               4.0 * double(rows) * (out + in) + 4.0 * double(splits) * out * in);
     NNQS_TRY((launch<tc::EPI_STORE, true>(g, ntn, s, splits)));
@@ -333,6 +385,7 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     g.vec_x = (in % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
     g.tmem_cols = tmem_cols_for(g.Nt);
     g.st = w.st;
+    setup_tma(g, epi, 1);
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;
     // algorithmic bytes: X in, the BF16 weights (and their low parts), Y out,
     // plus the activation output or the residual read

@@ -14,6 +14,7 @@
 // Every wait is bounded: on a timeout the kernel records NNQS_E_TIMEOUT,
 // skips the epilogue and still releases its TMEM.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -144,7 +145,34 @@ struct Args {
     int64_t kchunk;        // TRANS: reduction rows per blockIdx.z (multiple of 64)
     int tmem_cols;         // power of two >= max(32, Nt)
     DevStatus *st;
+    // TMA epilogue (use_tma): 3-D FP32 tensor maps {N, M, splits} of Y, Y2 and
+    // the residual / pre-activation, 128 x 32 boxes with the 128-byte swizzle
+    int use_tma;
+    CUtensorMap tmY, tmY2, tmR;
 };
+
+// TMA: one 32-column x 128-row FP32 box between shared memory (1024-byte
+// aligned, 128-byte swizzled) and global memory
+__device__ __forceinline__ void tma_store_box(const CUtensorMap *tm, uint32_t smem, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(smem), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_box(uint32_t smem, const CUtensorMap *tm, int x, int y, int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // TRANS = false: Y = X W^T (X FP32 [M][ldx], W BF16 [N][Kpad]).
 // TRANS = true : Y = A^T B over a long K (weight gradients): A(m,k) =
@@ -155,7 +183,7 @@ struct Args {
 //   MMAs per K step, operands good to about 16 bits instead of 8, the same
 //   global traffic.  Three CTAs per SM (64 KB of operand buffers each).
 template <int EPI, bool TRANS, bool SPLIT = false>
-__global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
+__global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __grid_constant__ Args g) {
     static_assert(!(TRANS && SPLIT), "split operands are for the forward layers only");
     constexpr int kOps = (SPLIT ? 2 : 1) * (kABytes + kBBytes);
     extern __shared__ uint8_t smem_raw[];
@@ -376,6 +404,81 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(Args g) {
     if (!ok) {
         if (tid == 0) {
             if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -10;
+        }
+    } else if (g.use_tma && Nt % 32 == 0) {  // whole boxes inside this CTA's columns
+        // 32-column boxes: TMEM -> registers (thread = row) -> epilogue ->
+        // shared memory in the TMA layout (row r at 128 r bytes, 16-byte chunk
+        // q at q ^ (r & 7)) -> one bulk tensor store per box; the residual or
+        // pre-activation box arrives by TMA load first.  Rows and columns
+        // outside the tensor are dropped by the store (zeros on the load).
+        constexpr bool kNeedR = EPI == EPI_RESID || EPI == EPI_DGELU || EPI == EPI_DRELU;
+        constexpr bool kTwo = EPI == EPI_GELU || EPI == EPI_RELU;
+        uint8_t *box = sbase, *box2 = sbase + 16384;
+        const uint32_t ubox = smem_u32(box), ubox2 = smem_u32(box2);
+        const int row = warp * 32 + lane;
+        const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
+        const int zc = TRANS ? (int)blockIdx.z : 0;
+        for (int c0 = 0; c0 < Nt && ok; c0 += 32) {
+            const int x = (int)(n0 + c0);
+            if (kNeedR) {
+                if (tid == 0) {
+                    mbar_expect(mb, 16384u);
+                    tma_load_box(ubox, &g.tmR, x, (int)m0, zc, mb);
+                }
+                ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+                phase ^= 1u;
+                if (!ok) break;
+            }
+            uint32_t r[32];
+            tmem_ld16(lane_base + uint32_t(c0), *reinterpret_cast<uint32_t(*)[16]>(r));
+            tmem_ld16(lane_base + uint32_t(c0 + 16), *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int off = row * 128 + ((q ^ (row & 7)) << 4);
+                float v[4], y[4], y2[4];
+                float4 rv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (kNeedR) rv = *reinterpret_cast<const float4 *>(box + off);
+                const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int64_t n = n0 + c0 + 4 * q + e;
+                    const float bias_v = (g.bias && n < g.N) ? __ldg(g.bias + n) : 0.f;
+                    v[e] = __uint_as_float(r[4 * q + e]) + bias_v;
+                    if (EPI == EPI_STORE) {
+                        y[e] = v[e];
+                    } else if (EPI == EPI_GELU) {
+                        y[e] = v[e];
+                        y2[e] = gelu_f(v[e]);
+                    } else if (EPI == EPI_RELU) {
+                        y[e] = v[e];
+                        y2[e] = v[e] > 0.f ? v[e] : 0.f;
+                    } else if (EPI == EPI_RESID) {
+                        y[e] = rr[e] + v[e];
+                    } else if (EPI == EPI_DGELU) {
+                        y[e] = v[e] * gelu_grad_f(rr[e]);
+                    } else {
+                        y[e] = rr[e] > 0.f ? v[e] : 0.f;
+                    }
+                }
+                *reinterpret_cast<float4 *>(box + off) = make_float4(y[0], y[1], y[2], y[3]);
+                if (kTwo) *reinterpret_cast<float4 *>(box2 + off) = make_float4(y2[0], y2[1], y2[2], y2[3]);
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store_box(&g.tmY, ubox, x, (int)m0, zc);
+                if (kTwo) tma_store_box(&g.tmY2, ubox2, x, (int)m0, zc);
+                bulk_commit();
+                bulk_wait_read();
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            if (!ok) {
+                if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -12;
+                mbar_wait(mb, phase);  // a residual load still in flight lands (bounded)
+            }
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
         }
     } else {
         // 64-column slabs: TMEM -> shared (thread = row) -> global (a warp
