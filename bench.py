@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (default steps/2, min 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-samples", type=int, default=N_SAMPLES, help="N_s per step (smaller for profiling)")
+    ap.add_argument("--no-layouts", action="store_true", help="skip the grouped/ungrouped layout comparison")
     return ap.parse_args()
 
 
@@ -391,6 +392,30 @@ def run_ours(args):
             others[k] = {"ms_per_step": mso, "value": nuo * info["n_terms"] / (mso * len(to) / 1e3),
                          "unit": "pairs/s", "energy_diff_ha": abs(e[k] - e["fp64"])}
         line["other_paths"] = others
+
+    # layout comparison (Sec. 3.4): bytes of the grouped and ungrouped string
+    # tables, and one sample-aware E_loc call per sweep on this step's samples
+    if rank == 0 and world == 1 and not args.no_layouts:
+        x, w = vmc.last_samples, vmc.last_weights
+        lp = B.logpsi(model, vmc.params, x, prec)
+        ham.build_ungrouped()
+        lay = {"bytes": ham.layout_bytes(), "sweep_ms": {}}
+        outs = {}
+        for name, fl in (("groups", B.SWEEP_GROUPS), ("pairs", B.SWEEP_PAIRS), ("terms", B.SWEEP_TERMS)):
+            B.eloc(ham, x, lp, wl.n_alpha, wl.n_beta, flags=fl)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs[name] = B.eloc(ham, x, lp, wl.n_alpha, wl.n_beta, flags=fl)
+            e1.record(stream)
+            e1.synchronize()
+            lay["sweep_ms"][name] = e0.elapsed_time(e1)
+        ref = outs["groups"]
+        lay["max_abs_diff_vs_groups"] = {k: float((v - ref).abs().max()) for k, v in outs.items() if k != "groups"}
+        lay["reduction_packed"] = 1 - lay["bytes"]["grouped"] / lay["bytes"]["ungrouped"]
+        lay["reduction_bytewise"] = 1 - lay["bytes"]["grouped_bytewise"] / lay["bytes"]["ungrouped_bytewise"]
+        line["layout_comparison"] = lay
 
     # end to end through the public API with host buffers: parameters in
     # from pinned memory, energy statistics and parameters out, every step

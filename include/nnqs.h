@@ -73,9 +73,12 @@ enum { NNQS_FP64 = 0, NNQS_MIXED = 1, NNQS_FP32 = 2, NNQS_BF16X3 = 3 };
 
 /* nnqs_eloc flags: choice of the sample-aware sweep.  GROUPS walks the
  * X/Y-mask groups for every sample (Alg. 2); PAIRS walks sample pairs and
- * looks the pair's X/Y mask up in a group hash; AUTO picks the cheaper by
- * their pair counts.  Both give the same sum. */
-enum { NNQS_SWEEP_AUTO = 0, NNQS_SWEEP_GROUPS = 1, NNQS_SWEEP_PAIRS = 2 };
+ * looks the pair's X/Y mask up in a group hash; AUTO picks the cheaper of
+ * the two by their pair counts; TERMS walks every Pauli string with its own
+ * X/Y mask (the ungrouped layout the grouping of Alg. 1 replaces, Sec. 3.4;
+ * needs nnqs_ham_build_ungrouped).  All give the same sum up to the order of
+ * floating-point additions. */
+enum { NNQS_SWEEP_AUTO = 0, NNQS_SWEEP_GROUPS = 1, NNQS_SWEEP_PAIRS = 2, NNQS_SWEEP_TERMS = 3 };
 
 const char *nnqs_last_error(void);
 const char *nnqs_status_string(int status);
@@ -142,6 +145,22 @@ nnqs_status nnqs_ham_export(const nnqs_ham *H, uint64_t *xy, int64_t *off, uint6
                             double *coef);
 
 void nnqs_ham_free(nnqs_ham *H);
+
+/* Ungrouped copy of the Hamiltonian for the layout comparison of Sec. 3.4:
+ * the X/Y mask of every string ([n_terms][W] uint64, device memory owned by
+ * the handle, freed by nnqs_ham_free).  Synchronous; idempotent.  Errors:
+ * NNQS_E_INVAL (null handle or no device tables), NNQS_E_CUDA. */
+nnqs_status nnqs_ham_build_ungrouped(nnqs_ham *H);
+
+/* Bytes of the two layouts of the same strings (Sec. 3.4, Alg. 1):
+ *   bytes[0] grouped, packed masks: per group W words + 4-byte offset +
+ *            1-byte spin code, per string W words (Y/Z) + 8-byte coefficient;
+ *   bytes[1] ungrouped, packed: per string 2W words (X/Y, Y/Z) + 8 bytes;
+ *   bytes[2] grouped with one byte per qubit: per group N + 4, per string
+ *            N + 8;
+ *   bytes[3] ungrouped with one byte per qubit: per string 2N + 4 + 8.
+ * Host only. */
+nnqs_status nnqs_ham_layout_bytes(const nnqs_ham *H, int64_t bytes[4]);
 
 /* ------------------------------------------------------------------ */
 /* Ansatz: transformer amplitude + MLP phase (Sec. 3.1), number mask    */

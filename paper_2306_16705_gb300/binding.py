@@ -21,7 +21,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_TABLE_FULL, E_TIMEOUT, E_SECTOR, E_NONFINITE, E_
     E_DUPLICATE, E_WORKSPACE = range(11)
 SA, EXACT = 0, 1
 FP64, MIXED, FP32, BF16X3 = 0, 1, 2, 3
-SWEEP_AUTO, SWEEP_GROUPS, SWEEP_PAIRS = 0, 1, 2
+SWEEP_AUTO, SWEEP_GROUPS, SWEEP_PAIRS, SWEEP_TERMS = 0, 1, 2, 3
 
 _STATUS_NAMES = {0: "NNQS_OK", 1: "NNQS_E_INVAL", 2: "NNQS_E_NOMEM", 3: "NNQS_E_CUDA",
                  4: "NNQS_E_TABLE_FULL", 5: "NNQS_E_TIMEOUT", 6: "NNQS_E_SECTOR",
@@ -55,6 +55,8 @@ _SIGS = {
     "nnqs_ham_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "nnqs_ham_export": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "nnqs_ham_free": (None, [ctypes.c_void_p]),
+    "nnqs_ham_build_ungrouped": (ctypes.c_int, [ctypes.c_void_p]),
+    "nnqs_ham_layout_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "nnqs_model_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "nnqs_model_free": (None, [ctypes.c_void_p]),
     "nnqs_model_param_count": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -183,6 +185,17 @@ class Hamiltonian:
         _check(lib().nnqs_ham_info(self._h, buf))
         keys = ["n_qubits", "n_words", "n_terms", "n_groups", "max_group", "device_bytes"]
         return dict(zip(keys, list(buf)))
+
+    def build_ungrouped(self):
+        """nnqs_ham_build_ungrouped: per-string X/Y masks on the device (for
+        the NNQS_SWEEP_TERMS sweep)."""
+        _check(lib().nnqs_ham_build_ungrouped(self._h))
+
+    def layout_bytes(self) -> dict:
+        """nnqs_ham_layout_bytes: bytes of the grouped and ungrouped layouts."""
+        buf = (ctypes.c_int64 * 4)()
+        _check(lib().nnqs_ham_layout_bytes(self._h, buf))
+        return dict(zip(["grouped", "ungrouped", "grouped_bytewise", "ungrouped_bytewise"], list(buf)))
 
     def export(self):
         """Host copies (xy[G,W], off[G+1], yz[T,W], coef[T]) of the tables."""

@@ -2,10 +2,12 @@
 // layout, and dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "model.h"
@@ -140,7 +142,39 @@ void nnqs_ham_free(nnqs_ham *H) {
     cudaFree(H->d_tcoef);
     cudaFree(H->d_ghkeys);
     cudaFree(H->d_ghvals);
+    cudaFree(H->d_txy);
     delete H;
+}
+
+nnqs_status nnqs_ham_build_ungrouped(nnqs_ham *H) {
+    if (!H) return set_error(NNQS_E_INVAL, "null handle");
+    if (!H->d_gxy) return set_error(NNQS_E_INVAL, "Hamiltonian has no device tables");
+    if (H->d_txy) return NNQS_OK;
+    const int W = H->W;
+    std::vector<uint64_t> txy(size_t(std::max<int64_t>(H->n_terms, 1)) * W, 0);
+    for (int64_t g = 0; g < H->n_groups; ++g)
+        for (int64_t t = H->goff[g]; t < H->goff[g + 1]; ++t)
+            for (int w = 0; w < W; ++w) txy[size_t(t) * W + w] = H->gxy[size_t(g) * W + w];
+    const size_t bytes = txy.size() * 8;
+    cudaError_t e = cudaMalloc(&H->d_txy, bytes);
+    if (e != cudaSuccess) {
+        H->d_txy = nullptr;
+        return cuda_error(e, "cudaMalloc (ungrouped X/Y masks)");
+    }
+    e = cudaMemcpy(H->d_txy, txy.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy (ungrouped X/Y masks)");
+    H->ungrouped_bytes = bytes;
+    return NNQS_OK;
+}
+
+nnqs_status nnqs_ham_layout_bytes(const nnqs_ham *H, int64_t bytes[4]) {
+    if (!H || !bytes) return set_error(NNQS_E_INVAL, "null argument");
+    const int64_t W = H->W, T = H->n_terms, G = H->n_groups, N = H->n_qubits;
+    bytes[0] = G * (8 * W + 4 + 1) + T * (8 * W + 8);  // grouped: masks, offsets, spin codes; terms: Y/Z, coef
+    bytes[1] = T * (16 * W + 8);                       // ungrouped: X/Y, Y/Z, coef per term
+    bytes[2] = G * (N + 4) + T * (N + 8);              // grouped, one byte per qubit
+    bytes[3] = T * (2 * N + 4 + 8);                    // ungrouped, one byte per qubit (+ 4-byte Y count)
+    return NNQS_OK;
 }
 
 nnqs_status nnqs_coupled_host(const nnqs_ham *H, const uint64_t *x, int n_alpha, int n_beta, uint64_t *xp,
@@ -204,7 +238,9 @@ nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *param
                       int n_beta, int mode, int prec, int flags, double *eloc_out, void *workspace,
                       size_t workspace_bytes, nnqs_stream stream) {
     NNQS_TRY(eloc_args(H, n_lut, row_begin, n_rows, n_alpha, n_beta, mode));
-    if (flags < NNQS_SWEEP_AUTO || flags > NNQS_SWEEP_PAIRS) return set_error(NNQS_E_INVAL, "unknown flags");
+    if (flags < NNQS_SWEEP_AUTO || flags > NNQS_SWEEP_TERMS) return set_error(NNQS_E_INVAL, "unknown flags");
+    if (flags == NNQS_SWEEP_TERMS && mode == NNQS_SA && !H->d_txy)
+        return set_error(NNQS_E_INVAL, "NNQS_SWEEP_TERMS needs nnqs_ham_build_ungrouped first");
     if (n_rows > 0 && (!lut || !eloc_out)) return set_error(NNQS_E_INVAL, "null device pointer");
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == NNQS_SA) {

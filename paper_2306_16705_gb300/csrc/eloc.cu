@@ -127,6 +127,68 @@ __global__ void __launch_bounds__(kSweepThreads)
     if (active) partial[blockIdx.y * n_rows + r] = make_double2(er, ei);
 }
 
+// TERMS sweep over the ungrouped layout: every string t carries its own X/Y
+// mask, so each string tests its coupled x' = x ^ xy_t on its own (spin
+// counts, table probe) and adds coef_t (-1)^{popc(x & yz_t)} psi(x')/psi(x).
+// The cost the grouping of Alg. 1 removes: N_h probes per row instead of
+// N_XY.  grid = (row tiles of 128, string chunks).
+constexpr int kTermTile = 256;
+template <int W>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_sweep_terms(const uint64_t *__restrict__ txy, const uint64_t *__restrict__ tyz,
+                  const double *__restrict__ tcoef, int64_t t_begin, int64_t t_end, int64_t terms_per_chunk,
+                  const uint64_t *__restrict__ lut, const double2 *__restrict__ lut_lp, HashTab<W> tab,
+                  int64_t row_begin, int64_t n_rows, double2 *__restrict__ partial) {
+    __shared__ uint64_t s_xy[kTermTile * W], s_yz[kTermTile * W];
+    __shared__ double s_c[kTermTile];
+    const int64_t r = blockIdx.x * (int64_t)kSweepThreads + threadIdx.x;
+    const bool active = r < n_rows;
+    Bits<W> x{};
+    double2 lx = make_double2(0.0, 0.0);
+    if (active) {
+        x = load_bits<W>(lut, row_begin + r);
+        lx = lut_lp[row_begin + r];
+    }
+    const int64_t c0 = t_begin + blockIdx.y * terms_per_chunk;
+    const int64_t c1 = min(t_end, c0 + terms_per_chunk);
+    double er = 0.0, ei = 0.0;
+    for (int64_t tt = c0; tt < c1; tt += kTermTile) {
+        const int nt = (int)min((int64_t)kTermTile, c1 - tt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nt * W; k += kSweepThreads) {
+            s_xy[k] = txy[tt * W + k];
+            s_yz[k] = tyz[tt * W + k];
+        }
+        for (int k = threadIdx.x; k < nt; k += kSweepThreads) s_c[k] = tcoef[tt + k];
+        __syncthreads();
+        if (!active) continue;
+        for (int k = 0; k < nt; ++k) {
+            int ma = 0, mb = 0, ra = 0, rb = 0;  // mask bits and electrons it removes, per spin
+            int par = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint64_t m = s_xy[k * W + w], v = m & x.w[w];
+                ma += __popcll(m & kEven);
+                mb += __popcll(m & ~kEven);
+                ra += __popcll(v & kEven);
+                rb += __popcll(v & ~kEven);
+                par += __popcll(x.w[w] & s_yz[k * W + w]);
+            }
+            if (2 * ra != ma || 2 * rb != mb) continue;
+            Bits<W> xp;
+#pragma unroll
+            for (int w = 0; w < W; ++w) xp.w[w] = x.w[w] ^ s_xy[k * W + w];
+            const int32_t j = tab.find(xp);
+            if (j < 0) continue;
+            const double c = (par & 1) ? -s_c[k] : s_c[k];
+            const double2 q = ratio(lx, lut_lp[j]);
+            er += c * q.x;
+            ei += c * q.y;
+        }
+    }
+    if (active) partial[blockIdx.y * n_rows + r] = make_double2(er, ei);
+}
+
 // PAIRS sweep.  grid = (row tiles of 128 * kPairRows, sample chunks).
 template <int W>
 __global__ void __launch_bounds__(kSweepThreads)
@@ -225,7 +287,7 @@ __global__ void __launch_bounds__(kSweepThreads)
 }
 
 struct SaPlan {
-    bool pairs;
+    bool pairs, terms;
     int64_t row_tiles, chunks, per_chunk;
     int64_t g_begin, g_end;
     bool has_diag;
@@ -257,6 +319,20 @@ SaPlan plan_sa(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags) {
         p.pairs = work_pairs < work_groups;
     // enough CTAs for ~8 per SM
     const int64_t target = 8 * (int64_t)num_sms();
+    p.terms = flags == NNQS_SWEEP_TERMS;
+    if (p.terms) {
+        // strings of the non-diagonal groups
+        p.pairs = false;
+        p.g_begin = p.has_diag ? H->goff[1] : 0;
+        p.g_end = H->n_terms;
+        const int64_t nt = p.g_end - p.g_begin;
+        p.row_tiles = std::max<int64_t>(1, (n_rows + kSweepThreads - 1) / kSweepThreads);
+        int64_t max_chunks = std::max<int64_t>(1, (nt + kTermTile - 1) / kTermTile);
+        p.chunks = std::min(max_chunks, std::max<int64_t>(1, (target + p.row_tiles - 1) / p.row_tiles));
+        p.per_chunk = std::max<int64_t>(1, (nt + p.chunks - 1) / p.chunks);
+        p.chunks = nt > 0 ? (nt + p.per_chunk - 1) / p.per_chunk : 0;
+        return p;
+    }
     if (p.pairs) {
         p.row_tiles = std::max<int64_t>(1, (n_rows + kSweepThreads * kPairRows - 1) / (kSweepThreads * kPairRows));
         int64_t max_chunks = std::max<int64_t>(1, (n_lut + kPairTile - 1) / kPairTile);
@@ -298,7 +374,13 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
     const double2 *lp2 = reinterpret_cast<const double2 *>(lut_lp);
     if (p.chunks > 0) {
         dim3 grid((unsigned)p.row_tiles, (unsigned)p.chunks);
-        if (p.pairs) {
+        if (p.terms) {
+            if (!H->d_txy) return set_error(NNQS_E_INVAL, "ungrouped layout not built");
+            note_work("k_sweep_terms", double(n_rows) * double(p.g_end - p.g_begin),
+                      double(p.row_tiles) * double(p.g_end - p.g_begin) * (16.0 * W + 8.0));
+            NNQS_LAUNCH("k_sweep_terms", s, k_sweep_terms<W><<<grid, kSweepThreads, 0, s>>>(H->d_txy, H->d_tyz, H->d_tcoef, p.g_begin, p.g_end,
+                                                             p.per_chunk, lut, lp2, tab, row_begin, n_rows, partial));
+        } else if (p.pairs) {
             const int maxw = H->max_xy_weight;
             // algorithmic work: one (row, sample) mask test each; bytes = one
             // read of the sample table per row tile
@@ -378,7 +460,7 @@ __global__ void __launch_bounds__(kStatThreads)
 // bytes for either sweep (the size query does not know which one a call forces)
 size_t eloc_sa_workspace(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int) {
     size_t best = 0;
-    for (int f : {NNQS_SWEEP_GROUPS, NNQS_SWEEP_PAIRS}) {
+    for (int f : {NNQS_SWEEP_GROUPS, NNQS_SWEEP_PAIRS, NNQS_SWEEP_TERMS}) {
         Arena a(nullptr);
         a.take<char>(kStatusBytes);
         if (H->W == 1)

@@ -99,6 +99,10 @@ struct nnqs_ham {
     int32_t *d_ghvals = nullptr;   // [cap]
     int64_t ghcap = 0;
     size_t device_bytes = 0;
+    // ungrouped layout (every term with its own X/Y mask), built on request
+    // for the layout comparison of Sec. 3.4 (nnqs_ham_build_ungrouped)
+    uint64_t *d_txy = nullptr;     // [T][W]
+    size_t ungrouped_bytes = 0;
 };
 
 namespace nnqs {

@@ -130,3 +130,31 @@ def test_model_layout_matches_named_shapes():
         assert (o, n) == (off, int(np.prod(shape))), name
         off += n
     assert m.n_params == off
+
+
+def test_layout_bytes_grouped_vs_ungrouped():
+    """Byte counts of the grouped layout (Alg. 1) and the ungrouped one it
+    replaces (Sec. 3.4): per-group and per-string sizes applied to the built
+    40-qubit Hamiltonian, and at 120 qubits (closed-form string and group
+    counts of dense integrals) the one-byte-per-qubit forms give 2.97 GB
+    against 4.85 GB, a 39 % reduction."""
+    from math import comb
+
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri, device=False)
+    i = ham.info()
+    T, G, N, W = i["n_terms"], i["n_groups"], i["n_qubits"], i["n_words"]
+    b = ham.layout_bytes()
+    assert b["grouped"] == G * (8 * W + 5) + T * (8 * W + 8)
+    assert b["ungrouped"] == T * (16 * W + 8)
+    assert b["grouped_bytewise"] == G * (N + 4) + T * (N + 8)
+    assert b["ungrouped_bytewise"] == T * (2 * N + 12)
+    assert b["grouped"] < b["ungrouped"]
+    n, N = 60, 120
+    T120 = 1 + N + comb(N, 2) + 4 * (N - 1) * comb(n, 2) + 12 * comb(n, 4) + 4 * comb(n, 2) ** 2
+    G120 = 1 + 2 * comb(n, 2) + 2 * comb(n, 4) + comb(n, 2) ** 2
+    d2 = G120 * (N + 4) + T120 * (N + 8)
+    d1 = T120 * (2 * N + 12)
+    assert abs(d2 / 1e9 - 2.97) < 0.01 and abs(d1 / 1e9 - 4.85) < 0.01
+    assert abs((1 - d2 / d1) - 0.39) < 0.01

@@ -190,3 +190,38 @@ def test_energy_stats_match_oracle():
         E, var = OV.energy_stats(e, w)
         assert abs(s[0] - E.real) < 1e-12 and abs(s[1] - E.imag) < 1e-12
         assert abs(s[2] - var) < 1e-12 * max(1, var) and s[3] == w.astype(np.float64).sum()
+
+
+def test_ungrouped_terms_sweep_equals_grouped(n40):
+    """The ungrouped layout (every string probes its own coupled x') gives the
+    sample-aware E_loc of the grouped sweeps (Alg. 2) up to the order of the
+    FP64 additions, on clustered 40-qubit samples and on the 70-qubit
+    two-word case."""
+    wl, ham, strings = n40
+    lut = I.clustered_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 3000, seed=11, n_centers=5)
+    lp = I.random_logpsi(len(lut), seed=12, amp_std=0.5)
+    ham.build_ungrouped()
+    a = run_gpu(ham, lut, lp, wl.n_alpha, wl.n_beta, B.SWEEP_TERMS)
+    b = run_gpu(ham, lut, lp, wl.n_alpha, wl.n_beta, B.SWEEP_GROUPS)
+    c = run_gpu(ham, lut, lp, wl.n_alpha, wl.n_beta, B.SWEEP_PAIRS)
+    sc = abs_scale(strings, lut, lp, lut, wl.n_alpha, wl.n_beta)
+    assert np.all(np.abs(a - b) <= 1e-12 * sc)
+    assert np.all(np.abs(a - c) <= 1e-12 * sc)
+    rb, nr = 101, 257
+    d = run_gpu(ham, lut, lp, wl.n_alpha, wl.n_beta, B.SWEEP_TERMS, rb, nr)
+    assert np.all(np.abs(d - a[rb:rb + nr]) <= 1e-12 * sc[rb:rb + nr])
+    # two words per bitstring
+    n = 35
+    act = [0, 9, 30, 31, 32, 34]
+    h0, eri0 = I.integrals(len(act), 5, 4)
+    h = np.zeros((n, n))
+    eri = np.zeros((n, n, n, n))
+    h[np.ix_(act, act)] = h0
+    eri[np.ix_(act, act, act, act)] = eri0
+    ham2 = B.build_pauli(h, eri)
+    ham2.build_ungrouped()
+    lut2 = I.clustered_sector_samples(n, 3, 2, 150, seed=3, n_centers=3, orbitals=act)
+    lp2 = I.random_logpsi(len(lut2), seed=4)
+    ref = OH.eloc_lut(*OH.build(h, eri), lut2, lp2, lut2, 3, 2)
+    got = run_gpu(ham2, lut2, lp2, 3, 2, B.SWEEP_TERMS)
+    assert np.all(np.abs(got - ref) <= TOL * abs_scale(OH.build(h, eri), lut2, lp2, lut2, 3, 2))
