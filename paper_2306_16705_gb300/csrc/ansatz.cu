@@ -1420,6 +1420,40 @@ __global__ void k_attn_decode(const R *__restrict__ pool, const int32_t *__restr
     for (int c = 0; c < DH; ++c) o[i * d + hh * DH + c] = ov[c];
 }
 
+// pi~(v | prefix) at position t from the head logits zr: the number mask
+// (children from which the remaining orbitals can still reach n_alpha,
+// n_beta) and a softmax over the allowed children in FP64 -> out[4]; false
+// when no child is allowed
+template <class R>
+__device__ __forceinline__ bool cond_from_logits(const uint64_t *xi, int T, int t, int n_alpha, int n_beta,
+                                                 const R (&zr)[4], double *out) {
+    int ca = 0, cb = 0;
+    for (int p2 = T - t; p2 < T; ++p2) {
+        ca += bit_of(xi, 2 * p2);
+        cb += bit_of(xi, 2 * p2 + 1);
+    }
+    const int rem = T - 1 - t;
+    double z[4], zmax = -INFINITY;
+    bool ok[4], any = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        z[v] = (double)zr[v];
+        const int aa = ca + (v & 1), bb = cb + (v >> 1);
+        ok[v] = aa <= n_alpha && bb <= n_beta && aa + rem >= n_alpha && bb + rem >= n_beta;
+        if (ok[v]) {
+            any = true;
+            zmax = fmax(zmax, z[v]);
+        }
+    }
+    double se = 0.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        if (ok[v]) se += exp(z[v] - zmax);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = ok[v] ? exp(z[v] - zmax) / se : 0.0;
+    return any;
+}
+
 // ---- fused key/value-cached decode layer on tensor cores (d = 64, F = 256)
 // One launch per layer and sampler step instead of seven: a CTA of 256
 // threads takes 128 prefixes (one new token each) through LayerNorm -> qkv
@@ -1459,6 +1493,15 @@ struct DecodeArgs {
     // [64 rows, 4 K blocks]
     const __nv_bfloat16 *tqkv, *to, *t1, *t2;
     DevStatus *st;
+    // first layer: the rows are the embeddings of the prefixes' last tokens
+    // (tok_emb[input] + pos_emb[t]) instead of h; last layer: final LayerNorm,
+    // head and the masked conditionals pi~(. | prefix) -> cond[n][4] instead
+    // of writing h
+    int first, last;
+    const uint64_t *x;  // [n][W] prefixes
+    int W, n_alpha, n_beta;
+    const float *tok_emb, *pos_emb, *lnf_g, *lnf_b, *hw, *hb;
+    double *cond;
 };
 
 // one bulk asynchronous copy global -> shared, completing `bytes` on mbar
@@ -1518,6 +1561,40 @@ __device__ __forceinline__ void dec_layernorm_row(const float *sH, int r, const 
                                    __ldg(reinterpret_cast<const float4 *>(b) + 2 * c + 1));
         const float x[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
         dec_store_granule(aHi, aLo, r, c, x, split);
+    }
+}
+
+// dec_layernorm_row's arithmetic with FP32 output values (the final LayerNorm)
+__device__ __forceinline__ void dec_layernorm_row_f32(const float *sH, int r, const float *__restrict__ g,
+                                                      const float *__restrict__ b, float (&y)[dec::kD]) {
+    float4 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        v[k] = make_float4(sH[r * dec::kHS + 4 * k], sH[r * dec::kHS + 4 * k + 1], sH[r * dec::kHS + 4 * k + 2],
+                           sH[r * dec::kHS + 4 * k + 3]);
+    float a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = ln_part_sum(v[k]);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < o; ++k) a[k] = a[k] + a[k + o];
+    const float mu = a[0] / float(dec::kD);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = ln_part_sq(v[k], mu);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < o; ++k) a[k] = a[k] + a[k + o];
+    const float rs = ln_rstd(a[0], dec::kD);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float4 o = ln_apply(v[k], mu, rs, __ldg(reinterpret_cast<const float4 *>(g) + k),
+                                  __ldg(reinterpret_cast<const float4 *>(b) + k));
+        y[4 * k] = o.x;
+        y[4 * k + 1] = o.y;
+        y[4 * k + 2] = o.z;
+        y[4 * k + 3] = o.w;
     }
 }
 
@@ -1652,11 +1729,19 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         bulk_g2s(bB, g.tqkv, q, wb);
         if (SPLIT) bulk_g2s(bB + kQkvLo, g.tqkv + kQKV * kD, q, wb);
     }
-    // residual rows
+    // residual rows (first layer: the embeddings, as k_embed_decode forms them)
     for (int it = tid; it < kRows * (kD / 4); it += kThreads) {
         const int r = it >> 4, c4 = it & 15;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (m0 + r < g.n) v = *reinterpret_cast<const float4 *>(g.h + (m0 + r) * kD + 4 * c4);
+        if (m0 + r < g.n) {
+            if (g.first) {
+                const int inp = g.t == 0 ? 4 : token_at(g.x + (m0 + r) * g.W, g.Tm, g.t - 1);
+                const float *te = g.tok_emb + inp * kD + 4 * c4, *pe = g.pos_emb + g.t * kD + 4 * c4;
+                v = make_float4(te[0] + pe[0], te[1] + pe[1], te[2] + pe[2], te[3] + pe[3]);
+            } else {
+                v = *reinterpret_cast<const float4 *>(g.h + (m0 + r) * kD + 4 * c4);
+            }
+        }
         sH[r * kHS + 4 * c4] = v.x;
         sH[r * kHS + 4 * c4 + 1] = v.y;
         sH[r * kHS + 4 * c4 + 2] = v.z;
@@ -1827,26 +1912,48 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     }
     if (ok) wait_mma();
     if (ok) {
-        // h += FFN + b2, back to global
+        // h += FFN + b2: back to global, or (last layer) into the shared rows
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int c0 = 32 * half + 16 * b;
             uint32_t r16[16];
             tc::tmem_ld16(tl + kColY + c0, r16);
-            if (row_ok) {
 #pragma unroll
-                for (int j = 0; j < 16; j += 4) {
-                    float v[4];
+            for (int j = 0; j < 16; j += 4) {
+                float v[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float y = __uint_as_float(r16[j + e]) + g.b2[c0 + j + e];
-                        v[e] = sH[row * kHS + c0 + j + e] + y;
-                    }
+                for (int e = 0; e < 4; ++e) {
+                    const float y = __uint_as_float(r16[j + e]) + g.b2[c0 + j + e];
+                    v[e] = sH[row * kHS + c0 + j + e] + y;
+                }
+                if (g.last) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) sH[row * kHS + c0 + j + e] = v[e];
+                } else if (row_ok) {
                     *reinterpret_cast<float4 *>(g.h + (m0 + row) * kD + c0 + j) = make_float4(v[0], v[1], v[2], v[3]);
                 }
             }
         }
-    } else if (tid == 0) {
+    }
+    if (g.last) {
+        // final LayerNorm (k_ln_fwd_v's sums), head logits (head_logits' sum)
+        // and the masked conditionals of the next token
+        __syncthreads();
+        if (ok && tid < kRows && m0 + tid < g.n) {
+            float hf[kD];
+            dec_layernorm_row_f32(sH, tid, g.lnf_g, g.lnf_b, hf);
+            float zr[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) zr[v] = g.hb[v];
+            for (int c = 0; c < kD; ++c)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) zr[v] += hf[c] * g.hw[v * kD + c];
+            if (!cond_from_logits<float>(g.x + (m0 + tid) * g.W, g.Tm, g.t, g.n_alpha, g.n_beta, zr,
+                                         g.cond + (m0 + tid) * 4))
+                record_status(g.st, NNQS_E_SECTOR, m0 + tid);
+        }
+    }
+    if (!ok && tid == 0) {
         if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -11;
         // let weight copies still in flight land (bounded) before the CTA ends
         for (int p = wdone; p < wissued; ++p) tc::mbar_wait(wb, (uint32_t)(p & 1));
@@ -1870,34 +1977,9 @@ __global__ void k_cond_last(const uint64_t *__restrict__ x, int W, const R *__re
     stage_head<R>(hw, d, shw);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint64_t *xi = x + i * W;
-    int ca = 0, cb = 0;
-    for (int p2 = T - t; p2 < T; ++p2) {
-        ca += bit_of(xi, 2 * p2);
-        cb += bit_of(xi, 2 * p2 + 1);
-    }
-    const int rem = T - 1 - t;
     R zr[4];
     head_logits<R>(hf + (i * S + S - 1) * d, shw, hb, d, zr);
-    double z[4], zmax = -INFINITY;
-    bool ok[4], any = false;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        z[v] = (double)zr[v];
-        const int aa = ca + (v & 1), bb = cb + (v >> 1);
-        ok[v] = aa <= n_alpha && bb <= n_beta && aa + rem >= n_alpha && bb + rem >= n_beta;
-        if (ok[v]) {
-            any = true;
-            zmax = fmax(zmax, z[v]);
-        }
-    }
-    double se = 0.0;
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-        if (ok[v]) se += exp(z[v] - zmax);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) cond[i * 4 + v] = ok[v] ? exp(z[v] - zmax) / se : 0.0;
-    if (!any) record_status(st, NNQS_E_SECTOR, i);
+    if (!cond_from_logits<R>(x + i * W, T, t, n_alpha, n_beta, zr, cond + i * 4)) record_status(st, NNQS_E_SECTOR, i);
 }
 
 // dz[(i*T+t)*4+v] = 1/2 dla_i ([v = x_t] - pi_v) on allowed children
@@ -2706,9 +2788,9 @@ nnqs_status launch_decode_layer(const DecodeArgs &g, cudaStream_t s) {
 }
 
 // one layer of the cached decode for n new tokens (rows h) in one launch
-nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, float *h, int64_t n,
-                               float *pool, const int32_t *anc, int t, int64_t g0, int l, DevStatus *st,
-                               cudaStream_t s) {
+nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
+                               float *h, int64_t n, float *pool, const int32_t *anc, int t, int64_t g0, int l,
+                               double *cond, DevStatus *st, cudaStream_t s) {
     if (n == 0) return NNQS_OK;
     const auto &Lw = V.layer[l];
     DecodeArgs g{};
@@ -2730,6 +2812,19 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
     g.b1 = Lw.b1;
     g.b2 = Lw.b2;
     const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(w.tiles);
+    g.first = l == 0;
+    g.last = l == M->L - 1;
+    g.x = x;
+    g.W = M->W;
+    g.n_alpha = M->cfg.n_alpha;
+    g.n_beta = M->cfg.n_beta;
+    g.tok_emb = V.tok;
+    g.pos_emb = V.pos;
+    g.lnf_g = V.lnf_g;
+    g.lnf_b = V.lnf_b;
+    g.hw = V.hw;
+    g.hb = V.hb;
+    g.cond = cond;
     g.tqkv = tiles + w.tile_off[tc_slot(l, 0)];
     g.to = tiles + w.tile_off[tc_slot(l, 1)];
     g.t1 = tiles + w.tile_off[tc_slot(l, 2)];
@@ -2750,15 +2845,16 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
     const int T = M->T, d = M->d, L = M->L, F = M->F, H = M->H, W = M->W;
     const int64_t rows = C;
     R *h = A.hbuf;
-    NNQS_LAUNCH("k_embed", s, k_embed_decode<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, t, T, d, V.tok, V.pos, h));
-    bool fused = false;
     if constexpr (sizeof(R) == 4) {
+        // fused: embedding in the first layer, conditionals in the last
         if (tcw && decode_fused_ok(M, *tcw)) {
-            fused = true;
-            for (int l = 0; l < L; ++l) NNQS_TRY(decode_layer_fused(M, V, *tcw, h, C, pool, anc, t, g0, l, st, s));
+            for (int l = 0; l < L; ++l)
+                NNQS_TRY(decode_layer_fused(M, V, *tcw, x, h, C, pool, anc, t, g0, l, cond, st, s));
+            return NNQS_OK;
         }
     }
-    for (int l = 0; l < L && !fused; ++l) {
+    NNQS_LAUNCH("k_embed", s, k_embed_decode<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, t, T, d, V.tok, V.pos, h));
+    for (int l = 0; l < L; ++l) {
         const auto &Lw = V.layer[l];
         R *qkv = pool + (g0 * L + l) * 3 * (int64_t)d;
         NNQS_TRY(ln_fwd<R>(s, h, Lw.ln1g, Lw.ln1b, A.a, nullptr, nullptr, rows, d));

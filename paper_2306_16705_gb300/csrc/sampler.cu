@@ -143,6 +143,7 @@ __device__ uint64_t binom_btrs(uint64_t n_, double p, Philox &rng, DevStatus *st
 __device__ uint64_t binomial(uint64_t n, double p, Philox &rng, DevStatus *st) {
     if (n == 0 || !(p > 0.0)) return 0;
     if (p >= 1.0) return n;
+    if (n == 1) return rng.uniform() < p ? 1 : 0;  // one draw: Bernoulli(p), no exp/log
     const bool flip = p > 0.5;
     const double pp = flip ? 1.0 - p : p;
     const uint64_t k = (double(n) * pp < 14.0) ? binom_inversion(n, pp, rng, st) : binom_btrs(n, pp, rng, st);
@@ -235,6 +236,46 @@ __global__ void k_scan_sums(int64_t *__restrict__ bsum, int64_t nb, int64_t *__r
 __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ bsum) {
     const int64_t i = blockIdx.x * (int64_t)kScan + threadIdx.x;
     if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+// the same exclusive scan in one CTA for short lists (n <= kScanOne): thread
+// t sums a contiguous run of elements, the run sums are scanned across the
+// block (warp shuffles, then the warp totals), and each run is rewritten
+// with its offset; *total = the sum
+constexpr int kScanOne = 65536;
+__global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ in, int64_t n,
+                                                  int64_t *__restrict__ out, int64_t *__restrict__ total) {
+    __shared__ int64_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t b = min(n, t * per), e = min(n, b + per);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += in[i];
+    // inclusive scan of the run sums within the warp
+    int64_t v = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        wsum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int64_t run = v - s + (warp > 0 ? wsum[warp - 1] : 0);  // exclusive offset of this run
+    for (int64_t i = b; i < e; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+    if (t == 1023) *total = wsum[31];
 }
 
 // children of prefix i in token order at slots off[i] ...
@@ -354,9 +395,13 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
         NNQS_LAUNCH("k_split", s, k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts,
                                                                            L.nchild, st));
         const int64_t nb = (n + kScan - 1) / kScan;
-        NNQS_LAUNCH("k_scan_blocks", s, k_scan_blocks<<<(unsigned)nb, kScan, 0, s>>>(L.nchild, n, L.off, L.bsum));
-        NNQS_LAUNCH("k_scan_sums", s, k_scan_sums<<<1, kScan, 0, s>>>(L.bsum, nb, L.total));
-        NNQS_LAUNCH("k_scan_add", s, k_scan_add<<<(unsigned)nb, kScan, 0, s>>>(L.off, n, L.bsum));
+        if (n <= kScanOne) {
+            NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, n, L.off, L.total));
+        } else {
+            NNQS_LAUNCH("k_scan_blocks", s, k_scan_blocks<<<(unsigned)nb, kScan, 0, s>>>(L.nchild, n, L.off, L.bsum));
+            NNQS_LAUNCH("k_scan_sums", s, k_scan_sums<<<1, kScan, 0, s>>>(L.bsum, nb, L.total));
+            NNQS_LAUNCH("k_scan_add", s, k_scan_add<<<(unsigned)nb, kScan, 0, s>>>(L.off, n, L.bsum));
+        }
         int64_t next = 0;
         NNQS_CUDA_TRY(cudaMemcpyAsync(&next, L.total, 8, cudaMemcpyDeviceToHost, s));
         NNQS_CUDA_TRY(cudaStreamSynchronize(s));
