@@ -853,14 +853,18 @@ nnqs_status act_bwd(cudaStream_t s, int act, R *dX, const R *Z, int64_t n);
 // epilogue, or by a separate pass)
 template <class R>
 nnqs_status bw_dx(cudaStream_t s, const TcWeights *tcw, int slot, const R *dY, int64_t rows, int64_t out, const R *Wt,
-                  int64_t in, R *dX, Scratch<R> scr, int act = 0, const R *Z = nullptr) {
+                  int64_t in, R *dX, Scratch<R> scr, int act = 0, const R *Z = nullptr, R *colpart = nullptr,
+                  bool *colpart_done = nullptr) {
+    if (colpart_done) *colpart_done = false;
     NNQS_TRY(linear_dx<R>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr));
     return act_bwd<R>(s, act, dX, Z, rows * in);
 }
 template <>
 nnqs_status bw_dx<float>(cudaStream_t s, const TcWeights *tcw, int slot, const float *dY, int64_t rows, int64_t out,
-                         const float *Wt, int64_t in, float *dX, Scratch<float> scr, int act, const float *Z) {
-    if (tcw) return tc_linear_dx(s, *tcw, slot, dY, rows, dX, act, Z);
+                         const float *Wt, int64_t in, float *dX, Scratch<float> scr, int act, const float *Z,
+                         float *colpart, bool *colpart_done) {
+    if (colpart_done) *colpart_done = false;
+    if (tcw) return tc_linear_dx(s, *tcw, slot, dY, rows, dX, act, Z, colpart, colpart_done);
     NNQS_TRY(linear_dx<float>(s, EPI_STORE, dY, rows, out, Wt, in, dX, scr));
     return act_bwd<float>(s, act, dX, Z, rows * in);
 }
@@ -1158,9 +1162,12 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
     smem_to_rows<R>(dst, so, ldo, T, d);
 }
 
+// colsum (optional): [n][3d] column sums of the sample's dq|dk|dv over its
+// T positions (added in position order), for the qkv bias gradient
 template <class R, int DH>
 __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__ o, const R *__restrict__ lse,
-                                const R *__restrict__ dout, R *__restrict__ dqkv, int T, int H, int d) {
+                                const R *__restrict__ dout, R *__restrict__ dqkv, int T, int H, int d,
+                                R *__restrict__ colsum) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int ldq = 3 * d + 1, ldo = d + 1;
     R *sq = reinterpret_cast<R *>(sm_raw);  // q|k|v [T][3d+1]
@@ -1245,6 +1252,13 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     }
     __syncthreads();
     smem_to_rows<R>(dqkv + i * T * 3 * d, sg, ldq, T, 3 * d);
+    if (colsum) {
+        for (int c = tid; c < 3 * d; c += nt) {
+            R acc = 0;
+            for (int t = 0; t < T; ++t) acc += sg[t * ldq + c];
+            colsum[i * 3 * d + c] = acc;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ head + masked log-softmax
@@ -2409,13 +2423,16 @@ nnqs_status attn_fwd(cudaStream_t s, int dh, const R *qkv, R *o, R *lse, int64_t
 
 template <int DH_, class R>
 nnqs_status launch_attn_bwd(cudaStream_t s, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
-                            int64_t n, int T, int H, int d) {
+                            int64_t n, int T, int H, int d, R *colsum, bool *sums) {
     const size_t sm = attn_bwd_smem_bytes<R>(T, H, d);
+    *sums = false;
     if (H * T <= 1024 && sm <= kAttnSmemMax && n > 0) {
         NNQS_TRY(allow_smem(k_attn_bwd_smem<R, DH_>, sm));
         const int threads = (H * T + 31) / 32 * 32;
         NNQS_LAUNCH("k_attn_bwd", s,
-                    k_attn_bwd_smem<R, DH_><<<(unsigned)n, threads, sm, s>>>(qkv, o, lse, dout, dqkv, T, H, d));
+                    k_attn_bwd_smem<R, DH_><<<(unsigned)n, threads, sm, s>>>(qkv, o, lse, dout, dqkv, T, H, d,
+                                                                              colsum));
+        *sums = colsum != nullptr;
         return NNQS_OK;
     }
     NNQS_LAUNCH("k_attn_bwd_q", s, k_attn_bwd_q<R, DH_><<<grid_for(n * H * T, 128), 128, 0, s>>>(qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d));
@@ -2425,15 +2442,17 @@ nnqs_status launch_attn_bwd(cudaStream_t s, const R *qkv, const R *o, const R *l
 
 template <class R>
 nnqs_status attn_bwd(cudaStream_t s, int dh, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
-                     int64_t n, int T, int H, int d) {
+                     int64_t n, int T, int H, int d, R *colsum = nullptr, bool *sums = nullptr) {
+    bool dummy = false;
+    if (!sums) sums = &dummy;
     switch (dh) {
-        case 1: return launch_attn_bwd<1>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-        case 2: return launch_attn_bwd<2>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-        case 4: return launch_attn_bwd<4>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-        case 8: return launch_attn_bwd<8>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-        case 16: return launch_attn_bwd<16>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-        case 32: return launch_attn_bwd<32>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
-        case 64: return launch_attn_bwd<64>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d);
+        case 1: return launch_attn_bwd<1>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
+        case 2: return launch_attn_bwd<2>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
+        case 4: return launch_attn_bwd<4>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
+        case 8: return launch_attn_bwd<8>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
+        case 16: return launch_attn_bwd<16>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
+        case 32: return launch_attn_bwd<32>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
+        case 64: return launch_attn_bwd<64>(s, qkv, o, lse, dout, dqkv, Dbuf, n, T, H, d, colsum, sums);
         default: return set_error(NNQS_E_UNSUPPORTED, "head dimension must be a power of two <= 64");
     }
 }
@@ -2506,6 +2525,8 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
 template <class R>
 struct Grads {
     R *dh, *dtmp, *dqkv, *du, *Dbuf, *dz, *dph, *dz1, *dz2;
+    R *qkvsum;    // [C][3d] per-sample column sums of dqkv (qkv bias gradient)
+    R *ucolpart;  // [ceil(C T / 128)][F] column sums of du per 128-row tile (FFN-in bias gradient)
     double2 *lp;  // forward output of the recomputation (not used further)
 };
 
@@ -2522,6 +2543,8 @@ void take_grads(const nnqs_model *M, int64_t C, Arena &a, Grads<R> &G) {
     G.dz1 = a.take<R>(C * P);
     G.dz2 = a.take<R>(C * P);
     G.lp = a.take<double2>(C);
+    G.qkvsum = a.take<R>(C * 3 * d);
+    G.ucolpart = a.take<R>((rows + 127) / 128 * F);
 }
 
 template <class R>
@@ -2572,18 +2595,29 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         // FFN: hout = hmid + gelu(a2 W1^T + b1) W2^T + b2
         // (b2's gradient came with the LayerNorm backward that produced dh)
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
-        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr, 1, u));
+        bool ucols = false;  // column sums of du per 128-row tile, from the input-gradient epilogue
+        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr, 1, u, G.ucolpart, &ucols));
         NNQS_TRY(bw_dw<R>(s, tcw, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, nullptr, scr));
+        if (ucols)
+            NNQS_TRY(colsum<R>(s, 0, G.ucolpart, nullptr, nullptr, nullptr, (rows + 127) / 128, F, gacc + Lg.b1,
+                               nullptr, scr));
+        else
+            NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 2), G.du, rows, F, Lw.w1, d, G.dtmp, scr));
         NNQS_TRY(ln_bwd_sums<R>(s, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g, G.dtmp, G.dh, rows, d,
                                 gacc + Lg.ln2_g, gacc + Lg.ln2_b, gacc + Lg.bo, scr));
         // attention: hmid = hin + attn(a) Wo^T + bo
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 1), G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
-        NNQS_TRY(attn_bwd<R>(s, M->dh, qkv, o, A.lse + (int64_t)l * C * H * T, G.dtmp, G.dqkv, G.Dbuf, C, T, H, d));
+        bool qsums = false;
+        NNQS_TRY(attn_bwd<R>(s, M->dh, qkv, o, A.lse + (int64_t)l * C * H * T, G.dtmp, G.dqkv, G.Dbuf, C, T, H, d,
+                             G.qkvsum, &qsums));
         NNQS_TRY(bw_dw<R>(s, tcw, G.dqkv, rows, 3 * d, a, d, gacc + Lg.wqkv, scr));
-        NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, nullptr, scr));
+        // qkv bias: per-sample sums from the attention kernel, else the rows
+        if (qsums)
+            NNQS_TRY(colsum<R>(s, 0, G.qkvsum, nullptr, nullptr, nullptr, C, 3 * d, gacc + Lg.bqkv, nullptr, scr));
+        else
+            NNQS_TRY(colsum<R>(s, 0, G.dqkv, nullptr, nullptr, nullptr, rows, 3 * d, gacc + Lg.bqkv, nullptr, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 0), G.dqkv, rows, 3 * d, Lw.wqkv, d, G.dtmp, scr));
         NNQS_TRY(ln_bwd_sums<R>(s, hin, A.mean1 + l * rows, A.rstd1 + l * rows, Lw.ln1g, G.dtmp, G.dh, rows, d,
                                 gacc + Lg.ln1_g, gacc + Lg.ln1_b, l > 0 ? gacc + Lo.layer[l - 1].b2 : nullptr, scr));

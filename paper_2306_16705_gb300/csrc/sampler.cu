@@ -238,27 +238,32 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
     if (i < n) out[i] += bsum[blockIdx.x];
 }
 
-// the same exclusive scan in one CTA for short lists (n <= kScanOne): thread
-// t sums a contiguous run of elements, the run sums are scanned across the
-// block (warp shuffles, then the warp totals), and each run is rewritten
-// with its offset; *total = the sum
+// the same exclusive scan in one CTA for short lists (n <= kScanOne): warp w
+// takes a contiguous segment and walks it 32 elements at a time (coalesced
+// loads, shuffle scan, running carry), the 32 segment totals are scanned,
+// and each warp rewrites its segment with the offsets; *total = the sum
 constexpr int kScanOne = 65536;
 __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ in, int64_t n,
                                                   int64_t *__restrict__ out, int64_t *__restrict__ total) {
     __shared__ int64_t wsum[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t b = min(n, t * per), e = min(n, b + per);
-    int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += in[i];
-    // inclusive scan of the run sums within the warp
-    int64_t v = s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t seg = ((n + 31) / 32 + 31) / 32 * 32;  // elements per warp, a multiple of 32
+    const int64_t b = min(n, warp * seg), e = min(n, b + seg);
+    // pass 1: the segment's own exclusive scan into out, and its total
+    int64_t carry = 0;
+    for (int64_t i0 = b; i0 < e; i0 += 32) {
+        const int64_t i = i0 + lane;
+        const int64_t x = i < e ? in[i] : 0;
+        int64_t v = x;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (i < e) out[i] = carry + v - x;
+        carry += __shfl_sync(0xffffffffu, v, 31);
     }
-    if (lane == 31) wsum[warp] = v;
+    if (lane == 0) wsum[warp] = carry;
     __syncthreads();
     if (warp == 0) {
         int64_t w = wsum[lane];
@@ -267,15 +272,14 @@ __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ i
             const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += u;
         }
-        wsum[lane] = w;  // inclusive over warps
+        wsum[lane] = w;  // inclusive over the segments
     }
     __syncthreads();
-    int64_t run = v - s + (warp > 0 ? wsum[warp - 1] : 0);  // exclusive offset of this run
-    for (int64_t i = b; i < e; ++i) {
-        out[i] = run;
-        run += in[i];
-    }
-    if (t == 1023) *total = wsum[31];
+    // pass 2: add the totals of the segments before this one
+    const int64_t base = warp > 0 ? wsum[warp - 1] : 0;
+    if (base != 0)
+        for (int64_t i = b + lane; i < e; i += 32) out[i] += base;
+    if (threadIdx.x == 0) *total = wsum[31];
 }
 
 // children of prefix i in token order at slots off[i] ...

@@ -281,7 +281,8 @@ nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeigh
 }
 
 nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX,
-                         int act, const float *Z) {
+                         int act, const float *Z, float *colpart, bool *colpart_done) {
+    if (colpart_done) *colpart_done = false;
     if (rows == 0) return NNQS_OK;
     if (act != 0 && Z == nullptr) return set_error(NNQS_E_INVAL, "tensor-core input gradient: pre-activation missing");
     tc::Args g{};
@@ -301,6 +302,10 @@ nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const flo
     g.st = w.st;
     g.resid = Z;
     setup_tma(g, act == 1 ? tc::EPI_DGELU : act == 2 ? tc::EPI_DRELU : tc::EPI_STORE, 1);
+    if (g.use_tma && g.Nt % 32 == 0 && colpart) {
+        g.colpart = colpart;
+        if (colpart_done) *colpart_done = true;
+    }
     note_work("k_tc_gemm", 2.0 * double(rows) * double(in) * double(out),
               4.0 * double(rows) * out + 2.0 * double(in) * g.Kpad + (act ? 8.0 : 4.0) * double(rows) * in);
     const int64_t ntn = (g.N + g.Nt - 1) / g.Nt;

@@ -149,6 +149,10 @@ struct Args {
     // the residual / pre-activation, 128 x 32 boxes with the 128-byte swizzle
     int use_tma;
     CUtensorMap tmY, tmY2, tmR;
+    // TMA epilogue, optional: column sums of this CTA's 128 output rows,
+    // colpart[row tile][N] (for the bias gradient of the layer whose input
+    // gradient Y is)
+    float *colpart;
 };
 
 // TMA: one 32-column x 128-row FP32 box between shared memory (1024-byte
@@ -465,6 +469,15 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
             }
             fence_async_smem();
             __syncthreads();
+            if (g.colpart && tid < 32 && n0 + c0 + tid < g.N) {
+                // rows of the box in order (rows past M are left out)
+                const int rmax = (int)min((int64_t)kTileM, g.M - m0);
+                const int q = tid >> 2, e = tid & 3;
+                float cs = 0.f;
+                for (int rr = 0; rr < rmax; ++rr)
+                    cs += *reinterpret_cast<const float *>(box + rr * 128 + ((q ^ (rr & 7)) << 4) + 4 * e);
+                g.colpart[blockIdx.y * g.N + n0 + c0 + tid] = cs;
+            }
             if (tid == 0) {
                 tma_store_box(&g.tmY, ubox, x, (int)m0, zc);
                 if (kTwo) tma_store_box(&g.tmY2, ubox2, x, (int)m0, zc);

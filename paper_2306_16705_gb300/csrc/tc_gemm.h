@@ -50,8 +50,11 @@ nnqs_status tc_linear_fwd_ld<double>(cudaStream_t s, const TcWeights &w, int slo
 
 // dX[rows][in] = dY[rows][out] W[out][in] on tensor cores (W^T copy of `slot`);
 // act 1 / 2 multiplies by GELU'(Z) / ReLU'(Z) of the pre-activation Z[rows][in]
+// colpart (optional): [ceil(rows/128)][in] column sums of dX per 128-row tile;
+// *colpart_done says whether they were written (TMA epilogue only)
 nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX,
-                         int act = 0, const float *Z = nullptr);
+                         int act = 0, const float *Z = nullptr, float *colpart = nullptr,
+                         bool *colpart_done = nullptr);
 // dW[out][in] += dY[rows][out]^T X[rows][in] on tensor cores, split over rows;
 // partials go to `scratch` (scratch_elems floats) and are added in order
 nnqs_status tc_linear_dw(cudaStream_t s, const float *dY, int64_t rows, int64_t out, const float *X, int64_t in,
