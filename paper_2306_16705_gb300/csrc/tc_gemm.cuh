@@ -469,14 +469,17 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
             }
             fence_async_smem();
             __syncthreads();
-            if (g.colpart && tid < 32 && n0 + c0 + tid < g.N) {
-                // rows of the box in order (rows past M are left out)
+            float *cpart = reinterpret_cast<float *>(box2);  // free in the one-output epilogues
+            if (!kTwo && g.colpart) {
+                // column tid & 31 over rows 32 (tid >> 5) .. + 31 of the box, in
+                // order (rows past M are left out); the four row groups are
+                // added in order below
                 const int rmax = (int)min((int64_t)kTileM, g.M - m0);
-                const int q = tid >> 2, e = tid & 3;
+                const int cl = tid & 31, q = cl >> 2, e = cl & 3, rg = tid >> 5;
                 float cs = 0.f;
-                for (int rr = 0; rr < rmax; ++rr)
+                for (int rr = 32 * rg; rr < min(32 * rg + 32, rmax); ++rr)
                     cs += *reinterpret_cast<const float *>(box + rr * 128 + ((q ^ (rr & 7)) << 4) + 4 * e);
-                g.colpart[blockIdx.y * g.N + n0 + c0 + tid] = cs;
+                cpart[rg * 32 + cl] = cs;
             }
             if (tid == 0) {
                 tma_store_box(&g.tmY, ubox, x, (int)m0, zc);
@@ -485,6 +488,9 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
                 bulk_wait_read();
             }
             __syncthreads();
+            if (!kTwo && g.colpart && tid < 32 && n0 + c0 + tid < g.N)
+                g.colpart[blockIdx.y * g.N + n0 + c0 + tid] =
+                    ((cpart[tid] + cpart[32 + tid]) + cpart[64 + tid]) + cpart[96 + tid];
         }
         if (tid == 0) {
             if (!ok) {
