@@ -108,6 +108,36 @@ __global__ void k_embed(const uint64_t *__restrict__ x, int W, int64_t n, int S,
     }
 }
 
+// the same with 16-byte stores (d % 4 == 0): thread = (row, 4 columns), the
+// row's input token read once per thread
+template <class R>
+__global__ void k_embed_v(const uint64_t *__restrict__ x, int W, int64_t n, int S, int T, int d,
+                          const R *__restrict__ tok_emb, const R *__restrict__ pos_emb, R *__restrict__ h,
+                          uint8_t *__restrict__ tok) {
+    const int d4 = d / 4;
+    const int64_t total = n * S * d4;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / d4;
+        const int c = 4 * (int)(idx - row * d4);
+        const int t = (int)(row % S);
+        const uint64_t *xi = x + (row / S) * W;
+        const int inp = t == 0 ? 4 : token_at(xi, T, t - 1);
+        const R *te = tok_emb + inp * d + c, *pe = pos_emb + t * d + c;
+        R *hr = h + row * d + c;
+        if constexpr (sizeof(R) == 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(te), b = *reinterpret_cast<const float4 *>(pe);
+            *reinterpret_cast<float4 *>(hr) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+        } else {
+            hr[0] = te[0] + pe[0];
+            hr[1] = te[1] + pe[1];
+            hr[2] = te[2] + pe[2];
+            hr[3] = te[3] + pe[3];
+        }
+        if (c == 0) tok[row] = (uint8_t)token_at(xi, T, t);
+    }
+}
+
 // ------------------------------------------------------------------ LayerNorm
 constexpr int kMaxDPerLane = 8;  // d <= 256
 
@@ -2467,7 +2497,10 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     const int Tm = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, W = M->W, N = M->N;
     const int T = S > 0 ? S : Tm;  // sequence length of this pass
     const int64_t rows = C * T;
-    NNQS_LAUNCH("k_embed", s, k_embed<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, T, Tm, d, V.tok, V.pos, A.hbuf, A.tok));
+    if (d % 4 == 0)
+        NNQS_LAUNCH("k_embed", s, k_embed_v<R><<<grid_for(rows * d / 4, 256), 256, 0, s>>>(x, W, C, T, Tm, d, V.tok, V.pos, A.hbuf, A.tok));
+    else
+        NNQS_LAUNCH("k_embed", s, k_embed<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, T, Tm, d, V.tok, V.pos, A.hbuf, A.tok));
     for (int l = 0; l < L; ++l) {
         const auto &Lw = V.layer[l];
         const int64_t k = A.keep ? l : 0;

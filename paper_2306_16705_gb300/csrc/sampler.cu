@@ -239,31 +239,31 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
 }
 
 // the same exclusive scan in one CTA for short lists (n <= kScanOne): warp w
-// takes a contiguous segment and walks it 32 elements at a time (coalesced
-// loads, shuffle scan, running carry), the 32 segment totals are scanned,
-// and each warp rewrites its segment with the offsets; *total = the sum
+// takes a contiguous segment; pass 1 sums it (four 32-element loads in
+// flight), the 32 segment totals are scanned, pass 2 walks the segment again
+// (loads batched the same way) with a shuffle scan per 32 elements and a
+// running carry starting at the segment's offset; *total = the sum
 constexpr int kScanOne = 65536;
 __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ in, int64_t n,
                                                   int64_t *__restrict__ out, int64_t *__restrict__ total) {
     __shared__ int64_t wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t seg = ((n + 31) / 32 + 31) / 32 * 32;  // elements per warp, a multiple of 32
+    const int64_t seg = ((n + 31) / 32 + 127) / 128 * 128;  // elements per warp, a multiple of 128
     const int64_t b = min(n, warp * seg), e = min(n, b + seg);
-    // pass 1: the segment's own exclusive scan into out, and its total
-    int64_t carry = 0;
-    for (int64_t i0 = b; i0 < e; i0 += 32) {
-        const int64_t i = i0 + lane;
-        const int64_t x = i < e ? in[i] : 0;
-        int64_t v = x;
+    int64_t part = 0;
+    for (int64_t i0 = b; i0 < e; i0 += 128) {
+        int32_t x[4];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + 32 * k + lane;
+            x[k] = i < e ? in[i] : 0;
         }
-        if (i < e) out[i] = carry + v - x;
-        carry += __shfl_sync(0xffffffffu, v, 31);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) part += x[k];
     }
-    if (lane == 0) wsum[warp] = carry;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) wsum[warp] = part;
     __syncthreads();
     if (warp == 0) {
         int64_t w = wsum[lane];
@@ -275,10 +275,27 @@ __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ i
         wsum[lane] = w;  // inclusive over the segments
     }
     __syncthreads();
-    // pass 2: add the totals of the segments before this one
-    const int64_t base = warp > 0 ? wsum[warp - 1] : 0;
-    if (base != 0)
-        for (int64_t i = b + lane; i < e; i += 32) out[i] += base;
+    int64_t carry = warp > 0 ? wsum[warp - 1] : 0;
+    for (int64_t i0 = b; i0 < e; i0 += 128) {
+        int32_t x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + 32 * k + lane;
+            x[k] = i < e ? in[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int64_t v = x[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            const int64_t i = i0 + 32 * k + lane;
+            if (i < e) out[i] = carry + v - x[k];
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
     if (threadIdx.x == 0) *total = wsum[31];
 }
 
