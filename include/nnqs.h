@@ -346,6 +346,22 @@ nnqs_status nnqs_adam_step(float *params, const float *grad, float *m, float *v,
                            int64_t step, double lr, double beta1, double beta2, double eps,
                            nnqs_stream stream);
 
+/* AdamW (Sec. 4.1 trains with it): Adam with decoupled weight decay,
+ * theta <- theta * (1 - lr * weight_decay), then the Adam step of
+ * nnqs_adam_step with the same arguments.  Same layout, ownership and
+ * errors as nnqs_adam_step; NNQS_E_INVAL also when weight_decay < 0 or
+ * lr * weight_decay >= 1.  weight_decay = 0 gives nnqs_adam_step. */
+nnqs_status nnqs_adamw_step(float *params, const float *grad, float *m, float *v, int64_t n,
+                            int64_t step, double lr, double beta1, double beta2, double eps,
+                            double weight_decay, nnqs_stream stream);
+
+/* Learning rate of training step `step` (1-based) under the warm-up schedule
+ * of Sec. 4.1: d_model^-0.5 * min(step^-0.5, step * warmup^-1.5); it rises
+ * linearly to its peak (d_model * warmup)^-0.5 at step = warmup and decays as
+ * step^-0.5 after.  Host only, no device work; 0 for step < 1, d_model < 1 or
+ * warmup < 1. */
+double nnqs_lr_warmup(int64_t step, int d_model, int64_t warmup);
+
 #ifdef __cplusplus
 }
 #endif

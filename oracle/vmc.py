@@ -47,6 +47,19 @@ def exact_distribution(params, sector_bits, n_alpha, n_beta, n_heads):
     return np.exp(2.0 * la)
 
 
+def adamw_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01):
+    """One AdamW update (Loshchilov & Hutter 2019, decoupled weight decay), the
+    optimiser of Sec. 4.1: shrink theta by (1 - lr * weight_decay), then take
+    the Adam step below with the same moments."""
+    return adam_step((1.0 - lr * weight_decay) * theta, grad, m, v, step, lr, beta1, beta2, eps)
+
+
+def lr_warmup(step, d_model, warmup=4000):
+    """Learning rate of training step ``step`` (1-based), Sec. 4.1:
+    d_model^-1/2 * min(step^-1/2, step * warmup^-3/2)."""
+    return d_model ** -0.5 * min(step ** -0.5, step * warmup ** -1.5)
+
+
 def adam_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2015, Algorithm 1), no weight decay.
     ``step`` is the 1-based step count after this update."""

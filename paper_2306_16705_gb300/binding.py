@@ -111,6 +111,10 @@ _SIGS = {
     "nnqs_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "nnqs_adamw_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "nnqs_lr_warmup": (ctypes.c_double, [ctypes.c_int64, ctypes.c_int, ctypes.c_int64]),
 }
 
 
@@ -406,6 +410,18 @@ def adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-
     """nnqs_adam_step, in place."""
     _check(lib().nnqs_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step),
                                 float(lr), float(beta1), float(beta2), float(eps), _stream()))
+
+
+def adamw_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01):
+    """nnqs_adamw_step, in place."""
+    _check(lib().nnqs_adamw_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step),
+                                 float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                                 _stream()))
+
+
+def lr_warmup(step, d_model, warmup=4000):
+    """nnqs_lr_warmup (host)."""
+    return lib().nnqs_lr_warmup(int(step), int(d_model), int(warmup))
 
 
 def to_device_bits(x: np.ndarray, device="cuda") -> torch.Tensor:

@@ -1477,24 +1477,29 @@ __device__ __forceinline__ bool cond_from_logits(const uint64_t *xi, int T, int 
         cb += bit_of(xi, 2 * p2 + 1);
     }
     const int rem = T - 1 - t;
-    double z[4], zmax = -INFINITY;
+    // the softmax runs in the logits' precision and is widened at the end:
+    // FP32 logits give FP32 conditionals (the binomial chain only needs them
+    // to ~1e-7 relative), FP64 logits FP64 ones
+    R z[4], zmax = neg_inf<R>();
     bool ok[4], any = false;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        z[v] = (double)zr[v];
+        z[v] = zr[v];
         const int aa = ca + (v & 1), bb = cb + (v >> 1);
         ok[v] = aa <= n_alpha && bb <= n_beta && aa + rem >= n_alpha && bb + rem >= n_beta;
         if (ok[v]) {
             any = true;
-            zmax = fmax(zmax, z[v]);
+            zmax = z[v] > zmax ? z[v] : zmax;
         }
     }
-    double se = 0.0;
+    R e[4], se = R(0);
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-        if (ok[v]) se += exp(z[v] - zmax);
+    for (int v = 0; v < 4; ++v) {
+        e[v] = ok[v] ? exp_<R>(z[v] - zmax) : R(0);
+        se += e[v];
+    }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) out[v] = ok[v] ? exp(z[v] - zmax) / se : 0.0;
+    for (int v = 0; v < 4; ++v) out[v] = ok[v] ? (double)(e[v] / se) : 0.0;
     return any;
 }
 
@@ -1511,7 +1516,10 @@ __device__ __forceinline__ bool cond_from_logits(const uint64_t *xi, int T, int 
 // K step, same epilogue sums, the same attention loop), so the cached
 // sampler still reproduces the recomputed conditionals bit for bit.
 namespace dec {
-constexpr int kThreads = 256, kRows = 128, kD = 64, kQKV = 192, kF = 256;
+constexpr int kThreads = 512, kRows = 128, kD = 64, kQKV = 192, kF = 256;
+// columns of a 64-column TMEM chunk per thread in the epilogues: warp w reads
+// lanes 32 (w % 4) .. + 31 (its TMEM lane quarter), columns kCW (w / 4) .. + kCW - 1
+constexpr int kCW = 64 * 4 / (kThreads / 32);
 constexpr int kOffA = 0;         // A operand hi [128][64] BF16 (16 KB); lo at +16 KB
 constexpr int kOffG = 32768;     // FFN-out A chunk hi / lo (+16 KB); before the FFN: Wo hi / lo (+8 KB)
 constexpr int kOffB = 65536;     // Wqkv hi / lo (+24 KB); after the qkv MMA: W1 hi, W1 lo, W2 hi, W2 lo
@@ -1522,6 +1530,9 @@ constexpr int kHS = 65;
 constexpr int kOffBar = kOffH + kRows * kHS * 4;
 constexpr int kSmem = kOffBar + 64 + 1024;  // 230,976 bytes
 constexpr uint32_t kColQKV = 0, kColO = 192, kColU = 256, kColY = 320, kTmemCols = 512;
+// TMEM columns of the four FFN-in chunks U_c: kColU, the free 384..511, and
+// the first 64 columns of the finished q|k|v
+__device__ __forceinline__ constexpr uint32_t col_u(int c) { return c == 0 ? kColU : c == 3 ? 0u : 256u + 64u * uint32_t(c + 1); }
 }  // namespace dec
 
 struct DecodeArgs {
@@ -1672,18 +1683,13 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
         m[k] = neg_inf<float>();
         lsum[k] = 0.f;
     }
-    // node ids of step j + 1 are read while step j's keys and values load
-    int64_t node[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) node[k] = 0 < t ? (int64_t)anc[rr[k] * Tm] : g0 + rr[k];
-    for (int j = 0; j <= t; ++j) {
-        float kk[NR][DH], vv[NR][DH];
-        int64_t nnext[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) nnext[k] = j + 1 < t ? (int64_t)anc[rr[k] * Tm + j + 1] : g0 + rr[k];
+    // keys and values of step j + 1 load while step j is computed (the last
+    // prefetch rereads the row's own node); node ids are read one step further
+    // ahead
+    auto load_kv = [&](const int64_t (&nd)[NR], float (&kk)[NR][DH], float (&vv)[NR][DH]) {
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            const float *base = pool + (node[k] * L + l) * row;
+            const float *base = pool + (nd[k] * L + l) * row;
 #pragma unroll
             for (int e = 0; e < DH; e += 4) {
                 const float4 k4 = *reinterpret_cast<const float4 *>(base + d + hh * DH + e);
@@ -1692,6 +1698,20 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
                 vv[k][e] = v4.x; vv[k][e + 1] = v4.y; vv[k][e + 2] = v4.z; vv[k][e + 3] = v4.w;
             }
         }
+    };
+    auto node_at = [&](int j, int k) -> int64_t { return j < t ? (int64_t)anc[rr[k] * Tm + j] : g0 + rr[k]; };
+    float kk[NR][DH], vv[NR][DH];
+    int64_t node[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) node[k] = node_at(0, k);
+    load_kv(node, kk, vv);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) node[k] = node_at(1, k);
+    for (int j = 0; j <= t; ++j) {
+        float kn[NR][DH], vn[NR][DH];
+        load_kv(node, kn, vn);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) node[k] = node_at(j + 2, k);
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
             float sc = 0;
@@ -1706,7 +1726,12 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
             m[k] = mn;
         }
 #pragma unroll
-        for (int k = 0; k < NR; ++k) node[k] = nnext[k];
+        for (int k = 0; k < NR; ++k)
+#pragma unroll
+            for (int c = 0; c < DH; ++c) {
+                kk[k][c] = kn[k][c];
+                vv[k][c] = vn[k][c];
+            }
     }
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -1773,23 +1798,36 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         bulk_g2s(bB, g.tqkv, q, wb);
         if (SPLIT) bulk_g2s(bB + kQkvLo, g.tqkv + kQKV * kD, q, wb);
     }
-    // residual rows (first layer: the embeddings, as k_embed_decode forms them)
-    for (int it = tid; it < kRows * (kD / 4); it += kThreads) {
-        const int r = it >> 4, c4 = it & 15;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (m0 + r < g.n) {
-            if (g.first) {
-                const int inp = g.t == 0 ? 4 : token_at(g.x + (m0 + r) * g.W, g.Tm, g.t - 1);
-                const float *te = g.tok_emb + inp * kD + 4 * c4, *pe = g.pos_emb + g.t * kD + 4 * c4;
-                v = make_float4(te[0] + pe[0], te[1] + pe[1], te[2] + pe[2], te[3] + pe[3]);
-            } else {
-                v = *reinterpret_cast<const float4 *>(g.h + (m0 + r) * kD + 4 * c4);
+    // residual rows (first layer: the embeddings, as k_embed_decode forms them);
+    // all of a thread's loads are issued before its shared stores
+    {
+        constexpr int kIt = kRows * (kD / 4) / kThreads;
+        float4 v[kIt];
+#pragma unroll
+        for (int i = 0; i < kIt; ++i) {
+            const int it = tid + kThreads * i;
+            const int r = it >> 4, c4 = it & 15;
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m0 + r < g.n) {
+                if (g.first) {
+                    const int inp = g.t == 0 ? 4 : token_at(g.x + (m0 + r) * g.W, g.Tm, g.t - 1);
+                    const float4 te = __ldg(reinterpret_cast<const float4 *>(g.tok_emb + inp * kD) + c4);
+                    const float4 pe = __ldg(reinterpret_cast<const float4 *>(g.pos_emb + g.t * kD) + c4);
+                    v[i] = make_float4(te.x + pe.x, te.y + pe.y, te.z + pe.z, te.w + pe.w);
+                } else {
+                    v[i] = *reinterpret_cast<const float4 *>(g.h + (m0 + r) * kD + 4 * c4);
+                }
             }
         }
-        sH[r * kHS + 4 * c4] = v.x;
-        sH[r * kHS + 4 * c4 + 1] = v.y;
-        sH[r * kHS + 4 * c4 + 2] = v.z;
-        sH[r * kHS + 4 * c4 + 3] = v.w;
+#pragma unroll
+        for (int i = 0; i < kIt; ++i) {
+            const int it = tid + kThreads * i;
+            const int r = it >> 4, c4 = it & 15;
+            sH[r * kHS + 4 * c4] = v[i].x;
+            sH[r * kHS + 4 * c4 + 1] = v[i].y;
+            sH[r * kHS + 4 * c4 + 2] = v[i].z;
+            sH[r * kHS + 4 * c4 + 3] = v[i].w;
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1809,7 +1847,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         phase ^= 1u;
         tc::fence_after_sync();
     };
-    const int q4 = warp & 3, half = warp >> 2, row = 32 * q4 + lane;
+    const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
     const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
     const bool row_ok = m0 + row < g.n;
 
@@ -1848,8 +1886,8 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         float *slab = reinterpret_cast<float *>(aHi);
         for (int c = 0; c < kQKV / 64; ++c) {
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int cl = 32 * half + 16 * b;  // column within the chunk
+            for (int b = 0; b < kCW / 16; ++b) {
+                const int cl = kCW * cq + 16 * b;  // column within the chunk
                 uint32_t r16[16];
                 tc::tmem_ld16(tl + kColQKV + 64 * c + cl, r16);
 #pragma unroll
@@ -1907,10 +1945,10 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         wait_mma();
     }
     if (ok) {
-        // h += attn Wo^T + bo (warp half: 32 columns)
+        // h += attn Wo^T + bo (kCW columns per thread)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int c0 = 32 * half + 16 * b;
+        for (int b = 0; b < kCW / 16; ++b) {
+            const int c0 = kCW * cq + 16 * b;
             uint32_t r16[16];
             tc::tmem_ld16(tl + kColO + c0, r16);
 #pragma unroll
@@ -1921,36 +1959,45 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         }
     }
     __syncthreads();
-    // ---- LayerNorm 2 -> FFN: MMA1(c) = LN2 W1_c^T, GELU -> G, MMA2(c) += G W2_c^T;
-    // MMA2(c) and MMA1(c+1) are committed together
+    // ---- LayerNorm 2 -> FFN: the four MMA1(c) = LN2 W1_c^T are issued together
+    // (TMEM columns of the finished q|k|v and free columns), then per chunk:
+    // GELU of U_c into registers while MMA2(c - 1) runs, G_c into shared
+    // memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
     if (ok && tid < kRows) dec_layernorm_row(sH, tid, g.ln2g, g.ln2b, aHi, aLo, SPLIT);
     sync_async();
     if (ok && tid == 0) {
-        dec_mma(tmem + kColU, uA, uA2, uB + kW1Hi, uB + kW1Lo, kD, SPLIT, false);
+#pragma unroll
+        for (int c = 0; c < kF / kD; ++c)
+            dec_mma(tmem + col_u(c), uA, uA2, uB + kW1Hi + 8192 * c, uB + kW1Lo + 8192 * c, kD, SPLIT, false);
         tc::mma_commit(mb);
     }
+    if (ok) wait_mma();
     for (int c = 0; c < kF / kD && ok; ++c) {
-        wait_mma();
-        if (!ok) break;
+        float x[kCW];
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int c0 = 32 * half + 16 * b;
+        for (int b = 0; b < kCW / 16; ++b) {
+            const int c0 = kCW * cq + 16 * b;
             uint32_t r16[16];
-            tc::tmem_ld16(tl + kColU + c0, r16);
+            tc::tmem_ld16(tl + col_u(c) + c0, r16);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) x[16 * b + e] = tc::gelu_f(__uint_as_float(r16[e]) + g.b1[kD * c + c0 + e]);
+        }
+        if (c > 0) {
+            wait_mma();
+            if (!ok) break;
+        }
+#pragma unroll
+        for (int b = 0; b < kCW / 16; ++b)
 #pragma unroll
             for (int gi = 0; gi < 2; ++gi) {
-                float x[8];
+                float xg[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = tc::gelu_f(__uint_as_float(r16[8 * gi + e]) + g.b1[kD * c + c0 + 8 * gi + e]);
-                dec_store_granule(gHi, gLo, row, (c0 >> 3) + gi, x, SPLIT);
+                for (int e = 0; e < 8; ++e) xg[e] = x[16 * b + 8 * gi + e];
+                dec_store_granule(gHi, gLo, row, ((kCW * cq + 16 * b) >> 3) + gi, xg, SPLIT);
             }
-        }
         sync_async();
         if (tid == 0) {
             dec_mma(tmem + kColY, uG, uG2, uB + kW2Hi + 8192 * c, uB + kW2Lo + 8192 * c, kD, SPLIT, c > 0);
-            if (c + 1 < kF / kD)
-                dec_mma(tmem + kColU, uA, uA2, uB + kW1Hi + 8192 * (c + 1), uB + kW1Lo + 8192 * (c + 1), kD, SPLIT,
-                        false);
             tc::mma_commit(mb);
         }
     }
@@ -1958,8 +2005,8 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     if (ok) {
         // h += FFN + b2: back to global, or (last layer) into the shared rows
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int c0 = 32 * half + 16 * b;
+        for (int b = 0; b < kCW / 16; ++b) {
+            const int c0 = kCW * cq + 16 * b;
             uint32_t r16[16];
             tc::tmem_ld16(tl + kColY + c0, r16);
 #pragma unroll
@@ -1989,9 +2036,10 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
             float zr[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) zr[v] = g.hb[v];
+#pragma unroll
             for (int c = 0; c < kD; ++c)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) zr[v] += hf[c] * g.hw[v * kD + c];
+                for (int v = 0; v < 4; ++v) zr[v] += hf[c] * __ldg(g.hw + v * kD + c);
             if (!cond_from_logits<float>(g.x + (m0 + tid) * g.W, g.Tm, g.t, g.n_alpha, g.n_beta, zr,
                                          g.cond + (m0 + tid) * 4))
                 record_status(g.st, NNQS_E_SECTOR, m0 + tid);

@@ -158,3 +158,22 @@ def test_layout_bytes_grouped_vs_ungrouped():
     d1 = T120 * (2 * N + 12)
     assert abs(d2 / 1e9 - 2.97) < 0.01 and abs(d1 / 1e9 - 4.85) < 0.01
     assert abs((1 - d2 / d1) - 0.39) < 0.01
+
+
+def test_lr_warmup_host_call_matches_oracle():
+    """nnqs_lr_warmup is host-only: it runs without a GPU and follows the
+    oracle's Sec. 4.1 schedule; invalid arguments give 0."""
+    from oracle import vmc as OV
+    for d in (32, 64, 128):
+        for i in (1, 2, 100, 3999, 4000, 4001, 12345, 10 ** 5):
+            assert B.lr_warmup(i, d, 4000) == pytest.approx(OV.lr_warmup(i, d, 4000), rel=1e-15)
+    assert B.lr_warmup(0, 64, 4000) == 0.0 and B.lr_warmup(5, 0, 4000) == 0.0 and B.lr_warmup(5, 64, 0) == 0.0
+
+
+def test_paper_sample_schedule():
+    """N_s of Sec. 4.1: 10^5 for the first 100 iterations, then tenfold per
+    100 iterations (the reading of 'gradually') up to 10^12."""
+    from paper_2306_16705_gb300.vmc import paper_n_samples
+    assert [paper_n_samples(i) for i in (0, 99)] == [10 ** 5] * 2
+    assert [paper_n_samples(i) for i in (100, 199, 200, 700)] == [10 ** 6, 10 ** 6, 10 ** 7, 10 ** 12]
+    assert paper_n_samples(10 ** 5) == 10 ** 12

@@ -102,3 +102,33 @@ def test_checkpoint_resume_is_bit_identical():
             c.step(check=True)
         assert torch.equal(a.params, c.params)
         assert torch.equal(a.m, c.m) and torch.equal(a.v, c.v)
+
+
+def test_paper_recipe_adamw_warmup_and_sample_schedule():
+    """The Sec. 4.1 recipe through the driver: each update is the oracle's
+    AdamW step with the warm-up learning rate of that step, the sampler runs
+    N_s = 10^5 in the first iterations, and a table overflow holds N_s."""
+    from oracle import vmc as OV
+    wl = I.WORKLOADS["n12"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    model = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+    flat = model.pack(I.workload_params(wl, std=0.05, phase_std=0.05))
+    vmc = VMC(ham, model, flat.clone(), prec=B.FP32, max_unique=512, seed=2, optimizer="adamw",
+              weight_decay=0.01, schedule="paper", warmup=50)
+    th = flat.double().cpu().numpy()
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for step in range(1, 4):
+        assert vmc.current_n_samples() == 10 ** 5
+        lr = vmc.current_lr()
+        assert lr == pytest.approx(OV.lr_warmup(step, wl.d_model, 50), rel=1e-15)
+        vmc.step()
+        assert int(vmc.last_weights.sum().item()) == 10 ** 5
+        g = vmc.grad.double().cpu().numpy()
+        th, m, v = OV.adamw_step(th, g, m, v, step, lr=lr, weight_decay=0.01)
+        assert np.abs(vmc.params.double().cpu().numpy() - th).max() < 1e-6
+    # a sample count whose unique prefixes overflow the table is divided by ten
+    small = VMC(ham, model, flat.clone(), prec=B.FP32, max_unique=64, seed=2, schedule="paper")
+    small.sample()
+    assert small.ns_hold is not None and small.ns_hold < 10 ** 5

@@ -259,3 +259,20 @@ def test_energy_gate_n40_against_plain_fp64(prec):
     assert abs(ep - e64) <= 1e-6, (ep, e64)
     g64, gp = g64.double().cpu().numpy(), gp.double().cpu().numpy()
     assert np.linalg.norm(gp - g64) <= 2e-2 * np.linalg.norm(g64)
+
+
+def test_adamw_matches_oracle():
+    rng = np.random.default_rng(1)
+    n = 100003
+    theta = rng.normal(size=n).astype(np.float32)
+    pt = torch.from_numpy(theta.copy()).cuda()
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    th, mm, vv = theta.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in range(1, 4):
+        g = rng.normal(size=n).astype(np.float32)
+        B.adamw_step(pt, torch.from_numpy(g).cuda(), m, v, step, lr=3e-3, weight_decay=0.05)
+        th, mm, vv = OV.adamw_step(th, g.astype(np.float64), mm, vv, step, lr=3e-3, weight_decay=0.05)
+    assert np.abs(pt.cpu().numpy() - th).max() < 1e-6
+    with pytest.raises(B.NNQSError):
+        B.adamw_step(pt, pt, m, v, 1, lr=1.0, weight_decay=1.0)

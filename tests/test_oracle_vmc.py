@@ -2,6 +2,7 @@
 numpy's weighted average, finite differences of the exact variational energy
 E(theta) of Eq. (energy3) under full enumeration, and torch.optim.Adam."""
 import numpy as np
+import pytest
 import torch
 
 from oracle import ansatz as OA
@@ -66,3 +67,43 @@ def test_adam_matches_torch():
         opt.step()
         theta, m, v = OV.adam_step(theta, g, m, v, step)
     assert np.abs(theta - t.detach().numpy()).max() < 1e-14
+
+
+def test_adamw_matches_torch():
+    """Decoupled weight decay (Sec. 4.1 trains with AdamW) against the library
+    routine torch.optim.AdamW; a sign or order slip in the decay term fails."""
+    rng = np.random.default_rng(4)
+    theta = rng.normal(size=50)
+    t = torch.tensor(theta.copy(), requires_grad=True)
+    opt = torch.optim.AdamW([t], lr=3e-3, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.05)
+    m = np.zeros(50)
+    v = np.zeros(50)
+    for step in range(1, 6):
+        g = rng.normal(size=50)
+        t.grad = torch.tensor(g)
+        opt.step()
+        theta, m, v = OV.adamw_step(theta, g, m, v, step, lr=3e-3, weight_decay=0.05)
+    assert np.abs(theta - t.detach().numpy()).max() < 1e-14
+    # weight_decay = 0 is plain Adam
+    th0 = rng.normal(size=8)
+    g = rng.normal(size=8)
+    a = OV.adamw_step(th0, g, np.zeros(8), np.zeros(8), 1, weight_decay=0.0)
+    b = OV.adam_step(th0, g, np.zeros(8), np.zeros(8), 1)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_lr_warmup_schedule():
+    """Sec. 4.1: d^-1/2 min(i^-1/2, i S_w^-3/2): linear rise to the peak
+    (d S_w)^-1/2 at i = S_w, then i^-1/2 decay; values worked by hand for
+    d = 64, S_w = 4000."""
+    d, sw = 64, 4000
+    assert OV.lr_warmup(1, d, sw) == pytest.approx(0.125 * 4000 ** -1.5, rel=1e-15)
+    assert OV.lr_warmup(1, d, sw) == pytest.approx(4.941058844013093e-07, rel=1e-12)
+    assert OV.lr_warmup(sw, d, sw) == pytest.approx(1 / np.sqrt(256000.0), rel=1e-15)
+    assert OV.lr_warmup(sw, d, sw) == pytest.approx(0.0019764235376052372, rel=1e-12)
+    for i in (2, 17, 1000, 3999):
+        assert OV.lr_warmup(i, d, sw) == pytest.approx(i * OV.lr_warmup(1, d, sw), rel=1e-13)
+    for i in (4001, 10 ** 4, 10 ** 5):
+        assert OV.lr_warmup(i, d, sw) == pytest.approx(OV.lr_warmup(sw, d, sw) * np.sqrt(sw / i), rel=1e-13)
+    lrs = [OV.lr_warmup(i, d, sw) for i in range(1, 3 * sw)]
+    assert int(np.argmax(lrs)) + 1 == sw
