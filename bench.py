@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-samples", type=int, default=N_SAMPLES, help="N_s per step (smaller for profiling)")
     ap.add_argument("--no-layouts", action="store_true", help="skip the grouped/ungrouped layout comparison")
+    ap.add_argument("--ladder", action="store_true",
+                    help="add the local-energy speed-up ladder (Sec. 4.3) to the CPU baseline (about a minute)")
     return ap.parse_args()
 
 
@@ -157,6 +159,74 @@ class OracleStep:
                 "sample": f"log psi of {n_fwd} and local energy + reverse mode of {n_rows} of the {N_SAMPLES} "
                           f"samples (table of all {N_SAMPLES}); step time extrapolated linearly to "
                           f"{N_SAMPLES}; no sampler"}
+
+
+# The speed-up ladder of Sec. 4.3 (Fig. speedup-eloc) on molecule-shaped
+# synthetic systems: 20, 28 and 38 spin orbitals with 12, 20 and 24 electrons
+# (the STO-3G sizes of C2, LiCl and C2H4O) and the paper's unique-sample
+# counts; random integrals (rank 8), N_u uniform sector draws, a stand-in
+# log psi table.
+LADDER = (("n20", 10, 6, 6, 10553, 5), ("n28", 14, 10, 10, 9271, 6), ("n38", 19, 12, 12, 25622, 7))
+
+
+def run_ladder(budget_s: float = 2.0):
+    """E_loc of every sample of S by the three CPU rungs (oracle/ladder.c,
+    OpenMP over rows on all host cores) and by the library's sample-aware
+    sweep on the GPU.  A CPU rung is timed on the first k rows, k a multiple
+    of the core count grown until the call takes budget_s, and extrapolated
+    linearly to N_u rows; the GPU rung runs all N_u rows (CUDA events, mean
+    of 5 after 2 warm-ups).  The GPU values are checked against the +LUT
+    rung's on the timed rows."""
+    import torch
+    from oracle import hamiltonian as OH
+    from oracle import ladder as OL
+    from paper_2306_16705_gb300 import binding as B
+    from paper_2306_16705_gb300 import inputs as I
+
+    nc = cores()
+    out = {}
+    for name, n, na, nb, nu, seed in LADDER:
+        N = 2 * n
+        h, eri = I.integrals(n, seed, 8)
+        gxy, goff, gyz, gcoef = OH.group(*OH.build(h, eri))
+        S = I.random_sector_samples(n, na, nb, nu, seed=seed)
+        lp = I.random_logpsi(nu, seed=seed, amp_std=0.1)
+        table = OL.tuple_table(S, lp, N)
+        secs, rows_timed, vals = {}, {}, {}
+        for rung in OL.RUNGS:
+            k = min(nu, nc)
+            while True:
+                t0 = time.perf_counter()
+                v = OL.eloc(rung, N, gxy, goff, gyz, gcoef, S, lp, S[:k], table)
+                dt = time.perf_counter() - t0
+                if dt >= budget_s or k >= nu:
+                    break
+                grow = max(2, int(budget_s / max(dt, 1e-4)))
+                k = min(nu, (k * grow + nc - 1) // nc * nc)
+            secs[rung], rows_timed[rung], vals[rung] = dt * nu / k, k, v
+        ham = B.build_pauli(h, eri)
+        Sd = B.to_device_bits(S)
+        lpd = torch.from_numpy(np.ascontiguousarray(lp)).cuda()
+        for _ in range(2):
+            got = B.eloc(ham, Sd, lpd, na, nb)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(5):
+            got = B.eloc(ham, Sd, lpd, na, nb, check=False)
+        e1.record(st)
+        e1.synchronize()
+        secs["gpu"] = e0.elapsed_time(e1) / 5 / 1e3
+        g = got.cpu().numpy()
+        k = rows_timed["lut"]
+        ref = vals["lut"]
+        diff = float(np.max(np.abs((g[:k, 0] + 1j * g[:k, 1]) - ref)) / max(1.0, float(np.abs(ref).max())))
+        out[name] = {
+            "n_qubits": N, "electrons": na + nb, "n_u": nu, "n_terms": int(len(gcoef)), "n_groups": int(len(gxy)),
+            "seconds": secs, "speedup_vs_bare": {r: secs["bare"] / secs[r] for r in secs},
+            "cpu_rows_timed": rows_timed, "gpu_vs_lut_max_scaled_diff": diff}
+    return {"cores": nc, "note": "CPU rungs: OpenMP over rows, timed on the first k rows and extrapolated to "
+                                  "N_u; GPU: the whole N_u rows", "systems": out}
 
 
 def cores():
@@ -455,6 +525,11 @@ def run_ours(args):
         except Exception as exc:  # keep the GPU line even if the oracle cannot build here
             line["cpu_baseline"] = {"value": None, "unit": "pairs/s", "cores": cores(), "kind": "oracle",
                                     "sample": f"failed: {exc}"}
+        if args.ladder:
+            try:
+                line["cpu_baseline"]["ladder"] = run_ladder()
+            except Exception as exc:
+                line["cpu_baseline"]["ladder"] = {"failed": str(exc)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -17,7 +17,10 @@ Modules
   ansatz       The transformer amplitude / MLP phase of Sec. 3.1 with the
                number mask of Sec. 3.3, forward and hand-written reverse mode.
   vmc          Eq. (energy) statistics, the gradient estimator of Sec. 2.1,
-               exact enumeration of p(x), the Adam update.
+               exact enumeration of p(x), the Adam and AdamW updates and the
+               warm-up learning rate of Sec. 4.1.
+  ladder       The CPU rungs of the local-energy speed-up ladder of Sec. 4.3
+               (bare, SA+FUSE, +LUT), all computing the sample-aware sum.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test
 (``tests/test_oracle_*.py``) except where a docstring says "parity unpinned".
@@ -28,21 +31,21 @@ import subprocess
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "ladder.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (OpenMP over samples) into _build/."""
+    """Compile oracle.c and ladder.c with gcc (OpenMP over samples) into _build/."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                           _SRC, "-o", tmp, "-lm"])
+                           *_SRCS, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -65,5 +68,8 @@ def lib():
             L.oracle_eloc_lut.restype = ctypes.c_int
             L.oracle_eloc_lut.argtypes = [ctypes.c_int, i64, p, p, p, i64, p, p, i64, p,
                                           ctypes.c_int, ctypes.c_int, p]
+            L.ladder_eloc.restype = ctypes.c_int
+            L.ladder_eloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, p, p, p, p, i64, p, p,
+                                      p, p, i64, p, p]
             _lib = L
     return _lib
