@@ -174,8 +174,8 @@ def run_ladder(budget_s: float = 2.0):
     OpenMP over rows on all host cores) and by the library's sample-aware
     sweep on the GPU.  A CPU rung is timed on the first k rows, k a multiple
     of the core count grown until the call takes budget_s, and extrapolated
-    linearly to N_u rows; the GPU rung runs all N_u rows (CUDA events, mean
-    of 5 after 2 warm-ups).  The GPU values are checked against the +LUT
+    linearly to N_u rows; the GPU rung runs all N_u rows (CUDA events, best
+    of 3 batches of 5 calls after 0.3 s of warm-up calls).  The GPU values are checked against the +LUT
     rung's on the timed rows."""
     import torch
     from oracle import hamiltonian as OH
@@ -207,16 +207,24 @@ def run_ladder(budget_s: float = 2.0):
         ham = B.build_pauli(h, eri)
         Sd = B.to_device_bits(S)
         lpd = torch.from_numpy(np.ascontiguousarray(lp)).cuda()
-        for _ in range(2):
-            got = B.eloc(ham, Sd, lpd, na, nb)
+        got = B.eloc(ham, Sd, lpd, na, nb)
+        # the GPU sat idle during the CPU rungs: run it for ~0.3 s so the
+        # clocks are up, then take the best of 3 batches of 5 calls
+        t_end = time.perf_counter() + 0.3
+        while time.perf_counter() < t_end:
+            B.eloc(ham, Sd, lpd, na, nb, check=False)
+            torch.cuda.synchronize()
         st = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(5):
-            got = B.eloc(ham, Sd, lpd, na, nb, check=False)
-        e1.record(st)
-        e1.synchronize()
-        secs["gpu"] = e0.elapsed_time(e1) / 5 / 1e3
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(5):
+                got = B.eloc(ham, Sd, lpd, na, nb, check=False)
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 5 / 1e3)
+        secs["gpu"] = best
         g = got.cpu().numpy()
         k = rows_timed["lut"]
         ref = vals["lut"]

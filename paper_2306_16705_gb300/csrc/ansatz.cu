@@ -1146,6 +1146,53 @@ __device__ __forceinline__ void smem_to_rows(R *__restrict__ dst, const R *src, 
     }
 }
 
+// rows_to_smem with every load of a thread issued before its shared stores
+// (one memory round trip per block instead of one per 16-byte piece): up to
+// MAXV 16-byte pieces per thread, for w a multiple of the vector width, a
+// 16-byte aligned source and T * w / V <= MAXV * blockDim.x (the caller
+// checks with fits())
+template <class R, int MAXV>
+struct RowBatch {
+    static constexpr int V = int(16 / sizeof(R));
+    ColVec<R, V> v[MAXV];
+    __device__ static bool fits(const R *src, int T, int w) {
+        return w % V == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 && T * (w / V) <= MAXV * (int)blockDim.x;
+    }
+    __device__ __forceinline__ void load(const R *__restrict__ src, int T, int w) {
+        const int total = T * (w / V);
+#pragma unroll
+        for (int k = 0; k < MAXV; ++k) {
+            const int e = threadIdx.x + k * blockDim.x;
+            if (e < total) v[k] = ld_vec<R, V>(src + (int64_t)e * V);
+        }
+    }
+    __device__ __forceinline__ void store(R *dst, int ld, int T, int w) const {
+        const int wv = w / V, total = T * wv;
+#pragma unroll
+        for (int k = 0; k < MAXV; ++k) {
+            const int e = threadIdx.x + k * blockDim.x;
+            if (e < total) {
+                const int r = e / wv, c = (e - r * wv) * V;
+#pragma unroll
+                for (int q = 0; q < V; ++q) dst[r * ld + c + q] = v[k].v[q];
+            }
+        }
+    }
+};
+
+// 16-byte pieces per thread of a sample's q|k|v rows (3 d = 3 H DH columns,
+// at least H T threads): 3 DH / V, capped
+template <class R, int DH>
+constexpr int qkv_pieces() {
+    constexpr int n = (3 * DH * int(sizeof(R)) + 15) / 16;
+    return n < 1 ? 1 : (n > 12 ? 12 : n);
+}
+template <class R, int DH>
+constexpr int row_pieces() {
+    constexpr int n = (DH * int(sizeof(R)) + 15) / 16;
+    return n < 1 ? 1 : (n > 4 ? 4 : n);
+}
+
 template <class R, int DH>
 __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R *__restrict__ lse, int T, int H,
                                 int d) {
@@ -1156,7 +1203,15 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
     const int64_t i = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     const R *src = qkv + i * T * 3 * d;
-    rows_to_smem<R>(sq, ldq, src, T, 3 * d);
+    {
+        RowBatch<R, qkv_pieces<R, DH>()> b;
+        if (b.fits(src, T, 3 * d)) {
+            b.load(src, T, 3 * d);
+            b.store(sq, ldq, T, 3 * d);
+        } else {
+            rows_to_smem<R>(sq, ldq, src, T, 3 * d);
+        }
+    }
     __syncthreads();
     if (tid < H * T) {
         const int hh = tid % H, q = tid / H;  // heads fastest: a warp holds a few positions (even loop trips)
@@ -1208,10 +1263,28 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     R *sD = slse + H * T;                    // [H][T]
     const int64_t i = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
-    rows_to_smem<R>(sq, ldq, qkv + i * T * 3 * d, T, 3 * d);
-    rows_to_smem<R>(sdo, ldo, dout + i * T * d, T, d);
-    rows_to_smem<R>(so, ldo, o + i * T * d, T, d);
-    for (int e = tid; e < H * T; e += nt) slse[e] = lse[i * H * T + e];
+    {
+        // all three blocks' loads in flight together
+        const R *s1 = qkv + i * T * 3 * d, *s2 = dout + i * T * d, *s3 = o + i * T * d;
+        RowBatch<R, qkv_pieces<R, DH>()> b1;
+        RowBatch<R, row_pieces<R, DH>()> b2, b3;
+        const bool f = b1.fits(s1, T, 3 * d) && b2.fits(s2, T, d) && b3.fits(s3, T, d);
+        R l0 = tid < H * T ? lse[i * H * T + tid] : R(0);
+        if (f) {
+            b1.load(s1, T, 3 * d);
+            b2.load(s2, T, d);
+            b3.load(s3, T, d);
+            b1.store(sq, ldq, T, 3 * d);
+            b2.store(sdo, ldo, T, d);
+            b3.store(so, ldo, T, d);
+        } else {
+            rows_to_smem<R>(sq, ldq, s1, T, 3 * d);
+            rows_to_smem<R>(sdo, ldo, s2, T, d);
+            rows_to_smem<R>(so, ldo, s3, T, d);
+        }
+        if (tid < H * T) slse[tid] = l0;
+        for (int e = tid + nt; e < H * T; e += nt) slse[e] = lse[i * H * T + e];
+    }
     __syncthreads();
     const R scale = R(1) / sqrt(R(DH));
     const bool act = tid < H * T;
