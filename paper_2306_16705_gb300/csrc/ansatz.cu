@@ -1129,10 +1129,16 @@ __device__ __forceinline__ void smem_to_rows(R *__restrict__ dst, const R *src, 
         const int wv = w / V, nt = blockDim.x;
         const int sr = nt / wv, sc = nt % wv;
         int r = threadIdx.x / wv, c = threadIdx.x % wv;
+        const bool vec = ld % V == 0;  // 16-byte shared rows
         while (r < T) {
             ColVec<R, V> v;
+            if (vec) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(src + r * ld + c * V);
+                memcpy(&v, &u, 16);
+            } else {
 #pragma unroll
-            for (int e = 0; e < V; ++e) v.v[e] = src[r * ld + c * V + e];
+                for (int e = 0; e < V; ++e) v.v[e] = src[r * ld + c * V + e];
+            }
             *reinterpret_cast<ColVec<R, V> *>(dst + (int64_t)r * w + c * V) = v;
             r += sr;
             c += sc;
@@ -1168,13 +1174,20 @@ struct RowBatch {
     }
     __device__ __forceinline__ void store(R *dst, int ld, int T, int w) const {
         const int wv = w / V, total = T * wv;
+        const bool vec = ld % V == 0;  // 16-byte shared rows
 #pragma unroll
         for (int k = 0; k < MAXV; ++k) {
             const int e = threadIdx.x + k * blockDim.x;
             if (e < total) {
                 const int r = e / wv, c = (e - r * wv) * V;
+                if (vec) {
+                    uint4 u;
+                    memcpy(&u, &v[k], 16);
+                    *reinterpret_cast<uint4 *>(dst + r * ld + c) = u;
+                } else {
 #pragma unroll
-                for (int q = 0; q < V; ++q) dst[r * ld + c + q] = v[k].v[q];
+                    for (int q = 0; q < V; ++q) dst[r * ld + c + q] = v[k].v[q];
+                }
             }
         }
     }
@@ -1193,15 +1206,56 @@ constexpr int row_pieces() {
     return n < 1 ? 1 : (n > 4 ? 4 : n);
 }
 
+// DH consecutive values of one head from shared memory: 16-byte reads when
+// DH is a multiple of the vector width and the rows are unpadded (kVec),
+// else scalar reads (padded rows)
+template <class R, int DH>
+struct HeadVec {
+    static constexpr int V = int(16 / sizeof(R));
+    static constexpr bool kVec = DH % V == 0;
+    __device__ __forceinline__ static void read(const R *p, R (&out)[DH]) {
+        if constexpr (kVec) {
+#pragma unroll
+            for (int c = 0; c < DH; c += V) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(p + c);
+                R tmp[V];
+                memcpy(tmp, &u, 16);
+#pragma unroll
+                for (int e = 0; e < V; ++e) out[c + e] = tmp[e];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < DH; ++c) out[c] = p[c];
+        }
+    }
+    __device__ __forceinline__ static void write(R *p, const R (&in)[DH]) {
+        if constexpr (kVec) {
+#pragma unroll
+            for (int c = 0; c < DH; c += V) {
+                uint4 u;
+                memcpy(&u, in + c, 16);
+                *reinterpret_cast<uint4 *>(p + c) = u;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < DH; ++c) p[c] = in[c];
+        }
+    }
+    // row stride in shared memory for w columns: unpadded (16-byte rows) for
+    // vector reads, else padded by one against bank conflicts
+    __host__ __device__ static constexpr int ld(int w) { return kVec ? w : w + 1; }
+};
+
 template <class R, int DH>
 __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R *__restrict__ lse, int T, int H,
                                 int d) {
+    using HV = HeadVec<R, DH>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    R *sq = reinterpret_cast<R *>(sm_raw);  // [T][3d+1]
-    const int ldq = 3 * d + 1, ldo = d + 1;
-    R *so = sq + T * ldq;                    // [T][d+1]
+    R *sq = reinterpret_cast<R *>(sm_raw);  // [T][ldq]
+    const int ldq = HV::ld(3 * d), ldo = HV::ld(d);
+    R *so = sq + T * ldq;                    // [T][ldo]
     const int64_t i = blockIdx.x;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x;
     const R *src = qkv + i * T * 3 * d;
     {
         RowBatch<R, qkv_pieces<R, DH>()> b;
@@ -1217,15 +1271,17 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
         const int hh = tid % H, q = tid / H;  // heads fastest: a warp holds a few positions (even loop trips)
         const R scale = R(1) / sqrt(R(DH));
         R qv[DH], acc[DH];
+        HV::read(sq + q * ldq + hh * DH, qv);
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
-            qv[c] = sq[q * ldq + hh * DH + c] * scale;
+            qv[c] = qv[c] * scale;
             acc[c] = 0;
         }
         R m = neg_inf<R>(), l = 0;
         for (int j = 0; j <= q; ++j) {
-            const R *kj = sq + j * ldq + d + hh * DH;
-            const R *vj = sq + j * ldq + 2 * d + hh * DH;
+            R kj[DH], vj[DH];
+            HV::read(sq + j * ldq + d + hh * DH, kj);
+            HV::read(sq + j * ldq + 2 * d + hh * DH, vj);
             R sc = 0;
 #pragma unroll
             for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
@@ -1239,7 +1295,8 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
         }
         const R inv = R(1) / l;
 #pragma unroll
-        for (int c = 0; c < DH; ++c) so[q * ldo + hh * DH + c] = acc[c] * inv;
+        for (int c = 0; c < DH; ++c) acc[c] = acc[c] * inv;
+        HV::write(so + q * ldo + hh * DH, acc);
         lse[(i * H + hh) * T + q] = m + log_<R>(l);
     }
     __syncthreads();
@@ -1253,12 +1310,13 @@ template <class R, int DH>
 __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__ o, const R *__restrict__ lse,
                                 const R *__restrict__ dout, R *__restrict__ dqkv, int T, int H, int d,
                                 R *__restrict__ colsum) {
+    using HV = HeadVec<R, DH>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int ldq = 3 * d + 1, ldo = d + 1;
-    R *sq = reinterpret_cast<R *>(sm_raw);  // q|k|v [T][3d+1]
-    R *sg = sq + T * ldq;                    // dq|dk|dv [T][3d+1]
-    R *sdo = sg + T * ldq;                   // dout [T][d+1]
-    R *so = sdo + T * ldo;                   // o [T][d+1]
+    const int ldq = HV::ld(3 * d), ldo = HV::ld(d);
+    R *sq = reinterpret_cast<R *>(sm_raw);  // q|k|v [T][ldq]
+    R *sg = sq + T * ldq;                    // dq|dk|dv [T][ldq]
+    R *sdo = sg + T * ldq;                   // dout [T][ldo]
+    R *so = sdo + T * ldo;                   // o [T][ldo]
     R *slse = so + T * ldo;                  // [H][T]
     R *sD = slse + H * T;                    // [H][T]
     const int64_t i = blockIdx.x;
@@ -1292,20 +1350,23 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     if (act) {
         // dq_q = scale sum_{j<=q} p_qj (dp_qj - D_q) k_j,  D_q = do_q . o_q
         const int q = pos;
-        R qv[DH], dov[DH], dq[DH];
+        R qv[DH], dov[DH], ov[DH], dq[DH];
+        HV::read(sq + q * ldq + hh * DH, qv);
+        HV::read(sdo + q * ldo + hh * DH, dov);
+        HV::read(so + q * ldo + hh * DH, ov);
         R D = 0;
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
-            qv[c] = sq[q * ldq + hh * DH + c] * scale;
-            dov[c] = sdo[q * ldo + hh * DH + c];
-            D += dov[c] * so[q * ldo + hh * DH + c];
+            qv[c] = qv[c] * scale;
+            D += dov[c] * ov[c];
             dq[c] = 0;
         }
         sD[hh * T + q] = D;
         const R L = slse[hh * T + q];
         for (int j = 0; j <= q; ++j) {
-            const R *kj = sq + j * ldq + d + hh * DH;
-            const R *vj = sq + j * ldq + 2 * d + hh * DH;
+            R kj[DH], vj[DH];
+            HV::read(sq + j * ldq + d + hh * DH, kj);
+            HV::read(sq + j * ldq + 2 * d + hh * DH, vj);
             R sc = 0, dp = 0;
 #pragma unroll
             for (int c = 0; c < DH; ++c) {
@@ -1317,22 +1378,22 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
             for (int c = 0; c < DH; ++c) dq[c] += ds * kj[c];
         }
 #pragma unroll
-        for (int c = 0; c < DH; ++c) sg[q * ldq + hh * DH + c] = dq[c] * scale;
+        for (int c = 0; c < DH; ++c) dq[c] = dq[c] * scale;
+        HV::write(sg + q * ldq + hh * DH, dq);
     }
     __syncthreads();
     if (act) {
         // dv_j = sum_{q>=j} p_qj do_q,  dk_j = scale sum_{q>=j} p_qj (dp_qj - D_q) q_q
         const int j = pos;
         R kv[DH], vv[DH], dk[DH], dv[DH];
+        HV::read(sq + j * ldq + d + hh * DH, kv);
+        HV::read(sq + j * ldq + 2 * d + hh * DH, vv);
 #pragma unroll
-        for (int c = 0; c < DH; ++c) {
-            kv[c] = sq[j * ldq + d + hh * DH + c];
-            vv[c] = sq[j * ldq + 2 * d + hh * DH + c];
-            dk[c] = dv[c] = 0;
-        }
+        for (int c = 0; c < DH; ++c) dk[c] = dv[c] = 0;
         for (int q = j; q < T; ++q) {
-            const R *qq = sq + q * ldq + hh * DH;
-            const R *dq = sdo + q * ldo + hh * DH;
+            R qq[DH], dq[DH];
+            HV::read(sq + q * ldq + hh * DH, qq);
+            HV::read(sdo + q * ldo + hh * DH, dq);
             R sc = 0, dp = 0;
 #pragma unroll
             for (int c = 0; c < DH; ++c) {
@@ -1348,10 +1409,9 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
             }
         }
 #pragma unroll
-        for (int c = 0; c < DH; ++c) {
-            sg[j * ldq + d + hh * DH + c] = dk[c] * scale;
-            sg[j * ldq + 2 * d + hh * DH + c] = dv[c];
-        }
+        for (int c = 0; c < DH; ++c) dk[c] = dk[c] * scale;
+        HV::write(sg + j * ldq + d + hh * DH, dk);
+        HV::write(sg + j * ldq + 2 * d + hh * DH, dv);
     }
     __syncthreads();
     smem_to_rows<R>(dqkv + i * T * 3 * d, sg, ldq, T, 3 * d);
