@@ -73,6 +73,32 @@ __global__ void k_build_lut_hash(const uint64_t *__restrict__ lut, int64_t n_lut
     tab.vals[slot] = (int32_t)i;
 }
 
+// the table's largest log|psi| (one block; max is order-free)
+__global__ void k_lp_max(const double2 *__restrict__ lp, int64_t n, double *__restrict__ amax) {
+    __shared__ double sh[1024];
+    double m = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, lp[i].x);
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + off]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *amax = sh[0];
+}
+
+// psi[j] = exp(log|psi_j| - A) (cos phase_j, sin phase_j)
+__global__ void k_lut_psi(const double2 *__restrict__ lp, int64_t n, const double *__restrict__ amax,
+                          double2 *__restrict__ psi) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double2 v = lp[j];
+    const double m = exp(v.x - *amax);
+    double s, c;
+    sincos(v.y, &s, &c);
+    psi[j] = make_double2(m * c, m * s);
+}
+
 // GROUPS sweep.  grid = (row tiles of 128, group chunks).
 template <int W>
 __global__ void __launch_bounds__(kSweepThreads)
@@ -80,17 +106,19 @@ __global__ void __launch_bounds__(kSweepThreads)
                    const uint8_t *__restrict__ gspin, int64_t g_begin, int64_t g_end,
                    int64_t groups_per_chunk, const uint64_t *__restrict__ tyz,
                    const double *__restrict__ tcoef, const uint64_t *__restrict__ lut,
-                   const double2 *__restrict__ lut_lp, HashTab<W> tab, int64_t row_begin,
+                   const double2 *__restrict__ lut_lp, const double2 *__restrict__ psi,
+                   const double *__restrict__ amax, HashTab<W> tab, int64_t row_begin,
                    int64_t n_rows, double2 *__restrict__ partial) {
     __shared__ uint64_t s_xy[kGroupTile * W];
     __shared__ uint8_t s_spin[kGroupTile];
     const int64_t r = blockIdx.x * (int64_t)kSweepThreads + threadIdx.x;
     const bool active = r < n_rows;
     Bits<W> x{};
-    double2 lx = make_double2(0.0, 0.0);
+    RowRatio rx;
+    rx.init(make_double2(0.0, 0.0), nullptr);
     if (active) {
         x = load_bits<W>(lut, row_begin + r);
-        lx = lut_lp[row_begin + r];
+        rx.init(lut_lp[row_begin + r], amax);
     }
     const int64_t c0 = g_begin + blockIdx.y * groups_per_chunk;
     const int64_t c1 = min(g_end, c0 + groups_per_chunk);
@@ -119,7 +147,7 @@ __global__ void __launch_bounds__(kSweepThreads)
             if (j < 0) continue;
             const int64_t g = gt + k;
             const double coef = group_coef<W>(x, __ldg(goff + g), __ldg(goff + g + 1), tyz, tcoef);
-            const double2 q = ratio(lx, lut_lp[j]);
+            const double2 q = rx.of(psi, lut_lp, j);
             er += coef * q.x;
             ei += coef * q.y;
         }
@@ -137,17 +165,19 @@ template <int W>
 __global__ void __launch_bounds__(kSweepThreads)
     k_sweep_terms(const uint64_t *__restrict__ txy, const uint64_t *__restrict__ tyz,
                   const double *__restrict__ tcoef, int64_t t_begin, int64_t t_end, int64_t terms_per_chunk,
-                  const uint64_t *__restrict__ lut, const double2 *__restrict__ lut_lp, HashTab<W> tab,
+                  const uint64_t *__restrict__ lut, const double2 *__restrict__ lut_lp,
+                  const double2 *__restrict__ psi, const double *__restrict__ amax, HashTab<W> tab,
                   int64_t row_begin, int64_t n_rows, double2 *__restrict__ partial) {
     __shared__ uint64_t s_xy[kTermTile * W], s_yz[kTermTile * W];
     __shared__ double s_c[kTermTile];
     const int64_t r = blockIdx.x * (int64_t)kSweepThreads + threadIdx.x;
     const bool active = r < n_rows;
     Bits<W> x{};
-    double2 lx = make_double2(0.0, 0.0);
+    RowRatio rx;
+    rx.init(make_double2(0.0, 0.0), nullptr);
     if (active) {
         x = load_bits<W>(lut, row_begin + r);
-        lx = lut_lp[row_begin + r];
+        rx.init(lut_lp[row_begin + r], amax);
     }
     const int64_t c0 = t_begin + blockIdx.y * terms_per_chunk;
     const int64_t c1 = min(t_end, c0 + terms_per_chunk);
@@ -181,7 +211,7 @@ __global__ void __launch_bounds__(kSweepThreads)
             const int32_t j = tab.find(xp);
             if (j < 0) continue;
             const double c = (par & 1) ? -s_c[k] : s_c[k];
-            const double2 q = ratio(lx, lut_lp[j]);
+            const double2 q = rx.of(psi, lut_lp, j);
             er += c * q.x;
             ei += c * q.y;
         }
@@ -193,6 +223,7 @@ __global__ void __launch_bounds__(kSweepThreads)
 template <int W>
 __global__ void __launch_bounds__(kSweepThreads)
     k_sweep_pairs(const uint64_t *__restrict__ lut, const double2 *__restrict__ lut_lp,
+                  const double2 *__restrict__ psi, const double *__restrict__ amax,
                   int64_t n_lut, int64_t cols_per_chunk, int max_weight, HashTab<W> gtab,
                   const uint32_t *__restrict__ goff, const uint64_t *__restrict__ tyz,
                   const double *__restrict__ tcoef, int64_t row_begin, int64_t n_rows,
@@ -201,7 +232,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     const int lane = threadIdx.x & 31;
     const int64_t rbase = blockIdx.x * (int64_t)(kSweepThreads * kPairRows);
     Bits<W> x[kPairRows];
-    double2 lx[kPairRows];
+    RowRatio rx[kPairRows];
     bool act[kPairRows];
     double er[kPairRows], ei[kPairRows];
 #pragma unroll
@@ -211,11 +242,11 @@ __global__ void __launch_bounds__(kSweepThreads)
         er[q] = ei[q] = 0.0;
         if (act[q]) {
             x[q] = load_bits<W>(lut, row_begin + r);
-            lx[q] = lut_lp[row_begin + r];
+            rx[q].init(lut_lp[row_begin + r], amax);
         } else {
 #pragma unroll
             for (int w = 0; w < W; ++w) x[q].w[w] = 0;
-            lx[q] = make_double2(0.0, 0.0);
+            rx[q].init(make_double2(0.0, 0.0), nullptr);
         }
     }
     const int64_t c0 = blockIdx.y * cols_per_chunk;
@@ -251,7 +282,7 @@ __global__ void __launch_bounds__(kSweepThreads)
             double2 rr[kPairRows];
 #pragma unroll
             for (int q = 0; q < kPairRows; ++q)
-                rr[q] = g[q] >= 0 ? ratio(lx[q], lut_lp[ct + k]) : make_double2(0.0, 0.0);
+                rr[q] = g[q] >= 0 ? rx[q].of(psi, lut_lp, ct + k) : make_double2(0.0, 0.0);
             while (hits) {
                 const int leader = __ffs(hits) - 1;
                 hits &= hits - 1;
@@ -293,16 +324,6 @@ struct SaPlan {
     bool has_diag;
 };
 
-int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-    }
-    return sms;
-}
 
 SaPlan plan_sa(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags) {
     SaPlan p{};
@@ -361,6 +382,8 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
     int32_t *hvals = ws.take<int32_t>(size_t(cap));
     double *diag = ws.take<double>(size_t(std::max<int64_t>(1, n_rows)));
     double2 *partial = ws.take<double2>(size_t(std::max<int64_t>(1, p.chunks * n_rows)));
+    double2 *psi = ws.take<double2>(size_t(std::max<int64_t>(1, n_lut)));
+    double *amax = ws.take<double>(1);
     if (ws.base == nullptr) return NNQS_OK;  // sizing pass
 
     if (n_rows == 0) return NNQS_OK;
@@ -373,13 +396,17 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
     }
     const double2 *lp2 = reinterpret_cast<const double2 *>(lut_lp);
     if (p.chunks > 0) {
+        NNQS_LAUNCH("k_lut_psi", s, k_lp_max<<<1, 1024, 0, s>>>(lp2, n_lut, amax));
+        NNQS_LAUNCH("k_lut_psi", s, k_lut_psi<<<grid_for(n_lut, 256), 256, 0, s>>>(lp2, n_lut, amax, psi));
+    }
+    if (p.chunks > 0) {
         dim3 grid((unsigned)p.row_tiles, (unsigned)p.chunks);
         if (p.terms) {
             if (!H->d_txy) return set_error(NNQS_E_INVAL, "ungrouped layout not built");
             note_work("k_sweep_terms", double(n_rows) * double(p.g_end - p.g_begin),
                       double(p.row_tiles) * double(p.g_end - p.g_begin) * (16.0 * W + 8.0));
             NNQS_LAUNCH("k_sweep_terms", s, k_sweep_terms<W><<<grid, kSweepThreads, 0, s>>>(H->d_txy, H->d_tyz, H->d_tcoef, p.g_begin, p.g_end,
-                                                             p.per_chunk, lut, lp2, tab, row_begin, n_rows, partial));
+                                                             p.per_chunk, lut, lp2, psi, amax, tab, row_begin, n_rows, partial));
         } else if (p.pairs) {
             const int maxw = H->max_xy_weight;
             // algorithmic work: one (row, sample) mask test each; bytes = one
@@ -387,13 +414,13 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
             note_work("k_sweep_pairs", double(n_rows) * double(n_lut),
                       double(p.row_tiles) * double(n_lut) * (8.0 * W + 16.0));
             HashTab<W> gtab{H->d_ghkeys, H->d_ghvals, uint64_t(H->ghcap - 1)};
-            NNQS_LAUNCH("k_sweep_pairs", s, k_sweep_pairs<W><<<grid, kSweepThreads, 0, s>>>(lut, lp2, n_lut, p.per_chunk, maxw, gtab, H->d_goff,
+            NNQS_LAUNCH("k_sweep_pairs", s, k_sweep_pairs<W><<<grid, kSweepThreads, 0, s>>>(lut, lp2, psi, amax, n_lut, p.per_chunk, maxw, gtab, H->d_goff,
                                                             H->d_tyz, H->d_tcoef, row_begin, n_rows, partial));
         } else {
             note_work("k_sweep_groups", double(n_rows) * double(p.g_end - p.g_begin),
                       double(p.row_tiles) * double(p.g_end - p.g_begin) * (8.0 * W + 1.0));
             NNQS_LAUNCH("k_sweep_groups", s, k_sweep_groups<W><<<grid, kSweepThreads, 0, s>>>(H->d_gxy, H->d_goff, H->d_gspin, p.g_begin, p.g_end,
-                                                             p.per_chunk, H->d_tyz, H->d_tcoef, lut, lp2, tab,
+                                                             p.per_chunk, H->d_tyz, H->d_tcoef, lut, lp2, psi, amax, tab,
                                                              row_begin, n_rows, partial));
         }
         NNQS_CUDA_TRY(cudaGetLastError());
@@ -486,6 +513,17 @@ nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, doubl
     NNQS_LAUNCH("k_stats", s, k_stats<<<1, kStatThreads, 3 * kStatThreads * sizeof(double), s>>>(reinterpret_cast<const double2 *>(eloc), w, n,
                                                                         stats));
     return NNQS_OK;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms;
 }
 
 }  // namespace nnqs

@@ -113,6 +113,7 @@ nnqs_status upload_ham(nnqs_ham *H);
 uint64_t hash_words(const uint64_t *k, int W);  // same mix as the device hash
 
 // eloc.cu
+int num_sms();  // SMs of the current device (152 if the query fails)
 size_t eloc_sa_workspace(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags);
 nnqs_status eloc_sa(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp, int64_t n_lut,
                     int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int flags,

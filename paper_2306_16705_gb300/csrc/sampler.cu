@@ -413,8 +413,12 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
             NNQS_TRY(cond_step_cached(M, ctx, L.pref[cur], n, t, g_cur, L.anc[cur], L.cond, st, s));
         else
             NNQS_TRY(cond_step(M, ctx, L.pref[cur], n, t + 1, L.cond, st, s));
-        NNQS_LAUNCH("k_split", s, k_split<<<grid_for(n, 128), 128, 0, s>>>(L.w[cur], L.cond, n, t, seed, L.counts,
-                                                                           L.nchild, st));
+        // the binomial draws are FP64-bound: few prefixes (the early steps,
+        // counts in the thousands) are spread one or a few per block over
+        // the SMs instead of sharing one SM's FP64 pipe
+        const int split_block = (int)std::min<int64_t>(128, std::max<int64_t>(1, (n + num_sms() - 1) / num_sms()));
+        NNQS_LAUNCH("k_split", s, k_split<<<(unsigned)((n + split_block - 1) / split_block), split_block, 0, s>>>(
+                                      L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st));
         const int64_t nb = (n + kScan - 1) / kScan;
         if (n <= kScanOne) {
             NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, n, L.off, L.total));

@@ -27,6 +27,38 @@ __device__ __forceinline__ double2 ratio(double2 lx, double2 ly) {
     return make_double2(mag * c, mag * s);
 }
 
+// psi(y)/psi(x) for one row x against table samples y.  With the table
+// psi[j] = exp(log|psi_j| - A) e^{i phase_j} (A = the table's largest
+// log|psi|, k_lut_psi) a ratio is one complex product with the row factor
+// exp(A - log|psi(x)|) e^{-i phase(x)}: no FP64 exp / sincos per coupled
+// sample.  Rows far below the table's maximum (A - log|psi(x)| > 600, where
+// the factor or psi[j] could leave the FP64 range) and tables whose maximum is
+// not finite keep the direct form.  The two forms differ by a few ulp.
+struct RowRatio {
+    double2 lx, f;
+    bool table;
+    __device__ __forceinline__ void init(double2 lx_, const double *__restrict__ amax) {
+        lx = lx_;
+        const double a = amax ? *amax : 0.0;
+        table = amax != nullptr && a - lx.x <= 600.0;
+        f = make_double2(0.0, 0.0);
+        if (table) {
+            const double m = exp(a - lx.x);
+            double s, c;
+            sincos(lx.y, &s, &c);
+            f = make_double2(m * c, -m * s);
+        }
+    }
+    __device__ __forceinline__ double2 of(const double2 *__restrict__ psi, const double2 *__restrict__ lp,
+                                          int64_t j) const {
+        if (table) {
+            const double2 p = psi[j];
+            return make_double2(p.x * f.x - p.y * f.y, p.x * f.y + p.y * f.x);
+        }
+        return ratio(lx, lp[j]);
+    }
+};
+
 // H_xx for each row: one warp per row over the diagonal group's terms,
 // lane-strided then shuffled in a fixed order.
 template <int W>

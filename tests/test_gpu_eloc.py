@@ -225,3 +225,23 @@ def test_ungrouped_terms_sweep_equals_grouped(n40):
     ref = OH.eloc_lut(*OH.build(h, eri), lut2, lp2, lut2, 3, 2)
     got = run_gpu(ham2, lut2, lp2, 3, 2, B.SWEEP_TERMS)
     assert np.all(np.abs(got - ref) <= TOL * abs_scale(OH.build(h, eri), lut2, lp2, lut2, 3, 2))
+
+
+@pytest.mark.parametrize("flags", [B.SWEEP_GROUPS, B.SWEEP_PAIRS, B.SWEEP_TERMS])
+def test_ratio_table_and_direct_rows(n12, flags):
+    """Every coupled sample is a hit on the whole 12-qubit sector.  The ratio
+    psi(x')/psi(x) comes from the per-sample table psi = exp(log|psi| - max)
+    e^{i phase} for ordinary rows, and from the direct FP64 exp / sincos for
+    rows more than 600 below the table's largest log|psi| (every 7th row
+    here, 650 below): both against the oracle's direct exp."""
+    wl, h, eri, ham, strings = n12
+    if flags == B.SWEEP_TERMS:
+        ham.build_ungrouped()
+    lut = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    lp = I.random_logpsi(len(lut), seed=21, amp_std=0.3)
+    lp[::7, 0] -= 650.0
+    got = run_gpu(ham, lut, lp, wl.n_alpha, wl.n_beta, flags)
+    ref = OH.eloc_lut(*strings, lut, lp, lut, wl.n_alpha, wl.n_beta)
+    sc = abs_scale(strings, lut, lp, lut, wl.n_alpha, wl.n_beta)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= TOL * sc)
