@@ -478,18 +478,21 @@ __global__ void __launch_bounds__(kColThreads) k_colred(const R *__restrict__ A,
                                                         const R *__restrict__ mean, const R *__restrict__ rstd,
                                                         int64_t rows, int cols, int64_t rows_per_block,
                                                         R *__restrict__ partial, unsigned *counter,
-                                                        R *__restrict__ out0, R *__restrict__ out1) {
+                                                        R *__restrict__ out0, R *__restrict__ out1,
+                                                        int chunk_cv, int last_reduce) {
     __shared__ R sh[(MODE ? 2 : 1) * kColThreads * VW];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const int64_t r0 = blockIdx.x * rows_per_block;
     const int64_t r1 = min(rows, r0 + rows_per_block);
     const int64_t pcols = (MODE ? 2 : 1) * (int64_t)cols;
-    const int cv = cols / VW;                // vector columns
-    const int ct = min(cv, kColThreads);     // threads per row within a column tile
-    const int phases = kColThreads / ct;     // rows in parallel
+    // vector columns of this block: chunk blockIdx.y of chunk_cv
+    const int cv_all = cols / VW;
+    const int cbeg = blockIdx.y * chunk_cv, cv = min(cv_all, cbeg + chunk_cv);
+    const int ct = min(cv - cbeg, kColThreads);  // threads per row within a column tile
+    const int phases = kColThreads / ct;         // rows in parallel
     const int p = tid / ct, j = tid % ct;
-    for (int v0 = 0; v0 < cv; v0 += ct) {
+    for (int v0 = cbeg; v0 < cv; v0 += ct) {
         const int vc = v0 + j;
         const bool act = p < phases && vc < cv;
         R acc[VW], acc2[VW];
@@ -559,10 +562,12 @@ __global__ void __launch_bounds__(kColThreads) k_colred(const R *__restrict__ A,
         }
         __syncthreads();
     }
-    // last block: add the partial rows of all blocks, in block order
+    // last block: add the partial rows of all blocks, in block order (wide
+    // rows leave this to k_sum_partials, spread over the columns)
+    if (!last_reduce) return;
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -571,13 +576,14 @@ __global__ void __launch_bounds__(kColThreads) k_colred(const R *__restrict__ A,
     if (tid == 0) *counter = 0u;
 }
 
-// out[c] += sum_b partial[b][c]; block x takes columns [32 x, 32 x + 32)
+// out[c] += sum_b partial[b][c] for c < cols, partial rows ld apart; block x
+// takes columns [32 x, 32 x + 32)
 template <class R>
 __global__ void __launch_bounds__(kColThreads) k_sum_partials(const R *__restrict__ partial, int64_t nblk,
-                                                              int64_t cols, R *__restrict__ out) {
+                                                              int64_t cols, R *__restrict__ out, int64_t ld = -1) {
     __shared__ R sh[kColThreads];
     const int64_t c0 = blockIdx.x * 32;
-    sum_partial_rows<R, 1>(partial, nblk, cols, (int)c0, (int)min(cols, c0 + 32), out, sh);
+    sum_partial_rows<R, 1>(partial, nblk, ld < 0 ? cols : ld, (int)c0, (int)min(cols, c0 + 32), out, sh);
 }
 
 // ---- LayerNorm backward with its parameter gradients (FP32, d = 4 LPR)
@@ -920,20 +926,35 @@ nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *me
     const bool vec = cols % V == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
                      (mode == 0 || reinterpret_cast<uintptr_t>(X) % 16 == 0);
     const int64_t pc = (mode ? 2 : 1) * (int64_t)cols;
-    int64_t nblk = std::min<int64_t>((rows + 63) / 64, 2 * sm_count());
+    // wide rows (more than 64 vector columns): 32-vector-column chunks over
+    // blockIdx.y (8 rows in flight per block instead of one or two), the
+    // partial rows then added column-parallel by k_sum_partials
+    const int vw = vec ? V : 1;
+    const int cv = cols / vw;
+    const bool wide = cv > 64;
+    const int chunk_cv = wide ? 32 : cv;
+    const int64_t n_chunks = (cv + chunk_cv - 1) / chunk_cv;
+    int64_t nblk = wide ? std::min<int64_t>((rows + 63) / 64, (8 * sm_count() + n_chunks - 1) / n_chunks)
+                        : std::min<int64_t>((rows + 63) / 64, 2 * sm_count());
     nblk = std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(pc)));
     nblk = std::max<int64_t>(nblk, 1);
     const int64_t rpb = (rows + nblk - 1) / nblk;
     nblk = (rows + rpb - 1) / rpb;
-    const unsigned g = (unsigned)nblk;
+    const dim3 g((unsigned)nblk, (unsigned)n_chunks);
+    const int lr = wide ? 0 : 1;
     if (mode == 0 && vec)
-        NNQS_LAUNCH("k_colred", s, (k_colred<R, 0, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 0, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1, chunk_cv, lr)));
     else if (mode == 0)
-        NNQS_LAUNCH("k_colred", s, (k_colred<R, 0, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 0, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1, chunk_cv, lr)));
     else if (vec)
-        NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, V><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1, chunk_cv, lr)));
     else
-        NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1)));
+        NNQS_LAUNCH("k_colred", s, (k_colred<R, 1, 1><<<g, kColThreads, 0, s>>>(A, X, mean, rstd, rows, cols, rpb, scr.buf, scr.ctr, out0, out1, chunk_cv, lr)));
+    if (wide) {
+        NNQS_LAUNCH("k_colred", s, (k_sum_partials<R><<<(unsigned)((cols + 31) / 32), kColThreads, 0, s>>>(scr.buf, nblk, cols, out0, pc)));
+        if (mode)
+            NNQS_LAUNCH("k_colred", s, (k_sum_partials<R><<<(unsigned)((cols + 31) / 32), kColThreads, 0, s>>>(scr.buf + cols, nblk, cols, out1, pc)));
+    }
     return NNQS_OK;
 }
 
@@ -2332,29 +2353,56 @@ __global__ void __launch_bounds__(kColThreads) k_head_bwd_fused(const R *__restr
 // blocked form: thread u of a block keeps weight column u and walks 32
 // samples (bits staged in shared memory); same sum order as k_phase_in
 constexpr int kPhaseRows = 32;
+// w1t[j][u] = w1[u][j]: the phase layer's input weights with the hidden unit
+// fastest, so a warp reads 32 consecutive units of one input
 template <class R>
-__global__ void k_phase_in_blk(const uint64_t *__restrict__ x, int W, int N, const R *__restrict__ w1,
-                               const R *__restrict__ b1, int64_t n, int P, R *__restrict__ z1, R *__restrict__ r1,
-                               R *__restrict__ xf) {
-    __shared__ uint64_t xs[kPhaseRows * 2];
+__global__ void k_phase_w1t(const R *__restrict__ w1, int P, int N, R *__restrict__ w1t) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)P * N) return;
+    const int u = (int)(idx / N), j = (int)(idx % N);
+    w1t[(int64_t)j * P + u] = w1[idx];
+}
+
+// kPhaseRows samples per block, thread = hidden unit u: z1 = b1 + the sum of
+// w1[u][j] over the occupied qubits j of the sample, in ascending j (the sum
+// k_phase_in forms); the samples' bits sit in registers, and a warp reads 32
+// consecutive units of input j from the transposed weights
+// samples per block: 32 (FP32), 16 (FP64), so that a thread's sums and bits
+// fit in the registers of a 512-thread block
+template <class R>
+constexpr int phase_rows() { return sizeof(R) == 8 ? 16 : kPhaseRows; }
+
+template <class R>
+__global__ void __launch_bounds__(512) k_phase_in_blk(const uint64_t *__restrict__ x, int W, int N,
+                                                      const R *__restrict__ w1t, const R *__restrict__ b1, int64_t n,
+                                                      int P, R *__restrict__ z1, R *__restrict__ r1,
+                                                      R *__restrict__ xf) {
+    constexpr int NR = phase_rows<R>();
+    __shared__ uint64_t xs[NR * 2];
     const int u = threadIdx.x;
-    const int64_t i0 = blockIdx.x * (int64_t)kPhaseRows;
-    const int ns = (int)min((int64_t)kPhaseRows, n - i0);
-    for (int k = threadIdx.x; k < ns * W; k += blockDim.x) xs[k] = x[i0 * W + k];
+    const int64_t i0 = blockIdx.x * (int64_t)NR;
+    const int ns = (int)min((int64_t)NR, n - i0);
+    for (int k = threadIdx.x; k < NR * W; k += blockDim.x) xs[k] = k < ns * W ? x[i0 * W + k] : 0ull;
     __syncthreads();
     if (u >= P) return;
-    R a[kPhaseRows];
+    R a[NR];
     const R bu = b1[u];
 #pragma unroll
-    for (int k = 0; k < kPhaseRows; ++k) a[k] = bu;
-    for (int j = 0; j < N; ++j) {
-        const R wj = w1[(int64_t)u * N + j];
+    for (int k = 0; k < NR; ++k) a[k] = bu;
+    for (int w = 0; w < W; ++w) {
+        uint64_t xr[NR];
 #pragma unroll
-        for (int k = 0; k < kPhaseRows; ++k)
-            if (k < ns && ((xs[k * W + (j >> 6)] >> (j & 63)) & 1ull)) a[k] += wj;
+        for (int k = 0; k < NR; ++k) xr[k] = xs[k * W + w];
+        const int jend = min(64, N - 64 * w);
+        for (int j = 0; j < jend; ++j) {
+            const R wj = w1t[(int64_t)(64 * w + j) * P + u];
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                if ((xr[k] >> j) & 1ull) a[k] += wj;
+        }
     }
 #pragma unroll
-    for (int k = 0; k < kPhaseRows; ++k) {
+    for (int k = 0; k < NR; ++k) {
         if (k >= ns) break;
         const int64_t o = (i0 + k) * P + u;
         z1[o] = a[k];
@@ -2410,6 +2458,83 @@ __global__ void k_phase_dz2(const R *__restrict__ dph, const R *__restrict__ w3,
     if (idx >= n * P) return;
     const int u = (int)(idx % P);
     dz2[idx] = z2[idx] > R(0) ? dph[idx / P] * w3[u] : R(0);
+}
+
+// Phase output layer backward in one pass over z2 (rows [r0, r0 + rpb) of a
+// block, thread = hidden unit): dz2 = dph w3 [z2 > 0] (k_phase_dz2's
+// expression) and the block's partial sums of dW3 = sum dph relu(z2),
+// db2 = sum dz2 and db3 = sum dph: partial[b] = [dW3 (P) | db2 (P) | db3]
+template <class R>
+__global__ void k_phase_out_bwd(const R *__restrict__ dph, const R *__restrict__ w3, const R *__restrict__ z2,
+                                int64_t n, int P, int64_t rpb, R *__restrict__ dz2, R *__restrict__ partial) {
+    const int64_t r0 = blockIdx.x * rpb, r1 = min(n, r0 + rpb);
+    const int64_t pw = 2 * (int64_t)P + 1;
+    for (int u = threadIdx.x; u < P; u += blockDim.x) {
+        const R wu = w3[u];
+        R aw = 0, ab = 0;
+#pragma unroll 4
+        for (int64_t i = r0; i < r1; ++i) {
+            const R g = dph[i], z = z2[i * P + u];
+            const R dz = z > R(0) ? g * wu : R(0);
+            dz2[i * P + u] = dz;
+            aw += g * (z > R(0) ? z : R(0));
+            ab += dz;
+        }
+        partial[blockIdx.x * pw + u] = aw;
+        partial[blockIdx.x * pw + P + u] = ab;
+    }
+    if (threadIdx.x == 0) {
+        R s3 = 0;
+        for (int64_t i = r0; i < r1; ++i) s3 += dph[i];
+        partial[blockIdx.x * pw + 2 * P] = s3;
+    }
+}
+
+// Phase input layer weight and bias gradients from dz1 and the occupation
+// bits (the 0/1 inputs): dW1[u][64 word + j] = sum_i dz1[i][u] bit_j(x_i[word]),
+// db1[u] = sum_i dz1[i][u] (word 0); per block partial[b][u][65].
+// grid = (row blocks, P / 64); thread = (unit u of a 64-unit slice, 16 inputs)
+template <class R>
+__global__ void __launch_bounds__(256) k_phase_in_bwd(const R *__restrict__ dz1, const uint64_t *__restrict__ x, int W,
+                                                      int64_t n, int P, int64_t rpb, int word,
+                                                      R *__restrict__ partial) {
+    const int64_t r0 = blockIdx.x * rpb, r1 = min(n, r0 + rpb);
+    const int jg = threadIdx.x >> 6, u = blockIdx.y * 64 + (threadIdx.x & 63);
+    if (u >= P) return;
+    R acc[16], ab = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0;
+#pragma unroll 4
+    for (int64_t i = r0; i < r1; ++i) {
+        const R v = dz1[i * P + u];
+        const uint64_t m = x[i * W + word] >> (16 * jg);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if ((m >> j) & 1ull) acc[j] += v;
+        ab += v;
+    }
+    R *pp = partial + (blockIdx.x * (int64_t)P + u) * 65;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) pp[16 * jg + j] = acc[j];
+    if (jg == 0) pp[64] = ab;
+}
+
+// out_w[u][64 word + j] += sum_b partial[b][u][j] (j < nj), out_b[u] += sum_b
+// partial[b][u][64] (out_b may be null), blocks in order
+template <class R>
+__global__ void k_phase_in_bwd_sum(const R *__restrict__ partial, int64_t nblk, int P, int N, int word, int nj,
+                                   R *__restrict__ out_w, R *__restrict__ out_b) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)P * 65) return;
+    const int u = (int)(idx / 65), j = (int)(idx % 65);
+    if (j < 64 && j >= nj) return;
+    if (j == 64 && !out_b) return;
+    R t = 0;
+    for (int64_t b = 0; b < nblk; ++b) t += partial[b * (int64_t)P * 65 + idx];
+    if (j == 64)
+        out_b[u] += t;
+    else
+        out_w[(int64_t)u * N + 64 * word + j] += t;
 }
 
 // a[idx] *= [z > 0]  or  a[idx] *= gelu'(z)
@@ -2552,6 +2677,7 @@ struct Acts {
     R *mean1 = nullptr, *rstd1 = nullptr, *mean2 = nullptr, *rstd2 = nullptr, *lse = nullptr;
     R *hf = nullptr, *meanf = nullptr, *rstdf = nullptr, *pi = nullptr;
     R *z1 = nullptr, *r1 = nullptr, *z2 = nullptr, *r2 = nullptr, *xf = nullptr;
+    R *w1t = nullptr;  // [N][P] phase input weights, unit fastest
     Scratch<R> scr{nullptr, 0, nullptr};
 };
 
@@ -2584,6 +2710,7 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     A.z2 = a.take<R>(C * P);
     A.r2 = a.take<R>(C * P);
     A.xf = keep ? a.take<R>(C * M->N) : nullptr;
+    A.w1t = a.take<R>((int64_t)M->N * P);
     // split-K / column-reduction partials: enough for the largest weight
     const int64_t wmax = std::max<int64_t>({3 * d * d, F * d, P * P, P * (int64_t)M->N});
     // split-K partials of weight gradients: ~600 splits of a layer matrix
@@ -2722,8 +2849,12 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     NNQS_LAUNCH("k_head", s, k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
                                                     M->cfg.n_beta, A.pi, out, st, row_offset));
     // phase MLP
-    if (P <= 1024 && W <= 2 && N <= P)
-        NNQS_LAUNCH("k_phase_in", s, k_phase_in_blk<R><<<(unsigned)((C + kPhaseRows - 1) / kPhaseRows), (P + 31) / 32 * 32, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
+    if (P <= 512 && W <= 2 && N <= P)
+    {
+        constexpr int NR = phase_rows<R>();
+        NNQS_LAUNCH("k_phase_in", s, k_phase_w1t<R><<<grid_for((int64_t)P * N, 256), 256, 0, s>>>(V.w1p, P, N, A.w1t));
+        NNQS_LAUNCH("k_phase_in", s, k_phase_in_blk<R><<<(unsigned)((C + NR - 1) / NR), (P + 31) / 32 * 32, 0, s>>>(x, W, N, A.w1t, V.b1p, C, P, A.z1, A.r1, A.xf));
+    }
     else
         NNQS_LAUNCH("k_phase_in", s, k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
     if (tcw) {
@@ -2771,15 +2902,35 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     (void)x;
     // ---- phase MLP
     NNQS_LAUNCH("k_seed_cols", s, k_seed_cols<R><<<grid_for(C, 256), 256, 0, s>>>(seed, C, G.dph));
-    // dW3[0][u] += sum_i dph_i r2[i][u]; db3 += sum_i dph_i
-    NNQS_TRY(linear_dw<R>(s, G.dph, C, 1, A.r2, P, gacc + Lo.ph_w3, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dph, nullptr, nullptr, nullptr, C, 1, gacc + Lo.ph_b3, nullptr, scr));
-    NNQS_LAUNCH("k_phase_dz2", s, k_phase_dz2<R><<<grid_for(C * P, 256), 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, G.dz2));
+    // dz2, dW3 = sum_i dph_i r2[i][:], db3 = sum_i dph_i and db2 = sum_i dz2 in
+    // one pass over z2 (r2 = relu(z2)), the partial rows added in block order
+    {
+        const int64_t pw = 2 * P + 1;
+        int64_t nblk = std::min<int64_t>((C + 15) / 16, 4 * sm_count());
+        nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(pw))));
+        const int64_t rpb = (C + nblk - 1) / nblk;
+        nblk = (C + rpb - 1) / rpb;
+        NNQS_LAUNCH("k_phase_dz2", s, k_phase_out_bwd<R><<<(unsigned)nblk, 256, 0, s>>>(G.dph, V.w3p, A.z2, C, P, rpb, G.dz2, scr.buf));
+        NNQS_LAUNCH("k_phase_dz2", s, (k_sum_partials<R><<<(unsigned)((P + 31) / 32), kColThreads, 0, s>>>(scr.buf, nblk, P, gacc + Lo.ph_w3, pw)));
+        NNQS_LAUNCH("k_phase_dz2", s, (k_sum_partials<R><<<(unsigned)((P + 31) / 32), kColThreads, 0, s>>>(scr.buf + P, nblk, P, gacc + Lo.ph_b2, pw)));
+        NNQS_LAUNCH("k_phase_dz2", s, (k_sum_partials<R><<<1, kColThreads, 0, s>>>(scr.buf + 2 * P, nblk, 1, gacc + Lo.ph_b3, pw)));
+    }
     NNQS_TRY(bw_dw<R>(s, tcw, G.dz2, C, P, A.r1, P, gacc + Lo.ph_w2, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dz2, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b2, nullptr, scr));
     NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(L, 0), G.dz2, C, P, V.w2p, P, G.dz1, scr, 2, A.z1));
-    NNQS_TRY(linear_dw<R>(s, G.dz1, C, P, A.xf, N, gacc + Lo.ph_w1, scr));
-    NNQS_TRY(colsum<R>(s, 0, G.dz1, nullptr, nullptr, nullptr, C, P, gacc + Lo.ph_b1, nullptr, scr));
+    // dW1 and db1 from dz1 and the occupation bits, 64 inputs per pass
+    {
+        const int W = M->W;
+        const int64_t ns = (P + 63) / 64;  // 64-unit slices
+        int64_t nblk = std::min<int64_t>((C + 31) / 32, (8 * sm_count() + ns - 1) / ns);
+        nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(P * 65))));
+        const int64_t rpb = (C + nblk - 1) / nblk;
+        nblk = (C + rpb - 1) / rpb;
+        for (int word = 0; word < W && 64 * word < N; ++word) {
+            const int nj = std::min(64, (int)N - 64 * word);
+            NNQS_LAUNCH("k_phase_in_bwd", s, k_phase_in_bwd<R><<<dim3((unsigned)nblk, (unsigned)ns), 256, 0, s>>>(G.dz1, x, W, C, P, rpb, word, scr.buf));
+            NNQS_LAUNCH("k_phase_in_bwd", s, k_phase_in_bwd_sum<R><<<grid_for((int64_t)P * 65, 256), 256, 0, s>>>(scr.buf, nblk, P, N, word, nj, gacc + Lo.ph_w1, word == 0 ? gacc + Lo.ph_b1 : nullptr));
+        }
+    }
     // ---- head
     {
         constexpr int VH = int(16 / sizeof(R));

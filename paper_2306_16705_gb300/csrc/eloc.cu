@@ -430,55 +430,66 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
     return NNQS_OK;
 }
 
-// ---- energy statistics: one CTA, fixed-order tree reductions ----
-constexpr int kStatThreads = 1024;
+// Energy statistics over 128 fixed row ranges (the FP64 sums of one block
+// were bound by a single SM's FP64 pipe): pass 0 gives the blocks' (sum w,
+// sum w Re E_loc, sum w Im E_loc), pass 1 the blocks' sum w |E_loc - E|^2 with
+// E from pass 0; k_stats_fin adds the block sums in block order.
+constexpr int kStatBlocks = 128, kStatPartThreads = 256;
 
-__device__ void block_sum3(double &a, double &b, double &c, double *sh) {
+__global__ void __launch_bounds__(kStatPartThreads)
+    k_stats_part(const double2 *__restrict__ e, const uint64_t *__restrict__ w, int64_t n, int pass,
+                 const double *__restrict__ stats, double *__restrict__ part) {
+    __shared__ double sh[3][kStatPartThreads];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    double a = 0.0, b = 0.0, c = 0.0;
+    const double er = pass ? stats[0] : 0.0, ei = pass ? stats[1] : 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kStatPartThreads) {
+        const double wi = (double)w[i];
+        const double2 v = e[i];
+        if (pass == 0) {
+            a += wi;
+            b += wi * v.x;
+            c += wi * v.y;
+        } else {
+            const double dr = v.x - er, di = v.y - ei;
+            a += wi * (dr * dr + di * di);
+        }
+    }
     const int t = threadIdx.x;
-    sh[t] = a;
-    sh[kStatThreads + t] = b;
-    sh[2 * kStatThreads + t] = c;
+    sh[0][t] = a;
+    sh[1][t] = b;
+    sh[2][t] = c;
     __syncthreads();
-    for (int off = kStatThreads / 2; off > 0; off >>= 1) {
+    for (int off = kStatPartThreads / 2; off > 0; off >>= 1) {
         if (t < off) {
-            sh[t] += sh[t + off];
-            sh[kStatThreads + t] += sh[kStatThreads + t + off];
-            sh[2 * kStatThreads + t] += sh[2 * kStatThreads + t + off];
+            sh[0][t] += sh[0][t + off];
+            sh[1][t] += sh[1][t + off];
+            sh[2][t] += sh[2][t + off];
         }
         __syncthreads();
     }
-    a = sh[0];
-    b = sh[kStatThreads];
-    c = sh[2 * kStatThreads];
-    __syncthreads();
+    if (t == 0) {
+        part[3 * blockIdx.x] = sh[0][0];
+        part[3 * blockIdx.x + 1] = sh[1][0];
+        part[3 * blockIdx.x + 2] = sh[2][0];
+    }
 }
 
-__global__ void __launch_bounds__(kStatThreads)
-    k_stats(const double2 *__restrict__ e, const uint64_t *__restrict__ w, int64_t n, double *__restrict__ stats) {
-    extern __shared__ double sh[];
-    double sw = 0.0, sr = 0.0, si = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += kStatThreads) {
-        const double wi = (double)w[i];
-        const double2 v = e[i];
-        sw += wi;
-        sr += wi * v.x;
-        si += wi * v.y;
+__global__ void k_stats_fin(const double *__restrict__ part, int nb, int pass, double *__restrict__ stats) {
+    if (threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        a += part[3 * k];
+        b += part[3 * k + 1];
+        c += part[3 * k + 2];
     }
-    block_sum3(sw, sr, si, sh);
-    const double er = sr / sw, ei = si / sw;
-    double sv = 0.0, z0 = 0.0, z1 = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += kStatThreads) {
-        const double wi = (double)w[i];
-        const double2 v = e[i];
-        const double dr = v.x - er, di = v.y - ei;
-        sv += wi * (dr * dr + di * di);
-    }
-    block_sum3(sv, z0, z1, sh);
-    if (threadIdx.x == 0) {
-        stats[0] = er;
-        stats[1] = ei;
-        stats[2] = sv / sw;
-        stats[3] = sw;
+    if (pass == 0) {
+        stats[0] = b / a;
+        stats[1] = c / a;
+        stats[3] = a;
+    } else {
+        stats[2] = a / stats[3];
     }
 }
 
@@ -507,11 +518,16 @@ nnqs_status eloc_sa(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp
     return eloc_sa_impl<2>(H, lut, lut_lp, n_lut, row_begin, n_rows, n_alpha, n_beta, flags, out, ws, status, s);
 }
 
-size_t stats_workspace(int64_t) { return kStatusBytes + 256; }
+size_t stats_workspace(int64_t) { return kStatusBytes + 256 + 3 * kStatBlocks * sizeof(double) + 256; }
 
-nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, double *stats, Arena &, cudaStream_t s) {
-    NNQS_LAUNCH("k_stats", s, k_stats<<<1, kStatThreads, 3 * kStatThreads * sizeof(double), s>>>(reinterpret_cast<const double2 *>(eloc), w, n,
-                                                                        stats));
+nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, double *stats, Arena &ws, cudaStream_t s) {
+    double *part = ws.take<double>(3 * kStatBlocks);
+    if (ws.base == nullptr) return NNQS_OK;
+    const double2 *e = reinterpret_cast<const double2 *>(eloc);
+    for (int pass = 0; pass < 2; ++pass) {
+        NNQS_LAUNCH("k_stats", s, k_stats_part<<<kStatBlocks, kStatPartThreads, 0, s>>>(e, w, n, pass, stats, part));
+        NNQS_LAUNCH("k_stats", s, k_stats_fin<<<1, 32, 0, s>>>(part, kStatBlocks, pass, stats));
+    }
     return NNQS_OK;
 }
 
