@@ -1262,9 +1262,10 @@ struct HeadVec {
             for (int c = 0; c < DH; ++c) p[c] = in[c];
         }
     }
-    // row stride in shared memory for w columns: unpadded (16-byte rows) for
-    // vector reads, else padded by one against bank conflicts
-    __host__ __device__ static constexpr int ld(int w) { return kVec ? w : w + 1; }
+    // row stride in shared memory for w columns, padded so that consecutive
+    // rows start 4 banks apart: 16 bytes (rows stay 16-byte aligned) for
+    // vector reads, one element for scalar ones
+    __host__ __device__ static constexpr int ld(int w) { return kVec ? w + V : w + 1; }
 };
 
 template <class R, int DH>
@@ -1368,21 +1369,30 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     const R scale = R(1) / sqrt(R(DH));
     const bool act = tid < H * T;
     const int hh = act ? tid % H : 0, pos = act ? tid / H : 0;  // heads fastest
+    // D_q = do_q . o_q for every (head, position) first, so that the two
+    // loops below (whose lengths q + 1 and T - j add up to T + 1 per thread)
+    // run without a barrier between them
+    R D = 0;
     if (act) {
-        // dq_q = scale sum_{j<=q} p_qj (dp_qj - D_q) k_j,  D_q = do_q . o_q
+        R dov[DH], ov[DH];
+        HV::read(sdo + pos * ldo + hh * DH, dov);
+        HV::read(so + pos * ldo + hh * DH, ov);
+#pragma unroll
+        for (int c = 0; c < DH; ++c) D += dov[c] * ov[c];
+        sD[hh * T + pos] = D;
+    }
+    __syncthreads();
+    if (act) {
+        // dq_q = scale sum_{j<=q} p_qj (dp_qj - D_q) k_j
         const int q = pos;
-        R qv[DH], dov[DH], ov[DH], dq[DH];
+        R qv[DH], dov[DH], dq[DH];
         HV::read(sq + q * ldq + hh * DH, qv);
         HV::read(sdo + q * ldo + hh * DH, dov);
-        HV::read(so + q * ldo + hh * DH, ov);
-        R D = 0;
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
             qv[c] = qv[c] * scale;
-            D += dov[c] * ov[c];
             dq[c] = 0;
         }
-        sD[hh * T + q] = D;
         const R L = slse[hh * T + q];
         for (int j = 0; j <= q; ++j) {
             R kj[DH], vj[DH];
@@ -1402,7 +1412,6 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         for (int c = 0; c < DH; ++c) dq[c] = dq[c] * scale;
         HV::write(sg + q * ldq + hh * DH, dq);
     }
-    __syncthreads();
     if (act) {
         // dv_j = sum_{q>=j} p_qj do_q,  dk_j = scale sum_{q>=j} p_qj (dp_qj - D_q) q_q
         const int j = pos;
@@ -2722,9 +2731,9 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
 constexpr size_t kAttnSmemMax = 200 * 1024;
 
 template <class R>
-size_t attn_fwd_smem_bytes(int T, int d) { return sizeof(R) * size_t(T) * (4 * d + 2); }
+size_t attn_fwd_smem_bytes(int T, int d) { return sizeof(R) * size_t(T) * (4 * d + 8); }
 template <class R>
-size_t attn_bwd_smem_bytes(int T, int H, int d) { return sizeof(R) * (size_t(T) * (8 * d + 4) + 2 * size_t(H) * T); }
+size_t attn_bwd_smem_bytes(int T, int H, int d) { return sizeof(R) * (size_t(T) * (8 * d + 16) + 2 * size_t(H) * T); }
 
 template <class K>
 nnqs_status allow_smem(K kernel, size_t bytes) {
