@@ -1394,6 +1394,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
             dq[c] = 0;
         }
         const R L = slse[hh * T + q];
+#pragma unroll 2
         for (int j = 0; j <= q; ++j) {
             R kj[DH], vj[DH];
             HV::read(sq + j * ldq + d + hh * DH, kj);
@@ -1420,6 +1421,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         HV::read(sq + j * ldq + 2 * d + hh * DH, vv);
 #pragma unroll
         for (int c = 0; c < DH; ++c) dk[c] = dv[c] = 0;
+#pragma unroll 2
         for (int q = j; q < T; ++q) {
             R qq[DH], dq[DH];
             HV::read(sq + q * ldq + hh * DH, qq);
@@ -1701,6 +1703,7 @@ __device__ __forceinline__ constexpr uint32_t col_u(int c) { return c == 0 ? kCo
 struct DecodeArgs {
     float *h;  // [n][64] residual rows of the new tokens, updated in place
     int64_t n;
+    int rpc;  // prefixes per CTA (<= 128; rows past it in the 128-row tile are idle)
     float *pool;  // [node][L][192] q|k|v
     int L, l, Tm, t;
     int64_t g0;
@@ -1944,7 +1947,8 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     const uint32_t wb = tc::smem_u32(wbar);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t m0 = blockIdx.x * (int64_t)kRows;
+    const int64_t m0 = blockIdx.x * (int64_t)g.rpc;
+    const int64_t n_cta = min(g.n, m0 + g.rpc);  // rows of this CTA are m0 .. n_cta - 1
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
                      "r"(kTmemCols)
@@ -1971,7 +1975,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
             const int it = tid + kThreads * i;
             const int r = it >> 4, c4 = it & 15;
             v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (m0 + r < g.n) {
+            if (m0 + r < n_cta) {
                 if (g.first) {
                     const int inp = g.t == 0 ? 4 : token_at(g.x + (m0 + r) * g.W, g.Tm, g.t - 1);
                     const float4 te = __ldg(reinterpret_cast<const float4 *>(g.tok_emb + inp * kD) + c4);
@@ -2012,7 +2016,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     };
     const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
     const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
-    const bool row_ok = m0 + row < g.n;
+    const bool row_ok = m0 + row < n_cta;
 
     // ---- LayerNorm 1 -> qkv
     if (tid < kRows) dec_layernorm_row(sH, tid, g.ln1g, g.ln1b, aHi, aLo, SPLIT);
@@ -2069,7 +2073,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
             for (int i = 0; i < kRows * 16 / kThreads; ++i) {
                 const int it = tid + kThreads * i;
                 const int r = it >> 4, gi = it & 15;
-                if (m0 + r < g.n) {
+                if (m0 + r < n_cta) {
                     float *prow = g.pool + ((g.g0 + m0 + r) * g.L + g.l) * (int64_t)kQKV + 64 * c;
                     *reinterpret_cast<float4 *>(prow + 4 * gi) =
                         *reinterpret_cast<const float4 *>(slab + r * 64 + 4 * (gi ^ (r & 15)));
@@ -2084,7 +2088,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         const int hh = tid % H;
         const int r0 = (tid / H) * NR;
         float o[NR][DH];
-        dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g.g0, m0 + r0, m0, g.n, g.t, g.L, g.l, hh, o);
+        dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g.g0, m0 + r0, m0, n_cta, g.t, g.L, g.l, hh, o);
 #pragma unroll
         for (int k = 0; k < NR; ++k)
 #pragma unroll
@@ -2193,7 +2197,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         // final LayerNorm (k_ln_fwd_v's sums), head logits (head_logits' sum)
         // and the masked conditionals of the next token
         __syncthreads();
-        if (ok && tid < kRows && m0 + tid < g.n) {
+        if (ok && tid < kRows && m0 + tid < n_cta) {
             float hf[kD];
             dec_layernorm_row_f32(sH, tid, g.lnf_g, g.lnf_b, hf);
             float zr[4];
@@ -3190,7 +3194,7 @@ nnqs_status launch_decode_layer(const DecodeArgs &g, cudaStream_t s) {
                                            dec::kSmem));
         attr = true;
     }
-    const unsigned grid = (unsigned)((g.n + dec::kRows - 1) / dec::kRows);
+    const unsigned grid = (unsigned)((g.n + g.rpc - 1) / g.rpc);
     NNQS_LAUNCH("k_decode_layer", s, (k_decode_layer<SPLIT, DH><<<grid, dec::kThreads, dec::kSmem, s>>>(g)));
     return NNQS_OK;
 }
@@ -3204,6 +3208,10 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
     DecodeArgs g{};
     g.h = h;
     g.n = n;
+    // prefixes per CTA: once there are more prefixes than SMs every SM gets a
+    // CTA (the late steps' attention is bound by memory traffic; the MMA
+    // tiles stay 128 rows, the rows past rpc idle)
+    g.rpc = (int)std::min<int64_t>(dec::kRows, std::max<int64_t>(1, (n + sm_count() - 1) / sm_count()));
     g.pool = pool;
     g.L = M->L;
     g.l = l;
