@@ -8,6 +8,7 @@
 
 #include "dev_common.cuh"
 #include "tc_gemm.cuh"
+#include "tc_gemm_ws.cuh"
 #include "tc_gemm.h"
 
 namespace nnqs {
@@ -225,6 +226,45 @@ int tmem_cols_for(int Nt) {
     return cols;
 }
 
+// the warp-specialised kernel takes a non-transposed layer with K = 64 (one
+// K chunk per tile) when the TMA epilogue is on, its boxes and the FP32 /
+// operand rings fit in shared memory, and there are enough row tiles to keep
+// every SM busy for a few tiles
+int ws_smem_of(const tc::Args &g, bool split) {
+    const int w_bytes = (split ? 2 : 1) * g.Nt * 128;
+    return (w_bytes + 1023) / 1024 * 1024 + 2 * tc::kWsStage + 2 * (split ? 2 : 1) * tc::kABytes + 2 * g.p_wg_epi +
+           tc::kWsFixed;
+}
+
+bool ws_eligible(tc::Args &g, bool split, int epi) {
+    if (!g.use_tma || g.Nt % 32 != 0 || g.Nt > 128 || g.K != tc::kChunkK || g.Kpad != tc::kChunkK) return false;
+    const int64_t m_tiles = (g.M + tc::kTileM - 1) / tc::kTileM;
+    if (m_tiles < 4 * int64_t(num_sms())) return false;
+    const bool two = epi == tc::EPI_GELU || epi == tc::EPI_RELU;
+    g.p_wg_epi = two ? 2 * 16384 : (g.Nt / 32 + 1) / 2 * 16384;
+    if (ws_smem_of(g, split) > tc::kWsSmemMax) return false;
+    return make_box_map(&g.tmX, g.X, g.K, g.M, 1, g.ldx);
+}
+
+template <int EPI, bool SPLIT>
+nnqs_status launch_ws(tc::Args g, cudaStream_t s) {
+    static int attr = 0;
+    const int smem = ws_smem_of(g, SPLIT);
+    if (smem > attr) {
+        NNQS_CUDA_TRY(
+            cudaFuncSetAttribute(tc::k_tc_gemm_ws<EPI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = smem;
+    }
+    const int ntiles = (int)((g.N + g.Nt - 1) / g.Nt);
+    const int64_t m_tiles = (g.M + tc::kTileM - 1) / tc::kTileM;
+    int64_t grid = (int64_t)(num_sms() / ntiles) * ntiles;
+    grid = std::min<int64_t>(grid, m_tiles * ntiles);
+    g.p_ntiles = ntiles;
+    g.tmem_cols = tmem_cols_for(2 * g.Nt);
+    NNQS_LAUNCH("k_tc_gemm", s, (tc::k_tc_gemm_ws<EPI, SPLIT><<<(unsigned)grid, tc::kWsThreads, smem, s>>>(g)));
+    return NNQS_OK;
+}
+
 }  // namespace
 
 void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
@@ -398,6 +438,11 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     note_work("k_tc_gemm", (w.split ? 6.0 : 2.0) * double(rows) * double(g.N) * double(in),
               4.0 * double(rows) * in + (w.split ? 4.0 : 2.0) * double(g.N) * g.Kpad +
                   (two ? 8.0 : 4.0) * double(rows) * g.N);
+    // the warp-specialised kernel only where it measured faster: the split
+    // forward with a plain store (the qkv layer: 412 -> 320 us for the four
+    // launches of a 40-qubit step); with two outputs or a residual its one
+    // epilogue role per SM is slower than three interleaved CTAs
+    if (w.split && epi == tc::EPI_STORE && ws_eligible(g, true, epi)) return launch_ws<tc::EPI_STORE, true>(g, s);
     if (w.split) {
         switch (epi) {
             case tc::EPI_STORE: return launch<tc::EPI_STORE, false, true>(g, ntn, s);

@@ -153,6 +153,12 @@ struct Args {
     // colpart[row tile][N] (for the bias gradient of the layer whose input
     // gradient Y is)
     float *colpart;
+    // warp-specialised kernel (k_tc_gemm_ws): N tiles, epilogue bytes per
+    // warpgroup, and X as a 3-D FP32 tensor map {K, M, 1} with 32 x 128 boxes
+    // and the 128-byte swizzle
+    int p_ntiles;
+    int p_wg_epi;
+    CUtensorMap tmX;
 };
 
 // TMA: one 32-column x 128-row FP32 box between shared memory (1024-byte
