@@ -2388,8 +2388,7 @@ constexpr int phase_rows() { return sizeof(R) == 8 ? 16 : kPhaseRows; }
 template <class R>
 __global__ void __launch_bounds__(512) k_phase_in_blk(const uint64_t *__restrict__ x, int W, int N,
                                                       const R *__restrict__ w1t, const R *__restrict__ b1, int64_t n,
-                                                      int P, R *__restrict__ z1, R *__restrict__ r1,
-                                                      R *__restrict__ xf) {
+                                                      int P, R *__restrict__ z1, R *__restrict__ r1) {
     constexpr int NR = phase_rows<R>();
     __shared__ uint64_t xs[NR * 2];
     const int u = threadIdx.x;
@@ -2420,14 +2419,12 @@ __global__ void __launch_bounds__(512) k_phase_in_blk(const uint64_t *__restrict
         const int64_t o = (i0 + k) * P + u;
         z1[o] = a[k];
         r1[o] = a[k] > R(0) ? a[k] : R(0);
-        if (xf && u < N) xf[(i0 + k) * N + u] = (R)((xs[k * W + (u >> 6)] >> (u & 63)) & 1ull);
     }
 }
 
 template <class R>
 __global__ void k_phase_in(const uint64_t *__restrict__ x, int W, int N, const R *__restrict__ w1,
-                           const R *__restrict__ b1, int64_t n, int P, R *__restrict__ z1, R *__restrict__ r1,
-                           R *__restrict__ xf) {
+                           const R *__restrict__ b1, int64_t n, int P, R *__restrict__ z1, R *__restrict__ r1) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * P) return;
     const int u = (int)(idx % P);
@@ -2438,8 +2435,6 @@ __global__ void k_phase_in(const uint64_t *__restrict__ x, int W, int N, const R
         if (bit_of(xi, j)) a += w1[(int64_t)u * N + j];
     z1[idx] = a;
     r1[idx] = a > R(0) ? a : R(0);
-    if (xf)
-        for (int j = u; j < N; j += P) xf[i * N + j] = (R)bit_of(xi, j);
 }
 
 // phase_i = b3 + sum_u r2[i][u] w3[u]  (one warp per sample)
@@ -2464,18 +2459,8 @@ __global__ void k_seed_cols(const double2 *__restrict__ seed, int64_t n, R *__re
 }
 
 // dz2 = dph_i w3[u] [z2 > 0]
-template <class R>
-__global__ void k_phase_dz2(const R *__restrict__ dph, const R *__restrict__ w3, const R *__restrict__ z2, int64_t n,
-                            int P, R *__restrict__ dz2) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n * P) return;
-    const int u = (int)(idx % P);
-    dz2[idx] = z2[idx] > R(0) ? dph[idx / P] * w3[u] : R(0);
-}
-
 // Phase output layer backward in one pass over z2 (rows [r0, r0 + rpb) of a
-// block, thread = hidden unit): dz2 = dph w3 [z2 > 0] (k_phase_dz2's
-// expression) and the block's partial sums of dW3 = sum dph relu(z2),
+// block, thread = hidden unit): dz2 = dph w3 [z2 > 0] and the block's partial sums of dW3 = sum dph relu(z2),
 // db2 = sum dz2 and db3 = sum dph: partial[b] = [dW3 (P) | db2 (P) | db3]
 template <class R>
 __global__ void k_phase_out_bwd(const R *__restrict__ dph, const R *__restrict__ w3, const R *__restrict__ z2,
@@ -2689,7 +2674,7 @@ struct Acts {
     R *a = nullptr, *a2 = nullptr, *qkv = nullptr, *o = nullptr, *u = nullptr, *gu = nullptr;
     R *mean1 = nullptr, *rstd1 = nullptr, *mean2 = nullptr, *rstd2 = nullptr, *lse = nullptr;
     R *hf = nullptr, *meanf = nullptr, *rstdf = nullptr, *pi = nullptr;
-    R *z1 = nullptr, *r1 = nullptr, *z2 = nullptr, *r2 = nullptr, *xf = nullptr;
+    R *z1 = nullptr, *r1 = nullptr, *z2 = nullptr, *r2 = nullptr;
     R *w1t = nullptr;  // [N][P] phase input weights, unit fastest
     Scratch<R> scr{nullptr, 0, nullptr};
 };
@@ -2722,7 +2707,6 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     A.r1 = a.take<R>(C * P);
     A.z2 = a.take<R>(C * P);
     A.r2 = a.take<R>(C * P);
-    A.xf = keep ? a.take<R>(C * M->N) : nullptr;
     A.w1t = a.take<R>((int64_t)M->N * P);
     // split-K / column-reduction partials: enough for the largest weight
     const int64_t wmax = std::max<int64_t>({3 * d * d, F * d, P * P, P * (int64_t)M->N});
@@ -2866,10 +2850,10 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     {
         constexpr int NR = phase_rows<R>();
         NNQS_LAUNCH("k_phase_in", s, k_phase_w1t<R><<<grid_for((int64_t)P * N, 256), 256, 0, s>>>(V.w1p, P, N, A.w1t));
-        NNQS_LAUNCH("k_phase_in", s, k_phase_in_blk<R><<<(unsigned)((C + NR - 1) / NR), (P + 31) / 32 * 32, 0, s>>>(x, W, N, A.w1t, V.b1p, C, P, A.z1, A.r1, A.xf));
+        NNQS_LAUNCH("k_phase_in", s, k_phase_in_blk<R><<<(unsigned)((C + NR - 1) / NR), (P + 31) / 32 * 32, 0, s>>>(x, W, N, A.w1t, V.b1p, C, P, A.z1, A.r1));
     }
     else
-        NNQS_LAUNCH("k_phase_in", s, k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1, A.xf));
+        NNQS_LAUNCH("k_phase_in", s, k_phase_in<R><<<grid_for(C * P, 256), 256, 0, s>>>(x, W, N, V.w1p, V.b1p, C, P, A.z1, A.r1));
     if (tcw) {
         NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(L, 0), EPI_RELU, A.r1, C, P, V.b2p, A.z2, A.r2, nullptr));
     } else {
