@@ -36,7 +36,7 @@ N_SAMPLES = 16384
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FMA: SMs x lanes x 2 x max clock
 # DRAM read + write bytes per k_tc_gemm launch of this step, from one ncu capture of the current kernel
 # at this workload (profiles/k_tc_gemm_energy_grad_n40.md); None once the kernel changes
-TC_GEMM_TRAFFIC_BYTES = 358.8e6
+TC_GEMM_TRAFFIC_BYTES = 358.4e6
 
 
 def parse():

@@ -29,10 +29,10 @@ constexpr int kTileM = 128;
 constexpr int kChunkK = 64;                      // BF16 per 128-byte row
 constexpr int kABytes = kTileM * kChunkK * 2;    // 16 KB
 constexpr int kMaxN = 128;                       // N per CTA: TMEM 128 columns, 4 CTAs per SM
-constexpr int kBBytes = kMaxN * kChunkK * 2;     // 32 KB
-constexpr int kSmemBytes = kABytes + kBBytes + 1024 + 64;
+constexpr int kBBytes = kMaxN * kChunkK * 2;     // 16 KB
+constexpr int kSmemBytes = kABytes + kBBytes + 1024 + 64 + 512;
 // split operands: high and low BF16 parts of A and B
-constexpr int kSmemBytesSplit = 2 * (kABytes + kBBytes) + 1024 + 64;
+constexpr int kSmemBytesSplit = 2 * (kABytes + kBBytes) + 1024 + 64 + 512;
 
 // EPI_DGELU / EPI_DRELU (input gradients): Y = acc * act'(Z) with the
 // pre-activation Z passed as `resid`
@@ -183,6 +183,11 @@ __device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// at most N of this thread's latest bulk store groups still reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read_n() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
 
 // TRANS = false: Y = X W^T (X FP32 [M][ldx], W BF16 [N][Kpad]).
 // TRANS = true : Y = A^T B over a long K (weight gradients): A(m,k) =
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
     }
     if (tid == 0) {
         mbar_init(smem_u32(mbar), 1);
+        for (int k = 0; k < 4; ++k) mbar_init(smem_u32(sbase + kOps + 24 + 8 * k), 1);  // epilogue residual slots
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before_sync();
@@ -418,30 +424,46 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
     } else if (g.use_tma && Nt % 32 == 0) {  // whole boxes inside this CTA's columns
         // 32-column boxes: TMEM -> registers (thread = row) -> epilogue ->
         // shared memory in the TMA layout (row r at 128 r bytes, 16-byte chunk
-        // q at q ^ (r & 7)) -> one bulk tensor store per box; the residual or
-        // pre-activation box arrives by TMA load first.  Rows and columns
-        // outside the tensor are dropped by the store (zeros on the load).
+        // q at q ^ (r & 7)) -> one bulk tensor store per box.  The boxes cycle
+        // through the free operand buffers (two-output epilogues through pairs
+        // (Y, activation)), so a box is computed while the stores of the
+        // previous ones drain; a slot is rewritten once its store has read it.
+        // Residual / pre-activation boxes are loaded by TMA into their slots
+        // ahead of use (all of them at once when every box has its own slot).
+        // Rows and columns outside the tensor are dropped by the store (zeros
+        // on the load).
         constexpr bool kNeedR = EPI == EPI_RESID || EPI == EPI_DGELU || EPI == EPI_DRELU;
         constexpr bool kTwo = EPI == EPI_GELU || EPI == EPI_RELU;
-        uint8_t *box = sbase, *box2 = sbase + 16384;
-        const uint32_t ubox = smem_u32(box), ubox2 = smem_u32(box2);
+        constexpr int kSlots = kOps / 16384;
+        // boxes whose slots are in use at once (at most the 4 residual barriers)
+        constexpr int kCyc = (kTwo ? kSlots / 2 : kSlots) < 4 ? (kTwo ? kSlots / 2 : kSlots) : 4;
+        const int nbox = Nt / 32;
         const int row = warp * 32 + lane;
         const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
         const int zc = TRANS ? (int)blockIdx.z : 0;
-        for (int c0 = 0; c0 < Nt && ok; c0 += 32) {
-            const int x = (int)(n0 + c0);
-            if (kNeedR) {
-                if (tid == 0) {
-                    mbar_expect(mb, 16384u);
-                    tma_load_box(ubox, &g.tmR, x, (int)m0, zc, mb);
-                }
-                ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
-                phase ^= 1u;
-                if (!ok) break;
-            }
+        float *cpart = reinterpret_cast<float *>(sbase + kOps + 64);
+        const uint32_t rb0 = smem_u32(sbase + kOps + 24);  // residual barrier of slot k at rb0 + 8 k
+        auto ybox = [&](int c) { return sbase + (kTwo ? 2 * (c % kCyc) : c % kCyc) * 16384; };
+        int r_issued = 0, r_done = 0;
+        auto issue_r = [&](int c) {
+            const uint32_t rb = rb0 + 8u * uint32_t(c % kCyc);
+            mbar_expect(rb, 16384u);
+            tma_load_box(smem_u32(ybox(c)), &g.tmR, (int)(n0 + 32 * c), (int)m0, zc, rb);
+            r_issued = c + 1;
+        };
+        if (kNeedR && tid == 0)
+            for (int c = 0; c < kCyc && c < nbox; ++c) issue_r(c);
+        for (int c = 0; c < nbox && ok; ++c) {
+            uint8_t *box = ybox(c), *box2 = box + 16384;
+            if (!kNeedR && tid == 0 && c >= kCyc) bulk_wait_read_n<kCyc - 1>();  // box c - kCyc's store has read it
+            bool good = true;
+            if (kNeedR) good = mbar_wait(rb0 + 8u * uint32_t(c % kCyc), uint32_t((c / kCyc) & 1));
+            ok = __syncthreads_and(good ? 1 : 0) != 0;
+            if (!ok) break;
+            if (kNeedR) r_done = c + 1;
             uint32_t r[32];
-            tmem_ld16(lane_base + uint32_t(c0), *reinterpret_cast<uint32_t(*)[16]>(r));
-            tmem_ld16(lane_base + uint32_t(c0 + 16), *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+            tmem_ld16(lane_base + uint32_t(32 * c), *reinterpret_cast<uint32_t(*)[16]>(r));
+            tmem_ld16(lane_base + uint32_t(32 * c + 16), *reinterpret_cast<uint32_t(*)[16]>(r + 16));
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int off = row * 128 + ((q ^ (row & 7)) << 4);
@@ -451,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
                 const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int64_t n = n0 + c0 + 4 * q + e;
+                    const int64_t n = n0 + 32 * c + 4 * q + e;
                     const float bias_v = (g.bias && n < g.N) ? __ldg(g.bias + n) : 0.f;
                     v[e] = __uint_as_float(r[4 * q + e]) + bias_v;
                     if (EPI == EPI_STORE) {
@@ -475,7 +497,6 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
             }
             fence_async_smem();
             __syncthreads();
-            float *cpart = reinterpret_cast<float *>(box2);  // free in the one-output epilogues
             if (!kTwo && g.colpart) {
                 // column tid & 31 over rows 32 (tid >> 5) .. + 31 of the box, in
                 // order (rows past M are left out); the four row groups are
@@ -488,20 +509,30 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
                 cpart[rg * 32 + cl] = cs;
             }
             if (tid == 0) {
-                tma_store_box(&g.tmY, ubox, x, (int)m0, zc);
-                if (kTwo) tma_store_box(&g.tmY2, ubox2, x, (int)m0, zc);
+                tma_store_box(&g.tmY, smem_u32(box), (int)(n0 + 32 * c), (int)m0, zc);
+                if (kTwo) tma_store_box(&g.tmY2, smem_u32(box2), (int)(n0 + 32 * c), (int)m0, zc);
                 bulk_commit();
-                bulk_wait_read();
             }
-            __syncthreads();
-            if (!kTwo && g.colpart && tid < 32 && n0 + c0 + tid < g.N)
-                g.colpart[blockIdx.y * g.N + n0 + c0 + tid] =
-                    ((cpart[tid] + cpart[32 + tid]) + cpart[64 + tid]) + cpart[96 + tid];
+            if (!kTwo && g.colpart) {
+                __syncthreads();  // also: no thread reads the box any more
+                if (tid < 32 && n0 + 32 * c + tid < g.N)
+                    g.colpart[blockIdx.y * g.N + n0 + 32 * c + tid] =
+                        ((cpart[tid] + cpart[32 + tid]) + cpart[64 + tid]) + cpart[96 + tid];
+            }
+            if (kNeedR && tid == 0 && c + kCyc < nbox) {
+                // the slot takes box c + kCyc's residual once every thread is
+                // done with it (the barrier above, or the one before the
+                // store) and the store has read it
+                bulk_wait_read();
+                issue_r(c + kCyc);
+            }
         }
         if (tid == 0) {
             if (!ok) {
                 if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -12;
-                mbar_wait(mb, phase);  // a residual load still in flight lands (bounded)
+                // residual loads still in flight land (bounded)
+                for (int c = r_done; c < r_issued; ++c)
+                    mbar_wait(rb0 + 8u * uint32_t(c % kCyc), uint32_t((c / kCyc) & 1));
             }
             asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
         }
