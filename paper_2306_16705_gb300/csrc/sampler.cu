@@ -74,7 +74,7 @@ struct Philox {
 };
 
 // log(k!) - [(k + 1/2) log(k + 1) - (k + 1) + log(2 pi)/2]: Stirling remainder
-__device__ double stirling_tail(double k) {
+__device__ __noinline__ double stirling_tail(double k) {
     if (k < 10.0) {
         return lgamma(k + 1.0) - ((k + 0.5) * log(k + 1.0) - (k + 1.0) + 0.91893853320467274178);
     }
@@ -83,7 +83,7 @@ __device__ double stirling_tail(double k) {
 }
 
 // inversion (sequential search from 0) for n p < 14, p <= 1/2
-__device__ uint64_t binom_inversion(uint64_t n, double p, Philox &rng, DevStatus *st) {
+__device__ __noinline__ uint64_t binom_inversion(uint64_t n, double p, Philox &rng, DevStatus *st) {
     const double q = 1.0 - p, s = p / q, a = (double(n) + 1.0) * s;
     const double r0 = exp(double(n) * log1p(-p));
     for (int attempt = 0; attempt < 16; ++attempt) {
@@ -111,7 +111,7 @@ __device__ uint64_t binom_inversion(uint64_t n, double p, Philox &rng, DevStatus
 // quickly inside the squeeze, otherwise compare log(v * hat) with the exact
 // log f(k)/f(m) written through Stirling's series (f the binomial pmf,
 // m its mode).
-__device__ uint64_t binom_btrs(uint64_t n_, double p, Philox &rng, DevStatus *st) {
+__device__ __noinline__ uint64_t binom_btrs(uint64_t n_, double p, Philox &rng, DevStatus *st) {
     const double n = (double)n_;
     const double q = 1.0 - p;
     const double m = floor((n + 1.0) * p);
@@ -140,6 +140,11 @@ __device__ uint64_t binom_btrs(uint64_t n_, double p, Philox &rng, DevStatus *st
     return (uint64_t)m;
 }
 
+// The rejection and inversion loops and the Stirling tail are kept out of
+// line (and k_split's category loop rolled) so that a thread's up to three
+// draws run through one copy of their code: the early steps run a handful of
+// threads, whose time is the latency of this FP64 code, instruction fetches
+// included.
 __device__ uint64_t binomial(uint64_t n, double p, Philox &rng, DevStatus *st) {
     if (n == 0 || !(p > 0.0)) return 0;
     if (p >= 1.0) return n;
@@ -171,7 +176,7 @@ __global__ void k_split(const uint64_t *__restrict__ w, const double *__restrict
         if (cond[i * 4 + v] > 0.0) last = v;
     if (last < 0 && rem > 0) record_status(st, NNQS_E_SECTOR, i);
     int nc = 0;
-#pragma unroll
+#pragma unroll 1
     for (int v = 0; v < 4; ++v) {
         const double pv = cond[i * 4 + v];
         uint64_t k = 0;
