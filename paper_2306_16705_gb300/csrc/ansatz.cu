@@ -1117,10 +1117,29 @@ __global__ void k_attn_bwd_kv(const R *__restrict__ qkv, const R *__restrict__ l
 // Shared-memory attention: one CTA per sample, the sample's q|k|v rows
 // staged once (padded rows, conflict-free column reads), one thread per
 // (head, position).  Used whenever a sample's rows fit in shared memory.
+// Column c of a staged input row sits at shared column swz_col<R, NC>(c):
+// the 16-byte pieces of a head (NC of them, NC a power of two <= 8) are
+// XOR-rotated by the index of the 128-byte bank row they start in, so that
+// the threads of a warp reading piece k of every head of one row (the
+// attention loops: all lanes on the same key row) hit distinct banks.  With
+// heads of 32 bytes (8 FP32) and no rotation, heads h and h + 4 share banks
+// and every such read takes two wavefronts.  NC = 1: no rotation.
+template <class R, int NC>
+__device__ __forceinline__ int swz_col(int c) {
+    constexpr int V = int(16 / sizeof(R));
+    if constexpr (NC <= 1) {
+        return c;
+    } else {
+        const int p = c / V;
+        return (p ^ ((p >> 3) & (NC - 1))) * V + (c - p * V);
+    }
+}
+
 // copies between a contiguous [T][w] block in global memory and shared rows
 // of stride ld (padded against bank conflicts): 16-byte global accesses when
-// w and the pointer allow, the (row, column) of a thread advanced by adds
-template <class R>
+// w and the pointer allow, the (row, column) of a thread advanced by adds;
+// columns placed by swz_col<R, NC>
+template <class R, int NC = 1>
 __device__ __forceinline__ void rows_to_smem(R *dst, int ld, const R *__restrict__ src, int T, int w) {
     constexpr int V = int(16 / sizeof(R));
     if (w % V == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) {
@@ -1129,8 +1148,9 @@ __device__ __forceinline__ void rows_to_smem(R *dst, int ld, const R *__restrict
         int r = threadIdx.x / wv, c = threadIdx.x % wv;
         while (r < T) {
             const ColVec<R, V> v = ld_vec<R, V>(src + (int64_t)r * w + c * V);
+            const int cs = swz_col<R, NC>(c * V);
 #pragma unroll
-            for (int e = 0; e < V; ++e) dst[r * ld + c * V + e] = v.v[e];
+            for (int e = 0; e < V; ++e) dst[r * ld + cs + e] = v.v[e];
             r += sr;
             c += sc;
             if (c >= wv) {
@@ -1139,7 +1159,7 @@ __device__ __forceinline__ void rows_to_smem(R *dst, int ld, const R *__restrict
             }
         }
     } else {
-        for (int e = threadIdx.x; e < T * w; e += blockDim.x) dst[(e / w) * ld + e % w] = src[e];
+        for (int e = threadIdx.x; e < T * w; e += blockDim.x) dst[(e / w) * ld + swz_col<R, NC>(e % w)] = src[e];
     }
 }
 
@@ -1193,6 +1213,8 @@ struct RowBatch {
             if (e < total) v[k] = ld_vec<R, V>(src + (int64_t)e * V);
         }
     }
+    // columns placed by swz_col<R, NC>
+    template <int NC = 1>
     __device__ __forceinline__ void store(R *dst, int ld, int T, int w) const {
         const int wv = w / V, total = T * wv;
         const bool vec = ld % V == 0;  // 16-byte shared rows
@@ -1200,7 +1222,7 @@ struct RowBatch {
         for (int k = 0; k < MAXV; ++k) {
             const int e = threadIdx.x + k * blockDim.x;
             if (e < total) {
-                const int r = e / wv, c = (e - r * wv) * V;
+                const int r = e / wv, c = swz_col<R, NC>((e - r * wv) * V);
                 if (vec) {
                     uint4 u;
                     memcpy(&u, &v[k], 16);
@@ -1234,6 +1256,25 @@ template <class R, int DH>
 struct HeadVec {
     static constexpr int V = int(16 / sizeof(R));
     static constexpr bool kVec = DH % V == 0;
+    // pieces per head rotated in staged input rows (swz_col); 1 = none
+    static constexpr int kNC = (kVec && DH / V <= 8) ? DH / V : 1;
+    // head values at column col (a multiple of DH) of a staged input row
+    // (placed by swz_col<R, kNC>): piece k from column swz_col(col + k V)
+    __device__ __forceinline__ static void read_in(const R *row, int col, R (&out)[DH]) {
+        if constexpr (kVec && kNC > 1) {
+            const int p0 = col / V, sx = (p0 >> 3) & (kNC - 1);
+#pragma unroll
+            for (int k = 0; k < kNC; ++k) {
+                const uint4 u = *reinterpret_cast<const uint4 *>(row + (p0 + (k ^ sx)) * V);
+                R tmp[V];
+                memcpy(tmp, &u, 16);
+#pragma unroll
+                for (int e = 0; e < V; ++e) out[k * V + e] = tmp[e];
+            }
+        } else {
+            read(row + col, out);
+        }
+    }
     __device__ __forceinline__ static void read(const R *p, R (&out)[DH]) {
         if constexpr (kVec) {
 #pragma unroll
@@ -1283,9 +1324,9 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
         RowBatch<R, qkv_pieces<R, DH>()> b;
         if (b.fits(src, T, 3 * d)) {
             b.load(src, T, 3 * d);
-            b.store(sq, ldq, T, 3 * d);
+            b.template store<HV::kNC>(sq, ldq, T, 3 * d);
         } else {
-            rows_to_smem<R>(sq, ldq, src, T, 3 * d);
+            rows_to_smem<R, HV::kNC>(sq, ldq, src, T, 3 * d);
         }
     }
     __syncthreads();
@@ -1293,7 +1334,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
         const int hh = tid % H, q = tid / H;  // heads fastest: a warp holds a few positions (even loop trips)
         const R scale = R(1) / sqrt(R(DH));
         R qv[DH], acc[DH];
-        HV::read(sq + q * ldq + hh * DH, qv);
+        HV::read_in(sq + q * ldq, hh * DH, qv);
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
             qv[c] = qv[c] * scale;
@@ -1302,8 +1343,8 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
         R m = neg_inf<R>(), l = 0;
         for (int j = 0; j <= q; ++j) {
             R kj[DH], vj[DH];
-            HV::read(sq + j * ldq + d + hh * DH, kj);
-            HV::read(sq + j * ldq + 2 * d + hh * DH, vj);
+            HV::read_in(sq + j * ldq, d + hh * DH, kj);
+            HV::read_in(sq + j * ldq, 2 * d + hh * DH, vj);
             R sc = 0;
 #pragma unroll
             for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
@@ -1354,13 +1395,13 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
             b1.load(s1, T, 3 * d);
             b2.load(s2, T, d);
             b3.load(s3, T, d);
-            b1.store(sq, ldq, T, 3 * d);
-            b2.store(sdo, ldo, T, d);
-            b3.store(so, ldo, T, d);
+            b1.template store<HV::kNC>(sq, ldq, T, 3 * d);
+            b2.template store<HV::kNC>(sdo, ldo, T, d);
+            b3.template store<HV::kNC>(so, ldo, T, d);
         } else {
-            rows_to_smem<R>(sq, ldq, s1, T, 3 * d);
-            rows_to_smem<R>(sdo, ldo, s2, T, d);
-            rows_to_smem<R>(so, ldo, s3, T, d);
+            rows_to_smem<R, HV::kNC>(sq, ldq, s1, T, 3 * d);
+            rows_to_smem<R, HV::kNC>(sdo, ldo, s2, T, d);
+            rows_to_smem<R, HV::kNC>(so, ldo, s3, T, d);
         }
         if (tid < H * T) slse[tid] = l0;
         for (int e = tid + nt; e < H * T; e += nt) slse[e] = lse[i * H * T + e];
@@ -1375,8 +1416,8 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     R D = 0;
     if (act) {
         R dov[DH], ov[DH];
-        HV::read(sdo + pos * ldo + hh * DH, dov);
-        HV::read(so + pos * ldo + hh * DH, ov);
+        HV::read_in(sdo + pos * ldo, hh * DH, dov);
+        HV::read_in(so + pos * ldo, hh * DH, ov);
 #pragma unroll
         for (int c = 0; c < DH; ++c) D += dov[c] * ov[c];
         sD[hh * T + pos] = D;
@@ -1386,8 +1427,8 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         // dq_q = scale sum_{j<=q} p_qj (dp_qj - D_q) k_j
         const int q = pos;
         R qv[DH], dov[DH], dq[DH];
-        HV::read(sq + q * ldq + hh * DH, qv);
-        HV::read(sdo + q * ldo + hh * DH, dov);
+        HV::read_in(sq + q * ldq, hh * DH, qv);
+        HV::read_in(sdo + q * ldo, hh * DH, dov);
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
             qv[c] = qv[c] * scale;
@@ -1397,8 +1438,8 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
 #pragma unroll 2
         for (int j = 0; j <= q; ++j) {
             R kj[DH], vj[DH];
-            HV::read(sq + j * ldq + d + hh * DH, kj);
-            HV::read(sq + j * ldq + 2 * d + hh * DH, vj);
+            HV::read_in(sq + j * ldq, d + hh * DH, kj);
+            HV::read_in(sq + j * ldq, 2 * d + hh * DH, vj);
             R sc = 0, dp = 0;
 #pragma unroll
             for (int c = 0; c < DH; ++c) {
@@ -1417,15 +1458,15 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         // dv_j = sum_{q>=j} p_qj do_q,  dk_j = scale sum_{q>=j} p_qj (dp_qj - D_q) q_q
         const int j = pos;
         R kv[DH], vv[DH], dk[DH], dv[DH];
-        HV::read(sq + j * ldq + d + hh * DH, kv);
-        HV::read(sq + j * ldq + 2 * d + hh * DH, vv);
+        HV::read_in(sq + j * ldq, d + hh * DH, kv);
+        HV::read_in(sq + j * ldq, 2 * d + hh * DH, vv);
 #pragma unroll
         for (int c = 0; c < DH; ++c) dk[c] = dv[c] = 0;
 #pragma unroll 2
         for (int q = j; q < T; ++q) {
             R qq[DH], dq[DH];
-            HV::read(sq + q * ldq + hh * DH, qq);
-            HV::read(sdo + q * ldo + hh * DH, dq);
+            HV::read_in(sq + q * ldq, hh * DH, qq);
+            HV::read_in(sdo + q * ldo, hh * DH, dq);
             R sc = 0, dp = 0;
 #pragma unroll
             for (int c = 0; c < DH; ++c) {
