@@ -52,6 +52,40 @@ __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
+// Units of the attention softmax.  FP64: natural units and exp().  FP32:
+// base-2 units -- the scores carry a factor log2 e, folded into the query
+// scale -- and the special-function unit's 2^x (ex2.approx.ftz: relative
+// error near 2^-22, results below 2^-126 flushed to zero, 2^-inf = 0), one
+// instruction where expf takes several.  Every attention kernel (forward,
+// cached decode, backward) forms its weights through these, so the cached
+// sampler still reproduces the recomputed conditionals bit for bit.  The
+// stored log-sum-exp stays in natural units.
+template <class R>
+struct Softmax;
+template <>
+struct Softmax<double> {
+    static constexpr double kUnit = 1.0;
+    __device__ static double pexp(double x) { return exp(x); }
+    __device__ static double lse(double m, double l) { return m + log(l); }  // natural, from (max, sum)
+    __device__ static double unit_lse(double L) { return L; }                // natural -> score units
+};
+template <>
+struct Softmax<float> {
+    static constexpr float kUnit = 1.44269504088896340736f;  // log2 e
+    __device__ static float pexp(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static float lse(float m, float l) { return (m + log2f(l)) * 0.69314718055994530942f; }
+    __device__ static float unit_lse(float L) { return L * kUnit; }
+};
+// the query factor 1 / sqrt(DH), in score units
+template <class R, int DH>
+__device__ __forceinline__ R score_scale() {
+    return R(1) / sqrt(R(DH)) * Softmax<R>::kUnit;
+}
+
 template <class R>
 __device__ __forceinline__ R gelu_(R x) {
     return R(0.5) * x * (R(1) + erf_<R>(x * R(0.70710678118654752440)));
@@ -1001,7 +1035,7 @@ __global__ void k_attn_fwd(const R *__restrict__ qkv, R *__restrict__ o, R *__re
     const int q = (int)(idx % T);
     const int hh = (int)((idx / T) % H);
     const int64_t i = idx / ((int64_t)T * H);
-    const R scale = R(1) / sqrt(R(DH));
+    const R scale = score_scale<R, DH>();
     const R *base = qkv + i * T * 3 * d;
     R qv[DH], acc[DH];
 #pragma unroll
@@ -1017,8 +1051,8 @@ __global__ void k_attn_fwd(const R *__restrict__ qkv, R *__restrict__ o, R *__re
 #pragma unroll
         for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
         const R mn = sc > m ? sc : m;
-        const R corr = exp_<R>(m - mn);
-        const R p = exp_<R>(sc - mn);
+        const R corr = Softmax<R>::pexp(m - mn);
+        const R p = Softmax<R>::pexp(sc - mn);
         l = l * corr + p;
 #pragma unroll
         for (int c = 0; c < DH; ++c) acc[c] = acc[c] * corr + p * vj[c];
@@ -1027,7 +1061,7 @@ __global__ void k_attn_fwd(const R *__restrict__ qkv, R *__restrict__ o, R *__re
     const R inv = R(1) / l;
 #pragma unroll
     for (int c = 0; c < DH; ++c) o[(i * T + q) * d + hh * DH + c] = acc[c] * inv;
-    lse[idx] = m + log_<R>(l);
+    lse[idx] = Softmax<R>::lse(m, l);
 }
 
 // dq for each query: dq = scale sum_j p_ij (dp_ij - D_i) k_j, dp_ij = do_i . v_j,
@@ -1041,19 +1075,19 @@ __global__ void k_attn_bwd_q(const R *__restrict__ qkv, const R *__restrict__ o,
     const int q = (int)(idx % T);
     const int hh = (int)((idx / T) % H);
     const int64_t i = idx / ((int64_t)T * H);
-    const R scale = R(1) / sqrt(R(DH));
+    const R scale = R(1) / sqrt(R(DH)), qs = score_scale<R, DH>();
     const R *base = qkv + i * T * 3 * d;
     R qv[DH], dov[DH], dq[DH];
     R D = 0;
 #pragma unroll
     for (int c = 0; c < DH; ++c) {
-        qv[c] = base[q * 3 * d + hh * DH + c] * scale;
+        qv[c] = base[q * 3 * d + hh * DH + c] * qs;
         dov[c] = dout[(i * T + q) * d + hh * DH + c];
         D += dov[c] * o[(i * T + q) * d + hh * DH + c];
         dq[c] = 0;
     }
     Dbuf[idx] = D;
-    const R L = lse[idx];
+    const R L = Softmax<R>::unit_lse(lse[idx]);
     for (int j = 0; j <= q; ++j) {
         const R *kj = base + j * 3 * d + d + hh * DH;
         const R *vj = base + j * 3 * d + 2 * d + hh * DH;
@@ -1063,7 +1097,7 @@ __global__ void k_attn_bwd_q(const R *__restrict__ qkv, const R *__restrict__ o,
             sc += qv[c] * kj[c];
             dp += dov[c] * vj[c];
         }
-        const R ds = exp_<R>(sc - L) * (dp - D);
+        const R ds = Softmax<R>::pexp(sc - L) * (dp - D);
 #pragma unroll
         for (int c = 0; c < DH; ++c) dq[c] += ds * kj[c];
     }
@@ -1080,7 +1114,7 @@ __global__ void k_attn_bwd_kv(const R *__restrict__ qkv, const R *__restrict__ l
     const int j = (int)(idx % T);
     const int hh = (int)((idx / T) % H);
     const int64_t i = idx / ((int64_t)T * H);
-    const R scale = R(1) / sqrt(R(DH));
+    const R scale = R(1) / sqrt(R(DH)), qs = score_scale<R, DH>();
     const R *base = qkv + i * T * 3 * d;
     R kv[DH], vv[DH], dk[DH], dv[DH];
 #pragma unroll
@@ -1099,7 +1133,7 @@ __global__ void k_attn_bwd_kv(const R *__restrict__ qkv, const R *__restrict__ l
             sc += qq[c] * kv[c];
             dp += dq[c] * vv[c];
         }
-        const R p = exp_<R>(sc * scale - lse[row0 + q]);
+        const R p = Softmax<R>::pexp(sc * qs - Softmax<R>::unit_lse(lse[row0 + q]));
         const R ds = p * (dp - Dbuf[row0 + q]);
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
@@ -1332,7 +1366,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
     __syncthreads();
     if (tid < H * T) {
         const int hh = tid % H, q = tid / H;  // heads fastest: a warp holds a few positions (even loop trips)
-        const R scale = R(1) / sqrt(R(DH));
+        const R scale = score_scale<R, DH>();
         R qv[DH], acc[DH];
         HV::read_in(sq + q * ldq, hh * DH, qv);
 #pragma unroll
@@ -1341,6 +1375,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
             acc[c] = 0;
         }
         R m = neg_inf<R>(), l = 0;
+#pragma unroll 2
         for (int j = 0; j <= q; ++j) {
             R kj[DH], vj[DH];
             HV::read_in(sq + j * ldq, d + hh * DH, kj);
@@ -1349,8 +1384,8 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
 #pragma unroll
             for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
             const R mn = sc > m ? sc : m;
-            const R corr = exp_<R>(m - mn);
-            const R p = exp_<R>(sc - mn);
+            const R corr = Softmax<R>::pexp(m - mn);
+            const R p = Softmax<R>::pexp(sc - mn);
             l = l * corr + p;
 #pragma unroll
             for (int c = 0; c < DH; ++c) acc[c] = acc[c] * corr + p * vj[c];
@@ -1360,7 +1395,7 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
 #pragma unroll
         for (int c = 0; c < DH; ++c) acc[c] = acc[c] * inv;
         HV::write(so + q * ldo + hh * DH, acc);
-        lse[(i * H + hh) * T + q] = m + log_<R>(l);
+        lse[(i * H + hh) * T + q] = Softmax<R>::lse(m, l);
     }
     __syncthreads();
     R *dst = o + i * T * d;
@@ -1390,7 +1425,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         RowBatch<R, qkv_pieces<R, DH>()> b1;
         RowBatch<R, row_pieces<R, DH>()> b2, b3;
         const bool f = b1.fits(s1, T, 3 * d) && b2.fits(s2, T, d) && b3.fits(s3, T, d);
-        R l0 = tid < H * T ? lse[i * H * T + tid] : R(0);
+        R l0 = tid < H * T ? Softmax<R>::unit_lse(lse[i * H * T + tid]) : R(0);
         if (f) {
             b1.load(s1, T, 3 * d);
             b2.load(s2, T, d);
@@ -1404,10 +1439,10 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
             rows_to_smem<R, HV::kNC>(so, ldo, s3, T, d);
         }
         if (tid < H * T) slse[tid] = l0;
-        for (int e = tid + nt; e < H * T; e += nt) slse[e] = lse[i * H * T + e];
+        for (int e = tid + nt; e < H * T; e += nt) slse[e] = Softmax<R>::unit_lse(lse[i * H * T + e]);
     }
     __syncthreads();
-    const R scale = R(1) / sqrt(R(DH));
+    const R scale = R(1) / sqrt(R(DH)), qs = score_scale<R, DH>();  // slse in score units
     const bool act = tid < H * T;
     const int hh = act ? tid % H : 0, pos = act ? tid / H : 0;  // heads fastest
     // D_q = do_q . o_q for every (head, position) first, so that the two
@@ -1431,7 +1466,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         HV::read_in(sdo + q * ldo, hh * DH, dov);
 #pragma unroll
         for (int c = 0; c < DH; ++c) {
-            qv[c] = qv[c] * scale;
+            qv[c] = qv[c] * qs;
             dq[c] = 0;
         }
         const R L = slse[hh * T + q];
@@ -1446,7 +1481,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
                 sc += qv[c] * kj[c];
                 dp += dov[c] * vj[c];
             }
-            const R ds = exp_<R>(sc - L) * (dp - D);
+            const R ds = Softmax<R>::pexp(sc - L) * (dp - D);
 #pragma unroll
             for (int c = 0; c < DH; ++c) dq[c] += ds * kj[c];
         }
@@ -1473,7 +1508,7 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
                 sc += qq[c] * kv[c];
                 dp += dq[c] * vv[c];
             }
-            const R p = exp_<R>(sc * scale - slse[hh * T + q]);
+            const R p = Softmax<R>::pexp(sc * qs - slse[hh * T + q]);
             const R ds = p * (dp - sD[hh * T + q]);
 #pragma unroll
             for (int c = 0; c < DH; ++c) {
@@ -1625,7 +1660,7 @@ template <class R, int DH>
 __device__ __forceinline__ void attn_decode_row(const R *__restrict__ pool, const int32_t *__restrict__ anc_row,
                                                 int64_t self, int t, int L, int l, int d, int hh, R (&o)[DH]) {
     const int64_t row = 3 * (int64_t)d;
-    const R scale = R(1) / sqrt(R(DH));
+    const R scale = score_scale<R, DH>();
     R qv[DH], acc[DH];
     const R *qp = pool + (self * L + l) * row + hh * DH;
 #pragma unroll
@@ -1643,8 +1678,8 @@ __device__ __forceinline__ void attn_decode_row(const R *__restrict__ pool, cons
 #pragma unroll
         for (int c = 0; c < DH; ++c) sc += qv[c] * kj[c];
         const R mn = sc > m ? sc : m;
-        const R corr = exp_<R>(m - mn);
-        const R p = exp_<R>(sc - mn);
+        const R corr = Softmax<R>::pexp(m - mn);
+        const R p = Softmax<R>::pexp(sc - mn);
         lsum = lsum * corr + p;
 #pragma unroll
         for (int c = 0; c < DH; ++c) acc[c] = acc[c] * corr + p * vj[c];
@@ -1873,7 +1908,7 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
                                                    int L, int l, int hh, float (&o)[NR][DH]) {
     constexpr int d = dec::kD;
     const int64_t row = 3 * (int64_t)d;
-    const float scale = 1.0f / sqrtf(float(DH));
+    const float scale = score_scale<float, DH>();
     float qv[NR][DH], acc[NR][DH], m[NR], lsum[NR];
     bool ok[NR];
     int64_t rr[NR];
@@ -1925,8 +1960,8 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
 #pragma unroll
             for (int c = 0; c < DH; ++c) sc += qv[k][c] * kk[k][c];
             const float mn = sc > m[k] ? sc : m[k];
-            const float corr = exp_<float>(m[k] - mn);
-            const float p = exp_<float>(sc - mn);
+            const float corr = Softmax<float>::pexp(m[k] - mn);
+            const float p = Softmax<float>::pexp(sc - mn);
             lsum[k] = lsum[k] * corr + p;
 #pragma unroll
             for (int c = 0; c < DH; ++c) acc[k][c] = acc[k][c] * corr + p * vv[k][c];
