@@ -154,11 +154,23 @@ class OracleStep:
                        wl.n_heads)
         t2 = time.perf_counter()
         step_s = (t1 - t0) / n_fwd * N_SAMPLES + (t2 - t1) / n_rows * N_SAMPLES
-        return {"step_s": step_s, "sampled_s": t2 - t0, "n_terms": self.n_terms,
+        return {"step_s": step_s, "sampled_s": t2 - t0, "rows_s": t2 - t1, "n_terms": self.n_terms,
                 "pairs_per_s": N_SAMPLES * self.n_terms / step_s,
                 "sample": f"log psi of {n_fwd} and local energy + reverse mode of {n_rows} of the {N_SAMPLES} "
                           f"samples (table of all {N_SAMPLES}); step time extrapolated linearly to "
                           f"{N_SAMPLES}; no sampler"}
+
+
+def sized_oracle_run(bench: "OracleStep", target_s: float):
+    """bench.run with the row sample grown (from 48 rows) until the timed
+    oracle work takes about target_s seconds (at most all N_u rows)."""
+    first = bench.run(512, 48)
+    if first["sampled_s"] >= 0.8 * target_s:
+        return first
+    rows_budget = target_s - (first["sampled_s"] - first["rows_s"])
+    n_rows = int(48 * rows_budget / max(first["rows_s"], 1e-3))
+    n_rows = max(48, min(N_SAMPLES, n_rows // 16 * 16))
+    return bench.run(512, n_rows)
 
 
 # The speed-up ladder of Sec. 4.3 (Fig. speedup-eloc) on molecule-shaped
@@ -256,10 +268,13 @@ def run_reference(args):
     bench = OracleStep(wl)
     for _ in range(max(0, min(args.warmup, 1))):
         bench.run(64, 8)
+    # each step a bounded sample: about 10 s of oracle work, less when many
+    # steps are asked for, so that the run stays within a few minutes
+    target_s = max(1.0, min(10.0, 150.0 / max(1, args.steps)))
     ts = []
     last = None
     for _ in range(args.steps):
-        last = bench.run(512, 48)
+        last = sized_oracle_run(bench, target_s)
         ts.append(last["step_s"])
     step_s = float(np.mean(ts))
     value = N_SAMPLES * last["n_terms"] / step_s
@@ -527,7 +542,7 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            base = OracleStep(wl).run(512, 48)
+            base = sized_oracle_run(OracleStep(wl), 10.0)
             line["cpu_baseline"] = {"value": base["pairs_per_s"], "unit": "pairs/s", "cores": cores(),
                                     "kind": "oracle", "sample": base["sample"]}
         except Exception as exc:  # keep the GPU line even if the oracle cannot build here
