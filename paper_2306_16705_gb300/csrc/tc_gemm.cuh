@@ -30,6 +30,9 @@ constexpr int kChunkK = 64;                      // BF16 per 128-byte row
 constexpr int kABytes = kTileM * kChunkK * 2;    // 16 KB
 constexpr int kMaxN = 128;                       // N per CTA: TMEM 128 columns, 4 CTAs per SM
 constexpr int kBBytes = kMaxN * kChunkK * 2;     // 16 KB
+// dynamic shared memory: 1024 bytes of alignment slack, the operand buffers
+// (kOps), then at kOps + 0 the MMA mbarrier, + 16 the TMEM address, + 24 the
+// four epilogue residual-slot mbarriers, + 64 the 512-byte column-sum scratch
 constexpr int kSmemBytes = kABytes + kBBytes + 1024 + 64 + 512;
 // split operands: high and low BF16 parts of A and B
 constexpr int kSmemBytesSplit = 2 * (kABytes + kBBytes) + 1024 + 64 + 512;
