@@ -154,7 +154,7 @@ class OracleStep:
                        wl.n_heads)
         t2 = time.perf_counter()
         step_s = (t1 - t0) / n_fwd * N_SAMPLES + (t2 - t1) / n_rows * N_SAMPLES
-        return {"step_s": step_s, "sampled_s": t2 - t0, "rows_s": t2 - t1, "n_terms": self.n_terms,
+        return {"step_s": step_s, "sampled_s": t2 - t0, "rows_s": t2 - t1, "n_rows": n_rows, "n_terms": self.n_terms,
                 "pairs_per_s": N_SAMPLES * self.n_terms / step_s,
                 "sample": f"log psi of {n_fwd} and local energy + reverse mode of {n_rows} of the {N_SAMPLES} "
                           f"samples (table of all {N_SAMPLES}); step time extrapolated linearly to "
@@ -274,7 +274,7 @@ def run_reference(args):
     ts = []
     last = None
     for _ in range(args.steps):
-        last = sized_oracle_run(bench, target_s)
+        last = sized_oracle_run(bench, target_s) if last is None else bench.run(512, last["n_rows"])
         ts.append(last["step_s"])
     step_s = float(np.mean(ts))
     value = N_SAMPLES * last["n_terms"] / step_s
