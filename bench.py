@@ -163,13 +163,13 @@ class OracleStep:
 
 def sized_oracle_run(bench: "OracleStep", target_s: float):
     """bench.run with the row sample grown (from 48 rows) until the timed
-    oracle work takes about target_s seconds (at most all N_u rows)."""
+    oracle work takes about target_s seconds (at most 4,096 rows)."""
     first = bench.run(512, 48)
     if first["sampled_s"] >= 0.8 * target_s:
         return first
     rows_budget = target_s - (first["sampled_s"] - first["rows_s"])
     n_rows = int(48 * rows_budget / max(first["rows_s"], 1e-3))
-    n_rows = max(48, min(N_SAMPLES, n_rows // 16 * 16))
+    n_rows = max(48, min(4096, n_rows // 16 * 16))  # at most 4,096 rows: a few GB of oracle activations
     return bench.run(512, n_rows)
 
 
