@@ -90,7 +90,10 @@ inline void below_mask(int j, uint64_t m[2]) {
 }
 
 // Expands scale * op_0 op_1 ... op_{n-1} (ladder operators j[k], creation
-// when cre[k]) into its 2^n strings and adds them to the map.
+// when cre[k]) into its 2^n strings and adds those with an even number of Y
+// to the map.  The odd ones fold to zero (Re((-i)^{nY}) = 0, Alg. 1) and
+// never share a key with an even one, so leaving them out changes no kept
+// coefficient and halves the insertions.
 void expand(StrMap &map, int nops, const int *j, const bool *cre, double scale) {
     uint64_t a[2] = {0, 0}, base[2] = {0, 0};
     int fixed_parity = 0;
@@ -113,6 +116,7 @@ void expand(StrMap &map, int nops, const int *j, const bool *cre, double scale) 
             if (!cre[k]) c = -c;
             for (int l = k + 1; l < nops; ++l) parity += (j[l] == j[k]);
         }
+        if ((__builtin_popcountll(a[0] & b[0]) + __builtin_popcountll(a[1] & b[1])) & 1) continue;
         map.add(a, b, (parity & 1) ? -c : c);
     }
 }
