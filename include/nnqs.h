@@ -25,8 +25,14 @@
  * - Workspace: every call that needs scratch device memory takes a
  *   caller-allocated device buffer `workspace` of at least the size its
  *   *_workspace_size function returns (256-byte aligned).  The library
- *   itself allocates device memory only in nnqs_build_pauli and
- *   nnqs_sample (documented there).
+ *   itself allocates device memory only for the Hamiltonian's tables, owned
+ *   by its handle (nnqs_build_pauli, nnqs_ham_build_ungrouped); the one
+ *   static array of nnqs_eloc_sa_noalloc is documented there.
+ * - Empty inputs: nnqs_logpsi with n = 0, nnqs_eloc with n_rows = 0 and
+ *   nnqs_sample with n_samples = 0 (*n_unique_out = 0) return NNQS_OK
+ *   after their argument checks and launch nothing; nnqs_energy_stats and
+ *   nnqs_energy_grad reject an empty sample set with NNQS_E_INVAL (the
+ *   weighted mean is undefined).
  * - No exception crosses the ABI.  nnqs_last_error() returns a thread-local
  *   message for the last non-OK status returned on this thread.
  */
