@@ -120,6 +120,22 @@ def test_argument_errors_are_status_codes():
     assert e.value.status == B.E_NONFINITE
 
 
+def test_entry_points_reject_bad_arguments_before_any_device_work():
+    """Null handles, negative counts and empty sample sets come back as
+    NNQS_E_INVAL with a message, from the host-side checks alone (these calls
+    touch no device)."""
+    L = B.lib()
+    assert L.nnqs_energy_stats(None, None, 0, None, None, 0, None) == B.E_INVAL
+    assert L.nnqs_last_error()
+    assert L.nnqs_energy_grad(None, None, None, None, None, 0, 0, None, None, None, None, None, 0,
+                              None) == B.E_INVAL
+    assert L.nnqs_logpsi(None, None, None, 4, 0, None, None, 0, None) == B.E_INVAL
+    assert L.nnqs_logpsi_backward(None, None, None, -1, 0, None, None, None, None, 0, None) == B.E_INVAL
+    assert L.nnqs_sample(None, None, 16, 1, 0, 0, 8, None, None, None, None, 0, None) == B.E_INVAL
+    assert L.nnqs_eloc(None, None, None, None, None, 0, 0, 0, 1, 1, 0, 0, 0, None, None, 0,
+                       None) == B.E_INVAL
+
+
 def test_model_layout_matches_named_shapes():
     wl = I.WORKLOADS["n40"]
     m = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
