@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-samples", type=int, default=N_SAMPLES, help="N_s per step (smaller for profiling)")
     ap.add_argument("--no-layouts", action="store_true", help="skip the grouped/ungrouped layout comparison")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the integer / FP64 / FP32 pipe measurements")
+    ap.add_argument("--exact-rows", type=int, default=1024,
+                    help="rows of the exact-mode side line (0 = skip)")
+    ap.add_argument("--n120-steps", type=int, default=3, help="timed steps of the 120-qubit side line (0 = skip)")
     ap.add_argument("--ladder", action="store_true",
                     help="add the local-energy speed-up ladder (Sec. 4.3) to the CPU baseline (about a minute)")
     return ap.parse_args()
@@ -293,7 +297,215 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+
+def model_flops_per_sample(wl) -> float:
+    """Method FLOPs of one ansatz forward (Sec. 3.1): the decoder layers'
+    four products (q|k|v, out-projection, FFN in and out), causal attention
+    (scores and weighted sum), the head and the phase MLP."""
+    T, d, L, H = wl.n_qubits // 2, wl.d_model, wl.n_layers, wl.n_heads
+    F, P, N = 4 * d, 512, wl.n_qubits
+    layers = 2.0 * T * L * (4 * d * d + 2 * d * F)
+    attn = 2.0 * L * H * (T * (T + 1) / 2) * (d // H) * 2
+    return layers + attn + 2.0 * T * d * 4 + 2.0 * (N * P + P * P + P)
+
+
+def sweep_roofline(prof: dict, peaks: dict, W: int) -> dict | None:
+    """Roofline of the sample-aware sweep (Alg. 2) against the measured
+    XOR+popcount rate: a pair-sweep test is W XOR+popcount tests, a group-sweep
+    test 2W (one per spin), a string-sweep test 5W."""
+    per = {"k_sweep_pairs": W, "k_sweep_groups": 2 * W, "k_sweep_terms": 5 * W}
+    fams = [(k, prof[k]) for k in per if k in prof and prof[k]["ms"] > 0]
+    if not fams or not peaks.get("xor_popc64_per_s"):
+        return None
+    k, f = max(fams, key=lambda kv: kv[1]["ms"])
+    tests = f["flops"]  # the launch sites count (row, group / sample / string) tests
+    rate = tests * per[k] / (f["ms"] / 1e3)
+    return {"kernel": k, "bound": "alu", "achieved": rate, "peak": peaks["xor_popc64_per_s"],
+            "unit": "xor+popc64/s", "frac": rate / peaks["xor_popc64_per_s"],
+            "tests_per_launch": tests / max(1, f["launches"]), "popc_per_test": per[k],
+            "launches": f["launches"], "avg_launch_ms": f["ms"] / max(1, f["launches"]),
+            "hbm_gbs": f["bytes"] / (f["ms"] / 1e3) / 1e9,
+            "peak_source": "nnqs_measure_peaks (measured in this run)"}
+
+
+def run_exact_side_line(ham, model, wl, params, x, prec, n_rows, peaks, tflops_peak):
+    """Exact-mode local energy (Eq. Eloc over every coupled x', Sec. 3.4 (2))
+    of the first n_rows samples of a step: coupled-set expansion and dedup,
+    the tensor-core ansatz forward over the unique coupled states, the fused
+    sweep.  Also 64 rows through the plain FP64 path for the error."""
+    import torch
+
+    from paper_2306_16705_gb300 import binding as B
+
+    rows = x[:n_rows].contiguous()
+    # |U|: the deduplicated coupled set the call below builds
+    Ud, cnt, _, _ = B.exact_coupled(ham, rows, wl.n_alpha, wl.n_beta, row_cap=16384)
+    n_u = int(Ud.shape[0])
+    n_x = int(cnt.sum().item())
+    del Ud
+    B.eloc(ham, rows[:32], None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params, prec=prec)
+    torch.cuda.synchronize()
+    B.profile_reset()
+    B.profile_enable(True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    got = B.eloc(ham, rows, None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params, prec=prec)
+    e1.record(st)
+    e1.synchronize()
+    prof = B.profile()
+    B.profile_enable(False)
+    t = e0.elapsed_time(e1) / 1e3
+    ansatz_ms = sum(v["ms"] for k, v in prof.items()
+                    if k not in ("k_insert_rows", "k_expand", "k_compact", "k_diag", "k_sweep_exact",
+                                 "k_reduce_partials"))
+    fl = model_flops_per_sample(wl) * n_u
+    tc = prof.get("k_tc_gemm", {"flops": 0.0, "ms": 0.0})
+    info = ham.info()
+    e64 = B.eloc(ham, rows[:64], None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params,
+                 prec=B.FP64)
+    d = (got[:64] - e64).abs().max().item()
+    return {
+        "rows": n_rows, "unique_coupled_states": n_u, "coupled_pairs": n_x, "ms": t * 1e3,
+        "coupled_states_per_s": n_u / t, "coupled_pairs_per_s": n_x / t,
+        "logical_pairs_per_s": n_rows * info["n_terms"] / t,
+        "ansatz_ms": ansatz_ms, "ansatz_model_tflops": fl / (ansatz_ms / 1e3) / 1e12,
+        "ansatz_frac_of_burst_bf16": fl / (ansatz_ms / 1e3) / 1e12 / tflops_peak,
+        "k_tc_gemm_tflops": tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] else None,
+        "stage_ms": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+        "max_abs_diff_vs_fp64_first64": d,
+        "max_rel_diff_vs_fp64_first64": d / max(1.0, e64.abs().max().item()),
+        "note": "prec " + {B.BF16X3: "bf16x3", B.MIXED: "mixed", B.FP32: "fp32", B.FP64: "fp64"}[prec] +
+                "; forward FLOPs = unique coupled states x method FLOPs per sample"}
+
+
+def run_n120_side_line(steps, warmup, peaks, clocks_on, local):
+    """The 120-qubit, 40-electron workload (seed 3, rank 32; 19,233,001
+    strings in 4,111,711 groups; d=128, 6 layers, 8 heads), shaped like the
+    benzene 6-31G run of Sec. 4.4: a VMC step samples N_s = 131,072 from the
+    random-init ansatz, replaces the counts by Zipf(1.2) weights, runs the
+    energy gradient in BF16X3 (local energy by the pair sweep, reverse mode
+    over recomputed activation chunks) and an Adam update."""
+    import torch
+
+    from paper_2306_16705_gb300 import binding as B
+    from paper_2306_16705_gb300 import inputs as I
+
+    wl = I.WORKLOADS["n120"]
+    h, eri = I.workload_integrals(wl)
+    t0 = time.perf_counter()
+    ham = B.build_pauli(h, eri)
+    build_s = time.perf_counter() - t0
+    info = ham.info()
+    model = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+    p0 = model.pack(I.workload_params(wl))
+    params = p0.clone()
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    grad = torch.empty_like(params)
+    ns = 131072
+    zipf = torch.from_numpy(I.zipf_counts(ns, 1.2, seed=3).astype(np.int64)).cuda()
+    nb = B.lib().nnqs_sample_workspace_size(model.handle, ns, B.BF16X3, 0)
+    ws_s = B.workspace(nb)
+    ws_g = B.workspace(B.lib().nnqs_energy_grad_workspace_size(ham.handle, model.handle, ns, B.BF16X3))
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(i, marks):
+        x, w = B.sample(model, params, ns, seed=5000 + i, max_unique=ns, prec=B.BF16X3, check=False, ws=ws_s)
+        marks[1].record(st)
+        stats, _, _ = B.energy_grad(ham, model, params, x, zipf[:x.shape[0]], B.BF16X3, check=False, ws=ws_g,
+                                    want_eloc=False, grad_out=grad)
+        marks[2].record(st)
+        B.adam_step(params, grad, m, v, 1, lr=1e-3)
+        return x.shape[0], stats
+
+    for i in range(warmup):
+        params.copy_(p0)
+        step(i, [torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+    B.profile_reset()
+    ts, stages, nus = [], {"sample": 0.0, "energy_grad": 0.0, "adam": 0.0}, []
+    with Clocks(local, clocks_on) as clk:
+        for i in range(steps):
+            params.copy_(p0)
+            m.zero_()
+            v.zero_()
+            flush.zero_()
+            mk = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            mk[0].record(st)
+            nu, stats = step(i, mk)
+            mk[3].record(st)
+            mk[3].synchronize()
+            ts.append(mk[0].elapsed_time(mk[3]))
+            stages["sample"] += mk[0].elapsed_time(mk[1])
+            stages["energy_grad"] += mk[1].elapsed_time(mk[2])
+            stages["adam"] += mk[2].elapsed_time(mk[3])
+            nus.append(nu)
+    # one more step with every launch timed, for the per-kernel split
+    B.profile_enable(True)
+    params.copy_(p0)
+    step(steps, [torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    prof = B.profile()
+    B.profile_enable(False)
+    ms = float(np.mean(ts))
+    nu = float(np.mean(nus))
+    out = {
+        "workload": "n120: 120 spin orbitals, 40 electrons, N_s=131072 (Zipf s=1.2 weights), d=128 L=6 H=8, "
+                    "19233001 Pauli strings / 4111711 groups",
+        "prec": "bf16x3", "steps": steps, "warmup": warmup, "ms_per_step": ms, "step_ms": [round(t, 2) for t in ts],
+        "n_u_mean": nu, "value": nu * info["n_terms"] / (ms / 1e3), "unit": "pairs/s",
+        "stage_ms_per_step": {k: round(v / steps, 3) for k, v in stages.items()},
+        "energy_ha": float(stats[0].item()), "hamiltonian_build_s": build_s,
+        "kernels_ms": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:10]},
+        "sweep_roofline": sweep_roofline(prof, peaks, 2),
+    }
+    sw = prof.get("k_sweep_pairs") or prof.get("k_sweep_groups")
+    if sw:
+        out["sweep_ms"] = sw["ms"]
+    if clocks_on:
+        out["clocks"] = clk.summary()
+    return out
+
+
+def single_core_oracle(wl_name: str, n_rows: int) -> dict:
+    """The oracle's sample-aware local energy of n_rows rows against the
+    full table, pinned to one host core (OpenMP and BLAS set to one thread
+    by the caller's environment), extrapolated linearly to N_u rows."""
+    from oracle import hamiltonian as OH
+    from paper_2306_16705_gb300 import inputs as I
+
+    wl = I.WORKLOADS[wl_name]
+    h, eri = I.workload_integrals(wl)
+    strings = OH.build(h, eri)
+    S = I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, N_SAMPLES, seed=wl.seed)
+    lp = I.random_logpsi(N_SAMPLES, seed=wl.seed, amp_std=0.1)
+    t0 = time.perf_counter()
+    OH.eloc_lut(*strings, S, lp, S[:n_rows], wl.n_alpha, wl.n_beta)
+    dt = time.perf_counter() - t0
+    n_terms = len(strings[2])
+    return {"value": n_rows * n_terms / dt, "unit": "pairs/s (local energy only)", "cores": 1,
+            "kind": "oracle", "sample": f"sample-aware local energy of {n_rows} of the {N_SAMPLES} rows against "
+                                        f"the full table, one core ({dt:.1f} s)"}
+
+
+def run_single_core(n_rows: int = 1024) -> dict | None:
+    """single_core_oracle in a child process bound to one core."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import os, json, sys; sys.path.insert(0, %r); "
+            "os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]}); "
+            "import bench; print(json.dumps(bench.single_core_oracle(%r, %d)))" % (ROOT, WORKLOAD, n_rows))
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if p.returncode != 0:
+        return {"failed": p.stderr[-300:]}
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
 # ---------------------------------------------------------------- our arm
+def replica_seed(rank: int) -> int:
+    """Run seed of replica ``rank``: every rank samples its own batches."""
+    return 1000 + int(rank)
+
+
 def aggregate_ranks(ms_step: float, n_u_total: int, dist, device):
     """Replicas: the job's step time is the slowest rank's, its work the sum of
     every rank's unique samples."""
@@ -334,8 +546,9 @@ def run_ours(args):
     def make(p):
         # replicas: each rank samples its own batch (different seeds)
         return VMC(ham, model, params0.clone(), prec=p, n_samples=args.n_samples, max_unique=1 << 15,
-                   seed=1000 + rank)
+                   seed=replica_seed(rank))
 
+    peaks_run = {} if args.no_peaks else B.measure_peaks()
     vmc = make(prec)
     p_init = vmc.params.clone()
     for _ in range(args.warmup):
@@ -406,26 +619,32 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+    tpk = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    tpk_src = "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback 1.7 PFLOP/s sustained"
     if name == "k_tc_gemm":
-        # the ansatz's layers are thin (K, N <= 4 d): ~25 flop per byte, far
-        # below the tensor ridge, so the bound is HBM; the tensor rate is given beside
+        # the ansatz's products are a dense contraction: the bound is the
+        # tensor pipe (sustained BF16, the kernel runs inside a long step),
+        # counted in the method's FLOPs (one product per layer, not the three
+        # BF16 products of the split forward); the HBM rate of the
+        # implementation's FP32 operand traffic is given beside it
         pk = float(peaks.get("hbm_gbs", 6800.0))
-        tpk = float(peaks.get("bf16_tflops_sustained", 1700.0))
         gbs = f["bytes"] / (f["ms"] / 1e3) / 1e9
         tflops = f["flops"] / (f["ms"] / 1e3) / 1e12
         traffic = (TC_GEMM_TRAFFIC_BYTES if TC_GEMM_TRAFFIC_BYTES and args.n_samples == N_SAMPLES
                    and args.prec == "bf16x3" else None)
-        roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s", "frac": gbs / pk,
-                "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
-                "tensor_tflops": tflops, "tensor_frac_of_sustained_bf16": tflops / tpk,
-                "algorithmic_bytes_per_launch": f["bytes"] / max(1, f["launches"]),
+        roof = {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": tpk, "unit": "TFLOP/s",
+                "frac": tflops / tpk, "traffic": traffic, "peak_source": tpk_src + " (of measured)",
+                "flops_per_launch": f["flops"] / max(1, f["launches"]),
+                "hbm": {"achieved_gbs": gbs, "peak_gbs": pk, "frac": gbs / pk,
+                        "algorithmic_bytes_per_launch": f["bytes"] / max(1, f["launches"]),
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"},
                 "launches": f["launches"], "avg_launch_ms": avg_ms}
     elif name == "k_gemm":
+        fpk = peaks_run.get("fp32_flops", FP32_PEAK_TFLOPS * 1e12) / 1e12
         achieved = f["flops"] / (f["ms"] / 1e3) / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP32 CUDA-core FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived)",
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fpk,
+                "unit": "TFLOP/s", "frac": achieved / fpk, "traffic": None,
+                "peak_source": "nnqs_measure_peaks FP32 FMA (measured)" if peaks_run else "derived FP32 peak",
                 "launches": f["launches"], "avg_launch_ms": avg_ms}
     elif f["flops"] > 0:
         achieved = f["flops"] / (f["ms"] / 1e3)
@@ -434,6 +653,20 @@ def run_ours(args):
     else:
         roof = {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "launches": f["launches"], "avg_launch_ms": avg_ms}
+    # the whole ansatz (forward + reverse mode + sampler) in method FLOPs
+    # against the sustained tensor peak, and the sweep against the measured
+    # XOR+popcount rate
+    fwd = model_flops_per_sample(wl)
+    n_u_step = n_u_total / max(1, args.steps * world)
+    rooflines = {"sweep": sweep_roofline(prof, peaks_run, 1),
+                 "energy_grad_ansatz": {
+                     "bound": "tensor", "unit": "TFLOP/s", "peak": tpk,
+                     "flops_per_step": 3.0 * fwd * n_u_step,
+                     "note": "method FLOPs of one forward and its reverse mode (2x) over the step's unique samples, "
+                             "divided by the energy-gradient stage time (which also holds the local energy)"}}
+    eg_ms = stages["energy_grad"] / args.steps
+    rooflines["energy_grad_ansatz"]["achieved"] = 3.0 * fwd * n_u_step / (eg_ms / 1e3) / 1e12
+    rooflines["energy_grad_ansatz"]["frac"] = rooflines["energy_grad_ansatz"]["achieved"] / tpk
 
     line = {
         "metric": "local-energy (sample x Pauli-term) evals/sec, whole VMC step",
@@ -451,6 +684,8 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB memset)"},
         "gpu_launches": launches,
         "roofline": roof,
+        "rooflines": rooflines,
+        "peaks_measured": peaks_run,
         "profiled_ms_per_step": float(np.mean(prof_times)),
         "stage_ms_per_step": {k: round(v / args.steps, 3) for k, v in stages.items()},
         "kernels_ms": {k: round(v["ms"], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
@@ -510,6 +745,19 @@ def run_ours(args):
         lay["reduction_bytewise"] = 1 - lay["bytes"]["grouped_bytewise"] / lay["bytes"]["ungrouped_bytewise"]
         line["layout_comparison"] = lay
 
+    if rank == 0 and world == 1 and args.exact_rows > 0:
+        try:
+            line["exact_mode"] = run_exact_side_line(ham, model, wl, vmc.params, vmc.last_samples, prec,
+                                                     args.exact_rows, peaks_run,
+                                                     float(peaks.get("bf16_tflops", 1890.0)))
+        except Exception as exc:
+            line["exact_mode"] = {"failed": str(exc)}
+    if rank == 0 and world == 1 and args.n120_steps > 0:
+        try:
+            line["n120"] = run_n120_side_line(args.n120_steps, 1, peaks_run, not args.no_clocks, local)
+        except Exception as exc:
+            line["n120"] = {"failed": str(exc)}
+
     # end to end through the public API with host buffers: parameters in
     # from pinned memory, energy statistics and parameters out, every step
     p_host = vmc.params.detach().cpu().pin_memory()
@@ -548,6 +796,10 @@ def run_ours(args):
         except Exception as exc:  # keep the GPU line even if the oracle cannot build here
             line["cpu_baseline"] = {"value": None, "unit": "pairs/s", "cores": cores(), "kind": "oracle",
                                     "sample": f"failed: {exc}"}
+        try:
+            line["cpu_baseline"]["single_core"] = run_single_core()
+        except Exception as exc:
+            line["cpu_baseline"]["single_core"] = {"failed": str(exc)}
         if args.ladder:
             try:
                 line["cpu_baseline"]["ladder"] = run_ladder()

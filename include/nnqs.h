@@ -110,6 +110,23 @@ int nnqs_profile_read(int index, char *name, int name_cap, uint64_t *launches, d
 int nnqs_profile_work(int index, double *flops, double *bytes);
 uint64_t nnqs_launch_count(void); /* kernel launches since the library loaded */
 
+/* Measured pipe throughput for roofline fractions (instrumentation, not
+ * part of the method; the paper has no counterpart).  Register-only loop
+ * kernels over every SM, timed with CUDA events on `stream` (best of three
+ * after a warm-up launch; synchronises):
+ *   out[0]  64-bit XOR + popcount tests per second (the mask test of the
+ *           sample-aware sweeps of Alg. 2: two 32-bit logic ops, two
+ *           popcounts and one add)
+ *   out[1]  32-bit integer ALU operations per second (logic op + add)
+ *   out[2]  FP64 FMA flops per second (2 per FMA)
+ *   out[3]  FP32 FMA flops per second (2 per FMA)
+ * sink: device buffer of nnqs_measure_peaks_sink_size() bytes that receives
+ * the loops' results (caller-owned, contents meaningless).  Reads and changes
+ * no clock or other device setting.  Errors: NNQS_E_INVAL, NNQS_E_WORKSPACE,
+ * NNQS_E_CUDA. */
+size_t nnqs_measure_peaks_sink_size(void);
+nnqs_status nnqs_measure_peaks(double out[4], void *sink, size_t sink_bytes, nnqs_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Hamiltonian: Eq. (eham) -> Jordan-Wigner Pauli strings, Eq. (sham),  */
 /* merged, coefficient-folded and grouped by X/Y mask as in Alg. 1 and  */
@@ -264,23 +281,58 @@ nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *param
  * fixed 64 MiB array in device memory that every GPU loading the library
  * holds until the process exits.  The paper has no counterpart: this is a
  * calling convention, not part of the method.
- *   Arguments and result as nnqs_eloc (mode NNQS_SA).  A call whose
- *   scratch would exceed 64 MiB (roughly 10^6 rows and table entries for
- *   N <= 64, somewhat fewer for two-word bitstrings) is rejected with
- *   NNQS_E_INVAL; use nnqs_eloc with a workspace then.
+ *   Arguments, argument checks and result as nnqs_eloc (mode NNQS_SA),
+ *   every NNQS_SWEEP_* flag included (NNQS_SWEEP_TERMS after
+ *   nnqs_ham_build_ungrouped).  The scratch a call needs is sized for the
+ *   sweep that call runs (NNQS_SWEEP_AUTO resolved first): 65 to 145 bytes
+ *   per table row, depending on the table size (the hash has a power-of-two
+ *   capacity) and the word count, so tables of about 5 x 10^5 rows fit; a
+ *   call above 64 MiB is rejected
+ *   with NNQS_E_INVAL before any launch; use nnqs_eloc with a workspace then.
  *   check != 0: synchronise `stream` and return the status the kernels
- *   recorded (sample outside the sector, duplicate, ...); check == 0: fully
- *   asynchronous, such errors are not reported.
+ *   recorded (sample outside the sector, duplicate, ...).  check == 0: fully
+ *   asynchronous, and errors the GPU detects are lost: the status word lives
+ *   in the shared array only until the next call clears it, and there is no
+ *   call to read it.  Callers that need those errors pass check != 0.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * previous call's contents (each call clears what must start at zero): calls
- * whose execution overlaps on the GPU -- from two streams, or two host
- * threads -- race on it and must be serialised by the caller. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture, and
+ * do not reset the device's primary context (cudaDeviceReset) after it: the
+ * kept address would then be stale.  All calls share the one array, which
+ * keeps the previous call's contents (each call clears what must start at
+ * zero): calls whose execution overlaps on the GPU -- from two streams, or
+ * two host threads -- race on it and must be serialised by the caller. */
 nnqs_status nnqs_eloc_sa_noalloc(const nnqs_ham *H, const uint64_t *lut, const double *lut_logpsi,
                                  int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha,
                                  int n_beta, int flags, double *eloc_out, int check,
                                  nnqs_stream stream);
+
+/* The coupled set of exact mode exactly as the GPU builds it for nnqs_eloc
+ * (mode NNQS_EXACT), exported for parity tests and inspection (Eq. Eloc over
+ * every x' with H_{x x'} != 0 structurally; the dedup of Sec. 3.4 (2)): the
+ * rows x = lut[row_begin + i], i < n_rows, and every x' = x ^ m over the
+ * groups m that keep the (n_alpha, n_beta) sector are inserted into the
+ * device hash table and numbered, as nnqs_eloc does before its forward.
+ * Outputs (device, caller-owned):
+ *   unique_out  [cap_unique][W]: the distinct keys U (rows and their coupled
+ *               states, each once) in the table's slot order (unspecified);
+ *               *n_unique_out (host) receives |U|
+ *   row_count   [n_rows] int32: number of coupled x' of row i (the identity
+ *               group included, so x itself is one of them)
+ *   row_idx     [n_rows][row_cap] int32: index into U of each coupled x' of
+ *               row i, in group order (ascending X/Y mask)
+ *   row_hxx     [n_rows][row_cap] double: H_{x x'} of those x'
+ * Errors: NNQS_E_INVAL (arguments; cap_unique < |U|, *n_unique_out still
+ * set), NNQS_E_WORKSPACE; device-detected (nnqs_workspace_status): a row
+ * outside the sector (NNQS_E_SECTOR), a row with more than row_cap coupled
+ * states (NNQS_E_TABLE_FULL; its count is still written).  Synchronises once
+ * (to read |U|).  Workspace: nnqs_exact_coupled_workspace_size. */
+size_t nnqs_exact_coupled_workspace_size(const nnqs_ham *H, int64_t n_rows);
+nnqs_status nnqs_exact_coupled(const nnqs_ham *H, const uint64_t *lut, int64_t n_lut, int64_t row_begin,
+                               int64_t n_rows, int n_alpha, int n_beta, uint64_t *unique_out,
+                               int64_t cap_unique, int64_t *n_unique_out, int32_t *row_count,
+                               int32_t *row_idx, double *row_hxx, int64_t row_cap, void *workspace,
+                               size_t workspace_bytes, nnqs_stream stream);
 
 /* Coupled set of one row (parity and debugging): every x' = x ^ m over the
  * groups m that keep the sector, in group order, with H_{x x'} (host

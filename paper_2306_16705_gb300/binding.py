@@ -82,6 +82,12 @@ _SIGS = {
                                             ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_void_p]),
+    "nnqs_exact_coupled_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64]),
+    "nnqs_exact_coupled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
     "nnqs_coupled_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p]),
@@ -108,6 +114,8 @@ _SIGS = {
                                          ctypes.c_void_p]),
     "nnqs_profile_work": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "nnqs_launch_count": (ctypes.c_uint64, []),
+    "nnqs_measure_peaks_sink_size": (ctypes.c_size_t, []),
+    "nnqs_measure_peaks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "nnqs_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
@@ -347,6 +355,32 @@ def eloc(ham: Hamiltonian, lut: torch.Tensor, lut_logpsi=None, n_alpha=0, n_beta
     return out
 
 
+def exact_coupled(ham: Hamiltonian, lut: torch.Tensor, n_alpha, n_beta, row_cap, row_begin=0,
+                  n_rows=None, cap_unique=None, check=True):
+    """nnqs_exact_coupled: (unique [n_U, W] int64 bits, row_count [n_rows]
+    int32, row_idx [n_rows, row_cap] int32, row_hxx [n_rows, row_cap] f64)."""
+    n_lut = lut.shape[0]
+    W = ham.info()["n_words"]
+    if n_rows is None:
+        n_rows = n_lut - row_begin
+    if cap_unique is None:
+        cap_unique = max(1, n_rows * int(row_cap))
+    dev = lut.device
+    uniq = torch.empty((cap_unique, W), dtype=torch.int64, device=dev)
+    cnt = torch.empty(max(n_rows, 1), dtype=torch.int32, device=dev)
+    idx = torch.empty((max(n_rows, 1), max(int(row_cap), 1)), dtype=torch.int32, device=dev)
+    hxx = torch.empty((max(n_rows, 1), max(int(row_cap), 1)), dtype=torch.float64, device=dev)
+    nu = ctypes.c_int64(0)
+    nb = lib().nnqs_exact_coupled_workspace_size(ham.handle, n_rows)
+    ws = workspace(nb, dev)
+    _check(lib().nnqs_exact_coupled(ham.handle, _ptr(lut), n_lut, row_begin, n_rows, n_alpha, n_beta,
+                                    _ptr(uniq), cap_unique, ctypes.byref(nu), _ptr(cnt), _ptr(idx),
+                                    _ptr(hxx), int(row_cap), _ptr(ws), nb, _stream()))
+    if check:
+        workspace_status(ws)
+    return uniq[:nu.value], cnt[:n_rows], idx[:n_rows], hxx[:n_rows]
+
+
 def energy_stats(eloc_t: torch.Tensor, weights: torch.Tensor, check=True):
     """nnqs_energy_stats: float64 [4] = Re E, Im E, Var, sum w."""
     n = eloc_t.shape[0]
@@ -443,6 +477,17 @@ def profile_reset():
 
 def launch_count() -> int:
     return int(lib().nnqs_launch_count())
+
+
+def measure_peaks(device=None) -> dict:
+    """nnqs_measure_peaks: measured XOR+popcount tests/s, 32-bit integer
+    ops/s, FP64 and FP32 FMA flop/s of the current device."""
+    nb = lib().nnqs_measure_peaks_sink_size()
+    sink = workspace(nb, device)
+    out = (ctypes.c_double * 4)()
+    _check(lib().nnqs_measure_peaks(out, _ptr(sink), nb, _stream()))
+    return {"xor_popc64_per_s": out[0], "int32_ops_per_s": out[1], "fp64_flops": out[2],
+            "fp32_flops": out[3]}
 
 
 def profile() -> dict:

@@ -40,6 +40,30 @@ static nnqs_status reset_status(void *ws, cudaStream_t s) {
     return NNQS_OK;
 }
 
+// argument checks shared by the local-energy entry points
+nnqs_status eloc_args(const nnqs_ham *H, int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha,
+                             int n_beta, int mode) {
+    if (!H) return set_error(NNQS_E_INVAL, "null Hamiltonian");
+    if (!H->d_gxy) return set_error(NNQS_E_INVAL, "Hamiltonian built with nnqs_build_pauli_host has no device tables");
+    if (n_lut < 0 || n_rows < 0 || row_begin < 0 || row_begin + n_rows > n_lut)
+        return set_error(NNQS_E_INVAL, "rows out of range of the sample table");
+    if (n_lut >= (int64_t(1) << 31)) return set_error(NNQS_E_INVAL, "sample table larger than 2^31 rows");
+    const int n = H->n_spatial;
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > n || n_beta > n)
+        return set_error(NNQS_E_INVAL, "electron counts out of range");
+    if (H->n_qubits % 64 == 0 && n_alpha == n && n_beta == n)
+        return set_error(NNQS_E_UNSUPPORTED, "fully occupied 64/128-qubit sector (all-ones key is the empty marker)");
+    if (mode != NNQS_SA && mode != NNQS_EXACT) return set_error(NNQS_E_INVAL, "unknown mode");
+    return NNQS_OK;
+}
+
+nnqs_status eloc_flags(const nnqs_ham *H, int flags, int mode) {
+    if (flags < NNQS_SWEEP_AUTO || flags > NNQS_SWEEP_TERMS) return set_error(NNQS_E_INVAL, "unknown flags");
+    if (flags == NNQS_SWEEP_TERMS && mode == NNQS_SA && !H->d_txy)
+        return set_error(NNQS_E_INVAL, "NNQS_SWEEP_TERMS needs nnqs_ham_build_ungrouped first");
+    return NNQS_OK;
+}
+
 }  // namespace nnqs
 
 using namespace nnqs;
@@ -210,22 +234,6 @@ nnqs_status nnqs_coupled_host(const nnqs_ham *H, const uint64_t *x, int n_alpha,
 }
 
 // ---------------------------------------------------------------- local energy
-static nnqs_status eloc_args(const nnqs_ham *H, int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha,
-                             int n_beta, int mode) {
-    if (!H) return set_error(NNQS_E_INVAL, "null Hamiltonian");
-    if (!H->d_gxy) return set_error(NNQS_E_INVAL, "Hamiltonian built with nnqs_build_pauli_host has no device tables");
-    if (n_lut < 0 || n_rows < 0 || row_begin < 0 || row_begin + n_rows > n_lut)
-        return set_error(NNQS_E_INVAL, "rows out of range of the sample table");
-    if (n_lut >= (int64_t(1) << 31)) return set_error(NNQS_E_INVAL, "sample table larger than 2^31 rows");
-    const int n = H->n_spatial;
-    if (n_alpha < 0 || n_beta < 0 || n_alpha > n || n_beta > n)
-        return set_error(NNQS_E_INVAL, "electron counts out of range");
-    if (H->n_qubits % 64 == 0 && n_alpha == n && n_beta == n)
-        return set_error(NNQS_E_UNSUPPORTED, "fully occupied 64/128-qubit sector (all-ones key is the empty marker)");
-    if (mode != NNQS_SA && mode != NNQS_EXACT) return set_error(NNQS_E_INVAL, "unknown mode");
-    return NNQS_OK;
-}
-
 size_t nnqs_eloc_workspace_size(const nnqs_ham *H, const nnqs_model *M, int64_t n_lut, int64_t n_rows, int mode,
                                 int prec) {
     if (!H || n_lut < 0 || n_rows < 0) return 0;
@@ -238,9 +246,7 @@ nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *param
                       int n_beta, int mode, int prec, int flags, double *eloc_out, void *workspace,
                       size_t workspace_bytes, nnqs_stream stream) {
     NNQS_TRY(eloc_args(H, n_lut, row_begin, n_rows, n_alpha, n_beta, mode));
-    if (flags < NNQS_SWEEP_AUTO || flags > NNQS_SWEEP_TERMS) return set_error(NNQS_E_INVAL, "unknown flags");
-    if (flags == NNQS_SWEEP_TERMS && mode == NNQS_SA && !H->d_txy)
-        return set_error(NNQS_E_INVAL, "NNQS_SWEEP_TERMS needs nnqs_ham_build_ungrouped first");
+    NNQS_TRY(eloc_flags(H, flags, mode));
     if (n_rows > 0 && (!lut || !eloc_out)) return set_error(NNQS_E_INVAL, "null device pointer");
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == NNQS_SA) {
@@ -258,6 +264,30 @@ nnqs_status nnqs_eloc(const nnqs_ham *H, const nnqs_model *M, const float *param
     Arena a(workspace);
     DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
     return eloc_exact(H, M, params, lut, n_lut, row_begin, n_rows, n_alpha, n_beta, prec, eloc_out, a, st, s);
+}
+
+size_t nnqs_exact_coupled_workspace_size(const nnqs_ham *H, int64_t n_rows) {
+    if (!H || n_rows < 0) return 0;
+    return exact_coupled_workspace(H, n_rows);
+}
+
+nnqs_status nnqs_exact_coupled(const nnqs_ham *H, const uint64_t *lut, int64_t n_lut, int64_t row_begin,
+                               int64_t n_rows, int n_alpha, int n_beta, uint64_t *unique_out, int64_t cap_unique,
+                               int64_t *n_unique_out, int32_t *row_count, int32_t *row_idx, double *row_hxx,
+                               int64_t row_cap, void *workspace, size_t workspace_bytes, nnqs_stream stream) {
+    NNQS_TRY(eloc_args(H, n_lut, row_begin, n_rows, n_alpha, n_beta, NNQS_EXACT));
+    if (!n_unique_out) return set_error(NNQS_E_INVAL, "null n_unique_out");
+    *n_unique_out = 0;
+    if (cap_unique < 0 || row_cap < 0) return set_error(NNQS_E_INVAL, "negative capacity");
+    if (n_rows > 0 && (!lut || !unique_out || !row_count || (row_cap > 0 && (!row_idx || !row_hxx))))
+        return set_error(NNQS_E_INVAL, "null device pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    NNQS_TRY(check_ws(workspace, workspace_bytes, exact_coupled_workspace(H, n_rows)));
+    NNQS_TRY(reset_status(workspace, s));
+    Arena a(workspace);
+    DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
+    return exact_coupled(H, lut, row_begin, n_rows, n_alpha, n_beta, unique_out, cap_unique, n_unique_out, row_count,
+                         row_idx, row_hxx, row_cap, a, st, s);
 }
 
 // ---------------------------------------------------------------- statistics

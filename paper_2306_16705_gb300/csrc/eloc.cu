@@ -510,6 +510,16 @@ size_t eloc_sa_workspace(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int) 
     return best;
 }
 
+size_t eloc_sa_workspace_for(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags) {
+    Arena a(nullptr);
+    a.take<char>(kStatusBytes);
+    if (H->W == 1)
+        eloc_sa_impl<1>(H, nullptr, nullptr, n_lut, 0, n_rows, 0, 0, flags, nullptr, a, nullptr, nullptr);
+    else
+        eloc_sa_impl<2>(H, nullptr, nullptr, n_lut, 0, n_rows, 0, 0, flags, nullptr, a, nullptr, nullptr);
+    return a.used + 256;
+}
+
 nnqs_status eloc_sa(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp, int64_t n_lut,
                     int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int flags, double *out,
                     Arena &ws, DevStatus *status, cudaStream_t s) {
@@ -581,17 +591,11 @@ extern "C" nnqs_status nnqs_eloc_sa_noalloc(const nnqs_ham *H, const uint64_t *l
                                             int n_beta, int flags, double *eloc_out, int check,
                                             nnqs_stream stream) {
     using namespace nnqs;
-    if (!H || !H->d_gxy) return set_error(NNQS_E_INVAL, "null Hamiltonian or one without device tables");
-    if (n_lut < 0 || n_rows < 0 || row_begin < 0 || row_begin + n_rows > n_lut)
-        return set_error(NNQS_E_INVAL, "rows out of range of the sample table");
-    if (n_lut >= (int64_t(1) << 31)) return set_error(NNQS_E_INVAL, "sample table larger than 2^31 rows");
-    if (n_alpha < 0 || n_beta < 0 || n_alpha > H->n_spatial || n_beta > H->n_spatial)
-        return set_error(NNQS_E_INVAL, "electron counts out of range");
-    if (H->n_qubits % 64 == 0 && n_alpha == H->n_spatial && n_beta == H->n_spatial)
-        return set_error(NNQS_E_UNSUPPORTED, "fully occupied 64/128-qubit sector");
-    if (flags < NNQS_SWEEP_AUTO || flags > NNQS_SWEEP_PAIRS) return set_error(NNQS_E_INVAL, "unknown flags");
+    NNQS_TRY(eloc_args(H, n_lut, row_begin, n_rows, n_alpha, n_beta, NNQS_SA));
+    NNQS_TRY(eloc_flags(H, flags, NNQS_SA));
     if (n_rows > 0 && (!lut || !lut_logpsi || !eloc_out)) return set_error(NNQS_E_INVAL, "null device pointer");
-    const size_t need = eloc_sa_workspace(H, n_lut, n_rows, flags);
+    // sized by the sweep this call runs (AUTO resolved), not the largest one
+    const size_t need = eloc_sa_workspace_for(H, n_lut, n_rows, flags);
     if (need > kNoAllocScratchBytes)
         return set_error(NNQS_E_INVAL, "nnqs_eloc_sa_noalloc: this table needs " + std::to_string(need) +
                                            " bytes of scratch, above the fixed " +

@@ -112,9 +112,17 @@ nnqs_status build_pauli_host(int n_spatial, const double *h, const double *eri, 
 nnqs_status upload_ham(nnqs_ham *H);
 uint64_t hash_words(const uint64_t *k, int W);  // same mix as the device hash
 
+// abi.cpp: argument checks shared by the local-energy entry points
+nnqs_status eloc_args(const nnqs_ham *H, int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta,
+                      int mode);
+nnqs_status eloc_flags(const nnqs_ham *H, int flags, int mode);
+
 // eloc.cu
 int num_sms();  // SMs of the current device (152 if the query fails)
+// bytes for any sweep (the size query takes no flags)
 size_t eloc_sa_workspace(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags);
+// bytes for the sweep a call with `flags` runs (AUTO resolved)
+size_t eloc_sa_workspace_for(const nnqs_ham *H, int64_t n_lut, int64_t n_rows, int flags);
 nnqs_status eloc_sa(const nnqs_ham *H, const uint64_t *lut, const double *lut_lp, int64_t n_lut,
                     int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int flags,
                     double *out, Arena &ws, DevStatus *status, cudaStream_t s);

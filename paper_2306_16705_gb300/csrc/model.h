@@ -74,5 +74,11 @@ size_t eloc_exact_workspace(const nnqs_ham *H, const nnqs_model *M, int64_t n_lu
 nnqs_status eloc_exact(const nnqs_ham *H, const nnqs_model *M, const float *params, const uint64_t *lut,
                        int64_t n_lut, int64_t row_begin, int64_t n_rows, int n_alpha, int n_beta, int prec,
                        double *out, Arena &ws, DevStatus *st, cudaStream_t s);
+// the coupled set exact mode builds, exported (nnqs_exact_coupled)
+size_t exact_coupled_workspace(const nnqs_ham *H, int64_t n_rows);
+nnqs_status exact_coupled(const nnqs_ham *H, const uint64_t *lut, int64_t row_begin, int64_t n_rows, int n_alpha,
+                          int n_beta, uint64_t *unique_out, int64_t cap_unique, int64_t *n_unique_out,
+                          int32_t *row_count, int32_t *row_idx, double *row_hxx, int64_t row_cap, Arena &ws,
+                          DevStatus *st, cudaStream_t s);
 
 }  // namespace nnqs

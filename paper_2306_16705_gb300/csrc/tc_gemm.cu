@@ -435,7 +435,9 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     // algorithmic bytes: X in, the BF16 weights (and their low parts), Y out,
     // plus the activation output or the residual read
     const bool two = epi == tc::EPI_GELU || epi == tc::EPI_RELU || epi == tc::EPI_RESID;
-    note_work("k_tc_gemm", (w.split ? 6.0 : 2.0) * double(rows) * double(g.N) * double(in),
+    // flops: the method's product only (the split mode issues three BF16
+    // products for it)
+    note_work("k_tc_gemm", 2.0 * double(rows) * double(g.N) * double(in),
               4.0 * double(rows) * in + (w.split ? 4.0 : 2.0) * double(g.N) * g.Kpad +
                   (two ? 8.0 : 4.0) * double(rows) * g.N);
     // the warp-specialised kernel only where it measured faster: the split

@@ -40,6 +40,12 @@ class EnergyFunction(torch.autograd.Function):
         return grad_out * grad, None, None, None, None, None
 
 
+def sample_seed(seed: int, it: int) -> int:
+    """Sampler seed of VMC iteration ``it`` for a run seeded ``seed``: the
+    Philox stream of each (run, iteration) pair is distinct."""
+    return int(seed) * 1_000_003 + int(it)
+
+
 def paper_n_samples(it: int, ns0: int = 10 ** 5, ns_max: int = 10 ** 12, first: int = 100,
                     every: int = 100) -> int:
     """N_s of VMC iteration ``it`` (0-based) under the Sec. 4.1 recipe: ns0
@@ -96,7 +102,7 @@ class VMC:
         return ns if self.ns_hold is None else min(ns, self.ns_hold)
 
     def sample(self, seed=None):
-        seed = self.seed * 1_000_003 + self.t if seed is None else seed
+        seed = sample_seed(self.seed, self.t) if seed is None else seed
         nb = B.lib().nnqs_sample_workspace_size(self.model.handle, self.max_unique, self.prec, 0)
         if self._ws_sample is None or self._ws_sample.numel() < nb:
             self._ws_sample = B.workspace(nb, self.params.device)

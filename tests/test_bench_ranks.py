@@ -39,6 +39,30 @@ def test_replica_aggregation_two_ranks():
         assert nu == 3000  # sum over ranks
 
 
+def _seed_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_2306_16705_gb300.vmc import sample_seed
+
+    # the sampler seeds this rank's replica uses in its first 50 VMC steps
+    mine = torch.tensor([sample_seed(bench.replica_seed(rank), t) for t in range(50)], dtype=torch.int64)
+    got = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(got, mine)
+    out[rank] = [g.tolist() for g in got]
+    dist.destroy_process_group()
+
+
 def test_replica_seeds_differ():
-    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")).read()
-    assert "seed=1000 + rank" in src
+    """Two gloo ranks exchange the sampler seeds of their first 50 steps: no
+    seed is used by both ranks (so their Philox streams, and the samples
+    drawn from them, differ; tests/test_gpu_vmc.py draws with both)."""
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_seed_worker, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+    a, b = out[0]
+    assert out[1] == [a, b]
+    assert len(set(a)) == 50 and len(set(b)) == 50 and not set(a) & set(b)

@@ -5,7 +5,13 @@ FP32 paths, including chunked batches and out-of-sector inputs.
 Tolerances: FP64 path 1e-10 relative (different summation order only);
 FP32 path 2e-4 absolute on log|psi| and phase (single rounding over ~10^2
 accumulated terms per output); gradients relative to the largest entry of
-each tensor: 1e-9 (FP64), 2e-3 (FP32)."""
+each tensor: 1e-9 (FP64), 2e-3 (FP32), and 4e-2 for the BF16 reverse mode of
+NNQS_MIXED and NNQS_BF16X3: every GEMM of the reverse mode rounds both
+operands to BF16 (relative error 2^-9 each), and a weight gradient of layer l
+is a product chain through the 4 - l layers above it, two rounded operands
+per GEMM and three GEMMs per layer on the path, so about 2 x 3 x 4 x 2^-9
+= 0.047 of the tensor's scale in the worst (first) layer; 4e-2 is that
+figure rounded down."""
 import numpy as np
 import pytest
 import torch
@@ -92,8 +98,11 @@ def test_out_of_sector_reports_status():
     assert out[4, 0] == -np.inf and np.all(np.isfinite(np.delete(out[:, 0], 4)))
 
 
+GRAD_TOL = {B.FP64: 1e-9, B.FP32: 2e-3, B.MIXED: 4e-2, B.BF16X3: 4e-2}
+
+
 @pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
-@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.MIXED, B.BF16X3])
 def test_backward_matches_oracle(case, prec):
     name, N, na, nb, d, L, H, ns = case
     ns = min(ns, 160)
@@ -105,11 +114,14 @@ def test_backward_matches_oracle(case, prec):
     G = m.unpack(g, params)
     _, _, cache = OA.forward(params, I.unpack_bits(x, N), na, nb, H, want_cache=True)
     R = OA.backward(cache, seed[:, 0], seed[:, 1])
-    tol = 1e-9 if prec == B.FP64 else 2e-3
+    tol = GRAD_TOL[prec]
+    worst = 0.0
     for k in params:
         ref = R[k]
         err = np.abs(G[k] - ref).max()
+        worst = max(worst, err / max(1e-3, np.abs(ref).max()))
         assert err <= tol * max(1e-3, np.abs(ref).max()), (k, err, np.abs(ref).max())
+    print(f"backward {name} prec={prec}: largest error / tensor scale = {worst:.3e}")
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])

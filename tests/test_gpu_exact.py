@@ -1,0 +1,225 @@
+"""Exact-mode local energy (Eq. Eloc over every coupled x', Sec. 3.4 (2)) on
+the GPU against the FP64 oracle, through the C ABI.
+
+1. The coupled set the GPU builds (device hash insert + dedup + numbering,
+   exported by nnqs_exact_coupled) is compared bit for bit with the oracle's
+   row of H (oracle.hamiltonian.coupled): per row the set of x', and the
+   union over rows.  H_{x x'} agrees within the rounding bound of two
+   recursive FP64 sums over the group's strings, 2 (g - 1) u sum_t |c_t|,
+   which lies far below 2 min_t |c_t| (>= 2e-12 after the drop rule): a
+   single wrong sign (-1)^{popc(x & yz_t)} would fail it.
+2. Exact mode with the ansatz in reduced precision (FP32, MIXED, BF16X3).
+   With delta(x) the complex error of log psi(x) of that precision,
+   E_gpu(x) - E(x) = sum_x' H_{x x'} psi'/psi (e^{delta' - delta} - 1), so
+   |E_gpu(x) - E(x)| <= S(x) (e^{2 eps} - 1) with S(x) = sum_x' |H_{x x'}
+   psi'/psi| and eps the largest |delta| over the row's coupled states.  The
+   test measures eps from nnqs_logpsi of the same precision against the
+   oracle forward, checks it against the precision's own log psi bound
+   (FP32 2e-4, MIXED 2e-2, BF16X3 1e-3 of max(1, |log psi|), as in the ansatz
+   tests), and then holds every row of exact mode to the bound above plus
+   the FP64 gate 1e-10 max(1, S(x))."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ansatz as OA
+from oracle import hamiltonian as OH
+from paper_2306_16705_gb300 import binding as B
+from paper_2306_16705_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+LP_TOL = {B.FP32: 2e-4, B.MIXED: 2e-2, B.BF16X3: 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    B.lib()
+
+
+def key_sort(a):
+    """Rows of a [k, W] uint64 array in ascending key order (top word most
+    significant), as the oracle returns them."""
+    W = a.shape[1]
+    return a[np.lexsort([a[:, w] for w in range(W)])]
+
+
+def group_tables(strings):
+    """X/Y mask -> (string count g, sum_t |c_t|) of its group."""
+    xy, yz, coef = strings
+    out = {}
+    for m, c in zip(map(tuple, xy.tolist()), coef):
+        g, s = out.get(m, (0, 0.0))
+        out[m] = (g + 1, s + abs(c))
+    return out
+
+
+def check_coupled_set(ham, strings, rows, na, nb):
+    xy, yz, coef = strings
+    W = rows.shape[1]
+    ref = [OH.coupled(xy, yz, coef, x, na, nb) for x in rows]
+    cap = max(len(r[0]) for r in ref)
+    Ud, cnt, idx, hxx = B.exact_coupled(ham, B.to_device_bits(rows), na, nb, row_cap=cap)
+    Uh = B.from_device_bits(Ud)
+    cnt, idx, hxx = cnt.cpu().numpy(), idx.cpu().numpy(), hxx.cpu().numpy()
+    # the deduplicated set: distinct keys, equal to the union of the rows'
+    # coupled sets (each row is in its own set through the identity group)
+    assert len({tuple(r) for r in Uh.tolist()}) == len(Uh)
+    want = set(map(tuple, rows.tolist()))
+    for xs, _ in ref:
+        want |= set(map(tuple, xs.tolist()))
+    assert {tuple(r) for r in Uh.tolist()} == want
+    groups = group_tables(strings)
+    min_c = np.abs(coef).min()
+    for i, (xs, hs) in enumerate(ref):
+        k = int(cnt[i])
+        assert k == len(xs), (i, k, len(xs))
+        assert np.all((idx[i, :k] >= 0) & (idx[i, :k] < len(Uh)))
+        got = Uh[idx[i, :k]]
+        order = np.lexsort([got[:, w] for w in range(W)])
+        assert np.array_equal(got[order], xs)  # bit-exact set
+        hg = hxx[i, :k][order]
+        masks = xs ^ rows[i][None, :]
+        for j in range(k):
+            g, sabs = groups[tuple(masks[j].tolist())]
+            tol = 2 * max(g - 1, 1) * U * sabs
+            assert tol < 2 * min_c  # a flipped sign would exceed the bound
+            assert abs(hg[j] - hs[j]) <= tol, (i, j, hg[j], hs[j], tol)
+    return len(Uh)
+
+
+def test_coupled_set_bit_exact_n12_all_rows():
+    wl = I.WORKLOADS["n12"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    rows = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    nU = check_coupled_set(ham, OH.build(h, eri), rows, wl.n_alpha, wl.n_beta)
+    assert nU == len(rows)  # the sector is closed under H
+
+
+def test_coupled_set_bit_exact_n40_64_rows():
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    strings = OH.build(h, eri)
+    # 48 clustered rows (coupled sets overlap: the dedup is exercised) and
+    # 16 uniform ones
+    rows = np.concatenate([
+        I.clustered_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 48, seed=61, n_centers=2),
+        I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 16, seed=62)])
+    rows = np.unique(rows, axis=0)
+    nU = check_coupled_set(ham, strings, rows, wl.n_alpha, wl.n_beta)
+    # C_x = 1 + 2 n_o n_v + 2 C(n_o,2) C(n_v,2) + (n_o n_v)^2 = 14,251 per row
+    assert nU < len(rows) * 14251
+
+
+def test_coupled_set_bit_exact_two_words():
+    """70 qubits: interacting orbitals on both sides of qubit 64."""
+    n = 35
+    act = [0, 9, 30, 31, 32, 34]
+    h0, eri0 = I.integrals(len(act), 5, 4)
+    h = np.zeros((n, n))
+    eri = np.zeros((n, n, n, n))
+    h[np.ix_(act, act)] = h0
+    eri[np.ix_(act, act, act, act)] = eri0
+    ham = B.build_pauli(h, eri)
+    rows = I.clustered_sector_samples(n, 3, 2, 120, seed=3, n_centers=3, orbitals=act)
+    check_coupled_set(ham, OH.build(h, eri), rows, 3, 2)
+
+
+def test_coupled_set_reports_small_row_cap():
+    wl = I.WORKLOADS["n12"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    rows = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)[:10].copy()
+    with pytest.raises(B.NNQSError) as e:
+        B.exact_coupled(ham, B.to_device_bits(rows), wl.n_alpha, wl.n_beta, row_cap=5)
+    assert e.value.status == B.E_TABLE_FULL
+    bad = rows.copy()
+    bad[3, 0] ^= np.uint64(1)
+    with pytest.raises(B.NNQSError) as e:
+        B.exact_coupled(ham, B.to_device_bits(bad), wl.n_alpha, wl.n_beta, row_cap=200)
+    assert e.value.status == B.E_SECTOR
+
+
+def model_for(wl, seed=7, std=0.2):
+    params = I.ansatz_params(wl.n_qubits, wl.d_model, wl.n_layers, seed, std=std, bias_std=0.1,
+                             phase_std=0.1)
+    m = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+    return m, params, m.pack(params)
+
+
+def exact_reduced(wl, ham, strings, rows, prec, seed):
+    m, params, flat = model_for(wl, seed=seed)
+    xy, yz, coef = strings
+    na, nb = wl.n_alpha, wl.n_beta
+    ref_rows = [OH.coupled(xy, yz, coef, x, na, nb) for x in rows]
+    states = np.unique(np.concatenate([rows] + [xs for xs, _ in ref_rows]), axis=0)
+    la, ph = OA.forward(params, I.unpack_bits(states, wl.n_qubits), na, nb, wl.n_heads)
+    lp_ref = np.stack([la, ph], 1)
+    lp_gpu = B.logpsi(m, flat, B.to_device_bits(states), prec).cpu().numpy()
+    delta = np.hypot(lp_gpu[:, 0] - lp_ref[:, 0], lp_gpu[:, 1] - lp_ref[:, 1])
+    scale = max(1.0, np.abs(lp_ref).max())
+    assert delta.max() <= LP_TOL[prec] * scale, (delta.max(), scale)
+    pos = {tuple(s): i for i, s in enumerate(states.tolist())}
+    got = B.eloc(ham, B.to_device_bits(rows), None, na, nb, mode=B.EXACT, model=m, params=flat,
+                 prec=prec).cpu().numpy()
+    got = got[:, 0] + 1j * got[:, 1]
+    worst = 0.0
+    for i, (xs, hs) in enumerate(ref_rows):
+        ix = pos[tuple(rows[i].tolist())]
+        jj = np.array([pos[tuple(v)] for v in xs.tolist()])
+        r = np.exp(lp_ref[jj, 0] - lp_ref[ix, 0] + 1j * (lp_ref[jj, 1] - lp_ref[ix, 1]))
+        e_ref = np.sum(hs * r)
+        S = np.sum(np.abs(hs * r))
+        eps = max(delta[ix], delta[jj].max())
+        bound = S * np.expm1(2 * eps) + 1e-10 * max(1.0, S)
+        err = abs(got[i] - e_ref)
+        assert err <= bound, (i, err, bound, eps, S)
+        worst = max(worst, err / max(1.0, S))
+    return worst
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.MIXED, B.BF16X3])
+def test_exact_mode_reduced_precision_n12(prec):
+    """Every row of the 400-state sector (its coupled sets stay inside it)."""
+    wl = I.WORKLOADS["n12"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    rows = I.sector_states(wl.n_spatial, wl.n_alpha, wl.n_beta)
+    exact_reduced(wl, ham, OH.build(h, eri), rows, prec, seed=31)
+
+
+@pytest.mark.parametrize("prec", [B.MIXED, B.BF16X3])
+def test_exact_mode_tensor_cores_n40_window(prec):
+    """A window of three 40-qubit rows: 14,251 coupled states each, all
+    through the tensor-core forward of the precision."""
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    rows = I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, 3, seed=63)
+    exact_reduced(wl, ham, OH.build(h, eri), rows, prec, seed=32)
+
+
+def test_exact_mode_bf16x3_against_fp64_gpu_n40():
+    """128 rows at 40 qubits (about 1.8 M coupled states): the BF16X3 exact
+    local energies against the FP64 exact path (itself held to the oracle
+    within 1e-10), and the weighted energy within the 1e-6 Ha gate."""
+    wl = I.WORKLOADS["n40"]
+    h, eri = I.workload_integrals(wl)
+    ham = B.build_pauli(h, eri)
+    m = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+    flat = m.pack(I.workload_params(wl))
+    xs, w = B.sample(m, flat, 16384, seed=77, max_unique=1 << 15, prec=B.BF16X3)
+    rows = xs[:128].contiguous()
+    w = w[:128].double()
+    e64 = B.eloc(ham, rows, None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=m, params=flat, prec=B.FP64)
+    e3 = B.eloc(ham, rows, None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=m, params=flat, prec=B.BF16X3)
+    E64 = float((w * e64[:, 0]).sum() / w.sum())
+    E3 = float((w * e3[:, 0]).sum() / w.sum())
+    assert abs(E3 - E64) <= 1e-6, (E3, E64)
+    d = (e3 - e64).abs().max().item()
+    assert d <= 1e-4 * max(1.0, e64.abs().max().item()), d
