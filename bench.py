@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "mixed", "fp32", "fp64"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "mixed", "fp32", "fp64", "fp8"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (default steps/2, min 2)")
@@ -375,7 +375,7 @@ def run_exact_side_line(ham, model, wl, params, x, prec, n_rows, peaks, tflops_p
         "stage_ms": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         "max_abs_diff_vs_fp64_first64": d,
         "max_rel_diff_vs_fp64_first64": d / max(1.0, e64.abs().max().item()),
-        "note": "prec " + {B.BF16X3: "bf16x3", B.MIXED: "mixed", B.FP32: "fp32", B.FP64: "fp64"}[prec] +
+        "note": "prec " + {B.BF16X3: "bf16x3", B.MIXED: "mixed", B.FP32: "fp32", B.FP64: "fp64", B.FP8: "fp8"}[prec] +
                 "; forward FLOPs = unique coupled states x method FLOPs per sample"}
 
 
@@ -423,7 +423,6 @@ def run_n120_side_line(steps, warmup, peaks, clocks_on, local):
         params.copy_(p0)
         step(i, [torch.cuda.Event(enable_timing=True) for _ in range(3)])
     torch.cuda.synchronize()
-    B.profile_reset()
     ts, stages, nus = [], {"sample": 0.0, "energy_grad": 0.0, "adam": 0.0}, []
     with Clocks(local, clocks_on) as clk:
         for i in range(steps):
@@ -442,6 +441,8 @@ def run_n120_side_line(steps, warmup, peaks, clocks_on, local):
             stages["adam"] += mk[2].elapsed_time(mk[3])
             nus.append(nu)
     # one more step with every launch timed, for the per-kernel split
+    torch.cuda.synchronize()
+    B.profile_reset()
     B.profile_enable(True)
     params.copy_(p0)
     step(steps, [torch.cuda.Event(enable_timing=True) for _ in range(3)])
@@ -534,7 +535,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.lib()
-    precs = {"bf16x3": B.BF16X3, "mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64}
+    precs = {"bf16x3": B.BF16X3, "mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64, "fp8": B.FP8}
     prec = precs[args.prec]
     wl = I.WORKLOADS[WORKLOAD]
     h, eri = I.workload_integrals(wl)
@@ -675,6 +676,7 @@ def run_ours(args):
         "dtype": {"bf16x3": "bf16 hi+lo split operands (forward), bf16 (reverse mode), f32 accumulate / "
                             "f64 local energy",
                   "fp32": "f32 ansatz / f64 local energy", "mixed": "bf16+f32 ansatz / f64 local energy",
+                  "fp8": "e4m3 (forward), bf16 (reverse mode), f32 accumulate / f64 local energy",
                   "fp64": "f64"}[args.prec],
         "data": "synthetic (random integrals seed 1 rank 16; random-init ansatz)",
         "config": {"workload": f"n40: 40 spin orbitals, 20 electrons, N_s={args.n_samples}, "
@@ -710,7 +712,7 @@ def run_ours(args):
                               "energy_diff_by_prec_ha": {k: abs(v - e["fp64"]) for k, v in e.items() if k != "fp64"}}
         # the other fast paths' step times
         others = {}
-        for k in ("bf16x3", "mixed", "fp32"):
+        for k in ("bf16x3", "mixed", "fp32", "fp8"):
             if k == args.prec:
                 continue
             vo = make(precs[k])

@@ -73,9 +73,14 @@ enum { NNQS_SA = 0, NNQS_EXACT = 1 };
  * NNQS_BF16X3 = as NNQS_MIXED, but every forward linear layer splits its
  * operands into high and low BF16 parts (x = x_h + x_l, x_h = bf16(x)) and
  * sums three tensor-core products x_h w_h + x_h w_l + x_l w_h, so log psi
- * carries about 16 operand bits instead of 8 (the reverse mode stays BF16).
+ * carries about 16 operand bits instead of 8 (the reverse mode stays BF16);
+ * NNQS_FP8 = every forward linear layer of log psi on tcgen05 with E4M3
+ * operands (kind::f8f6f4, FP32 accumulation): activations unscaled, each
+ * weight row scaled by a power of two that brings its largest entry into
+ * (224, 448] and divided out of the accumulator; the reverse mode and the
+ * sampler's conditionals use BF16 operands as NNQS_MIXED does.
  * Local-energy ratios, sums and statistics are FP64 in every mode. */
-enum { NNQS_FP64 = 0, NNQS_MIXED = 1, NNQS_FP32 = 2, NNQS_BF16X3 = 3 };
+enum { NNQS_FP64 = 0, NNQS_MIXED = 1, NNQS_FP32 = 2, NNQS_BF16X3 = 3, NNQS_FP8 = 4 };
 
 /* nnqs_eloc flags: choice of the sample-aware sweep.  GROUPS walks the
  * X/Y-mask groups for every sample (Alg. 2); PAIRS walks sample pairs and

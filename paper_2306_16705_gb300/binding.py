@@ -20,7 +20,7 @@ _lib = None
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TABLE_FULL, E_TIMEOUT, E_SECTOR, E_NONFINITE, E_UNSUPPORTED, \
     E_DUPLICATE, E_WORKSPACE = range(11)
 SA, EXACT = 0, 1
-FP64, MIXED, FP32, BF16X3 = 0, 1, 2, 3
+FP64, MIXED, FP32, BF16X3, FP8 = 0, 1, 2, 3, 4
 SWEEP_AUTO, SWEEP_GROUPS, SWEEP_PAIRS, SWEEP_TERMS = 0, 1, 2, 3
 
 _STATUS_NAMES = {0: "NNQS_OK", 1: "NNQS_E_INVAL", 2: "NNQS_E_NOMEM", 3: "NNQS_E_CUDA",

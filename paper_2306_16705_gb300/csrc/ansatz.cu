@@ -3120,6 +3120,7 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
     if (tensor) tc_weights_take(M, ws, &tcw);
     tcw.st = st;
     tcw.split = tcm == 2;
+    tcw.fp8 = tcm == 3;
     const int64_t C = chunk_for(M, n, sizeof(R), false);
     Acts<R> A;
     take_acts<R>(M, C, false, ws, A);
@@ -3144,6 +3145,7 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
     if (tensor) tc_weights_take(M, ws, &tcw);
     tcw.st = st;
     tcw.split = tcm == 2;
+    tcw.fp8 = tcm == 3;
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
     Acts<R> A;
     take_acts<R>(M, C, true, ws, A);
@@ -3179,6 +3181,7 @@ nnqs_status fwd_bwd_impl(const nnqs_model *M, const float *params, const uint64_
     if (tensor) tc_weights_take(M, ws, &tcw);
     tcw.st = st;
     tcw.split = tcm == 2;
+    tcw.fp8 = tcm == 3;
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
     if (C < n) return set_error(NNQS_E_INVAL, "fused forward/backward needs one chunk");
     Acts<R> A;
@@ -3400,6 +3403,7 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
         c->params = pr;
         if (c->tensor) tc_weights_take(M, ws, &c->tcw);
         c->tcw.split = tc_mode(prec) == 2;
+        c->tcw.fp8 = false;  // NNQS_FP8 samples with BF16 operands (as NNQS_MIXED)
         c->C = chunk_for(M, std::max<int64_t>(max_prefixes, 1), sizeof(float), false);
         take_acts<float>(M, c->C, false, ws, c->Af);
         NNQS_LAUNCH("k_convert_params", s, k_convert_params<float><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));

@@ -34,9 +34,12 @@ namespace nnqs {
 
 ParamLayout make_layout(const nnqs_model_cfg &c);
 
-inline bool prec_valid(int p) { return p == NNQS_FP64 || p == NNQS_MIXED || p == NNQS_FP32 || p == NNQS_BF16X3; }
-// tensor-core use of a precision: 0 none, 1 BF16 operands, 2 split BF16 operands in the forward layers
-inline int tc_mode(int p) { return p == NNQS_MIXED ? 1 : p == NNQS_BF16X3 ? 2 : 0; }
+inline bool prec_valid(int p) {
+    return p == NNQS_FP64 || p == NNQS_MIXED || p == NNQS_FP32 || p == NNQS_BF16X3 || p == NNQS_FP8;
+}
+// tensor-core use of a precision: 0 none, 1 BF16 operands, 2 split BF16
+// operands in the forward layers, 3 E4M3 operands in the forward layers
+inline int tc_mode(int p) { return p == NNQS_MIXED ? 1 : p == NNQS_BF16X3 ? 2 : p == NNQS_FP8 ? 3 : 0; }
 
 // ansatz.cu
 size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward);

@@ -2,6 +2,7 @@
 // BF16 copies of the weight matrices (K padded to 64 with zeros) and their
 // low parts, and the launch of tc::k_tc_gemm.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +52,47 @@ __global__ void k_to_bf16_all(const float *__restrict__ params, ConvTab tab) {
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         jb.dst[i] = hi;
         if (jb.dst_lo) jb.dst_lo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+// E4M3 copy of one forward matrix per blockIdx.y (slot job), one warp per
+// row: s_n = 2^k with k the largest integer such that max_k |W[n][k]| 2^k <=
+// 448 (1 for an all-zero row), dst[n][c] = e4m3(W[n][c] s_n) (zero past K),
+// inv[n] = 2^-k
+struct Fp8Job {
+    int64_t src, rows, cols, pad;
+    uint8_t *dst;
+    float *inv;
+};
+struct Fp8Tab {
+    int n;
+    Fp8Job j[64];
+};
+
+__global__ void k_to_fp8_all(const float *__restrict__ params, Fp8Tab tab) {
+    const Fp8Job jb = tab.j[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < jb.rows; r += warps) {
+        const float *w = params + jb.src + r * jb.cols;
+        float amax = 0.f;
+        for (int64_t c = lane; c < jb.cols; c += 32) amax = fmaxf(amax, fabsf(w[c]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        int k = 0;
+        if (amax > 0.f && isfinite(amax)) {
+            int e;
+            frexpf(448.f / amax, &e);  // 448 / amax = f 2^e with f in [0.5, 1)
+            k = e - 1;                 // 2^k <= 448 / amax < 2^(k+1)
+            for (int it = 0; it < 4 && ldexpf(amax, k) > 448.f; ++it) --k;  // rounding of the quotient
+            k = max(-120, min(120, k));  // 2^k and 2^-k stay finite normal floats
+        }
+        const float sc = ldexpf(1.f, k);
+        for (int64_t c = lane; c < jb.pad; c += 32) {
+            const float v = c < jb.cols ? w[c] * sc : 0.f;
+            jb.dst[r * jb.pad + c] = (uint8_t)(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+        }
+        if (lane == 0) jb.inv[r] = ldexpf(1.f, -k);
     }
 }
 
@@ -184,18 +226,18 @@ void slot_shapes(const nnqs_model *M, int slot, int64_t &N, int64_t &K, int64_t 
     }
 }
 
-bool g_attr_set[2][2][tc::kNumEpi] = {};
+bool g_attr_set[2][2][2][tc::kNumEpi] = {};
 
-template <int EPI, bool TRANS = false, bool SPLIT = false>
+template <int EPI, bool TRANS = false, bool SPLIT = false, bool FP8 = false>
 nnqs_status launch(const tc::Args &g, int64_t n_tiles_n, cudaStream_t s, int64_t splits = 1) {
     constexpr int smem = SPLIT ? tc::kSmemBytesSplit : tc::kSmemBytes;
-    if (!g_attr_set[TRANS][SPLIT][EPI]) {
-        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI, TRANS, SPLIT>,
+    if (!g_attr_set[TRANS][SPLIT][FP8][EPI]) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm<EPI, TRANS, SPLIT, FP8>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        g_attr_set[TRANS][SPLIT][EPI] = true;
+        g_attr_set[TRANS][SPLIT][FP8][EPI] = true;
     }
     dim3 grid((unsigned)n_tiles_n, (unsigned)((g.M + tc::kTileM - 1) / tc::kTileM), (unsigned)splits);
-    NNQS_LAUNCH("k_tc_gemm", s, (tc::k_tc_gemm<EPI, TRANS, SPLIT><<<grid, tc::kThreads, smem, s>>>(g)));
+    NNQS_LAUNCH("k_tc_gemm", s, (tc::k_tc_gemm<EPI, TRANS, SPLIT, FP8><<<grid, tc::kThreads, smem, s>>>(g)));
     return NNQS_OK;
 }
 
@@ -295,6 +337,17 @@ void tc_weights_take(const nnqs_model *M, Arena &a, TcWeights *w) {
         tiles += 2 * int64_t(t.rows[sl]) * t.pcols[sl];
     }
     t.tiles = a.take<__nv_bfloat16>(size_t(std::max<int64_t>(tiles, 1)));
+    int64_t b8 = 0, s8 = 0;
+    for (int sl = 0; sl < n_slots; ++sl) {
+        if (sl / 4 == M->L && sl % 4 != 0) continue;
+        t.off8[sl] = b8;
+        t.soff8[sl] = s8;
+        t.pcols8[sl] = (int32_t)((t.cols[sl] + 127) / 128 * 128);
+        b8 += int64_t(t.rows[sl]) * t.pcols8[sl];
+        s8 += t.rows[sl];
+    }
+    t.w8 = a.take<uint8_t>(size_t(std::max<int64_t>(b8, 16)));
+    t.w8inv = a.take<float>(size_t(std::max<int64_t>(s8, 1)));
 }
 
 nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeights &w, cudaStream_t s) {
@@ -317,7 +370,19 @@ nnqs_status tc_weights_prepare(const nnqs_model *M, const float *params, TcWeigh
         if (sl < 4 * M->L)
             tab.j[tab.n++] = ConvJob{w.src[sl], N, K, Kp, tl + w.tile_off[sl], tl + w.tile_off[sl] + N * Kp, 2};
     }
-    return flush();
+    NNQS_TRY(flush());
+    if (!w.fp8) return NNQS_OK;
+    Fp8Tab t8{};
+    for (int sl = 0; sl < w.n_slots; ++sl) {
+        if (sl / 4 == M->L && sl % 4 != 0) continue;
+        t8.j[t8.n++] = Fp8Job{w.src[sl], w.rows[sl], w.cols[sl], w.pcols8[sl], w.w8 + w.off8[sl], w.w8inv + w.soff8[sl]};
+        if (t8.n == 64 || sl + 1 == w.n_slots) {
+            NNQS_LAUNCH("k_to_bf16", s, k_to_fp8_all<<<dim3(16, (unsigned)t8.n), 256, 0, s>>>(params, t8));
+            t8.n = 0;
+        }
+    }
+    if (t8.n > 0) NNQS_LAUNCH("k_to_bf16", s, k_to_fp8_all<<<dim3(16, (unsigned)t8.n), 256, 0, s>>>(params, t8));
+    return NNQS_OK;
 }
 
 nnqs_status tc_linear_dx(cudaStream_t s, const TcWeights &w, int slot, const float *dY, int64_t rows, float *dX,
@@ -440,6 +505,18 @@ nnqs_status tc_linear_fwd_ld<float>(cudaStream_t s, const TcWeights &w, int slot
     note_work("k_tc_gemm", 2.0 * double(rows) * double(g.N) * double(in),
               4.0 * double(rows) * in + (w.split ? 4.0 : 2.0) * double(g.N) * g.Kpad +
                   (two ? 8.0 : 4.0) * double(rows) * g.N);
+    if (w.fp8) {
+        g.W8 = w.w8 + w.off8[slot];
+        g.Kpad8 = w.pcols8[slot];
+        g.wsinv = w.w8inv + w.soff8[slot];
+        switch (epi) {
+            case tc::EPI_STORE: return launch<tc::EPI_STORE, false, false, true>(g, ntn, s);
+            case tc::EPI_GELU: return launch<tc::EPI_GELU, false, false, true>(g, ntn, s);
+            case tc::EPI_RELU: return launch<tc::EPI_RELU, false, false, true>(g, ntn, s);
+            case tc::EPI_RESID: return launch<tc::EPI_RESID, false, false, true>(g, ntn, s);
+            default: return set_error(NNQS_E_INVAL, "tensor-core layer: bad epilogue");
+        }
+    }
     // the warp-specialised kernel only where it measured faster: the split
     // forward with a plain store (the qkv layer: 412 -> 320 us for the four
     // launches of a 40-qubit step); with two outputs or a residual its one

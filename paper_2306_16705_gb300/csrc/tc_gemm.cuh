@@ -16,6 +16,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,6 +62,21 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
 __host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3 (format 0), both K-major
+__host__ __device__ __forceinline__ uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// one M x N x 32 step with E4M3 operands (32 bytes of a 128-byte K row)
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -129,6 +145,19 @@ __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
     return make_uint4(p[0], p[1], p[2], p[3]);
 }
 
+// 16 FP32 values -> 16 E4M3 bytes in element order (round to nearest,
+// saturating to +-448)
+__device__ __forceinline__ uint4 pack16_e4m3(const float (&v)[16]) {
+    uint32_t p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t a = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * q], v[4 * q + 1]), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t b = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * q + 2], v[4 * q + 3]), __NV_SATFINITE, __NV_E4M3);
+        p[q] = (a & 0xFFFFu) | (b << 16);
+    }
+    return make_uint4(p[0], p[1], p[2], p[3]);
+}
+
 struct Args {
     const float *X;        // [M][ldx], K valid columns
     int64_t ldx;
@@ -162,6 +191,11 @@ struct Args {
     int p_ntiles;
     int p_wg_epi;
     CUtensorMap tmX;
+    // FP8 (E4M3) forward: W8 [Npad][Kpad8] bytes, each output row n scaled by
+    // a power of two s_n, and wsinv[n] = 1 / s_n applied to the accumulator
+    const uint8_t *W8;
+    int64_t Kpad8;
+    const float *wsinv;
 };
 
 // TMA: one 32-column x 128-row FP32 box between shared memory (1024-byte
@@ -200,9 +234,14 @@ __device__ __forceinline__ void bulk_wait_read_n() {
 //   (Xh = bf16(X), Xl = bf16(X - Xh)) and Y = Xh Wh + Xh Wl + Xl Wh: three
 //   MMAs per K step, operands good to about 16 bits instead of 8, the same
 //   global traffic.  Three CTAs per SM (64 KB of operand buffers each).
-template <int EPI, bool TRANS, bool SPLIT = false>
+// FP8 (TRANS = false, SPLIT = false only): X and W in E4M3, K chunks of 128
+//   (one 128-byte row per operand row), kind::f8f6f4 MMAs of K = 32; W rows
+//   carry a power-of-two scale that the epilogue divides out.
+template <int EPI, bool TRANS, bool SPLIT = false, bool FP8 = false>
 __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __grid_constant__ Args g) {
     static_assert(!(TRANS && SPLIT), "split operands are for the forward layers only");
+    static_assert(!(FP8 && (TRANS || SPLIT)), "E4M3 operands are for the plain forward layers only");
+    constexpr int kCK = FP8 ? 128 : kChunkK;  // K elements per chunk: one 128-byte row
     constexpr int kOps = (SPLIT ? 2 : 1) * (kABytes + kBBytes);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -237,14 +276,14 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = idesc_bf16(kTileM, Nt);
+    const uint32_t idesc = FP8 ? idesc_e4m3(kTileM, Nt) : idesc_bf16(kTileM, Nt);
     const uint32_t mb = smem_u32(mbar);
 
     bool ok = true;
     uint32_t phase = 0;
     const int64_t kbeg = TRANS ? blockIdx.z * g.kchunk : 0;
     const int64_t kend = TRANS ? min(g.K, kbeg + g.kchunk) : g.K;
-    const int nchunks = (int)((kend - kbeg + kChunkK - 1) / kChunkK);
+    const int nchunks = (int)((kend - kbeg + kCK - 1) / kCK);
     // operand granules of one K chunk, held in registers as packed BF16:
     // 8 A granules and up to 8 B granules per thread
     uint4 ra[8], rb[8], ra2[8], rb2[8];  // ra2/rb2: low parts (SPLIT)
@@ -275,6 +314,39 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
         }
     };
     auto load_chunk = [&](int64_t k0) {
+        if constexpr (FP8) {
+            // A: 8 consecutive threads cover one row's 128 values, 16 each
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int it = tid + i * kThreads;
+                const int r = it >> 3, c = it & 7;
+                const int64_t m = m0 + r;
+                const int64_t k = k0 + c * 16;
+                float v[16];
+                if (m < g.M && g.vec_x && k + 16 <= g.K) {
+                    const float4 *src = reinterpret_cast<const float4 *>(g.X + m * g.ldx + k);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 f = __ldg(src + q);
+                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = (m < g.M && k + e < g.K) ? g.X[m * g.ldx + k + e] : 0.f;
+                }
+                ra[i] = pack16_e4m3(v);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i * kThreads >= Nt * 8) break;
+                const int it = tid + i * kThreads;
+                const int r = it >> 3, c = it & 7;
+                const int64_t n = n0 + r;
+                rb[i] = n < g.N ? __ldg(reinterpret_cast<const uint4 *>(g.W8 + n * g.Kpad8 + k0 + c * 16))
+                                : make_uint4(0u, 0u, 0u, 0u);
+            }
+            return;
+        }
         if (tvec) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -402,7 +474,9 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
             const uint64_t da2 = desc_sw128(smem_u32(sA2)), db2 = desc_sw128(smem_u32(sB2));
 #pragma unroll
             for (int k = 0; k < kChunkK / 16; ++k) {  // +32 bytes per K=16 step inside the swizzle atom
-                if (SPLIT) {  // small terms first
+                if (FP8) {
+                    mma_e4m3(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                } else if (SPLIT) {  // small terms first
                     mma_bf16(tmem, da2 + uint64_t(2 * k), db + uint64_t(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
                     mma_bf16(tmem, da + uint64_t(2 * k), db2 + uint64_t(2 * k), idesc, 1u);
                     mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, 1u);
@@ -413,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
             mma_commit(mb);
         }
         // the next chunk's loads are in flight while the MMAs run
-        if (kc + 1 < nchunks) load_chunk(kbeg + int64_t(kc + 1) * kChunkK);
+        if (kc + 1 < nchunks) load_chunk(kbeg + int64_t(kc + 1) * kCK);
         // every thread saw the MMAs retire (or gave up) before the buffers are
         // reused; the flag is made CTA-uniform so no barrier below diverges
         ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
@@ -478,7 +552,9 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
                 for (int e = 0; e < 4; ++e) {
                     const int64_t n = n0 + 32 * c + 4 * q + e;
                     const float bias_v = (g.bias && n < g.N) ? __ldg(g.bias + n) : 0.f;
-                    v[e] = __uint_as_float(r[4 * q + e]) + bias_v;
+                    float a = __uint_as_float(r[4 * q + e]);
+                    if (FP8) a *= n < g.N ? __ldg(g.wsinv + n) : 0.f;
+                    v[e] = a + bias_v;
                     if (EPI == EPI_STORE) {
                         y[e] = v[e];
                     } else if (EPI == EPI_GELU) {
@@ -571,6 +647,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
             const int64_t n = n0 + c0 + cc;
             const bool col_ok = (r0 < rp) && (n < g.N);
             const float bias_v = (g.bias && col_ok) ? __ldg(g.bias + n) : 0.f;
+            const float ws_v = (FP8 && col_ok) ? __ldg(g.wsinv + n) : 1.f;
             const int nrow = (kTileM + rp - 1) / rp;
             for (int b = 0; 16 * b < nrow; ++b) {
                 float rv[16];
@@ -588,7 +665,8 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 4) k_tc_gemm(const __gri
                     const int rr = r0 + rp * (16 * b + j);
                     const int64_t m = m0 + rr;
                     if (!col_ok || rr >= kTileM || m >= g.M) continue;
-                    const float v = slab[rr * 64 + (cc ^ (rr & 31))] + bias_v;
+                    const float v = (FP8 ? slab[rr * 64 + (cc ^ (rr & 31))] * ws_v : slab[rr * 64 + (cc ^ (rr & 31))]) +
+                                    bias_v;
                     const int64_t o = zoff + m * g.ldy + n;
                     if (EPI == EPI_STORE) {
                         g.Y[o] = v;

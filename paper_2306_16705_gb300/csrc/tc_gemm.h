@@ -1,4 +1,4 @@
-// BF16 tensor-core (tcgen05) linear layers for NNQS_MIXED and NNQS_BF16X3:
+// Tensor-core (tcgen05) linear layers for NNQS_MIXED, NNQS_BF16X3 and NNQS_FP8:
 // BF16 copies of the weight matrices (and their low parts), and
 // Y = X W^T + epilogue with FP32 accumulation.
 #pragma once
@@ -21,6 +21,14 @@ struct TcWeights {
     // at tile_off, low part right after: one bulk copy puts a block in place
     void *tiles = nullptr;
     int64_t tile_off[4 * 64 + 1] = {};
+    // NNQS_FP8: E4M3 copies of the forward matrices [N][pad128(K)], each row
+    // n scaled by a power of two s_n (its largest entry lands in (224, 448]),
+    // and 1 / s_n per row
+    bool fp8 = false;
+    uint8_t *w8 = nullptr;
+    float *w8inv = nullptr;
+    int64_t off8[4 * 64 + 1] = {}, soff8[4 * 64 + 1] = {};
+    int32_t pcols8[4 * 64 + 1] = {};
     DevStatus *st = nullptr;       // where a timed-out wait is recorded
 };
 
