@@ -1270,6 +1270,42 @@ struct RowBatch {
     }
 };
 
+// Head groups: a sample whose whole attention state does not fit one CTA's
+// shared memory is split over gridDim.y CTAs, CTA g taking heads
+// [g Hg, (g + 1) Hg) (columns [g dg, (g + 1) dg) of every d-wide segment).
+// seg_rows_to_smem gathers a [T][nseg dfull] block's nseg segments, columns
+// off .. off + dg - 1 of each, into staged rows [seg 0 | seg 1 | ...] of
+// width nseg dg (columns placed by swz_col<R, NC>); smem_to_seg_rows writes
+// staged rows back the same way (unrotated).  Both need 16-byte aligned
+// rows and dg, dfull, off multiples of the vector width.
+template <class R, int NC>
+__device__ __forceinline__ void seg_rows_to_smem(R *dst, int ld, const R *__restrict__ src, int T, int nseg,
+                                                 int dfull, int off, int dg) {
+    constexpr int V = int(16 / sizeof(R));
+    const int pv = dg / V, per_row = nseg * pv;
+    for (int e = threadIdx.x; e < T * per_row; e += blockDim.x) {
+        const int r = e / per_row, q = e - r * per_row, sg = q / pv, c = (q - sg * pv) * V;
+        const ColVec<R, V> v = ld_vec<R, V>(src + ((int64_t)r * nseg + sg) * dfull + off + c);
+        const int cs = swz_col<R, NC>(sg * dg + c);
+#pragma unroll
+        for (int k = 0; k < V; ++k) dst[r * ld + cs + k] = v.v[k];
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void smem_to_seg_rows(R *__restrict__ dst, const R *src, int ld, int T, int nseg, int dfull,
+                                                 int off, int dg) {
+    constexpr int V = int(16 / sizeof(R));
+    const int pv = dg / V, per_row = nseg * pv;
+    for (int e = threadIdx.x; e < T * per_row; e += blockDim.x) {
+        const int r = e / per_row, q = e - r * per_row, sg = q / pv, c = (q - sg * pv) * V;
+        ColVec<R, V> v;
+#pragma unroll
+        for (int k = 0; k < V; ++k) v.v[k] = src[r * ld + sg * dg + c + k];
+        *reinterpret_cast<ColVec<R, V> *>(dst + ((int64_t)r * nseg + sg) * dfull + off + c) = v;
+    }
+}
+
 // 16-byte pieces per thread of a sample's q|k|v rows (3 d = 3 H DH columns,
 // at least H T threads): 3 DH / V, capped
 template <class R, int DH>
@@ -1404,10 +1440,12 @@ __global__ void k_attn_fwd_smem(const R *__restrict__ qkv, R *__restrict__ o, R 
 
 // colsum (optional): [n][3d] column sums of the sample's dq|dk|dv over its
 // T positions (added in position order), for the qkv bias gradient
+// With head groups (gridDim.y > 1): H and d are the group's heads and width,
+// Hfull and dfull the model's; blockIdx.y is the group.
 template <class R, int DH>
 __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__ o, const R *__restrict__ lse,
                                 const R *__restrict__ dout, R *__restrict__ dqkv, int T, int H, int d,
-                                R *__restrict__ colsum) {
+                                R *__restrict__ colsum, int Hfull, int dfull) {
     using HV = HeadVec<R, DH>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int ldq = HV::ld(3 * d), ldo = HV::ld(d);
@@ -1419,7 +1457,15 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
     R *sD = slse + H * T;                    // [H][T]
     const int64_t i = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
-    {
+    const bool grouped = gridDim.y > 1;
+    const int goff = blockIdx.y * d;  // first column of this group within a segment
+    if (grouped) {
+        seg_rows_to_smem<R, HV::kNC>(sq, ldq, qkv + i * T * 3 * dfull, T, 3, dfull, goff, d);
+        seg_rows_to_smem<R, HV::kNC>(sdo, ldo, dout + i * T * dfull, T, 1, dfull, goff, d);
+        seg_rows_to_smem<R, HV::kNC>(so, ldo, o + i * T * dfull, T, 1, dfull, goff, d);
+        const R *lg = lse + (i * Hfull + blockIdx.y * H) * T;
+        for (int e = tid; e < H * T; e += nt) slse[e] = Softmax<R>::unit_lse(lg[e]);
+    } else {
         // all three blocks' loads in flight together
         const R *s1 = qkv + i * T * 3 * d, *s2 = dout + i * T * d, *s3 = o + i * T * d;
         RowBatch<R, qkv_pieces<R, DH>()> b1;
@@ -1522,12 +1568,16 @@ __global__ void k_attn_bwd_smem(const R *__restrict__ qkv, const R *__restrict__
         HV::write(sg + j * ldq + 2 * d + hh * DH, dv);
     }
     __syncthreads();
-    smem_to_rows<R>(dqkv + i * T * 3 * d, sg, ldq, T, 3 * d);
+    if (grouped)
+        smem_to_seg_rows<R>(dqkv + i * T * 3 * dfull, sg, ldq, T, 3, dfull, goff, d);
+    else
+        smem_to_rows<R>(dqkv + i * T * 3 * d, sg, ldq, T, 3 * d);
     if (colsum) {
         for (int c = tid; c < 3 * d; c += nt) {
             R acc = 0;
             for (int t = 0; t < T; ++t) acc += sg[t * ldq + c];
-            colsum[i * 3 * d + c] = acc;
+            const int seg = c / d;
+            colsum[i * 3 * dfull + seg * dfull + goff + (c - seg * d)] = acc;
         }
     }
 }
@@ -2835,14 +2885,23 @@ nnqs_status attn_fwd(cudaStream_t s, int dh, const R *qkv, R *o, R *lse, int64_t
 template <int DH_, class R>
 nnqs_status launch_attn_bwd(cudaStream_t s, const R *qkv, const R *o, const R *lse, const R *dout, R *dqkv, R *Dbuf,
                             int64_t n, int T, int H, int d, R *colsum, bool *sums) {
-    const size_t sm = attn_bwd_smem_bytes<R>(T, H, d);
     *sums = false;
-    if (H * T <= 1024 && sm <= kAttnSmemMax && n > 0) {
+    // the fewest head groups whose per-CTA state fits shared memory (the
+    // group width a multiple of the 16-byte vector, rows 16-byte aligned)
+    constexpr int V = int(16 / sizeof(R));
+    for (int G = 1; G <= H && n > 0; G *= 2) {
+        if (H % G != 0) break;
+        const int Hg = H / G, dg = d / G;
+        if (G > 1 && (dg % V != 0 || reinterpret_cast<uintptr_t>(qkv) % 16 || reinterpret_cast<uintptr_t>(o) % 16 ||
+                      reinterpret_cast<uintptr_t>(dout) % 16 || reinterpret_cast<uintptr_t>(dqkv) % 16))
+            break;
+        const size_t sm = attn_bwd_smem_bytes<R>(T, Hg, dg);
+        if (Hg * T > 1024 || sm > kAttnSmemMax) continue;
         NNQS_TRY(allow_smem(k_attn_bwd_smem<R, DH_>, sm));
-        const int threads = (H * T + 31) / 32 * 32;
+        const int threads = (Hg * T + 31) / 32 * 32;
         NNQS_LAUNCH("k_attn_bwd", s,
-                    k_attn_bwd_smem<R, DH_><<<(unsigned)n, threads, sm, s>>>(qkv, o, lse, dout, dqkv, T, H, d,
-                                                                              colsum));
+                    k_attn_bwd_smem<R, DH_><<<dim3((unsigned)n, (unsigned)G), threads, sm, s>>>(
+                        qkv, o, lse, dout, dqkv, T, Hg, dg, colsum, H, d));
         *sums = colsum != nullptr;
         return NNQS_OK;
     }

@@ -196,3 +196,23 @@ def test_backward_mixed_close_to_fp64():
     assert np.linalg.norm(gmx - g64) <= 5e-2 * np.linalg.norm(g64)
     gx3 = B.logpsi_backward(m, flat, x, seed, B.BF16X3).cpu().numpy()
     assert np.linalg.norm(gx3 - g64) <= 5e-2 * np.linalg.norm(g64)
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+def test_backward_head_groups_match_oracle(prec):
+    """120 qubits (60 tokens), d = 128, 8 heads: one sample's attention state
+    is larger than a CTA's shared memory, so the attention reverse mode splits
+    the heads over 2 (FP32) or 4 (FP64) CTAs per sample.  Gradients against
+    the oracle's reverse mode with the tolerances above."""
+    N, na, nb, d, L, H, ns = 120, 20, 20, 128, 1, 8, 12
+    m, params, flat = make(N, na, nb, d, L, H, seed=17, hidden=64, std=0.1)
+    x = I.random_sector_samples(N // 2, na, nb, ns, seed=5)
+    rng = np.random.default_rng(2)
+    seed = np.stack([rng.normal(size=ns), rng.normal(size=ns)], 1)
+    g = B.logpsi_backward(m, flat, B.to_device_bits(x), torch.from_numpy(seed).cuda(), prec)
+    G = m.unpack(g, params)
+    _, _, cache = OA.forward(params, I.unpack_bits(x, N), na, nb, H, want_cache=True)
+    R = OA.backward(cache, seed[:, 0], seed[:, 1])
+    for k in params:
+        err = np.abs(G[k] - R[k]).max()
+        assert err <= GRAD_TOL[prec] * max(1e-3, np.abs(R[k]).max()), (k, err, np.abs(R[k]).max())
