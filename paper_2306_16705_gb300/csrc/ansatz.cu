@@ -16,12 +16,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 
 #include "dev_common.cuh"
 #include "model.h"
 #include "tc_gemm.h"
 #include "tc_gemm.cuh"
+#include "fwd_fused.cuh"
 
 namespace nnqs {
 namespace {
@@ -2927,6 +2929,10 @@ nnqs_status attn_bwd(cudaStream_t s, int dh, const R *qkv, const R *o, const R *
     }
 }
 
+template <class R>
+nnqs_status phase_mlp(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A, double2 *out,
+                      const TcWeights *tcw, cudaStream_t s);
+
 // Forward of one chunk of C samples (x: [C][W]), writing out[C] (log|psi|, phase).
 // cond != null: sampling mode -- x are prefixes of S-1 tokens, the output is
 // pi~(. | prefix) at position S-1 (no phase, no log psi).
@@ -2980,7 +2986,14 @@ nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t
     }
     NNQS_LAUNCH("k_head", s, k_head<R><<<grid_for(C * 32, 256), 256, 0, s>>>(x, W, A.hf, V.hw, V.hb, A.tok, C, T, d, M->cfg.n_alpha,
                                                     M->cfg.n_beta, A.pi, out, st, row_offset));
-    // phase MLP
+    return phase_mlp<R>(M, V, x, C, A, out, tcw, s);
+}
+
+// phase MLP N -> P -> P -> 1 (ReLU) of C samples into out[i].y
+template <class R>
+nnqs_status phase_mlp(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A, double2 *out,
+                      const TcWeights *tcw, cudaStream_t s) {
+    const int P = M->P, W = M->W, N = M->N, L = M->L;
     if (P <= 512 && W <= 2 && N <= P)
     {
         constexpr int NR = phase_rows<R>();
@@ -3170,6 +3183,58 @@ size_t workspace_impl(const nnqs_model *M, int64_t n, bool backward, bool tensor
     return a.used + 1024;
 }
 
+// NNQS_FUSED_FORWARD=0 in the environment keeps the layer-by-layer forward
+// (for comparisons); read once
+bool fused_fwd_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("NNQS_FUSED_FORWARD");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+// arguments of the fused forward for C samples x (FP32 parameters V, BF16
+// weight images of tcw)
+FusedFwdArgs fused_args(const nnqs_model *M, const Views<float> &V, const TcWeights &tcw, const uint64_t *x,
+                        int64_t C, double2 *out, DevStatus *st, int64_t row_offset) {
+    FusedFwdArgs a{};
+    a.x = x;
+    a.n = C;
+    a.W = M->W;
+    a.T = M->T;
+    a.L = M->L;
+    a.n_alpha = M->cfg.n_alpha;
+    a.n_beta = M->cfg.n_beta;
+    a.spt = 128 / M->T;
+    a.n_tiles = (C + a.spt - 1) / a.spt;
+    a.tok = V.tok;
+    a.pos = V.pos;
+    a.lnf_g = V.lnf_g;
+    a.lnf_b = V.lnf_b;
+    a.hw = V.hw;
+    a.hb = V.hb;
+    const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(tcw.tiles);
+    for (int l = 0; l < M->L; ++l) {
+        const auto &Lw = V.layer[l];
+        a.ln1g[l] = Lw.ln1g;
+        a.ln1b[l] = Lw.ln1b;
+        a.bqkv[l] = Lw.bqkv;
+        a.bo[l] = Lw.bo;
+        a.ln2g[l] = Lw.ln2g;
+        a.ln2b[l] = Lw.ln2b;
+        a.b1[l] = Lw.b1;
+        a.b2[l] = Lw.b2;
+        a.tqkv[l] = tiles + tcw.tile_off[tc_slot(l, 0)];
+        a.to[l] = tiles + tcw.tile_off[tc_slot(l, 1)];
+        a.t1[l] = tiles + tcw.tile_off[tc_slot(l, 2)];
+        a.t2[l] = tiles + tcw.tile_off[tc_slot(l, 3)];
+    }
+    a.out = out;
+    a.st = st;
+    a.row_offset = row_offset;
+    return a;
+}
+
 template <class R>
 nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, double *out, Arena &ws,
                          DevStatus *st, int tcm, cudaStream_t s) {
@@ -3186,10 +3251,21 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
     NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
     const Views<R> V = make_views<R>(M, pr);
+    // BF16 (split or not) with d = 64: the whole transformer of a 128-row
+    // tile in one persistent kernel (fwd_fused.cu); the phase MLP after it
+    const bool fused = tensor && !tcw.fp8 && sizeof(R) == 4 && fused_fwd_enabled() &&
+                       fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L);
     for (int64_t c0 = 0; c0 < n; c0 += C) {
         const int64_t cn = std::min(C, n - c0);
-        NNQS_TRY(forward_chunk<R>(M, V, x + c0 * M->W, cn, A, reinterpret_cast<double2 *>(out) + c0, st, c0,
-                                  tensor ? &tcw : nullptr, s));
+        double2 *oc = reinterpret_cast<double2 *>(out) + c0;
+        if constexpr (sizeof(R) == 4) {
+            if (fused) {
+                NNQS_TRY(fused_fwd_launch(fused_args(M, V, tcw, x + c0 * M->W, cn, oc, st, c0), tcw.split, M->dh, s));
+                NNQS_TRY(phase_mlp<R>(M, V, x + c0 * M->W, cn, A, oc, &tcw, s));
+                continue;
+            }
+        }
+        NNQS_TRY(forward_chunk<R>(M, V, x + c0 * M->W, cn, A, oc, st, c0, tensor ? &tcw : nullptr, s));
     }
     return NNQS_OK;
 }

@@ -1,0 +1,545 @@
+// Fused forward of the transformer amplitude (Sec. 3.1, Eq. auto; mask of
+// Sec. 3.3) for log|psi| of whole samples, on tcgen05 tensor cores.
+//
+// A persistent CTA of 512 threads per SM walks 128-row tiles of token rows
+// (floor(128 / T) samples of T tokens each) and keeps every activation of a
+// tile on chip through all decoder layers: the residual rows in shared
+// memory (FP32), the A operands as BF16 (split hi/lo) swizzled tiles, the
+// accumulators in TMEM, the keys and values of the tile in shared memory for
+// the causal attention (a sample's tokens never leave its tile), and the
+// weights brought in by bulk asynchronous copies of their pre-swizzled
+// images while the previous phase computes:
+//   embedding -> [LN1 -> qkv MMA -> attention -> out-projection MMA +
+//   residual -> LN2 -> four FFN-in MMAs -> GELU chunks -> FFN-out MMAs +
+//   residual] x L -> final LN -> head -> masked log-softmax of each row's
+//   token -> log|psi| = 1/2 sum over the sample's rows.
+// Per sample only its bitstring is read and one double written; the phase
+// MLP runs separately.  The arithmetic is the unfused FP32/BF16 path's up to
+// the order of floating-point sums (not bit-identical to it).
+//
+// Shared memory (1024-aligned base):
+//   [0, 32K)      A tile hi / lo  (LN output, attention output)
+//   [32K, 64K)    G tile hi / lo  (GELU chunk); before the FFN: Wo hi / lo
+//   [64K, 128K)   k | v of the tile [128][128] FP32 (attention); then W2
+//   [128K, 192K)  Wqkv hi / lo; after the qkv MMA: W1 hi / lo
+//   [192K, ...)   residual rows [128][65] FP32, per-row log pi~, barriers
+// TMEM (512 columns): q | k | v [0, 192), out-projection [192, 256), the four
+// FFN-in chunks [256, 512), FFN-out [0, 64) (over q, consumed by then).
+//
+// Every wait is bounded (tc::mbar_wait): on a timeout the CTA records
+// NNQS_E_TIMEOUT, lets its weight copies land (bounded) and frees its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dev_common.cuh"
+#include "fwd_fused.cuh"
+#include "tc_gemm.cuh"
+
+namespace nnqs {
+namespace {
+namespace ff {
+constexpr int kThreads = 512, kRows = 128, kD = 64, kQKV = 192, kF = 256;
+constexpr int kOffA = 0, kOffA2 = 16384, kOffG = 32768, kOffG2 = 49152;
+constexpr int kOffKV = 65536, kOffWB = 131072, kOffH = 196608;
+constexpr int kHS = 65;
+constexpr int kOffLP = kOffH + kRows * kHS * 4;
+constexpr int kOffBar = kOffLP + kRows * 4;
+constexpr int kSmem = kOffBar + 64 + 1024;  // 231,488 bytes
+constexpr uint32_t kColQ = 0, kColO = 192, kColU = 256, kColY = 0, kTmemCols = 512;
+constexpr float kLog2e = 1.44269504088896340736f;
+}  // namespace ff
+
+__device__ __forceinline__ void ff_bulk(uint8_t *dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ float ff_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// element (r, c) of the tile's k | v rows: 16-byte pieces XOR-rotated by the
+// row so that lanes reading the same piece of different rows use different banks
+__device__ __forceinline__ int kv_at(int r, int c) { return r * 128 + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3); }
+
+// 8 values as one granule of a swizzled A-operand tile row (hi, and lo when split)
+__device__ __forceinline__ void ff_granule(uint8_t *hi, uint8_t *lo, int r, int c, const float *v, bool split) {
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = v[e];
+    const int off = r * 128 + ((c ^ (r & 7)) << 4);
+    *reinterpret_cast<uint4 *>(hi + off) = tc::pack8(x);
+    if (split) {
+        float y[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = x[e] - __bfloat162float(__float2bfloat16_rn(x[e]));
+        *reinterpret_cast<uint4 *>(lo + off) = tc::pack8(y);
+    }
+}
+
+// LayerNorm (eps 1e-5) of residual row r into the A tile
+__device__ __forceinline__ void ff_layernorm(const float *sH, int r, const float *__restrict__ gam,
+                                             const float *__restrict__ bet, uint8_t *hi, uint8_t *lo, bool split) {
+    float v[ff::kD];
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < ff::kD; ++c) {
+        v[c] = sH[r * ff::kHS + c];
+        s += v[c];
+    }
+    const float mu = s / float(ff::kD);
+    float q = 0.f;
+#pragma unroll
+    for (int c = 0; c < ff::kD; ++c) q += (v[c] - mu) * (v[c] - mu);
+    const float rs = 1.0f / sqrtf(q / float(ff::kD) + 1e-5f);
+#pragma unroll
+    for (int gi = 0; gi < 8; ++gi) {
+        float y[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int c = 8 * gi + e;
+            y[e] = (v[c] - mu) * rs * __ldg(gam + c) + __ldg(bet + c);
+        }
+        ff_granule(hi, lo, r, gi, y, split);
+    }
+}
+
+// 4 K steps (K = 64) of one 128 x N product into TMEM: with split operands
+// lo.hi + hi.lo + hi.hi per step
+__device__ __forceinline__ void ff_mma(uint32_t tmem, uint32_t aHi, uint32_t aLo, uint32_t bHi, uint32_t bLo, int N,
+                                       bool split, bool acc0) {
+    const uint32_t idesc = tc::idesc_bf16(ff::kRows, N);
+    const uint64_t da = tc::desc_sw128(aHi), db = tc::desc_sw128(bHi);
+    const uint64_t da2 = tc::desc_sw128(aLo), db2 = tc::desc_sw128(bLo);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t acc = (acc0 || k > 0) ? 1u : 0u;
+        if (split) {
+            tc::mma_bf16(tmem, da2 + uint64_t(2 * k), db + uint64_t(2 * k), idesc, acc);
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db2 + uint64_t(2 * k), idesc, 1u);
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, 1u);
+        } else {
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, acc);
+        }
+    }
+}
+
+__device__ __forceinline__ int ff_bit(const uint64_t *x, int j) { return (int)((x[j >> 6] >> (j & 63)) & 1ull); }
+// token at position t: spatial orbital T-1-t, value y_alpha + 2 y_beta
+__device__ __forceinline__ int ff_token(const uint64_t *x, int T, int t) {
+    const int p = T - 1 - t;
+    return ff_bit(x, 2 * p) + 2 * ff_bit(x, 2 * p + 1);
+}
+
+template <bool SPLIT, int DH>
+__global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_constant__ FusedFwdArgs g) {
+    using namespace ff;
+    constexpr int H = kD / DH;
+    constexpr int HPT = H / 4;  // heads of one thread: its row's 16-column quarter
+    static_assert(HPT * DH == 16, "a thread covers 16 columns of q");
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sb = smem_raw + (base - raw);
+    uint8_t *aHi = sb + kOffA, *aLo = sb + kOffA2, *gHi = sb + kOffG, *gLo = sb + kOffG2;
+    float *sKV = reinterpret_cast<float *>(sb + kOffKV);
+    float *sH = reinterpret_cast<float *>(sb + kOffH);
+    float *sLP = reinterpret_cast<float *>(sb + kOffLP);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 32);
+    // barriers: MMA completion, weight region B (Wqkv / W1), Wo (G region), W2 (k|v region)
+    const uint32_t mb = base + kOffBar, bWB = mb + 8, bWO = mb + 16, bW2 = mb + 24;
+    const uint32_t uA = base + kOffA, uA2 = base + kOffA2, uG = base + kOffG, uG2 = base + kOffG2;
+    const uint32_t uKV = base + kOffKV, uWB = base + kOffWB;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
+    const int T = g.T, rows_used = g.spt * T;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) tc::mbar_init(mb + 8u * b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
+
+    bool ok = true;
+    uint32_t ph_mma = 0;
+    uint32_t n_wb = 0, d_wb = 0, n_wo = 0, d_wo = 0, n_w2 = 0, d_w2 = 0;  // copies issued / waited per barrier
+    auto sync_async = [&]() {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+    auto wait_mma = [&]() {
+        ok = __syncthreads_and(tc::mbar_wait(mb, ph_mma) ? 1 : 0) != 0;
+        ph_mma ^= 1u;
+        tc::fence_after_sync();
+    };
+    auto wait_bar = [&](uint32_t bar, uint32_t &done) {
+        ok = __syncthreads_and(tc::mbar_wait(bar, done & 1u) ? 1 : 0) != 0;
+        if (ok) ++done;
+    };
+    // weight copies (thread 0 issues; every thread counts)
+    auto issue_wqkv = [&](int l) {
+        constexpr uint32_t q = kQKV * 128;
+        if (tid == 0) {
+            tc::fence_async_smem();
+            tc::mbar_expect(bWB, SPLIT ? 2 * q : q);
+            ff_bulk(sb + kOffWB, g.tqkv[l], q, bWB);
+            if (SPLIT) ff_bulk(sb + kOffWB + q, static_cast<const __nv_bfloat16 *>(g.tqkv[l]) + kQKV * kD, q, bWB);
+        }
+        ++n_wb;
+    };
+    auto issue_w1_wo = [&](int l) {
+        constexpr uint32_t b1 = kF * 128, bo = kD * 128;
+        if (tid == 0) {
+            tc::fence_async_smem();
+            tc::mbar_expect(bWB, SPLIT ? 2 * b1 : b1);
+            ff_bulk(sb + kOffWB, g.t1[l], b1, bWB);
+            if (SPLIT) ff_bulk(sb + kOffWB + b1, static_cast<const __nv_bfloat16 *>(g.t1[l]) + kF * kD, b1, bWB);
+            tc::mbar_expect(bWO, SPLIT ? 2 * bo : bo);
+            ff_bulk(gHi, g.to[l], bo, bWO);
+            if (SPLIT) ff_bulk(gHi + bo, static_cast<const __nv_bfloat16 *>(g.to[l]) + kD * kD, bo, bWO);
+        }
+        ++n_wb;
+        ++n_wo;
+    };
+    auto issue_w2 = [&](int l) {
+        constexpr uint32_t b2 = kD * kF * 2;  // four 8 KB K blocks
+        if (tid == 0) {
+            tc::fence_async_smem();
+            tc::mbar_expect(bW2, SPLIT ? 2 * b2 : b2);
+            ff_bulk(sb + kOffKV, g.t2[l], b2, bW2);
+            if (SPLIT) ff_bulk(sb + kOffKV + b2, static_cast<const __nv_bfloat16 *>(g.t2[l]) + kD * kF, b2, bW2);
+        }
+        ++n_w2;
+    };
+
+    if (blockIdx.x < g.n_tiles) issue_wqkv(0);
+    const float qscale = (1.0f / sqrtf(float(DH))) * kLog2e;  // scores in base-2 units
+    for (int64_t tile = blockIdx.x; tile < g.n_tiles && ok; tile += gridDim.x) {
+        const int64_t s0 = tile * g.spt;
+        // embeddings of the tile's rows (padding rows and samples past n: zero)
+        for (int e = tid; e < kRows * (kD / 4); e += kThreads) {
+            const int r = e >> 4, c4 = e & 15;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < rows_used) {
+                const int sl = r / T, t = r - sl * T;
+                const int64_t i = s0 + sl;
+                if (i < g.n) {
+                    const int inp = t == 0 ? 4 : ff_token(g.x + i * g.W, T, t - 1);
+                    const float4 te = __ldg(reinterpret_cast<const float4 *>(g.tok + inp * kD) + c4);
+                    const float4 pe = __ldg(reinterpret_cast<const float4 *>(g.pos + t * kD) + c4);
+                    v = make_float4(te.x + pe.x, te.y + pe.y, te.z + pe.z, te.w + pe.w);
+                }
+            }
+            float *hr = sH + r * kHS + 4 * c4;
+            hr[0] = v.x;
+            hr[1] = v.y;
+            hr[2] = v.z;
+            hr[3] = v.w;
+        }
+        __syncthreads();
+        for (int l = 0; l < g.L && ok; ++l) {
+            // ---- LN1 -> A; qkv product
+            if (tid < kRows) ff_layernorm(sH, tid, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
+            wait_bar(bWB, d_wb);
+            sync_async();
+            if (!ok) break;
+            if (tid == 0) {
+                ff_mma(tmem + kColQ, uA, uA2, uWB, uWB + kQKV * 128, kQKV, SPLIT, false);
+                tc::mma_commit(mb);
+            }
+            wait_mma();
+            if (!ok) break;
+            issue_w1_wo(l);  // Wqkv consumed: W1 over it, Wo into the G region
+            // ---- k | v + bias into shared memory (thread: 32 columns of its row)
+            {
+                const float *bq = g.bqkv[l];
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    const int tc0 = 64 + 32 * cq + 16 * hf;  // TMEM column = bias index
+                    uint32_t r16[16];
+                    tc::tmem_ld16(tl + tc0, r16);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const int c = tc0 - 64 + 4 * p;  // column of k | v
+                        float4 v;
+                        v.x = __uint_as_float(r16[4 * p]) + __ldg(bq + tc0 + 4 * p);
+                        v.y = __uint_as_float(r16[4 * p + 1]) + __ldg(bq + tc0 + 4 * p + 1);
+                        v.z = __uint_as_float(r16[4 * p + 2]) + __ldg(bq + tc0 + 4 * p + 2);
+                        v.w = __uint_as_float(r16[4 * p + 3]) + __ldg(bq + tc0 + 4 * p + 3);
+                        *reinterpret_cast<float4 *>(sKV + kv_at(row, c)) = v;
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- causal attention within the row's sample: thread (row,
+            // quarter cq) takes heads cq HPT .. + HPT - 1 (q columns 16 cq ..)
+            float o[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) o[c] = 0.f;
+            {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColQ + 16 * cq, r16);
+                if (row < rows_used) {
+                    const float *bq = g.bqkv[l];
+                    float qv[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) qv[c] = (__uint_as_float(r16[c]) + __ldg(bq + 16 * cq + c)) * qscale;
+                    const int sl = row / T, t = row - sl * T, r0 = sl * T;
+                    float m[HPT], ls[HPT];
+#pragma unroll
+                    for (int h = 0; h < HPT; ++h) {
+                        m[h] = -INFINITY;
+                        ls[h] = 0.f;
+                    }
+                    for (int j = 0; j <= t; ++j) {
+                        const int rj = r0 + j;
+                        float kk[16], vv[16];
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const float4 a = *reinterpret_cast<const float4 *>(sKV + kv_at(rj, 16 * cq + 4 * p));
+                            const float4 b = *reinterpret_cast<const float4 *>(sKV + kv_at(rj, 64 + 16 * cq + 4 * p));
+                            kk[4 * p] = a.x; kk[4 * p + 1] = a.y; kk[4 * p + 2] = a.z; kk[4 * p + 3] = a.w;
+                            vv[4 * p] = b.x; vv[4 * p + 1] = b.y; vv[4 * p + 2] = b.z; vv[4 * p + 3] = b.w;
+                        }
+#pragma unroll
+                        for (int h = 0; h < HPT; ++h) {
+                            float sc = 0.f;
+#pragma unroll
+                            for (int c = 0; c < DH; ++c) sc += qv[h * DH + c] * kk[h * DH + c];
+                            const float mn = sc > m[h] ? sc : m[h];
+                            const float corr = ff_ex2(m[h] - mn);
+                            const float p = ff_ex2(sc - mn);
+                            ls[h] = ls[h] * corr + p;
+#pragma unroll
+                            for (int c = 0; c < DH; ++c) o[h * DH + c] = o[h * DH + c] * corr + p * vv[h * DH + c];
+                            m[h] = mn;
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < HPT; ++h) {
+                        const float inv = 1.0f / ls[h];
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) o[h * DH + c] *= inv;
+                    }
+                }
+            }
+            tc::fence_async_smem();  // (every thread: its generic accesses before the async copy below)
+            __syncthreads();         // k | v and q read by everyone
+            issue_w2(l);             // the k | v region takes W2
+            ff_granule(aHi, aLo, row, 2 * cq, o, SPLIT);
+            ff_granule(aHi, aLo, row, 2 * cq + 1, o + 8, SPLIT);
+            wait_bar(bWO, d_wo);
+            sync_async();
+            if (!ok) break;
+            // ---- out-projection + residual
+            if (tid == 0) {
+                ff_mma(tmem + kColO, uA, uA2, uG, uG + kD * 128, kD, SPLIT, false);
+                tc::mma_commit(mb);
+            }
+            wait_mma();
+            if (!ok) break;
+            {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColO + 16 * cq, r16);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = 16 * cq + j;
+                    sH[row * kHS + c] += __uint_as_float(r16[j]) + __ldg(g.bo[l] + c);
+                }
+            }
+            __syncthreads();
+            // ---- LN2 -> A; the four FFN-in chunks issued together
+            if (tid < kRows) ff_layernorm(sH, tid, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
+            wait_bar(bWB, d_wb);
+            sync_async();
+            if (!ok) break;
+            if (tid == 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    ff_mma(tmem + kColU + 64 * c, uA, uA2, uWB + 8192 * c, uWB + kF * 128 + 8192 * c, kD, SPLIT,
+                           false);
+                tc::mma_commit(mb);
+            }
+            wait_mma();
+            if (!ok) break;
+            // W1 consumed: the next Wqkv (this tile's next layer, or the first
+            // layer of this CTA's next tile) comes in during the FFN
+            if (l + 1 < g.L)
+                issue_wqkv(l + 1);
+            else if (tile + gridDim.x < g.n_tiles)
+                issue_wqkv(0);
+            wait_bar(bW2, d_w2);
+            if (!ok) break;
+            // ---- per chunk: GELU(U_c + b1) -> G while the previous FFN-out
+            // product runs, then Y += G W2_c^T
+            for (int c = 0; c < 4 && ok; ++c) {
+                float x[16];
+                {
+                    uint32_t r16[16];
+                    tc::tmem_ld16(tl + kColU + 64 * c + 16 * cq, r16);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        x[j] = tc::gelu_f(__uint_as_float(r16[j]) + __ldg(g.b1[l] + 64 * c + 16 * cq + j));
+                }
+                if (c > 0) {
+                    wait_mma();
+                    if (!ok) break;
+                }
+                ff_granule(gHi, gLo, row, 2 * cq, x, SPLIT);
+                ff_granule(gHi, gLo, row, 2 * cq + 1, x + 8, SPLIT);
+                sync_async();
+                if (tid == 0) {
+                    ff_mma(tmem + kColY, uG, uG2, uKV + 8192 * c, uKV + kD * kF * 2 + 8192 * c, kD, SPLIT, c > 0);
+                    tc::mma_commit(mb);
+                }
+            }
+            if (!ok) break;
+            wait_mma();
+            if (!ok) break;
+            {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColY + 16 * cq, r16);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = 16 * cq + j;
+                    sH[row * kHS + c] += __uint_as_float(r16[j]) + __ldg(g.b2[l] + c);
+                }
+            }
+            __syncthreads();
+        }
+        if (!ok) break;
+        // ---- final LayerNorm, head logits and the masked log-softmax of the
+        // token each row predicts (position t predicts token t)
+        if (tid < kRows) {
+            float lp = 0.f;
+            const int sl = tid / T, t = tid - sl * T;
+            const int64_t i = s0 + sl;
+            if (tid < rows_used && i < g.n) {
+                const uint64_t *xi = g.x + i * g.W;
+                float v[kD];
+                float s = 0.f;
+#pragma unroll
+                for (int c = 0; c < kD; ++c) {
+                    v[c] = sH[tid * kHS + c];
+                    s += v[c];
+                }
+                const float mu = s / float(kD);
+                float q = 0.f;
+#pragma unroll
+                for (int c = 0; c < kD; ++c) q += (v[c] - mu) * (v[c] - mu);
+                const float rs = 1.0f / sqrtf(q / float(kD) + 1e-5f);
+                float z[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) z[k] = __ldg(g.hb + k);
+#pragma unroll
+                for (int c = 0; c < kD; ++c) {
+                    const float y = (v[c] - mu) * rs * __ldg(g.lnf_g + c) + __ldg(g.lnf_b + c);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) z[k] += y * __ldg(g.hw + k * kD + c);
+                }
+                int ca = 0, cb = 0;  // electrons on the orbitals of tokens < t
+                for (int p2 = T - t; p2 < T; ++p2) {
+                    ca += ff_bit(xi, 2 * p2);
+                    cb += ff_bit(xi, 2 * p2 + 1);
+                }
+                const int rem = T - 1 - t;
+                bool okv[4];
+                float zmax = -INFINITY;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int a = ca + (k & 1), b = cb + (k >> 1);
+                    okv[k] = a <= g.n_alpha && b <= g.n_beta && a + rem >= g.n_alpha && b + rem >= g.n_beta;
+                    if (okv[k] && z[k] > zmax) zmax = z[k];
+                }
+                float se = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (okv[k]) se += expf(z[k] - zmax);
+                const int tk = ff_token(xi, T, t);
+                lp = okv[tk] ? z[tk] - (zmax + logf(se)) : -INFINITY;
+            }
+            sLP[tid] = lp;
+        }
+        __syncthreads();
+        if (tid < g.spt) {
+            const int64_t i = s0 + tid;
+            if (i < g.n) {
+                float sum = 0.f;
+                bool bad = false;
+                for (int t = 0; t < T; ++t) {
+                    const float v = sLP[tid * T + t];
+                    if (v == -INFINITY)
+                        bad = true;
+                    else
+                        sum += v;
+                }
+                g.out[i].x = bad ? -(double)INFINITY : 0.5 * (double)sum;
+                if (bad) record_status(g.st, NNQS_E_SECTOR, g.row_offset + i);
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok && tid == 0) {
+        if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -13;
+        // weight copies still in flight land (bounded) before the CTA ends
+        for (; d_wb < n_wb; ++d_wb) tc::mbar_wait(bWB, d_wb & 1u);
+        for (; d_wo < n_wo; ++d_wo) tc::mbar_wait(bWO, d_wo & 1u);
+        for (; d_w2 < n_w2; ++d_w2) tc::mbar_wait(bW2, d_w2 & 1u);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ff::kTmemCols)
+                     : "memory");
+    }
+}
+
+template <bool SPLIT, int DH>
+nnqs_status launch_fused(const FusedFwdArgs &a, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_fused<SPLIT, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           ff::kSmem));
+        attr = true;
+    }
+    const int64_t grid = std::min<int64_t>(a.n_tiles, num_sms());
+    NNQS_LAUNCH("k_fwd_fused", s, (k_fwd_fused<SPLIT, DH><<<(unsigned)grid, ff::kThreads, ff::kSmem, s>>>(a)));
+    return NNQS_OK;
+}
+
+}  // namespace
+
+bool fused_fwd_supported(int d, int F, int dh, int T, int L) {
+    return d == ff::kD && F == ff::kF && (dh == 8 || dh == 16) && T >= 1 && T <= 64 && L >= 1 &&
+           L <= kFusedMaxLayers;
+}
+
+nnqs_status fused_fwd_launch(const FusedFwdArgs &a, bool split, int dh, cudaStream_t s) {
+    if (a.n <= 0) return NNQS_OK;
+    if (a.spt < 1 || a.spt * a.T > ff::kRows) return set_error(NNQS_E_INVAL, "fused forward: bad tile shape");
+    note_work("k_fwd_fused",
+              double(a.n) * a.T * a.L * 2.0 * (4.0 * ff::kD * ff::kD + 2.0 * ff::kD * ff::kF),
+              double(a.n) * (8.0 * a.W + 8.0));
+    if (split) return dh == 8 ? launch_fused<true, 8>(a, s) : launch_fused<true, 16>(a, s);
+    return dh == 8 ? launch_fused<false, 8>(a, s) : launch_fused<false, 16>(a, s);
+}
+
+}  // namespace nnqs

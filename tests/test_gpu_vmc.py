@@ -331,11 +331,15 @@ def test_energy_function_autograd(n12):
         step = float(fp[k].item()) - float(fm[k].item())
         fd = (surrogate(fp) - surrogate(fm)) / step
         assert abs(fd - g[k]) <= 1e-5 * max(1.0, abs(fd)) + 1e-7, (k, fd, g[k])
+    # torch.optim consumes the gradient: Adam's first step moves every
+    # parameter whose gradient is well above eps by lr
     opt = torch.optim.Adam([p], lr=1e-3)
     before = p.detach().clone()
     opt.step()
     moved = (p.detach() - before).abs()
-    assert torch.all(moved[p.grad != 0] > 0)
+    big = p.grad.abs() > 1e-5
+    assert big.sum() > 1000
+    assert torch.allclose(moved[big], torch.full_like(moved[big], 1e-3), rtol=1e-2)
 
 
 def test_replica_samples_differ():
