@@ -3235,6 +3235,41 @@ FusedFwdArgs fused_args(const nnqs_model *M, const Views<float> &V, const TcWeig
     return a;
 }
 
+// Forward of C samples keeping every activation for the reverse mode: the
+// fused kernel in keep mode where it applies (BF16 / split BF16, d = 64),
+// else the layer-by-layer forward.
+template <class R>
+nnqs_status forward_keep(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
+                         double2 *out, DevStatus *st, int64_t row_offset, const TcWeights *tcw, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        if (tcw && !tcw->fp8 && A.keep && fused_fwd_enabled() && fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L)) {
+            FusedFwdArgs a = fused_args(M, V, *tcw, x, C, out, st, row_offset);
+            a.rows = C * M->T;
+            a.hbuf = A.hbuf;
+            a.a = A.a;
+            a.a2 = A.a2;
+            a.hmid = A.hmid;
+            a.o = A.o;
+            a.qkv = A.qkv;
+            a.u = A.u;
+            a.gu = A.gu;
+            a.mean1 = A.mean1;
+            a.rstd1 = A.rstd1;
+            a.mean2 = A.mean2;
+            a.rstd2 = A.rstd2;
+            a.lse = A.lse;
+            a.hf = A.hf;
+            a.meanf = A.meanf;
+            a.rstdf = A.rstdf;
+            a.pi = A.pi;
+            a.tok_out = A.tok;
+            NNQS_TRY(fused_fwd_launch(a, tcw->split, M->dh, s));
+            return phase_mlp<R>(M, V, x, C, A, out, tcw, s);
+        }
+    }
+    return forward_chunk<R>(M, V, x, C, A, out, st, row_offset, tcw, s);
+}
+
 template <class R>
 nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, double *out, Arena &ws,
                          DevStatus *st, int tcm, cudaStream_t s) {
@@ -3295,7 +3330,7 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
         const int64_t cn = std::min(C, n - c0);
         const uint64_t *xc = x + c0 * M->W;
         // recompute the forward (tensor cores for NNQS_MIXED), keeping activations
-        NNQS_TRY(forward_chunk<R>(M, V, xc, cn, A, G.lp, st, c0, tensor ? &tcw : nullptr, s));
+        NNQS_TRY(forward_keep<R>(M, V, xc, cn, A, G.lp, st, c0, tensor ? &tcw : nullptr, s));
         NNQS_TRY(backward_chunk<R>(M, V, xc, cn, A, G, reinterpret_cast<const double2 *>(seed) + c0, gacc,
                                    tensor ? &tcw : nullptr, s));
     }
@@ -3328,7 +3363,7 @@ nnqs_status fwd_bwd_impl(const nnqs_model *M, const float *params, const uint64_
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
     if (tensor) NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
     const Views<R> V = make_views<R>(M, pr);
-    NNQS_TRY(forward_chunk<R>(M, V, x, n, A, reinterpret_cast<double2 *>(lp_out), st, 0, tensor ? &tcw : nullptr, s));
+    NNQS_TRY(forward_keep<R>(M, V, x, n, A, reinterpret_cast<double2 *>(lp_out), st, 0, tensor ? &tcw : nullptr, s));
     NNQS_TRY(between());
     NNQS_TRY(backward_chunk<R>(M, V, x, n, A, G, reinterpret_cast<const double2 *>(seed), gacc,
                                tensor ? &tcw : nullptr, s));

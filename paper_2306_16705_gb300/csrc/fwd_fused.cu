@@ -81,31 +81,48 @@ __device__ __forceinline__ void ff_granule(uint8_t *hi, uint8_t *lo, int r, int 
     }
 }
 
-// LayerNorm (eps 1e-5) of residual row r into the A tile
-__device__ __forceinline__ void ff_layernorm(const float *sH, int r, const float *__restrict__ gam,
-                                             const float *__restrict__ bet, uint8_t *hi, uint8_t *lo, bool split) {
-    float v[ff::kD];
+// LayerNorm (eps 1e-5) of residual rows by 4 lanes per row: warp w takes rows
+// 8 w .. 8 w + 7, lane 4 k + p the 16 columns 16 p .. of row 8 w + k.  The
+// normalised values y (FP32) are returned for stores; the A tile gets them as
+// BF16 (hi / lo) when `hi` is not null.  With `keep`, the row's input, y and
+// (by the p = 0 lane) mean / rstd go to global memory row `grow`.
+struct LnOut {
+    float y[16];
+    float mu, rs;
+};
+__device__ __forceinline__ LnOut ff_layernorm(const float *sH, int r, int p, const float *__restrict__ gam,
+                                              const float *__restrict__ bet, uint8_t *hi, uint8_t *lo, bool split) {
+    LnOut o;
+    float v[16];
     float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < ff::kD; ++c) {
-        v[c] = sH[r * ff::kHS + c];
+    for (int c = 0; c < 16; ++c) {
+        v[c] = sH[r * ff::kHS + 16 * p + c];
         s += v[c];
     }
-    const float mu = s / float(ff::kD);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    o.mu = s / float(ff::kD);
     float q = 0.f;
 #pragma unroll
-    for (int c = 0; c < ff::kD; ++c) q += (v[c] - mu) * (v[c] - mu);
-    const float rs = 1.0f / sqrtf(q / float(ff::kD) + 1e-5f);
+    for (int c = 0; c < 16; ++c) q += (v[c] - o.mu) * (v[c] - o.mu);
+    q += __shfl_xor_sync(0xffffffffu, q, 1);
+    q += __shfl_xor_sync(0xffffffffu, q, 2);
+    o.rs = 1.0f / sqrtf(q / float(ff::kD) + 1e-5f);
 #pragma unroll
-    for (int gi = 0; gi < 8; ++gi) {
-        float y[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int c = 8 * gi + e;
-            y[e] = (v[c] - mu) * rs * __ldg(gam + c) + __ldg(bet + c);
-        }
-        ff_granule(hi, lo, r, gi, y, split);
+    for (int c = 0; c < 16; ++c) o.y[c] = (v[c] - o.mu) * o.rs * __ldg(gam + 16 * p + c) + __ldg(bet + 16 * p + c);
+    if (hi) {
+        ff_granule(hi, lo, r, 2 * p, o.y, split);
+        ff_granule(hi, lo, r, 2 * p + 1, o.y + 8, split);
     }
+    return o;
+}
+
+// 16 floats to global memory (16-byte aligned)
+__device__ __forceinline__ void ff_st16(float *dst, const float *v) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        reinterpret_cast<float4 *>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
 }
 
 // 4 K steps (K = 64) of one 128 x N product into TMEM: with split operands
@@ -135,7 +152,7 @@ __device__ __forceinline__ int ff_token(const uint64_t *x, int T, int t) {
     return ff_bit(x, 2 * p) + 2 * ff_bit(x, 2 * p + 1);
 }
 
-template <bool SPLIT, int DH>
+template <bool SPLIT, int DH, bool KEEP>
 __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_constant__ FusedFwdArgs g) {
     using namespace ff;
     constexpr int H = kD / DH;
@@ -256,7 +273,24 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
         __syncthreads();
         for (int l = 0; l < g.L && ok; ++l) {
             // ---- LN1 -> A; qkv product
-            if (tid < kRows) ff_layernorm(sH, tid, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
+            {
+                const int lr = 8 * warp + (lane >> 2), lq = lane & 3;
+                const LnOut n1 = ff_layernorm(sH, lr, lq, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
+                if constexpr (KEEP) {
+                    const int64_t gr = s0 * T + lr, at = (int64_t)l * g.rows + gr;
+                    if (lr < rows_used && gr < g.rows) {
+                        float hv[16];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + 16 * lq + c];
+                        ff_st16(g.hbuf + at * kD + 16 * lq, hv);
+                        ff_st16(g.a + at * kD + 16 * lq, n1.y);
+                        if (lq == 0) {
+                            g.mean1[at] = n1.mu;
+                            g.rstd1[at] = n1.rs;
+                        }
+                    }
+                }
+            }
             wait_bar(bWB, d_wb);
             sync_async();
             if (!ok) break;
@@ -284,6 +318,11 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                         v.z = __uint_as_float(r16[4 * p + 2]) + __ldg(bq + tc0 + 4 * p + 2);
                         v.w = __uint_as_float(r16[4 * p + 3]) + __ldg(bq + tc0 + 4 * p + 3);
                         *reinterpret_cast<float4 *>(sKV + kv_at(row, c)) = v;
+                        if constexpr (KEEP) {
+                            const int64_t gr = s0 * T + row;
+                            if (row < rows_used && gr < g.rows)
+                                *reinterpret_cast<float4 *>(g.qkv + ((int64_t)l * g.rows + gr) * kQKV + tc0 + 4 * p) = v;
+                        }
                     }
                 }
             }
@@ -300,8 +339,14 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     const float *bq = g.bqkv[l];
                     float qv[16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) qv[c] = (__uint_as_float(r16[c]) + __ldg(bq + 16 * cq + c)) * qscale;
+                    for (int c = 0; c < 16; ++c) qv[c] = __uint_as_float(r16[c]) + __ldg(bq + 16 * cq + c);
                     const int sl = row / T, t = row - sl * T, r0 = sl * T;
+                    const int64_t gr = s0 * T + row;
+                    if constexpr (KEEP) {
+                        if (gr < g.rows) ff_st16(g.qkv + ((int64_t)l * g.rows + gr) * kQKV + 16 * cq, qv);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) qv[c] *= qscale;
                     float m[HPT], ls[HPT];
 #pragma unroll
                     for (int h = 0; h < HPT; ++h) {
@@ -338,6 +383,17 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
 #pragma unroll
                         for (int c = 0; c < DH; ++c) o[h * DH + c] *= inv;
                     }
+                    if constexpr (KEEP) {
+                        if (gr < g.rows) {
+                            ff_st16(g.o + ((int64_t)l * g.rows + gr) * kD + 16 * cq, o);
+                            // log-sum-exp of each head's scores, natural units
+                            const int64_t i = s0 + sl;
+#pragma unroll
+                            for (int h = 0; h < HPT; ++h)
+                                g.lse[(((int64_t)l * g.n + i) * H + cq * HPT + h) * T + t] =
+                                    (m[h] + log2f(ls[h])) * 0.69314718055994530942f;
+                        }
+                    }
                 }
             }
             tc::fence_async_smem();  // (every thread: its generic accesses before the async copy below)
@@ -358,15 +414,34 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             {
                 uint32_t r16[16];
                 tc::tmem_ld16(tl + kColO + 16 * cq, r16);
+                float hv[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int c = 16 * cq + j;
-                    sH[row * kHS + c] += __uint_as_float(r16[j]) + __ldg(g.bo[l] + c);
+                    hv[j] = sH[row * kHS + c] + (__uint_as_float(r16[j]) + __ldg(g.bo[l] + c));
+                    sH[row * kHS + c] = hv[j];
+                }
+                if constexpr (KEEP) {
+                    const int64_t gr = s0 * T + row;
+                    if (row < rows_used && gr < g.rows) ff_st16(g.hmid + ((int64_t)l * g.rows + gr) * kD + 16 * cq, hv);
                 }
             }
             __syncthreads();
             // ---- LN2 -> A; the four FFN-in chunks issued together
-            if (tid < kRows) ff_layernorm(sH, tid, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
+            {
+                const int lr = 8 * warp + (lane >> 2), lq = lane & 3;
+                const LnOut n2 = ff_layernorm(sH, lr, lq, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
+                if constexpr (KEEP) {
+                    const int64_t gr = s0 * T + lr, at = (int64_t)l * g.rows + gr;
+                    if (lr < rows_used && gr < g.rows) {
+                        ff_st16(g.a2 + at * kD + 16 * lq, n2.y);
+                        if (lq == 0) {
+                            g.mean2[at] = n2.mu;
+                            g.rstd2[at] = n2.rs;
+                        }
+                    }
+                }
+            }
             wait_bar(bWB, d_wb);
             sync_async();
             if (!ok) break;
@@ -394,9 +469,20 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                 {
                     uint32_t r16[16];
                     tc::tmem_ld16(tl + kColU + 64 * c + 16 * cq, r16);
+                    float uv[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        x[j] = tc::gelu_f(__uint_as_float(r16[j]) + __ldg(g.b1[l] + 64 * c + 16 * cq + j));
+                    for (int j = 0; j < 16; ++j) {
+                        uv[j] = __uint_as_float(r16[j]) + __ldg(g.b1[l] + 64 * c + 16 * cq + j);
+                        x[j] = tc::gelu_f(uv[j]);
+                    }
+                    if constexpr (KEEP) {
+                        const int64_t gr = s0 * T + row;
+                        if (row < rows_used && gr < g.rows) {
+                            const int64_t at = ((int64_t)l * g.rows + gr) * kF + 64 * c + 16 * cq;
+                            ff_st16(g.u + at, uv);
+                            ff_st16(g.gu + at, x);
+                        }
+                    }
                 }
                 if (c > 0) {
                     wait_mma();
@@ -426,56 +512,69 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
         }
         if (!ok) break;
         // ---- final LayerNorm, head logits and the masked log-softmax of the
-        // token each row predicts (position t predicts token t)
-        if (tid < kRows) {
-            float lp = 0.f;
-            const int sl = tid / T, t = tid - sl * T;
-            const int64_t i = s0 + sl;
-            if (tid < rows_used && i < g.n) {
-                const uint64_t *xi = g.x + i * g.W;
-                float v[kD];
-                float s = 0.f;
+        // token each row predicts (position t predicts token t): 4 lanes per row
+        {
+            const int lr = 8 * warp + (lane >> 2), lq = lane & 3;
+            const LnOut nf = ff_layernorm(sH, lr, lq, g.lnf_g, g.lnf_b, nullptr, nullptr, false);
+            float z[4];
 #pragma unroll
-                for (int c = 0; c < kD; ++c) {
-                    v[c] = sH[tid * kHS + c];
-                    s += v[c];
-                }
-                const float mu = s / float(kD);
-                float q = 0.f;
+            for (int k = 0; k < 4; ++k) {
+                float a = 0.f;
 #pragma unroll
-                for (int c = 0; c < kD; ++c) q += (v[c] - mu) * (v[c] - mu);
-                const float rs = 1.0f / sqrtf(q / float(kD) + 1e-5f);
-                float z[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) z[k] = __ldg(g.hb + k);
-#pragma unroll
-                for (int c = 0; c < kD; ++c) {
-                    const float y = (v[c] - mu) * rs * __ldg(g.lnf_g + c) + __ldg(g.lnf_b + c);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) z[k] += y * __ldg(g.hw + k * kD + c);
-                }
-                int ca = 0, cb = 0;  // electrons on the orbitals of tokens < t
-                for (int p2 = T - t; p2 < T; ++p2) {
-                    ca += ff_bit(xi, 2 * p2);
-                    cb += ff_bit(xi, 2 * p2 + 1);
-                }
-                const int rem = T - 1 - t;
-                bool okv[4];
-                float zmax = -INFINITY;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int a = ca + (k & 1), b = cb + (k >> 1);
-                    okv[k] = a <= g.n_alpha && b <= g.n_beta && a + rem >= g.n_alpha && b + rem >= g.n_beta;
-                    if (okv[k] && z[k] > zmax) zmax = z[k];
-                }
-                float se = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (okv[k]) se += expf(z[k] - zmax);
-                const int tk = ff_token(xi, T, t);
-                lp = okv[tk] ? z[tk] - (zmax + logf(se)) : -INFINITY;
+                for (int c = 0; c < 16; ++c) a += nf.y[c] * __ldg(g.hw + k * kD + 16 * lq + c);
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a += __shfl_xor_sync(0xffffffffu, a, 2);
+                z[k] = a + __ldg(g.hb + k);
             }
-            sLP[tid] = lp;
+            const int sl = lr / T, t = lr - sl * T;
+            const int64_t i = s0 + sl, gr = s0 * T + lr;
+            const bool valid = lr < rows_used && i < g.n;
+            if constexpr (KEEP) {
+                if (valid) {
+                    float hv[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + 16 * lq + c];
+                    ff_st16(g.hbuf + ((int64_t)g.L * g.rows + gr) * kD + 16 * lq, hv);
+                    ff_st16(g.hf + gr * kD + 16 * lq, nf.y);
+                    if (lq == 0) {
+                        g.meanf[gr] = nf.mu;
+                        g.rstdf[gr] = nf.rs;
+                    }
+                }
+            }
+            if (lq == 0) {
+                float lp = 0.f;
+                if (valid) {
+                    const uint64_t *xi = g.x + i * g.W;
+                    int ca = 0, cb = 0;  // electrons on the orbitals of tokens < t
+                    for (int p2 = T - t; p2 < T; ++p2) {
+                        ca += ff_bit(xi, 2 * p2);
+                        cb += ff_bit(xi, 2 * p2 + 1);
+                    }
+                    const int rem = T - 1 - t;
+                    bool okv[4];
+                    float zmax = -INFINITY;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int a = ca + (k & 1), b = cb + (k >> 1);
+                        okv[k] = a <= g.n_alpha && b <= g.n_beta && a + rem >= g.n_alpha && b + rem >= g.n_beta;
+                        if (okv[k] && z[k] > zmax) zmax = z[k];
+                    }
+                    float se = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (okv[k]) se += expf(z[k] - zmax);
+                    const float lse = zmax + logf(se);
+                    const int tk = ff_token(xi, T, t);
+                    lp = okv[tk] ? z[tk] - lse : -INFINITY;
+                    if constexpr (KEEP) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) g.pi[gr * 4 + k] = okv[k] ? expf(z[k] - lse) : 0.f;
+                        g.tok_out[gr] = (uint8_t)tk;
+                    }
+                }
+                sLP[lr] = lp;
+            }
         }
         __syncthreads();
         if (tid < g.spt) {
@@ -512,17 +611,23 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
     }
 }
 
-template <bool SPLIT, int DH>
+template <bool SPLIT, int DH, bool KEEP>
 nnqs_status launch_fused(const FusedFwdArgs &a, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_fused<SPLIT, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_fused<SPLIT, DH, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            ff::kSmem));
         attr = true;
     }
     const int64_t grid = std::min<int64_t>(a.n_tiles, num_sms());
-    NNQS_LAUNCH("k_fwd_fused", s, (k_fwd_fused<SPLIT, DH><<<(unsigned)grid, ff::kThreads, ff::kSmem, s>>>(a)));
+    NNQS_LAUNCH("k_fwd_fused", s, (k_fwd_fused<SPLIT, DH, KEEP><<<(unsigned)grid, ff::kThreads, ff::kSmem, s>>>(a)));
     return NNQS_OK;
+}
+
+template <bool KEEP>
+nnqs_status launch_fused_keep(const FusedFwdArgs &a, bool split, int dh, cudaStream_t s) {
+    if (split) return dh == 8 ? launch_fused<true, 8, KEEP>(a, s) : launch_fused<true, 16, KEEP>(a, s);
+    return dh == 8 ? launch_fused<false, 8, KEEP>(a, s) : launch_fused<false, 16, KEEP>(a, s);
 }
 
 }  // namespace
@@ -538,8 +643,8 @@ nnqs_status fused_fwd_launch(const FusedFwdArgs &a, bool split, int dh, cudaStre
     note_work("k_fwd_fused",
               double(a.n) * a.T * a.L * 2.0 * (4.0 * ff::kD * ff::kD + 2.0 * ff::kD * ff::kF),
               double(a.n) * (8.0 * a.W + 8.0));
-    if (split) return dh == 8 ? launch_fused<true, 8>(a, s) : launch_fused<true, 16>(a, s);
-    return dh == 8 ? launch_fused<false, 8>(a, s) : launch_fused<false, 16>(a, s);
+    if (a.hbuf) return launch_fused_keep<true>(a, split, dh, s);
+    return launch_fused_keep<false>(a, split, dh, s);
 }
 
 }  // namespace nnqs
