@@ -3183,15 +3183,19 @@ size_t workspace_impl(const nnqs_model *M, int64_t n, bool backward, bool tensor
     return a.used + 1024;
 }
 
-// NNQS_FUSED_FORWARD=0 in the environment keeps the layer-by-layer forward
-// (for comparisons); read once
-bool fused_fwd_enabled() {
-    static const bool on = [] {
+// Which forwards run fused (fwd_fused.cu), from NNQS_FUSED_FORWARD in the
+// environment (read once): 0 = none (the layer-by-layer forward everywhere,
+// for comparisons), 1 = log psi only (nnqs_logpsi, exact mode; the default),
+// 2 = also the reverse mode's forward, with its activations written out.
+int fused_fwd_level() {
+    static const int level = [] {
         const char *e = std::getenv("NNQS_FUSED_FORWARD");
-        return !(e && e[0] == '0');
+        if (!e || !e[0]) return 1;
+        return e[0] == '0' ? 0 : e[0] == '2' ? 2 : 1;
     }();
-    return on;
+    return level;
 }
+bool fused_fwd_enabled() { return fused_fwd_level() >= 1; }
 
 // arguments of the fused forward for C samples x (FP32 parameters V, BF16
 // weight images of tcw)
@@ -3242,8 +3246,10 @@ template <class R>
 nnqs_status forward_keep(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
                          double2 *out, DevStatus *st, int64_t row_offset, const TcWeights *tcw, cudaStream_t s) {
     if constexpr (sizeof(R) == 4) {
-        if (tcw && !tcw->fp8 && A.keep && fused_fwd_enabled() && fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L)) {
+        if (tcw && !tcw->fp8 && A.keep && fused_fwd_level() >= 2 &&
+            fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L)) {
             FusedFwdArgs a = fused_args(M, V, *tcw, x, C, out, st, row_offset);
+            if (!fused_fwd_aligned(a)) return forward_chunk<R>(M, V, x, C, A, out, st, row_offset, tcw, s);
             a.rows = C * M->T;
             a.hbuf = A.hbuf;
             a.a = A.a;
@@ -3295,9 +3301,12 @@ nnqs_status forward_impl(const nnqs_model *M, const float *params, const uint64_
         double2 *oc = reinterpret_cast<double2 *>(out) + c0;
         if constexpr (sizeof(R) == 4) {
             if (fused) {
-                NNQS_TRY(fused_fwd_launch(fused_args(M, V, tcw, x + c0 * M->W, cn, oc, st, c0), tcw.split, M->dh, s));
-                NNQS_TRY(phase_mlp<R>(M, V, x + c0 * M->W, cn, A, oc, &tcw, s));
-                continue;
+                const FusedFwdArgs fa = fused_args(M, V, tcw, x + c0 * M->W, cn, oc, st, c0);
+                if (fused_fwd_aligned(fa)) {
+                    NNQS_TRY(fused_fwd_launch(fa, tcw.split, M->dh, s));
+                    NNQS_TRY(phase_mlp<R>(M, V, x + c0 * M->W, cn, A, oc, &tcw, s));
+                    continue;
+                }
             }
         }
         NNQS_TRY(forward_chunk<R>(M, V, x + c0 * M->W, cn, A, oc, st, c0, tensor ? &tcw : nullptr, s));

@@ -15,7 +15,8 @@
 //   token -> log|psi| = 1/2 sum over the sample's rows.
 // Per sample only its bitstring is read and one double written; the phase
 // MLP runs separately.  The arithmetic is the unfused FP32/BF16 path's up to
-// the order of floating-point sums (not bit-identical to it).
+// the order of floating-point sums and the GELU's erf (ff_gelu; not
+// bit-identical to it).
 //
 // Shared memory (1024-aligned base):
 //   [0, 32K)      A tile hi / lo  (LN output, attention output)
@@ -60,6 +61,34 @@ __device__ __forceinline__ float ff_ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// 16 consecutive floats of a 16-byte aligned parameter vector
+__device__ __forceinline__ void ff_ld16(const float *__restrict__ p, float (&v)[16]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + k);
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
+    }
+}
+
+// GELU x Phi(x) = x (1 + erf(x / sqrt 2)) / 2 with erf from the rational
+// approximation of Abramowitz and Stegun, Handbook of Mathematical Functions
+// (1964), eq. 7.1.26: erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5))))
+// e^{-z^2}, t = 1 / (1 + p z) for z >= 0, odd in z, absolute error at most
+// 1.5e-7 -- far below the 2^-16 relative resolution of the split-BF16 operand
+// the value feeds; branch-free, two special-function instructions.
+__device__ __forceinline__ float ff_gelu(float x) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float e = ff_ex2(-(z * z) * 1.44269504088896340736f);
+    const float erf_abs = 1.0f - poly * e;
+    return 0.5f * x * (1.0f + copysignf(erf_abs, x));
 }
 
 // element (r, c) of the tile's k | v rows: 16-byte pieces XOR-rotated by the
@@ -109,8 +138,11 @@ __device__ __forceinline__ LnOut ff_layernorm(const float *sH, int r, int p, con
     q += __shfl_xor_sync(0xffffffffu, q, 1);
     q += __shfl_xor_sync(0xffffffffu, q, 2);
     o.rs = 1.0f / sqrtf(q / float(ff::kD) + 1e-5f);
+    float gv[16], bv[16];
+    ff_ld16(gam + 16 * p, gv);
+    ff_ld16(bet + 16 * p, bv);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) o.y[c] = (v[c] - o.mu) * o.rs * __ldg(gam + 16 * p + c) + __ldg(bet + 16 * p + c);
+    for (int c = 0; c < 16; ++c) o.y[c] = (v[c] - o.mu) * o.rs * gv[c] + bv[c];
     if (hi) {
         ff_granule(hi, lo, r, 2 * p, o.y, split);
         ff_granule(hi, lo, r, 2 * p + 1, o.y + 8, split);
@@ -309,14 +341,16 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     const int tc0 = 64 + 32 * cq + 16 * hf;  // TMEM column = bias index
                     uint32_t r16[16];
                     tc::tmem_ld16(tl + tc0, r16);
+                    float bv[16];
+                    ff_ld16(bq + tc0, bv);
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
                         const int c = tc0 - 64 + 4 * p;  // column of k | v
                         float4 v;
-                        v.x = __uint_as_float(r16[4 * p]) + __ldg(bq + tc0 + 4 * p);
-                        v.y = __uint_as_float(r16[4 * p + 1]) + __ldg(bq + tc0 + 4 * p + 1);
-                        v.z = __uint_as_float(r16[4 * p + 2]) + __ldg(bq + tc0 + 4 * p + 2);
-                        v.w = __uint_as_float(r16[4 * p + 3]) + __ldg(bq + tc0 + 4 * p + 3);
+                        v.x = __uint_as_float(r16[4 * p]) + bv[4 * p];
+                        v.y = __uint_as_float(r16[4 * p + 1]) + bv[4 * p + 1];
+                        v.z = __uint_as_float(r16[4 * p + 2]) + bv[4 * p + 2];
+                        v.w = __uint_as_float(r16[4 * p + 3]) + bv[4 * p + 3];
                         *reinterpret_cast<float4 *>(sKV + kv_at(row, c)) = v;
                         if constexpr (KEEP) {
                             const int64_t gr = s0 * T + row;
@@ -338,8 +372,9 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                 if (row < rows_used) {
                     const float *bq = g.bqkv[l];
                     float qv[16];
+                    ff_ld16(bq + 16 * cq, qv);
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) qv[c] = __uint_as_float(r16[c]) + __ldg(bq + 16 * cq + c);
+                    for (int c = 0; c < 16; ++c) qv[c] += __uint_as_float(r16[c]);
                     const int sl = row / T, t = row - sl * T, r0 = sl * T;
                     const int64_t gr = s0 * T + row;
                     if constexpr (KEEP) {
@@ -414,11 +449,12 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             {
                 uint32_t r16[16];
                 tc::tmem_ld16(tl + kColO + 16 * cq, r16);
-                float hv[16];
+                float hv[16], bv[16];
+                ff_ld16(g.bo[l] + 16 * cq, bv);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int c = 16 * cq + j;
-                    hv[j] = sH[row * kHS + c] + (__uint_as_float(r16[j]) + __ldg(g.bo[l] + c));
+                    hv[j] = sH[row * kHS + c] + (__uint_as_float(r16[j]) + bv[j]);
                     sH[row * kHS + c] = hv[j];
                 }
                 if constexpr (KEEP) {
@@ -470,10 +506,11 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     uint32_t r16[16];
                     tc::tmem_ld16(tl + kColU + 64 * c + 16 * cq, r16);
                     float uv[16];
+                    ff_ld16(g.b1[l] + 64 * c + 16 * cq, uv);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        uv[j] = __uint_as_float(r16[j]) + __ldg(g.b1[l] + 64 * c + 16 * cq + j);
-                        x[j] = tc::gelu_f(uv[j]);
+                        uv[j] += __uint_as_float(r16[j]);
+                        x[j] = ff_gelu(uv[j]);
                     }
                     if constexpr (KEEP) {
                         const int64_t gr = s0 * T + row;
@@ -502,10 +539,12 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             {
                 uint32_t r16[16];
                 tc::tmem_ld16(tl + kColY + 16 * cq, r16);
+                float bv[16];
+                ff_ld16(g.b2[l] + 16 * cq, bv);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int c = 16 * cq + j;
-                    sH[row * kHS + c] += __uint_as_float(r16[j]) + __ldg(g.b2[l] + c);
+                    sH[row * kHS + c] += __uint_as_float(r16[j]) + bv[j];
                 }
             }
             __syncthreads();
@@ -519,9 +558,10 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             float z[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                float a = 0.f;
+                float a = 0.f, wv[16];
+                ff_ld16(g.hw + k * kD + 16 * lq, wv);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) a += nf.y[c] * __ldg(g.hw + k * kD + 16 * lq + c);
+                for (int c = 0; c < 16; ++c) a += nf.y[c] * wv[c];
                 a += __shfl_xor_sync(0xffffffffu, a, 1);
                 a += __shfl_xor_sync(0xffffffffu, a, 2);
                 z[k] = a + __ldg(g.hb + k);
@@ -631,6 +671,16 @@ nnqs_status launch_fused_keep(const FusedFwdArgs &a, bool split, int dh, cudaStr
 }
 
 }  // namespace
+
+bool fused_fwd_aligned(const FusedFwdArgs &a) {
+    auto al = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    bool ok = al(a.tok) && al(a.pos) && al(a.lnf_g) && al(a.lnf_b) && al(a.hw);
+    for (int l = 0; l < a.L; ++l)
+        ok = ok && al(a.ln1g[l]) && al(a.ln1b[l]) && al(a.bqkv[l]) && al(a.bo[l]) && al(a.ln2g[l]) &&
+             al(a.ln2b[l]) && al(a.b1[l]) && al(a.b2[l]) && al(a.tqkv[l]) && al(a.to[l]) && al(a.t1[l]) &&
+             al(a.t2[l]);
+    return ok;
+}
 
 bool fused_fwd_supported(int d, int F, int dh, int T, int L) {
     return d == ff::kD && F == ff::kF && (dh == 8 || dh == 16) && T >= 1 && T <= 64 && L >= 1 &&

@@ -41,6 +41,8 @@ struct FusedFwdArgs {
 
 // d = 64, FFN width 256, head dimension 8 or 16, T <= 64, BF16 (split or not)
 bool fused_fwd_supported(int d, int F, int dh, int T, int L);
+// every parameter vector and weight image 16-byte aligned (vector loads, bulk copies)
+bool fused_fwd_aligned(const FusedFwdArgs &a);
 nnqs_status fused_fwd_launch(const FusedFwdArgs &a, bool split, int dh, cudaStream_t s);
 
 }  // namespace nnqs
