@@ -56,6 +56,12 @@ def parse():
     ap.add_argument("--exact-rows", type=int, default=1024,
                     help="rows of the exact-mode side line (0 = skip)")
     ap.add_argument("--n120-steps", type=int, default=3, help="timed steps of the 120-qubit side line (0 = skip)")
+    ap.add_argument("--case", default=None,
+                    choices=["sweep-pairs", "sweep-groups", "logpsi", "logpsi-unfused", "eloc-exact"],
+                    help="time one hot-path call alone (for profiling) instead of the VMC step")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload of --case (n40, n76, n120, n30, n12)")
+    ap.add_argument("--n", type=int, default=16384, help="samples (table rows) of --case")
+    ap.add_argument("--rows", type=int, default=0, help="rows of --case sweeps / exact mode (0 = all)")
     ap.add_argument("--ladder", action="store_true",
                     help="add the local-energy speed-up ladder (Sec. 4.3) to the CPU baseline (about a minute)")
     return ap.parse_args()
@@ -345,22 +351,29 @@ def run_exact_side_line(ham, model, wl, params, x, prec, n_rows, peaks, tflops_p
     del Ud
     B.eloc(ham, rows[:32], None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params, prec=prec)
     torch.cuda.synchronize()
-    B.profile_reset()
-    B.profile_enable(True)
     st = torch.cuda.current_stream()
+    # the call timed alone (CUDA events on the stream), then once more with
+    # every launch bracketed by events for the per-kernel split
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     got = B.eloc(ham, rows, None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params, prec=prec)
     e1.record(st)
     e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    B.profile_reset()
+    B.profile_enable(True)
+    B.eloc(ham, rows, None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params, prec=prec)
+    torch.cuda.synchronize()
     prof = B.profile()
     B.profile_enable(False)
-    t = e0.elapsed_time(e1) / 1e3
+    prof_ms = sum(v["ms"] for v in prof.values())
     ansatz_ms = sum(v["ms"] for k, v in prof.items()
                     if k not in ("k_insert_rows", "k_expand", "k_compact", "k_diag", "k_sweep_exact",
                                  "k_reduce_partials"))
+    # the ansatz's share of the profiled call, applied to the call timed alone
+    ansatz_ms = ansatz_ms / max(prof_ms, 1e-9) * t * 1e3
     fl = model_flops_per_sample(wl) * n_u
-    tc = prof.get("k_tc_gemm", {"flops": 0.0, "ms": 0.0})
+    tc = prof.get("k_fwd_fused") or prof.get("k_tc_gemm") or {"flops": 0.0, "ms": 0.0}
     info = ham.info()
     e64 = B.eloc(ham, rows[:64], None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model, params=params,
                  prec=B.FP64)
@@ -371,12 +384,13 @@ def run_exact_side_line(ham, model, wl, params, x, prec, n_rows, peaks, tflops_p
         "logical_pairs_per_s": n_rows * info["n_terms"] / t,
         "ansatz_ms": ansatz_ms, "ansatz_model_tflops": fl / (ansatz_ms / 1e3) / 1e12,
         "ansatz_frac_of_burst_bf16": fl / (ansatz_ms / 1e3) / 1e12 / tflops_peak,
-        "k_tc_gemm_tflops": tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] else None,
+        "transformer_kernel_tflops": tc["flops"] / (tc["ms"] / 1e3) / 1e12 if tc["ms"] else None,
         "stage_ms": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         "max_abs_diff_vs_fp64_first64": d,
         "max_rel_diff_vs_fp64_first64": d / max(1.0, e64.abs().max().item()),
         "note": "prec " + {B.BF16X3: "bf16x3", B.MIXED: "mixed", B.FP32: "fp32", B.FP64: "fp64", B.FP8: "fp8"}[prec] +
-                "; forward FLOPs = unique coupled states x method FLOPs per sample"}
+                "; ms = the call timed alone; forward FLOPs = unique coupled states x method FLOPs per sample; "
+                "stage_ms and ansatz share from a second, per-launch-profiled call"}
 
 
 def run_n120_side_line(steps, warmup, peaks, clocks_on, local):
@@ -813,8 +827,58 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    """One hot-path call on a named workload, timed alone (three warm-up
+    calls, then the mean of five with CUDA events): the sample-aware sweeps
+    over uniform sector samples with a stand-in log psi table, the ansatz
+    forward (fused, or layer by layer), or exact-mode E_loc of the first rows.
+    For profilers: the kernel of interest runs 8 times (3 warm-up + 5)."""
+    import torch
+
+    from paper_2306_16705_gb300 import binding as B
+    from paper_2306_16705_gb300 import inputs as I
+
+    if args.case == "logpsi-unfused":
+        os.environ["NNQS_FUSED_FORWARD"] = "0"
+    wl = I.WORKLOADS[args.workload]
+    S = I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, args.n, seed=3)
+    x = B.to_device_bits(S)
+    rows = args.rows or args.n
+    prec = {"bf16x3": B.BF16X3, "mixed": B.MIXED, "fp32": B.FP32, "fp64": B.FP64, "fp8": B.FP8}[args.prec]
+    if args.case.startswith("sweep") or args.case == "eloc-exact":
+        h, eri = I.workload_integrals(wl)
+        ham = B.build_pauli(h, eri)
+    if args.case.startswith("sweep"):
+        lp = torch.from_numpy(I.random_logpsi(args.n, seed=4, amp_std=0.1)).cuda()
+        fl = B.SWEEP_PAIRS if args.case == "sweep-pairs" else B.SWEEP_GROUPS
+        call = lambda: B.eloc(ham, x, lp, wl.n_alpha, wl.n_beta, flags=fl, n_rows=rows, check=False)
+    else:
+        model = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+        flat = model.pack(I.workload_params(wl))
+        if args.case == "eloc-exact":
+            call = lambda: B.eloc(ham, x[:rows], None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model,
+                                  params=flat, prec=prec, check=False)
+        else:
+            call = lambda: B.logpsi(model, flat, x, prec, check=False)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(5):
+        call()
+    e1.record(st)
+    e1.synchronize()
+    print(json.dumps({"case": args.case, "workload": args.workload, "n": args.n, "rows": rows, "prec": args.prec,
+                      "ms_per_call": e0.elapsed_time(e1) / 5}), flush=True)
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
