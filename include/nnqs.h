@@ -393,8 +393,11 @@ size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int p
  * children are pruned.  Outputs (device) samples_out [max_unique][W] and
  * weights_out [max_unique]; *n_unique_out (host) = unique samples written,
  * sorted ascending.  Returns NNQS_E_TABLE_FULL if a step holds more than
- * max_unique prefixes.  Synchronises the stream once per step (the width
- * of the next step is data-dependent). */
+ * max_unique prefixes.  With the key/value cache, BF16 or split-BF16
+ * arithmetic, d_model = 64, max_unique <= 65536 and one activation chunk,
+ * the level sizes stay on the device and the stream is synchronised once at
+ * the end (to return *n_unique_out); otherwise once per step (the width of
+ * the next step is data-dependent). */
 nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uint64_t n_samples,
                         uint64_t seed, int prec, int flags, int64_t max_unique,
                         uint64_t *samples_out, uint64_t *weights_out, int64_t *n_unique_out,

@@ -1851,6 +1851,12 @@ struct DecodeArgs {
     int W, n_alpha, n_beta;
     const float *tok_emb, *pos_emb, *lnf_g, *lnf_b, *hw, *hb;
     double *cond;
+    // device-side counts (the sampler's steps without a host round trip):
+    // when n_dev is set, n = *n_dev and g0 = *g0_dev, and the prefixes per CTA
+    // are ceil(n / n_sms) (at most 128) computed on the device; the grid is
+    // sized for the capacity and CTAs past n return at once
+    const int64_t *n_dev, *g0_dev;
+    int n_sms;
 };
 
 // one bulk asynchronous copy global -> shared, completing `bytes` on mbar
@@ -2075,8 +2081,17 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     const uint32_t wb = tc::smem_u32(wbar);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t m0 = blockIdx.x * (int64_t)g.rpc;
-    const int64_t n_cta = min(g.n, m0 + g.rpc);  // rows of this CTA are m0 .. n_cta - 1
+    int64_t n = g.n, g0 = g.g0;
+    int rpc = g.rpc;
+    if (g.n_dev) {
+        n = *g.n_dev;
+        g0 = *g.g0_dev;
+        const int64_t per = (n + g.n_sms - 1) / g.n_sms;
+        rpc = per < 1 ? 1 : (per > kRows ? kRows : (int)per);
+    }
+    const int64_t m0 = blockIdx.x * (int64_t)rpc;
+    if (m0 >= n) return;  // (device-side counts only: a CTA with no rows)
+    const int64_t n_cta = min(n, m0 + rpc);  // rows of this CTA are m0 .. n_cta - 1
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
                      "r"(kTmemCols)
@@ -2202,7 +2217,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
                 const int it = tid + kThreads * i;
                 const int r = it >> 4, gi = it & 15;
                 if (m0 + r < n_cta) {
-                    float *prow = g.pool + ((g.g0 + m0 + r) * g.L + g.l) * (int64_t)kQKV + 64 * c;
+                    float *prow = g.pool + ((g0 + m0 + r) * g.L + g.l) * (int64_t)kQKV + 64 * c;
                     *reinterpret_cast<float4 *>(prow + 4 * gi) =
                         *reinterpret_cast<const float4 *>(slab + r * 64 + 4 * (gi ^ (r & 15)));
                 }
@@ -2216,7 +2231,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         const int hh = tid % H;
         const int r0 = (tid / H) * NR;
         float o[NR][DH];
-        dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g.g0, m0 + r0, m0, n_cta, g.t, g.L, g.l, hh, o);
+        dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g0, m0 + r0, m0, n_cta, g.t, g.L, g.l, hh, o);
 #pragma unroll
         for (int k = 0; k < NR; ++k)
 #pragma unroll
@@ -3436,20 +3451,28 @@ nnqs_status launch_decode_layer(const DecodeArgs &g, cudaStream_t s) {
                                            dec::kSmem));
         attr = true;
     }
-    const unsigned grid = (unsigned)((g.n + g.rpc - 1) / g.rpc);
+    // device-side counts: enough CTAs for any n <= g.n (the capacity)
+    const unsigned grid = g.n_dev ? (unsigned)std::max<int64_t>(g.n_sms, (g.n + dec::kRows - 1) / dec::kRows)
+                                  : (unsigned)((g.n + g.rpc - 1) / g.rpc);
     NNQS_LAUNCH("k_decode_layer", s, (k_decode_layer<SPLIT, DH><<<grid, dec::kThreads, dec::kSmem, s>>>(g)));
     return NNQS_OK;
 }
 
 // one layer of the cached decode for n new tokens (rows h) in one launch
+// n_dev / g0_dev (optional): the counts live on the device; n is then the
+// capacity (an upper bound of *n_dev) and g0 is ignored
 nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
                                float *h, int64_t n, float *pool, const int32_t *anc, int t, int64_t g0, int l,
-                               double *cond, DevStatus *st, cudaStream_t s) {
+                               double *cond, DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
+                               const int64_t *g0_dev = nullptr) {
     if (n == 0) return NNQS_OK;
     const auto &Lw = V.layer[l];
     DecodeArgs g{};
     g.h = h;
     g.n = n;
+    g.n_dev = n_dev;
+    g.g0_dev = g0_dev;
+    g.n_sms = sm_count();
     // prefixes per CTA: once there are more prefixes than SMs every SM gets a
     // CTA (the late steps' attention is bound by memory traffic; the MMA
     // tiles stay 128 rows, the rows past rpc idle)
@@ -3611,6 +3634,23 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
                                          anc + c0 * M->T, ctx->Af, cond + c0 * 4, st, ctx->tensor ? &ctx->tcw : nullptr, s));
         }
     }
+    return NNQS_OK;
+}
+
+bool cond_cached_dev_ok(const nnqs_model *M, const CondCtx *ctx, int64_t cap) {
+    return ctx->prec != NNQS_FP64 && ctx->tensor && decode_fused_ok(M, ctx->tcw) && cap <= ctx->C;
+}
+
+nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, const int64_t *n_dev,
+                                 const int64_t *g0_dev, int64_t cap, int t, const int32_t *anc, double *cond,
+                                 DevStatus *st, cudaStream_t s) {
+    if (t >= kMaxDepth) return set_error(NNQS_E_UNSUPPORTED, "more than 64 tokens");
+    if (!cond_cached_dev_ok(M, ctx, cap)) return set_error(NNQS_E_UNSUPPORTED, "no fused decode for this model");
+    ctx->tcw.st = st;
+    const Views<float> V = make_views<float>(M, static_cast<float *>(ctx->params));
+    for (int l = 0; l < M->L; ++l)
+        NNQS_TRY(decode_layer_fused(M, V, ctx->tcw, prefixes, ctx->Af.hbuf, cap, static_cast<float *>(ctx->pool), anc,
+                                    t, 0, l, cond, st, s, n_dev, g0_dev));
     return NNQS_OK;
 }
 

@@ -70,6 +70,13 @@ nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixe
 // (row stride T) the nodes of prefix i's ancestors at depths 0..t-1
 nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, int64_t n, int t,
                              int64_t g0, const int32_t *anc, double *cond, DevStatus *st, cudaStream_t s);
+// the cached step with the counts on the device (no host round trip):
+// prefixes g0 .. g0 + n - 1 with n = *n_dev <= cap and g0 = *g0_dev; only for
+// the fused decode layer (BF16 / split BF16, d = 64) and cap within one chunk
+bool cond_cached_dev_ok(const nnqs_model *M, const CondCtx *ctx, int64_t cap);
+nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, const int64_t *n_dev,
+                                 const int64_t *g0_dev, int64_t cap, int t, const int32_t *anc, double *cond,
+                                 DevStatus *st, cudaStream_t s);
 void cond_destroy(CondCtx *c);
 
 // eloc_exact.cu

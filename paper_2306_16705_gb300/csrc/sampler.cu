@@ -157,9 +157,15 @@ __device__ uint64_t binomial(uint64_t n, double p, Philox &rng, DevStatus *st) {
 }
 
 // multinomial split of each prefix's count; nchild[i] = children with count > 0
+// n_dev (optional): the count lives on the device; prefixes are then spread
+// block-major (prefix i on block i % gridDim.x), so that the few prefixes of
+// the early steps land on different SMs.  The draws depend on i only.
 __global__ void k_split(const uint64_t *__restrict__ w, const double *__restrict__ cond, int64_t n, int step,
-                        uint64_t seed, uint64_t *__restrict__ counts, int32_t *__restrict__ nchild, DevStatus *st) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                        uint64_t seed, uint64_t *__restrict__ counts, int32_t *__restrict__ nchild, DevStatus *st,
+                        const int64_t *__restrict__ n_dev) {
+    const int64_t i = n_dev ? blockIdx.x + (int64_t)gridDim.x * threadIdx.x
+                            : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n_dev) n = *n_dev;
     if (i >= n) return;
     Philox rng;
     rng.k0 = (uint32_t)seed;
@@ -250,8 +256,10 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
 // running carry starting at the segment's offset; *total = the sum
 constexpr int kScanOne = 65536;
 __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ in, int64_t n,
-                                                  int64_t *__restrict__ out, int64_t *__restrict__ total) {
+                                                  int64_t *__restrict__ out, int64_t *__restrict__ total,
+                                                  const int64_t *__restrict__ n_dev) {
     __shared__ int64_t wsum[32];
+    if (n_dev) n = *n_dev;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t seg = ((n + 31) / 32 + 127) / 128 * 128;  // elements per warp, a multiple of 128
     const int64_t b = min(n, warp * seg), e = min(n, b + seg);
@@ -311,8 +319,13 @@ __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ i
 __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
                        const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
                        uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, const int32_t *__restrict__ anc,
-                       int32_t *__restrict__ nanc, int64_t g_cur, DevStatus *st) {
+                       int32_t *__restrict__ nanc, int64_t g_cur, DevStatus *st, const int64_t *__restrict__ n_dev,
+                       const int64_t *__restrict__ g_dev) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n_dev) {
+        n = *n_dev;
+        g_cur = *g_dev;
+    }
     if (i >= n) return;
     int64_t j = off[i];
     const int p = T - 1 - step;  // orbital of this token
@@ -335,12 +348,28 @@ __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__rest
     }
 }
 
+// end of a step with the counts on the device: cnt[cur ^ 1] = the next
+// level's size (the scan's total, clamped to the capacity after recording
+// NNQS_E_TABLE_FULL), cnt[2] += this level's size (the first tree node of the
+// next level)
+__global__ void k_advance(int64_t *cnt, int cur, const int64_t *__restrict__ total, int64_t cap, DevStatus *st) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t nn = *total;
+    if (nn > cap) {
+        record_status(st, NNQS_E_TABLE_FULL, nn);
+        nn = cap;
+    }
+    cnt[2] += cnt[cur];
+    cnt[cur ^ 1] = nn;
+}
+
 struct SLayout {
     uint64_t *pref[2], *w[2], *counts;
     double *cond;
     int32_t *nchild;
     int64_t *off, *bsum, *total;
     int32_t *anc[2];  // key/value cache: ancestor tables of the current and next level
+    int64_t *cnt;     // device-side counts: level sizes [2], first node of the current level
     char *region;
     int64_t kv_nodes;
 };
@@ -358,6 +387,7 @@ SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &
     L.off = a.take<int64_t>(size_t(cap));
     L.bsum = a.take<int64_t>(size_t((cap + kScan - 1) / kScan + 1));
     L.total = a.take<int64_t>(1);
+    L.cnt = a.take<int64_t>(4);
     L.kv_nodes = cached ? int64_t(M->T) * cap + 1 : 0;
     for (int k = 0; k < 2; ++k) L.anc[k] = cached ? a.take<int32_t>(size_t(cap) * M->T) : nullptr;
     L.region = a.take<char>(cond_workspace(M, cap, prec, L.kv_nodes));
@@ -410,6 +440,43 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     // level 0: the empty prefix holds every sample
     NNQS_CUDA_TRY(cudaMemsetAsync(L.pref[0], 0, size_t(W) * 8, s));
     NNQS_CUDA_TRY(cudaMemcpyAsync(L.w[0], &n_samples, 8, cudaMemcpyHostToDevice, s));
+    if (cached && max_unique <= kScanOne && cond_cached_dev_ok(M, ctx, max_unique)) {
+        // the whole walk without a host round trip: every kernel reads the
+        // level's size from the device and is sized for the capacity; one
+        // synchronisation at the end reads the number of unique samples
+        const int64_t cnt0[4] = {1, 0, 0, 0};
+        NNQS_CUDA_TRY(cudaMemcpyAsync(L.cnt, cnt0, sizeof cnt0, cudaMemcpyHostToDevice, s));
+        const int64_t cap = max_unique;
+        const unsigned sgrid = (unsigned)std::max<int64_t>(num_sms(), (cap + 127) / 128);
+        int cur = 0;
+        for (int t = 0; t < T && rc == NNQS_OK; ++t) {
+            rc = cond_step_cached_dev(M, ctx, L.pref[cur], L.cnt + cur, L.cnt + 2, cap, t, L.anc[cur], L.cond, st, s);
+            if (rc != NNQS_OK) break;
+            NNQS_LAUNCH("k_split", s, k_split<<<sgrid, 128, 0, s>>>(L.w[cur], L.cond, cap, t, seed, L.counts, L.nchild,
+                                                                    st, L.cnt + cur));
+            NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, cap, L.off, L.total, L.cnt + cur));
+            NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(cap, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, cap, W, T, t,
+                                                                              cap, L.pref[cur ^ 1], L.w[cur ^ 1],
+                                                                              L.anc[cur], L.anc[cur ^ 1], 0, st,
+                                                                              L.cnt + cur, L.cnt + 2));
+            NNQS_LAUNCH("k_emit", s, k_advance<<<1, 32, 0, s>>>(L.cnt, cur, L.total, cap, st));
+            cur ^= 1;
+        }
+        cond_destroy(ctx);
+        if (rc != NNQS_OK) return rc;
+        int64_t n_final = 0;
+        NNQS_CUDA_TRY(cudaMemcpyAsync(&n_final, L.cnt + cur, 8, cudaMemcpyDeviceToHost, s));
+        NNQS_CUDA_TRY(cudaStreamSynchronize(s));
+        DevStatus hst{};
+        NNQS_CUDA_TRY(cudaMemcpy(&hst, st, sizeof hst, cudaMemcpyDeviceToHost));
+        if (hst.code == NNQS_E_TABLE_FULL)
+            return set_error(NNQS_E_TABLE_FULL, "a step held " + std::to_string(hst.index) +
+                                                    " prefixes, above max_unique " + std::to_string(max_unique));
+        NNQS_CUDA_TRY(cudaMemcpyAsync(samples_out, L.pref[cur], size_t(n_final) * W * 8, cudaMemcpyDeviceToDevice, s));
+        NNQS_CUDA_TRY(cudaMemcpyAsync(weights_out, L.w[cur], size_t(n_final) * 8, cudaMemcpyDeviceToDevice, s));
+        *n_unique_out = n_final;
+        return NNQS_OK;
+    }
     int64_t n = 1;
     int cur = 0;
     int64_t g_cur = 0;  // tree-node id of the first prefix of the current level
@@ -423,10 +490,10 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
         // the SMs instead of sharing one SM's FP64 pipe
         const int split_block = (int)std::min<int64_t>(128, std::max<int64_t>(1, (n + num_sms() - 1) / num_sms()));
         NNQS_LAUNCH("k_split", s, k_split<<<(unsigned)((n + split_block - 1) / split_block), split_block, 0, s>>>(
-                                      L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st));
+                                      L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st, nullptr));
         const int64_t nb = (n + kScan - 1) / kScan;
         if (n <= kScanOne) {
-            NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, n, L.off, L.total));
+            NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, n, L.off, L.total, nullptr));
         } else {
             NNQS_LAUNCH("k_scan_blocks", s, k_scan_blocks<<<(unsigned)nb, kScan, 0, s>>>(L.nchild, n, L.off, L.bsum));
             NNQS_LAUNCH("k_scan_sums", s, k_scan_sums<<<1, kScan, 0, s>>>(L.bsum, nb, L.total));
@@ -440,7 +507,8 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
                                                     " prefixes, above max_unique " + std::to_string(max_unique));
         NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t,
                                                                          max_unique, L.pref[cur ^ 1], L.w[cur ^ 1],
-                                                                         L.anc[cur], L.anc[cur ^ 1], g_cur, st));
+                                                                         L.anc[cur], L.anc[cur ^ 1], g_cur, st,
+                                                                         nullptr, nullptr));
         cur ^= 1;
         g_cur += n;
         n = next;

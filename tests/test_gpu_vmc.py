@@ -355,3 +355,19 @@ def test_replica_samples_differ():
     (x0, w0), (x1, w1) = draws
     assert int(w0.sum().item()) == int(w1.sum().item()) == 4096
     assert not (x0.shape == x1.shape and torch.equal(x0, x1) and torch.equal(w0, w1))
+
+
+def test_sampler_device_counts_table_full_n40():
+    """The cached sampler with the fused decode layer (40 qubits, split BF16)
+    keeps the level sizes on the device and synchronises once: a table that
+    overflows still reports NNQS_E_TABLE_FULL, and a sufficient one gives
+    the same draws as the recomputation."""
+    wl = I.WORKLOADS["n40"]
+    m, params, flat = model_for(wl, seed=31, std=0.3)
+    with pytest.raises(B.NNQSError) as e:
+        B.sample(m, flat, 20000, seed=3, max_unique=64, prec=B.BF16X3)
+    assert e.value.status == B.E_TABLE_FULL
+    xa, wa = B.sample(m, flat, 20000, seed=3, max_unique=32768, prec=B.BF16X3)
+    xb, wb = B.sample(m, flat, 20000, seed=3, max_unique=32768, prec=B.BF16X3, flags=B.SAMPLE_RECOMPUTE)
+    assert torch.equal(xa, xb) and torch.equal(wa, wb)
+    assert int(wa.sum().item()) == 20000
