@@ -724,6 +724,15 @@ def run_ours(args):
                               "energy_ha": e["fp64"],
                               "energy_diff_ha": abs(e[args.prec] - e["fp64"]),
                               "energy_diff_by_prec_ha": {k: abs(v - e["fp64"]) for k, v in e.items() if k != "fp64"}}
+        if peaks_run.get("fp64_flops"):
+            # the ansatz's method FLOPs (forward + reverse mode) of the step
+            # against the measured FP64 FMA rate: the plain path's CUDA-core bound
+            fl64 = 3.0 * model_flops_per_sample(wl) * nu64 / args.fp64_steps / (ms64 / 1e3)
+            line["fp64_plain"]["roofline"] = {
+                "bound": "alu", "unit": "TFLOP/s", "achieved": fl64 / 1e12, "peak": peaks_run["fp64_flops"] / 1e12,
+                "frac": fl64 / peaks_run["fp64_flops"],
+                "peak_source": "nnqs_measure_peaks FP64 FMA (measured in this run)",
+                "note": "method FLOPs of one forward and its reverse mode over the step's samples / step time"}
         # the other fast paths' step times
         others = {}
         for k in ("bf16x3", "mixed", "fp32", "fp8"):

@@ -3637,6 +3637,11 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
     return NNQS_OK;
 }
 
+bool cond_dev_walk_ok(const nnqs_model *M, int prec, int64_t cap) {
+    return prec != NNQS_FP64 && tc_mode(prec) != 0 && M->d == dec::kD && M->F == dec::kF &&
+           (M->dh == 8 || M->dh == 16) && cap <= chunk_for(M, std::max<int64_t>(cap, 1), sizeof(float), false);
+}
+
 bool cond_cached_dev_ok(const nnqs_model *M, const CondCtx *ctx, int64_t cap) {
     return ctx->prec != NNQS_FP64 && ctx->tensor && decode_fused_ok(M, ctx->tcw) && cap <= ctx->C;
 }

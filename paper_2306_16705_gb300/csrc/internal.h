@@ -30,6 +30,8 @@ nnqs_status cuda_error(cudaError_t e, const char *where);
 
 // ---- launches: counting and optional CUDA-event timing (prof.cpp) ---------
 cudaError_t note_launch();  // counts one launch, returns cudaGetLastError()
+void note_replay(uint64_t launches);  // a CUDA-graph replay of that many kernel launches
+bool profiling_on();
 // algorithmic work (flops, bytes) of a launch, for roofline accounting
 void note_work(const char *name, double flops, double bytes);
 class ProfScope {

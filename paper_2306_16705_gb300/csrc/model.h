@@ -74,6 +74,8 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
 // prefixes g0 .. g0 + n - 1 with n = *n_dev <= cap and g0 = *g0_dev; only for
 // the fused decode layer (BF16 / split BF16, d = 64) and cap within one chunk
 bool cond_cached_dev_ok(const nnqs_model *M, const CondCtx *ctx, int64_t cap);
+// the same test from the model and the precision alone (before any context)
+bool cond_dev_walk_ok(const nnqs_model *M, int prec, int64_t cap);
 nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, const int64_t *n_dev,
                                  const int64_t *g0_dev, int64_t cap, int t, const int32_t *anc, double *cond,
                                  DevStatus *st, cudaStream_t s);

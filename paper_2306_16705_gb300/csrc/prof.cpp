@@ -61,6 +61,10 @@ cudaError_t note_launch() {
     return cudaGetLastError();
 }
 
+void note_replay(uint64_t launches) { g_launches.fetch_add(launches, std::memory_order_relaxed); }
+
+bool profiling_on() { return g_enabled.load(std::memory_order_relaxed); }
+
 ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s) {
     if (!g_enabled.load(std::memory_order_relaxed)) return;
     if (cudaEventCreate(&e0_) != cudaSuccess) return;

@@ -23,6 +23,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dev_common.cuh"
@@ -162,10 +164,11 @@ __device__ uint64_t binomial(uint64_t n, double p, Philox &rng, DevStatus *st) {
 // the early steps land on different SMs.  The draws depend on i only.
 __global__ void k_split(const uint64_t *__restrict__ w, const double *__restrict__ cond, int64_t n, int step,
                         uint64_t seed, uint64_t *__restrict__ counts, int32_t *__restrict__ nchild, DevStatus *st,
-                        const int64_t *__restrict__ n_dev) {
+                        const int64_t *__restrict__ n_dev, const uint64_t *__restrict__ seed_dev) {
     const int64_t i = n_dev ? blockIdx.x + (int64_t)gridDim.x * threadIdx.x
                             : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n_dev) n = *n_dev;
+    if (seed_dev) seed = *seed_dev;
     if (i >= n) return;
     Philox rng;
     rng.k0 = (uint32_t)seed;
@@ -348,6 +351,17 @@ __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__rest
     }
 }
 
+// level 0 of the device-count walk: the empty prefix holds all n_samples =
+// args[0] samples; level sizes {1, 0}, first node 0
+__global__ void k_level0(uint64_t *pref, int W, uint64_t *w, int64_t *cnt, const uint64_t *args) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < W; ++k) pref[k] = 0;
+    w[0] = args[0];
+    cnt[0] = 1;
+    cnt[1] = 0;
+    cnt[2] = 0;
+}
+
 // end of a step with the counts on the device: cnt[cur ^ 1] = the next
 // level's size (the scan's total, clamped to the capacity after recording
 // NNQS_E_TABLE_FULL), cnt[2] += this level's size (the first tree node of the
@@ -370,6 +384,7 @@ struct SLayout {
     int64_t *off, *bsum, *total;
     int32_t *anc[2];  // key/value cache: ancestor tables of the current and next level
     int64_t *cnt;     // device-side counts: level sizes [2], first node of the current level
+    uint64_t *args;   // device copies of n_samples and seed (read by the device-count walk)
     char *region;
     int64_t kv_nodes;
 };
@@ -388,10 +403,158 @@ SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &
     L.bsum = a.take<int64_t>(size_t((cap + kScan - 1) / kScan + 1));
     L.total = a.take<int64_t>(1);
     L.cnt = a.take<int64_t>(4);
+    L.args = a.take<uint64_t>(2);
     L.kv_nodes = cached ? int64_t(M->T) * cap + 1 : 0;
     for (int k = 0; k < 2; ++k) L.anc[k] = cached ? a.take<int32_t>(size_t(cap) * M->T) : nullptr;
     L.region = a.take<char>(cond_workspace(M, cap, prec, L.kv_nodes));
     return L;
+}
+
+}  // namespace
+}  // namespace nnqs
+
+namespace nnqs {
+namespace {
+
+// The whole walk with the level sizes on the device: every kernel reads the
+// level's size (and the seed) from device memory and is sized for the
+// capacity, so no step waits for the host, and the sequence -- parameter
+// conversion, weight images, level 0, then per step the fused decode layers,
+// split, scan, emit and advance -- is the same on every call with the same
+// model, parameters, workspace and capacity.  Such repeated calls replay it
+// as a CUDA graph (captured on the second call; the first runs the kernels
+// directly), which removes most of the per-launch gaps of its ~165 launches.
+// With profiling on, the kernels always run directly.
+struct GraphKey {
+    int dev;
+    const nnqs_model *M;
+    nnqs_model_cfg cfg;
+    const float *params;
+    int prec;
+    int64_t cap;
+    const void *ws;
+    size_t ws_bytes;
+    bool operator==(const GraphKey &o) const {
+        return dev == o.dev && M == o.M && std::memcmp(&cfg, &o.cfg, sizeof cfg) == 0 && params == o.params &&
+               prec == o.prec && cap == o.cap && ws == o.ws && ws_bytes == o.ws_bytes;
+    }
+};
+struct GraphEntry {
+    GraphKey key;
+    int calls = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;
+    uint64_t last_use = 0;
+};
+constexpr size_t kMaxGraphs = 8;
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+uint64_t g_graph_clock = 0;
+
+nnqs_status walk_kernels(const nnqs_model *M, const float *params, int prec, int64_t cap, const SLayout &L,
+                         DevStatus *st, cudaStream_t s) {
+    Arena sub(L.region);
+    CondCtx *ctx = nullptr;
+    nnqs_status rc = cond_create(M, params, prec, cap, L.kv_nodes, sub, &ctx, s);
+    const int W = M->W, T = M->T;
+    const unsigned sgrid = (unsigned)std::max<int64_t>(num_sms(), (cap + 127) / 128);
+    if (rc == NNQS_OK) {
+        NNQS_LAUNCH("k_emit", s, k_level0<<<1, 32, 0, s>>>(L.pref[0], W, L.w[0], L.cnt, L.args));
+        int cur = 0;
+        for (int t = 0; t < T && rc == NNQS_OK; ++t) {
+            rc = cond_step_cached_dev(M, ctx, L.pref[cur], L.cnt + cur, L.cnt + 2, cap, t, L.anc[cur], L.cond, st, s);
+            if (rc != NNQS_OK) break;
+            NNQS_LAUNCH("k_split", s, k_split<<<sgrid, 128, 0, s>>>(L.w[cur], L.cond, cap, t, 0, L.counts, L.nchild, st,
+                                                                    L.cnt + cur, L.args + 1));
+            NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, cap, L.off, L.total, L.cnt + cur));
+            NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(cap, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, cap, W, T, t,
+                                                                              cap, L.pref[cur ^ 1], L.w[cur ^ 1],
+                                                                              L.anc[cur], L.anc[cur ^ 1], 0, st,
+                                                                              L.cnt + cur, L.cnt + 2));
+            NNQS_LAUNCH("k_emit", s, k_advance<<<1, 32, 0, s>>>(L.cnt, cur, L.total, cap, st));
+            cur ^= 1;
+        }
+    }
+    cond_destroy(ctx);
+    return rc;
+}
+
+nnqs_status dev_walk(const nnqs_model *M, const float *params, uint64_t n_samples, uint64_t seed, int prec,
+                     int64_t cap, const SLayout &L, DevStatus *st, uint64_t *samples_out, uint64_t *weights_out,
+                     int64_t *n_unique_out, const void *workspace, size_t workspace_bytes, cudaStream_t s) {
+    const uint64_t args[2] = {n_samples, seed};
+    NNQS_CUDA_TRY(cudaMemcpyAsync(L.args, args, sizeof args, cudaMemcpyHostToDevice, s));
+    nnqs_status rc = NNQS_OK;
+    if (profiling_on()) {
+        rc = walk_kernels(M, params, prec, cap, L, st, s);
+    } else {
+        GraphKey key{};
+        NNQS_CUDA_TRY(cudaGetDevice(&key.dev));
+        key.M = M;
+        key.cfg = M->cfg;
+        key.params = params;
+        key.prec = prec;
+        key.cap = cap;
+        key.ws = workspace;
+        key.ws_bytes = workspace_bytes;
+        std::unique_lock<std::mutex> lk(g_graph_mu);
+        GraphEntry *e = nullptr;
+        for (auto &g : g_graphs)
+            if (g.key == key) e = &g;
+        if (!e) {
+            if (g_graphs.size() >= kMaxGraphs) {  // drop the least recently used
+                auto old = std::min_element(g_graphs.begin(), g_graphs.end(), [](const GraphEntry &a, const GraphEntry &b) {
+                    return a.last_use < b.last_use;
+                });
+                if (old->exec) cudaGraphExecDestroy(old->exec);
+                g_graphs.erase(old);
+            }
+            g_graphs.push_back(GraphEntry{key});
+            e = &g_graphs.back();
+        }
+        e->last_use = ++g_graph_clock;
+        ++e->calls;
+        if (e->exec) {
+            NNQS_CUDA_TRY(cudaGraphLaunch(e->exec, s));
+            note_replay(e->launches);
+        } else if (e->calls >= 2) {
+            // capture the walk once; any failure falls back to direct launches
+            const uint64_t l0 = nnqs_launch_count();
+            cudaGraph_t graph = nullptr;
+            bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (captured) {
+                rc = walk_kernels(M, params, prec, cap, L, st, s);
+                captured = cudaStreamEndCapture(s, &graph) == cudaSuccess && rc == NNQS_OK;
+            }
+            cudaGraphExec_t exec = nullptr;
+            if (captured && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+                e->exec = exec;
+                e->launches = nnqs_launch_count() - l0;
+                NNQS_CUDA_TRY(cudaGraphLaunch(exec, s));
+            } else {
+                cudaGetLastError();
+                rc = walk_kernels(M, params, prec, cap, L, st, s);
+            }
+            if (graph) cudaGraphDestroy(graph);
+        } else {
+            rc = walk_kernels(M, params, prec, cap, L, st, s);
+        }
+    }
+    if (rc != NNQS_OK) return rc;
+    // after T steps the last level sits at index T % 2
+    const int cur = M->T & 1;
+    int64_t n_final = 0;
+    NNQS_CUDA_TRY(cudaMemcpyAsync(&n_final, L.cnt + cur, 8, cudaMemcpyDeviceToHost, s));
+    NNQS_CUDA_TRY(cudaStreamSynchronize(s));
+    DevStatus hst{};
+    NNQS_CUDA_TRY(cudaMemcpy(&hst, st, sizeof hst, cudaMemcpyDeviceToHost));
+    if (hst.code == NNQS_E_TABLE_FULL)
+        return set_error(NNQS_E_TABLE_FULL, "a step held " + std::to_string(hst.index) + " prefixes, above max_unique " +
+                                                std::to_string(cap));
+    NNQS_CUDA_TRY(cudaMemcpyAsync(samples_out, L.pref[cur], size_t(n_final) * M->W * 8, cudaMemcpyDeviceToDevice, s));
+    NNQS_CUDA_TRY(cudaMemcpyAsync(weights_out, L.w[cur], size_t(n_final) * 8, cudaMemcpyDeviceToDevice, s));
+    *n_unique_out = n_final;
+    return NNQS_OK;
 }
 
 }  // namespace
@@ -429,6 +592,9 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     if (L.kv_nodes >= (int64_t(1) << 31))
         return set_error(NNQS_E_UNSUPPORTED, "key/value cache above 2^31 nodes (T * max_unique)");
     if (n_samples == 0) return NNQS_OK;
+    if (cached && max_unique <= kScanOne && cond_dev_walk_ok(M, prec, max_unique))
+        return dev_walk(M, params, n_samples, seed, prec, max_unique, L, st, samples_out, weights_out, n_unique_out,
+                        workspace, workspace_bytes, s);
     Arena sub(L.region);
     CondCtx *ctx = nullptr;
     nnqs_status rc = cond_create(M, params, prec, max_unique, L.kv_nodes, sub, &ctx, s);
@@ -440,43 +606,6 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     // level 0: the empty prefix holds every sample
     NNQS_CUDA_TRY(cudaMemsetAsync(L.pref[0], 0, size_t(W) * 8, s));
     NNQS_CUDA_TRY(cudaMemcpyAsync(L.w[0], &n_samples, 8, cudaMemcpyHostToDevice, s));
-    if (cached && max_unique <= kScanOne && cond_cached_dev_ok(M, ctx, max_unique)) {
-        // the whole walk without a host round trip: every kernel reads the
-        // level's size from the device and is sized for the capacity; one
-        // synchronisation at the end reads the number of unique samples
-        const int64_t cnt0[4] = {1, 0, 0, 0};
-        NNQS_CUDA_TRY(cudaMemcpyAsync(L.cnt, cnt0, sizeof cnt0, cudaMemcpyHostToDevice, s));
-        const int64_t cap = max_unique;
-        const unsigned sgrid = (unsigned)std::max<int64_t>(num_sms(), (cap + 127) / 128);
-        int cur = 0;
-        for (int t = 0; t < T && rc == NNQS_OK; ++t) {
-            rc = cond_step_cached_dev(M, ctx, L.pref[cur], L.cnt + cur, L.cnt + 2, cap, t, L.anc[cur], L.cond, st, s);
-            if (rc != NNQS_OK) break;
-            NNQS_LAUNCH("k_split", s, k_split<<<sgrid, 128, 0, s>>>(L.w[cur], L.cond, cap, t, seed, L.counts, L.nchild,
-                                                                    st, L.cnt + cur));
-            NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, cap, L.off, L.total, L.cnt + cur));
-            NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(cap, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, cap, W, T, t,
-                                                                              cap, L.pref[cur ^ 1], L.w[cur ^ 1],
-                                                                              L.anc[cur], L.anc[cur ^ 1], 0, st,
-                                                                              L.cnt + cur, L.cnt + 2));
-            NNQS_LAUNCH("k_emit", s, k_advance<<<1, 32, 0, s>>>(L.cnt, cur, L.total, cap, st));
-            cur ^= 1;
-        }
-        cond_destroy(ctx);
-        if (rc != NNQS_OK) return rc;
-        int64_t n_final = 0;
-        NNQS_CUDA_TRY(cudaMemcpyAsync(&n_final, L.cnt + cur, 8, cudaMemcpyDeviceToHost, s));
-        NNQS_CUDA_TRY(cudaStreamSynchronize(s));
-        DevStatus hst{};
-        NNQS_CUDA_TRY(cudaMemcpy(&hst, st, sizeof hst, cudaMemcpyDeviceToHost));
-        if (hst.code == NNQS_E_TABLE_FULL)
-            return set_error(NNQS_E_TABLE_FULL, "a step held " + std::to_string(hst.index) +
-                                                    " prefixes, above max_unique " + std::to_string(max_unique));
-        NNQS_CUDA_TRY(cudaMemcpyAsync(samples_out, L.pref[cur], size_t(n_final) * W * 8, cudaMemcpyDeviceToDevice, s));
-        NNQS_CUDA_TRY(cudaMemcpyAsync(weights_out, L.w[cur], size_t(n_final) * 8, cudaMemcpyDeviceToDevice, s));
-        *n_unique_out = n_final;
-        return NNQS_OK;
-    }
     int64_t n = 1;
     int cur = 0;
     int64_t g_cur = 0;  // tree-node id of the first prefix of the current level
@@ -490,7 +619,7 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
         // the SMs instead of sharing one SM's FP64 pipe
         const int split_block = (int)std::min<int64_t>(128, std::max<int64_t>(1, (n + num_sms() - 1) / num_sms()));
         NNQS_LAUNCH("k_split", s, k_split<<<(unsigned)((n + split_block - 1) / split_block), split_block, 0, s>>>(
-                                      L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st, nullptr));
+                                      L.w[cur], L.cond, n, t, seed, L.counts, L.nchild, st, nullptr, nullptr));
         const int64_t nb = (n + kScan - 1) / kScan;
         if (n <= kScanOne) {
             NNQS_LAUNCH("k_scan", s, k_scan_one<<<1, 1024, 0, s>>>(L.nchild, n, L.off, L.total, nullptr));

@@ -371,3 +371,26 @@ def test_sampler_device_counts_table_full_n40():
     xb, wb = B.sample(m, flat, 20000, seed=3, max_unique=32768, prec=B.BF16X3, flags=B.SAMPLE_RECOMPUTE)
     assert torch.equal(xa, xb) and torch.equal(wa, wb)
     assert int(wa.sum().item()) == 20000
+
+
+def test_sampler_graph_replays_n40():
+    """Repeated calls with the same model, parameters and workspace replay the
+    device-count walk as a CUDA graph (captured on the second call): the
+    draws of every call equal the direct walk's, the seed and N_s of each
+    call are honoured, and parameter updates between calls are seen."""
+    wl = I.WORKLOADS["n40"]
+    m, params, flat = model_for(wl, seed=32, std=0.3)
+    nb = B.lib().nnqs_sample_workspace_size(m.handle, 1 << 15, B.BF16X3, 0)
+    ws = B.workspace(nb)
+    ref = {sd: B.sample(m, flat, 12000, seed=sd, max_unique=1 << 15, prec=B.BF16X3, flags=B.SAMPLE_RECOMPUTE)
+           for sd in (11, 12)}
+    for k in range(4):  # direct, capture + launch, replay, replay
+        sd = 11 if k % 2 == 0 else 12
+        x, w = B.sample(m, flat, 12000, seed=sd, max_unique=1 << 15, prec=B.BF16X3, ws=ws)
+        assert torch.equal(x, ref[sd][0]) and torch.equal(w, ref[sd][1]), k
+    x, w = B.sample(m, flat, 5000, seed=11, max_unique=1 << 15, prec=B.BF16X3, ws=ws)
+    assert int(w.sum().item()) == 5000
+    flat.mul_(1.5)  # new parameter values at the same address
+    x2, w2 = B.sample(m, flat, 12000, seed=11, max_unique=1 << 15, prec=B.BF16X3, ws=ws)
+    xr, wr = B.sample(m, flat, 12000, seed=11, max_unique=1 << 15, prec=B.BF16X3, flags=B.SAMPLE_RECOMPUTE)
+    assert torch.equal(x2, xr) and torch.equal(w2, wr)
