@@ -91,9 +91,13 @@ __device__ __forceinline__ float ff_gelu(float x) {
     return 0.5f * x * (1.0f + copysignf(erf_abs, x));
 }
 
-// element (r, c) of the tile's k | v rows: 16-byte pieces XOR-rotated by the
-// row so that lanes reading the same piece of different rows use different banks
-__device__ __forceinline__ int kv_at(int r, int c) { return r * 128 + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3); }
+// element (r, c) of the tile's k | v rows, r of sample sl of the tile: the
+// 16-byte pieces XOR-rotated by (r ^ sl) & 7, so that the lanes of a warp
+// reading the same piece of their samples' rows s T + j (one row per sample)
+// and the lanes writing consecutive rows of one sample use different banks
+__device__ __forceinline__ int kv_at(int r, int c, int sl) {
+    return r * 128 + ((((c >> 2) ^ ((r ^ sl) & 7))) << 2) + (c & 3);
+}
 
 // 8 values as one granule of a swizzled A-operand tile row (hi, and lo when split)
 __device__ __forceinline__ void ff_granule(uint8_t *hi, uint8_t *lo, int r, int c, const float *v, bool split) {
@@ -111,14 +115,43 @@ __device__ __forceinline__ void ff_granule(uint8_t *hi, uint8_t *lo, int r, int 
 }
 
 // LayerNorm (eps 1e-5) of residual rows by 4 lanes per row: warp w takes rows
-// 8 w .. 8 w + 7, lane 4 k + p the 16 columns 16 p .. of row 8 w + k.  The
-// normalised values y (FP32) are returned for stores; the A tile gets them as
-// BF16 (hi / lo) when `hi` is not null.  With `keep`, the row's input, y and
-// (by the p = 0 lane) mean / rstd go to global memory row `grow`.
+// 8 w .. 8 w + 7, lane 4 k + p of row 8 w + k the columns 8 p .. 8 p + 7 and
+// 32 + 8 p .. 32 + 8 p + 7 (so that the 32 lanes' reads of the residual rows,
+// stride 65, fall in 32 different banks).  y[0..7] and y[8..15] are those
+// columns' normalised values; the A tile gets them as BF16 (hi / lo, granules
+// p and p + 4) when `hi` is not null.
 struct LnOut {
     float y[16];
     float mu, rs;
 };
+
+// the 16 columns of LayerNorm part p of a 64-wide vector: 8 p .. and 32 + 8 p ..
+__device__ __forceinline__ int ln_col(int p, int c) { return (c < 8 ? 8 * p : 32 + 8 * p - 8) + c; }
+
+// 16 floats of LayerNorm part p from a 16-byte aligned vector
+__device__ __forceinline__ void ff_ld_part(const float *__restrict__ vec, int p, float (&v)[16]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(vec + 32 * h + 8 * p) + k);
+            v[8 * h + 4 * k] = a.x;
+            v[8 * h + 4 * k + 1] = a.y;
+            v[8 * h + 4 * k + 2] = a.z;
+            v[8 * h + 4 * k + 3] = a.w;
+        }
+}
+
+// 16 floats of LayerNorm part p to a 16-byte aligned row
+__device__ __forceinline__ void ff_st_part(float *row, int p, const float *v) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            reinterpret_cast<float4 *>(row + 32 * h + 8 * p)[k] =
+                make_float4(v[8 * h + 4 * k], v[8 * h + 4 * k + 1], v[8 * h + 4 * k + 2], v[8 * h + 4 * k + 3]);
+}
+
 __device__ __forceinline__ LnOut ff_layernorm(const float *sH, int r, int p, const float *__restrict__ gam,
                                               const float *__restrict__ bet, uint8_t *hi, uint8_t *lo, bool split) {
     LnOut o;
@@ -126,7 +159,7 @@ __device__ __forceinline__ LnOut ff_layernorm(const float *sH, int r, int p, con
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-        v[c] = sH[r * ff::kHS + 16 * p + c];
+        v[c] = sH[r * ff::kHS + ln_col(p, c)];
         s += v[c];
     }
     s += __shfl_xor_sync(0xffffffffu, s, 1);
@@ -139,13 +172,13 @@ __device__ __forceinline__ LnOut ff_layernorm(const float *sH, int r, int p, con
     q += __shfl_xor_sync(0xffffffffu, q, 2);
     o.rs = 1.0f / sqrtf(q / float(ff::kD) + 1e-5f);
     float gv[16], bv[16];
-    ff_ld16(gam + 16 * p, gv);
-    ff_ld16(bet + 16 * p, bv);
+    ff_ld_part(gam, p, gv);
+    ff_ld_part(bet, p, bv);
 #pragma unroll
     for (int c = 0; c < 16; ++c) o.y[c] = (v[c] - o.mu) * o.rs * gv[c] + bv[c];
     if (hi) {
-        ff_granule(hi, lo, r, 2 * p, o.y, split);
-        ff_granule(hi, lo, r, 2 * p + 1, o.y + 8, split);
+        ff_granule(hi, lo, r, p, o.y, split);
+        ff_granule(hi, lo, r, p + 4, o.y + 8, split);
     }
     return o;
 }
@@ -313,9 +346,9 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     if (lr < rows_used && gr < g.rows) {
                         float hv[16];
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + 16 * lq + c];
-                        ff_st16(g.hbuf + at * kD + 16 * lq, hv);
-                        ff_st16(g.a + at * kD + 16 * lq, n1.y);
+                        for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + ln_col(lq, c)];
+                        ff_st_part(g.hbuf + at * kD, lq, hv);
+                        ff_st_part(g.a + at * kD, lq, n1.y);
                         if (lq == 0) {
                             g.mean1[at] = n1.mu;
                             g.rstd1[at] = n1.rs;
@@ -351,7 +384,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                         v.y = __uint_as_float(r16[4 * p + 1]) + bv[4 * p + 1];
                         v.z = __uint_as_float(r16[4 * p + 2]) + bv[4 * p + 2];
                         v.w = __uint_as_float(r16[4 * p + 3]) + bv[4 * p + 3];
-                        *reinterpret_cast<float4 *>(sKV + kv_at(row, c)) = v;
+                        *reinterpret_cast<float4 *>(sKV + kv_at(row, c, row / T)) = v;
                         if constexpr (KEEP) {
                             const int64_t gr = s0 * T + row;
                             if (row < rows_used && gr < g.rows)
@@ -393,8 +426,9 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                         float kk[16], vv[16];
 #pragma unroll
                         for (int p = 0; p < 4; ++p) {
-                            const float4 a = *reinterpret_cast<const float4 *>(sKV + kv_at(rj, 16 * cq + 4 * p));
-                            const float4 b = *reinterpret_cast<const float4 *>(sKV + kv_at(rj, 64 + 16 * cq + 4 * p));
+                            const float4 a = *reinterpret_cast<const float4 *>(sKV + kv_at(rj, 16 * cq + 4 * p, sl));
+                            const float4 b =
+                                *reinterpret_cast<const float4 *>(sKV + kv_at(rj, 64 + 16 * cq + 4 * p, sl));
                             kk[4 * p] = a.x; kk[4 * p + 1] = a.y; kk[4 * p + 2] = a.z; kk[4 * p + 3] = a.w;
                             vv[4 * p] = b.x; vv[4 * p + 1] = b.y; vv[4 * p + 2] = b.z; vv[4 * p + 3] = b.w;
                         }
@@ -470,7 +504,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                 if constexpr (KEEP) {
                     const int64_t gr = s0 * T + lr, at = (int64_t)l * g.rows + gr;
                     if (lr < rows_used && gr < g.rows) {
-                        ff_st16(g.a2 + at * kD + 16 * lq, n2.y);
+                        ff_st_part(g.a2 + at * kD, lq, n2.y);
                         if (lq == 0) {
                             g.mean2[at] = n2.mu;
                             g.rstd2[at] = n2.rs;
@@ -559,7 +593,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 float a = 0.f, wv[16];
-                ff_ld16(g.hw + k * kD + 16 * lq, wv);
+                ff_ld_part(g.hw + k * kD, lq, wv);
 #pragma unroll
                 for (int c = 0; c < 16; ++c) a += nf.y[c] * wv[c];
                 a += __shfl_xor_sync(0xffffffffu, a, 1);
@@ -573,9 +607,9 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                 if (valid) {
                     float hv[16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + 16 * lq + c];
-                    ff_st16(g.hbuf + ((int64_t)g.L * g.rows + gr) * kD + 16 * lq, hv);
-                    ff_st16(g.hf + gr * kD + 16 * lq, nf.y);
+                    for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + ln_col(lq, c)];
+                    ff_st_part(g.hbuf + ((int64_t)g.L * g.rows + gr) * kD, lq, hv);
+                    ff_st_part(g.hf + gr * kD, lq, nf.y);
                     if (lq == 0) {
                         g.meanf[gr] = nf.mu;
                         g.rstdf[gr] = nf.rs;
