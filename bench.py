@@ -880,18 +880,31 @@ def run_case(args):
                                   params=flat, prec=prec, check=False)
         else:
             call = lambda: B.logpsi(model, flat, x, prec, check=False)
-    for _ in range(3):
+    heavy = args.case == "eloc-exact"  # seconds per call at full size: one warm-up, two timed
+    n_warm, n_timed = (1, 2) if heavy else (3, 5)
+    for _ in range(n_warm):
         call()
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    for _ in range(5):
-        call()
+    for _ in range(n_timed):
+        out = call()
     e1.record(st)
     e1.synchronize()
-    print(json.dumps({"case": args.case, "workload": args.workload, "n": args.n, "rows": rows, "prec": args.prec,
-                      "ms_per_call": e0.elapsed_time(e1) / 5}), flush=True)
+    line = {"case": args.case, "workload": args.workload, "n": args.n, "rows": rows, "prec": args.prec,
+            "ms_per_call": e0.elapsed_time(e1) / n_timed}
+    if heavy:
+        # the exact local energies of the rows beside the sample-aware ones
+        # (sum over x' in the table only, Alg. 2) with the same log psi
+        Ud, cnt, _, _ = B.exact_coupled(ham, x[:rows], wl.n_alpha, wl.n_beta, row_cap=0, check=False,
+                                        cap_unique=rows * ham.info()["n_groups"])
+        lp = B.logpsi(model, flat, x, prec)
+        sa = B.eloc(ham, x, lp, wl.n_alpha, wl.n_beta, n_rows=rows)
+        line.update({"unique_coupled_states": int(Ud.shape[0]),
+                     "coupled_states_per_s": int(Ud.shape[0]) / (line["ms_per_call"] / 1e3),
+                     "mean_eloc_exact": float(out[:, 0].mean()), "mean_eloc_sample_aware": float(sa[:, 0].mean())})
+    print(json.dumps(line), flush=True)
 
 
 def main():
