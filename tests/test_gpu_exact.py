@@ -234,3 +234,38 @@ def test_exact_mode_bf16x3_against_fp64_gpu_n40():
     assert abs(E[B.BF16X3] - E[B.FP64]) <= 1e-5
     d = (e[B.BF16X3] - e[B.FP64]).abs().max().item()
     assert d <= 1e-4 * max(1.0, e[B.FP64].abs().max().item()), d
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.BF16X3])
+def test_exact_mode_two_words(prec):
+    """70 qubits (two-word keys: the 128-bit CAS dedup and two-word sweeps),
+    interacting orbitals on both sides of qubit 64, an ansatz of d = 64 (the
+    fused forward in BF16X3): FP64 within 1e-10 of the oracle's exact E_loc,
+    BF16X3 within the log-psi-error bound of the module docstring."""
+    n = 35
+    act = [0, 9, 30, 31, 32, 34]
+    h0, eri0 = I.integrals(len(act), 5, 4)
+    h = np.zeros((n, n))
+    eri = np.zeros((n, n, n, n))
+    h[np.ix_(act, act)] = h0
+    eri[np.ix_(act, act, act, act)] = eri0
+    ham = B.build_pauli(h, eri)
+    strings = OH.build(h, eri)
+    rows = I.clustered_sector_samples(n, 3, 2, 40, seed=3, n_centers=3, orbitals=act)
+
+    class WL:  # the model's shape for model_for / exact_reduced
+        n_qubits, n_alpha, n_beta, d_model, n_layers, n_heads = 70, 3, 2, 64, 2, 8
+
+    if prec == B.FP64:
+        m, params, flat = model_for(WL, seed=33)
+
+        def fn(packed):
+            return OA.forward(params, I.unpack_bits(packed, 70), 3, 2, 8)
+
+        ref = OH.eloc_exact(*strings, rows, 3, 2, fn)
+        got = B.eloc(ham, B.to_device_bits(rows), None, 3, 2, mode=B.EXACT, model=m, params=flat,
+                     prec=B.FP64).cpu().numpy()
+        got = got[:, 0] + 1j * got[:, 1]
+        assert np.abs(got - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
+    else:
+        exact_reduced(WL, ham, strings, rows, prec, seed=33)
