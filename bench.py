@@ -34,9 +34,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "n40"
 N_SAMPLES = 16384
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FMA: SMs x lanes x 2 x max clock
-# DRAM read + write bytes per k_tc_gemm launch of this step, from one ncu capture of the current kernel
-# at this workload (profiles/k_tc_gemm_energy_grad_n40.md); None once the kernel changes
-TC_GEMM_TRAFFIC_BYTES = 358.4e6
+# the tcgen05 kernels of the ansatz (forward, fused reverse mode, sampler decode, the remaining GEMMs)
+TENSOR_KERNELS = ("k_fwd_fused", "k_bwd_attn", "k_bwd_ffn", "k_decode_layer", "k_tc_gemm")
+# DRAM read + write bytes per launch of this step's kernels, from ncu captures of the current kernels at
+# this workload (profiles/); a kernel leaves this table when it changes
+KERNEL_TRAFFIC_BYTES = {}
 
 
 def parse():
@@ -57,7 +59,8 @@ def parse():
                     help="rows of the exact-mode side line (0 = skip)")
     ap.add_argument("--n120-steps", type=int, default=3, help="timed steps of the 120-qubit side line (0 = skip)")
     ap.add_argument("--case", default=None,
-                    choices=["sweep-pairs", "sweep-groups", "logpsi", "logpsi-unfused", "eloc-exact"],
+                    choices=["sweep-pairs", "sweep-groups", "logpsi", "logpsi-unfused", "grad", "grad-unfused",
+                             "eloc-exact"],
                     help="time one hot-path call alone (for profiling) instead of the VMC step")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --case (n40, n76, n120, n30, n12)")
     ap.add_argument("--n", type=int, default=16384, help="samples (table rows) of --case")
@@ -650,44 +653,47 @@ def run_ours(args):
         pass
     tpk = float(peaks.get("bf16_tflops_sustained", 1700.0))
     tpk_src = "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback 1.7 PFLOP/s sustained"
-    if name == "k_tc_gemm":
-        # the ansatz's products are a dense contraction: the bound is the
-        # tensor pipe (sustained BF16, the kernel runs inside a long step),
-        # counted in the method's FLOPs (one product per layer, not the three
-        # BF16 products of the split forward); the HBM rate of the
-        # implementation's FP32 operand traffic is given beside it
-        pk = float(peaks.get("hbm_gbs", 6800.0))
-        gbs = f["bytes"] / (f["ms"] / 1e3) / 1e9
-        tflops = f["flops"] / (f["ms"] / 1e3) / 1e12
-        traffic = (TC_GEMM_TRAFFIC_BYTES if TC_GEMM_TRAFFIC_BYTES and args.n_samples == N_SAMPLES
-                   and args.prec == "bf16x3" else None)
-        roof = {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": tpk, "unit": "TFLOP/s",
-                "frac": tflops / tpk, "traffic": traffic, "peak_source": tpk_src + " (of measured)",
-                "flops_per_launch": f["flops"] / max(1, f["launches"]),
-                "hbm": {"achieved_gbs": gbs, "peak_gbs": pk, "frac": gbs / pk,
-                        "algorithmic_bytes_per_launch": f["bytes"] / max(1, f["launches"]),
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"},
-                "launches": f["launches"], "avg_launch_ms": avg_ms}
-    elif name == "k_gemm":
-        fpk = peaks_run.get("fp32_flops", FP32_PEAK_TFLOPS * 1e12) / 1e12
-        achieved = f["flops"] / (f["ms"] / 1e3) / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fpk,
-                "unit": "TFLOP/s", "frac": achieved / fpk, "traffic": None,
-                "peak_source": "nnqs_measure_peaks FP32 FMA (measured)" if peaks_run else "derived FP32 peak",
-                "launches": f["launches"], "avg_launch_ms": avg_ms}
-    elif f["flops"] > 0:
-        achieved = f["flops"] / (f["ms"] / 1e3)
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "unit": "work/s", "peak": None,
-                "frac": None, "traffic": None, "launches": f["launches"], "avg_launch_ms": avg_ms}
-    else:
-        roof = {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "launches": f["launches"], "avg_launch_ms": avg_ms}
+    hpk = float(peaks.get("hbm_gbs", 6800.0))
+
+    def kernel_roofline(kname, kf):
+        avg = kf["ms"] / max(1, kf["launches"])
+        if kname in TENSOR_KERNELS:
+            # the ansatz's products are dense contractions: the bound is the
+            # tensor pipe (sustained BF16, the kernels run inside a long step),
+            # counted in the method's FLOPs (one product per layer, not the
+            # three BF16 products of split operands); the HBM rate of the bytes
+            # the launch sites attribute is given beside it
+            gbs = kf["bytes"] / (kf["ms"] / 1e3) / 1e9
+            tflops = kf["flops"] / (kf["ms"] / 1e3) / 1e12
+            traffic = (KERNEL_TRAFFIC_BYTES.get(kname) if args.n_samples == N_SAMPLES and args.prec == "bf16x3"
+                       else None)
+            return {"kernel": kname, "bound": "tensor", "achieved": tflops, "peak": tpk, "unit": "TFLOP/s",
+                    "frac": tflops / tpk, "traffic": traffic, "peak_source": tpk_src + " (of measured)",
+                    "flops_per_launch": kf["flops"] / max(1, kf["launches"]),
+                    "hbm": {"achieved_gbs": gbs, "peak_gbs": hpk, "frac": gbs / hpk,
+                            "algorithmic_bytes_per_launch": kf["bytes"] / max(1, kf["launches"]),
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"},
+                    "launches": kf["launches"], "avg_launch_ms": avg}
+        if kname == "k_gemm":
+            fpk = peaks_run.get("fp32_flops", FP32_PEAK_TFLOPS * 1e12) / 1e12
+            achieved = kf["flops"] / (kf["ms"] / 1e3) / 1e12
+            return {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fpk,
+                    "unit": "TFLOP/s", "frac": achieved / fpk, "traffic": None,
+                    "peak_source": "nnqs_measure_peaks FP32 FMA (measured)" if peaks_run else "derived FP32 peak",
+                    "launches": kf["launches"], "avg_launch_ms": avg}
+        if kname.startswith("k_sweep") and sweep_roofline(prof, peaks_run, 1):
+            return sweep_roofline(prof, peaks_run, 1)
+        return {"kernel": kname, "bound": "unknown", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launches": kf["launches"], "avg_launch_ms": avg}
+
+    roof = kernel_roofline(name, f)
     # the whole ansatz (forward + reverse mode + sampler) in method FLOPs
     # against the sustained tensor peak, and the sweep against the measured
     # XOR+popcount rate
     fwd = model_flops_per_sample(wl)
     n_u_step = n_u_total / max(1, args.steps * world)
     rooflines = {"sweep": sweep_roofline(prof, peaks_run, 1),
+                 "tensor_kernels": {k: kernel_roofline(k, prof[k]) for k in TENSOR_KERNELS if k in prof},
                  "energy_grad_ansatz": {
                      "bound": "tensor", "unit": "TFLOP/s", "peak": tpk,
                      "flops_per_step": 3.0 * fwd * n_u_step,
@@ -851,15 +857,18 @@ def run_case(args):
     """One hot-path call on a named workload, timed alone (three warm-up
     calls, then the mean of five with CUDA events): the sample-aware sweeps
     over uniform sector samples with a stand-in log psi table, the ansatz
-    forward (fused, or layer by layer), or exact-mode E_loc of the first rows.
+    forward (fused, or layer by layer), the forward with its reverse mode for
+    a random seed vector (fused, or layer by layer), or exact-mode E_loc of
+    the first rows.
     For profilers: the kernel of interest runs 8 times (3 warm-up + 5)."""
     import torch
 
     from paper_2306_16705_gb300 import binding as B
     from paper_2306_16705_gb300 import inputs as I
 
-    if args.case == "logpsi-unfused":
+    if args.case in ("logpsi-unfused", "grad-unfused"):
         os.environ["NNQS_FUSED_FORWARD"] = "0"
+        os.environ["NNQS_FUSED_BACKWARD"] = "0"
     wl = I.WORKLOADS[args.workload]
     S = I.random_sector_samples(wl.n_spatial, wl.n_alpha, wl.n_beta, args.n, seed=3)
     x = B.to_device_bits(S)
@@ -878,6 +887,11 @@ def run_case(args):
         if args.case == "eloc-exact":
             call = lambda: B.eloc(ham, x[:rows], None, wl.n_alpha, wl.n_beta, mode=B.EXACT, model=model,
                                   params=flat, prec=prec, check=False)
+        elif args.case.startswith("grad"):
+            # the ansatz forward and its reverse mode for a seed vector d E / d log psi
+            rng = np.random.default_rng(5)
+            seed = torch.from_numpy(np.stack([rng.normal(size=args.n), rng.normal(size=args.n)], 1)).cuda()
+            call = lambda: B.logpsi_backward(model, flat, x, seed, prec)
         else:
             call = lambda: B.logpsi(model, flat, x, prec, check=False)
     heavy = args.case == "eloc-exact"  # seconds per call at full size: one warm-up, two timed

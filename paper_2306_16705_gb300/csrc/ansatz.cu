@@ -23,6 +23,7 @@
 #include "model.h"
 #include "tc_gemm.h"
 #include "tc_gemm.cuh"
+#include "bwd_fused.cuh"
 #include "fwd_fused.cuh"
 
 namespace nnqs {
@@ -3033,6 +3034,7 @@ struct Grads {
     R *qkvsum;    // [C][3d] per-sample column sums of dqkv (qkv bias gradient)
     R *ucolpart;  // [ceil(C T / 128)][F] column sums of du per 128-row tile (FFN-in bias gradient)
     double2 *lp;  // forward output of the recomputation (not used further)
+    float *part;  // fused reverse mode: per-CTA partial gradients of one layer
 };
 
 template <class R>
@@ -3050,6 +3052,25 @@ void take_grads(const nnqs_model *M, int64_t C, Arena &a, Grads<R> &G) {
     G.lp = a.take<double2>(C);
     G.qkvsum = a.take<R>(C * 3 * d);
     G.ucolpart = a.take<R>((rows + 127) / 128 * F);
+    G.part = bwd_ffn_supported(M->d, M->F) ? a.take<float>(size_t(num_sms()) * kBwdFfnPart) : nullptr;
+}
+
+// Whether the reverse mode of the decoder layers runs fused (bwd_fused.cu),
+// from NNQS_FUSED_BACKWARD in the environment (read once): 0 = the
+// layer-by-layer reverse mode (for comparisons), else fused where it applies
+// (BF16 / split BF16 forward operands, d = 64, FFN width 256).
+bool fused_bwd_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("NNQS_FUSED_BACKWARD");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+// the decoder layers' reverse mode runs fused for this model and weights
+bool fused_bwd_applies(const nnqs_model *M, const TcWeights *tcw) {
+    return tcw && !tcw->fp8 && fused_bwd_enabled() && bwd_ffn_supported(M->d, M->F) &&
+           bwd_attn_supported(M->d, M->dh, M->T);
 }
 
 template <class R>
@@ -3109,6 +3130,8 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     // (the column sums of the new dh are the last layer's FFN-out bias gradient)
     NNQS_TRY(ln_bwd_sums<R>(s, hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d, gacc + Lo.lnf_g,
                             gacc + Lo.lnf_b, gacc + Lo.layer[L - 1].b2, scr));
+    const bool fused_ffn = sizeof(R) == 4 && G.part && fused_bwd_applies(M, tcw);
+    const bool fused_attn = fused_ffn;
     for (int l = L - 1; l >= 0; --l) {
         const auto &Lw = V.layer[l];
         const auto &Lg = Lo.layer[l];
@@ -3119,19 +3142,65 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
         const R *u = A.u + (int64_t)l * rows * F, *gu = A.gu + (int64_t)l * rows * F;
         // FFN: hout = hmid + gelu(a2 W1^T + b1) W2^T + b2
         // (b2's gradient came with the LayerNorm backward that produced dh)
-        NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
-        bool ucols = false;  // column sums of du per 128-row tile, from the input-gradient epilogue
-        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr, 1, u, G.ucolpart, &ucols));
-        NNQS_TRY(bw_dw<R>(s, tcw, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
-        if (ucols)
-            NNQS_TRY(colsum<R>(s, 0, G.ucolpart, nullptr, nullptr, nullptr, (rows + 127) / 128, F, gacc + Lg.b1,
-                               nullptr, scr));
-        else
-            NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, nullptr, scr));
-        NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 2), G.du, rows, F, Lw.w1, d, G.dtmp, scr));
-        NNQS_TRY(ln_bwd_sums<R>(s, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g, G.dtmp, G.dh, rows, d,
-                                gacc + Lg.ln2_g, gacc + Lg.ln2_b, gacc + Lg.bo, scr));
+        bool ffn_done = false;
+        if constexpr (sizeof(R) == 4) {
+            if (fused_ffn) {
+                const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(tcw->tiles);
+                BwdFfnArgs fa{};
+                fa.hmid = hmid;
+                fa.dh = G.dh;
+                fa.rows = rows;
+                fa.ln2g = Lw.ln2g;
+                fa.ln2b = Lw.ln2b;
+                fa.b1 = Lw.b1;
+                fa.t1 = tiles + tcw->tile_off[tc_slot(l, 2)];
+                fa.t2 = tiles + tcw->tile_off[tc_slot(l, 3)];
+                fa.part = G.part;
+                fa.st = tcw->st;
+                NNQS_TRY(bwd_ffn_launch(fa, tcw->split, s));
+                NNQS_TRY(bwd_ffn_reduce(G.part, bwd_ffn_grid(rows), gacc + Lg.w1, gacc + Lg.w2, gacc + Lg.b1,
+                                        gacc + Lg.ln2_g, gacc + Lg.ln2_b, gacc + Lg.bo, s));
+                ffn_done = true;
+            }
+        }
+        if (!ffn_done) {
+            NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, gu, F, gacc + Lg.w2, scr));
+            bool ucols = false;  // column sums of du per 128-row tile, from the input-gradient epilogue
+            NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 3), G.dh, rows, d, Lw.w2, F, G.du, scr, 1, u, G.ucolpart, &ucols));
+            NNQS_TRY(bw_dw<R>(s, tcw, G.du, rows, F, a2, d, gacc + Lg.w1, scr));
+            if (ucols)
+                NNQS_TRY(colsum<R>(s, 0, G.ucolpart, nullptr, nullptr, nullptr, (rows + 127) / 128, F, gacc + Lg.b1,
+                                   nullptr, scr));
+            else
+                NNQS_TRY(colsum<R>(s, 0, G.du, nullptr, nullptr, nullptr, rows, F, gacc + Lg.b1, nullptr, scr));
+            NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 2), G.du, rows, F, Lw.w1, d, G.dtmp, scr));
+            NNQS_TRY(ln_bwd_sums<R>(s, hmid, A.mean2 + l * rows, A.rstd2 + l * rows, Lw.ln2g, G.dtmp, G.dh, rows, d,
+                                    gacc + Lg.ln2_g, gacc + Lg.ln2_b, gacc + Lg.bo, scr));
+        }
         // attention: hmid = hin + attn(a) Wo^T + bo
+        if constexpr (sizeof(R) == 4) {
+            if (fused_attn) {
+                const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(tcw->tiles);
+                BwdAttnArgs aa{};
+                aa.hin = hin;
+                aa.dh = G.dh;
+                aa.n = C;
+                aa.T = T;
+                aa.spt = 128 / T;
+                aa.ln1g = Lw.ln1g;
+                aa.ln1b = Lw.ln1b;
+                aa.bqkv = Lw.bqkv;
+                aa.tqkv = tiles + tcw->tile_off[tc_slot(l, 0)];
+                aa.to = tiles + tcw->tile_off[tc_slot(l, 1)];
+                aa.part = G.part;
+                aa.st = tcw->st;
+                NNQS_TRY(bwd_attn_launch(aa, tcw->split, M->dh, s));
+                NNQS_TRY(bwd_attn_reduce(G.part, bwd_attn_grid(C, T), gacc + Lg.wqkv, gacc + Lg.wo, gacc + Lg.bqkv,
+                                         gacc + Lg.ln1_g, gacc + Lg.ln1_b, l > 0 ? gacc + Lo.layer[l - 1].b2 : nullptr,
+                                         s));
+                continue;
+            }
+        }
         NNQS_TRY(bw_dw<R>(s, tcw, G.dh, rows, d, o, d, gacc + Lg.wo, scr));
         NNQS_TRY(bw_dx<R>(s, tcw, tc_slot(l, 1), G.dh, rows, d, Lw.wo, d, G.dtmp, scr));
         bool qsums = false;
@@ -3261,24 +3330,29 @@ template <class R>
 nnqs_status forward_keep(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
                          double2 *out, DevStatus *st, int64_t row_offset, const TcWeights *tcw, cudaStream_t s) {
     if constexpr (sizeof(R) == 4) {
-        if (tcw && !tcw->fp8 && A.keep && fused_fwd_level() >= 2 &&
+        // the fused reverse mode recomputes each layer from its input and
+        // hmid: the fused forward then writes only those (and the head's)
+        const bool lite = fused_bwd_applies(M, tcw);
+        if (tcw && !tcw->fp8 && A.keep && (fused_fwd_level() >= 2 || (lite && fused_fwd_level() >= 1)) &&
             fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L)) {
             FusedFwdArgs a = fused_args(M, V, *tcw, x, C, out, st, row_offset);
             if (!fused_fwd_aligned(a)) return forward_chunk<R>(M, V, x, C, A, out, st, row_offset, tcw, s);
             a.rows = C * M->T;
             a.hbuf = A.hbuf;
-            a.a = A.a;
-            a.a2 = A.a2;
             a.hmid = A.hmid;
-            a.o = A.o;
-            a.qkv = A.qkv;
-            a.u = A.u;
-            a.gu = A.gu;
-            a.mean1 = A.mean1;
-            a.rstd1 = A.rstd1;
-            a.mean2 = A.mean2;
-            a.rstd2 = A.rstd2;
-            a.lse = A.lse;
+            if (!lite) {
+                a.a = A.a;
+                a.a2 = A.a2;
+                a.o = A.o;
+                a.qkv = A.qkv;
+                a.u = A.u;
+                a.gu = A.gu;
+                a.mean1 = A.mean1;
+                a.rstd1 = A.rstd1;
+                a.mean2 = A.mean2;
+                a.rstd2 = A.rstd2;
+                a.lse = A.lse;
+            }
             a.hf = A.hf;
             a.meanf = A.meanf;
             a.rstdf = A.rstdf;
@@ -3461,6 +3535,15 @@ nnqs_status launch_decode_layer(const DecodeArgs &g, cudaStream_t s) {
 // one layer of the cached decode for n new tokens (rows h) in one launch
 // n_dev / g0_dev (optional): the counts live on the device; n is then the
 // capacity (an upper bound of *n_dev) and g0 is ignored
+// the four GEMMs of one fused decode layer over n prefixes (method FLOPs) and
+// its bytes: the new k | v rows and the layer's input and output rows, the
+// weight images once
+void note_decode_work(int64_t n, bool split) {
+    note_work("k_decode_layer", 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
+              4.0 * double(n) * (2 * dec::kD + dec::kQKV) +
+                  2.0 * (split ? 2.0 : 1.0) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF));
+}
+
 nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
                                float *h, int64_t n, float *pool, const int32_t *anc, int t, int64_t g0, int l,
                                double *cond, DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
@@ -3511,10 +3594,9 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
     g.t1 = tiles + w.tile_off[tc_slot(l, 2)];
     g.t2 = tiles + w.tile_off[tc_slot(l, 3)];
     g.st = st;
-    // work per launch (for the profile): the four GEMMs of the layer
-    note_work("k_decode_layer", 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
-              4.0 * double(n) * (2 * dec::kD + dec::kQKV) + 2.0 * (w.split ? 2.0 : 1.0) *
-                                                                 (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF));
+    // work per launch (for the profile); with the level size on the device
+    // the walk notes it once the size is known (n is the capacity here)
+    if (!n_dev) note_decode_work(n, w.split);
     if (w.split) return M->dh == 8 ? launch_decode_layer<true, 8>(g, s) : launch_decode_layer<true, 16>(g, s);
     return M->dh == 8 ? launch_decode_layer<false, 8>(g, s) : launch_decode_layer<false, 16>(g, s);
 }
@@ -3653,6 +3735,12 @@ nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64
     if (!cond_cached_dev_ok(M, ctx, cap)) return set_error(NNQS_E_UNSUPPORTED, "no fused decode for this model");
     ctx->tcw.st = st;
     const Views<float> V = make_views<float>(M, static_cast<float *>(ctx->params));
+    if (profiling_on()) {  // the level's size, for the profile's work count (profiling runs wait anyway)
+        int64_t n = 0;
+        NNQS_CUDA_TRY(cudaMemcpyAsync(&n, n_dev, 8, cudaMemcpyDeviceToHost, s));
+        NNQS_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int l = 0; l < M->L; ++l) note_decode_work(n, ctx->tcw.split);
+    }
     for (int l = 0; l < M->L; ++l)
         NNQS_TRY(decode_layer_fused(M, V, ctx->tcw, prefixes, ctx->Af.hbuf, cap, static_cast<float *>(ctx->pool), anc,
                                     t, 0, l, cond, st, s, n_dev, g0_dev));

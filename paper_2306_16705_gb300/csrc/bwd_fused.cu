@@ -1,0 +1,1044 @@
+// Fused reverse mode of the decoder layers (Sec. 3.1; the energy gradient of
+// Sec. 2.1) on tcgen05 tensor cores.
+//
+// FFN half of a layer (k_bwd_ffn), per 128-row tile of token rows:
+//   a2 = LN2(hmid)                       (recomputed, split BF16 when the forward was)
+//   u = a2 W1^T + b1, gu = GELU(u)       (recomputed on the tensor cores)
+//   dgu = dy W2, du = dgu * GELU'(u)
+//   da2 = du W1, dhmid = dy + LN2'(da2)  (written over dy)
+//   dW2 += dy^T gu, dW1 += du^T a2, db1 += sum du, dgamma2 / dbeta2 / dbo
+// The FFN width is walked in two halves of 128 so that the weight-gradient
+// accumulators (dW1 and dW2^T, 256 TMEM columns) stay in TMEM over every tile
+// of the CTA; the weight-gradient products read their operands transposed
+// (MN-major descriptors) from the same swizzled tiles the other products read
+// K-major, so nothing is copied to transpose it.  Each CTA writes one
+// partial; bwd_ffn_reduce adds them in CTA order (deterministic).
+//
+// Shared memory (1024-aligned base):
+//   [0, 32K)      a2 hi / lo            [128][64] BF16, 128-byte swizzle
+//   [32K, 48K)    dy                    [128][64] BF16
+//   [48K, 80K)    gu of the half        two [128][64] panels
+//   [80K, 112K)   du of the half        two [128][64] panels
+//   [112K, 176K)  W1 image hi / lo      [256][64]
+//   [176K, 208K)  W2 image hi           four [64][64] K blocks
+//   [208K, 216K)  row-sum exchange, then the column-sum combine
+// TMEM: dW1 [0, 128) (halves 64 columns each), dW2^T [128, 256), u / dgu of
+// the half [256, 384), da2 [384, 448).
+//
+// Every wait is bounded (tc::mbar_wait): on a timeout the CTA records
+// NNQS_E_TIMEOUT, lets its weight copies land (bounded) and frees its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "bwd_fused.cuh"
+#include "dev_common.cuh"
+#include "tc_gemm.cuh"
+
+namespace nnqs {
+namespace {
+namespace fb {
+constexpr int kThreads = 512, kRows = 128, kD = 64, kF = 256;
+constexpr int kOffA = 0, kOffA2 = 16384, kOffDY = 32768, kOffGU = 49152, kOffDU = 81920;
+constexpr int kOffW1 = 114688, kOffW2 = 180224, kOffRed = 212992;
+constexpr int kOffBar = kOffRed + 8192;
+constexpr int kSmem = kOffBar + 64 + 1024;  // 222,272 bytes
+constexpr uint32_t kColW1 = 0, kColW2 = 128, kColU = 256, kColDA = 384, kTmemCols = 512;
+constexpr int kCols = 448;  // column sums combined per CTA: db1 256 | dgamma2 64 | dbeta2 64 | dbo 64
+}  // namespace fb
+
+__device__ __forceinline__ void fb_bulk(uint8_t *dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// shared-memory descriptor of an MN-major (transposed) operand, 128-byte
+// swizzle: 128-byte rows of 64 BF16 along M (or N), one row per K index,
+// 8-row groups along K 1024 bytes apart, 64-wide M (N) blocks `lbo` bytes apart
+__device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t(1024u >> 4) << 32;
+    d |= uint64_t(1) << 46;
+    d |= uint64_t(2) << 61;
+    return d;
+}
+
+// kind::f16 instruction descriptor (BF16 in, FP32 out) with the transpose
+// (MN-major) flags of A and B
+__device__ __forceinline__ uint32_t idesc_t(int M, int N, bool ta, bool tb) {
+    return tc::idesc_bf16(M, N) | (uint32_t(ta) << 15) | (uint32_t(tb) << 16);
+}
+
+__device__ __forceinline__ float fb_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// GELU(x) = x Phi(x) and GELU'(x) = Phi(x) + x phi(x), with erf from
+// Abramowitz and Stegun (1964) eq. 7.1.26 as in the fused forward (absolute
+// error at most 1.5e-7); e^{-x^2 / 2} serves both erf and phi
+__device__ __forceinline__ void fb_gelu2(float x, float &g, float &dg) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float e = fb_ex2(-(z * z) * 1.44269504088896340736f);
+    const float phi_cdf = 0.5f * (1.0f + copysignf(1.0f - poly * e, x));
+    g = x * phi_cdf;
+    dg = phi_cdf + x * e * 0.39894228040143267794f;
+}
+
+// 16 floats from a 16-byte aligned address (read-only data)
+__device__ __forceinline__ void fb_ldg16(const float *__restrict__ p, float (&v)[16]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + k);
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
+    }
+}
+// 16 floats from global memory this kernel also writes
+__device__ __forceinline__ void fb_ld16(const float *p, float (&v)[16]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[k];
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
+    }
+}
+__device__ __forceinline__ void fb_st16(float *p, const float *v) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        reinterpret_cast<float4 *>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+
+// 8 values as granule `gi` of row r of a swizzled [128][64] BF16 panel (hi),
+// and their low parts v - bf16(v) in `lo` when given
+__device__ __forceinline__ void fb_granule(uint8_t *hi, uint8_t *lo, int r, int gi, const float *v) {
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = v[e];
+    const int off = r * 128 + ((gi ^ (r & 7)) << 4);
+    *reinterpret_cast<uint4 *>(hi + off) = tc::pack8(x);
+    if (lo) {
+        float y[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = x[e] - __bfloat162float(__float2bfloat16_rn(x[e]));
+        *reinterpret_cast<uint4 *>(lo + off) = tc::pack8(y);
+    }
+}
+
+// Sums over the warp's 32 lanes (one row each) of v[0 .. N): recursive
+// halving, each lane keeping the half of the remaining columns its lane bit
+// selects and adding the partner's copy of them (N - 1 shuffles).  Lane l
+// returns the sum of column l (N = 32) or of column l >> 1 (N = 16).  v is
+// consumed.
+template <int N>
+__device__ __forceinline__ float fb_colsum(float (&v)[N], int lane) {
+    static_assert(N == 32 || N == 16, "16 or 32 columns");
+#pragma unroll
+    for (int half = N / 2, m = 16; half >= 1; half >>= 1, m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = up ? v[i] : v[i + half];
+            const float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    float r = v[0];
+    if (N == 16) r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
+// one 128 x N product over K = 64 (four K = 16 steps) from K-major A and B
+// tiles; with split operands lo.hi + hi.lo + hi.hi per step
+__device__ __forceinline__ void fb_mma_kmajor(uint32_t tmem, uint32_t aHi, uint32_t aLo, uint32_t bHi, uint32_t bLo,
+                                              int N, bool split, bool acc0) {
+    const uint32_t idesc = tc::idesc_bf16(fb::kRows, N);
+    const uint64_t da = tc::desc_sw128(aHi), db = tc::desc_sw128(bHi);
+    const uint64_t da2 = tc::desc_sw128(aLo), db2 = tc::desc_sw128(bLo);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t acc = (acc0 || k > 0) ? 1u : 0u;
+        if (split) {
+            tc::mma_bf16(tmem, da2 + uint64_t(2 * k), db + uint64_t(2 * k), idesc, acc);
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db2 + uint64_t(2 * k), idesc, 1u);
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, 1u);
+        } else {
+            tc::mma_bf16(tmem, da + uint64_t(2 * k), db + uint64_t(2 * k), idesc, acc);
+        }
+    }
+}
+
+// D[M = 128][N] (+)= A^T B over the tile's 128 rows (K): A and B are row-major
+// [128 rows][features] swizzled tiles read MN-major; A spans two 64-feature
+// panels `lboA` bytes apart, B one
+__device__ __forceinline__ void fb_mma_rows(uint32_t tmem, uint32_t a, uint32_t lboA, uint32_t b, int N, bool acc0) {
+    const uint32_t idesc = idesc_t(fb::kRows, N, true, true);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        tc::mma_bf16(tmem, desc_mn(a + 2048u * k, lboA), desc_mn(b + 2048u * k, 16384u), idesc,
+                     (acc0 || k > 0) ? 1u : 0u);
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_constant__ BwdFfnArgs g) {
+    using namespace fb;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sb = smem_raw + (base - raw);
+    float *red = reinterpret_cast<float *>(sb + kOffRed);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 32);
+    const uint32_t mb = base + kOffBar, bW = mb + 8;
+    const uint32_t uA = base + kOffA, uA2 = base + kOffA2, uDY = base + kOffDY, uGU = base + kOffGU;
+    const uint32_t uDU = base + kOffDU, uW1 = base + kOffW1, uW2 = base + kOffW2;
+    uint8_t *aHi = sb + kOffA, *aLo = SPLIT ? sb + kOffA2 : nullptr;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
+    const int64_t n_tiles = (g.rows + kRows - 1) / kRows;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::mbar_init(bW, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
+
+    // the weight images, once per CTA
+    constexpr uint32_t kWB = kF * kD * 2;  // 32 KB
+    if (tid == 0) {
+        tc::mbar_expect(bW, (SPLIT ? 3u : 2u) * kWB);
+        fb_bulk(sb + kOffW1, g.t1, kWB, bW);
+        if (SPLIT) fb_bulk(sb + kOffW1 + kWB, static_cast<const __nv_bfloat16 *>(g.t1) + kF * kD, kWB, bW);
+        fb_bulk(sb + kOffW2, g.t2, kWB, bW);
+    }
+    bool ok = __syncthreads_and(tc::mbar_wait(bW, 0) ? 1 : 0) != 0;
+    const bool w_landed = ok;
+    uint32_t ph = 0;
+    auto sync_async = [&]() {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+    auto wait_mma = [&]() {
+        ok = __syncthreads_and(tc::mbar_wait(mb, ph) ? 1 : 0) != 0;
+        ph ^= 1u;
+        tc::fence_after_sync();
+    };
+
+    float cs_b1a = 0.f, cs_b1b = 0.f, cs_g = 0.f, cs_b = 0.f, cs_o = 0.f;  // column sums (db1 halves, LN2, dbo)
+    bool first = true;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t gr = tile * kRows + row;
+        const bool valid = gr < g.rows;
+        // ---- LN2 of the saved residual rows -> a2 (A); dy -> DY
+        // (thread: row `row`, columns 16 cq .. 16 cq + 15; rows past the end are zero)
+        float mu, rs;
+        {
+            float hv[16], dv[16];
+            if (valid) {
+                fb_ldg16(g.hmid + gr * kD + 16 * cq, hv);
+                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
+            }
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) s += hv[c];
+            red[row * 4 + cq] = s;
+            __syncthreads();
+            mu = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
+            float q = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) q += (hv[c] - mu) * (hv[c] - mu);
+            red[512 + row * 4 + cq] = q;
+            __syncthreads();
+            rs = 1.0f / sqrtf((red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
+                               red[512 + row * 4 + 3]) * (1.0f / kD) + 1e-5f);
+            float gv[16], bv[16], y[16];
+            fb_ldg16(g.ln2g + 16 * cq, gv);
+            fb_ldg16(g.ln2b + 16 * cq, bv);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) y[c] = valid ? (hv[c] - mu) * rs * gv[c] + bv[c] : 0.f;
+            fb_granule(aHi, aLo, row, 2 * cq, y);
+            fb_granule(aHi, aLo, row, 2 * cq + 1, y + 8);
+            fb_granule(sb + kOffDY, nullptr, row, 2 * cq, dv);
+            fb_granule(sb + kOffDY, nullptr, row, 2 * cq + 1, dv + 8);
+        }
+        sync_async();
+        if (tid == 0) {
+            fb_mma_kmajor(tmem + kColU, uA, uA2, uW1, uW1 + kWB, 128, SPLIT, false);
+            tc::mma_commit(mb);
+        }
+        for (int h = 0; h < 2 && ok; ++h) {
+            wait_mma();
+            if (!ok) break;
+            // ---- GELU of u = U_h + b1 -> gu (BF16); GELU'(u) kept
+            float gp[32];
+            uint8_t *gpan = sb + kOffGU + (cq >> 1) * 16384;
+            uint8_t *dpan = sb + kOffDU + (cq >> 1) * 16384;
+            const int gbase = 4 * (cq & 1);
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColU + 32 * cq + 16 * hf, r16);
+                float bv[16], x[16];
+                fb_ldg16(g.b1 + 128 * h + 32 * cq + 16 * hf, bv);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) fb_gelu2(__uint_as_float(r16[j]) + bv[j], x[j], gp[16 * hf + j]);
+                fb_granule(gpan, nullptr, row, gbase + 2 * hf, x);
+                fb_granule(gpan, nullptr, row, gbase + 2 * hf + 1, x + 8);
+            }
+            sync_async();
+            if (tid == 0) {
+                // dgu_h = dy W2[:, half h]: B is the FFN-out image read
+                // transposed (K = its 64 rows, N = 128 of its columns)
+                const uint32_t id = idesc_t(kRows, 128, false, true);
+                const uint64_t dA = tc::desc_sw128(uDY);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc::mma_bf16(tmem + kColU, dA + uint64_t(2 * k), desc_mn(uW2 + 2u * h * 8192u + 2048u * k, 8192u),
+                                 id, k > 0 ? 1u : 0u);
+                // dW2^T[half h] += gu_h^T dy
+                fb_mma_rows(tmem + kColW2 + 64 * h, uGU, 16384u, uDY, kD, !first);
+                tc::mma_commit(mb);
+            }
+            wait_mma();
+            if (!ok) break;
+            // ---- du = dgu * GELU'(u) -> DU (BF16); column sums for db1
+            float du[32];
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColU + 32 * cq + 16 * hf, r16);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) du[16 * hf + j] = __uint_as_float(r16[j]) * gp[16 * hf + j];
+                fb_granule(dpan, nullptr, row, gbase + 2 * hf, du + 16 * hf);
+                fb_granule(dpan, nullptr, row, gbase + 2 * hf + 1, du + 16 * hf + 8);
+            }
+            const float csu = fb_colsum<32>(du, lane);
+            if (h == 0)
+                cs_b1a += csu;
+            else
+                cs_b1b += csu;
+            sync_async();
+            if (tid == 0) {
+                // da2 += du_h W1[half h]: B is the FFN-in image read
+                // transposed (K = 128 of its rows, N = its 64 columns)
+                const uint32_t id = idesc_t(kRows, kD, false, true);
+#pragma unroll
+                for (int kb = 0; kb < 2; ++kb) {
+                    const uint64_t dA = tc::desc_sw128(uDU + 16384u * kb);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tc::mma_bf16(tmem + kColDA, dA + uint64_t(2 * k),
+                                     desc_mn(uW1 + uint32_t(128 * h + 64 * kb + 16 * k) * 128u, 16384u), id,
+                                     (h | kb | k) ? 1u : 0u);
+                }
+                // dW1[half h] += du_h^T a2
+                fb_mma_rows(tmem + kColW1 + 64 * h, uDU, 16384u, uA, kD, !first);
+                // the second half's u (over the first half's dgu, read above)
+                if (h == 0) fb_mma_kmajor(tmem + kColU, uA, uA2, uW1 + 16384u, uW1 + kWB + 16384u, 128, SPLIT, false);
+                tc::mma_commit(mb);
+            }
+        }
+        if (!ok) break;
+        wait_mma();
+        if (!ok) break;
+        // ---- LN2 backward: dhmid = dy + rs (da2 g - mean(da2 g) - xh mean(da2 g xh))
+        {
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
+            float hv[16], dv[16], gv[16], da[16], xh[16];
+            if (valid) {
+                fb_ldg16(g.hmid + gr * kD + 16 * cq, hv);
+                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
+            }
+            fb_ldg16(g.ln2g + 16 * cq, gv);
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                da[c] = __uint_as_float(r16[c]);
+                xh[c] = valid ? (hv[c] - mu) * rs : 0.f;
+                const float dx = da[c] * gv[c];
+                s1 += dx;
+                s2 += dx * xh[c];
+            }
+            red[row * 4 + cq] = s1;
+            red[512 + row * 4 + cq] = s2;
+            __syncthreads();
+            const float m1 = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
+            const float m2 = (red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
+                              red[512 + row * 4 + 3]) * (1.0f / kD);
+            float out[16], t[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) out[c] = valid ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
+            if (valid) fb_st16(g.dh + gr * kD + 16 * cq, out);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) t[c] = da[c] * xh[c];
+            cs_g += fb_colsum<16>(t, lane);
+            cs_b += fb_colsum<16>(da, lane);
+            cs_o += fb_colsum<16>(out, lane);
+        }
+        __syncthreads();
+        first = false;
+    }
+    if (ok && !first) {
+        // ---- this CTA's partial: the TMEM accumulators, then the column sums
+        // of the four row quadrants added in order
+        float *part = g.part + (int64_t)blockIdx.x * kBwdFfnPart;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColW1 + 64 * h + 16 * cq, r16);
+            float v[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r16[c]);
+            fb_st16(part + (128 * h + row) * kD + 16 * cq, v);
+            tc::tmem_ld16(tl + kColW2 + 64 * h + 16 * cq, r16);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) part[kF * kD + (16 * cq + c) * kF + 128 * h + row] = __uint_as_float(r16[c]);
+        }
+        float *cs = red + q4 * kCols;
+        cs[32 * cq + lane] = cs_b1a;
+        cs[128 + 32 * cq + lane] = cs_b1b;
+        if ((lane & 1) == 0) {
+            cs[256 + 16 * cq + (lane >> 1)] = cs_g;
+            cs[320 + 16 * cq + (lane >> 1)] = cs_b;
+            cs[384 + 16 * cq + (lane >> 1)] = cs_o;
+        }
+        __syncthreads();
+        for (int e = tid; e < kCols; e += kThreads)
+            part[2 * kF * kD + e] = ((red[e] + red[kCols + e]) + red[2 * kCols + e]) + red[3 * kCols + e];
+    }
+    if (!ok && tid == 0) {
+        if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -14;
+        if (!w_landed) tc::mbar_wait(bW, 0);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(fb::kTmemCols)
+                     : "memory");
+    }
+}
+
+// sum over `grid` CTA partials, in CTA order, added into the gradients
+__global__ void k_bwd_ffn_reduce(const float *__restrict__ part, int grid, float *dw1, float *dw2, float *db1,
+                                 float *dg2, float *db2, float *dbo) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kBwdFfnPart) return;
+    float s = 0.f;
+    for (int c = 0; c < grid; ++c) s += part[(int64_t)c * kBwdFfnPart + e];
+    constexpr int a = 256 * 64, b = 2 * a, c1 = b + 256, c2 = c1 + 64, c3 = c2 + 64;
+    float *dst = e < a ? dw1 + e : e < b ? dw2 + (e - a) : e < c1 ? db1 + (e - b) : e < c2 ? dg2 + (e - c1)
+                 : e < c3 ? db2 + (e - c2) : dbo + (e - c3);
+    *dst += s;
+}
+
+// ---------------------------------------------------------------------------
+// Attention half of a layer (k_bwd_attn), per tile of floor(128 / T) whole
+// samples (a sample's tokens never leave its tile, so the causal attention
+// and its reverse mode need no other tile):
+//   a = LN1(hin), q | k | v = a Wqkv^T + bqkv    (recomputed; split BF16 when the forward was)
+//   do = dhmid Wo                                 (tensor cores)
+//   per head: o, log-sum-exp recomputed; D = do . o; P = softmax;
+//     dq = scale sum_j P (do . v_j - D) k_j, dk, dv over the later queries  (CUDA cores, FP32)
+//   da = dqkv Wqkv, dh_in = dhmid + LN1'(da)     (written over dhmid)
+//   dWqkv += dqkv^T a, dWo += dhmid^T o, dbqkv, dgamma1 / dbeta1, sum dh_in
+// The heads are walked in two groups of 32 columns of q | k | v | do, whose
+// FP32 values go through shared memory for the other rows of the sample.
+//
+// Shared memory (1024-aligned base):
+//   [0, 32K)       a hi / lo                 [128][64] BF16
+//   [32K, 48K)     dhmid                     [128][64] BF16
+//   [48K, 64K)     o                         [128][64] BF16 (right after dhmid:
+//                                            the second 64-row block of the dWo product's A)
+//   [64K, 112K)    dq | dk | dv              three [128][64] panels
+//   [112K, 178K)   the group's q | k | v | do [128][132] FP32 (the qkv image's low
+//                                            part at the start of a tile)
+//   [178K, 202K)   qkv image hi              [192][64]
+//   [202K, 210K)   out-projection image hi   [64][64]
+//   [210K, 218K)   row-sum exchange, the group's log-sum-exp and D; the column-sum combine
+// TMEM: dWqkv [0, 128) (rows 0..127, then rows 64..191), dWo [128, 192)
+// (lanes 0..63), q | k | v [192, 384), do [384, 448), da [448, 512).
+namespace fa {
+constexpr int kThreads = 512, kRows = 128, kD = 64, kQKV = 192;
+constexpr int kOffA = 0, kOffA2 = 16384, kOffDH = 32768, kOffO = 49152, kOffDQ = 65536;
+constexpr int kOffS = 114688, kSS = 132;  // scratch row stride (floats)
+constexpr int kOffWQ = 182272, kOffWO = 206848, kOffRed = 215040;
+constexpr int kOffBar = kOffRed + 8192;
+constexpr int kSmem = kOffBar + 64 + 1024;  // 224,320 bytes
+constexpr uint32_t kColWQ = 0, kColWO = 128, kColQKV = 192, kColDO = 384, kColDA = 448, kTmemCols = 512;
+constexpr int kCols = 384;  // column sums per CTA: dbqkv 192 | dgamma1 64 | dbeta1 64 | dsum 64
+constexpr float kLog2e = 1.44269504088896340736f;
+}  // namespace fa
+
+// DH consecutive TMEM columns of this warp's 32 lanes
+template <int DH>
+__device__ __forceinline__ void fa_tmem_ld(uint32_t taddr, float (&v)[DH]) {
+    if constexpr (DH == 16) {
+        uint32_t r[16];
+        tc::tmem_ld16(taddr, r);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+    } else {
+        uint32_t r[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+    }
+}
+
+template <int DH>
+__device__ __forceinline__ void fa_ld(const float *p, float (&v)[DH]) {
+#pragma unroll
+    for (int k = 0; k < DH / 4; ++k) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[k];
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
+    }
+}
+template <int DH>
+__device__ __forceinline__ void fa_st(float *p, const float (&v)[DH]) {
+#pragma unroll
+    for (int k = 0; k < DH / 4; ++k)
+        reinterpret_cast<float4 *>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <int DH>
+__device__ __forceinline__ float fa_dot(const float (&a)[DH], const float (&b)[DH]) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) s = fmaf(a[c], b[c], s);
+    return s;
+}
+
+template <bool SPLIT, int DH>
+__global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_constant__ BwdAttnArgs g) {
+    using namespace fa;
+    constexpr int HPG = 32 / DH;  // heads per group of 32 columns
+    static_assert(HPG * DH == 32, "head dimension 8 or 16");
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sb = smem_raw + (base - raw);
+    float *red = reinterpret_cast<float *>(sb + kOffRed);
+    float *sS = reinterpret_cast<float *>(sb + kOffS);
+    float *sLse = red + 1024, *sD = red + 1536;  // [128][4] each
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 32);
+    const uint32_t mb = base + kOffBar, bW = mb + 8, bL = mb + 16;
+    const uint32_t uA = base + kOffA, uA2 = base + kOffA2, uDH = base + kOffDH, uO = base + kOffO;
+    const uint32_t uDQ = base + kOffDQ, uS = base + kOffS, uWQ = base + kOffWQ, uWO = base + kOffWO;
+    uint8_t *aHi = sb + kOffA, *aLo = SPLIT ? sb + kOffA2 : nullptr;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
+    const int T = g.T, rows_used = g.spt * T;
+    const int64_t rows = g.n * T, n_tiles = (g.n + g.spt - 1) / g.spt;
+    const int tt = row % T, r0 = row - tt;  // the row's token and its sample's first row in the tile
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::mbar_init(bW, 1);
+        tc::mbar_init(bL, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
+
+    constexpr uint32_t kWQB = kQKV * 128, kWOB = kD * 128;  // 24 KB, 8 KB
+    if (tid == 0) {
+        tc::mbar_expect(bW, kWQB + kWOB);
+        fb_bulk(sb + kOffWQ, g.tqkv, kWQB, bW);
+        fb_bulk(sb + kOffWO, g.to, kWOB, bW);
+    }
+    bool ok = __syncthreads_and(tc::mbar_wait(bW, 0) ? 1 : 0) != 0;
+    const bool w_landed = ok;
+    uint32_t ph = 0, n_lo = 0, d_lo = 0;  // low-part copies issued / waited
+    auto sync_async = [&]() {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+    auto wait_mma = [&]() {
+        ok = __syncthreads_and(tc::mbar_wait(mb, ph) ? 1 : 0) != 0;
+        ph ^= 1u;
+        tc::fence_after_sync();
+    };
+    const float qscale = (1.0f / sqrtf(float(DH))) * kLog2e;  // scores in base-2 units
+    const float scale = 1.0f / sqrtf(float(DH));
+
+    float csq00 = 0.f, csq01 = 0.f, csq10 = 0.f, csq11 = 0.f;  // dbqkv column sums per group (see the flush)
+    float cs_g = 0.f, cs_b = 0.f, cs_o = 0.f;
+    bool first = true;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t s0 = tile * g.spt;
+        const int64_t gr = s0 * T + row;
+        const bool valid = row < rows_used && gr < rows;
+        if (SPLIT && tid == 0) {  // the qkv image's low part into the scratch region
+            tc::fence_async_smem();
+            tc::mbar_expect(bL, kWQB);
+            fb_bulk(sb + kOffS, static_cast<const __nv_bfloat16 *>(g.tqkv) + kQKV * kD, kWQB, bL);
+        }
+        if (SPLIT) ++n_lo;
+        // ---- LN1 of the saved layer input -> a (A); dhmid -> DH
+        float mu, rs;
+        {
+            float hv[16], dv[16];
+            if (valid) {
+                fb_ldg16(g.hin + gr * kD + 16 * cq, hv);
+                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
+            }
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) s += hv[c];
+            red[row * 4 + cq] = s;
+            __syncthreads();
+            mu = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
+            float q = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) q += (hv[c] - mu) * (hv[c] - mu);
+            red[512 + row * 4 + cq] = q;
+            __syncthreads();
+            rs = 1.0f / sqrtf((red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
+                               red[512 + row * 4 + 3]) * (1.0f / kD) + 1e-5f);
+            float gv[16], bv[16], y[16];
+            fb_ldg16(g.ln1g + 16 * cq, gv);
+            fb_ldg16(g.ln1b + 16 * cq, bv);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) y[c] = valid ? (hv[c] - mu) * rs * gv[c] + bv[c] : 0.f;
+            fb_granule(aHi, aLo, row, 2 * cq, y);
+            fb_granule(aHi, aLo, row, 2 * cq + 1, y + 8);
+            fb_granule(sb + kOffDH, nullptr, row, 2 * cq, dv);
+            fb_granule(sb + kOffDH, nullptr, row, 2 * cq + 1, dv + 8);
+        }
+        if (SPLIT) {
+            ok = __syncthreads_and(tc::mbar_wait(bL, d_lo & 1u) ? 1 : 0) != 0;
+            if (!ok) break;
+            ++d_lo;
+        }
+        sync_async();
+        if (tid == 0) {
+            fb_mma_kmajor(tmem + kColQKV, uA, uA2, uWQ, uS, kQKV, SPLIT, false);
+            // do = dhmid Wo: B is the out-projection image read transposed
+            const uint32_t id = idesc_t(kRows, kD, false, true);
+            const uint64_t dA = tc::desc_sw128(uDH);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                tc::mma_bf16(tmem + kColDO, dA + uint64_t(2 * k), desc_mn(uWO + 2048u * k, 8192u), id, k > 0 ? 1u : 0u);
+            tc::mma_commit(mb);
+        }
+        wait_mma();
+        if (!ok) break;
+        // ---- the heads in two groups of 32 columns
+#pragma unroll 1
+        for (int gq = 0; gq < 2; ++gq) {
+            const bool active = cq < HPG;      // warp-uniform
+            const int hg = gq * HPG + cq;      // head
+            const int c0 = DH * hg;            // its columns of q (k: 64 + c0, v: 128 + c0)
+            float* srow = sS + row * kSS + cq * 4 * DH;
+            if (active) {
+                float q[DH], k[DH], v[DH], d[DH], b[DH];
+                fa_tmem_ld<DH>(tl + kColQKV + c0, q);
+                fa_tmem_ld<DH>(tl + kColQKV + 64 + c0, k);
+                fa_tmem_ld<DH>(tl + kColQKV + 128 + c0, v);
+                fa_tmem_ld<DH>(tl + kColDO + c0, d);
+                fa_ld<DH>(g.bqkv + c0, b);
+#pragma unroll
+                for (int c = 0; c < DH; ++c) q[c] += b[c];
+                fa_ld<DH>(g.bqkv + 64 + c0, b);
+#pragma unroll
+                for (int c = 0; c < DH; ++c) k[c] += b[c];
+                fa_ld<DH>(g.bqkv + 128 + c0, b);
+#pragma unroll
+                for (int c = 0; c < DH; ++c) v[c] += b[c];
+                fa_st<DH>(srow, q);
+                fa_st<DH>(srow + DH, k);
+                fa_st<DH>(srow + 2 * DH, v);
+                fa_st<DH>(srow + 3 * DH, d);
+            }
+            __syncthreads();
+            // forward recomputation: o, log-sum-exp (base 2) and D = do . o
+            if (active) {
+                float o[DH];
+#pragma unroll
+                for (int c = 0; c < DH; ++c) o[c] = 0.f;
+                if (valid) {
+                    float qs[DH];
+                    fa_ld<DH>(srow, qs);
+#pragma unroll
+                    for (int c = 0; c < DH; ++c) qs[c] *= qscale;
+                    float m = -INFINITY, l = 0.f;
+                    for (int j = 0; j <= tt; ++j) {
+                        const float *sj = sS + (r0 + j) * kSS + cq * 4 * DH;
+                        float kj[DH], vj[DH];
+                        fa_ld<DH>(sj + DH, kj);
+                        fa_ld<DH>(sj + 2 * DH, vj);
+                        const float sc = fa_dot<DH>(qs, kj);
+                        const float mn = sc > m ? sc : m;
+                        const float corr = fb_ex2(m - mn), p = fb_ex2(sc - mn);
+                        l = l * corr + p;
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) o[c] = o[c] * corr + p * vj[c];
+                        m = mn;
+                    }
+                    const float inv = 1.0f / l;
+#pragma unroll
+                    for (int c = 0; c < DH; ++c) o[c] *= inv;
+                    float dd[DH];
+                    fa_ld<DH>(srow + 3 * DH, dd);
+                    sLse[row * 4 + cq] = m + log2f(l);
+                    sD[row * 4 + cq] = fa_dot<DH>(dd, o);
+                }
+#pragma unroll
+                for (int e = 0; e < DH / 8; ++e) fb_granule(sb + kOffO, nullptr, row, c0 / 8 + e, o + 8 * e);
+            }
+            __syncthreads();
+            // reverse mode: dq over this query's keys, dk and dv over the
+            // queries that see this row's key
+            if (active) {
+                float dq[DH], dk[DH], dv[DH];
+#pragma unroll
+                for (int c = 0; c < DH; ++c) dq[c] = dk[c] = dv[c] = 0.f;
+                if (valid) {
+                    {
+                        float qs[DH], dd[DH];
+                        fa_ld<DH>(srow, qs);
+                        fa_ld<DH>(srow + 3 * DH, dd);
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) qs[c] *= qscale;
+                        const float lse = sLse[row * 4 + cq], D = sD[row * 4 + cq];
+                        for (int j = 0; j <= tt; ++j) {
+                            const float *sj = sS + (r0 + j) * kSS + cq * 4 * DH;
+                            float kj[DH], vj[DH];
+                            fa_ld<DH>(sj + DH, kj);
+                            fa_ld<DH>(sj + 2 * DH, vj);
+                            const float p = fb_ex2(fa_dot<DH>(qs, kj) - lse);
+                            const float ds = p * (fa_dot<DH>(dd, vj) - D);
+#pragma unroll
+                            for (int c = 0; c < DH; ++c) dq[c] = fmaf(ds, kj[c], dq[c]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) dq[c] *= scale;
+                    }
+                    {
+                        float ks[DH], vv[DH];
+                        fa_ld<DH>(srow + DH, ks);
+                        fa_ld<DH>(srow + 2 * DH, vv);
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) ks[c] *= qscale;
+                        for (int j = tt; j < T; ++j) {
+                            const int rj = r0 + j;
+                            const float *sj = sS + rj * kSS + cq * 4 * DH;
+                            float qj[DH], dj[DH];
+                            fa_ld<DH>(sj, qj);
+                            fa_ld<DH>(sj + 3 * DH, dj);
+                            const float p = fb_ex2(fa_dot<DH>(qj, ks) - sLse[rj * 4 + cq]);
+                            const float ds = p * (fa_dot<DH>(dj, vv) - sD[rj * 4 + cq]);
+#pragma unroll
+                            for (int c = 0; c < DH; ++c) {
+                                dk[c] = fmaf(ds, qj[c], dk[c]);
+                                dv[c] = fmaf(p, dj[c], dv[c]);
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) dk[c] *= scale;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < DH / 8; ++e) {
+                    fb_granule(sb + kOffDQ, nullptr, row, c0 / 8 + e, dq + 8 * e);
+                    fb_granule(sb + kOffDQ + 16384, nullptr, row, c0 / 8 + e, dk + 8 * e);
+                    fb_granule(sb + kOffDQ + 32768, nullptr, row, c0 / 8 + e, dv + 8 * e);
+                }
+                // column sums of dq | dk | dv over the warp's 32 rows
+                if constexpr (DH == 8) {
+                    float t[32];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        t[c] = dq[c];
+                        t[8 + c] = dk[c];
+                        t[16 + c] = dv[c];
+                        t[24 + c] = 0.f;
+                    }
+                    const float c32 = fb_colsum<32>(t, lane);
+                    if (gq == 0)
+                        csq00 += c32;
+                    else
+                        csq10 += c32;
+                } else {
+                    float t[32], t2[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        t[c] = dq[c];
+                        t[16 + c] = dk[c];
+                        t2[c] = dv[c];
+                    }
+                    const float c32 = fb_colsum<32>(t, lane), c16 = fb_colsum<16>(t2, lane);
+                    if (gq == 0) {
+                        csq00 += c32;
+                        csq01 += c16;
+                    } else {
+                        csq10 += c32;
+                        csq11 += c16;
+                    }
+                }
+            }
+            __syncthreads();  // the scratch, log-sum-exp and D are rewritten by the next group
+        }
+        sync_async();
+        if (tid == 0) {
+            // da = dqkv Wqkv: B is the qkv image read transposed (K = its 192 rows)
+            const uint32_t id = idesc_t(kRows, kD, false, true);
+#pragma unroll
+            for (int kb = 0; kb < 3; ++kb) {
+                const uint64_t dA = tc::desc_sw128(uDQ + 16384u * kb);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc::mma_bf16(tmem + kColDA, dA + uint64_t(2 * k),
+                                 desc_mn(uWQ + uint32_t(64 * kb + 16 * k) * 128u, 16384u), id, (kb | k) ? 1u : 0u);
+            }
+            // dWqkv rows 0..127 and 64..191 += dqkv^T a; dWo += dhmid^T o
+            // (rows 64..127 of that product read the o panel after dhmid: unused)
+            fb_mma_rows(tmem + kColWQ, uDQ, 16384u, uA, kD, !first);
+            fb_mma_rows(tmem + kColWQ + 64, uDQ + 16384u, 16384u, uA, kD, !first);
+            fb_mma_rows(tmem + kColWO, uDH, 16384u, uO, kD, !first);
+            tc::mma_commit(mb);
+        }
+        wait_mma();
+        if (!ok) break;
+        // ---- LN1 backward: dh_in = dhmid + rs (da g - mean(da g) - xh mean(da g xh))
+        {
+            uint32_t r16[16];
+            tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
+            float hv[16], dv[16], gv[16], da[16], xh[16];
+            if (valid) {
+                fb_ldg16(g.hin + gr * kD + 16 * cq, hv);
+                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
+            }
+            fb_ldg16(g.ln1g + 16 * cq, gv);
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                da[c] = valid ? __uint_as_float(r16[c]) : 0.f;
+                xh[c] = valid ? (hv[c] - mu) * rs : 0.f;
+                const float dx = da[c] * gv[c];
+                s1 += dx;
+                s2 += dx * xh[c];
+            }
+            red[row * 4 + cq] = s1;
+            red[512 + row * 4 + cq] = s2;
+            __syncthreads();
+            const float m1 = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
+            const float m2 = (red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
+                              red[512 + row * 4 + 3]) * (1.0f / kD);
+            float out[16], t[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) out[c] = valid ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
+            if (valid) fb_st16(g.dh + gr * kD + 16 * cq, out);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) t[c] = da[c] * xh[c];
+            cs_g += fb_colsum<16>(t, lane);
+            cs_b += fb_colsum<16>(da, lane);
+            cs_o += fb_colsum<16>(out, lane);
+        }
+        sync_async();  // (the next tile's copy into the scratch region follows these reads)
+        first = false;
+    }
+    if (ok && !first) {
+        float *part = g.part + (int64_t)blockIdx.x * kBwdAttnPart;
+        {
+            uint32_t r16[16];
+            float v[16];
+            // dWqkv rows 0..127 (lane = row)
+            tc::tmem_ld16(tl + kColWQ + 16 * cq, r16);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r16[c]);
+            fb_st16(part + row * kD + 16 * cq, v);
+            // rows 64..191: lanes 64..127 hold rows 128..191
+            tc::tmem_ld16(tl + kColWQ + 64 + 16 * cq, r16);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r16[c]);
+            if (row >= 64) fb_st16(part + (64 + row) * kD + 16 * cq, v);
+            // dWo (lanes 0..63)
+            tc::tmem_ld16(tl + kColWO + 16 * cq, r16);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r16[c]);
+            if (row < 64) fb_st16(part + kQKV * kD + row * kD + 16 * cq, v);
+        }
+        float *cs = red + q4 * kCols;
+        for (int e = tid; e < 4 * kCols; e += kThreads) red[e] = 0.f;
+        __syncthreads();
+        if (cq < HPG) {
+#pragma unroll
+            for (int gq = 0; gq < 2; ++gq) {
+                const int c0 = DH * (gq * HPG + cq);
+                const float a0 = gq == 0 ? csq00 : csq10, a1 = gq == 0 ? csq01 : csq11;
+                if constexpr (DH == 8) {
+                    if (lane < 24) cs[(lane >> 3) * 64 + c0 + (lane & 7)] = a0;
+                } else {
+                    cs[(lane >> 4) * 64 + c0 + (lane & 15)] = a0;
+                    if ((lane & 1) == 0) cs[128 + c0 + (lane >> 1)] = a1;
+                }
+            }
+        }
+        if ((lane & 1) == 0) {
+            cs[192 + 16 * cq + (lane >> 1)] = cs_g;
+            cs[256 + 16 * cq + (lane >> 1)] = cs_b;
+            cs[320 + 16 * cq + (lane >> 1)] = cs_o;
+        }
+        __syncthreads();
+        for (int e = tid; e < kCols; e += kThreads)
+            part[kQKV * kD + kD * kD + e] = ((red[e] + red[kCols + e]) + red[2 * kCols + e]) + red[3 * kCols + e];
+    }
+    if (!ok && tid == 0) {
+        if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -15;
+        if (!w_landed) tc::mbar_wait(bW, 0);
+        for (; d_lo < n_lo; ++d_lo) tc::mbar_wait(bL, d_lo & 1u);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(fa::kTmemCols)
+                     : "memory");
+    }
+}
+
+__global__ void k_bwd_attn_reduce(const float *__restrict__ part, int grid, float *dwqkv, float *dwo, float *dbqkv,
+                                  float *dg1, float *db1, float *dsum) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kBwdAttnPart) return;
+    constexpr int a = 192 * 64, b = a + 64 * 64, c1 = b + 192, c2 = c1 + 64, c3 = c2 + 64;
+    float *dst = e < a ? dwqkv + e : e < b ? dwo + (e - a) : e < c1 ? dbqkv + (e - b) : e < c2 ? dg1 + (e - c1)
+                 : e < c3 ? db1 + (e - c2) : (dsum ? dsum + (e - c3) : nullptr);
+    if (!dst) return;
+    float s = 0.f;
+    for (int c = 0; c < grid; ++c) s += part[(int64_t)c * kBwdAttnPart + e];
+    *dst += s;
+}
+
+template <bool SPLIT, int DH>
+nnqs_status launch_attn(const BwdAttnArgs &a, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        NNQS_CUDA_TRY(
+            cudaFuncSetAttribute(k_bwd_attn<SPLIT, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, fa::kSmem));
+        attr = true;
+    }
+    NNQS_LAUNCH("k_bwd_attn", s, (k_bwd_attn<SPLIT, DH><<<(unsigned)bwd_attn_grid(a.n, a.T), fa::kThreads, fa::kSmem, s>>>(a)));
+    return NNQS_OK;
+}
+
+template <bool SPLIT>
+nnqs_status launch_ffn(const BwdFfnArgs &a, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_bwd_ffn<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb::kSmem));
+        attr = true;
+    }
+    NNQS_LAUNCH("k_bwd_ffn", s, (k_bwd_ffn<SPLIT><<<(unsigned)bwd_ffn_grid(a.rows), fb::kThreads, fb::kSmem, s>>>(a)));
+    return NNQS_OK;
+}
+
+}  // namespace
+
+bool bwd_ffn_supported(int d, int F) { return d == fb::kD && F == fb::kF; }
+
+int bwd_ffn_grid(int64_t rows) {
+    const int64_t tiles = (rows + fb::kRows - 1) / fb::kRows;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms()));
+}
+
+nnqs_status bwd_ffn_launch(const BwdFfnArgs &a, bool split, cudaStream_t s) {
+    if (a.rows <= 0) return NNQS_OK;
+    auto al = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    if (!al(a.hmid) || !al(a.dh) || !al(a.ln2g) || !al(a.ln2b) || !al(a.b1) || !al(a.t1) || !al(a.t2))
+        return set_error(NNQS_E_INVAL, "fused FFN reverse mode: operands not 16-byte aligned");
+    // method FLOPs: the recomputed FFN-in product and the four reverse products
+    note_work("k_bwd_ffn", double(a.rows) * 2.0 * fb::kD * fb::kF * 5.0, double(a.rows) * fb::kD * 4.0 * 3.0);
+    return split ? launch_ffn<true>(a, s) : launch_ffn<false>(a, s);
+}
+
+nnqs_status bwd_ffn_reduce(const float *part, int grid, float *dw1, float *dw2, float *db1, float *dg2, float *db2,
+                           float *dbo, cudaStream_t s) {
+    NNQS_LAUNCH("k_bwd_reduce", s, (k_bwd_ffn_reduce<<<(kBwdFfnPart + 255) / 256, 256, 0, s>>>(part, grid, dw1, dw2, db1, dg2, db2, dbo)));
+    return NNQS_OK;
+}
+
+bool bwd_attn_supported(int d, int dh, int T) { return d == fa::kD && (dh == 8 || dh == 16) && T >= 1 && T <= 64; }
+
+int bwd_attn_grid(int64_t n, int T) {
+    const int64_t spt = 128 / std::max(T, 1), tiles = (n + spt - 1) / spt;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms()));
+}
+
+nnqs_status bwd_attn_launch(const BwdAttnArgs &a, bool split, int dh, cudaStream_t s) {
+    if (a.n <= 0) return NNQS_OK;
+    if (a.T < 1 || a.T > 64 || a.spt != 128 / a.T) return set_error(NNQS_E_INVAL, "fused attention reverse mode: bad tile shape");
+    auto al = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    if (!al(a.hin) || !al(a.dh) || !al(a.ln1g) || !al(a.ln1b) || !al(a.bqkv) || !al(a.tqkv) || !al(a.to))
+        return set_error(NNQS_E_INVAL, "fused attention reverse mode: operands not 16-byte aligned");
+    // method FLOPs: the recomputed qkv product, do, da and the two weight products
+    const double rows = double(a.n) * a.T;
+    note_work("k_bwd_attn", rows * 2.0 * fa::kD * (3.0 * fa::kQKV + 2.0 * fa::kD), rows * fa::kD * 4.0 * 3.0);
+    if (split) return dh == 8 ? launch_attn<true, 8>(a, s) : launch_attn<true, 16>(a, s);
+    return dh == 8 ? launch_attn<false, 8>(a, s) : launch_attn<false, 16>(a, s);
+}
+
+nnqs_status bwd_attn_reduce(const float *part, int grid, float *dwqkv, float *dwo, float *dbqkv, float *dg1,
+                            float *db1, float *dsum, cudaStream_t s) {
+    NNQS_LAUNCH("k_bwd_reduce", s, (k_bwd_attn_reduce<<<(kBwdAttnPart + 255) / 256, 256, 0, s>>>(part, grid, dwqkv, dwo, dbqkv, dg1, db1, dsum)));
+    return NNQS_OK;
+}
+
+}  // namespace nnqs

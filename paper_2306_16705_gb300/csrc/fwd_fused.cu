@@ -217,7 +217,7 @@ __device__ __forceinline__ int ff_token(const uint64_t *x, int T, int t) {
     return ff_bit(x, 2 * p) + 2 * ff_bit(x, 2 * p + 1);
 }
 
-template <bool SPLIT, int DH, bool KEEP>
+template <bool SPLIT, int DH, int KEEP>
 __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_constant__ FusedFwdArgs g) {
     using namespace ff;
     constexpr int H = kD / DH;
@@ -341,17 +341,19 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             {
                 const int lr = 8 * warp + (lane >> 2), lq = lane & 3;
                 const LnOut n1 = ff_layernorm(sH, lr, lq, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
-                if constexpr (KEEP) {
+                if constexpr (KEEP >= 1) {
                     const int64_t gr = s0 * T + lr, at = (int64_t)l * g.rows + gr;
                     if (lr < rows_used && gr < g.rows) {
                         float hv[16];
 #pragma unroll
                         for (int c = 0; c < 16; ++c) hv[c] = sH[lr * kHS + ln_col(lq, c)];
                         ff_st_part(g.hbuf + at * kD, lq, hv);
-                        ff_st_part(g.a + at * kD, lq, n1.y);
-                        if (lq == 0) {
-                            g.mean1[at] = n1.mu;
-                            g.rstd1[at] = n1.rs;
+                        if constexpr (KEEP >= 2) {
+                            ff_st_part(g.a + at * kD, lq, n1.y);
+                            if (lq == 0) {
+                                g.mean1[at] = n1.mu;
+                                g.rstd1[at] = n1.rs;
+                            }
                         }
                     }
                 }
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                         v.z = __uint_as_float(r16[4 * p + 2]) + bv[4 * p + 2];
                         v.w = __uint_as_float(r16[4 * p + 3]) + bv[4 * p + 3];
                         *reinterpret_cast<float4 *>(sKV + kv_at(row, c, row / T)) = v;
-                        if constexpr (KEEP) {
+                        if constexpr (KEEP >= 2) {
                             const int64_t gr = s0 * T + row;
                             if (row < rows_used && gr < g.rows)
                                 *reinterpret_cast<float4 *>(g.qkv + ((int64_t)l * g.rows + gr) * kQKV + tc0 + 4 * p) = v;
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     for (int c = 0; c < 16; ++c) qv[c] += __uint_as_float(r16[c]);
                     const int sl = row / T, t = row - sl * T, r0 = sl * T;
                     const int64_t gr = s0 * T + row;
-                    if constexpr (KEEP) {
+                    if constexpr (KEEP >= 2) {
                         if (gr < g.rows) ff_st16(g.qkv + ((int64_t)l * g.rows + gr) * kQKV + 16 * cq, qv);
                     }
 #pragma unroll
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
 #pragma unroll
                         for (int c = 0; c < DH; ++c) o[h * DH + c] *= inv;
                     }
-                    if constexpr (KEEP) {
+                    if constexpr (KEEP >= 2) {
                         if (gr < g.rows) {
                             ff_st16(g.o + ((int64_t)l * g.rows + gr) * kD + 16 * cq, o);
                             // log-sum-exp of each head's scores, natural units
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     hv[j] = sH[row * kHS + c] + (__uint_as_float(r16[j]) + bv[j]);
                     sH[row * kHS + c] = hv[j];
                 }
-                if constexpr (KEEP) {
+                if constexpr (KEEP >= 1) {
                     const int64_t gr = s0 * T + row;
                     if (row < rows_used && gr < g.rows) ff_st16(g.hmid + ((int64_t)l * g.rows + gr) * kD + 16 * cq, hv);
                 }
@@ -501,7 +503,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             {
                 const int lr = 8 * warp + (lane >> 2), lq = lane & 3;
                 const LnOut n2 = ff_layernorm(sH, lr, lq, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
-                if constexpr (KEEP) {
+                if constexpr (KEEP >= 2) {
                     const int64_t gr = s0 * T + lr, at = (int64_t)l * g.rows + gr;
                     if (lr < rows_used && gr < g.rows) {
                         ff_st_part(g.a2 + at * kD, lq, n2.y);
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                         uv[j] += __uint_as_float(r16[j]);
                         x[j] = ff_gelu(uv[j]);
                     }
-                    if constexpr (KEEP) {
+                    if constexpr (KEEP >= 2) {
                         const int64_t gr = s0 * T + row;
                         if (row < rows_used && gr < g.rows) {
                             const int64_t at = ((int64_t)l * g.rows + gr) * kF + 64 * c + 16 * cq;
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
             const int sl = lr / T, t = lr - sl * T;
             const int64_t i = s0 + sl, gr = s0 * T + lr;
             const bool valid = lr < rows_used && i < g.n;
-            if constexpr (KEEP) {
+            if constexpr (KEEP >= 1) {
                 if (valid) {
                     float hv[16];
 #pragma unroll
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
                     const float lse = zmax + logf(se);
                     const int tk = ff_token(xi, T, t);
                     lp = okv[tk] ? z[tk] - lse : -INFINITY;
-                    if constexpr (KEEP) {
+                    if constexpr (KEEP >= 1) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) g.pi[gr * 4 + k] = okv[k] ? expf(z[k] - lse) : 0.f;
                         g.tok_out[gr] = (uint8_t)tk;
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(ff::kThreads, 1) k_fwd_fused(const __grid_cons
     }
 }
 
-template <bool SPLIT, int DH, bool KEEP>
+template <bool SPLIT, int DH, int KEEP>
 nnqs_status launch_fused(const FusedFwdArgs &a, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
@@ -698,7 +700,7 @@ nnqs_status launch_fused(const FusedFwdArgs &a, cudaStream_t s) {
     return NNQS_OK;
 }
 
-template <bool KEEP>
+template <int KEEP>
 nnqs_status launch_fused_keep(const FusedFwdArgs &a, bool split, int dh, cudaStream_t s) {
     if (split) return dh == 8 ? launch_fused<true, 8, KEEP>(a, s) : launch_fused<true, 16, KEEP>(a, s);
     return dh == 8 ? launch_fused<false, 8, KEEP>(a, s) : launch_fused<false, 16, KEEP>(a, s);
@@ -727,8 +729,8 @@ nnqs_status fused_fwd_launch(const FusedFwdArgs &a, bool split, int dh, cudaStre
     note_work("k_fwd_fused",
               double(a.n) * a.T * a.L * 2.0 * (4.0 * ff::kD * ff::kD + 2.0 * ff::kD * ff::kF),
               double(a.n) * (8.0 * a.W + 8.0));
-    if (a.hbuf) return launch_fused_keep<true>(a, split, dh, s);
-    return launch_fused_keep<false>(a, split, dh, s);
+    if (a.hbuf) return a.a ? launch_fused_keep<2>(a, split, dh, s) : launch_fused_keep<1>(a, split, dh, s);
+    return launch_fused_keep<0>(a, split, dh, s);
 }
 
 }  // namespace nnqs

@@ -25,13 +25,15 @@ struct FusedFwdArgs {
     // [64 x 64], FFN in [256 x 64], FFN out [64 x 256] as four K blocks
     const void *tqkv[kFusedMaxLayers], *to[kFusedMaxLayers], *t1[kFusedMaxLayers], *t2[kFusedMaxLayers];
     double2 *out;       // [n]: .x = log|psi| written (.y untouched)
-    // keep mode (hbuf not null): every activation the reverse mode reads, in
-    // the layout of the layer-by-layer forward (row = sample * T + t of this
-    // call, rows = n T): hbuf [L+1][rows][64] (input of each layer, then the
-    // final residual), a / a2 / hmid / o [L][rows][64], qkv [L][rows][192],
-    // u / gu [L][rows][256], mean1 / rstd1 / mean2 / rstd2 [L][rows],
-    // lse [L][n][H][T] (natural units), hf [rows][64], meanf / rstdf [rows],
-    // pi [rows][4], tok_out [rows] (the token of each row)
+    // keep mode (hbuf not null): activations for the reverse mode, in the
+    // layout of the layer-by-layer forward (row = sample * T + t of this call,
+    // rows = n T): hbuf [L+1][rows][64] (input of each layer, then the final
+    // residual), hmid [L][rows][64], hf [rows][64], meanf / rstdf [rows],
+    // pi [rows][4], tok_out [rows] (the token of each row); with `a` not null
+    // also a / a2 / o [L][rows][64], qkv [L][rows][192], u / gu
+    // [L][rows][256], mean1 / rstd1 / mean2 / rstd2 [L][rows] and
+    // lse [L][n][H][T] (natural units).  The fused reverse mode needs only
+    // the first group: it recomputes the rest on chip.
     float *hbuf, *a, *a2, *hmid, *o, *qkv, *u, *gu, *mean1, *rstd1, *mean2, *rstd2, *lse, *hf, *meanf, *rstdf, *pi;
     uint8_t *tok_out;
     int64_t rows;

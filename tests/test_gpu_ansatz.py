@@ -256,3 +256,32 @@ def test_logpsi_fused_forward_two_chunks():
     got = B.logpsi(m, flat, B.to_device_bits(x), B.BF16X3).cpu().numpy()
     one = B.logpsi(m, flat, B.to_device_bits(S), B.BF16X3).cpu().numpy()
     assert np.array_equal(got, np.concatenate([one] * 34))
+
+
+@pytest.mark.parametrize("case", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
+@pytest.mark.parametrize("prec", [B.MIXED, B.BF16X3])
+def test_backward_fused_matches_oracle(case, prec):
+    """The fused reverse mode of the decoder layers (k_bwd_ffn: one 128-row
+    tile's FFN half with its forward recomputed on chip, weight gradients in
+    TMEM over the CTA's tiles) that the BF16 and split-BF16 reverse modes use
+    for d = 64: every gradient tensor of the transformer against the oracle's
+    reverse mode with the BF16 bounds above, over ragged tiles, two-word keys,
+    head dimension 16 and T = 64.  (The phase MLP is not part of the fused
+    kernel; its gradient is checked above, and with BF16 forward operands a
+    ReLU' that flips at a pre-activation near zero makes it discontinuous.)"""
+    name, N, na, nb, L, H, ns = case
+    ns = min(ns, 600)
+    m, params, flat = make(N, na, nb, 64, L, H, seed=29, hidden=96, std=0.2)
+    x = I.random_sector_samples(N // 2, na, nb, ns, seed=9)
+    rng = np.random.default_rng(3)
+    seed = np.stack([rng.normal(size=ns), rng.normal(size=ns)], 1)
+    g = B.logpsi_backward(m, flat, B.to_device_bits(x), torch.from_numpy(seed).cuda(), prec)
+    G = m.unpack(g, params)
+    _, _, cache = OA.forward(params, I.unpack_bits(x, N), na, nb, H, want_cache=True)
+    R = OA.backward(cache, seed[:, 0], seed[:, 1])
+    worst = 0.0
+    for k in (k for k in params if not k.startswith("phase.")):
+        err = np.abs(G[k] - R[k]).max()
+        worst = max(worst, err / max(1e-3, np.abs(R[k]).max()))
+        assert err <= GRAD_TOL[prec] * max(1e-3, np.abs(R[k]).max()), (k, err, np.abs(R[k]).max())
+    print(f"fused backward {name} prec={prec}: largest error / tensor scale = {worst:.3e}")
