@@ -2824,7 +2824,9 @@ struct Acts {
 };
 
 template <class R>
-void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) {
+// lite: the fused reverse mode's keep set (the layers' inputs and mid
+// residuals, the head's activations); the per-layer activations stay null
+void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A, bool lite = false) {
     const int64_t T = M->T, d = M->d, L = M->L, F = M->F, P = M->P, rows = C * T, H = M->H;
     const int64_t Lk = keep ? L : 1;
     A.C = C;
@@ -2832,17 +2834,19 @@ void take_acts(const nnqs_model *M, int64_t C, bool keep, Arena &a, Acts<R> &A) 
     A.tok = a.take<uint8_t>(rows);
     A.hbuf = a.take<R>((keep ? (L + 1) : 2) * rows * d);
     A.hmid = a.take<R>(Lk * rows * d);
-    A.a = a.take<R>(Lk * rows * d);
-    A.a2 = a.take<R>(Lk * rows * d);
-    A.qkv = a.take<R>(Lk * rows * 3 * d);
-    A.o = a.take<R>(Lk * rows * d);
-    A.u = a.take<R>(Lk * rows * F);
-    A.gu = a.take<R>(Lk * rows * F);
-    A.mean1 = a.take<R>(Lk * rows);
-    A.rstd1 = a.take<R>(Lk * rows);
-    A.mean2 = a.take<R>(Lk * rows);
-    A.rstd2 = a.take<R>(Lk * rows);
-    A.lse = a.take<R>(Lk * C * H * T);
+    if (!lite) {
+        A.a = a.take<R>(Lk * rows * d);
+        A.a2 = a.take<R>(Lk * rows * d);
+        A.qkv = a.take<R>(Lk * rows * 3 * d);
+        A.o = a.take<R>(Lk * rows * d);
+        A.u = a.take<R>(Lk * rows * F);
+        A.gu = a.take<R>(Lk * rows * F);
+        A.mean1 = a.take<R>(Lk * rows);
+        A.rstd1 = a.take<R>(Lk * rows);
+        A.mean2 = a.take<R>(Lk * rows);
+        A.rstd2 = a.take<R>(Lk * rows);
+        A.lse = a.take<R>(Lk * C * H * T);
+    }
     A.hf = a.take<R>(rows * d);
     A.meanf = a.take<R>(rows);
     A.rstdf = a.take<R>(rows);
@@ -3038,20 +3042,24 @@ struct Grads {
 };
 
 template <class R>
-void take_grads(const nnqs_model *M, int64_t C, Arena &a, Grads<R> &G) {
+void take_grads(const nnqs_model *M, int64_t C, Arena &a, Grads<R> &G, bool lite = false) {
     const int64_t T = M->T, d = M->d, F = M->F, P = M->P, rows = C * T, H = M->H;
     G.dh = a.take<R>(rows * d);
     G.dtmp = a.take<R>(rows * std::max<int64_t>(d, 4));
-    G.dqkv = a.take<R>(rows * 3 * d);
-    G.du = a.take<R>(rows * F);
-    G.Dbuf = a.take<R>(C * H * T);
+    if (!lite) {
+        G.dqkv = a.take<R>(rows * 3 * d);
+        G.du = a.take<R>(rows * F);
+        G.Dbuf = a.take<R>(C * H * T);
+    }
     G.dz = a.take<R>(rows * 4);
     G.dph = a.take<R>(C);
     G.dz1 = a.take<R>(C * P);
     G.dz2 = a.take<R>(C * P);
     G.lp = a.take<double2>(C);
-    G.qkvsum = a.take<R>(C * 3 * d);
-    G.ucolpart = a.take<R>((rows + 127) / 128 * F);
+    if (!lite) {
+        G.qkvsum = a.take<R>(C * 3 * d);
+        G.ucolpart = a.take<R>((rows + 127) / 128 * F);
+    }
     G.part = bwd_ffn_supported(M->d, M->F) ? a.take<float>(size_t(num_sms()) * kBwdFfnPart) : nullptr;
 }
 
@@ -3071,6 +3079,17 @@ bool fused_bwd_enabled() {
 bool fused_bwd_applies(const nnqs_model *M, const TcWeights *tcw) {
     return tcw && !tcw->fp8 && fused_bwd_enabled() && bwd_ffn_supported(M->d, M->F) &&
            bwd_attn_supported(M->d, M->dh, M->T);
+}
+
+int fused_fwd_level();
+
+// The reverse mode of precision mode tcm (tc_mode) keeps only the lite set:
+// the fused forward and the fused reverse mode both apply.  The workspace
+// sizes and both reverse-mode entry points decide it here.
+bool reverse_lite(const nnqs_model *M, int tcm) {
+    return (tcm == 1 || tcm == 2) && fused_bwd_enabled() && bwd_ffn_supported(M->d, M->F) &&
+           bwd_attn_supported(M->d, M->dh, M->T) && fused_fwd_level() >= 1 &&
+           fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L);
 }
 
 template <class R>
@@ -3251,18 +3270,19 @@ int64_t chunk_for(const nnqs_model *M, int64_t n, size_t rbytes, bool backward) 
 }
 
 template <class R>
-size_t workspace_impl(const nnqs_model *M, int64_t n, bool backward, bool tensor) {
+size_t workspace_impl(const nnqs_model *M, int64_t n, bool backward, int tcm) {
     Arena a(nullptr);
     a.take<char>(kStatusBytes);
     a.take<R>(M->lay.total);  // converted parameters
     if (backward) a.take<R>(M->lay.total);  // gradient accumulator
-    if (tensor) tc_weights_take(M, a);
+    if (tcm) tc_weights_take(M, a);
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), backward);
+    const bool lite = backward && sizeof(R) == 4 && reverse_lite(M, tcm);
     Acts<R> A;
-    take_acts<R>(M, C, backward, a, A);
+    take_acts<R>(M, C, backward, a, A, lite);
     if (backward) {
         Grads<R> G;
-        take_grads<R>(M, C, a, G);
+        take_grads<R>(M, C, a, G, lite);
     }
     return a.used + 1024;
 }
@@ -3332,11 +3352,17 @@ nnqs_status forward_keep(const nnqs_model *M, const Views<R> &V, const uint64_t 
     if constexpr (sizeof(R) == 4) {
         // the fused reverse mode recomputes each layer from its input and
         // hmid: the fused forward then writes only those (and the head's)
-        const bool lite = fused_bwd_applies(M, tcw);
+        // (a workspace without the per-layer activations, A.a null, holds only those)
+        const bool lite = !A.a || fused_bwd_applies(M, tcw);
+        if (!A.a && !(tcw && fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L)))
+            return set_error(NNQS_E_INVAL, "lite reverse-mode workspace without the fused forward");
         if (tcw && !tcw->fp8 && A.keep && (fused_fwd_level() >= 2 || (lite && fused_fwd_level() >= 1)) &&
             fused_fwd_supported(M->d, M->F, M->dh, M->T, M->L)) {
             FusedFwdArgs a = fused_args(M, V, *tcw, x, C, out, st, row_offset);
-            if (!fused_fwd_aligned(a)) return forward_chunk<R>(M, V, x, C, A, out, st, row_offset, tcw, s);
+            if (!fused_fwd_aligned(a)) {
+                if (!A.a) return set_error(NNQS_E_INVAL, "fused forward: parameters not 16-byte aligned");
+                return forward_chunk<R>(M, V, x, C, A, out, st, row_offset, tcw, s);
+            }
             a.rows = C * M->T;
             a.hbuf = A.hbuf;
             a.hmid = A.hmid;
@@ -3415,10 +3441,11 @@ nnqs_status backward_impl(const nnqs_model *M, const float *params, const uint64
     tcw.split = tcm == 2;
     tcw.fp8 = tcm == 3;
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
+    const bool lite = sizeof(R) == 4 && reverse_lite(M, tcm);
     Acts<R> A;
-    take_acts<R>(M, C, true, ws, A);
+    take_acts<R>(M, C, true, ws, A, lite);
     Grads<R> G;
-    take_grads<R>(M, C, ws, G);
+    take_grads<R>(M, C, ws, G, lite);
     NNQS_CUDA_TRY(cudaMemsetAsync(A.scr.ctr, 0, sizeof(unsigned), s));
     NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
@@ -3452,10 +3479,11 @@ nnqs_status fwd_bwd_impl(const nnqs_model *M, const float *params, const uint64_
     tcw.fp8 = tcm == 3;
     const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
     if (C < n) return set_error(NNQS_E_INVAL, "fused forward/backward needs one chunk");
+    const bool lite = sizeof(R) == 4 && reverse_lite(M, tcm);
     Acts<R> A;
-    take_acts<R>(M, C, true, ws, A);
+    take_acts<R>(M, C, true, ws, A, lite);
     Grads<R> G;
-    take_grads<R>(M, C, ws, G);
+    take_grads<R>(M, C, ws, G, lite);
     NNQS_CUDA_TRY(cudaMemsetAsync(A.scr.ctr, 0, sizeof(unsigned), s));
     NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
     NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
@@ -3766,8 +3794,8 @@ nnqs_status cond_step(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixe
 }
 
 size_t logpsi_workspace(const nnqs_model *M, int64_t n, int prec, bool backward) {
-    if (prec == NNQS_FP64) return workspace_impl<double>(M, n, backward, false);
-    return workspace_impl<float>(M, n, backward, tc_mode(prec) != 0);
+    if (prec == NNQS_FP64) return workspace_impl<double>(M, n, backward, 0);
+    return workspace_impl<float>(M, n, backward, tc_mode(prec));
 }
 
 nnqs_status logpsi_forward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,

@@ -53,6 +53,11 @@ __device__ __forceinline__ void fb_bulk(uint8_t *dst, const void *src, uint32_t 
                  : "memory");
 }
 
+// bring `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2
+__device__ __forceinline__ void fb_prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // shared-memory descriptor of an MN-major (transposed) operand, 128-byte
 // swizzle: 128-byte rows of 64 BF16 along M (or N), one row per K index,
 // 8-row groups along K 1024 bytes apart, 64-wide M (N) blocks `lbo` bytes apart
@@ -253,6 +258,11 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int64_t gr = tile * kRows + row;
         const bool valid = gr < g.rows;
+        if (tid == 0 && tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
+            const int64_t r1 = (tile + gridDim.x) * kRows, nr = g.rows - r1 < kRows ? g.rows - r1 : kRows;
+            fb_prefetch_l2(g.hmid + r1 * kD, uint32_t(nr * kD * 4));
+            fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
+        }
         // ---- LN2 of the saved residual rows -> a2 (A); dy -> DY
         // (thread: row `row`, columns 16 cq .. 16 cq + 15; rows past the end are zero)
         float mu, rs;
@@ -268,16 +278,16 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
             float s = 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) s += hv[c];
-            red[row * 4 + cq] = s;
+            red[cq * 128 + row] = s;
             __syncthreads();
-            mu = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
+            mu = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
             float q = 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) q += (hv[c] - mu) * (hv[c] - mu);
-            red[512 + row * 4 + cq] = q;
+            red[512 + cq * 128 + row] = q;
             __syncthreads();
-            rs = 1.0f / sqrtf((red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
-                               red[512 + row * 4 + 3]) * (1.0f / kD) + 1e-5f);
+            rs = 1.0f / sqrtf((red[512 + row] + red[640 + row] + red[768 + row] +
+                               red[896 + row]) * (1.0f / kD) + 1e-5f);
             float gv[16], bv[16], y[16];
             fb_ldg16(g.ln2g + 16 * cq, gv);
             fb_ldg16(g.ln2b + 16 * cq, bv);
@@ -390,12 +400,12 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
                 s1 += dx;
                 s2 += dx * xh[c];
             }
-            red[row * 4 + cq] = s1;
-            red[512 + row * 4 + cq] = s2;
+            red[cq * 128 + row] = s1;
+            red[512 + cq * 128 + row] = s2;
             __syncthreads();
-            const float m1 = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
-            const float m2 = (red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
-                              red[512 + row * 4 + 3]) * (1.0f / kD);
+            const float m1 = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
+            const float m2 = (red[512 + row] + red[640 + row] + red[768 + row] +
+                              red[896 + row]) * (1.0f / kD);
             float out[16], t[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) out[c] = valid ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
@@ -474,7 +484,9 @@ __global__ void k_bwd_ffn_reduce(const float *__restrict__ part, int grid, float
 //   da = dqkv Wqkv, dh_in = dhmid + LN1'(da)     (written over dhmid)
 //   dWqkv += dqkv^T a, dWo += dhmid^T o, dbqkv, dgamma1 / dbeta1, sum dh_in
 // The heads are walked in two groups of 32 columns of q | k | v | do, whose
-// FP32 values go through shared memory for the other rows of the sample.
+// FP32 values go through shared memory for the other rows of the sample; the
+// causal loops run token-major (one thread per (token, sample, head)), the
+// rest row-major (one thread per (row, head), as TMEM lanes are rows).
 //
 // Shared memory (1024-aligned base):
 //   [0, 32K)       a hi / lo                 [128][64] BF16
@@ -482,20 +494,24 @@ __global__ void k_bwd_ffn_reduce(const float *__restrict__ part, int grid, float
 //   [48K, 64K)     o                         [128][64] BF16 (right after dhmid:
 //                                            the second 64-row block of the dWo product's A)
 //   [64K, 112K)    dq | dk | dv              three [128][64] panels
-//   [112K, 178K)   the group's q | k | v | do [128][132] FP32 (the qkv image's low
-//                                            part at the start of a tile)
-//   [178K, 202K)   qkv image hi              [192][64]
-//   [202K, 210K)   out-projection image hi   [64][64]
-//   [210K, 218K)   row-sum exchange, the group's log-sum-exp and D; the column-sum combine
+//   [112K, 186K)   the group's q | k | v | do, log-sum-exp, D per (row, head),
+//                                            FP32 (the qkv image's low part at the start of a tile)
+//   [186K, 210K)   qkv image hi              [192][64]
+//   [210K, 218K)   out-projection image hi   [64][64]
+//   [218K, 224K)   row-sum exchange; the column-sum combine
 // TMEM: dWqkv [0, 128) (rows 0..127, then rows 64..191), dWo [128, 192)
 // (lanes 0..63), q | k | v [192, 384), do [384, 448), da [448, 512).
 namespace fa {
 constexpr int kThreads = 512, kRows = 128, kD = 64, kQKV = 192;
 constexpr int kOffA = 0, kOffA2 = 16384, kOffDH = 32768, kOffO = 49152, kOffDQ = 65536;
-constexpr int kOffS = 114688, kSS = 132;  // scratch row stride (floats)
-constexpr int kOffWQ = 182272, kOffWO = 206848, kOffRed = 215040;
-constexpr int kOffBar = kOffRed + 8192;
-constexpr int kSmem = kOffBar + 64 + 1024;  // 224,320 bytes
+// scratch: per row four head slots of 36 floats (q | k | v | do of head
+// dimension 8, then log-sum-exp and D; two slots of 68 for dimension 16) and
+// 4 floats of padding, so that the 16-byte pieces the token-major loops read
+// (6 samples x 4 heads of one key) fall in different bank groups
+constexpr int kOffS = 114688, kSS = 148;
+constexpr int kOffWQ = 190464, kOffWO = 215040, kOffRed = 223232;
+constexpr int kOffBar = kOffRed + 6144;
+constexpr int kSmem = kOffBar + 64 + 1024;  // 230,464 bytes
 constexpr uint32_t kColWQ = 0, kColWO = 128, kColQKV = 192, kColDO = 384, kColDA = 448, kTmemCols = 512;
 constexpr int kCols = 384;  // column sums per CTA: dbqkv 192 | dgamma1 64 | dbeta1 64 | dsum 64
 constexpr float kLog2e = 1.44269504088896340736f;
@@ -550,6 +566,7 @@ template <bool SPLIT, int DH>
 __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_constant__ BwdAttnArgs g) {
     using namespace fa;
     constexpr int HPG = 32 / DH;  // heads per group of 32 columns
+    constexpr int kSlot = 4 * DH + 4;  // q | k | v | do | log-sum-exp, D (base 2), -, -
     static_assert(HPG * DH == 32, "head dimension 8 or 16");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
@@ -557,7 +574,6 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
     uint8_t *sb = smem_raw + (base - raw);
     float *red = reinterpret_cast<float *>(sb + kOffRed);
     float *sS = reinterpret_cast<float *>(sb + kOffS);
-    float *sLse = red + 1024, *sD = red + 1536;  // [128][4] each
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 32);
     const uint32_t mb = base + kOffBar, bW = mb + 8, bL = mb + 16;
     const uint32_t uA = base + kOffA, uA2 = base + kOffA2, uDH = base + kOffDH, uO = base + kOffO;
@@ -618,6 +634,11 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
         const int64_t s0 = tile * g.spt;
         const int64_t gr = s0 * T + row;
         const bool valid = row < rows_used && gr < rows;
+        if (tid == 0 && tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
+            const int64_t r1 = (tile + gridDim.x) * g.spt * T, nr = rows - r1 < rows_used ? rows - r1 : rows_used;
+            fb_prefetch_l2(g.hin + r1 * kD, uint32_t(nr * kD * 4));
+            fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
+        }
         if (SPLIT && tid == 0) {  // the qkv image's low part into the scratch region
             tc::fence_async_smem();
             tc::mbar_expect(bL, kWQB);
@@ -638,16 +659,16 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
             float s = 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) s += hv[c];
-            red[row * 4 + cq] = s;
+            red[cq * 128 + row] = s;
             __syncthreads();
-            mu = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
+            mu = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
             float q = 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) q += (hv[c] - mu) * (hv[c] - mu);
-            red[512 + row * 4 + cq] = q;
+            red[512 + cq * 128 + row] = q;
             __syncthreads();
-            rs = 1.0f / sqrtf((red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
-                               red[512 + row * 4 + 3]) * (1.0f / kD) + 1e-5f);
+            rs = 1.0f / sqrtf((red[512 + row] + red[640 + row] + red[768 + row] +
+                               red[896 + row]) * (1.0f / kD) + 1e-5f);
             float gv[16], bv[16], y[16];
             fb_ldg16(g.ln1g + 16 * cq, gv);
             fb_ldg16(g.ln1b + 16 * cq, bv);
@@ -676,14 +697,16 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
         }
         wait_mma();
         if (!ok) break;
-        // ---- the heads in two groups of 32 columns
+        // ---- the heads in two groups of 32 columns of q | k | v | do
+        const int ipt = g.spt * HPG;  // work items (sample, head) per token position
 #pragma unroll 1
         for (int gq = 0; gq < 2; ++gq) {
-            const bool active = cq < HPG;      // warp-uniform
-            const int hg = gq * HPG + cq;      // head
-            const int c0 = DH * hg;            // its columns of q (k: 64 + c0, v: 128 + c0)
-            float* srow = sS + row * kSS + cq * 4 * DH;
-            if (active) {
+            // (1) thread (row, head cq of the group): q | k | v (+ bias) and do
+            // from TMEM to the row's slot; rows outside the tile's samples get
+            // zero o
+            if (cq < HPG) {  // warp-uniform
+                const int c0 = DH * (gq * HPG + cq);
+                float *slot = sS + row * kSS + cq * kSlot;
                 float q[DH], k[DH], v[DH], d[DH], b[DH];
                 fa_tmem_ld<DH>(tl + kColQKV + c0, q);
                 fa_tmem_ld<DH>(tl + kColQKV + 64 + c0, k);
@@ -698,113 +721,144 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
                 fa_ld<DH>(g.bqkv + 128 + c0, b);
 #pragma unroll
                 for (int c = 0; c < DH; ++c) v[c] += b[c];
-                fa_st<DH>(srow, q);
-                fa_st<DH>(srow + DH, k);
-                fa_st<DH>(srow + 2 * DH, v);
-                fa_st<DH>(srow + 3 * DH, d);
+                fa_st<DH>(slot, q);
+                fa_st<DH>(slot + DH, k);
+                fa_st<DH>(slot + 2 * DH, v);
+                fa_st<DH>(slot + 3 * DH, d);
+                if (!valid) {
+                    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int e = 0; e < DH / 8; ++e) fb_granule(sb + kOffO, nullptr, row, c0 / 8 + e, z);
+                }
             }
             __syncthreads();
+            // (2) thread = (token position, sample, head), token-major: a warp
+            // holds one or two token positions, so the lengths of its causal
+            // loops (t + 1 keys for dq, T - t queries for dk and dv) nearly agree
+            const int ti = tid / ipt, rem = tid - ti * ipt, sl = rem / HPG, hh = rem - sl * HPG;
+            const bool act = ti < T && s0 + sl < g.n;
+            const int r0 = sl * T, ri = r0 + ti;
+            const int c0 = DH * (gq * HPG + hh);
+            float *slot = act ? sS + ri * kSS + hh * kSlot : sS;
             // forward recomputation: o, log-sum-exp (base 2) and D = do . o
-            if (active) {
-                float o[DH];
+            if (act) {
+                float qs[DH], o[DH];
+                fa_ld<DH>(slot, qs);
 #pragma unroll
-                for (int c = 0; c < DH; ++c) o[c] = 0.f;
-                if (valid) {
-                    float qs[DH];
-                    fa_ld<DH>(srow, qs);
-#pragma unroll
-                    for (int c = 0; c < DH; ++c) qs[c] *= qscale;
-                    float m = -INFINITY, l = 0.f;
-                    for (int j = 0; j <= tt; ++j) {
-                        const float *sj = sS + (r0 + j) * kSS + cq * 4 * DH;
-                        float kj[DH], vj[DH];
-                        fa_ld<DH>(sj + DH, kj);
-                        fa_ld<DH>(sj + 2 * DH, vj);
-                        const float sc = fa_dot<DH>(qs, kj);
-                        const float mn = sc > m ? sc : m;
-                        const float corr = fb_ex2(m - mn), p = fb_ex2(sc - mn);
-                        l = l * corr + p;
-#pragma unroll
-                        for (int c = 0; c < DH; ++c) o[c] = o[c] * corr + p * vj[c];
-                        m = mn;
-                    }
-                    const float inv = 1.0f / l;
-#pragma unroll
-                    for (int c = 0; c < DH; ++c) o[c] *= inv;
-                    float dd[DH];
-                    fa_ld<DH>(srow + 3 * DH, dd);
-                    sLse[row * 4 + cq] = m + log2f(l);
-                    sD[row * 4 + cq] = fa_dot<DH>(dd, o);
+                for (int c = 0; c < DH; ++c) {
+                    qs[c] *= qscale;
+                    o[c] = 0.f;
                 }
+                float m = -INFINITY, l = 0.f;
+                for (int j = 0; j <= ti; ++j) {
+                    const float *sj = sS + (r0 + j) * kSS + hh * kSlot;
+                    float kj[DH], vj[DH];
+                    fa_ld<DH>(sj + DH, kj);
+                    fa_ld<DH>(sj + 2 * DH, vj);
+                    const float sc = fa_dot<DH>(qs, kj);
+                    const float mn = sc > m ? sc : m;
+                    const float corr = fb_ex2(m - mn), p = fb_ex2(sc - mn);
+                    l = l * corr + p;
 #pragma unroll
-                for (int e = 0; e < DH / 8; ++e) fb_granule(sb + kOffO, nullptr, row, c0 / 8 + e, o + 8 * e);
+                    for (int c = 0; c < DH; ++c) o[c] = o[c] * corr + p * vj[c];
+                    m = mn;
+                }
+                const float inv = 1.0f / l;
+#pragma unroll
+                for (int c = 0; c < DH; ++c) o[c] *= inv;
+                float dd[DH];
+                fa_ld<DH>(slot + 3 * DH, dd);
+                slot[4 * DH] = m + log2f(l);
+                slot[4 * DH + 1] = fa_dot<DH>(dd, o);
+#pragma unroll
+                for (int e = 0; e < DH / 8; ++e) fb_granule(sb + kOffO, nullptr, ri, c0 / 8 + e, o + 8 * e);
             }
             __syncthreads();
             // reverse mode: dq over this query's keys, dk and dv over the
             // queries that see this row's key
-            if (active) {
-                float dq[DH], dk[DH], dv[DH];
+            float dq[DH], dk[DH], dv[DH];
 #pragma unroll
-                for (int c = 0; c < DH; ++c) dq[c] = dk[c] = dv[c] = 0.f;
+            for (int c = 0; c < DH; ++c) dq[c] = dk[c] = dv[c] = 0.f;
+            if (act) {
+                {
+                    float qs[DH], dd[DH];
+                    fa_ld<DH>(slot, qs);
+                    fa_ld<DH>(slot + 3 * DH, dd);
+#pragma unroll
+                    for (int c = 0; c < DH; ++c) qs[c] *= qscale;
+                    const float lse = slot[4 * DH], D = slot[4 * DH + 1];
+                    for (int j = 0; j <= ti; ++j) {
+                        const float *sj = sS + (r0 + j) * kSS + hh * kSlot;
+                        float kj[DH], vj[DH];
+                        fa_ld<DH>(sj + DH, kj);
+                        fa_ld<DH>(sj + 2 * DH, vj);
+                        const float p = fb_ex2(fa_dot<DH>(qs, kj) - lse);
+                        const float ds = p * (fa_dot<DH>(dd, vj) - D);
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) dq[c] = fmaf(ds, kj[c], dq[c]);
+                    }
+                }
+                {
+                    float ks[DH], vv[DH];
+                    fa_ld<DH>(slot + DH, ks);
+                    fa_ld<DH>(slot + 2 * DH, vv);
+#pragma unroll
+                    for (int c = 0; c < DH; ++c) ks[c] *= qscale;
+                    for (int j = ti; j < T; ++j) {
+                        const float *sj = sS + (r0 + j) * kSS + hh * kSlot;
+                        float qj[DH], dj[DH];
+                        fa_ld<DH>(sj, qj);
+                        fa_ld<DH>(sj + 3 * DH, dj);
+                        const float2 ld = *reinterpret_cast<const float2 *>(sj + 4 * DH);  // log-sum-exp, D
+                        const float p = fb_ex2(fa_dot<DH>(qj, ks) - ld.x);
+                        const float ds = p * (fa_dot<DH>(dj, vv) - ld.y);
+#pragma unroll
+                        for (int c = 0; c < DH; ++c) {
+                            dk[c] = fmaf(ds, qj[c], dk[c]);
+                            dv[c] = fmaf(p, dj[c], dv[c]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < DH; ++c) {
+                    dq[c] *= scale;
+                    dk[c] *= scale;
+                }
+            }
+            __syncthreads();  // every loop has read q | k | v | do
+            if (act) {
+                fa_st<DH>(slot, dq);
+                fa_st<DH>(slot + DH, dk);
+                fa_st<DH>(slot + 2 * DH, dv);
+            }
+            __syncthreads();
+            // (3) thread (row, head cq): dq | dk | dv to the BF16 tile (zero
+            // outside the samples) and their column sums over the warp's rows
+            if (cq < HPG) {
+                const int cc = DH * (gq * HPG + cq);
+                const float *slot3 = sS + row * kSS + cq * kSlot;
+                float a[DH], b[DH], c3[DH];
                 if (valid) {
-                    {
-                        float qs[DH], dd[DH];
-                        fa_ld<DH>(srow, qs);
-                        fa_ld<DH>(srow + 3 * DH, dd);
+                    fa_ld<DH>(slot3, a);
+                    fa_ld<DH>(slot3 + DH, b);
+                    fa_ld<DH>(slot3 + 2 * DH, c3);
+                } else {
 #pragma unroll
-                        for (int c = 0; c < DH; ++c) qs[c] *= qscale;
-                        const float lse = sLse[row * 4 + cq], D = sD[row * 4 + cq];
-                        for (int j = 0; j <= tt; ++j) {
-                            const float *sj = sS + (r0 + j) * kSS + cq * 4 * DH;
-                            float kj[DH], vj[DH];
-                            fa_ld<DH>(sj + DH, kj);
-                            fa_ld<DH>(sj + 2 * DH, vj);
-                            const float p = fb_ex2(fa_dot<DH>(qs, kj) - lse);
-                            const float ds = p * (fa_dot<DH>(dd, vj) - D);
-#pragma unroll
-                            for (int c = 0; c < DH; ++c) dq[c] = fmaf(ds, kj[c], dq[c]);
-                        }
-#pragma unroll
-                        for (int c = 0; c < DH; ++c) dq[c] *= scale;
-                    }
-                    {
-                        float ks[DH], vv[DH];
-                        fa_ld<DH>(srow + DH, ks);
-                        fa_ld<DH>(srow + 2 * DH, vv);
-#pragma unroll
-                        for (int c = 0; c < DH; ++c) ks[c] *= qscale;
-                        for (int j = tt; j < T; ++j) {
-                            const int rj = r0 + j;
-                            const float *sj = sS + rj * kSS + cq * 4 * DH;
-                            float qj[DH], dj[DH];
-                            fa_ld<DH>(sj, qj);
-                            fa_ld<DH>(sj + 3 * DH, dj);
-                            const float p = fb_ex2(fa_dot<DH>(qj, ks) - sLse[rj * 4 + cq]);
-                            const float ds = p * (fa_dot<DH>(dj, vv) - sD[rj * 4 + cq]);
-#pragma unroll
-                            for (int c = 0; c < DH; ++c) {
-                                dk[c] = fmaf(ds, qj[c], dk[c]);
-                                dv[c] = fmaf(p, dj[c], dv[c]);
-                            }
-                        }
-#pragma unroll
-                        for (int c = 0; c < DH; ++c) dk[c] *= scale;
-                    }
+                    for (int c = 0; c < DH; ++c) a[c] = b[c] = c3[c] = 0.f;
                 }
 #pragma unroll
                 for (int e = 0; e < DH / 8; ++e) {
-                    fb_granule(sb + kOffDQ, nullptr, row, c0 / 8 + e, dq + 8 * e);
-                    fb_granule(sb + kOffDQ + 16384, nullptr, row, c0 / 8 + e, dk + 8 * e);
-                    fb_granule(sb + kOffDQ + 32768, nullptr, row, c0 / 8 + e, dv + 8 * e);
+                    fb_granule(sb + kOffDQ, nullptr, row, cc / 8 + e, a + 8 * e);
+                    fb_granule(sb + kOffDQ + 16384, nullptr, row, cc / 8 + e, b + 8 * e);
+                    fb_granule(sb + kOffDQ + 32768, nullptr, row, cc / 8 + e, c3 + 8 * e);
                 }
-                // column sums of dq | dk | dv over the warp's 32 rows
                 if constexpr (DH == 8) {
                     float t[32];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        t[c] = dq[c];
-                        t[8 + c] = dk[c];
-                        t[16 + c] = dv[c];
+                        t[c] = a[c];
+                        t[8 + c] = b[c];
+                        t[16 + c] = c3[c];
                         t[24 + c] = 0.f;
                     }
                     const float c32 = fb_colsum<32>(t, lane);
@@ -816,9 +870,9 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
                     float t[32], t2[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
-                        t[c] = dq[c];
-                        t[16 + c] = dk[c];
-                        t2[c] = dv[c];
+                        t[c] = a[c];
+                        t[16 + c] = b[c];
+                        t2[c] = c3[c];
                     }
                     const float c32 = fb_colsum<32>(t, lane), c16 = fb_colsum<16>(t2, lane);
                     if (gq == 0) {
@@ -830,7 +884,7 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
                     }
                 }
             }
-            __syncthreads();  // the scratch, log-sum-exp and D are rewritten by the next group
+            __syncthreads();  // the slots are rewritten by the next group
         }
         sync_async();
         if (tid == 0) {
@@ -875,12 +929,12 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
                 s1 += dx;
                 s2 += dx * xh[c];
             }
-            red[row * 4 + cq] = s1;
-            red[512 + row * 4 + cq] = s2;
+            red[cq * 128 + row] = s1;
+            red[512 + cq * 128 + row] = s2;
             __syncthreads();
-            const float m1 = (red[row * 4] + red[row * 4 + 1] + red[row * 4 + 2] + red[row * 4 + 3]) * (1.0f / kD);
-            const float m2 = (red[512 + row * 4] + red[512 + row * 4 + 1] + red[512 + row * 4 + 2] +
-                              red[512 + row * 4 + 3]) * (1.0f / kD);
+            const float m1 = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
+            const float m2 = (red[512 + row] + red[640 + row] + red[768 + row] +
+                              red[896 + row]) * (1.0f / kD);
             float out[16], t[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) out[c] = valid ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
