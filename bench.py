@@ -35,7 +35,7 @@ WORKLOAD = "n40"
 N_SAMPLES = 16384
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FMA: SMs x lanes x 2 x max clock
 # the tcgen05 kernels of the ansatz (forward, fused reverse mode, sampler decode, the remaining GEMMs)
-TENSOR_KERNELS = ("k_fwd_fused", "k_bwd_attn", "k_bwd_ffn", "k_decode_layer", "k_tc_gemm")
+TENSOR_KERNELS = ("k_fwd_fused", "k_bwd_attn", "k_bwd_ffn", "k_decode_step", "k_tc_gemm")
 # DRAM read + write bytes per launch of this step's kernels, from ncu captures of the current kernels at
 # this workload (profiles/); a kernel leaves this table when it changes
 KERNEL_TRAFFIC_BYTES = {}

@@ -1829,25 +1829,25 @@ constexpr uint32_t kColQKV = 0, kColO = 192, kColU = 256, kColY = 320, kTmemCols
 __device__ __forceinline__ constexpr uint32_t col_u(int c) { return c == 0 ? kColU : c == 3 ? 0u : 256u + 64u * uint32_t(c + 1); }
 }  // namespace dec
 
+constexpr int kDecMaxLayers = 16;
+
 struct DecodeArgs {
-    float *h;  // [n][64] residual rows of the new tokens, updated in place
     int64_t n;
     int rpc;  // prefixes per CTA (<= 128; rows past it in the 128-row tile are idle)
     float *pool;  // [node][L][192] q|k|v
-    int L, l, Tm, t;
+    int L, Tm, t;
     int64_t g0;
     const int32_t *anc;  // [n][Tm] ancestor nodes at depths 0..t-1
-    const float *ln1g, *ln1b, *ln2g, *ln2b, *bqkv, *bo, *b1, *b2;
-    // swizzled shared-memory images of the weights (high part, then the low
-    // part): qkv [192 rows], out-projection [64], FFN in [256], FFN out
-    // [64 rows, 4 K blocks]
-    const __nv_bfloat16 *tqkv, *to, *t1, *t2;
+    // per layer: LayerNorm, bias vectors and the swizzled shared-memory images
+    // of the weights (high part, then the low part): qkv [192 rows],
+    // out-projection [64], FFN in [256], FFN out [64 rows, 4 K blocks]
+    const float *ln1g[kDecMaxLayers], *ln1b[kDecMaxLayers], *ln2g[kDecMaxLayers], *ln2b[kDecMaxLayers];
+    const float *bqkv[kDecMaxLayers], *bo[kDecMaxLayers], *b1[kDecMaxLayers], *b2[kDecMaxLayers];
+    const __nv_bfloat16 *tqkv[kDecMaxLayers], *to[kDecMaxLayers], *t1[kDecMaxLayers], *t2[kDecMaxLayers];
     DevStatus *st;
-    // first layer: the rows are the embeddings of the prefixes' last tokens
-    // (tok_emb[input] + pos_emb[t]) instead of h; last layer: final LayerNorm,
-    // head and the masked conditionals pi~(. | prefix) -> cond[n][4] instead
-    // of writing h
-    int first, last;
+    // the rows enter as the embeddings of the prefixes' last tokens
+    // (tok_emb[input] + pos_emb[t]); after the last layer: final LayerNorm,
+    // head and the masked conditionals pi~(. | prefix) -> cond[n][4]
     const uint64_t *x;  // [n][W] prefixes
     int W, n_alpha, n_beta;
     const float *tok_emb, *pos_emb, *lnf_g, *lnf_b, *hw, *hb;
@@ -2063,7 +2063,7 @@ __device__ __forceinline__ void dec_mma(uint32_t tmem, uint32_t aHi, uint32_t aL
 }
 
 template <bool SPLIT, int DH>
-__global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g) {
+__global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_constant__ DecodeArgs g) {
     using namespace dec;
     constexpr int H = kD / DH, NR = kRows * H / kThreads;  // rows per thread in the attention
     extern __shared__ uint8_t smem_raw[];
@@ -2093,6 +2093,14 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
     const int64_t m0 = blockIdx.x * (int64_t)rpc;
     if (m0 >= n) return;  // (device-side counts only: a CTA with no rows)
     const int64_t n_cta = min(n, m0 + rpc);  // rows of this CTA are m0 .. n_cta - 1
+    // weight copies: phase 2 l brings layer l's Wqkv, phase 2 l + 1 its Wo,
+    // W1 and W2 (one barrier, waited in issue order)
+    auto issue_wqkv = [&](int l) {
+        constexpr uint32_t q = kQKV * 128;
+        mbar_expect_tx(wb, SPLIT ? 2 * q : q);
+        bulk_g2s(bB, g.tqkv[l], q, wb);
+        if (SPLIT) bulk_g2s(bB + kQkvLo, g.tqkv[l] + kQKV * kD, q, wb);
+    };
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
                      "r"(kTmemCols)
@@ -2103,14 +2111,11 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         tc::mbar_init(tc::smem_u32(mbar), 1);
         tc::mbar_init(wb, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // qkv weights (phase 0 of the weight barrier)
-        constexpr uint32_t q = kQKV * 128;
-        mbar_expect_tx(wb, SPLIT ? 2 * q : q);
-        bulk_g2s(bB, g.tqkv, q, wb);
-        if (SPLIT) bulk_g2s(bB + kQkvLo, g.tqkv + kQKV * kD, q, wb);
+        issue_wqkv(0);
     }
-    // residual rows (first layer: the embeddings, as k_embed_decode forms them);
-    // all of a thread's loads are issued before its shared stores
+    int wissued = 1, wdone = 0;  // weight-barrier phases issued / seen complete
+    // residual rows: the embeddings, as k_embed_decode forms them; all of a
+    // thread's loads are issued before its shared stores
     {
         constexpr int kIt = kRows * (kD / 4) / kThreads;
         float4 v[kIt];
@@ -2120,14 +2125,10 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
             const int r = it >> 4, c4 = it & 15;
             v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (m0 + r < n_cta) {
-                if (g.first) {
-                    const int inp = g.t == 0 ? 4 : token_at(g.x + (m0 + r) * g.W, g.Tm, g.t - 1);
-                    const float4 te = __ldg(reinterpret_cast<const float4 *>(g.tok_emb + inp * kD) + c4);
-                    const float4 pe = __ldg(reinterpret_cast<const float4 *>(g.pos_emb + g.t * kD) + c4);
-                    v[i] = make_float4(te.x + pe.x, te.y + pe.y, te.z + pe.z, te.w + pe.w);
-                } else {
-                    v[i] = *reinterpret_cast<const float4 *>(g.h + (m0 + r) * kD + 4 * c4);
-                }
+                const int inp = g.t == 0 ? 4 : token_at(g.x + (m0 + r) * g.W, g.Tm, g.t - 1);
+                const float4 te = __ldg(reinterpret_cast<const float4 *>(g.tok_emb + inp * kD) + c4);
+                const float4 pe = __ldg(reinterpret_cast<const float4 *>(g.pos_emb + g.t * kD) + c4);
+                v[i] = make_float4(te.x + pe.x, te.y + pe.y, te.z + pe.z, te.w + pe.w);
             }
         }
 #pragma unroll
@@ -2158,203 +2159,202 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_layer(DecodeArgs g)
         phase ^= 1u;
         tc::fence_after_sync();
     };
+    auto wait_weights = [&]() {
+        ok = __syncthreads_and(tc::mbar_wait(wb, uint32_t(wdone & 1)) ? 1 : 0) != 0;
+        if (ok) ++wdone;
+    };
     const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
     const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
-    const bool row_ok = m0 + row < n_cta;
 
-    // ---- LayerNorm 1 -> qkv
-    if (tid < kRows) dec_layernorm_row(sH, tid, g.ln1g, g.ln1b, aHi, aLo, SPLIT);
-    int wissued = 1, wdone = 0;  // weight-barrier phases issued / seen complete
-    ok = __syncthreads_and(tc::mbar_wait(wb, 0) ? 1 : 0) != 0;
-    if (ok) wdone = 1;
-    sync_async();
-    if (ok && tid == 0) {
-        dec_mma(tmem + kColQKV, uA, uA2, uB, uB + kQkvLo, kQKV, SPLIT, false);
-        tc::mma_commit(mb);
-    }
-    if (ok) wait_mma();
-    if (ok) {
-        // Wo into the (idle) FFN-out tile, the FFN weights over Wqkv (phase 1
-        // of the weight barrier): copies in flight during the epilogue and the
-        // attention
-        wissued = 2;
+    for (int l = 0; l < g.L && ok; ++l) {
+        // ---- LayerNorm 1 -> qkv
+        if (tid < kRows) dec_layernorm_row(sH, tid, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
+        wait_weights();  // Wqkv of layer l
+        sync_async();
+        if (!ok) break;
+        if (tid == 0) {
+            dec_mma(tmem + kColQKV, uA, uA2, uB, uB + kQkvLo, kQKV, SPLIT, false);
+            tc::mma_commit(mb);
+        }
+        wait_mma();
+        if (!ok) break;
+        // Wo into the (idle) FFN-out tile, the FFN weights over Wqkv: copies in
+        // flight during the epilogue and the attention
+        ++wissued;
         if (tid == 0) {
             constexpr uint32_t bo = kD * 128, bf = kF * 128;  // 8 KB, 32 KB
             mbar_expect_tx(wb, SPLIT ? 2 * (bo + 2 * bf) : bo + 2 * bf);
-            bulk_g2s(gHi, g.to, bo, wb);
-            bulk_g2s(bB + kW1Hi, g.t1, bf, wb);
-            bulk_g2s(bB + kW2Hi, g.t2, bf, wb);
+            bulk_g2s(gHi, g.to[l], bo, wb);
+            bulk_g2s(bB + kW1Hi, g.t1[l], bf, wb);
+            bulk_g2s(bB + kW2Hi, g.t2[l], bf, wb);
             if (SPLIT) {
-                bulk_g2s(gHi + 8192, g.to + kD * kD, bo, wb);
-                bulk_g2s(bB + kW1Lo, g.t1 + kF * kD, bf, wb);
-                bulk_g2s(bB + kW2Lo, g.t2 + kD * kF, bf, wb);
+                bulk_g2s(gHi + 8192, g.to[l] + kD * kD, bo, wb);
+                bulk_g2s(bB + kW1Lo, g.t1[l] + kF * kD, bf, wb);
+                bulk_g2s(bB + kW2Lo, g.t2[l] + kD * kF, bf, wb);
             }
         }
         // q|k|v + bias into the pool rows of the new nodes, 64 columns at a
         // time through the (free) A tile: TMEM -> shared (thread = row, 16-byte
         // granules XOR-swizzled by the row) -> global (16 threads per row, each
         // row a contiguous 256-byte segment)
-        float *slab = reinterpret_cast<float *>(aHi);
-        for (int c = 0; c < kQKV / 64; ++c) {
+        {
+            const float *bq = g.bqkv[l];
+            float *slab = reinterpret_cast<float *>(aHi);
+            for (int c = 0; c < kQKV / 64; ++c) {
 #pragma unroll
-            for (int b = 0; b < kCW / 16; ++b) {
-                const int cl = kCW * cq + 16 * b;  // column within the chunk
-                uint32_t r16[16];
-                tc::tmem_ld16(tl + kColQKV + 64 * c + cl, r16);
+                for (int b = 0; b < kCW / 16; ++b) {
+                    const int cl = kCW * cq + 16 * b;  // column within the chunk
+                    uint32_t r16[16];
+                    tc::tmem_ld16(tl + kColQKV + 64 * c + cl, r16);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int gi = (cl >> 2) + q;
-                    const int col = 64 * c + 4 * gi;
-                    *reinterpret_cast<float4 *>(slab + row * 64 + 4 * (gi ^ (row & 15))) =
-                        make_float4(__uint_as_float(r16[4 * q]) + g.bqkv[col],
-                                    __uint_as_float(r16[4 * q + 1]) + g.bqkv[col + 1],
-                                    __uint_as_float(r16[4 * q + 2]) + g.bqkv[col + 2],
-                                    __uint_as_float(r16[4 * q + 3]) + g.bqkv[col + 3]);
+                    for (int q = 0; q < 4; ++q) {
+                        const int gi = (cl >> 2) + q;
+                        const int col = 64 * c + 4 * gi;
+                        *reinterpret_cast<float4 *>(slab + row * 64 + 4 * (gi ^ (row & 15))) =
+                            make_float4(__uint_as_float(r16[4 * q]) + bq[col], __uint_as_float(r16[4 * q + 1]) + bq[col + 1],
+                                        __uint_as_float(r16[4 * q + 2]) + bq[col + 2],
+                                        __uint_as_float(r16[4 * q + 3]) + bq[col + 3]);
+                    }
                 }
-            }
-            __syncthreads();
+                __syncthreads();
 #pragma unroll
-            for (int i = 0; i < kRows * 16 / kThreads; ++i) {
-                const int it = tid + kThreads * i;
-                const int r = it >> 4, gi = it & 15;
-                if (m0 + r < n_cta) {
-                    float *prow = g.pool + ((g0 + m0 + r) * g.L + g.l) * (int64_t)kQKV + 64 * c;
-                    *reinterpret_cast<float4 *>(prow + 4 * gi) =
-                        *reinterpret_cast<const float4 *>(slab + r * 64 + 4 * (gi ^ (r & 15)));
+                for (int i = 0; i < kRows * 16 / kThreads; ++i) {
+                    const int it = tid + kThreads * i;
+                    const int r = it >> 4, gi = it & 15;
+                    if (m0 + r < n_cta) {
+                        float *prow = g.pool + ((g0 + m0 + r) * g.L + l) * (int64_t)kQKV + 64 * c;
+                        *reinterpret_cast<float4 *>(prow + 4 * gi) =
+                            *reinterpret_cast<const float4 *>(slab + r * 64 + 4 * (gi ^ (r & 15)));
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
-    }
-    __syncthreads();  // this CTA's pool rows are visible to all its threads
-    if (ok) {
         // ---- attention (thread: head tid % H of the NR rows of group tid / H) -> A tile
-        const int hh = tid % H;
-        const int r0 = (tid / H) * NR;
-        float o[NR][DH];
-        dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g0, m0 + r0, m0, n_cta, g.t, g.L, g.l, hh, o);
+        {
+            const int hh = tid % H;
+            const int r0 = (tid / H) * NR;
+            float o[NR][DH];
+            dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g0, m0 + r0, m0, n_cta, g.t, g.L, l, hh, o);
 #pragma unroll
-        for (int k = 0; k < NR; ++k)
+            for (int k = 0; k < NR; ++k)
 #pragma unroll
-            for (int gi = 0; gi < DH / 8; ++gi) {
-                float x[8];
+                for (int gi = 0; gi < DH / 8; ++gi) {
+                    float x[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = o[k][8 * gi + e];
-                dec_store_granule(aHi, aLo, r0 + k, hh * (DH / 8) + gi, x, SPLIT);
-            }
-    }
-    if (ok) {
-        ok = __syncthreads_and(tc::mbar_wait(wb, 1) ? 1 : 0) != 0;
-        if (ok) wdone = 2;
-    }
-    sync_async();
-    if (ok) {
+                    for (int e = 0; e < 8; ++e) x[e] = o[k][8 * gi + e];
+                    dec_store_granule(aHi, aLo, r0 + k, hh * (DH / 8) + gi, x, SPLIT);
+                }
+        }
+        wait_weights();  // Wo, W1, W2 of layer l
+        sync_async();
+        if (!ok) break;
         if (tid == 0) {
             dec_mma(tmem + kColO, uA, uA2, uG, uG + 8192, kD, SPLIT, false);
             tc::mma_commit(mb);
         }
         wait_mma();
-    }
-    if (ok) {
-        // h += attn Wo^T + bo (kCW columns per thread)
+        if (!ok) break;
+        {
+            // h += attn Wo^T + bo (kCW columns per thread)
+            const float *bo = g.bo[l];
 #pragma unroll
-        for (int b = 0; b < kCW / 16; ++b) {
-            const int c0 = kCW * cq + 16 * b;
-            uint32_t r16[16];
-            tc::tmem_ld16(tl + kColO + c0, r16);
+            for (int b = 0; b < kCW / 16; ++b) {
+                const int c0 = kCW * cq + 16 * b;
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColO + c0, r16);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float v = __uint_as_float(r16[j]) + g.bo[c0 + j];
-                sH[row * kHS + c0 + j] = sH[row * kHS + c0 + j] + v;
+                for (int j = 0; j < 16; ++j) {
+                    const float v = __uint_as_float(r16[j]) + bo[c0 + j];
+                    sH[row * kHS + c0 + j] = sH[row * kHS + c0 + j] + v;
+                }
             }
         }
-    }
-    __syncthreads();
-    // ---- LayerNorm 2 -> FFN: the four MMA1(c) = LN2 W1_c^T are issued together
-    // (TMEM columns of the finished q|k|v and free columns), then per chunk:
-    // GELU of U_c into registers while MMA2(c - 1) runs, G_c into shared
-    // memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
-    if (ok && tid < kRows) dec_layernorm_row(sH, tid, g.ln2g, g.ln2b, aHi, aLo, SPLIT);
-    sync_async();
-    if (ok && tid == 0) {
-#pragma unroll
-        for (int c = 0; c < kF / kD; ++c)
-            dec_mma(tmem + col_u(c), uA, uA2, uB + kW1Hi + 8192 * c, uB + kW1Lo + 8192 * c, kD, SPLIT, false);
-        tc::mma_commit(mb);
-    }
-    if (ok) wait_mma();
-    for (int c = 0; c < kF / kD && ok; ++c) {
-        float x[kCW];
-#pragma unroll
-        for (int b = 0; b < kCW / 16; ++b) {
-            const int c0 = kCW * cq + 16 * b;
-            uint32_t r16[16];
-            tc::tmem_ld16(tl + col_u(c) + c0, r16);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) x[16 * b + e] = tc::gelu_f(__uint_as_float(r16[e]) + g.b1[kD * c + c0 + e]);
-        }
-        if (c > 0) {
-            wait_mma();
-            if (!ok) break;
-        }
-#pragma unroll
-        for (int b = 0; b < kCW / 16; ++b)
-#pragma unroll
-            for (int gi = 0; gi < 2; ++gi) {
-                float xg[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) xg[e] = x[16 * b + 8 * gi + e];
-                dec_store_granule(gHi, gLo, row, ((kCW * cq + 16 * b) >> 3) + gi, xg, SPLIT);
-            }
+        __syncthreads();
+        // ---- LayerNorm 2 -> FFN: the four MMA1(c) = LN2 W1_c^T are issued
+        // together (TMEM columns of the finished q|k|v and free columns), then
+        // per chunk: GELU of U_c into registers while MMA2(c - 1) runs, G_c
+        // into shared memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
+        if (tid < kRows) dec_layernorm_row(sH, tid, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
         sync_async();
         if (tid == 0) {
-            dec_mma(tmem + kColY, uG, uG2, uB + kW2Hi + 8192 * c, uB + kW2Lo + 8192 * c, kD, SPLIT, c > 0);
+#pragma unroll
+            for (int c = 0; c < kF / kD; ++c)
+                dec_mma(tmem + col_u(c), uA, uA2, uB + kW1Hi + 8192 * c, uB + kW1Lo + 8192 * c, kD, SPLIT, false);
             tc::mma_commit(mb);
         }
-    }
-    if (ok) wait_mma();
-    if (ok) {
-        // h += FFN + b2: back to global, or (last layer) into the shared rows
+        wait_mma();
+        if (!ok) break;
+        // W1 consumed: the next layer's Wqkv comes in over it during the FFN
+        if (l + 1 < g.L) {
+            ++wissued;
+            if (tid == 0) issue_wqkv(l + 1);
+        }
+        const float *b1 = g.b1[l];
+        for (int c = 0; c < kF / kD && ok; ++c) {
+            float x[kCW];
 #pragma unroll
-        for (int b = 0; b < kCW / 16; ++b) {
-            const int c0 = kCW * cq + 16 * b;
-            uint32_t r16[16];
-            tc::tmem_ld16(tl + kColY + c0, r16);
+            for (int b = 0; b < kCW / 16; ++b) {
+                const int c0 = kCW * cq + 16 * b;
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + col_u(c) + c0, r16);
 #pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-                float v[4];
+                for (int e = 0; e < 16; ++e) x[16 * b + e] = tc::gelu_f(__uint_as_float(r16[e]) + b1[kD * c + c0 + e]);
+            }
+            if (c > 0) {
+                wait_mma();
+                if (!ok) break;
+            }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float y = __uint_as_float(r16[j + e]) + g.b2[c0 + j + e];
-                    v[e] = sH[row * kHS + c0 + j + e] + y;
+            for (int b = 0; b < kCW / 16; ++b)
+#pragma unroll
+                for (int gi = 0; gi < 2; ++gi) {
+                    float xg[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) xg[e] = x[16 * b + 8 * gi + e];
+                    dec_store_granule(gHi, gLo, row, ((kCW * cq + 16 * b) >> 3) + gi, xg, SPLIT);
                 }
-                if (g.last) {
+            sync_async();
+            if (tid == 0) {
+                dec_mma(tmem + kColY, uG, uG2, uB + kW2Hi + 8192 * c, uB + kW2Lo + 8192 * c, kD, SPLIT, c > 0);
+                tc::mma_commit(mb);
+            }
+        }
+        if (!ok) break;
+        wait_mma();
+        if (!ok) break;
+        {
+            // h += FFN + b2, in the shared rows
+            const float *b2 = g.b2[l];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) sH[row * kHS + c0 + j + e] = v[e];
-                } else if (row_ok) {
-                    *reinterpret_cast<float4 *>(g.h + (m0 + row) * kD + c0 + j) = make_float4(v[0], v[1], v[2], v[3]);
+            for (int b = 0; b < kCW / 16; ++b) {
+                const int c0 = kCW * cq + 16 * b;
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColY + c0, r16);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float y = __uint_as_float(r16[j]) + b2[c0 + j];
+                    sH[row * kHS + c0 + j] = sH[row * kHS + c0 + j] + y;
                 }
             }
         }
-    }
-    if (g.last) {
-        // final LayerNorm (k_ln_fwd_v's sums), head logits (head_logits' sum)
-        // and the masked conditionals of the next token
         __syncthreads();
-        if (ok && tid < kRows && m0 + tid < n_cta) {
-            float hf[kD];
-            dec_layernorm_row_f32(sH, tid, g.lnf_g, g.lnf_b, hf);
-            float zr[4];
+    }
+    // ---- final LayerNorm (k_ln_fwd_v's sums), head logits (head_logits'
+    // sum) and the masked conditionals of the next token
+    if (ok && tid < kRows && m0 + tid < n_cta) {
+        float hf[kD];
+        dec_layernorm_row_f32(sH, tid, g.lnf_g, g.lnf_b, hf);
+        float zr[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) zr[v] = g.hb[v];
+        for (int v = 0; v < 4; ++v) zr[v] = g.hb[v];
 #pragma unroll
-            for (int c = 0; c < kD; ++c)
+        for (int c = 0; c < kD; ++c)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) zr[v] += hf[c] * __ldg(g.hw + v * kD + c);
-            if (!cond_from_logits<float>(g.x + (m0 + tid) * g.W, g.Tm, g.t, g.n_alpha, g.n_beta, zr,
-                                         g.cond + (m0 + tid) * 4))
-                record_status(g.st, NNQS_E_SECTOR, m0 + tid);
-        }
+            for (int v = 0; v < 4; ++v) zr[v] += hf[c] * __ldg(g.hw + v * kD + c);
+        if (!cond_from_logits<float>(g.x + (m0 + tid) * g.W, g.Tm, g.t, g.n_alpha, g.n_beta, zr,
+                                     g.cond + (m0 + tid) * 4))
+            record_status(g.st, NNQS_E_SECTOR, m0 + tid);
     }
     if (!ok && tid == 0) {
         if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -11;
@@ -3536,7 +3536,7 @@ nnqs_status attn_decode(cudaStream_t s, int dh, const R *pool, const int32_t *an
 
 // one decoding step for C prefixes at depth t (global node ids g0 ...)
 bool decode_fused_ok(const nnqs_model *M, const TcWeights &w) {
-    if (M->d != dec::kD || M->F != dec::kF || (M->dh != 8 && M->dh != 16)) return false;
+    if (M->d != dec::kD || M->F != dec::kF || (M->dh != 8 && M->dh != 16) || M->L > kDecMaxLayers) return false;
     for (int l = 0; l < M->L; ++l) {
         if (w.pcols[tc_slot(l, 0)] != 64 || w.pcols[tc_slot(l, 1)] != 64 || w.pcols[tc_slot(l, 2)] != 64 ||
             w.pcols[tc_slot(l, 3)] != 256)
@@ -3546,40 +3546,38 @@ bool decode_fused_ok(const nnqs_model *M, const TcWeights &w) {
 }
 
 template <bool SPLIT, int DH>
-nnqs_status launch_decode_layer(const DecodeArgs &g, cudaStream_t s) {
+nnqs_status launch_decode_step(const DecodeArgs &g, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_decode_layer<SPLIT, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        NNQS_CUDA_TRY(cudaFuncSetAttribute(k_decode_step<SPLIT, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            dec::kSmem));
         attr = true;
     }
     // device-side counts: enough CTAs for any n <= g.n (the capacity)
     const unsigned grid = g.n_dev ? (unsigned)std::max<int64_t>(g.n_sms, (g.n + dec::kRows - 1) / dec::kRows)
                                   : (unsigned)((g.n + g.rpc - 1) / g.rpc);
-    NNQS_LAUNCH("k_decode_layer", s, (k_decode_layer<SPLIT, DH><<<grid, dec::kThreads, dec::kSmem, s>>>(g)));
+    NNQS_LAUNCH("k_decode_step", s, (k_decode_step<SPLIT, DH><<<grid, dec::kThreads, dec::kSmem, s>>>(g)));
     return NNQS_OK;
 }
 
-// one layer of the cached decode for n new tokens (rows h) in one launch
-// n_dev / g0_dev (optional): the counts live on the device; n is then the
-// capacity (an upper bound of *n_dev) and g0 is ignored
-// the four GEMMs of one fused decode layer over n prefixes (method FLOPs) and
-// its bytes: the new k | v rows and the layer's input and output rows, the
-// weight images once
-void note_decode_work(int64_t n, bool split) {
-    note_work("k_decode_layer", 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
-              4.0 * double(n) * (2 * dec::kD + dec::kQKV) +
-                  2.0 * (split ? 2.0 : 1.0) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF));
+// the four GEMMs of every layer of one fused decoding step over n prefixes
+// (method FLOPs) and its bytes: per layer the new k | v rows, the weight
+// images once
+void note_decode_work(int64_t n, bool split, int L) {
+    note_work("k_decode_step", L * 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
+              L * (4.0 * double(n) * 2 * dec::kD +
+                   2.0 * (split ? 2.0 : 1.0) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF)));
 }
 
-nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
-                               float *h, int64_t n, float *pool, const int32_t *anc, int t, int64_t g0, int l,
-                               double *cond, DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
-                               const int64_t *g0_dev = nullptr) {
+// One decoding step of all layers for n prefixes at depth t (global node ids
+// g0 ...): the embeddings of their last tokens in, the conditionals of the
+// next token out (k_decode_step)
+nnqs_status decode_step_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
+                              int64_t n, float *pool, const int32_t *anc, int t, int64_t g0, double *cond,
+                              DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
+                              const int64_t *g0_dev = nullptr) {
     if (n == 0) return NNQS_OK;
-    const auto &Lw = V.layer[l];
     DecodeArgs g{};
-    g.h = h;
     g.n = n;
     g.n_dev = n_dev;
     g.g0_dev = g0_dev;
@@ -3590,22 +3588,26 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
     g.rpc = (int)std::min<int64_t>(dec::kRows, std::max<int64_t>(1, (n + sm_count() - 1) / sm_count()));
     g.pool = pool;
     g.L = M->L;
-    g.l = l;
     g.Tm = M->T;
     g.t = t;
     g.g0 = g0;
     g.anc = anc;
-    g.ln1g = Lw.ln1g;
-    g.ln1b = Lw.ln1b;
-    g.ln2g = Lw.ln2g;
-    g.ln2b = Lw.ln2b;
-    g.bqkv = Lw.bqkv;
-    g.bo = Lw.bo;
-    g.b1 = Lw.b1;
-    g.b2 = Lw.b2;
     const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(w.tiles);
-    g.first = l == 0;
-    g.last = l == M->L - 1;
+    for (int l = 0; l < M->L; ++l) {
+        const auto &Lw = V.layer[l];
+        g.ln1g[l] = Lw.ln1g;
+        g.ln1b[l] = Lw.ln1b;
+        g.ln2g[l] = Lw.ln2g;
+        g.ln2b[l] = Lw.ln2b;
+        g.bqkv[l] = Lw.bqkv;
+        g.bo[l] = Lw.bo;
+        g.b1[l] = Lw.b1;
+        g.b2[l] = Lw.b2;
+        g.tqkv[l] = tiles + w.tile_off[tc_slot(l, 0)];
+        g.to[l] = tiles + w.tile_off[tc_slot(l, 1)];
+        g.t1[l] = tiles + w.tile_off[tc_slot(l, 2)];
+        g.t2[l] = tiles + w.tile_off[tc_slot(l, 3)];
+    }
     g.x = x;
     g.W = M->W;
     g.n_alpha = M->cfg.n_alpha;
@@ -3617,16 +3619,12 @@ nnqs_status decode_layer_fused(const nnqs_model *M, const Views<float> &V, const
     g.hw = V.hw;
     g.hb = V.hb;
     g.cond = cond;
-    g.tqkv = tiles + w.tile_off[tc_slot(l, 0)];
-    g.to = tiles + w.tile_off[tc_slot(l, 1)];
-    g.t1 = tiles + w.tile_off[tc_slot(l, 2)];
-    g.t2 = tiles + w.tile_off[tc_slot(l, 3)];
     g.st = st;
     // work per launch (for the profile); with the level size on the device
     // the walk notes it once the size is known (n is the capacity here)
-    if (!n_dev) note_decode_work(n, w.split);
-    if (w.split) return M->dh == 8 ? launch_decode_layer<true, 8>(g, s) : launch_decode_layer<true, 16>(g, s);
-    return M->dh == 8 ? launch_decode_layer<false, 8>(g, s) : launch_decode_layer<false, 16>(g, s);
+    if (!n_dev) note_decode_work(n, w.split, M->L);
+    if (w.split) return M->dh == 8 ? launch_decode_step<true, 8>(g, s) : launch_decode_step<true, 16>(g, s);
+    return M->dh == 8 ? launch_decode_step<false, 8>(g, s) : launch_decode_step<false, 16>(g, s);
 }
 
 template <class R>
@@ -3638,11 +3636,7 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
     R *h = A.hbuf;
     if constexpr (sizeof(R) == 4) {
         // fused: embedding in the first layer, conditionals in the last
-        if (tcw && decode_fused_ok(M, *tcw)) {
-            for (int l = 0; l < L; ++l)
-                NNQS_TRY(decode_layer_fused(M, V, *tcw, x, h, C, pool, anc, t, g0, l, cond, st, s));
-            return NNQS_OK;
-        }
+        if (tcw && decode_fused_ok(M, *tcw)) return decode_step_fused(M, V, *tcw, x, C, pool, anc, t, g0, cond, st, s);
     }
     NNQS_LAUNCH("k_embed", s, k_embed_decode<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, t, T, d, V.tok, V.pos, h));
     for (int l = 0; l < L; ++l) {
@@ -3767,11 +3761,10 @@ nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64
         int64_t n = 0;
         NNQS_CUDA_TRY(cudaMemcpyAsync(&n, n_dev, 8, cudaMemcpyDeviceToHost, s));
         NNQS_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int l = 0; l < M->L; ++l) note_decode_work(n, ctx->tcw.split);
+        note_decode_work(n, ctx->tcw.split, M->L);
     }
-    for (int l = 0; l < M->L; ++l)
-        NNQS_TRY(decode_layer_fused(M, V, ctx->tcw, prefixes, ctx->Af.hbuf, cap, static_cast<float *>(ctx->pool), anc,
-                                    t, 0, l, cond, st, s, n_dev, g0_dev));
+    NNQS_TRY(decode_step_fused(M, V, ctx->tcw, prefixes, cap, static_cast<float *>(ctx->pool), anc, t, 0, cond, st, s,
+                               n_dev, g0_dev));
     return NNQS_OK;
 }
 
