@@ -59,8 +59,8 @@ def parse():
                     help="rows of the exact-mode side line (0 = skip)")
     ap.add_argument("--n120-steps", type=int, default=3, help="timed steps of the 120-qubit side line (0 = skip)")
     ap.add_argument("--case", default=None,
-                    choices=["sweep-pairs", "sweep-groups", "logpsi", "logpsi-unfused", "grad", "grad-unfused",
-                             "eloc-exact"],
+                    choices=["sweep-pairs", "sweep-groups", "sweep-pairs-sampled", "sweep-groups-sampled", "logpsi",
+                             "logpsi-unfused", "grad", "grad-unfused", "eloc-exact"],
                     help="time one hot-path call alone (for profiling) instead of the VMC step")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of --case (n40, n76, n120, n30, n12)")
     ap.add_argument("--n", type=int, default=16384, help="samples (table rows) of --case")
@@ -856,7 +856,8 @@ def run_ours(args):
 def run_case(args):
     """One hot-path call on a named workload, timed alone (three warm-up
     calls, then the mean of five with CUDA events): the sample-aware sweeps
-    over uniform sector samples with a stand-in log psi table, the ansatz
+    over uniform sector samples with a stand-in log psi table or over the
+    sampler's own draws from the random-init ansatz (-sampled), the ansatz
     forward (fused, or layer by layer), the forward with its reverse mode for
     a random seed vector (fused, or layer by layer), or exact-mode E_loc of
     the first rows.
@@ -877,7 +878,17 @@ def run_case(args):
     if args.case.startswith("sweep") or args.case == "eloc-exact":
         h, eri = I.workload_integrals(wl)
         ham = B.build_pauli(h, eri)
-    if args.case.startswith("sweep"):
+    if args.case.endswith("-sampled"):
+        # the step's own input: unique samples drawn by the sampler from the
+        # random-init ansatz, with their log psi
+        model = B.Model(wl.n_qubits, wl.n_alpha, wl.n_beta, wl.d_model, wl.n_layers, wl.n_heads)
+        flat = model.pack(I.workload_params(wl))
+        x, _ = B.sample(model, flat, args.n, seed=1000, max_unique=max(1 << 15, 2 * args.n), prec=B.BF16X3)
+        rows = min(rows, x.shape[0])
+        lp = B.logpsi(model, flat, x, B.BF16X3)
+        fl = B.SWEEP_PAIRS if args.case.startswith("sweep-pairs") else B.SWEEP_GROUPS
+        call = lambda: B.eloc(ham, x, lp, wl.n_alpha, wl.n_beta, flags=fl, n_rows=rows, check=False)
+    elif args.case.startswith("sweep"):
         lp = torch.from_numpy(I.random_logpsi(args.n, seed=4, amp_std=0.1)).cuda()
         fl = B.SWEEP_PAIRS if args.case == "sweep-pairs" else B.SWEEP_GROUPS
         call = lambda: B.eloc(ham, x, lp, wl.n_alpha, wl.n_beta, flags=fl, n_rows=rows, check=False)

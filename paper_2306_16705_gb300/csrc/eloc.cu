@@ -229,7 +229,6 @@ __global__ void __launch_bounds__(kSweepThreads)
                   const double *__restrict__ tcoef, int64_t row_begin, int64_t n_rows,
                   double2 *__restrict__ partial) {
     __shared__ uint64_t s_y[kPairTile * W];
-    const int lane = threadIdx.x & 31;
     const int64_t rbase = blockIdx.x * (int64_t)(kSweepThreads * kPairRows);
     Bits<W> x[kPairRows];
     RowRatio rx[kPairRows];
@@ -275,38 +274,24 @@ __global__ void __launch_bounds__(kSweepThreads)
                 g[q] = (d == 0 || d > max_weight || !act[q]) ? -1 : gtab.find(m);
                 any |= g[q] >= 0;
             }
-            unsigned hits = __ballot_sync(0xffffffffu, any);
-            if (hits == 0) continue;
-            // each lane's ratios psi(y)/psi(x) in parallel, then the whole warp
-            // sums the popcount signs of one hit's group at a time
-            double2 rr[kPairRows];
+            if (!any) continue;
+            // each lane its own hits: the ratio psi(y)/psi(x) and the popcount
+            // signs over the hit's group, the group's strings in order (the
+            // sampler's samples cluster, so hits are common and the lanes'
+            // dependent loads overlap; a group averages about five strings)
 #pragma unroll
-            for (int q = 0; q < kPairRows; ++q)
-                rr[q] = g[q] >= 0 ? rx[q].of(psi, lut_lp, ct + k) : make_double2(0.0, 0.0);
-            while (hits) {
-                const int leader = __ffs(hits) - 1;
-                hits &= hits - 1;
-#pragma unroll
-                for (int q = 0; q < kPairRows; ++q) {
-                    const int32_t gq = __shfl_sync(0xffffffffu, g[q], leader);
-                    if (gq < 0) continue;
-                    Bits<W> xq;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) xq.w[w] = __shfl_sync(0xffffffffu, x[q].w[w], leader);
-                    const uint32_t t0 = __ldg(goff + gq), t1 = __ldg(goff + gq + 1);
-                    double c = 0.0;
-                    for (uint32_t t = t0 + lane; t < t1; t += 32) {
-                        const Bits<W> yz = load_bits<W>(tyz, t);
-                        const double v = __ldg(tcoef + t);
-                        c += (popc_and<W>(xq, yz) & 1) ? -v : v;
-                    }
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-                    if (lane == leader) {
-                        er[q] += c * rr[q].x;
-                        ei[q] += c * rr[q].y;
-                    }
+            for (int q = 0; q < kPairRows; ++q) {
+                if (g[q] < 0) continue;
+                const double2 rr = rx[q].of(psi, lut_lp, ct + k);
+                const uint32_t t0 = __ldg(goff + g[q]), t1 = __ldg(goff + g[q] + 1);
+                double c = 0.0;
+                for (uint32_t t = t0; t < t1; ++t) {
+                    const Bits<W> yz = load_bits<W>(tyz, t);
+                    const double v = __ldg(tcoef + t);
+                    c += (popc_and<W>(x[q], yz) & 1) ? -v : v;
                 }
+                er[q] += c * rr.x;
+                ei[q] += c * rr.y;
             }
         }
     }
