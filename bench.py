@@ -593,11 +593,12 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def timed(n_steps, v, stages=None):
-        # every timed step starts from the same random-init parameters and
-        # Adam state (restored outside the timed region; the Adam update
-        # itself runs inside), so each step samples the same distribution
-        p0, m0, v0, t0 = v.params.clone(), v.m.clone(), v.v.clone(), v.t
+    def timed(n_steps, v, stages=None, state=None):
+        # every timed step starts from the same random-init parameters, Adam
+        # state and step count (restored outside the timed region; the Adam
+        # update itself runs inside), so each step draws the same samples;
+        # `state` (params, m, v, t) fixes that start across several calls
+        p0, m0, v0, t0 = state if state is not None else (v.params.clone(), v.m.clone(), v.v.clone(), v.t)
         ts, nu = [], 0
         for _ in range(n_steps):
             v.params.copy_(p0)
@@ -620,20 +621,21 @@ def run_ours(args):
                 stages["adam"] += marks[1].elapsed_time(marks[2])
         return ts, nu
 
+    state0 = (vmc.params.clone(), vmc.m.clone(), vmc.v.clone(), vmc.t)
     l0 = B.launch_count()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local, not args.no_clocks) as clk:
-        times, n_u_total = timed(args.steps, vmc)
+        times, n_u_total = timed(args.steps, vmc, state=state0)
     torch.cuda.synchronize()
     launches = B.launch_count() - l0
-    # the same number of steps again with every launch bracketed by CUDA
-    # events: per-kernel device times for the roofline
+    # the same steps again (same start state, so the same samples) with every
+    # launch bracketed by CUDA events: per-kernel device times for the roofline
     B.profile_reset()
     B.profile_enable(True)
     stages = {"sample": 0.0, "energy_grad": 0.0, "adam": 0.0}
-    prof_times, _ = timed(args.steps, vmc, stages)
+    prof_times, _ = timed(args.steps, vmc, stages, state=state0)
     prof = B.profile()
     B.profile_enable(False)
     ms_step = float(np.mean(times))

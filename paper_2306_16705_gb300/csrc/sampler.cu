@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -451,6 +452,16 @@ std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;
 uint64_t g_graph_clock = 0;
 
+// CUDA-graph replay of the walk, from NNQS_SAMPLE_GRAPH in the environment
+// (read once): 0 = always launch the kernels directly (comparisons)
+bool sample_graphs_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("NNQS_SAMPLE_GRAPH");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 nnqs_status walk_kernels(const nnqs_model *M, const float *params, int prec, int64_t cap, const SLayout &L,
                          DevStatus *st, cudaStream_t s) {
     Arena sub(L.region);
@@ -485,7 +496,7 @@ nnqs_status dev_walk(const nnqs_model *M, const float *params, uint64_t n_sample
     const uint64_t args[2] = {n_samples, seed};
     NNQS_CUDA_TRY(cudaMemcpyAsync(L.args, args, sizeof args, cudaMemcpyHostToDevice, s));
     nnqs_status rc = NNQS_OK;
-    if (profiling_on()) {
+    if (profiling_on() || !sample_graphs_enabled()) {
         rc = walk_kernels(M, params, prec, cap, L, st, s);
     } else {
         GraphKey key{};
