@@ -37,8 +37,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FMA: SMs x lanes 
 # the tcgen05 kernels of the ansatz (forward, fused reverse mode, sampler decode, the remaining GEMMs)
 TENSOR_KERNELS = ("k_fwd_fused", "k_bwd_attn", "k_bwd_ffn", "k_decode_step", "k_tc_gemm")
 # DRAM read + write bytes per launch of this step's kernels, from ncu captures of the current kernels at
-# this workload (profiles/); a kernel leaves this table when it changes
-KERNEL_TRAFFIC_BYTES = {}
+# this workload (profiles/k_bwd_fused_energy_grad_n40.md); a kernel leaves this table when it changes.
+# k_decode_step's traffic grows with the token step (profiles/k_decode_step_sample_n40.md): no single figure.
+KERNEL_TRAFFIC_BYTES = {"k_bwd_ffn": 167.9e6 + 46.7e6, "k_bwd_attn": 167.9e6 + 40.3e6}
 
 
 def parse():

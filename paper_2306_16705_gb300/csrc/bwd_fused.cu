@@ -466,6 +466,7 @@ __global__ void k_bwd_ffn_reduce(const float *__restrict__ part, int grid, float
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= kBwdFfnPart) return;
     float s = 0.f;
+#pragma unroll 8
     for (int c = 0; c < grid; ++c) s += part[(int64_t)c * kBwdFfnPart + e];
     constexpr int a = 256 * 64, b = 2 * a, c1 = b + 256, c2 = c1 + 64, c3 = c2 + 64;
     float *dst = e < a ? dw1 + e : e < b ? dw2 + (e - a) : e < c1 ? db1 + (e - b) : e < c2 ? dg2 + (e - c1)
@@ -1017,6 +1018,7 @@ __global__ void k_bwd_attn_reduce(const float *__restrict__ part, int grid, floa
                  : e < c3 ? db1 + (e - c2) : (dsum ? dsum + (e - c3) : nullptr);
     if (!dst) return;
     float s = 0.f;
+#pragma unroll 8
     for (int c = 0; c < grid; ++c) s += part[(int64_t)c * kBwdAttnPart + e];
     *dst += s;
 }

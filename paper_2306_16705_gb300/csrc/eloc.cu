@@ -418,7 +418,7 @@ nnqs_status eloc_sa_impl(const nnqs_ham *H, const uint64_t *lut, const double *l
 // Energy statistics over 128 fixed row ranges (the FP64 sums of one block
 // were bound by a single SM's FP64 pipe): pass 0 gives the blocks' (sum w,
 // sum w Re E_loc, sum w Im E_loc), pass 1 the blocks' sum w |E_loc - E|^2 with
-// E from pass 0; k_stats_fin adds the block sums in block order.
+// E from pass 0; k_stats_fin adds the block sums by a fixed tree.
 constexpr int kStatBlocks = 128, kStatPartThreads = 256;
 
 __global__ void __launch_bounds__(kStatPartThreads)
@@ -461,14 +461,23 @@ __global__ void __launch_bounds__(kStatPartThreads)
     }
 }
 
-__global__ void k_stats_fin(const double *__restrict__ part, int nb, int pass, double *__restrict__ stats) {
-    if (threadIdx.x != 0) return;
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int k = 0; k < nb; ++k) {
-        a += part[3 * k];
-        b += part[3 * k + 1];
-        c += part[3 * k + 2];
+__global__ void __launch_bounds__(kStatBlocks) k_stats_fin(const double *__restrict__ part, int nb, int pass,
+                                                           double *__restrict__ stats) {
+    // the block sums added by a fixed tree (nb <= kStatBlocks, a power of two)
+    __shared__ double sh[3][kStatBlocks];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sh[c][t] = t < nb ? part[3 * t + c] : 0.0;
+    __syncthreads();
+    for (int off = kStatBlocks / 2; off > 0; off >>= 1) {
+        if (t < off) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[c][t] += sh[c][t + off];
+        }
+        __syncthreads();
     }
+    if (t != 0) return;
+    const double a = sh[0][0], b = sh[1][0], c = sh[2][0];
     if (pass == 0) {
         stats[0] = b / a;
         stats[1] = c / a;
@@ -477,7 +486,6 @@ __global__ void k_stats_fin(const double *__restrict__ part, int nb, int pass, d
         stats[2] = a / stats[3];
     }
 }
-
 }  // namespace
 
 // bytes for either sweep (the size query does not know which one a call forces)
@@ -521,7 +529,7 @@ nnqs_status energy_stats(const double *eloc, const uint64_t *w, int64_t n, doubl
     const double2 *e = reinterpret_cast<const double2 *>(eloc);
     for (int pass = 0; pass < 2; ++pass) {
         NNQS_LAUNCH("k_stats", s, k_stats_part<<<kStatBlocks, kStatPartThreads, 0, s>>>(e, w, n, pass, stats, part));
-        NNQS_LAUNCH("k_stats", s, k_stats_fin<<<1, 32, 0, s>>>(part, kStatBlocks, pass, stats));
+        NNQS_LAUNCH("k_stats", s, k_stats_fin<<<1, kStatBlocks, 0, s>>>(part, kStatBlocks, pass, stats));
     }
     return NNQS_OK;
 }
