@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(256) k_ln_bwd_sums(const float *__restrict__ x
                                                      const float *__restrict__ dy, float *__restrict__ acc,
                                                      int64_t rows, float *__restrict__ partial, unsigned *counter,
                                                      float *__restrict__ out_g, float *__restrict__ out_b,
-                                                     float *__restrict__ out_h) {
+                                                     float *__restrict__ out_h, bool acc_zero) {
     constexpr int RPW = 32 / LPR, d = 4 * LPR, NW = 8;
     __shared__ float sh[NW * 3 * d > kColThreads * 4 ? NW * 3 * d : kColThreads * 4];
     __shared__ bool last;
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(256) k_ln_bwd_sums(const float *__restrict__ x
             const bool ok = row < rows;
             xv[u] = ok ? __ldg(reinterpret_cast<const float4 *>(x + row * d) + l) : z4;
             dv[u] = ok ? __ldg(reinterpret_cast<const float4 *>(dy + row * d) + l) : z4;
-            av[u] = ok ? reinterpret_cast<const float4 *>(acc + row * d)[l] : z4;
+            av[u] = ok && !acc_zero ? reinterpret_cast<const float4 *>(acc + row * d)[l] : z4;
             mu[u] = ok ? mean[row] : 0.f;
             rs[u] = ok ? rstd[row] : 0.f;
         }
@@ -1000,7 +1000,7 @@ nnqs_status colsum(cudaStream_t s, int mode, const R *A, const R *X, const R *me
 // pass for FP32 rows of d = 4 LPR, else the separate kernels
 template <class R>
 nnqs_status ln_bwd_sums(cudaStream_t s, const R *x, const R *mean, const R *rstd, const R *g, const R *dy, R *acc,
-                        int64_t rows, int d, R *out_g, R *out_b, R *out_h, Scratch<R> scr) {
+                        int64_t rows, int d, R *out_g, R *out_b, R *out_h, Scratch<R> scr, bool acc_zero = false) {
     if (rows == 0) return NNQS_OK;
     if constexpr (sizeof(R) == 4) {
         if (ln_vec_ok<R>(d) && al16(x) && al16(g) && al16(dy) && al16(acc) && d >= 4) {
@@ -1008,7 +1008,7 @@ nnqs_status ln_bwd_sums(cudaStream_t s, const R *x, const R *mean, const R *rstd
             const int64_t per_block = 8 * (32 / lpr) * kLnRows;
             int64_t nblk = std::min<int64_t>((rows + per_block - 1) / per_block, 2 * sm_count());
             nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)(scr.elems / size_t(3 * d))));
-#define NNQS_LNS(LPR) NNQS_LAUNCH("k_ln_bwd", s, (k_ln_bwd_sums<LPR><<<(unsigned)nblk, 256, 0, s>>>(x, mean, rstd, g, dy, acc, rows, scr.buf, scr.ctr, out_g, out_b, out_h)))
+#define NNQS_LNS(LPR) NNQS_LAUNCH("k_ln_bwd", s, (k_ln_bwd_sums<LPR><<<(unsigned)nblk, 256, 0, s>>>(x, mean, rstd, g, dy, acc, rows, scr.buf, scr.ctr, out_g, out_b, out_h, acc_zero)))
             switch (lpr) {
                 case 1: NNQS_LNS(1); break;
                 case 2: NNQS_LNS(2); break;
@@ -1021,6 +1021,7 @@ nnqs_status ln_bwd_sums(cudaStream_t s, const R *x, const R *mean, const R *rstd
             return NNQS_OK;
         }
     }
+    if (acc_zero) NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(acc, rows * d, R(0)));
     NNQS_TRY(ln_bwd<R>(s, x, mean, rstd, g, dy, acc, rows, d));
     NNQS_TRY(colsum<R>(s, 1, dy, x, mean, rstd, rows, d, out_g, out_b, scr));
     if (out_h) NNQS_TRY(colsum<R>(s, 0, acc, nullptr, nullptr, nullptr, rows, d, out_h, nullptr, scr));
@@ -1885,42 +1886,51 @@ __device__ __forceinline__ void dec_store_granule(uint8_t *hi, uint8_t *lo, int 
     }
 }
 
-// LayerNorm of residual row r (shared, stride 65) into the A tile: the lane
-// sums of the 16-lane FP32 kernel combined in its butterfly order
-__device__ __forceinline__ void dec_layernorm_row(const float *sH, int r, const float *__restrict__ g,
-                                                  const float *__restrict__ b, uint8_t *aHi, uint8_t *aLo, bool split) {
-    float4 v[16];
+// LayerNorm of residual row r (shared, stride 65) into the A tile, the lane sums
+// of the 16-lane FP32 kernel combined in its tree order, over 4 lanes per row
+// (lanes 4 r' .. 4 r' + 3 of a warp, lq = lane & 3): lane lq holds the float4 pieces lq, lq + 4, lq + 8, lq + 12, so
+// the first two levels of the 16-piece tree (pieces k + 8, then k + 4) are its
+// own and the last two (k + 2, k + 1) are shuffles with lanes lq ^ 2 and lq ^ 1.
+// Every addition pairs the same two values as one lane walking the tree (IEEE
+// addition commutes), so the results are the same bits; each lane writes its
+// four pieces as half granules.
+__device__ __forceinline__ void dec_layernorm_row4(const float *sH, int r, int lq, const float *__restrict__ g,
+                                                   const float *__restrict__ b, uint8_t *aHi, uint8_t *aLo,
+                                                   bool split) {
+    float4 v[4];
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-        v[k] = make_float4(sH[r * dec::kHS + 4 * k], sH[r * dec::kHS + 4 * k + 1], sH[r * dec::kHS + 4 * k + 2],
+    for (int m = 0; m < 4; ++m) {
+        const int k = lq + 4 * m;
+        v[m] = make_float4(sH[r * dec::kHS + 4 * k], sH[r * dec::kHS + 4 * k + 1], sH[r * dec::kHS + 4 * k + 2],
                            sH[r * dec::kHS + 4 * k + 3]);
-    float a[16];
+    }
+    float s = (ln_part_sum(v[0]) + ln_part_sum(v[2])) + (ln_part_sum(v[1]) + ln_part_sum(v[3]));
+    s = s + __shfl_xor_sync(0xffffffffu, s, 2);
+    s = s + __shfl_xor_sync(0xffffffffu, s, 1);
+    const float mu = s / float(dec::kD);
+    float q = (ln_part_sq(v[0], mu) + ln_part_sq(v[2], mu)) + (ln_part_sq(v[1], mu) + ln_part_sq(v[3], mu));
+    q = q + __shfl_xor_sync(0xffffffffu, q, 2);
+    q = q + __shfl_xor_sync(0xffffffffu, q, 1);
+    const float rs = ln_rstd(q, dec::kD);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) a[k] = ln_part_sum(v[k]);
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < o; ++k) a[k] = a[k] + a[k + o];
-    const float mu = a[0] / float(dec::kD);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) a[k] = ln_part_sq(v[k], mu);
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < o; ++k) a[k] = a[k] + a[k + o];
-    const float rs = ln_rstd(a[0], dec::kD);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float4 y0 = ln_apply(v[2 * c], mu, rs, __ldg(reinterpret_cast<const float4 *>(g) + 2 * c),
-                                   __ldg(reinterpret_cast<const float4 *>(b) + 2 * c));
-        const float4 y1 = ln_apply(v[2 * c + 1], mu, rs, __ldg(reinterpret_cast<const float4 *>(g) + 2 * c + 1),
-                                   __ldg(reinterpret_cast<const float4 *>(b) + 2 * c + 1));
-        const float x[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-        dec_store_granule(aHi, aLo, r, c, x, split);
+    for (int m = 0; m < 4; ++m) {
+        const int k = lq + 4 * m, c = k >> 1;
+        const float4 y = ln_apply(v[m], mu, rs, __ldg(reinterpret_cast<const float4 *>(g) + k),
+                                  __ldg(reinterpret_cast<const float4 *>(b) + k));
+        const int off = r * 128 + ((c ^ (r & 7)) << 4) + 8 * (k & 1);
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(y.x, y.y), h1 = __floats2bfloat162_rn(y.z, y.w);
+        *reinterpret_cast<uint2 *>(aHi + off) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1));
+        if (split) {
+            const __nv_bfloat162 l0 = __floats2bfloat162_rn(y.x - __low2float(h0), y.y - __high2float(h0));
+            const __nv_bfloat162 l1 = __floats2bfloat162_rn(y.z - __low2float(h1), y.w - __high2float(h1));
+            *reinterpret_cast<uint2 *>(aLo + off) =
+                make_uint2(*reinterpret_cast<const uint32_t *>(&l0), *reinterpret_cast<const uint32_t *>(&l1));
+        }
     }
 }
 
-// dec_layernorm_row's arithmetic with FP32 output values (the final LayerNorm)
+// the same LayerNorm by one lane per row, FP32 output values (the final LayerNorm)
 __device__ __forceinline__ void dec_layernorm_row_f32(const float *sH, int r, const float *__restrict__ g,
                                                       const float *__restrict__ b, float (&y)[dec::kD]) {
     float4 v[16];
@@ -2168,7 +2178,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
 
     for (int l = 0; l < g.L && ok; ++l) {
         // ---- LayerNorm 1 -> qkv
-        if (tid < kRows) dec_layernorm_row(sH, tid, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
+        dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
         wait_weights();  // Wqkv of layer l
         sync_async();
         if (!ok) break;
@@ -2275,7 +2285,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         // together (TMEM columns of the finished q|k|v and free columns), then
         // per chunk: GELU of U_c into registers while MMA2(c - 1) runs, G_c
         // into shared memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
-        if (tid < kRows) dec_layernorm_row(sH, tid, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
+        dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
         sync_async();
         if (tid == 0) {
 #pragma unroll
@@ -3145,10 +3155,10 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
     }
     // final LayerNorm
     const R *hlast = A.hbuf + (int64_t)L * rows * d;
-    NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(rows * d, 256), 256, 0, s>>>(G.dh, rows * d, R(0)));
-    // (the column sums of the new dh are the last layer's FFN-out bias gradient)
+    // dh = the final LayerNorm's input gradient (written, not added); the
+    // column sums of the new dh are the last layer's FFN-out bias gradient
     NNQS_TRY(ln_bwd_sums<R>(s, hlast, A.meanf, A.rstdf, V.lnf_g, G.dtmp, G.dh, rows, d, gacc + Lo.lnf_g,
-                            gacc + Lo.lnf_b, gacc + Lo.layer[L - 1].b2, scr));
+                            gacc + Lo.lnf_b, gacc + Lo.layer[L - 1].b2, scr, true));
     const bool fused_ffn = sizeof(R) == 4 && G.part && fused_bwd_applies(M, tcw);
     const bool fused_attn = fused_ffn;
     for (int l = L - 1; l >= 0; --l) {
