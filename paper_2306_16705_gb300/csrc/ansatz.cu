@@ -1712,7 +1712,8 @@ constexpr int kMaxDepth = 64;
 // cached sampler reproduces the recomputed conditionals bit for bit).
 template <class R, int DH>
 __device__ __forceinline__ void attn_decode_row(const R *__restrict__ pool, const int32_t *__restrict__ anc_row,
-                                                int64_t self, int t, int L, int l, int d, int hh, R (&o)[DH]) {
+                                                int64_t anc_stride, int64_t self, int t, int L, int l, int d, int hh,
+                                                R (&o)[DH]) {
     const int64_t row = 3 * (int64_t)d;
     const R scale = score_scale<R, DH>();
     R qv[DH], acc[DH];
@@ -1724,7 +1725,7 @@ __device__ __forceinline__ void attn_decode_row(const R *__restrict__ pool, cons
     }
     R m = neg_inf<R>(), lsum = 0;
     for (int j = 0; j <= t; ++j) {
-        const int64_t node = j < t ? (int64_t)anc_row[j] : self;
+        const int64_t node = j < t ? (int64_t)anc_row[j * anc_stride] : self;
         const R *base = pool + (node * L + l) * row;
         const R *kj = base + d + hh * DH;
         const R *vj = base + 2 * d + hh * DH;
@@ -1744,17 +1745,17 @@ __device__ __forceinline__ void attn_decode_row(const R *__restrict__ pool, cons
     for (int c = 0; c < DH; ++c) o[c] = acc[c] * inv;
 }
 
-// anc: [n][T] ancestor table of the current level (row i lists the nodes of
-// prefix i at depths 0..t-1); prefix i is node g0 + i
+// anc: depth-major ancestor table of the current level (anc[j * anc_stride +
+// i] is the node of prefix i at depth j < t); prefix i is node g0 + i
 template <class R, int DH>
-__global__ void k_attn_decode(const R *__restrict__ pool, const int32_t *__restrict__ anc, int Tm, int64_t g0,
-                              int64_t n, int t, int L, int l, int H, int d, R *__restrict__ o) {
+__global__ void k_attn_decode(const R *__restrict__ pool, const int32_t *__restrict__ anc, int64_t anc_stride,
+                              int64_t g0, int64_t n, int t, int L, int l, int H, int d, R *__restrict__ o) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * H) return;
     const int hh = (int)(idx % H);
     const int64_t i = idx / H;
     R ov[DH];
-    attn_decode_row<R, DH>(pool, anc + i * Tm, g0 + i, t, L, l, d, hh, ov);
+    attn_decode_row<R, DH>(pool, anc + i, anc_stride, g0 + i, t, L, l, d, hh, ov);
 #pragma unroll
     for (int c = 0; c < DH; ++c) o[i * d + hh * DH + c] = ov[c];
 }
@@ -1838,7 +1839,8 @@ struct DecodeArgs {
     float *pool;  // [node][L][192] q|k|v
     int L, Tm, t;
     int64_t g0;
-    const int32_t *anc;  // [n][Tm] ancestor nodes at depths 0..t-1
+    const int32_t *anc;  // depth-major ancestor nodes: anc[j * anc_stride + i], depths j < t
+    int64_t anc_stride;
     // per layer: LayerNorm, bias vectors and the swizzled shared-memory images
     // of the weights (high part, then the low part): qkv [192 rows],
     // out-projection [64], FFN in [256], FFN out [64 rows, 4 K blocks]
@@ -1973,8 +1975,8 @@ __device__ __forceinline__ void dec_layernorm_row_f32(const float *sH, int r, co
 // instead and give zeros.
 template <int DH, int NR>
 __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ pool, const int32_t *__restrict__ anc,
-                                                   int Tm, int64_t g0, int64_t r0, int64_t safe, int64_t n, int t,
-                                                   int L, int l, int hh, float (&o)[NR][DH]) {
+                                                   int64_t anc_stride, int64_t g0, int64_t r0, int64_t safe, int64_t n,
+                                                   int t, int L, int l, int hh, float (&o)[NR][DH]) {
     constexpr int d = dec::kD;
     const int64_t row = 3 * (int64_t)d;
     const float scale = score_scale<float, DH>();
@@ -2010,7 +2012,7 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
             }
         }
     };
-    auto node_at = [&](int j, int k) -> int64_t { return j < t ? (int64_t)anc[rr[k] * Tm + j] : g0 + rr[k]; };
+    auto node_at = [&](int j, int k) -> int64_t { return j < t ? (int64_t)anc[j * anc_stride + rr[k]] : g0 + rr[k]; };
     float kk[NR][DH], vv[NR][DH];
     int64_t node[NR];
 #pragma unroll
@@ -2245,7 +2247,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
             const int hh = tid % H;
             const int r0 = (tid / H) * NR;
             float o[NR][DH];
-            dec_attention_rows<DH, NR>(g.pool, g.anc, g.Tm, g0, m0 + r0, m0, n_cta, g.t, g.L, l, hh, o);
+            dec_attention_rows<DH, NR>(g.pool, g.anc, g.anc_stride, g0, m0 + r0, m0, n_cta, g.t, g.L, l, hh, o);
 #pragma unroll
             for (int k = 0; k < NR; ++k)
 #pragma unroll
@@ -3522,24 +3524,24 @@ size_t cond_workspace_impl(const nnqs_model *M, int64_t max_prefixes, bool tenso
 }  // namespace
 
 template <int DH_, class R>
-nnqs_status launch_attn_decode(cudaStream_t s, const R *pool, const int32_t *anc, int Tm, int64_t g0, int64_t n, int t,
+nnqs_status launch_attn_decode(cudaStream_t s, const R *pool, const int32_t *anc, int64_t anc_stride, int64_t g0, int64_t n, int t,
                                int L, int l, int H, int d, R *o) {
     NNQS_LAUNCH("k_attn_decode", s,
-                k_attn_decode<R, DH_><<<grid_for(n * H, 128), 128, 0, s>>>(pool, anc, Tm, g0, n, t, L, l, H, d, o));
+                k_attn_decode<R, DH_><<<grid_for(n * H, 128), 128, 0, s>>>(pool, anc, anc_stride, g0, n, t, L, l, H, d, o));
     return NNQS_OK;
 }
 
 template <class R>
-nnqs_status attn_decode(cudaStream_t s, int dh, const R *pool, const int32_t *anc, int Tm, int64_t g0, int64_t n, int t,
+nnqs_status attn_decode(cudaStream_t s, int dh, const R *pool, const int32_t *anc, int64_t anc_stride, int64_t g0, int64_t n, int t,
                         int L, int l, int H, int d, R *o) {
     switch (dh) {
-        case 1: return launch_attn_decode<1>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
-        case 2: return launch_attn_decode<2>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
-        case 4: return launch_attn_decode<4>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
-        case 8: return launch_attn_decode<8>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
-        case 16: return launch_attn_decode<16>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
-        case 32: return launch_attn_decode<32>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
-        case 64: return launch_attn_decode<64>(s, pool, anc, Tm, g0, n, t, L, l, H, d, o);
+        case 1: return launch_attn_decode<1>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
+        case 2: return launch_attn_decode<2>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
+        case 4: return launch_attn_decode<4>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
+        case 8: return launch_attn_decode<8>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
+        case 16: return launch_attn_decode<16>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
+        case 32: return launch_attn_decode<32>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
+        case 64: return launch_attn_decode<64>(s, pool, anc, anc_stride, g0, n, t, L, l, H, d, o);
         default: return set_error(NNQS_E_UNSUPPORTED, "head dimension must be a power of two <= 64");
     }
 }
@@ -3570,12 +3572,13 @@ nnqs_status launch_decode_step(const DecodeArgs &g, cudaStream_t s) {
     return NNQS_OK;
 }
 
-// the four GEMMs of every layer of one fused decoding step over n prefixes
-// (method FLOPs) and its bytes: per layer the new k | v rows, the weight
-// images once
-void note_decode_work(int64_t n, bool split, int L) {
+// the four GEMMs of every layer of one fused decoding step over n prefixes at
+// depth t (method FLOPs) and its bytes: per layer and prefix the keys and
+// values of its t ancestors and itself read, its q | k | v row written, and
+// the weight images once
+void note_decode_work(int64_t n, bool split, int L, int t) {
     note_work("k_decode_step", L * 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
-              L * (4.0 * double(n) * 2 * dec::kD +
+              L * (double(n) * 4.0 * (2.0 * dec::kD * (t + 1) + dec::kQKV) +
                    2.0 * (split ? 2.0 : 1.0) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF)));
 }
 
@@ -3583,8 +3586,8 @@ void note_decode_work(int64_t n, bool split, int L) {
 // g0 ...): the embeddings of their last tokens in, the conditionals of the
 // next token out (k_decode_step)
 nnqs_status decode_step_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
-                              int64_t n, float *pool, const int32_t *anc, int t, int64_t g0, double *cond,
-                              DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
+                              int64_t n, float *pool, const int32_t *anc, int64_t anc_stride, int t, int64_t g0,
+                              double *cond, DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
                               const int64_t *g0_dev = nullptr) {
     if (n == 0) return NNQS_OK;
     DecodeArgs g{};
@@ -3602,6 +3605,7 @@ nnqs_status decode_step_fused(const nnqs_model *M, const Views<float> &V, const 
     g.t = t;
     g.g0 = g0;
     g.anc = anc;
+    g.anc_stride = anc_stride;
     const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(w.tiles);
     for (int l = 0; l < M->L; ++l) {
         const auto &Lw = V.layer[l];
@@ -3632,21 +3636,22 @@ nnqs_status decode_step_fused(const nnqs_model *M, const Views<float> &V, const 
     g.st = st;
     // work per launch (for the profile); with the level size on the device
     // the walk notes it once the size is known (n is the capacity here)
-    if (!n_dev) note_decode_work(n, w.split, M->L);
+    if (!n_dev) note_decode_work(n, w.split, M->L, t);
     if (w.split) return M->dh == 8 ? launch_decode_step<true, 8>(g, s) : launch_decode_step<true, 16>(g, s);
     return M->dh == 8 ? launch_decode_step<false, 8>(g, s) : launch_decode_step<false, 16>(g, s);
 }
 
 template <class R>
 nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, int t, int64_t g0,
-                         R *pool, const int32_t *anc, Acts<R> &A, double *cond, DevStatus *st,
+                         R *pool, const int32_t *anc, int64_t anc_stride, Acts<R> &A, double *cond, DevStatus *st,
                          const TcWeights *tcw, cudaStream_t s) {
     const int T = M->T, d = M->d, L = M->L, F = M->F, H = M->H, W = M->W;
     const int64_t rows = C;
     R *h = A.hbuf;
     if constexpr (sizeof(R) == 4) {
         // fused: embedding in the first layer, conditionals in the last
-        if (tcw && decode_fused_ok(M, *tcw)) return decode_step_fused(M, V, *tcw, x, C, pool, anc, t, g0, cond, st, s);
+        if (tcw && decode_fused_ok(M, *tcw))
+            return decode_step_fused(M, V, *tcw, x, C, pool, anc, anc_stride, t, g0, cond, st, s);
     }
     NNQS_LAUNCH("k_embed", s, k_embed_decode<R><<<grid_for(rows * d, 256), 256, 0, s>>>(x, W, C, t, T, d, V.tok, V.pos, h));
     for (int l = 0; l < L; ++l) {
@@ -3660,7 +3665,7 @@ nnqs_status decode_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t 
             NNQS_TRY(gemm<R>(s, EPI_STORE, A.a, d, 1, Lw.wqkv, d, 1, qkv, (int64_t)L * 3 * d, nullptr, Lw.bqkv, nullptr,
                              rows, 3 * d, d, A.scr));
         }
-        NNQS_TRY(attn_decode<R>(s, M->dh, pool, anc, T, g0, C, t, L, l, H, d, A.o));
+        NNQS_TRY(attn_decode<R>(s, M->dh, pool, anc, anc_stride, g0, C, t, L, l, H, d, A.o));
         if (tcw) {
             NNQS_TRY(tc_linear_fwd<R>(s, *tcw, tc_slot(l, 1), EPI_RESID, A.o, rows, d, Lw.bo, h, nullptr, h));
         } else {
@@ -3691,6 +3696,7 @@ struct CondCtx {
     Acts<double> Ad;
     void *pool = nullptr;  // key/value cache [nodes][L][3d]
     int64_t pool_nodes = 0;
+    int64_t anc_stride = 0;  // rows of the depth-major ancestor tables (the prefix capacity)
 };
 
 size_t cond_workspace(const nnqs_model *M, int64_t max_prefixes, int prec, int64_t kv_nodes) {
@@ -3706,6 +3712,7 @@ nnqs_status cond_create(const nnqs_model *M, const float *params, int prec, int6
     c->prec = prec;
     c->tensor = tc_mode(prec) != 0;
     c->pool_nodes = kv_nodes;
+    c->anc_stride = max_prefixes;
     if (prec == NNQS_FP64) {
         double *pr = ws.take<double>(M->lay.total);
         c->pool = ws.take<double>(size_t(kv_nodes) * M->L * 3 * M->d);
@@ -3741,11 +3748,12 @@ nnqs_status cond_step_cached(const nnqs_model *M, CondCtx *ctx, const uint64_t *
         if (ctx->prec == NNQS_FP64) {
             const Views<double> V = make_views<double>(M, static_cast<double *>(ctx->params));
             NNQS_TRY(decode_chunk<double>(M, V, prefixes + c0 * M->W, cn, t, g0 + c0, static_cast<double *>(ctx->pool),
-                                          anc + c0 * M->T, ctx->Ad, cond + c0 * 4, st, nullptr, s));
+                                          anc + c0, ctx->anc_stride, ctx->Ad, cond + c0 * 4, st, nullptr, s));
         } else {
             const Views<float> V = make_views<float>(M, static_cast<float *>(ctx->params));
             NNQS_TRY(decode_chunk<float>(M, V, prefixes + c0 * M->W, cn, t, g0 + c0, static_cast<float *>(ctx->pool),
-                                         anc + c0 * M->T, ctx->Af, cond + c0 * 4, st, ctx->tensor ? &ctx->tcw : nullptr, s));
+                                         anc + c0, ctx->anc_stride, ctx->Af, cond + c0 * 4, st,
+                                         ctx->tensor ? &ctx->tcw : nullptr, s));
         }
     }
     return NNQS_OK;
@@ -3771,10 +3779,10 @@ nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64
         int64_t n = 0;
         NNQS_CUDA_TRY(cudaMemcpyAsync(&n, n_dev, 8, cudaMemcpyDeviceToHost, s));
         NNQS_CUDA_TRY(cudaStreamSynchronize(s));
-        note_decode_work(n, ctx->tcw.split, M->L);
+        note_decode_work(n, ctx->tcw.split, M->L, t);
     }
-    NNQS_TRY(decode_step_fused(M, V, ctx->tcw, prefixes, cap, static_cast<float *>(ctx->pool), anc, t, 0, cond, st, s,
-                               n_dev, g0_dev));
+    NNQS_TRY(decode_step_fused(M, V, ctx->tcw, prefixes, cap, static_cast<float *>(ctx->pool), anc, ctx->anc_stride, t,
+                               0, cond, st, s, n_dev, g0_dev));
     return NNQS_OK;
 }
 

@@ -318,8 +318,9 @@ __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ i
 
 // children of prefix i in token order at slots off[i] ...
 // children of prefix i go to rows off[i].. of the next level; with the
-// key/value cache each child's ancestor row is its parent's row plus the
-// parent's own node g_cur + i at depth `step`
+// key/value cache each child's ancestors are its parent's plus the parent's
+// own node g_cur + i at depth `step` (the tables are depth-major, [T][cap]:
+// a warp's lanes write consecutive entries of one depth)
 __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
                        const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
                        uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, const int32_t *__restrict__ anc,
@@ -345,8 +346,8 @@ __global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__rest
         if (v & 2) npref[j * W + ((2 * p + 1) >> 6)] |= 1ull << ((2 * p + 1) & 63);
         nw[j] = c;
         if (nanc) {
-            for (int lev = 0; lev < step; ++lev) nanc[j * T + lev] = anc[i * T + lev];
-            nanc[j * T + step] = (int32_t)(g_cur + i);
+            for (int lev = 0; lev < step; ++lev) nanc[lev * cap + j] = anc[lev * cap + i];
+            nanc[step * cap + j] = (int32_t)(g_cur + i);
         }
         ++j;
     }
@@ -383,7 +384,7 @@ struct SLayout {
     double *cond;
     int32_t *nchild;
     int64_t *off, *bsum, *total;
-    int32_t *anc[2];  // key/value cache: ancestor tables of the current and next level
+    int32_t *anc[2];  // key/value cache: ancestor tables [T][cap] of the current and next level
     int64_t *cnt;     // device-side counts: level sizes [2], first node of the current level
     uint64_t *args;   // device copies of n_samples and seed (read by the device-count walk)
     char *region;
