@@ -381,8 +381,15 @@ nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, const float
  * every prefix against a key/value cache of the prefix tree (each node keeps
  * its own rows; memory T * max_unique * n_layers * 3 d values);
  * NNQS_SAMPLE_RECOMPUTE re-runs the whole prefix at every step instead (no
- * cache).  Both give bit-identical draws. */
-enum { NNQS_SAMPLE_RECOMPUTE = 1 };
+ * cache).  Both give bit-identical draws.
+ * NNQS_SAMPLE_KEEP (with the cache; BF16 or split-BF16 arithmetic, d_model
+ * 64, max_unique <= 65536, else NNQS_E_UNSUPPORTED) also keeps in the
+ * workspace, for every tree node the decode visits, its residual row at each
+ * layer's input and after each layer's attention and its final residual
+ * (2 L + 1 rows of d_model floats per node, T max_unique + 1 nodes), and the
+ * last level's ancestor table: what nnqs_energy_grad_sampled reads instead of
+ * running the forward again.  The draws are the same with or without it. */
+enum { NNQS_SAMPLE_RECOMPUTE = 1, NNQS_SAMPLE_KEEP = 2 };
 
 size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec, int flags);
 
@@ -402,6 +409,31 @@ nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uint64_t n_sam
                         uint64_t seed, int prec, int flags, int64_t max_unique,
                         uint64_t *samples_out, uint64_t *weights_out, int64_t *n_unique_out,
                         void *workspace, size_t workspace_bytes, nnqs_stream stream);
+
+/* nnqs_energy_grad with the forward's quantities taken from the tree the
+ * last nnqs_sample call with NNQS_SAMPLE_KEEP left in sample_workspace
+ * (sample_workspace_bytes, max_unique and prec as in that call), instead of
+ * running the forward again: each token row's layer inputs and mid residuals
+ * are its tree node's, the final LayerNorm, head and log|psi| follow from
+ * them, the phase MLP and the local energy run as in nnqs_energy_grad, and
+ * the reverse mode is the fused one (Sec. 2.1 gradient estimator).
+ * samples / weights / n_u: that call's outputs, unmodified and in its order
+ * (a row that differs records NNQS_E_INVAL in the workspace status).  Same
+ * outputs, layout and errors as nnqs_energy_grad; NNQS_E_UNSUPPORTED outside
+ * BF16 / split-BF16 arithmetic, d_model 64, FFN width 256, head dimension 8
+ * or 16, T <= 64 (the fused reverse mode's reach); NNQS_E_WORKSPACE when
+ * sample_workspace is smaller than an NNQS_SAMPLE_KEEP call needs.  The
+ * sampler's workspace is only read. */
+size_t nnqs_energy_grad_sampled_workspace_size(const nnqs_ham *H, const nnqs_model *M, int64_t n_u, int prec);
+/* 1 if nnqs_sample with NNQS_SAMPLE_KEEP and nnqs_energy_grad_sampled apply
+ * to this model, precision and max_unique, else 0 (host only). */
+int nnqs_energy_grad_sampled_supported(const nnqs_model *M, int prec, int64_t max_unique);
+nnqs_status nnqs_energy_grad_sampled(const nnqs_ham *H, const nnqs_model *M, const float *params,
+                                     const void *sample_workspace, size_t sample_workspace_bytes,
+                                     int64_t max_unique, const uint64_t *samples, const uint64_t *weights,
+                                     int64_t n_u, int prec, double *stats, double *eloc_out, double *grad_f64,
+                                     float *grad_f32, void *workspace, size_t workspace_bytes,
+                                     nnqs_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* Optimiser step.                                                       */

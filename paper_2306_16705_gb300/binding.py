@@ -102,6 +102,15 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                         ctypes.c_void_p]),
+    "nnqs_energy_grad_sampled_supported": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
+    "nnqs_energy_grad_sampled_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_void_p,
+                                                                  ctypes.c_int64, ctypes.c_int]),
+    "nnqs_energy_grad_sampled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                ctypes.c_void_p]),
     "nnqs_sample_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                                      ctypes.c_int]),
     "nnqs_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
@@ -419,11 +428,38 @@ def energy_grad(ham: Hamiltonian, model: Model, params, samples, weights, prec=F
 
 
 SAMPLE_RECOMPUTE = 1
+SAMPLE_KEEP = 2
+
+
+def energy_grad_sampled(ham: Hamiltonian, model: Model, params, sample_ws, max_unique: int, samples, weights,
+                        prec=BF16X3, check=True, ws=None, want_eloc=True, grad_out=None):
+    """nnqs_energy_grad_sampled: energy_grad's outputs, the forward's
+    quantities taken from the tree of the last sample(..., flags=SAMPLE_KEEP)
+    call with workspace ``sample_ws`` (whose samples and weights these are)."""
+    n = samples.shape[0]
+    stats = torch.empty(4, dtype=torch.float64, device=samples.device)
+    el = torch.empty((n, 2), dtype=torch.float64, device=samples.device) if want_eloc else None
+    grad = grad_out if grad_out is not None else torch.empty(model.n_params, dtype=torch.float32,
+                                                             device=samples.device)
+    g64 = grad if grad.dtype == torch.float64 else None
+    g32 = grad if grad.dtype == torch.float32 else None
+    nb = lib().nnqs_energy_grad_sampled_workspace_size(ham.handle, model.handle, n, prec)
+    if ws is None or ws.numel() < nb:
+        ws = workspace(nb, samples.device)
+    _check(lib().nnqs_energy_grad_sampled(ham.handle, model.handle, _ptr(params), _ptr(sample_ws),
+                                          sample_ws.numel(), int(max_unique), _ptr(samples), _ptr(weights), n,
+                                          prec, _ptr(stats), _ptr(el), _ptr(g64), _ptr(g32), _ptr(ws),
+                                          ws.numel(), _stream()))
+    if check:
+        workspace_status(ws)
+    return stats, el, grad
 
 
 def sample(model: Model, params, n_samples: int, seed: int, max_unique: int, prec=FP64,
            check=True, ws=None, flags=0):
-    """nnqs_sample: (samples [n_u, W] uint64 as int64 tensor, weights [n_u])."""
+    """nnqs_sample: (samples [n_u, W] uint64 as int64 tensor, weights [n_u]).
+    With SAMPLE_KEEP in ``flags`` the workspace ``ws`` (allocated by the
+    caller for that flag) then holds what energy_grad_sampled reads."""
     W = model.n_words
     dev = params.device
     s = torch.empty((max_unique, W), dtype=torch.int64, device=dev)

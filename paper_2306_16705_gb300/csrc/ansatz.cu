@@ -1861,6 +1861,11 @@ struct DecodeArgs {
     // sized for the capacity and CTAs past n return at once
     const int64_t *n_dev, *g0_dev;
     int n_sms;
+    // optional (both null or both set): per tree node the residual row at
+    // each layer's input and after its attention, act[node][L][2][64], and the
+    // final residual fin[node][64] (what the reverse mode of the energy
+    // gradient reads, nnqs_energy_grad_sampled)
+    float *act, *fin;
 };
 
 // one bulk asynchronous copy global -> shared, completing `bytes` on mbar
@@ -2074,6 +2079,20 @@ __device__ __forceinline__ void dec_mma(uint32_t tmem, uint32_t aHi, uint32_t aL
     }
 }
 
+// the CTA's residual rows (shared, stride 65) to rows of a per-node pool:
+// thread (row tid / 4, quarter tid % 4) copies 16 floats of a valid row
+__device__ __forceinline__ void dec_store_rows(const float *sH, float *dst, int64_t node0, int64_t rows,
+                                               int64_t node_stride) {
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+    if (r >= rows) return;
+    float *o = dst + (node0 + r) * node_stride + 16 * q;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        reinterpret_cast<float4 *>(o)[k] =
+            make_float4(sH[r * dec::kHS + 16 * q + 4 * k], sH[r * dec::kHS + 16 * q + 4 * k + 1],
+                        sH[r * dec::kHS + 16 * q + 4 * k + 2], sH[r * dec::kHS + 16 * q + 4 * k + 3]);
+}
+
 template <bool SPLIT, int DH>
 __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_constant__ DecodeArgs g) {
     using namespace dec;
@@ -2178,7 +2197,9 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
     const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
     const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
 
+    const int64_t act_stride = 2 * (int64_t)g.L * kD;  // floats per node of g.act
     for (int l = 0; l < g.L && ok; ++l) {
+        if (g.act) dec_store_rows(sH, g.act + 2 * l * kD, g0 + m0, n_cta - m0, act_stride);
         // ---- LayerNorm 1 -> qkv
         dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
         wait_weights();  // Wqkv of layer l
@@ -2283,6 +2304,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
             }
         }
         __syncthreads();
+        if (g.act) dec_store_rows(sH, g.act + (2 * l + 1) * kD, g0 + m0, n_cta - m0, act_stride);
         // ---- LayerNorm 2 -> FFN: the four MMA1(c) = LN2 W1_c^T are issued
         // together (TMEM columns of the finished q|k|v and free columns), then
         // per chunk: GELU of U_c into registers while MMA2(c - 1) runs, G_c
@@ -2352,6 +2374,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         }
         __syncthreads();
     }
+    if (ok && g.fin) dec_store_rows(sH, g.fin, g0 + m0, n_cta - m0, kD);
     // ---- final LayerNorm (k_ln_fwd_v's sums), head logits (head_logits'
     // sum) and the masked conditionals of the next token
     if (ok && tid < kRows && m0 + tid < n_cta) {
@@ -3588,7 +3611,7 @@ void note_decode_work(int64_t n, bool split, int L, int t) {
 nnqs_status decode_step_fused(const nnqs_model *M, const Views<float> &V, const TcWeights &w, const uint64_t *x,
                               int64_t n, float *pool, const int32_t *anc, int64_t anc_stride, int t, int64_t g0,
                               double *cond, DevStatus *st, cudaStream_t s, const int64_t *n_dev = nullptr,
-                              const int64_t *g0_dev = nullptr) {
+                              const int64_t *g0_dev = nullptr, float *act = nullptr, float *fin = nullptr) {
     if (n == 0) return NNQS_OK;
     DecodeArgs g{};
     g.n = n;
@@ -3634,6 +3657,8 @@ nnqs_status decode_step_fused(const nnqs_model *M, const Views<float> &V, const 
     g.hb = V.hb;
     g.cond = cond;
     g.st = st;
+    g.act = act;
+    g.fin = fin;
     // work per launch (for the profile); with the level size on the device
     // the walk notes it once the size is known (n is the capacity here)
     if (!n_dev) note_decode_work(n, w.split, M->L, t);
@@ -3770,7 +3795,7 @@ bool cond_cached_dev_ok(const nnqs_model *M, const CondCtx *ctx, int64_t cap) {
 
 nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, const int64_t *n_dev,
                                  const int64_t *g0_dev, int64_t cap, int t, const int32_t *anc, double *cond,
-                                 DevStatus *st, cudaStream_t s) {
+                                 DevStatus *st, cudaStream_t s, float *act, float *fin) {
     if (t >= kMaxDepth) return set_error(NNQS_E_UNSUPPORTED, "more than 64 tokens");
     if (!cond_cached_dev_ok(M, ctx, cap)) return set_error(NNQS_E_UNSUPPORTED, "no fused decode for this model");
     ctx->tcw.st = st;
@@ -3782,7 +3807,7 @@ nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64
         note_decode_work(n, ctx->tcw.split, M->L, t);
     }
     NNQS_TRY(decode_step_fused(M, V, ctx->tcw, prefixes, cap, static_cast<float *>(ctx->pool), anc, ctx->anc_stride, t,
-                               0, cond, st, s, n_dev, g0_dev));
+                               0, cond, st, s, n_dev, g0_dev, act, fin));
     return NNQS_OK;
 }
 
@@ -3825,12 +3850,210 @@ bool logpsi_single_chunk(const nnqs_model *M, int64_t n, int prec) {
     return chunk_for(M, std::max<int64_t>(n, 1), prec == NNQS_FP64 ? sizeof(double) : sizeof(float), true) >= n;
 }
 
+// ---------------------------------------------------------------- rows from the sampler's tree
+// The activations of every token row (sample i, position t) as the sampler's
+// decode step left them at row t's tree node anc[t * stride + i]
+// (NNQS_SAMPLE_KEEP): each layer's input and mid residual, the final residual;
+// then the final LayerNorm, the head and the masked log-softmax of the row's
+// token, as the forward's last part computes them.  4 lanes per row, 16
+// columns each; lane 0 of a row writes its conditionals, token and log
+// probability (lprow), k_rows_logpsi adds a sample's rows.
+constexpr int kRowsPerBlock = 64;
+__global__ void __launch_bounds__(4 * kRowsPerBlock) k_rows_from_nodes(
+    const uint64_t *__restrict__ x, int W, int64_t n, int T, int L, const float *__restrict__ act,
+    const float *__restrict__ fin, const int32_t *__restrict__ anc, int64_t stride, const float *__restrict__ lnf_g,
+    const float *__restrict__ lnf_b, const float *__restrict__ hw, const float *__restrict__ hb, int n_alpha,
+    int n_beta, float *__restrict__ hbuf, float *__restrict__ hmid, float *__restrict__ hf, float *__restrict__ meanf,
+    float *__restrict__ rstdf, float *__restrict__ pi, uint8_t *__restrict__ tok, float *__restrict__ lprow) {
+    constexpr int d = 64;
+    const int64_t rows = n * T;
+    const int64_t r = blockIdx.x * (int64_t)kRowsPerBlock + (threadIdx.x >> 2);
+    const int q = threadIdx.x & 3;
+    const bool valid = r < rows;
+    const int64_t i = valid ? r / T : 0;
+    const int t = valid ? (int)(r - i * T) : 0;
+    const int64_t node = valid ? (int64_t)anc[t * stride + i] : 0;
+    if (valid) {
+        for (int l = 0; l < L; ++l) {
+            const float4 *a0 = reinterpret_cast<const float4 *>(act + ((node * L + l) * 2) * d + 16 * q);
+            const float4 *a1 = reinterpret_cast<const float4 *>(act + ((node * L + l) * 2 + 1) * d + 16 * q);
+            float4 *h0 = reinterpret_cast<float4 *>(hbuf + ((int64_t)l * rows + r) * d + 16 * q);
+            float4 *h1 = reinterpret_cast<float4 *>(hmid + ((int64_t)l * rows + r) * d + 16 * q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                h0[k] = __ldg(a0 + k);
+                h1[k] = __ldg(a1 + k);
+            }
+        }
+    }
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 f = valid ? __ldg(reinterpret_cast<const float4 *>(fin + node * d + 16 * q) + k)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * k] = f.x;
+        v[4 * k + 1] = f.y;
+        v[4 * k + 2] = f.z;
+        v[4 * k + 3] = f.w;
+    }
+    if (valid) {
+        float4 *hl = reinterpret_cast<float4 *>(hbuf + ((int64_t)L * rows + r) * d + 16 * q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hl[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    // final LayerNorm (eps 1e-5) over the row's 64 columns
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s += v[c];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    const float mu = s / float(d);
+    float qv = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) qv += (v[c] - mu) * (v[c] - mu);
+    qv += __shfl_xor_sync(0xffffffffu, qv, 1);
+    qv += __shfl_xor_sync(0xffffffffu, qv, 2);
+    const float rs = 1.0f / sqrtf(qv / float(d) + 1e-5f);
+    float y[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y[c] = (v[c] - mu) * rs * __ldg(lnf_g + 16 * q + c) + __ldg(lnf_b + 16 * q + c);
+    if (valid) {
+        float4 *ho = reinterpret_cast<float4 *>(hf + r * d + 16 * q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ho[k] = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+        if (q == 0) {
+            meanf[r] = mu;
+            rstdf[r] = rs;
+        }
+    }
+    // head logits and the masked log-softmax of the row's token
+    float z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float a = 0.f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) a += y[c] * __ldg(hw + k * d + 16 * q + c);
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        z[k] = a + __ldg(hb + k);
+    }
+    if (!valid || q != 0) return;
+    const uint64_t *xi = x + i * W;
+    int ca = 0, cb = 0;  // electrons on the orbitals of tokens < t
+    for (int p2 = T - t; p2 < T; ++p2) {
+        ca += bit_of(xi, 2 * p2);
+        cb += bit_of(xi, 2 * p2 + 1);
+    }
+    const int rem = T - 1 - t;
+    bool okv[4];
+    float zmax = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int a = ca + (k & 1), b = cb + (k >> 1);
+        okv[k] = a <= n_alpha && b <= n_beta && a + rem >= n_alpha && b + rem >= n_beta;
+        if (okv[k] && z[k] > zmax) zmax = z[k];
+    }
+    float se = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (okv[k]) se += expf(z[k] - zmax);
+    const float lse = zmax + logf(se);
+    const int tk = token_at(xi, T, t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pi[r * 4 + k] = okv[k] ? expf(z[k] - lse) : 0.f;
+    tok[r] = (uint8_t)tk;
+    lprow[r] = okv[tk] ? z[tk] - lse : -INFINITY;
+}
+
+// log|psi| of each sample: half the sum of its rows' log probabilities (in
+// position order); an out-of-sector token gives -inf and NNQS_E_SECTOR
+__global__ void k_rows_logpsi(const float *__restrict__ lprow, int64_t n, int T, double2 *__restrict__ out,
+                              DevStatus *st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float sum = 0.f;
+    bool bad = false;
+    for (int t = 0; t < T; ++t) {
+        const float v = lprow[i * T + t];
+        if (v == -INFINITY)
+            bad = true;
+        else
+            sum += v;
+    }
+    out[i].x = bad ? -(double)INFINITY : 0.5 * (double)sum;
+    if (bad) record_status(st, NNQS_E_SECTOR, i);
+}
+
+// the samples must be the last level of the kept tree, row for row
+__global__ void k_rows_match(const uint64_t *__restrict__ x, const uint64_t *__restrict__ pref, int64_t n, int W,
+                             DevStatus *st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int w = 0; w < W; ++w)
+        if (x[i * W + w] != pref[i * W + w]) {
+            record_status(st, NNQS_E_INVAL, i);
+            return;
+        }
+}
+
+// forward quantities of the reverse mode from the sampler's tree, then
+// `between` (which fills `seed`), then the fused reverse mode
+nnqs_status rows_fwd_bwd_impl(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, double *lp_out,
+                              const double *seed, double *g64, float *g32, Arena &ws, DevStatus *st, int tcm,
+                              cudaStream_t s, const std::function<nnqs_status()> &between, const SampleKept &kept) {
+    using R = float;
+    if (!reverse_lite(M, tcm)) return set_error(NNQS_E_UNSUPPORTED, "no fused reverse mode for this model or precision");
+    R *pr = ws.take<R>(M->lay.total);
+    R *gacc = ws.take<R>(M->lay.total);
+    TcWeights tcw{};
+    tc_weights_take(M, ws, &tcw);
+    tcw.st = st;
+    tcw.split = tcm == 2;
+    tcw.fp8 = false;
+    const int64_t C = chunk_for(M, std::max<int64_t>(n, 1), sizeof(R), true);
+    if (C < n) return set_error(NNQS_E_INVAL, "forward/backward from the sampler's rows needs one chunk");
+    Acts<R> A;
+    take_acts<R>(M, C, true, ws, A, true);
+    Grads<R> G;
+    take_grads<R>(M, C, ws, G, true);
+    const int T = M->T;
+    const int64_t rows = n * T;
+    NNQS_CUDA_TRY(cudaMemsetAsync(A.scr.ctr, 0, sizeof(unsigned), s));
+    NNQS_LAUNCH("k_convert_params", s, k_convert_params<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(params, pr, M->lay.total));
+    NNQS_LAUNCH("k_fill", s, k_fill<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, R(0)));
+    NNQS_TRY(tc_weights_prepare(M, params, tcw, s));
+    const Views<R> V = make_views<R>(M, pr);
+    NNQS_LAUNCH("k_rows_match", s, k_rows_match<<<grid_for(n, 256), 256, 0, s>>>(x, kept.pref, n, M->W, st));
+    NNQS_LAUNCH("k_rows_from_nodes", s,
+                k_rows_from_nodes<<<(unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock), 4 * kRowsPerBlock, 0, s>>>(
+                    x, M->W, n, T, M->L, kept.act, kept.fin, kept.anc, kept.stride, V.lnf_g, V.lnf_b, V.hw, V.hb,
+                    M->cfg.n_alpha, M->cfg.n_beta, A.hbuf, A.hmid, A.hf, A.meanf, A.rstdf, A.pi, A.tok, G.dtmp));
+    double2 *out = reinterpret_cast<double2 *>(lp_out);
+    NNQS_LAUNCH("k_rows_logpsi", s, k_rows_logpsi<<<grid_for(n, 256), 256, 0, s>>>(G.dtmp, n, T, out, st));
+    NNQS_TRY(phase_mlp<R>(M, V, x, n, A, out, &tcw, s));
+    NNQS_TRY(between());
+    NNQS_TRY(backward_chunk<R>(M, V, x, n, A, G, reinterpret_cast<const double2 *>(seed), gacc, &tcw, s));
+    NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
+    return NNQS_OK;
+}
+
 nnqs_status logpsi_forward_backward(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n, int prec,
                                     double *lp_out, const double *seed, double *g64, float *g32, Arena &ws,
                                     DevStatus *st, cudaStream_t s, const std::function<nnqs_status()> &between) {
     if (prec == NNQS_FP64)
         return fwd_bwd_impl<double>(M, params, x, n, lp_out, seed, g64, g32, ws, st, 0, s, between);
     return fwd_bwd_impl<float>(M, params, x, n, lp_out, seed, g64, g32, ws, st, tc_mode(prec), s, between);
+}
+
+bool reverse_lite_ok(const nnqs_model *M, int tcm) { return reverse_lite(M, tcm); }
+
+nnqs_status logpsi_forward_backward_rows(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n,
+                                         int prec, double *lp_out, const double *seed, double *g64, float *g32,
+                                         Arena &ws, DevStatus *st, cudaStream_t s,
+                                         const std::function<nnqs_status()> &between, const SampleKept &kept) {
+    const int tcm = tc_mode(prec);
+    if (tcm != 1 && tcm != 2) return set_error(NNQS_E_UNSUPPORTED, "rows from the sampler: BF16 or split BF16 only");
+    return rows_fwd_bwd_impl(M, params, x, n, lp_out, seed, g64, g32, ws, st, tcm, s, between, kept);
 }
 
 }  // namespace nnqs

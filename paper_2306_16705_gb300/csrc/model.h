@@ -78,8 +78,31 @@ bool cond_cached_dev_ok(const nnqs_model *M, const CondCtx *ctx, int64_t cap);
 bool cond_dev_walk_ok(const nnqs_model *M, int prec, int64_t cap);
 nnqs_status cond_step_cached_dev(const nnqs_model *M, CondCtx *ctx, const uint64_t *prefixes, const int64_t *n_dev,
                                  const int64_t *g0_dev, int64_t cap, int t, const int32_t *anc, double *cond,
-                                 DevStatus *st, cudaStream_t s);
+                                 DevStatus *st, cudaStream_t s, float *act = nullptr,
+                                 float *fin = nullptr);
 void cond_destroy(CondCtx *c);
+
+// sampler.cu: what an NNQS_SAMPLE_KEEP call left in its workspace -- per tree
+// node the layers' input and mid residual rows act[node][L][2][d] and the
+// final residual fin[node][d], the last level's depth-major ancestor table
+// anc[t * stride + i] (the node of sample i's row t) and its prefixes pref
+// [stride][W] (the samples, in the order returned)
+struct SampleKept {
+    const float *act, *fin;
+    const int32_t *anc;
+    const uint64_t *pref;
+    int64_t stride;
+};
+bool sample_keep_ok(const nnqs_model *M, int prec, int64_t max_unique);
+bool reverse_lite_ok(const nnqs_model *M, int tcm);  // ansatz.cu: the fused reverse mode and its lite workspace apply
+nnqs_status sample_kept(const nnqs_model *M, int prec, int64_t max_unique, const void *ws, size_t ws_bytes,
+                        SampleKept *out);
+// logpsi_forward_backward with the forward's quantities taken from the tree an
+// NNQS_SAMPLE_KEEP sampler call kept (x: that call's samples, in its order)
+nnqs_status logpsi_forward_backward_rows(const nnqs_model *M, const float *params, const uint64_t *x, int64_t n,
+                                         int prec, double *lp_out, const double *seed, double *g64, float *g32,
+                                         Arena &ws, DevStatus *st, cudaStream_t s,
+                                         const std::function<nnqs_status()> &between, const SampleKept &kept);
 
 // eloc_exact.cu
 size_t eloc_exact_workspace(const nnqs_ham *H, const nnqs_model *M, int64_t n_lut, int64_t n_rows, int prec);

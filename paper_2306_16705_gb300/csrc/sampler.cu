@@ -389,9 +389,10 @@ struct SLayout {
     uint64_t *args;   // device copies of n_samples and seed (read by the device-count walk)
     char *region;
     int64_t kv_nodes;
+    float *act, *fin;  // NNQS_SAMPLE_KEEP: per tree node the layers' input and mid residual rows, the final residual
 };
 
-SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &a) {
+SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &a, bool keep = false) {
     SLayout L{};
     const int W = M->W;
     for (int k = 0; k < 2; ++k) {
@@ -409,6 +410,8 @@ SLayout slayout(const nnqs_model *M, int64_t cap, int prec, bool cached, Arena &
     L.kv_nodes = cached ? int64_t(M->T) * cap + 1 : 0;
     for (int k = 0; k < 2; ++k) L.anc[k] = cached ? a.take<int32_t>(size_t(cap) * M->T) : nullptr;
     L.region = a.take<char>(cond_workspace(M, cap, prec, L.kv_nodes));
+    L.act = keep ? a.take<float>(size_t(L.kv_nodes) * 2 * M->L * M->d) : nullptr;
+    L.fin = keep ? a.take<float>(size_t(L.kv_nodes) * M->d) : nullptr;
     return L;
 }
 
@@ -436,9 +439,10 @@ struct GraphKey {
     int64_t cap;
     const void *ws;
     size_t ws_bytes;
+    bool keep;
     bool operator==(const GraphKey &o) const {
         return dev == o.dev && M == o.M && std::memcmp(&cfg, &o.cfg, sizeof cfg) == 0 && params == o.params &&
-               prec == o.prec && cap == o.cap && ws == o.ws && ws_bytes == o.ws_bytes;
+               prec == o.prec && cap == o.cap && ws == o.ws && ws_bytes == o.ws_bytes && keep == o.keep;
     }
 };
 struct GraphEntry {
@@ -474,7 +478,8 @@ nnqs_status walk_kernels(const nnqs_model *M, const float *params, int prec, int
         NNQS_LAUNCH("k_emit", s, k_level0<<<1, 32, 0, s>>>(L.pref[0], W, L.w[0], L.cnt, L.args));
         int cur = 0;
         for (int t = 0; t < T && rc == NNQS_OK; ++t) {
-            rc = cond_step_cached_dev(M, ctx, L.pref[cur], L.cnt + cur, L.cnt + 2, cap, t, L.anc[cur], L.cond, st, s);
+            rc = cond_step_cached_dev(M, ctx, L.pref[cur], L.cnt + cur, L.cnt + 2, cap, t, L.anc[cur], L.cond, st, s,
+                                      L.act, L.fin);
             if (rc != NNQS_OK) break;
             NNQS_LAUNCH("k_split", s, k_split<<<sgrid, 128, 0, s>>>(L.w[cur], L.cond, cap, t, 0, L.counts, L.nchild, st,
                                                                     L.cnt + cur, L.args + 1));
@@ -509,6 +514,7 @@ nnqs_status dev_walk(const nnqs_model *M, const float *params, uint64_t n_sample
         key.cap = cap;
         key.ws = workspace;
         key.ws_bytes = workspace_bytes;
+        key.keep = L.act != nullptr;
         std::unique_lock<std::mutex> lk(g_graph_mu);
         GraphEntry *e = nullptr;
         for (auto &g : g_graphs)
@@ -574,11 +580,39 @@ nnqs_status dev_walk(const nnqs_model *M, const float *params, uint64_t n_sample
 
 using namespace nnqs;
 
+namespace nnqs {
+
+bool sample_keep_ok(const nnqs_model *M, int prec, int64_t max_unique) {
+    return max_unique >= 1 && max_unique <= kScanOne && cond_dev_walk_ok(M, prec, max_unique);
+}
+
+nnqs_status sample_kept(const nnqs_model *M, int prec, int64_t max_unique, const void *ws, size_t ws_bytes,
+                        SampleKept *out) {
+    if (!ws || reinterpret_cast<uintptr_t>(ws) % 256)
+        return set_error(NNQS_E_INVAL, "sampler workspace null or misaligned");
+    if (!sample_keep_ok(M, prec, max_unique))
+        return set_error(NNQS_E_UNSUPPORTED, "no NNQS_SAMPLE_KEEP walk for this model, precision or max_unique");
+    if (ws_bytes < nnqs_sample_workspace_size(M, max_unique, prec, NNQS_SAMPLE_KEEP))
+        return set_error(NNQS_E_WORKSPACE, "sampler workspace smaller than an NNQS_SAMPLE_KEEP call's");
+    Arena a(const_cast<void *>(ws));
+    a.take<char>(kStatusBytes);
+    const SLayout L = slayout(M, max_unique, prec, true, a, true);
+    const int cur = M->T & 1;  // the last level after T steps
+    out->act = L.act;
+    out->fin = L.fin;
+    out->anc = L.anc[cur];
+    out->pref = L.pref[cur];
+    out->stride = max_unique;
+    return NNQS_OK;
+}
+
+}  // namespace nnqs
+
 extern "C" size_t nnqs_sample_workspace_size(const nnqs_model *M, int64_t max_unique, int prec, int flags) {
     if (!M || max_unique < 1) return 0;
     Arena a(nullptr);
     a.take<char>(kStatusBytes);
-    slayout(M, max_unique, prec, !(flags & NNQS_SAMPLE_RECOMPUTE), a);
+    slayout(M, max_unique, prec, !(flags & NNQS_SAMPLE_RECOMPUTE), a, (flags & NNQS_SAMPLE_KEEP) != 0);
     return a.used + 1024;
 }
 
@@ -589,7 +623,11 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     if (!M || !params || !samples_out || !weights_out || !n_unique_out || max_unique < 1)
         return set_error(NNQS_E_INVAL, "null argument or max_unique < 1");
     if (!prec_valid(prec)) return set_error(NNQS_E_INVAL, "bad precision");
-    if (flags & ~NNQS_SAMPLE_RECOMPUTE) return set_error(NNQS_E_INVAL, "unknown sampler flags");
+    if (flags & ~(NNQS_SAMPLE_RECOMPUTE | NNQS_SAMPLE_KEEP)) return set_error(NNQS_E_INVAL, "unknown sampler flags");
+    const bool keep = (flags & NNQS_SAMPLE_KEEP) != 0;
+    if (keep && ((flags & NNQS_SAMPLE_RECOMPUTE) || !sample_keep_ok(M, prec, max_unique)))
+        return set_error(NNQS_E_UNSUPPORTED, "NNQS_SAMPLE_KEEP needs the cached device walk (BF16 or split BF16, "
+                                             "d_model 64, max_unique <= 65536)");
     if (n_samples > (uint64_t(1) << 53)) return set_error(NNQS_E_INVAL, "n_samples above 2^53");
     *n_unique_out = 0;
     const bool cached = !(flags & NNQS_SAMPLE_RECOMPUTE);
@@ -600,7 +638,7 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
     NNQS_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(DevStatus), s));
     Arena a(workspace);
     DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
-    const SLayout L = slayout(M, max_unique, prec, cached, a);
+    const SLayout L = slayout(M, max_unique, prec, cached, a, keep);
     if (L.kv_nodes >= (int64_t(1) << 31))
         return set_error(NNQS_E_UNSUPPORTED, "key/value cache above 2^31 nodes (T * max_unique)");
     if (n_samples == 0) return NNQS_OK;

@@ -120,3 +120,59 @@ extern "C" nnqs_status nnqs_energy_grad(const nnqs_ham *H, const nnqs_model *M, 
     }
     return NNQS_OK;
 }
+
+extern "C" int nnqs_energy_grad_sampled_supported(const nnqs_model *M, int prec, int64_t max_unique) {
+    const int tcm = tc_mode(prec);
+    return M && (tcm == 1 || tcm == 2) && sample_keep_ok(M, prec, max_unique) && reverse_lite_ok(M, tcm) ? 1 : 0;
+}
+
+extern "C" size_t nnqs_energy_grad_sampled_workspace_size(const nnqs_ham *H, const nnqs_model *M, int64_t n_u,
+                                                          int prec) {
+    return nnqs_energy_grad_workspace_size(H, M, n_u, prec);
+}
+
+extern "C" nnqs_status nnqs_energy_grad_sampled(const nnqs_ham *H, const nnqs_model *M, const float *params,
+                                                const void *sample_workspace, size_t sample_workspace_bytes,
+                                                int64_t max_unique, const uint64_t *samples, const uint64_t *weights,
+                                                int64_t n_u, int prec, double *stats, double *eloc_out,
+                                                double *grad_f64, float *grad_f32, void *workspace,
+                                                size_t workspace_bytes, nnqs_stream stream) {
+    if (!H || !M || n_u <= 0) return set_error(NNQS_E_INVAL, "null handle or empty sample set");
+    if (!H->d_gxy) return set_error(NNQS_E_INVAL, "Hamiltonian has no device tables");
+    if (!params || !samples || !weights || !stats || (!grad_f64 && !grad_f32))
+        return set_error(NNQS_E_INVAL, "null device pointer");
+    if (M->N != H->n_qubits) return set_error(NNQS_E_INVAL, "model and Hamiltonian disagree on the qubit count");
+    if (!prec_valid(prec)) return set_error(NNQS_E_INVAL, "bad precision");
+    if (n_u > max_unique) return set_error(NNQS_E_INVAL, "more samples than the sampler call's max_unique");
+    SampleKept kept{};
+    NNQS_TRY(sample_kept(M, prec, max_unique, sample_workspace, sample_workspace_bytes, &kept));
+    const size_t need = nnqs_energy_grad_sampled_workspace_size(H, M, n_u, prec);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256 || workspace_bytes < need)
+        return set_error(NNQS_E_WORKSPACE, "workspace null, misaligned or smaller than " + std::to_string(need));
+    cudaStream_t s = (cudaStream_t)stream;
+    NNQS_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(DevStatus), s));
+    Arena a(workspace);
+    DevStatus *st = a.take<DevStatus>(kStatusBytes / sizeof(DevStatus));
+    const Layout L = layout(H, M, n_u, prec, a);
+    if (!L.fused) return set_error(NNQS_E_INVAL, "more samples than one activation chunk");
+    double *eloc = eloc_out ? eloc_out : L.eloc;
+    auto middle = [&]() -> nnqs_status {
+        {
+            Arena sub(L.region2);
+            NNQS_TRY(eloc_sa(H, samples, L.lp, n_u, 0, n_u, M->cfg.n_alpha, M->cfg.n_beta, NNQS_SWEEP_AUTO, eloc,
+                             sub, st, s));
+        }
+        {
+            Arena sub(L.region2);
+            NNQS_TRY(energy_stats(eloc, weights, n_u, stats, sub, s));
+        }
+        NNQS_LAUNCH("k_seeds", s, k_seeds<<<grid_for(n_u, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(eloc),
+                                                                           weights, stats, n_u,
+                                                                           reinterpret_cast<double2 *>(L.seed)));
+        return NNQS_OK;
+    };
+    Arena sub(L.region);
+    return logpsi_forward_backward_rows(M, params, samples, n_u, prec, L.lp, L.seed, grad_f64, grad_f32, sub, st, s,
+                                        middle, kept);
+}
+

@@ -66,7 +66,8 @@ class VMC:
     def __init__(self, ham: B.Hamiltonian, model: B.Model, params: torch.Tensor, prec=B.MIXED,
                  n_samples: int = 16384, max_unique: int = 1 << 16, lr: float = 1e-3,
                  betas=(0.9, 0.999), eps: float = 1e-8, seed: int = 0, optimizer: str = "adam",
-                 weight_decay: float = 0.01, schedule: str | None = None, warmup: int = 4000):
+                 weight_decay: float = 0.01, schedule: str | None = None, warmup: int = 4000,
+                 tree_reuse: bool | None = None):
         if optimizer not in ("adam", "adamw") or schedule not in (None, "paper"):
             raise ValueError("optimizer must be adam or adamw, schedule None or paper")
         self.optimizer, self.weight_decay, self.schedule, self.warmup = optimizer, weight_decay, schedule, warmup
@@ -77,6 +78,13 @@ class VMC:
         self.v = torch.zeros_like(self.params)
         self.t = 0
         self.n_samples, self.max_unique = int(n_samples), int(max_unique)
+        # the energy gradient reads the forward's quantities from the tree the
+        # sampler decoded (NNQS_SAMPLE_KEEP + nnqs_energy_grad_sampled) where
+        # that applies; tree_reuse=False keeps the separate forward
+        ok = bool(B.lib().nnqs_energy_grad_sampled_supported(model.handle, prec, self.max_unique))
+        if tree_reuse and not ok:
+            raise ValueError("tree reuse needs BF16 / split-BF16 arithmetic, d_model 64 and max_unique <= 65536")
+        self.tree_reuse = ok if tree_reuse is None else bool(tree_reuse)
         self.lr, self.betas, self.eps = lr, betas, eps
         self.seed = int(seed)
         self._ws_sample = None
@@ -103,14 +111,15 @@ class VMC:
 
     def sample(self, seed=None):
         seed = sample_seed(self.seed, self.t) if seed is None else seed
-        nb = B.lib().nnqs_sample_workspace_size(self.model.handle, self.max_unique, self.prec, 0)
+        flags = B.SAMPLE_KEEP if self.tree_reuse else 0
+        nb = B.lib().nnqs_sample_workspace_size(self.model.handle, self.max_unique, self.prec, flags)
         if self._ws_sample is None or self._ws_sample.numel() < nb:
             self._ws_sample = B.workspace(nb, self.params.device)
         ns = self.current_n_samples()
         while True:
             try:
                 out = B.sample(self.model, self.params, ns, seed, self.max_unique, self.prec,
-                               check=False, ws=self._ws_sample)
+                               check=False, ws=self._ws_sample, flags=flags)
             except B.NNQSError as e:
                 # paper schedule: hold N_s below the value that overflowed the table
                 if self.schedule != "paper" or e.status != B.E_TABLE_FULL or ns <= 1:
@@ -129,9 +138,14 @@ class VMC:
         if marks is not None:
             marks.append(torch.cuda.Event(enable_timing=True))
             marks[-1].record()
-        stats, _, _ = B.energy_grad(self.ham, self.model, self.params, x, w, self.prec,
-                                    check=check, ws=self._ws_grad_for(x.shape[0]),
-                                    want_eloc=False, grad_out=self.grad)
+        if self.tree_reuse:
+            stats, _, _ = B.energy_grad_sampled(self.ham, self.model, self.params, self._ws_sample, self.max_unique,
+                                                x, w, self.prec, check=check, ws=self._ws_grad_for(x.shape[0]),
+                                                want_eloc=False, grad_out=self.grad)
+        else:
+            stats, _, _ = B.energy_grad(self.ham, self.model, self.params, x, w, self.prec,
+                                        check=check, ws=self._ws_grad_for(x.shape[0]),
+                                        want_eloc=False, grad_out=self.grad)
         if marks is not None:
             marks.append(torch.cuda.Event(enable_timing=True))
             marks[-1].record()
