@@ -3129,7 +3129,8 @@ bool reverse_lite(const nnqs_model *M, int tcm) {
 
 template <class R>
 nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
-                           Grads<R> &G, const double2 *seed, R *gacc, const TcWeights *tcw, cudaStream_t s) {
+                           Grads<R> &G, const double2 *seed, R *gacc, const TcWeights *tcw, cudaStream_t s,
+                           const SampleKept *kept = nullptr) {
     const int T = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, N = M->N;
     const int64_t rows = C * T;
     const ParamLayout &Lo = M->lay;
@@ -3186,6 +3187,11 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
                             gacc + Lo.lnf_b, gacc + Lo.layer[L - 1].b2, scr, true));
     const bool fused_ffn = sizeof(R) == 4 && G.part && fused_bwd_applies(M, tcw);
     const bool fused_attn = fused_ffn;
+    // with the sampler's tree, the fused halves read each token row's layer
+    // input and mid residual from its tree node (act[node][L][2][d])
+    if (kept && !fused_ffn) return set_error(NNQS_E_UNSUPPORTED, "rows from the sampler's tree need the fused reverse mode");
+    BwdRowSource src{};
+    if (kept) src = BwdRowSource{kept->anc, kept->stride, 2 * (int64_t)L * d, T};
     for (int l = L - 1; l >= 0; --l) {
         const auto &Lw = V.layer[l];
         const auto &Lg = Lo.layer[l];
@@ -3201,7 +3207,9 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
             if (fused_ffn) {
                 const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(tcw->tiles);
                 BwdFfnArgs fa{};
-                fa.hmid = hmid;
+                fa.hmid = kept ? reinterpret_cast<const float *>(kept->act) + (2 * l + 1) * (int64_t)d
+                               : reinterpret_cast<const float *>(hmid);
+                fa.src = src;
                 fa.dh = G.dh;
                 fa.rows = rows;
                 fa.ln2g = Lw.ln2g;
@@ -3236,7 +3244,9 @@ nnqs_status backward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_
             if (fused_attn) {
                 const __nv_bfloat16 *tiles = static_cast<const __nv_bfloat16 *>(tcw->tiles);
                 BwdAttnArgs aa{};
-                aa.hin = hin;
+                aa.hin = kept ? reinterpret_cast<const float *>(kept->act) + 2 * l * (int64_t)d
+                              : reinterpret_cast<const float *>(hin);
+                aa.src = src;
                 aa.dh = G.dh;
                 aa.n = C;
                 aa.T = T;
@@ -3853,18 +3863,20 @@ bool logpsi_single_chunk(const nnqs_model *M, int64_t n, int prec) {
 // ---------------------------------------------------------------- rows from the sampler's tree
 // The activations of every token row (sample i, position t) as the sampler's
 // decode step left them at row t's tree node anc[t * stride + i]
-// (NNQS_SAMPLE_KEEP): each layer's input and mid residual, the final residual;
-// then the final LayerNorm, the head and the masked log-softmax of the row's
-// token, as the forward's last part computes them.  4 lanes per row, 16
-// columns each; lane 0 of a row writes its conditionals, token and log
-// probability (lprow), k_rows_logpsi adds a sample's rows.
+// (NNQS_SAMPLE_KEEP): the final residual and, when `layers` is set, each
+// layer's input and mid residual (the fused reverse mode reads those from the
+// nodes itself); then the final LayerNorm, the head and the masked
+// log-softmax of the row's token, as the forward's last part computes them.
+// 4 lanes per row, 16 columns each; lane 0 of a row writes its conditionals,
+// token and log probability (lprow), k_rows_logpsi adds a sample's rows.
 constexpr int kRowsPerBlock = 64;
 __global__ void __launch_bounds__(4 * kRowsPerBlock) k_rows_from_nodes(
     const uint64_t *__restrict__ x, int W, int64_t n, int T, int L, const float *__restrict__ act,
     const float *__restrict__ fin, const int32_t *__restrict__ anc, int64_t stride, const float *__restrict__ lnf_g,
     const float *__restrict__ lnf_b, const float *__restrict__ hw, const float *__restrict__ hb, int n_alpha,
-    int n_beta, float *__restrict__ hbuf, float *__restrict__ hmid, float *__restrict__ hf, float *__restrict__ meanf,
-    float *__restrict__ rstdf, float *__restrict__ pi, uint8_t *__restrict__ tok, float *__restrict__ lprow) {
+    int n_beta, bool layers, float *__restrict__ hbuf, float *__restrict__ hmid, float *__restrict__ hf,
+    float *__restrict__ meanf, float *__restrict__ rstdf, float *__restrict__ pi, uint8_t *__restrict__ tok,
+    float *__restrict__ lprow) {
     constexpr int d = 64;
     const int64_t rows = n * T;
     const int64_t r = blockIdx.x * (int64_t)kRowsPerBlock + (threadIdx.x >> 2);
@@ -3873,7 +3885,7 @@ __global__ void __launch_bounds__(4 * kRowsPerBlock) k_rows_from_nodes(
     const int64_t i = valid ? r / T : 0;
     const int t = valid ? (int)(r - i * T) : 0;
     const int64_t node = valid ? (int64_t)anc[t * stride + i] : 0;
-    if (valid) {
+    if (valid && layers) {
         for (int l = 0; l < L; ++l) {
             const float4 *a0 = reinterpret_cast<const float4 *>(act + ((node * L + l) * 2) * d + 16 * q);
             const float4 *a1 = reinterpret_cast<const float4 *>(act + ((node * L + l) * 2 + 1) * d + 16 * q);
@@ -4027,12 +4039,13 @@ nnqs_status rows_fwd_bwd_impl(const nnqs_model *M, const float *params, const ui
     NNQS_LAUNCH("k_rows_from_nodes", s,
                 k_rows_from_nodes<<<(unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock), 4 * kRowsPerBlock, 0, s>>>(
                     x, M->W, n, T, M->L, kept.act, kept.fin, kept.anc, kept.stride, V.lnf_g, V.lnf_b, V.hw, V.hb,
-                    M->cfg.n_alpha, M->cfg.n_beta, A.hbuf, A.hmid, A.hf, A.meanf, A.rstdf, A.pi, A.tok, G.dtmp));
+                    M->cfg.n_alpha, M->cfg.n_beta, false, A.hbuf, A.hmid, A.hf, A.meanf, A.rstdf, A.pi, A.tok,
+                    G.dtmp));
     double2 *out = reinterpret_cast<double2 *>(lp_out);
     NNQS_LAUNCH("k_rows_logpsi", s, k_rows_logpsi<<<grid_for(n, 256), 256, 0, s>>>(G.dtmp, n, T, out, st));
     NNQS_TRY(phase_mlp<R>(M, V, x, n, A, out, &tcw, s));
     NNQS_TRY(between());
-    NNQS_TRY(backward_chunk<R>(M, V, x, n, A, G, reinterpret_cast<const double2 *>(seed), gacc, &tcw, s));
+    NNQS_TRY(backward_chunk<R>(M, V, x, n, A, G, reinterpret_cast<const double2 *>(seed), gacc, &tcw, s, &kept));
     NNQS_LAUNCH("k_grad_out", s, k_grad_out<R><<<grid_for(M->lay.total, 256), 256, 0, s>>>(gacc, M->lay.total, g64, g32));
     return NNQS_OK;
 }

@@ -58,6 +58,25 @@ __device__ __forceinline__ void fb_prefetch_l2(const void *p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// the saved row of token row gr (see BwdRowSource)
+__device__ __forceinline__ const float *fb_row(const float *base, int64_t gr, const BwdRowSource &src) {
+    if (!src.anc) return base + gr * 64;
+    const int64_t i = gr / src.T;
+    const int t = int(gr - i * src.T);
+    return base + int64_t(__ldg(src.anc + t * src.anc_stride + i)) * src.node_stride;
+}
+
+// the next tile's saved rows [r1, r1 + nr) into L2: one bulk prefetch when
+// they are contiguous, else one 256-byte prefetch per row by threads 0 .. nr - 1
+__device__ __forceinline__ void fb_prefetch_rows(const float *base, int64_t r1, int64_t nr, const BwdRowSource &src,
+                                                 int tid) {
+    if (!src.anc) {
+        if (tid == 0) fb_prefetch_l2(base + r1 * 64, uint32_t(nr * 64 * 4));
+    } else if (tid < nr) {
+        fb_prefetch_l2(fb_row(base, r1 + tid, src), 256u);
+    }
+}
+
 // shared-memory descriptor of an MN-major (transposed) operand, 128-byte
 // swizzle: 128-byte rows of 64 BF16 along M (or N), one row per K index,
 // 8-row groups along K 1024 bytes apart, 64-wide M (N) blocks `lbo` bytes apart
@@ -258,10 +277,11 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int64_t gr = tile * kRows + row;
         const bool valid = gr < g.rows;
-        if (tid == 0 && tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
+        const float *hrow = valid ? fb_row(g.hmid, gr, g.src) : g.hmid;
+        if (tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
             const int64_t r1 = (tile + gridDim.x) * kRows, nr = g.rows - r1 < kRows ? g.rows - r1 : kRows;
-            fb_prefetch_l2(g.hmid + r1 * kD, uint32_t(nr * kD * 4));
-            fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
+            fb_prefetch_rows(g.hmid, r1, nr, g.src, tid);
+            if (tid == 0) fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
         }
         // ---- LN2 of the saved residual rows -> a2 (A); dy -> DY
         // (thread: row `row`, columns 16 cq .. 16 cq + 15; rows past the end are zero)
@@ -269,7 +289,7 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
         {
             float hv[16], dv[16];
             if (valid) {
-                fb_ldg16(g.hmid + gr * kD + 16 * cq, hv);
+                fb_ldg16(hrow + 16 * cq, hv);
                 fb_ld16(g.dh + gr * kD + 16 * cq, dv);
             } else {
 #pragma unroll
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
             tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
             float hv[16], dv[16], gv[16], da[16], xh[16];
             if (valid) {
-                fb_ldg16(g.hmid + gr * kD + 16 * cq, hv);
+                fb_ldg16(hrow + 16 * cq, hv);
                 fb_ld16(g.dh + gr * kD + 16 * cq, dv);
             } else {
 #pragma unroll
@@ -635,10 +655,11 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
         const int64_t s0 = tile * g.spt;
         const int64_t gr = s0 * T + row;
         const bool valid = row < rows_used && gr < rows;
-        if (tid == 0 && tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
+        const float *hrow = valid ? fb_row(g.hin, gr, g.src) : g.hin;
+        if (tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
             const int64_t r1 = (tile + gridDim.x) * g.spt * T, nr = rows - r1 < rows_used ? rows - r1 : rows_used;
-            fb_prefetch_l2(g.hin + r1 * kD, uint32_t(nr * kD * 4));
-            fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
+            fb_prefetch_rows(g.hin, r1, nr, g.src, tid);
+            if (tid == 0) fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
         }
         if (SPLIT && tid == 0) {  // the qkv image's low part into the scratch region
             tc::fence_async_smem();
@@ -651,7 +672,7 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
         {
             float hv[16], dv[16];
             if (valid) {
-                fb_ldg16(g.hin + gr * kD + 16 * cq, hv);
+                fb_ldg16(hrow + 16 * cq, hv);
                 fb_ld16(g.dh + gr * kD + 16 * cq, dv);
             } else {
 #pragma unroll
@@ -914,7 +935,7 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
             tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
             float hv[16], dv[16], gv[16], da[16], xh[16];
             if (valid) {
-                fb_ldg16(g.hin + gr * kD + 16 * cq, hv);
+                fb_ldg16(hrow + 16 * cq, hv);
                 fb_ld16(g.dh + gr * kD + 16 * cq, dv);
             } else {
 #pragma unroll
@@ -1060,6 +1081,8 @@ nnqs_status bwd_ffn_launch(const BwdFfnArgs &a, bool split, cudaStream_t s) {
     auto al = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
     if (!al(a.hmid) || !al(a.dh) || !al(a.ln2g) || !al(a.ln2b) || !al(a.b1) || !al(a.t1) || !al(a.t2))
         return set_error(NNQS_E_INVAL, "fused FFN reverse mode: operands not 16-byte aligned");
+    if (a.src.anc && (a.src.T < 1 || a.src.anc_stride < 1 || a.src.node_stride % 4 != 0))
+        return set_error(NNQS_E_INVAL, "fused FFN reverse mode: bad tree row source");
     // method FLOPs: the recomputed FFN-in product and the four reverse products
     note_work("k_bwd_ffn", double(a.rows) * 2.0 * fb::kD * fb::kF * 5.0, double(a.rows) * fb::kD * 4.0 * 3.0);
     return split ? launch_ffn<true>(a, s) : launch_ffn<false>(a, s);
@@ -1084,6 +1107,8 @@ nnqs_status bwd_attn_launch(const BwdAttnArgs &a, bool split, int dh, cudaStream
     auto al = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
     if (!al(a.hin) || !al(a.dh) || !al(a.ln1g) || !al(a.ln1b) || !al(a.bqkv) || !al(a.tqkv) || !al(a.to))
         return set_error(NNQS_E_INVAL, "fused attention reverse mode: operands not 16-byte aligned");
+    if (a.src.anc && (a.src.T != a.T || a.src.anc_stride < 1 || a.src.node_stride % 4 != 0))
+        return set_error(NNQS_E_INVAL, "fused attention reverse mode: bad tree row source");
     // method FLOPs: the recomputed qkv product, do, da and the two weight products
     const double rows = double(a.n) * a.T;
     note_work("k_bwd_attn", rows * 2.0 * fa::kD * (3.0 * fa::kQKV + 2.0 * fa::kD), rows * fa::kD * 4.0 * 3.0);

@@ -14,10 +14,21 @@ namespace nnqs {
 // dW1 [256][64] | dW2 [64][256] | db1 [256] | dgamma2 [64] | dbeta2 [64] | dbo [64]
 constexpr int kBwdFfnPart = 256 * 64 + 64 * 256 + 256 + 3 * 64;
 
+// Where the saved rows live: row r of a contiguous [rows][64] array, or (anc
+// set) the row of the tree node of token row r = i T + t, node
+// anc[t * anc_stride + i], whose rows are node_stride floats apart (the
+// sampler's kept activations)
+struct BwdRowSource {
+    const int32_t *anc;
+    int64_t anc_stride, node_stride;
+    int T;
+};
+
 struct BwdFfnArgs {
-    const float *hmid;  // [rows][64] residual after the attention (the input of LN2)
+    const float *hmid;  // [rows][64] residual after the attention (the input of LN2); with src.anc, node 0's row
     float *dh;          // [rows][64] in: gradient of the layer output; out: gradient of hmid
     int64_t rows;
+    BwdRowSource src;   // src.anc null: hmid is contiguous
     const float *ln2g, *ln2b, *b1;  // 16-byte aligned
     // BF16 shared-memory images of the forward: FFN-in W1 [256][64] (high
     // part, low part right after) and FFN-out W2 as four [64][64] K blocks
@@ -42,10 +53,11 @@ nnqs_status bwd_ffn_reduce(const float *part, int grid, float *dw1, float *dw2, 
 constexpr int kBwdAttnPart = 192 * 64 + 64 * 64 + 192 + 3 * 64;
 
 struct BwdAttnArgs {
-    const float *hin;   // [rows][64] the layer's input (LN1's input)
+    const float *hin;   // [rows][64] the layer's input (LN1's input); with src.anc, node 0's row
     float *dh;          // [rows][64] in: gradient of hmid; out: gradient of the layer input
     int64_t n;          // samples; rows = n T
     int T, spt;         // tokens per sample, samples per 128-row tile (floor(128 / T))
+    BwdRowSource src;   // src.anc null: hin is contiguous (src.T must equal T when set)
     const float *ln1g, *ln1b, *bqkv;  // 16-byte aligned
     // BF16 shared-memory images of the forward: qkv [192][64] (high part, low
     // part right after) and the out-projection [64][64] (high part)
