@@ -1825,10 +1825,11 @@ constexpr int kOffH = kOffB + 131072;  // residual rows [128][65] FP32
 constexpr int kHS = 65;
 constexpr int kOffBar = kOffH + kRows * kHS * 4;
 constexpr int kSmem = kOffBar + 64 + 1024;  // 230,976 bytes
-constexpr uint32_t kColQKV = 0, kColO = 192, kColU = 256, kColY = 320, kTmemCols = 512;
-// TMEM columns of the four FFN-in chunks U_c: kColU, the free 384..511, and
-// the first 64 columns of the finished q|k|v
-__device__ __forceinline__ constexpr uint32_t col_u(int c) { return c == 0 ? kColU : c == 3 ? 0u : 256u + 64u * uint32_t(c + 1); }
+// TMEM columns: q|k|v, then the attention's out-projection; the FFN-in
+// product U (256 columns, one N = 256 product over the finished q|k|v and out-
+// projection columns, chunk c at 64 c) and the FFN-out accumulator after them
+constexpr uint32_t kColQKV = 0, kColO = 192, kColU = 0, kColY = 256, kTmemCols = 512;
+__device__ __forceinline__ constexpr uint32_t col_u(int c) { return kColU + 64u * uint32_t(c); }
 }  // namespace dec
 
 constexpr int kDecMaxLayers = 16;
@@ -2305,16 +2306,14 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         }
         __syncthreads();
         if (g.act) dec_store_rows(sH, g.act + (2 * l + 1) * kD, g0 + m0, n_cta - m0, act_stride);
-        // ---- LayerNorm 2 -> FFN: the four MMA1(c) = LN2 W1_c^T are issued
-        // together (TMEM columns of the finished q|k|v and free columns), then
-        // per chunk: GELU of U_c into registers while MMA2(c - 1) runs, G_c
-        // into shared memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
+        // ---- LayerNorm 2 -> FFN: U = LN2 W1^T as one N = 256 product (the
+        // four 64-row chunks of the W1 image are consecutive), then per chunk:
+        // GELU of U_c into registers while MMA2(c - 1) runs, G_c into shared
+        // memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
         dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
         sync_async();
         if (tid == 0) {
-#pragma unroll
-            for (int c = 0; c < kF / kD; ++c)
-                dec_mma(tmem + col_u(c), uA, uA2, uB + kW1Hi + 8192 * c, uB + kW1Lo + 8192 * c, kD, SPLIT, false);
+            dec_mma(tmem + kColU, uA, uA2, uB + kW1Hi, uB + kW1Lo, kF, SPLIT, false);
             tc::mma_commit(mb);
         }
         wait_mma();
