@@ -127,17 +127,7 @@ __device__ __forceinline__ void fb_ldg16(const float *__restrict__ p, float (&v)
         v[4 * k + 3] = a.w;
     }
 }
-// 16 floats from global memory this kernel also writes
-__device__ __forceinline__ void fb_ld16(const float *p, float (&v)[16]) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float4 a = reinterpret_cast<const float4 *>(p)[k];
-        v[4 * k] = a.x;
-        v[4 * k + 1] = a.y;
-        v[4 * k + 2] = a.z;
-        v[4 * k + 3] = a.w;
-    }
-}
+
 __device__ __forceinline__ void fb_st16(float *p, const float *v) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -181,6 +171,128 @@ __device__ __forceinline__ float fb_colsum(float (&v)[N], int lane) {
     float r = v[0];
     if (N == 16) r += __shfl_xor_sync(0xffffffffu, r, 1);
     return r;
+}
+
+// ---- Four lanes per row.  The LayerNorm phases touch the rows in global
+// memory; with one row per lane (the TMEM lane mapping) a warp's 16-byte
+// access spans 32 rows and costs 32 L1 wavefronts.  There, lanes 4 r' .. 4 r' + 3
+// of a warp hold tile row tid / 4 instead, lane lq = tid % 4 the float4
+// pieces lq + 4 m of it (columns 16 m + 4 lq .. + 3, m = 0..3, v[4 m + e]),
+// so one access covers eight whole 256-byte rows.
+
+__device__ __forceinline__ void fb_ld_row4(const float *__restrict__ p, int lq, float (&v)[16]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + lq + 4 * m);
+        v[4 * m] = a.x;
+        v[4 * m + 1] = a.y;
+        v[4 * m + 2] = a.z;
+        v[4 * m + 3] = a.w;
+    }
+}
+
+// the same for rows this kernel also writes (no read-only path)
+__device__ __forceinline__ void fb_ld_row4_rw(const float *p, int lq, float (&v)[16]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[lq + 4 * m];
+        v[4 * m] = a.x;
+        v[4 * m + 1] = a.y;
+        v[4 * m + 2] = a.z;
+        v[4 * m + 3] = a.w;
+    }
+}
+
+__device__ __forceinline__ void fb_st_row4(float *p, int lq, const float (&v)[16]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        reinterpret_cast<float4 *>(p)[lq + 4 * m] = make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
+}
+
+// sum over the row's four lanes
+__device__ __forceinline__ float fb_sum4(float s) {
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    return s;
+}
+
+// mean and 1 / sqrt(variance + 1e-5) of a row held in four lanes
+__device__ __forceinline__ void fb_ln_stats4(const float (&v)[16], float &mu, float &rs) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s += v[c];
+    mu = fb_sum4(s) * (1.0f / 64);
+    float q = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) q += (v[c] - mu) * (v[c] - mu);
+    rs = 1.0f / sqrtf(fb_sum4(q) * (1.0f / 64) + 1e-5f);
+}
+
+// a lane's four pieces of row r as half granules (4 BF16) of a swizzled
+// [128][64] panel: the high part, and the low part v - bf16(v) when lo is set
+__device__ __forceinline__ void fb_half_granules(uint8_t *hi, uint8_t *lo, int r, int lq, const float (&v)[16]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int k = lq + 4 * m, c = k >> 1;
+        const int off = r * 128 + ((c ^ (r & 7)) << 4) + 8 * (k & 1);
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[4 * m], v[4 * m + 1]);
+        const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[4 * m + 2], v[4 * m + 3]);
+        *reinterpret_cast<uint2 *>(hi + off) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1));
+        if (lo) {
+            const __nv_bfloat162 l0 = __floats2bfloat162_rn(v[4 * m] - __low2float(h0), v[4 * m + 1] - __high2float(h0));
+            const __nv_bfloat162 l1 =
+                __floats2bfloat162_rn(v[4 * m + 2] - __low2float(h1), v[4 * m + 3] - __high2float(h1));
+            *reinterpret_cast<uint2 *>(lo + off) =
+                make_uint2(*reinterpret_cast<const uint32_t *>(&l0), *reinterpret_cast<const uint32_t *>(&l1));
+        }
+    }
+}
+
+// first of the two columns whose sums fb_colsum8 leaves in lane `lane`
+__device__ __forceinline__ int fb_col8(int lane) {
+    return 16 * (2 * ((lane >> 4) & 1) + ((lane >> 3) & 1)) + 4 * (lane & 3) + 2 * ((lane >> 2) & 1);
+}
+
+// Column sums over the warp's eight rows (the lanes with the same lq) of a
+// lane's 16 columns: recursive halving over lane bits 16, 8, 4 (14
+// shuffles); the lane returns the sums of columns fb_col8(lane) and + 1.  v is
+// consumed.
+__device__ __forceinline__ float2 fb_colsum8(float (&v)[16], int lane) {
+#pragma unroll
+    for (int half = 8, m = 16; half >= 2; half >>= 1, m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = up ? v[i] : v[i + half];
+            const float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    return make_float2(v[0], v[1]);
+}
+
+// da (a TMEM accumulator, one row per lane) through shared memory [128][68]
+// FP32 into the four-lanes-per-row mapping: the TMEM-mapped thread (row,
+// columns 16 cq ..) stores, every thread reads its row r4's pieces after the
+// barrier the caller places between
+constexpr int kDaS = 68;
+__device__ __forceinline__ void fb_da_store(float *daS, int row, int cq, const uint32_t (&r16)[16]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<float4 *>(daS + row * kDaS + 16 * cq + 4 * j) =
+            make_float4(__uint_as_float(r16[4 * j]), __uint_as_float(r16[4 * j + 1]), __uint_as_float(r16[4 * j + 2]),
+                        __uint_as_float(r16[4 * j + 3]));
+}
+__device__ __forceinline__ void fb_da_load(const float *daS, int r4, int lq, float (&v)[16]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float4 a = *reinterpret_cast<const float4 *>(daS + r4 * kDaS + 4 * (lq + 4 * m));
+        v[4 * m] = a.x;
+        v[4 * m + 1] = a.y;
+        v[4 * m + 2] = a.z;
+        v[4 * m + 3] = a.w;
+    }
 }
 
 // one 128 x N product over K = 64 (four K = 16 steps) from K-major A and B
@@ -230,6 +342,7 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
+    const int r4 = tid >> 2, lq = tid & 3;
     const int64_t n_tiles = (g.rows + kRows - 1) / kRows;
 
     if (warp == 0) {
@@ -272,51 +385,40 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
         tc::fence_after_sync();
     };
 
-    float cs_b1a = 0.f, cs_b1b = 0.f, cs_g = 0.f, cs_b = 0.f, cs_o = 0.f;  // column sums (db1 halves, LN2, dbo)
+    float cs_b1a = 0.f, cs_b1b = 0.f;  // column sums of du (db1 halves), one column per lane
+    // column sums of the LN2 parameters' gradients and dbo over this warp's
+    // rows, columns fb_col8(lane) and + 1
+    float2 cs_g = make_float2(0.f, 0.f), cs_b = make_float2(0.f, 0.f), cs_o = make_float2(0.f, 0.f);
     bool first = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t gr = tile * kRows + row;
-        const bool valid = gr < g.rows;
-        const float *hrow = valid ? fb_row(g.hmid, gr, g.src) : g.hmid;
+        // rows of the four-lanes-per-row phases: tile row r4, global row g4
+        const int64_t g4 = tile * kRows + r4;
+        const bool ok4 = g4 < g.rows;
         if (tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
             const int64_t r1 = (tile + gridDim.x) * kRows, nr = g.rows - r1 < kRows ? g.rows - r1 : kRows;
             fb_prefetch_rows(g.hmid, r1, nr, g.src, tid);
             if (tid == 0) fb_prefetch_l2(g.dh + r1 * kD, uint32_t(nr * kD * 4));
         }
-        // ---- LN2 of the saved residual rows -> a2 (A); dy -> DY
-        // (thread: row `row`, columns 16 cq .. 16 cq + 15; rows past the end are zero)
-        float mu, rs;
+        // ---- LN2 of the saved residual rows -> a2 (A); dy -> DY (four lanes
+        // per row; rows past the end are zero)
         {
             float hv[16], dv[16];
-            if (valid) {
-                fb_ldg16(hrow + 16 * cq, hv);
-                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            if (ok4) {
+                fb_ld_row4(fb_row(g.hmid, g4, g.src), lq, hv);
+                fb_ld_row4_rw(g.dh + g4 * kD, lq, dv);
             } else {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
             }
-            float s = 0.f;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) s += hv[c];
-            red[cq * 128 + row] = s;
-            __syncthreads();
-            mu = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
-            float q = 0.f;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) q += (hv[c] - mu) * (hv[c] - mu);
-            red[512 + cq * 128 + row] = q;
-            __syncthreads();
-            rs = 1.0f / sqrtf((red[512 + row] + red[640 + row] + red[768 + row] +
-                               red[896 + row]) * (1.0f / kD) + 1e-5f);
+            float mu, rs;
+            fb_ln_stats4(hv, mu, rs);
             float gv[16], bv[16], y[16];
-            fb_ldg16(g.ln2g + 16 * cq, gv);
-            fb_ldg16(g.ln2b + 16 * cq, bv);
+            fb_ld_row4(g.ln2g, lq, gv);
+            fb_ld_row4(g.ln2b, lq, bv);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) y[c] = valid ? (hv[c] - mu) * rs * gv[c] + bv[c] : 0.f;
-            fb_granule(aHi, aLo, row, 2 * cq, y);
-            fb_granule(aHi, aLo, row, 2 * cq + 1, y + 8);
-            fb_granule(sb + kOffDY, nullptr, row, 2 * cq, dv);
-            fb_granule(sb + kOffDY, nullptr, row, 2 * cq + 1, dv + 8);
+            for (int c = 0; c < 16; ++c) y[c] = ok4 ? (hv[c] - mu) * rs * gv[c] + bv[c] : 0.f;
+            fb_half_granules(aHi, aLo, r4, lq, y);
+            fb_half_granules(sb + kOffDY, nullptr, r4, lq, dv);
         }
         sync_async();
         if (tid == 0) {
@@ -398,43 +500,50 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
         if (!ok) break;
         wait_mma();
         if (!ok) break;
-        // ---- LN2 backward: dhmid = dy + rs (da2 g - mean(da2 g) - xh mean(da2 g xh))
+        // ---- LN2 backward: dhmid = dy + rs (da2 g - mean(da2 g) - xh mean(da2 g xh)),
+        // four lanes per row; da2 leaves TMEM through the (now free) gu | du region
         {
-            uint32_t r16[16];
-            tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
+            float *daS = reinterpret_cast<float *>(sb + kOffGU);
+            {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
+                fb_da_store(daS, row, cq, r16);
+            }
+            __syncthreads();
             float hv[16], dv[16], gv[16], da[16], xh[16];
-            if (valid) {
-                fb_ldg16(hrow + 16 * cq, hv);
-                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            if (ok4) {
+                fb_ld_row4(fb_row(g.hmid, g4, g.src), lq, hv);
+                fb_ld_row4_rw(g.dh + g4 * kD, lq, dv);
             } else {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
             }
-            fb_ldg16(g.ln2g + 16 * cq, gv);
+            fb_da_load(daS, r4, lq, da);
+            fb_ld_row4(g.ln2g, lq, gv);
+            float mu, rs;
+            fb_ln_stats4(hv, mu, rs);
             float s1 = 0.f, s2 = 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                da[c] = __uint_as_float(r16[c]);
-                xh[c] = valid ? (hv[c] - mu) * rs : 0.f;
+                xh[c] = ok4 ? (hv[c] - mu) * rs : 0.f;
                 const float dx = da[c] * gv[c];
                 s1 += dx;
                 s2 += dx * xh[c];
             }
-            red[cq * 128 + row] = s1;
-            red[512 + cq * 128 + row] = s2;
-            __syncthreads();
-            const float m1 = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
-            const float m2 = (red[512 + row] + red[640 + row] + red[768 + row] +
-                              red[896 + row]) * (1.0f / kD);
+            const float m1 = fb_sum4(s1) * (1.0f / kD), m2 = fb_sum4(s2) * (1.0f / kD);
             float out[16], t[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) out[c] = valid ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
-            if (valid) fb_st16(g.dh + gr * kD + 16 * cq, out);
+            for (int c = 0; c < 16; ++c) out[c] = ok4 ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
+            if (ok4) fb_st_row4(g.dh + g4 * kD, lq, out);
 #pragma unroll
             for (int c = 0; c < 16; ++c) t[c] = da[c] * xh[c];
-            cs_g += fb_colsum<16>(t, lane);
-            cs_b += fb_colsum<16>(da, lane);
-            cs_o += fb_colsum<16>(out, lane);
+            const float2 sg = fb_colsum8(t, lane), sbt = fb_colsum8(da, lane), so = fb_colsum8(out, lane);
+            cs_g.x += sg.x;
+            cs_g.y += sg.y;
+            cs_b.x += sbt.x;
+            cs_b.y += sbt.y;
+            cs_o.x += so.x;
+            cs_o.y += so.y;
         }
         __syncthreads();
         first = false;
@@ -458,14 +567,25 @@ __global__ void __launch_bounds__(fb::kThreads, 1) k_bwd_ffn(const __grid_consta
         float *cs = red + q4 * kCols;
         cs[32 * cq + lane] = cs_b1a;
         cs[128 + 32 * cq + lane] = cs_b1b;
-        if ((lane & 1) == 0) {
-            cs[256 + 16 * cq + (lane >> 1)] = cs_g;
-            cs[320 + 16 * cq + (lane >> 1)] = cs_b;
-            cs[384 + 16 * cq + (lane >> 1)] = cs_o;
-        }
+        // the LN2 and dbo sums per warp ([16][192] over the free gu region),
+        // added in warp order
+        float *lnp = reinterpret_cast<float *>(sb + kOffGU);
+        const int c8 = fb_col8(lane);
+        lnp[warp * 192 + c8] = cs_g.x;
+        lnp[warp * 192 + c8 + 1] = cs_g.y;
+        lnp[warp * 192 + 64 + c8] = cs_b.x;
+        lnp[warp * 192 + 64 + c8 + 1] = cs_b.y;
+        lnp[warp * 192 + 128 + c8] = cs_o.x;
+        lnp[warp * 192 + 128 + c8 + 1] = cs_o.y;
         __syncthreads();
-        for (int e = tid; e < kCols; e += kThreads)
+        for (int e = tid; e < kF; e += kThreads)
             part[2 * kF * kD + e] = ((red[e] + red[kCols + e]) + red[2 * kCols + e]) + red[3 * kCols + e];
+        for (int e = tid; e < 192; e += kThreads) {
+            float sum = 0.f;
+#pragma unroll 4
+            for (int w = 0; w < kThreads / 32; ++w) sum += lnp[w * 192 + e];
+            part[2 * kF * kD + kF + e] = sum;
+        }
     }
     if (!ok && tid == 0) {
         if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -14;
@@ -603,9 +723,9 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
+    const int r4 = tid >> 2, lq = tid & 3;
     const int T = g.T, rows_used = g.spt * T;
     const int64_t rows = g.n * T, n_tiles = (g.n + g.spt - 1) / g.spt;
-    const int tt = row % T, r0 = row - tt;  // the row's token and its sample's first row in the tile
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
@@ -649,13 +769,16 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
     const float scale = 1.0f / sqrtf(float(DH));
 
     float csq00 = 0.f, csq01 = 0.f, csq10 = 0.f, csq11 = 0.f;  // dbqkv column sums per group (see the flush)
-    float cs_g = 0.f, cs_b = 0.f, cs_o = 0.f;
+    // column sums of the LN1 parameters' gradients and of dh_in over this
+    // warp's rows, columns fb_col8(lane) and + 1
+    float2 cs_g = make_float2(0.f, 0.f), cs_b = make_float2(0.f, 0.f), cs_o = make_float2(0.f, 0.f);
     bool first = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int64_t s0 = tile * g.spt;
-        const int64_t gr = s0 * T + row;
-        const bool valid = row < rows_used && gr < rows;
-        const float *hrow = valid ? fb_row(g.hin, gr, g.src) : g.hin;
+        const bool valid = row < rows_used && s0 * T + row < rows;  // (TMEM-lane mapping)
+        // rows of the four-lanes-per-row phases: tile row r4, global row g4
+        const int64_t g4 = s0 * T + r4;
+        const bool ok4 = r4 < rows_used && g4 < rows;
         if (tile + gridDim.x < n_tiles) {  // the next tile's rows into L2 meanwhile
             const int64_t r1 = (tile + gridDim.x) * g.spt * T, nr = rows - r1 < rows_used ? rows - r1 : rows_used;
             fb_prefetch_rows(g.hin, r1, nr, g.src, tid);
@@ -667,39 +790,26 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
             fb_bulk(sb + kOffS, static_cast<const __nv_bfloat16 *>(g.tqkv) + kQKV * kD, kWQB, bL);
         }
         if (SPLIT) ++n_lo;
-        // ---- LN1 of the saved layer input -> a (A); dhmid -> DH
-        float mu, rs;
+        // ---- LN1 of the saved layer input -> a (A); dhmid -> DH (four lanes
+        // per row; rows outside the tile's samples are zero)
         {
             float hv[16], dv[16];
-            if (valid) {
-                fb_ldg16(hrow + 16 * cq, hv);
-                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            if (ok4) {
+                fb_ld_row4(fb_row(g.hin, g4, g.src), lq, hv);
+                fb_ld_row4_rw(g.dh + g4 * kD, lq, dv);
             } else {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
             }
-            float s = 0.f;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) s += hv[c];
-            red[cq * 128 + row] = s;
-            __syncthreads();
-            mu = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
-            float q = 0.f;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) q += (hv[c] - mu) * (hv[c] - mu);
-            red[512 + cq * 128 + row] = q;
-            __syncthreads();
-            rs = 1.0f / sqrtf((red[512 + row] + red[640 + row] + red[768 + row] +
-                               red[896 + row]) * (1.0f / kD) + 1e-5f);
+            float mu, rs;
+            fb_ln_stats4(hv, mu, rs);
             float gv[16], bv[16], y[16];
-            fb_ldg16(g.ln1g + 16 * cq, gv);
-            fb_ldg16(g.ln1b + 16 * cq, bv);
+            fb_ld_row4(g.ln1g, lq, gv);
+            fb_ld_row4(g.ln1b, lq, bv);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) y[c] = valid ? (hv[c] - mu) * rs * gv[c] + bv[c] : 0.f;
-            fb_granule(aHi, aLo, row, 2 * cq, y);
-            fb_granule(aHi, aLo, row, 2 * cq + 1, y + 8);
-            fb_granule(sb + kOffDH, nullptr, row, 2 * cq, dv);
-            fb_granule(sb + kOffDH, nullptr, row, 2 * cq + 1, dv + 8);
+            for (int c = 0; c < 16; ++c) y[c] = ok4 ? (hv[c] - mu) * rs * gv[c] + bv[c] : 0.f;
+            fb_half_granules(aHi, aLo, r4, lq, y);
+            fb_half_granules(sb + kOffDH, nullptr, r4, lq, dv);
         }
         if (SPLIT) {
             ok = __syncthreads_and(tc::mbar_wait(bL, d_lo & 1u) ? 1 : 0) != 0;
@@ -929,43 +1039,50 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
         }
         wait_mma();
         if (!ok) break;
-        // ---- LN1 backward: dh_in = dhmid + rs (da g - mean(da g) - xh mean(da g xh))
+        // ---- LN1 backward: dh_in = dhmid + rs (da g - mean(da g) - xh mean(da g xh)),
+        // four lanes per row; da leaves TMEM through the (now free) dq | dk | dv region
         {
-            uint32_t r16[16];
-            tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
+            float *daS = reinterpret_cast<float *>(sb + kOffDQ);
+            {
+                uint32_t r16[16];
+                tc::tmem_ld16(tl + kColDA + 16 * cq, r16);
+                fb_da_store(daS, row, cq, r16);
+            }
+            __syncthreads();
             float hv[16], dv[16], gv[16], da[16], xh[16];
-            if (valid) {
-                fb_ldg16(hrow + 16 * cq, hv);
-                fb_ld16(g.dh + gr * kD + 16 * cq, dv);
+            if (ok4) {
+                fb_ld_row4(fb_row(g.hin, g4, g.src), lq, hv);
+                fb_ld_row4_rw(g.dh + g4 * kD, lq, dv);
+                fb_da_load(daS, r4, lq, da);
             } else {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) hv[c] = dv[c] = 0.f;
+                for (int c = 0; c < 16; ++c) hv[c] = dv[c] = da[c] = 0.f;
             }
-            fb_ldg16(g.ln1g + 16 * cq, gv);
+            fb_ld_row4(g.ln1g, lq, gv);
+            float mu, rs;
+            fb_ln_stats4(hv, mu, rs);
             float s1 = 0.f, s2 = 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                da[c] = valid ? __uint_as_float(r16[c]) : 0.f;
-                xh[c] = valid ? (hv[c] - mu) * rs : 0.f;
+                xh[c] = ok4 ? (hv[c] - mu) * rs : 0.f;
                 const float dx = da[c] * gv[c];
                 s1 += dx;
                 s2 += dx * xh[c];
             }
-            red[cq * 128 + row] = s1;
-            red[512 + cq * 128 + row] = s2;
-            __syncthreads();
-            const float m1 = (red[row] + red[128 + row] + red[256 + row] + red[384 + row]) * (1.0f / kD);
-            const float m2 = (red[512 + row] + red[640 + row] + red[768 + row] +
-                              red[896 + row]) * (1.0f / kD);
+            const float m1 = fb_sum4(s1) * (1.0f / kD), m2 = fb_sum4(s2) * (1.0f / kD);
             float out[16], t[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) out[c] = valid ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
-            if (valid) fb_st16(g.dh + gr * kD + 16 * cq, out);
+            for (int c = 0; c < 16; ++c) out[c] = ok4 ? dv[c] + rs * (da[c] * gv[c] - m1 - xh[c] * m2) : 0.f;
+            if (ok4) fb_st_row4(g.dh + g4 * kD, lq, out);
 #pragma unroll
             for (int c = 0; c < 16; ++c) t[c] = da[c] * xh[c];
-            cs_g += fb_colsum<16>(t, lane);
-            cs_b += fb_colsum<16>(da, lane);
-            cs_o += fb_colsum<16>(out, lane);
+            const float2 sg = fb_colsum8(t, lane), sbt = fb_colsum8(da, lane), so = fb_colsum8(out, lane);
+            cs_g.x += sg.x;
+            cs_g.y += sg.y;
+            cs_b.x += sbt.x;
+            cs_b.y += sbt.y;
+            cs_o.x += so.x;
+            cs_o.y += so.y;
         }
         sync_async();  // (the next tile's copy into the scratch region follows these reads)
         first = false;
@@ -1007,14 +1124,25 @@ __global__ void __launch_bounds__(fa::kThreads, 1) k_bwd_attn(const __grid_const
                 }
             }
         }
-        if ((lane & 1) == 0) {
-            cs[192 + 16 * cq + (lane >> 1)] = cs_g;
-            cs[256 + 16 * cq + (lane >> 1)] = cs_b;
-            cs[320 + 16 * cq + (lane >> 1)] = cs_o;
-        }
+        // the LN1 and dh_in sums per warp ([16][192] over the free dq | dk | dv
+        // region), added in warp order
+        float *lnp = reinterpret_cast<float *>(sb + kOffDQ);
+        const int c8 = fb_col8(lane);
+        lnp[warp * 192 + c8] = cs_g.x;
+        lnp[warp * 192 + c8 + 1] = cs_g.y;
+        lnp[warp * 192 + 64 + c8] = cs_b.x;
+        lnp[warp * 192 + 64 + c8 + 1] = cs_b.y;
+        lnp[warp * 192 + 128 + c8] = cs_o.x;
+        lnp[warp * 192 + 128 + c8 + 1] = cs_o.y;
         __syncthreads();
-        for (int e = tid; e < kCols; e += kThreads)
+        for (int e = tid; e < kQKV; e += kThreads)
             part[kQKV * kD + kD * kD + e] = ((red[e] + red[kCols + e]) + red[2 * kCols + e]) + red[3 * kCols + e];
+        for (int e = tid; e < 192; e += kThreads) {
+            float sum = 0.f;
+#pragma unroll 4
+            for (int w = 0; w < kThreads / 32; ++w) sum += lnp[w * 192 + e];
+            part[kQKV * kD + kD * kD + kQKV + e] = sum;
+        }
     }
     if (!ok && tid == 0) {
         if (atomicCAS(&g.st->code, 0, (int)NNQS_E_TIMEOUT) == 0) g.st->index = -15;
