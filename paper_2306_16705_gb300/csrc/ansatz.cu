@@ -1817,7 +1817,7 @@ constexpr int kThreads = 512, kRows = 128, kD = 64, kQKV = 192, kF = 256;
 // lanes 32 (w % 4) .. + 31 (its TMEM lane quarter), columns kCW (w / 4) .. + kCW - 1
 constexpr int kCW = 64 * 4 / (kThreads / 32);
 constexpr int kOffA = 0;         // A operand hi [128][64] BF16 (16 KB); lo at +16 KB
-constexpr int kOffG = 32768;     // FFN-out A chunk hi / lo (+16 KB); before the FFN: Wo hi / lo (+8 KB)
+constexpr int kOffG = 32768;     // Wo hi / lo (+8 KB); in the FFN [0, 128 KB) holds its [128][256] GELU operand
 constexpr int kOffB = 65536;     // Wqkv hi / lo (+24 KB); after the qkv MMA: W1 hi, W1 lo, W2 hi, W2 lo
 constexpr int kQkvLo = 24576;
 constexpr int kW1Hi = 0, kW1Lo = 32768, kW2Hi = 65536, kW2Lo = 98304;  // 4 chunks of 8 KB each
@@ -2103,13 +2103,13 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *sb = smem_raw + (base - raw);
     uint8_t *aHi = sb + kOffA, *aLo = sb + kOffA + 16384;
-    uint8_t *gHi = sb + kOffG, *gLo = sb + kOffG + 16384;
+    uint8_t *gHi = sb + kOffG;
     uint8_t *bB = sb + kOffB;
     float *sH = reinterpret_cast<float *>(sb + kOffH);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + kOffBar);
     uint64_t *wbar = reinterpret_cast<uint64_t *>(sb + kOffBar + 8);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sb + kOffBar + 16);
-    const uint32_t uA = base + kOffA, uA2 = base + kOffA + 16384, uG = base + kOffG, uG2 = base + kOffG + 16384;
+    const uint32_t uA = base + kOffA, uA2 = base + kOffA + 16384, uG = base + kOffG;
     const uint32_t uB = base + kOffB;
     const uint32_t wb = tc::smem_u32(wbar);
 
@@ -2307,9 +2307,8 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         __syncthreads();
         if (g.act) dec_store_rows(sH, g.act + (2 * l + 1) * kD, g0 + m0, n_cta - m0, act_stride);
         // ---- LayerNorm 2 -> FFN: U = LN2 W1^T as one N = 256 product (the
-        // four 64-row chunks of the W1 image are consecutive), then per chunk:
-        // GELU of U_c into registers while MMA2(c - 1) runs, G_c into shared
-        // memory once MMA2(c - 1) has read G, MMA2(c) += G_c W2_c^T
+        // four 64-row chunks of the W1 image are consecutive), then GELU and
+        // the FFN-out product (below)
         dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
         sync_async();
         if (tid == 0) {
@@ -2318,13 +2317,14 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         }
         wait_mma();
         if (!ok) break;
-        // W1 consumed: the next layer's Wqkv comes in over it during the FFN
-        if (l + 1 < g.L) {
-            ++wissued;
-            if (tid == 0) issue_wqkv(l + 1);
-        }
+        // GELU of every chunk U_c into shared memory first: the A and G tiles
+        // and the FFN-in weights' region (all read by finished products) hold
+        // the whole [128][256] operand, chunk c at 16 KB c (high part) and
+        // 64 KB + 16 KB c (low part); then the 4 x 4 K steps of the FFN-out
+        // product in the order of the chunked walk, Y = sum_c G_c W2_c^T
         const float *b1 = g.b1[l];
-        for (int c = 0; c < kF / kD && ok; ++c) {
+#pragma unroll 1
+        for (int c = 0; c < kF / kD; ++c) {
             float x[kCW];
 #pragma unroll
             for (int b = 0; b < kCW / 16; ++b) {
@@ -2334,10 +2334,6 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
 #pragma unroll
                 for (int e = 0; e < 16; ++e) x[16 * b + e] = tc::gelu_f(__uint_as_float(r16[e]) + b1[kD * c + c0 + e]);
             }
-            if (c > 0) {
-                wait_mma();
-                if (!ok) break;
-            }
 #pragma unroll
             for (int b = 0; b < kCW / 16; ++b)
 #pragma unroll
@@ -2345,17 +2341,26 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
                     float xg[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) xg[e] = x[16 * b + 8 * gi + e];
-                    dec_store_granule(gHi, gLo, row, ((kCW * cq + 16 * b) >> 3) + gi, xg, SPLIT);
+                    dec_store_granule(sb + 16384 * c, sb + 65536 + 16384 * c, row, ((kCW * cq + 16 * b) >> 3) + gi,
+                                      xg, SPLIT);
                 }
-            sync_async();
-            if (tid == 0) {
-                dec_mma(tmem + kColY, uG, uG2, uB + kW2Hi + 8192 * c, uB + kW2Lo + 8192 * c, kD, SPLIT, c > 0);
-                tc::mma_commit(mb);
-            }
         }
-        if (!ok) break;
+        sync_async();
+        if (tid == 0) {
+#pragma unroll
+            for (int c = 0; c < kF / kD; ++c)
+                dec_mma(tmem + kColY, base + 16384u * c, base + 65536u + 16384u * c, uB + kW2Hi + 8192 * c,
+                        uB + kW2Lo + 8192 * c, kD, SPLIT, c > 0);
+            tc::mma_commit(mb);
+        }
         wait_mma();
         if (!ok) break;
+        // the FFN-out product has read the operand: the next layer's Wqkv
+        // comes in over its low part
+        if (l + 1 < g.L) {
+            ++wissued;
+            if (tid == 0) issue_wqkv(l + 1);
+        }
         {
             // h += FFN + b2, in the shared rows
             const float *b2 = g.b2[l];
