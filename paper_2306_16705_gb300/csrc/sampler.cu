@@ -254,29 +254,33 @@ __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *
 }
 
 // the same exclusive scan in one CTA for short lists (n <= kScanOne): warp w
-// takes a contiguous segment; pass 1 sums it (four 32-element loads in
-// flight), the 32 segment totals are scanned, pass 2 walks the segment again
-// (loads batched the same way) with a shuffle scan per 32 elements and a
-// running carry starting at the segment's offset; *total = the sum
+// takes a contiguous segment (a multiple of 512); pass 1 sums it 512 elements
+// at a time (16 loads in flight per lane), the 32 segment totals are scanned,
+// pass 2 walks the segment again the same way with a 32-bit shuffle scan per
+// 32 elements (a piece of at most 4 x 32 children) and a running 64-bit carry
+// starting at the segment's offset; *total = the sum
 constexpr int kScanOne = 65536;
 __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ in, int64_t n,
                                                   int64_t *__restrict__ out, int64_t *__restrict__ total,
                                                   const int64_t *__restrict__ n_dev) {
+    constexpr int kB = 16;  // 32-element pieces per batch
     __shared__ int64_t wsum[32];
     if (n_dev) n = *n_dev;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t seg = ((n + 31) / 32 + 127) / 128 * 128;  // elements per warp, a multiple of 128
+    const int64_t seg = ((n + 31) / 32 + 32 * kB - 1) / (32 * kB) * (32 * kB);  // elements per warp
     const int64_t b = min(n, warp * seg), e = min(n, b + seg);
     int64_t part = 0;
-    for (int64_t i0 = b; i0 < e; i0 += 128) {
-        int32_t x[4];
+    for (int64_t i0 = b; i0 < e; i0 += 32 * kB) {
+        int32_t x[kB];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kB; ++k) {
             const int64_t i = i0 + 32 * k + lane;
             x[k] = i < e ? in[i] : 0;
         }
+        int32_t sx = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) part += x[k];
+        for (int k = 0; k < kB; ++k) sx += x[k];
+        part += sx;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -293,23 +297,23 @@ __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ i
     }
     __syncthreads();
     int64_t carry = warp > 0 ? wsum[warp - 1] : 0;
-    for (int64_t i0 = b; i0 < e; i0 += 128) {
-        int32_t x[4];
+    for (int64_t i0 = b; i0 < e; i0 += 32 * kB) {
+        int32_t x[kB];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kB; ++k) {
             const int64_t i = i0 + 32 * k + lane;
             x[k] = i < e ? in[i] : 0;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int64_t v = x[k];
+        for (int k = 0; k < kB; ++k) {
+            int32_t v = x[k];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
                 if (lane >= o) v += u;
             }
             const int64_t i = i0 + 32 * k + lane;
-            if (i < e) out[i] = carry + v - x[k];
+            if (i < e) out[i] = carry + (int64_t)(v - x[k]);
             carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
@@ -321,55 +325,12 @@ __global__ void __launch_bounds__(1024) k_scan_one(const int32_t *__restrict__ i
 // key/value cache each child's ancestors are its parent's plus the parent's
 // own node g_cur + i at depth `step` (the tables are depth-major, [T][cap]:
 // a warp's lanes write consecutive entries of one depth)
-__global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
-                       const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
-                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, const int32_t *__restrict__ anc,
-                       int32_t *__restrict__ nanc, int64_t g_cur, DevStatus *st, const int64_t *__restrict__ n_dev,
-                       const int64_t *__restrict__ g_dev) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (n_dev) {
-        n = *n_dev;
-        g_cur = *g_dev;
-    }
-    if (i >= n) return;
-    int64_t j = off[i];
-    const int p = T - 1 - step;  // orbital of this token
-    for (int v = 0; v < 4; ++v) {
-        const uint64_t c = counts[i * 4 + v];
-        if (c == 0) continue;
-        if (j >= cap) {
-            record_status(st, NNQS_E_TABLE_FULL, i);
-            return;
-        }
-        for (int w = 0; w < W; ++w) npref[j * W + w] = pref[i * W + w];
-        if (v & 1) npref[j * W + ((2 * p) >> 6)] |= 1ull << ((2 * p) & 63);
-        if (v & 2) npref[j * W + ((2 * p + 1) >> 6)] |= 1ull << ((2 * p + 1) & 63);
-        nw[j] = c;
-        if (nanc) {
-            for (int lev = 0; lev < step; ++lev) nanc[lev * cap + j] = anc[lev * cap + i];
-            nanc[step * cap + j] = (int32_t)(g_cur + i);
-        }
-        ++j;
-    }
-}
-
-// level 0 of the device-count walk: the empty prefix holds all n_samples =
-// args[0] samples; level sizes {1, 0}, first node 0
-__global__ void k_level0(uint64_t *pref, int W, uint64_t *w, int64_t *cnt, const uint64_t *args) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int k = 0; k < W; ++k) pref[k] = 0;
-    w[0] = args[0];
-    cnt[0] = 1;
-    cnt[1] = 0;
-    cnt[2] = 0;
-}
-
 // end of a step with the counts on the device: cnt[cur ^ 1] = the next
 // level's size (the scan's total, clamped to the capacity after recording
 // NNQS_E_TABLE_FULL), cnt[2] += this level's size (the first tree node of the
 // next level)
-__global__ void k_advance(int64_t *cnt, int cur, const int64_t *__restrict__ total, int64_t cap, DevStatus *st) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void advance_counts(int64_t *cnt, int cur, const int64_t *total, int64_t cap,
+                                               DevStatus *st) {
     int64_t nn = *total;
     if (nn > cap) {
         record_status(st, NNQS_E_TABLE_FULL, nn);
@@ -379,13 +340,72 @@ __global__ void k_advance(int64_t *cnt, int cur, const int64_t *__restrict__ tot
     cnt[cur ^ 1] = nn;
 }
 
+__global__ void k_emit(const uint64_t *__restrict__ pref, const uint64_t *__restrict__ counts,
+                       const int64_t *__restrict__ off, int64_t n, int W, int T, int step, int64_t cap,
+                       uint64_t *__restrict__ npref, uint64_t *__restrict__ nw, const int32_t *__restrict__ anc,
+                       int32_t *__restrict__ nanc, int64_t g_cur, DevStatus *st, const int64_t *__restrict__ n_dev,
+                       const int64_t *__restrict__ g_dev, int64_t *adv, int cur, const int64_t *__restrict__ total) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n_dev) {
+        n = *n_dev;
+        g_cur = *g_dev;
+    }
+    if (i < n) {
+        int64_t j = off[i];
+        const int p = T - 1 - step;  // orbital of this token
+        for (int v = 0; v < 4; ++v) {
+            const uint64_t c = counts[i * 4 + v];
+            if (c == 0) continue;
+            if (j >= cap) {
+                record_status(st, NNQS_E_TABLE_FULL, i);
+                break;
+            }
+            for (int w = 0; w < W; ++w) npref[j * W + w] = pref[i * W + w];
+            if (v & 1) npref[j * W + ((2 * p) >> 6)] |= 1ull << ((2 * p) & 63);
+            if (v & 2) npref[j * W + ((2 * p + 1) >> 6)] |= 1ull << ((2 * p + 1) & 63);
+            nw[j] = c;
+            if (nanc) {
+                for (int lev = 0; lev < step; ++lev) nanc[lev * cap + j] = anc[lev * cap + i];
+                nanc[step * cap + j] = (int32_t)(g_cur + i);
+            }
+            ++j;
+        }
+    }
+    if (adv) {
+        // device-side counts: the last block to finish advances them (every
+        // other block read them before its arrival); adv[3] counts arrivals
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned long long done = atomicAdd(reinterpret_cast<unsigned long long *>(adv + 3), 1ull);
+            if (done == gridDim.x - 1) {
+                __threadfence();
+                advance_counts(adv, cur, total, cap, st);
+                adv[3] = 0;
+            }
+        }
+    }
+}
+
+// level 0 of the device-count walk: the empty prefix holds all n_samples =
+// args[0] samples; level sizes {1, 0}, first node 0, no emit arrivals yet
+__global__ void k_level0(uint64_t *pref, int W, uint64_t *w, int64_t *cnt, const uint64_t *args) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < W; ++k) pref[k] = 0;
+    w[0] = args[0];
+    cnt[0] = 1;
+    cnt[1] = 0;
+    cnt[2] = 0;
+    cnt[3] = 0;
+}
+
 struct SLayout {
     uint64_t *pref[2], *w[2], *counts;
     double *cond;
     int32_t *nchild;
     int64_t *off, *bsum, *total;
     int32_t *anc[2];  // key/value cache: ancestor tables [T][cap] of the current and next level
-    int64_t *cnt;     // device-side counts: level sizes [2], first node of the current level
+    int64_t *cnt;     // device-side counts: level sizes [2], first node of the current level, k_emit arrivals
     uint64_t *args;   // device copies of n_samples and seed (read by the device-count walk)
     char *region;
     int64_t kv_nodes;
@@ -487,8 +507,8 @@ nnqs_status walk_kernels(const nnqs_model *M, const float *params, int prec, int
             NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(cap, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, cap, W, T, t,
                                                                               cap, L.pref[cur ^ 1], L.w[cur ^ 1],
                                                                               L.anc[cur], L.anc[cur ^ 1], 0, st,
-                                                                              L.cnt + cur, L.cnt + 2));
-            NNQS_LAUNCH("k_emit", s, k_advance<<<1, 32, 0, s>>>(L.cnt, cur, L.total, cap, st));
+                                                                              L.cnt + cur, L.cnt + 2, L.cnt, cur,
+                                                                              L.total));
             cur ^= 1;
         }
     }
@@ -687,7 +707,7 @@ extern "C" nnqs_status nnqs_sample(const nnqs_model *M, const float *params, uin
         NNQS_LAUNCH("k_emit", s, k_emit<<<grid_for(n, 128), 128, 0, s>>>(L.pref[cur], L.counts, L.off, n, W, T, t,
                                                                          max_unique, L.pref[cur ^ 1], L.w[cur ^ 1],
                                                                          L.anc[cur], L.anc[cur ^ 1], g_cur, st,
-                                                                         nullptr, nullptr));
+                                                                         nullptr, nullptr, nullptr, 0, nullptr));
         cur ^= 1;
         g_cur += n;
         n = next;
