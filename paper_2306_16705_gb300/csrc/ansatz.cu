@@ -1837,7 +1837,7 @@ constexpr int kDecMaxLayers = 16;
 struct DecodeArgs {
     int64_t n;
     int rpc;  // prefixes per CTA (<= 128; rows past it in the 128-row tile are idle)
-    float *pool;  // [node][L][192] q|k|v
+    float *pool;  // [node][L][192] q|k|v (the fused step writes k|v only: its q stays on chip)
     int L, Tm, t;
     int64_t g0;
     const int32_t *anc;  // depth-major ancestor nodes: anc[j * anc_stride + i], depths j < t
@@ -1977,12 +1977,15 @@ __device__ __forceinline__ void dec_layernorm_row_f32(const float *sH, int r, co
 // keys and values of the NR rows are loaded together.  Threads hh = 0..H-1
 // of a row group sit in consecutive lanes, so a warp's load covers whole
 // 256-byte key (or value) segments of a few rows.
-// Rows at or past n (the tail of the last CTA) read row `safe` (a valid row)
-// instead and give zeros.
+// The rows' q come from qslab (the CTA's tile, [128][64] FP32 with 16-byte
+// granules XOR-swizzled by the row; tile row = row - safe).  Rows at or past
+// n (the tail of the last CTA) read row `safe` (a valid row) instead and give
+// zeros.
 template <int DH, int NR>
-__device__ __forceinline__ void dec_attention_rows(const float *__restrict__ pool, const int32_t *__restrict__ anc,
-                                                   int64_t anc_stride, int64_t g0, int64_t r0, int64_t safe, int64_t n,
-                                                   int t, int L, int l, int hh, float (&o)[NR][DH]) {
+__device__ __forceinline__ void dec_attention_rows(const float *__restrict__ pool, const float *qslab,
+                                                   const int32_t *__restrict__ anc, int64_t anc_stride, int64_t g0,
+                                                   int64_t r0, int64_t safe, int64_t n, int t, int L, int l, int hh,
+                                                   float (&o)[NR][DH]) {
     constexpr int d = dec::kD;
     const int64_t row = 3 * (int64_t)d;
     const float scale = score_scale<float, DH>();
@@ -1993,15 +1996,22 @@ __device__ __forceinline__ void dec_attention_rows(const float *__restrict__ poo
     for (int k = 0; k < NR; ++k) {
         ok[k] = r0 + k < n;
         rr[k] = ok[k] ? r0 + k : safe;
-        const float *qp = pool + ((g0 + rr[k]) * L + l) * row + hh * DH;
+        const int tr = (int)(rr[k] - safe);  // tile row (safe = the CTA's first row)
 #pragma unroll
-        for (int c = 0; c < DH; ++c) {
-            qv[k][c] = qp[c] * scale;
-            acc[k][c] = 0.f;
+        for (int e = 0; e < DH / 4; ++e) {
+            const int gi = hh * (DH / 4) + e;
+            const float4 q4 = *reinterpret_cast<const float4 *>(qslab + tr * 64 + 4 * (gi ^ (tr & 15)));
+            qv[k][4 * e] = q4.x * scale;
+            qv[k][4 * e + 1] = q4.y * scale;
+            qv[k][4 * e + 2] = q4.z * scale;
+            qv[k][4 * e + 3] = q4.w * scale;
         }
+#pragma unroll
+        for (int c = 0; c < DH; ++c) acc[k][c] = 0.f;
         m[k] = neg_inf<float>();
         lsum[k] = 0.f;
     }
+    __syncthreads();  // every q is read before the outputs go to the same tile
     // keys and values of step j + 1 load while step j is computed (the last
     // prefetch rereads the row's own node); node ids are read one step further
     // ahead
@@ -2227,14 +2237,16 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
                 bulk_g2s(bB + kW2Lo, g.t2[l] + kD * kF, bf, wb);
             }
         }
-        // q|k|v + bias into the pool rows of the new nodes, 64 columns at a
-        // time through the (free) A tile: TMEM -> shared (thread = row, 16-byte
+        // k|v + bias into the pool rows of the new nodes, 64 columns at a time
+        // through the (free) A tile: TMEM -> shared (thread = row, 16-byte
         // granules XOR-swizzled by the row) -> global (16 threads per row, each
-        // row a contiguous 256-byte segment)
+        // row a contiguous 256-byte segment); q + bias last, left in the tile
+        // for this step's attention (only the rows' own attention reads it)
+        float *slab = reinterpret_cast<float *>(aHi);
         {
             const float *bq = g.bqkv[l];
-            float *slab = reinterpret_cast<float *>(aHi);
-            for (int c = 0; c < kQKV / 64; ++c) {
+            for (int cc = 1; cc <= kQKV / 64; ++cc) {
+                const int c = cc % (kQKV / 64);  // 1 (k), 2 (v), then 0 (q)
 #pragma unroll
                 for (int b = 0; b < kCW / 16; ++b) {
                     const int cl = kCW * cq + 16 * b;  // column within the chunk
@@ -2251,6 +2263,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
                     }
                 }
                 __syncthreads();
+                if (c == 0) break;
 #pragma unroll
                 for (int i = 0; i < kRows * 16 / kThreads; ++i) {
                     const int it = tid + kThreads * i;
@@ -2269,7 +2282,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
             const int hh = tid % H;
             const int r0 = (tid / H) * NR;
             float o[NR][DH];
-            dec_attention_rows<DH, NR>(g.pool, g.anc, g.anc_stride, g0, m0 + r0, m0, n_cta, g.t, g.L, l, hh, o);
+            dec_attention_rows<DH, NR>(g.pool, slab, g.anc, g.anc_stride, g0, m0 + r0, m0, n_cta, g.t, g.L, l, hh, o);
 #pragma unroll
             for (int k = 0; k < NR; ++k)
 #pragma unroll
