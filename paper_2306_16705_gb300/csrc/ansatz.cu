@@ -48,12 +48,6 @@ template <>
 __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 template <>
 __device__ __forceinline__ float log_<float>(float x) { return logf(x); }
-template <class R>
-__device__ __forceinline__ R rsqrt_(R x);
-template <>
-__device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
-template <>
-__device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
 // Units of the attention softmax.  FP64: natural units and exp().  FP32:
 // base-2 units -- the scores carry a factor log2 e, folded into the query
@@ -3012,7 +3006,7 @@ template <class R>
 nnqs_status forward_chunk(const nnqs_model *M, const Views<R> &V, const uint64_t *x, int64_t C, Acts<R> &A,
                           double2 *out, DevStatus *st, int64_t row_offset, const TcWeights *tcw, cudaStream_t s,
                           int S = 0, double *cond = nullptr) {
-    const int Tm = M->T, d = M->d, L = M->L, F = M->F, P = M->P, H = M->H, W = M->W, N = M->N;
+    const int Tm = M->T, d = M->d, L = M->L, F = M->F, H = M->H, W = M->W;
     const int T = S > 0 ? S : Tm;  // sequence length of this pass
     const int64_t rows = C * T;
     if (d % 4 == 0)
