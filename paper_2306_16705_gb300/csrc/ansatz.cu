@@ -2201,12 +2201,17 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
     };
     const int q4 = warp & 3, cq = warp >> 2, row = 32 * q4 + lane;
     const uint32_t tl = tmem + (uint32_t(32 * q4) << 16);
+    // warps whose rows all lie past the CTA's share skip the per-row work
+    // (the products keep rows apart, and those rows are never stored): the
+    // TMEM-lane quadrant of 32 rows, the LayerNorms' 8 rows per warp
+    const int rows_live = (int)(n_cta - m0);
+    const bool q_live = 32 * q4 < rows_live, ln_live = 8 * warp < rows_live;
 
     const int64_t act_stride = 2 * (int64_t)g.L * kD;  // floats per node of g.act
     for (int l = 0; l < g.L && ok; ++l) {
         if (g.act) dec_store_rows(sH, g.act + 2 * l * kD, g0 + m0, n_cta - m0, act_stride);
         // ---- LayerNorm 1 -> qkv
-        dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
+        if (ln_live) dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln1g[l], g.ln1b[l], aHi, aLo, SPLIT);
         wait_weights();  // Wqkv of layer l
         sync_async();
         if (!ok) break;
@@ -2242,7 +2247,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
             for (int cc = 1; cc <= kQKV / 64; ++cc) {
                 const int c = cc % (kQKV / 64);  // 1 (k), 2 (v), then 0 (q)
 #pragma unroll
-                for (int b = 0; b < kCW / 16; ++b) {
+                for (int b = 0; b < (q_live ? kCW / 16 : 0); ++b) {
                     const int cl = kCW * cq + 16 * b;  // column within the chunk
                     uint32_t r16[16];
                     tc::tmem_ld16(tl + kColQKV + 64 * c + cl, r16);
@@ -2300,7 +2305,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
             // h += attn Wo^T + bo (kCW columns per thread)
             const float *bo = g.bo[l];
 #pragma unroll
-            for (int b = 0; b < kCW / 16; ++b) {
+            for (int b = 0; b < (q_live ? kCW / 16 : 0); ++b) {
                 const int c0 = kCW * cq + 16 * b;
                 uint32_t r16[16];
                 tc::tmem_ld16(tl + kColO + c0, r16);
@@ -2316,7 +2321,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         // ---- LayerNorm 2 -> FFN: U = LN2 W1^T as one N = 256 product (the
         // four 64-row chunks of the W1 image are consecutive), then GELU and
         // the FFN-out product (below)
-        dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
+        if (ln_live) dec_layernorm_row4(sH, tid >> 2, tid & 3, g.ln2g[l], g.ln2b[l], aHi, aLo, SPLIT);
         sync_async();
         if (tid == 0) {
             dec_mma(tmem + kColU, uA, uA2, uB + kW1Hi, uB + kW1Lo, kF, SPLIT, false);
@@ -2331,7 +2336,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
         // product in the order of the chunked walk, Y = sum_c G_c W2_c^T
         const float *b1 = g.b1[l];
 #pragma unroll 1
-        for (int c = 0; c < kF / kD; ++c) {
+        for (int c = 0; c < (q_live ? kF / kD : 0); ++c) {
             float x[kCW];
 #pragma unroll
             for (int b = 0; b < kCW / 16; ++b) {
@@ -2372,7 +2377,7 @@ __global__ void __launch_bounds__(dec::kThreads, 1) k_decode_step(const __grid_c
             // h += FFN + b2, in the shared rows
             const float *b2 = g.b2[l];
 #pragma unroll
-            for (int b = 0; b < kCW / 16; ++b) {
+            for (int b = 0; b < (q_live ? kCW / 16 : 0); ++b) {
                 const int c0 = kCW * cq + 16 * b;
                 uint32_t r16[16];
                 tc::tmem_ld16(tl + kColY + c0, r16);
