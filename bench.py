@@ -39,9 +39,9 @@ TENSOR_KERNELS = ("k_fwd_fused", "k_bwd_attn", "k_bwd_ffn", "k_decode_step", "k_
 # DRAM read + write bytes per launch of this step's kernels, from ncu captures of the current kernels; a
 # kernel leaves this table when it changes.  The reverse-mode halves: one launch each at 16,384 samples of
 # 20 tokens (profiles/k_bwd_fused_energy_grad_n40.md); k_decode_step: the mean over the 20 launches of one
-# sampling of this workload, 0.9 MB at the first token step to 494 MB at the last
+# sampling of this workload, 0.9 MB at the first token step to 477 MB at the last
 # (profiles/k_decode_step_sample_n40.md).
-KERNEL_TRAFFIC_BYTES = {"k_bwd_ffn": 167.9e6 + 50.0e6, "k_bwd_attn": 167.9e6 + 48.1e6, "k_decode_step": 164.8e6}
+KERNEL_TRAFFIC_BYTES = {"k_bwd_ffn": 167.9e6 + 50.0e6, "k_bwd_attn": 167.9e6 + 48.1e6, "k_decode_step": 155.9e6}
 
 
 def parse():

@@ -3625,9 +3625,12 @@ nnqs_status launch_decode_step(const DecodeArgs &g, cudaStream_t s) {
 // depth t (method FLOPs) and its bytes: per layer and prefix the keys and
 // values of its t ancestors and itself read, its q | k | v row written, and
 // the weight images once
+// method FLOPs of the step's products; bytes: per row and layer the keys and
+// values of its t + 1 ancestors (itself included) read and its own k|v row
+// written, and the layer's BF16 weight images
 void note_decode_work(int64_t n, bool split, int L, int t) {
     note_work("k_decode_step", L * 2.0 * double(n) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF),
-              L * (double(n) * 4.0 * (2.0 * dec::kD * (t + 1) + dec::kQKV) +
+              L * (double(n) * 4.0 * (2.0 * dec::kD * (t + 1) + 2.0 * dec::kD) +
                    2.0 * (split ? 2.0 : 1.0) * (4.0 * dec::kD * dec::kD + 2.0 * dec::kD * dec::kF)));
 }
 
