@@ -129,10 +129,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU(x) = x Phi(x) with erf of Abramowitz and Stegun (1964), eq. 7.1.26:
+// erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-z^2}, t = 1 / (1 + p z)
+// for z >= 0, odd in z, absolute error at most 1.5e-7 (far below the 2^-16
+// relative resolution of the split-BF16 operands the values feed); branch-free,
+// two special-function instructions.  The fused forward and reverse mode use
+// the same form and operation order.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// 1 - erf(|x| / sqrt 2), from the polynomial, and e = exp(-x^2 / 2)
+__device__ __forceinline__ float erfc_as(float x, float &e) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    e = ex2_approx(-(z * z) * 1.44269504088896340736f);
+    return poly * e;
+}
+__device__ __forceinline__ float gelu_f(float x) {
+    float e;
+    const float erf_abs = 1.0f - erfc_as(x, e);
+    return 0.5f * x * (1.0f + copysignf(erf_abs, x));
+}
 // d gelu / dx = Phi(x) + x phi(x)
 __device__ __forceinline__ float gelu_grad_f(float x) {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143267794f;
+    float e;
+    const float phi_cdf = 0.5f * (1.0f + copysignf(1.0f - erfc_as(x, e), x));
+    return phi_cdf + x * e * 0.39894228040143267794f;
 }
 
 __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
