@@ -23,7 +23,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "dev_common.cuh"
 #include "internal.h"
@@ -551,29 +550,19 @@ int num_sms() {
 // Scratch for nnqs_eloc_sa_noalloc: one file-scope device array, present on
 // every GPU that loads this library until the process exits.  Host code must
 // not use the symbol itself as a device address: its device address is
-// looked up once per device with cudaGetSymbolAddress.
+// looked up with cudaGetSymbolAddress.
 namespace nnqs {
 namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
-
-// device address of the scratch array on the current device (looked up on
-// the first call per device, with that device current)
+// device address of the scratch array in the current context, looked up on
+// every call (an address kept from an earlier call would outlive a context
+// reset)
 nnqs_status noalloc_scratch(void **out) {
-    int dev = 0;
-    NNQS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(NNQS_E_UNSUPPORTED, "device index beyond 63");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_addr[dev] == nullptr) {
-        void *p = nullptr;
-        NNQS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    NNQS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = p;
     return NNQS_OK;
 }
 }  // namespace
