@@ -193,3 +193,24 @@ def test_paper_sample_schedule():
     assert [paper_n_samples(i) for i in (0, 99)] == [10 ** 5] * 2
     assert [paper_n_samples(i) for i in (100, 199, 200, 700)] == [10 ** 6, 10 ** 6, 10 ** 7, 10 ** 12]
     assert paper_n_samples(10 ** 5) == 10 ** 12
+
+
+def test_tree_reuse_host_logic():
+    """The host-side rules of the energy gradient from the sampler's tree
+    (nnqs_energy_grad_sampled): it applies to d_model = 64 with BF16 or split
+    BF16 arithmetic and at most 65,536 unique samples, and the keep-mode
+    sampler workspace holds the kept rows on top of the plain one (2 L + 1
+    rows of 64 floats per tree node, at least T max_unique nodes)."""
+    lib = B.lib()
+    m = B.Model(40, 10, 10, 64, 4, 8)
+    assert lib.nnqs_energy_grad_sampled_supported(m.handle, B.BF16X3, 1 << 15) == 1
+    assert lib.nnqs_energy_grad_sampled_supported(m.handle, B.MIXED, 1 << 15) == 1
+    assert lib.nnqs_energy_grad_sampled_supported(m.handle, B.FP32, 1 << 15) == 0
+    assert lib.nnqs_energy_grad_sampled_supported(m.handle, B.FP64, 1 << 15) == 0
+    assert lib.nnqs_energy_grad_sampled_supported(m.handle, B.BF16X3, 1 << 17) == 0
+    small = B.Model(12, 3, 3, 32, 2, 4)
+    assert lib.nnqs_energy_grad_sampled_supported(small.handle, B.BF16X3, 512) == 0
+    mu = 1 << 12
+    plain = lib.nnqs_sample_workspace_size(m.handle, mu, B.BF16X3, 0)
+    keep = lib.nnqs_sample_workspace_size(m.handle, mu, B.BF16X3, B.SAMPLE_KEEP)
+    assert keep - plain >= 20 * mu * (2 * 4 + 1) * 64 * 4
