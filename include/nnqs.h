@@ -57,7 +57,7 @@ typedef enum {
     NNQS_E_TIMEOUT = 5,      /* a bounded device wait gave up */
     NNQS_E_SECTOR = 6,       /* a sample breaks the (n_alpha, n_beta) sector */
     NNQS_E_NONFINITE = 7,    /* NaN or Inf met in an input or result */
-    NNQS_E_UNSUPPORTED = 8,  /* valid request this build does not implement */
+    NNQS_E_UNSUPPORTED = 8,  /* valid request the library does not implement */
     NNQS_E_DUPLICATE = 9,    /* the sample table holds a bitstring twice */
     NNQS_E_WORKSPACE = 10    /* workspace null, misaligned or too small */
 } nnqs_status;

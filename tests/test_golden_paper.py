@@ -1,6 +1,6 @@
 """Pins against numbers the paper prints (tests/golden/paper_counts.txt).
 
-The paper's molecules need integrals this build does not have, so their
+The paper's molecules need integrals that are not available offline, so their
 printed string counts bound the oracle rather than fix it: a molecule's
 Hamiltonian is the generic one with some coefficients exactly zero, so its
 N_h can be at most the count the oracle's builder gives for dense generic
